@@ -1,0 +1,130 @@
+"""Oracle: plain, slow, obviously correct FP64 CPU reference (test infrastructure only).
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py``
+may import this package.  It shares no code with the CUDA path
+(``paper_2410_19075_gb300``) and never imports it.
+
+What it computes (each function cites the passage it follows):
+  * ``rhs``      -- node right-hand sides, coupling sums by brute force over every
+                    neighbour: Kuramoto-Sakaguchi Eq. (3) with m = 0, eps = 1 and
+                    Algorithm 1; FitzHugh-Nagumo Eq. (2) with a rotational coupling
+                    matrix; Hodgkin-Huxley Eq. (1) as the classic 4-variable neuron.
+  * ``rk4``      -- classic fixed-step fourth-order Runge-Kutta over the network.
+  * ``order_parameter`` -- Kuramoto order parameter |mean exp(i phi)| (the
+                    synchronization analysis of Section V).
+  * ``window_sum`` -- brute-force window sums of one quantity (ring: R neighbours
+                    each side, Section IV 1D networks; cube: periodic (2P+1)^3 box,
+                    index k*N1^2 + j*N1 + i, Section IV 3D networks).
+
+Parity pins for every function live in tests/test_oracle_pins.py.
+"""
+import ctypes
+import numpy as np
+
+from .build import build as _build
+
+KS, FHN, HH = 0, 1, 2
+RING, CUBE = 0, 1
+REVERSE, INCLUDE_SELF = 1, 2
+_DIM = {KS: 1, FHN: 2, HH: 4}
+_NPARAM = {KS: 3, FHN: 4, HH: 8}
+
+_lib = None
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int64)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(_build())
+        i64, c_int, c_double = ctypes.c_int64, ctypes.c_int, ctypes.c_double
+        _lib.orc_rhs.argtypes = [c_int, c_int, i64, i64, _dp, c_int, _dp, _dp, _dp, c_int, c_int]
+        _lib.orc_rk4.argtypes = [c_int, c_int, i64, i64, _dp, c_int, _dp, _dp, i64, c_double, _dp, c_int, c_int]
+        _lib.orc_window_sum.argtypes = [c_int, i64, i64, _dp, i64, _ip, _dp, c_int]
+        _lib.orc_rhs_sampled.argtypes = [c_int, c_int, i64, i64, _dp, c_int, _dp, _dp, i64, _ip, _dp, c_int, c_int]
+        _lib.orc_order_parameter.argtypes = [i64, _dp]
+        _lib.orc_order_parameter.restype = c_double
+        for name in ("orc_hh_alpha_m", "orc_hh_beta_m", "orc_hh_alpha_h", "orc_hh_beta_h",
+                     "orc_hh_alpha_n", "orc_hh_beta_n"):
+            fn = getattr(_lib, name)
+            fn.argtypes = [c_double]
+            fn.restype = c_double
+    return _lib
+
+
+def _d(a):
+    return a.ctypes.data_as(_dp) if a is not None else None
+
+
+def _arr(a, n=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if n is not None and a.size != n:
+        raise ValueError(f"expected {n} values, got {a.size}")
+    return a
+
+
+def nodes_of(topo, N):
+    return N ** 3 if topo == CUBE else N
+
+
+def _check(st, what):
+    if st != 0:
+        raise ValueError(f"oracle {what} failed with status {st}")
+
+
+def rhs(model, topo, N, R, params, x, node_param=None, flags=0, threads=0):
+    """Right-hand side f(x) of every node (SoA in, SoA out)."""
+    n = nodes_of(topo, N) * _DIM[model]
+    x = _arr(x, n)
+    p = _arr(params)
+    npar = _arr(node_param, nodes_of(topo, N)) if node_param is not None else None
+    k = np.empty(n)
+    _check(lib().orc_rhs(model, topo, N, R, _d(p), p.size, _d(npar), _d(x), _d(k), flags, threads), "rhs")
+    return k
+
+
+def rhs_sampled(model, topo, N, R, params, x, query, node_param=None, flags=0, threads=0):
+    """Right-hand side of the listed nodes only: array (d, len(query))."""
+    x = _arr(x, nodes_of(topo, N) * _DIM[model])
+    p = _arr(params)
+    q = np.ascontiguousarray(query, dtype=np.int64)
+    npar = _arr(node_param, nodes_of(topo, N)) if node_param is not None else None
+    out = np.empty(_DIM[model] * q.size)
+    _check(lib().orc_rhs_sampled(model, topo, N, R, _d(p), p.size, _d(npar), _d(x), q.size,
+                                 q.ctypes.data_as(_ip), _d(out), flags, threads), "rhs_sampled")
+    return out.reshape(_DIM[model], q.size)
+
+
+def rk4(model, topo, N, R, params, y0, n_steps, dt, node_param=None, flags=0, threads=0,
+        record_order=False):
+    """Advance y0 by n_steps classic RK4 steps of size dt.  Returns (y, order) where
+    order holds the order parameter at t = 0 and after each step (Kuramoto only)."""
+    y = _arr(y0, nodes_of(topo, N) * _DIM[model]).copy()
+    p = _arr(params)
+    npar = _arr(node_param, nodes_of(topo, N)) if node_param is not None else None
+    order = np.empty(n_steps + 1) if (record_order and model == KS) else None
+    _check(lib().orc_rk4(model, topo, N, R, _d(p), p.size, _d(npar), _d(y), n_steps, float(dt),
+                         _d(order), flags, threads), "rk4")
+    return y, order
+
+
+def window_sum(topo, N, R, f, query=None, flags=0):
+    """Brute-force sum of f over the window of each queried node (all nodes by default)."""
+    f = _arr(f, nodes_of(topo, N))
+    q = np.arange(nodes_of(topo, N), dtype=np.int64) if query is None else np.ascontiguousarray(query, dtype=np.int64)
+    out = np.empty(q.size)
+    _check(lib().orc_window_sum(topo, N, R, _d(f), q.size, q.ctypes.data_as(_ip), _d(out), flags), "window_sum")
+    return out
+
+
+def order_parameter(phi):
+    phi = _arr(phi)
+    return lib().orc_order_parameter(phi.size, _d(phi))
+
+
+def hh_rates(V):
+    """(alpha_m, beta_m, alpha_h, beta_h, alpha_n, beta_n) at membrane voltage V (mV)."""
+    L = lib()
+    return tuple(getattr(L, n)(float(V)) for n in ("orc_hh_alpha_m", "orc_hh_beta_m", "orc_hh_alpha_h",
+                                                     "orc_hh_beta_h", "orc_hh_alpha_n", "orc_hh_beta_n"))

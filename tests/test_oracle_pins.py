@@ -1,0 +1,412 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+None of these compares the oracle with itself: each expected value comes from a
+closed form (twisted and in-phase states, Eq. (3)), an invariant (antisymmetry,
+roll equivariance), a derivative of the equations (Eq. (2), (3), (1)), a
+textbook table (HH rates), an independent integrator (scipy DOP853) or brute
+force written from the geometric definition of the window.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2410_19075_gb300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- geometry
+def ring_member(N, R, i, j, include_self=False):
+    d = abs(i - j) % N
+    d = min(d, N - d)
+    return (d <= R) and (include_self or d != 0)
+
+
+def cube_member(N1, P, a, b, include_self=False):
+    ca = (a % N1, (a // N1) % N1, a // (N1 * N1))
+    cb = (b % N1, (b // N1) % N1, b // (N1 * N1))
+    ds = []
+    for x, y in zip(ca, cb):
+        d = abs(x - y) % N1
+        ds.append(min(d, N1 - d))
+    return all(d <= P for d in ds) and (include_self or any(d != 0 for d in ds))
+
+
+def twisted_ring_omega(N, R, q, omega, mu, alpha):
+    """Closed form: phi_j = 2 pi q j / N rotates uniformly at
+    omega - (mu/R) sin(alpha) sin(R k/2) cos((R+1) k/2) / sin(k/2), k = 2 pi q / N."""
+    k = 2 * math.pi * q / N
+    return omega - (mu / R) * math.sin(alpha) * math.sin(R * k / 2) * math.cos((R + 1) * k / 2) / math.sin(k / 2)
+
+
+def twisted_cube_omega(N1, P, q, omega, mu, alpha):
+    """Plane wave along one axis on the (2P+1)^3 box without self:
+    omega + mu sin(alpha) [1 - (2P+1)^2 D] / ((2P+1)^3 - 1), D = sin((2P+1)k/2)/sin(k/2)."""
+    k = 2 * math.pi * q / N1
+    w = 2 * P + 1
+    D = math.sin(w * k / 2) / math.sin(k / 2)
+    return omega + mu * math.sin(alpha) * (1 - w * w * D) / (w ** 3 - 1)
+
+
+# ---------------------------------------------------------------- Kuramoto
+@pytest.mark.parametrize("topo,N,R", [(oracle.RING, 16, 5), (oracle.RING, 11, 5), (oracle.CUBE, 5, 1), (oracle.CUBE, 7, 2)])
+def test_ks_in_phase_state_rotates_at_omega_minus_mu_sin_alpha(topo, N, R):
+    omega, mu, alpha = 0.3, 0.8, 1.46
+    n = oracle.nodes_of(topo, N)
+    y0 = np.full(n, 0.7)
+    y, order = oracle.rk4(oracle.KS, topo, N, R, [omega, mu, alpha], y0, 200, 0.01, record_order=True)
+    expect = 0.7 + (omega - mu * math.sin(alpha)) * 2.0
+    assert np.abs(y - expect).max() < 1e-12
+    assert np.abs(order - 1.0).max() < 1e-14
+
+
+@pytest.mark.parametrize("N,R,q", [(33, 7, 1), (33, 7, 3), (15, 7, 2), (64, 20, 5), (9, 1, 1)])
+def test_ks_ring_twisted_state_closed_form(N, R, q):
+    omega, mu, alpha = 0.1, 1.0, 1.46
+    j = np.arange(N)
+    y0 = 2 * math.pi * q * j / N + 0.25
+    T = 100
+    y, order = oracle.rk4(oracle.KS, oracle.RING, N, R, [omega, mu, alpha], y0, T, 0.01, record_order=True)
+    Om = twisted_ring_omega(N, R, q, omega, mu, alpha)
+    assert np.abs(y - y0 - Om * T * 0.01).max() < 1e-12
+    # order parameter of a twisted state (q not a multiple of N) is zero
+    assert np.abs(order).max() < 1e-13
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+@pytest.mark.parametrize("N1,P,q", [(7, 2, 1), (9, 3, 2), (5, 1, 2)])
+def test_ks_cube_twisted_state_closed_form(axis, N1, P, q):
+    omega, mu, alpha = -0.2, 1.0, 1.52
+    idx = np.arange(N1 ** 3)
+    coord = [idx % N1, (idx // N1) % N1, idx // (N1 * N1)][axis]
+    y0 = 2 * math.pi * q * coord / N1 - 1.0
+    T = 50
+    y, _ = oracle.rk4(oracle.KS, oracle.CUBE, N1, P, [omega, mu, alpha], y0, T, 0.01)
+    Om = twisted_cube_omega(N1, P, q, omega, mu, alpha)
+    assert np.abs(y - y0 - Om * T * 0.01).max() < 1e-12
+
+
+def test_ks_zero_coupling_is_pure_drift():
+    N, R = 40, 9
+    y0 = I.ks_phases(7, 0, N)
+    y, _ = oracle.rk4(oracle.KS, oracle.RING, N, R, [0.37, 0.0, 1.2], y0, 300, 0.01)
+    assert np.abs(y - (y0 + 0.37 * 3.0)).max() < 1e-12
+
+
+@pytest.mark.parametrize("topo,N,R", [(oracle.RING, 50, 12), (oracle.CUBE, 6, 2)])
+def test_ks_mean_phase_conserved_without_lag(topo, N, R):
+    n = oracle.nodes_of(topo, N)
+    y0 = I.ks_phases(8, 0, n)
+    y, _ = oracle.rk4(oracle.KS, topo, N, R, [0.0, 1.0, 0.0], y0, 200, 0.01)
+    assert abs(y.mean() - y0.mean()) < 1e-13
+    assert np.abs(y - y0).max() > 1e-3  # the dynamics did move
+
+
+def test_ks_include_self_twisted_closed_form():
+    N, R, q = 21, 6, 2
+    omega, mu, alpha = 0.0, 1.0, 1.3
+    k = 2 * math.pi * q / N
+    y0 = k * np.arange(N)
+    y, _ = oracle.rk4(oracle.KS, oracle.RING, N, R, [omega, mu, alpha], y0, 100, 0.01, flags=oracle.INCLUDE_SELF)
+    S = 1 + 2 * sum(math.cos(k * d) for d in range(1, R + 1))
+    Om = omega - mu * math.sin(alpha) * S / (2 * R + 1)
+    assert np.abs(y - y0 - Om).max() < 1e-12
+
+
+def _fd_jacobian(model, topo, N, R, params, x, h=1e-6, node_param=None):
+    n = x.size
+    J = np.empty((n, n))
+    for c in range(n):
+        xp = x.copy(); xp[c] += h
+        xm = x.copy(); xm[c] -= h
+        J[:, c] = (oracle.rhs(model, topo, N, R, params, xp, node_param) -
+                   oracle.rhs(model, topo, N, R, params, xm, node_param)) / (2 * h)
+    return J
+
+
+@pytest.mark.parametrize("topo,N,R", [(oracle.RING, 13, 4), (oracle.RING, 9, 4), (oracle.CUBE, 5, 1)])
+def test_ks_jacobian_matches_equation(topo, N, R):
+    """d/dphi_j of omega - (mu/K) sum sin(phi_i - phi_j + alpha) is
+    (mu/K) cos(phi_i - phi_j + alpha) for j in the window, 0 outside."""
+    omega, mu, alpha = 0.1, 0.9, 1.46
+    n = oracle.nodes_of(topo, N)
+    x = I.ks_phases(11, 0, n)
+    J = _fd_jacobian(oracle.KS, topo, N, R, [omega, mu, alpha], x)
+    member = ring_member if topo == oracle.RING else cube_member
+    K = 2 * R if topo == oracle.RING else (2 * R + 1) ** 3 - 1
+    for i in range(n):
+        diag = 0.0
+        for j in range(n):
+            if j == i:
+                continue
+            e = (mu / K) * math.cos(x[i] - x[j] + alpha) if member(N, R, i, j) else 0.0
+            diag -= e
+            assert abs(J[i, j] - e) < 1e-8, (i, j)
+        assert abs(J[i, i] - diag) < 1e-8
+
+
+# ---------------------------------------------------------------- FitzHugh-Nagumo
+def test_fhn_jacobian_matches_rotational_coupling():
+    N, R = 11, 3
+    eps, a, sigma, phi = 0.05, 0.5, 0.1, math.pi / 2 - 0.1
+    B = np.array([[math.cos(phi), math.sin(phi)], [-math.sin(phi), math.cos(phi)]])
+    x = I.fhn_state(12, 0, N)
+    J = _fd_jacobian(oracle.FHN, oracle.RING, N, R, [eps, a, sigma, phi], x)
+    K = 2 * R
+    u = x[:N]
+    scale = np.array([1 / eps, 1.0])
+    for i in range(N):
+        for j in range(N):
+            for r in range(2):
+                for c in range(2):
+                    got = J[r * N + i, c * N + j]
+                    if j == i:
+                        local = [[(1 - u[i] ** 2) / eps, -1 / eps], [1.0, 0.0]][r][c]
+                        e = local - sigma * B[r, c] * scale[r]
+                    elif ring_member(N, R, i, j):
+                        e = sigma * B[r, c] * scale[r] / K
+                    else:
+                        e = 0.0
+                    assert abs(got - e) < 2e-7, (i, j, r, c, got, e)
+
+
+def test_fhn_fixed_point_is_stationary():
+    N, R = 9, 2
+    a = 0.5
+    us, vs = -a, -a + a ** 3 / 3
+    x = np.concatenate([np.full(N, us), np.full(N, vs)])
+    k = oracle.rhs(oracle.FHN, oracle.RING, N, R, I.fhn_params(a=a), x)
+    assert np.abs(k).max() < 1e-15
+
+
+def test_fhn_synchronous_network_follows_single_node():
+    """All nodes equal: the coupling vanishes and every node follows Eq. (2)
+    for one uncoupled element, integrated here by scipy's DOP853."""
+    scipy_integrate = pytest.importorskip("scipy.integrate")
+    eps, a = 0.05, 0.5
+
+    def f(t, z):
+        u, v = z
+        return [(u - u ** 3 / 3 - v) / eps, u + a]
+
+    u0, v0 = 1.2, -0.4
+    sol = scipy_integrate.solve_ivp(f, (0, 1.0), [u0, v0], method="DOP853", rtol=1e-13, atol=1e-13)
+    N, R = 7, 3
+    x = np.concatenate([np.full(N, u0), np.full(N, v0)])
+    y, _ = oracle.rk4(oracle.FHN, oracle.RING, N, R, I.fhn_params(), x, 1000, 0.001)
+    assert np.abs(y[:N] - sol.y[0, -1]).max() < 1e-9
+    assert np.abs(y[N:] - sol.y[1, -1]).max() < 1e-9
+
+
+# ---------------------------------------------------------------- Hodgkin-Huxley
+def _golden(name):
+    out = {}
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            key, val, tol = line.split()
+            out[key] = (float(val), float(tol))
+    return out
+
+
+def _hh_rates_from_rhs(V):
+    """Extract alpha and beta from the oracle's gate equations:
+    dx/dt = alpha (1 - x) - beta x, so dx/dt = alpha at x = 0 and -beta at x = 1."""
+    N, R = 3, 1
+    p = I.hh_params(g=0.0)
+    out = {}
+    for x_val in (0.0, 1.0):
+        y = np.concatenate([np.full(N, V), np.full(N, x_val), np.full(N, x_val), np.full(N, x_val)])
+        k = oracle.rhs(oracle.HH, oracle.RING, N, R, p, y, node_param=np.zeros(N))
+        for g, name in ((1, "m"), (2, "h"), (3, "n")):
+            if x_val == 0.0:
+                out["alpha_" + name] = k[g * N]
+            else:
+                out["beta_" + name] = -k[g * N]
+    return out
+
+
+def test_hh_rates_match_textbook_values():
+    gold = _golden("hh_rest_gating.txt")
+    r = _hh_rates_from_rhs(-65.0)
+    for key in ("alpha_m", "beta_m", "alpha_h", "beta_h", "alpha_n", "beta_n"):
+        val, tol = gold[key]
+        assert abs(r[key] - val) <= tol, key
+    for g in "mhn":
+        val, tol = gold[g + "_inf"]
+        inf = r["alpha_" + g] / (r["alpha_" + g] + r["beta_" + g])
+        assert abs(inf - val) <= tol, g
+    val, tol = gold["alpha_m@-40"]
+    assert abs(_hh_rates_from_rhs(-40.0)["alpha_m"] - val) <= tol
+    val, tol = gold["alpha_n@-55"]
+    assert abs(_hh_rates_from_rhs(-55.0)["alpha_n"] - val) <= tol
+    # continuity across the removable singularities
+    for V, key, lim in ((-40.0, "alpha_m", 1.0), (-55.0, "alpha_n", 0.1)):
+        for dv in (1e-9, -1e-9, 1e-5, -1e-5):
+            assert abs(_hh_rates_from_rhs(V + dv)[key] - lim) < 1e-5
+
+
+def test_hh_rests_near_minus_65_and_fires_at_68_hz():
+    gold = _golden("hh_rest_gating.txt")
+    N, R = 3, 1
+    p = I.hh_params(g=0.0)
+    r = _hh_rates_from_rhs(-65.0)
+    gates = [r["alpha_" + g] / (r["alpha_" + g] + r["beta_" + g]) for g in "mhn"]
+    y0 = np.concatenate([np.full(N, -65.0)] + [np.full(N, v) for v in gates])
+    y, _ = oracle.rk4(oracle.HH, oracle.RING, N, R, p, y0, 5000, 0.01, node_param=np.zeros(N))
+    assert abs(y[0] + 65.0) < 0.05
+    # repetitive firing at I = 10
+    V = []
+    y = y0.copy()
+    for _ in range(120):
+        y, _ = oracle.rk4(oracle.HH, oracle.RING, N, R, p, y, 100, 0.01, node_param=np.full(N, 10.0))
+        V.append(y[0])
+    # coarse sampling at 1 ms is enough to count spikes over 120 ms
+    V = np.array(V)
+    ups = np.where((V[:-1] < -20) & (V[1:] >= -20))[0]
+    assert len(ups) >= 6
+    period = (ups[-1] - ups[1]) / (len(ups) - 2)
+    val, tol = gold["period_ms@I=10"]
+    assert abs(period - val) <= 1.0 + tol
+
+
+def test_hh_coupling_jacobian():
+    N, R = 9, 2
+    g, Cm = 0.1, 1.0
+    x = I.hh_state(13, 0, N)
+    iext = I.hh_iext(13, 0, N)
+    J = _fd_jacobian(oracle.HH, oracle.RING, N, R, I.hh_params(g=g, Cm=Cm), x, h=1e-5, node_param=iext)
+    K = 2 * R
+    for i in range(N):
+        for j in range(N):
+            if j == i:
+                continue
+            e = g / (K * Cm) if ring_member(N, R, i, j) else 0.0
+            assert abs(J[i, j] - e) < 1e-7
+            # gates of other nodes never enter
+            for v in (1, 2, 3):
+                assert abs(J[i, v * N + j]) < 1e-9
+
+
+def test_hh_uncoupled_network_follows_single_neuron():
+    """g = 0: every node follows the classic HH neuron; scipy DOP853 of the same
+    textbook equations is the reference, and RK4's global error drops ~16x per
+    halving of dt."""
+    scipy_integrate = pytest.importorskip("scipy.integrate")
+
+    def xe(x):
+        return 1.0 if x == 0 else x / -math.expm1(-x)
+
+    def f(t, z, I_ext):
+        V, m, h, n = z
+        am, bm = xe((V + 40) / 10), 4 * math.exp(-(V + 65) / 18)
+        ah, bh = 0.07 * math.exp(-(V + 65) / 20), 1 / (1 + math.exp(-(V + 35) / 10))
+        an, bn = 0.1 * xe((V + 55) / 10), 0.125 * math.exp(-(V + 65) / 80)
+        dV = I_ext - 120 * m ** 3 * h * (V - 50) - 36 * n ** 4 * (V + 77) - 0.3 * (V + 54.4)
+        return [dV, am * (1 - m) - bm * m, ah * (1 - h) - bh * h, an * (1 - n) - bn * n]
+
+    z0 = [-62.0, 0.05, 0.6, 0.32]
+    T = 20.0
+    sol = scipy_integrate.solve_ivp(f, (0, T), z0, args=(10.0,), method="DOP853", rtol=1e-12, atol=1e-12)
+    N, R = 5, 2
+    errs = []
+    for dt in (0.02, 0.01):
+        y0 = np.concatenate([np.full(N, v) for v in z0])
+        y, _ = oracle.rk4(oracle.HH, oracle.RING, N, R, I.hh_params(g=0.0), y0, int(round(T / dt)), dt,
+                          node_param=np.full(N, 10.0))
+        errs.append(max(abs(y[v * N] - sol.y[v, -1]) for v in range(4)))
+    assert errs[1] < 1e-3
+    assert 8 < errs[0] / errs[1] < 24
+
+
+# ---------------------------------------------------------------- shared properties
+@pytest.mark.parametrize("model", [oracle.KS, oracle.FHN, oracle.HH])
+def test_ring_roll_equivariance(model):
+    N, R, shift = 37, 8, 5
+    d = {oracle.KS: 1, oracle.FHN: 2, oracle.HH: 4}[model]
+    p = {oracle.KS: I.ks_params(), oracle.FHN: I.fhn_params(), oracle.HH: I.hh_params()}[model]
+    x = I.initial_state(model, 14, 0, N).reshape(d, N)
+    npar = I.hh_iext(14, 0, N) if model == oracle.HH else None
+    y1, _ = oracle.rk4(model, oracle.RING, N, R, p, x.ravel(), 50, 0.01, node_param=npar)
+    y2, _ = oracle.rk4(model, oracle.RING, N, R, p, np.roll(x, shift, axis=1).ravel(), 50, 0.01,
+                       node_param=None if npar is None else np.roll(npar, shift))
+    assert np.abs(np.roll(y1.reshape(d, N), shift, axis=1) - y2.reshape(d, N)).max() < 1e-12
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_cube_roll_equivariance(axis):
+    N1, P = 7, 2
+    x = I.ks_phases(15, 0, N1 ** 3).reshape(N1, N1, N1)  # [k][j][i]
+    p = I.ks_params(alpha=1.52)
+    y1, _ = oracle.rk4(oracle.KS, oracle.CUBE, N1, P, p, x.ravel(), 20, 0.01)
+    y2, _ = oracle.rk4(oracle.KS, oracle.CUBE, N1, P, p, np.roll(x, 2, axis=axis).ravel(), 20, 0.01)
+    assert np.abs(np.roll(y1.reshape(N1, N1, N1), 2, axis=axis) - y2.reshape(N1, N1, N1)).max() < 1e-12
+
+
+@pytest.mark.parametrize("topo,N,R", [(oracle.RING, 3, 1), (oracle.RING, 7, 3), (oracle.RING, 16, 4),
+                                      (oracle.RING, 33, 10), (oracle.CUBE, 3, 1), (oracle.CUBE, 5, 2),
+                                      (oracle.CUBE, 6, 1)])
+def test_window_sum_brute_force_from_geometry(topo, N, R):
+    n = oracle.nodes_of(topo, N)
+    f = I.uniform(16, 0, 0, n, -1, 1)
+    member = ring_member if topo == oracle.RING else cube_member
+    got = oracle.window_sum(topo, N, R, f)
+    for i in range(n):
+        e = sum(f[j] for j in range(n) if member(N, R, i, j))
+        assert abs(got[i] - e) < 1e-12
+
+
+@pytest.mark.parametrize("model", [oracle.KS, oracle.FHN, oracle.HH])
+def test_rk4_fourth_order_self_convergence(model):
+    N, R = 24, 5
+    d = {oracle.KS: 1, oracle.FHN: 2, oracle.HH: 4}[model]
+    p = {oracle.KS: I.ks_params(), oracle.FHN: I.fhn_params(), oracle.HH: I.hh_params()}[model]
+    x = I.initial_state(model, 17, 0, N)
+    npar = I.hh_iext(17, 0, N) if model == oracle.HH else None
+    T = 0.4 if model != oracle.HH else 2.0
+    # FHN with eps = 0.05 is mildly stiff: start closer to the asymptotic regime
+    dts = (0.005, 0.0025, 0.00125) if model == oracle.FHN else (0.02, 0.01, 0.005)
+    sols = []
+    for dt in dts:
+        y, _ = oracle.rk4(model, oracle.RING, N, R, p, x, int(round(T / dt)), dt, node_param=npar)
+        sols.append(y)
+    e1 = np.abs(sols[0] - sols[1]).max()
+    e2 = np.abs(sols[1] - sols[2]).max()
+    assert 12 < e1 / e2 < 20, (e1, e2)
+    assert d > 0
+
+
+def test_order_parameter_closed_forms():
+    assert abs(oracle.order_parameter(np.full(100, 2.3)) - 1.0) < 1e-14
+    phi = 2 * math.pi * 3 * np.arange(100) / 100
+    assert oracle.order_parameter(phi) < 1e-14
+    x = I.ks_phases(18, 0, 500)
+    r0 = oracle.order_parameter(x)
+    assert abs(oracle.order_parameter(x + 1.234) - r0) < 1e-14
+    # two clusters at opposite phases with weights 3:1 give |3 - 1| / 4
+    phi = np.concatenate([np.full(300, 0.4), np.full(100, 0.4 + math.pi)])
+    assert abs(oracle.order_parameter(phi) - 0.5) < 1e-14
+
+
+def test_reverse_order_agrees_on_short_horizons():
+    N, R = 200, 70
+    x = I.ks_phases(19, 0, N)
+    y1, _ = oracle.rk4(oracle.KS, oracle.RING, N, R, I.ks_params(), x, 100, 0.01)
+    y2, _ = oracle.rk4(oracle.KS, oracle.RING, N, R, I.ks_params(), x, 100, 0.01, flags=oracle.REVERSE)
+    assert np.abs(y1 - y2).max() < 1e-13
+
+
+def test_invalid_arguments_rejected():
+    with pytest.raises(ValueError):
+        oracle.rk4(oracle.KS, oracle.RING, 10, 5, I.ks_params(), np.zeros(10), 1, 0.01)  # 2R+1 > N
+    with pytest.raises(ValueError):
+        oracle.rk4(oracle.KS, oracle.RING, 10, 0, I.ks_params(), np.zeros(10), 1, 0.01)
+    with pytest.raises(ValueError):
+        oracle.rk4(oracle.FHN, oracle.CUBE, 5, 1, I.fhn_params(), np.zeros(250), 1, 0.01)
+    with pytest.raises(ValueError):
+        oracle.rk4(oracle.KS, oracle.RING, 10, 2, I.ks_params(), np.zeros(10), 1, 0.0)
