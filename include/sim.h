@@ -1,0 +1,145 @@
+/*
+ * sim.h -- C ABI of the GB300 network-dynamics stepper.
+ *
+ * One explicit RK4 time step of a large network of nonlocally coupled
+ * oscillators (Sudakov & Maistrenko, "Parallelization of Network Dynamics
+ * Computations in Heterogeneous Distributed Environment", arXiv:2410.19075):
+ * every RK4 stage gathers each node's coupling sum over its nonlocal
+ * neighbourhood, evaluates the node's right-hand side and updates the stage
+ * state.  Everything runs on one GPU; there is no CPU fallback.
+ *
+ * Conventions shared by every entry point
+ *   - Return value: a sim_status (0 = SIM_OK, negative = error).  Nothing aborts
+ *     the process.  sim_last_error() gives a message for the calling thread.
+ *   - Handles are not thread-safe: use one handle per host thread.
+ *   - Host buffers are owned by the caller and only read or written during the
+ *     call.  The handle owns every device buffer it allocates and frees it in
+ *     sim_destroy().
+ *   - State layout: variable-major (SoA), FP64, little-endian.  Variable v of
+ *     node i is at [v * nodes + i].  Ring: node i in [0, N).  Cube: node
+ *     k*N1^2 + j*N1 + i (Section IV, 3D networks).
+ *   - Work is issued asynchronously on the handle's CUDA stream (the stream
+ *     given at creation; NULL means the legacy default stream).  Device errors
+ *     from earlier asynchronous work surface at the next call that synchronises.
+ */
+#ifndef SIM_H
+#define SIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sim_handle *sim_t;
+
+/* Node models.
+ * SIM_KS  Kuramoto-Sakaguchi, Eq. (3) with m = 0, eps = 1 (Algorithm 1):
+ *         dphi_i/dt = omega - (mu/K) sum_{j in W(i)} sin(phi_i - phi_j + alpha).
+ *         1 variable (phi).  params = {omega, mu, alpha}.
+ * SIM_FHN FitzHugh-Nagumo, Eq. (2) with tau = 0, D = 0, I_app = 0 and a
+ *         rotational coupling matrix B = [[cos p, sin p], [-sin p, cos p]]:
+ *         eps du_i/dt = u_i - u_i^3/3 - v_i + (sigma/K) sum_j [B00 (u_j-u_i) + B01 (v_j-v_i)]
+ *             dv_i/dt = u_i + a         + (sigma/K) sum_j [B10 (u_j-u_i) + B11 (v_j-v_i)]
+ *         2 variables (u, v).  params = {eps, a, sigma, p}.
+ * SIM_HH  Hodgkin-Huxley, Eq. (1) specialised to the classic neuron (V, m, h, n)
+ *         with textbook rates (rest near -65 mV) and diffusive coupling of V to
+ *         the mean of its window: Cm dV/dt = I_ext,i - I_Na - I_K - I_L
+ *         + g (mean_{j in W(i)} V_j - V_i).  4 variables.
+ *         params = {Cm, gNa, gK, gL, ENa, EK, EL, g}; I_ext per node via
+ *         sim_set_node_param (default 0).
+ * K is the number of links of a node: 2R on the ring, (2P+1)^3 - 1 on the cube
+ * (one more of each with SIM_FLAG_INCLUDE_SELF). */
+typedef enum { SIM_KS = 0, SIM_FHN = 1, SIM_HH = 2 } sim_model;
+
+/* Topologies (Section IV).
+ * SIM_RING    node i couples to i-R..i+R (mod N), R = radius, 2R+1 <= N.
+ * SIM_CUBE3D  periodic N1^3 lattice (N = N1), node couples to the (2P+1)^3 box
+ *             around it, P = radius, 2P+1 <= N1.  Kuramoto only. */
+typedef enum { SIM_RING = 0, SIM_CUBE3D = 1 } sim_topology;
+
+typedef enum {
+    SIM_OK = 0,
+    SIM_EINVAL = -1,      /* invalid argument; nothing was changed */
+    SIM_ENOMEM = -2,      /* device allocation failed (or over an admission budget) */
+    SIM_EDEVICE = -3,     /* a CUDA call failed; the message says which */
+    SIM_ETIMEOUT = -4,    /* a bounded device-side wait gave up; results are invalid */
+    SIM_ENONFINITE = -5,  /* the state left the representable range (NaN, Inf or overflow) */
+    SIM_EBUSY = -6        /* the handle is in use (e.g. captured) */
+} sim_status;
+
+/* Creation flags. */
+#define SIM_FLAG_INCLUDE_SELF 1u /* count the node itself as one of its links */
+
+/* Bytes of device memory sim_create() allocates for this network (for
+ * admission control).  Returns 0 for invalid arguments. */
+size_t sim_workspace_bytes(int model, int topology, int64_t N, int64_t radius);
+
+/* Create a network.  params: n_params doubles in the model's order (above).
+ * stream: a cudaStream_t (may be torch's current stream) or NULL.
+ * The initial state is all zeros until sim_set_state().
+ * Errors: SIM_EINVAL (unknown model/topology, 2*radius+1 > N, radius < 1,
+ * non-finite params, wrong n_params), SIM_ENOMEM, SIM_EDEVICE. */
+int sim_create(sim_t *out, int model, int topology, int64_t N, int64_t radius,
+               const double *params, int n_params, unsigned flags, void *stream);
+
+/* Number of nodes (N or N1^3) and of state variables per node. */
+int64_t sim_nodes(sim_t h);
+int sim_dim(sim_t h);
+
+/* Copy a full state (d * nodes doubles, SoA) from host memory.  Resets the
+ * observable record: the order parameter of this state is recorded as t = 0.
+ * Returns after the copy has been issued; the host buffer may be reused when
+ * the call returns.  Errors: SIM_EINVAL if n_values != d * nodes. */
+int sim_set_state(sim_t h, const double *host_soa, int64_t n_values);
+
+/* Same, from device memory (dev_soa must stay valid until the stream reaches
+ * the copy). */
+int sim_set_state_device(sim_t h, const double *dev_soa, int64_t n_values);
+
+/* Per-node parameter: which = 0 is the HH external current I_ext,i
+ * (n = nodes doubles, host memory).  SIM_EINVAL for other models. */
+int sim_set_node_param(sim_t h, int which, const double *host, int64_t n);
+
+/* Advance the network by n_steps classic RK4 steps of size dt (asynchronous on
+ * the handle's stream; launched as a captured CUDA graph).  dt > 0.
+ * Errors from the device (SIM_ETIMEOUT, SIM_ENONFINITE) surface at the next
+ * synchronising call. */
+int sim_step(sim_t h, int64_t n_steps, double dt);
+
+/* Copy the state to host memory (synchronises the stream).  Returns the device
+ * error status accumulated since creation, if any. */
+int sim_get_state(sim_t h, double *host_soa, int64_t n_values);
+
+/* Copy the state to device memory (asynchronous). */
+int sim_get_state_device(sim_t h, double *dev_soa, int64_t n_values);
+
+/* Evaluate the right-hand side f(y) of every node at the current state, through
+ * the same fused stage kernel sim_step() uses for RK4 stage 1, and copy it to
+ * host memory (d * nodes doubles, SoA; synchronises).  The state is not changed.
+ * Useful for sampled checks of large networks and for Jacobian studies. */
+int sim_rhs(sim_t h, double *host_k, int64_t n_values);
+
+/* Kuramoto order parameter |mean_j exp(i phi_j)| at t = 0 and after every step
+ * since the last call (synchronises).  Writes at most max_values values to
+ * host_R and their count to *n_written.  Values not yet read are kept for the
+ * most recent 65536 steps; older ones are dropped.  Other models write 0 values. */
+int sim_observables(sim_t h, double *host_R, int64_t max_values, int64_t *n_written);
+
+/* Wait for all work issued on the handle's stream and report device errors. */
+int sim_sync(sim_t h);
+
+/* Steps completed (issued) since the last sim_set_state. */
+int64_t sim_steps_done(sim_t h);
+
+/* Message of the last non-OK status returned on this thread (never NULL). */
+const char *sim_last_error(void);
+
+/* Free all device memory of the handle (synchronises first).  NULL is a no-op. */
+void sim_destroy(sim_t h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SIM_H */

@@ -1,0 +1,70 @@
+// Internal declarations shared by the translation units of libsim (not part of
+// the public C ABI in include/sim.h).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "models.cuh"
+
+namespace simk {
+
+constexpr int kRingThreads = 256;       // threads per CTA
+constexpr int kRingNodesPerThread = 4;  // consecutive nodes per thread
+constexpr int kRingTile = kRingThreads * kRingNodesPerThread; // nodes per CTA
+constexpr int kSubTile = 256;           // nodes per exact-prefix sub-tile
+constexpr int kSubLog2 = 8;
+
+// Device buffers and sizes of one ring network (plain path).
+struct RingPlan {
+    int model;
+    int64_t N, R;
+    int64_t nsub;  // ceil(N / kSubTile)
+    int64_t nctas; // ceil(N / kRingTile)
+    int F, lim;    // fixed-point grid 2^-F, range |f| < 2^lim
+    ModelParams mp;
+    double *y;          // D * N, the state y_n
+    double *acc;        // D * N, RK4 accumulator k1 + 2 k2 + 2 k3
+    double *xg[2];      // NX * N each, local stage-input variables (HH gates)
+    const double *node_param; // N (HH I_ext) or nullptr
+    int64_t *lam[2];    // NQ * N each: inclusive prefix of Q(f) inside each sub-tile
+    i128 *ofs[2];       // NQ * (nsub + 1) each: exclusive prefix at sub-tile starts
+    LookbackSlot *slots; // nctas
+    unsigned long long *ticket;
+    unsigned *err;
+    double *obs;        // order-parameter ring buffer
+    int64_t obs_cap;
+    unsigned long long *obs_ctr;
+};
+
+// Ring: f(y) -> lam[0], ofs[0] and the order parameter of y (Kuramoto).
+cudaError_t ring_prologue(const RingPlan &p, cudaStream_t s);
+// Ring: stage 1 only with dt = 0, so acc receives f(y) and y is untouched.
+cudaError_t ring_rhs(const RingPlan &p, cudaStream_t s);
+// Ring: one RK4 step, 4 fused stage kernels.
+cudaError_t ring_step(const RingPlan &p, double dt, cudaStream_t s);
+
+// Device buffers of one periodic cubic lattice (Kuramoto only).
+struct CubePlan {
+    int64_t N1, P;
+    int F;            // fixed-point grid of the box sums
+    ModelParams mp;
+    double *y, *acc;  // N1^3
+    double *f;        // 2 * N1^3: sin, cos of the current stage input
+    int64_t *sx;      // 2 * N1^3: window sums along x
+    int64_t *sxy;     // 2 * N1^3: box sums over x and y
+    i128 *partial;    // per-CTA partial sums of the order parameter
+    unsigned long long *done_ctr;
+    unsigned *err;
+    double *obs;
+    int64_t obs_cap;
+    unsigned long long *obs_ctr;
+    int zgrid;        // CTAs of the z pass
+};
+
+cudaError_t cube_configure(); // once per process, before the first launch
+cudaError_t cube_prologue(const CubePlan &p, cudaStream_t s);
+cudaError_t cube_step(const CubePlan &p, double dt, cudaStream_t s);
+cudaError_t cube_rhs(const CubePlan &p, cudaStream_t s); // acc <- f(y)
+
+} // namespace simk

@@ -1,0 +1,112 @@
+// Node right-hand sides evaluated from exact window sums (FP64).
+//
+// Every model is written as: a coupled quantity f(x) of a node's stage input
+// (the "exchange" variables of the paper's memory layout, Section III.B), whose
+// window sums W = sum_{j in window incl. self} Q(f_j) arrive as exact
+// fixed-point integers, and a local right-hand side.
+#pragma once
+#include "common.cuh"
+
+namespace simk {
+
+// Derived constants, computed once on the host in FP64.
+struct ModelParams {
+    double c[8];
+    int64_t wsize;    // window size including the node itself (2R+1 or (2P+1)^3)
+    int include_self; // 1: the node is one of its own links
+};
+
+template <int M> struct Model;
+
+// Kuramoto-Sakaguchi, Eq. (3) with m = 0, eps = 1 (Algorithm 1):
+//   dphi_i/dt = omega - (mu/K) sum_{j in W(i)} sin(phi_i - phi_j + alpha)
+//             = omega + (mu/K) [cos(phi_i+alpha) S_sin - sin(phi_i+alpha) S_cos],
+// S_sin = sum_j sin phi_j, S_cos = sum_j cos phi_j (angle-difference identity,
+// so the window only needs sums of sin and cos).
+// c = {omega, mu/K, sin alpha, cos alpha}.  Coupled quantity (sin phi, cos phi).
+template <> struct Model<0> {
+    static constexpr int D = 1, NQ = 2, NX = 0, F = 53;
+    __device__ __forceinline__ static void coupled(const double (&x)[D], double (&f)[NQ])
+    {
+        sincos(x[0], &f[0], &f[1]);
+    }
+    __device__ __forceinline__ static void rhs(const ModelParams &P, int F_, const double (&fo)[NQ],
+                                               const int64_t (&qo)[NQ], const i128 (&W)[NQ],
+                                               const double *, double, double (&k)[D])
+    {
+        const i128 ss = P.include_self ? W[0] : W[0] - (i128)qo[0];
+        const i128 sc = P.include_self ? W[1] : W[1] - (i128)qo[1];
+        const double Ss = fixed_to_double(ss, F_), Sc = fixed_to_double(sc, F_);
+        const double s = fo[0], c = fo[1];
+        const double sxa = s * P.c[3] + c * P.c[2]; // sin(phi + alpha)
+        const double cxa = c * P.c[3] - s * P.c[2]; // cos(phi + alpha)
+        k[0] = P.c[0] + P.c[1] * (cxa * Ss - sxa * Sc);
+    }
+};
+
+// FitzHugh-Nagumo, Eq. (2) with tau = 0, D = 0, I_app = 0 and the rotational
+// coupling matrix B = [[b00, b01], [b10, b11]] = [[cos p, sin p], [-sin p, cos p]]:
+//   du/dt = (u - u^3/3 - v + (sigma/K) [b00 Cu + b01 Cv]) / eps
+//   dv/dt =  u + a        + (sigma/K) [b10 Cu + b11 Cv]
+// with Cu = sum_{j in W(i)} (u_j - u_i) = W_u - wsize * Q(u_i), exact in fixed point.
+// c = {1/eps, a, sigma/K, b00, b01, b10, b11}.  Coupled quantity (u, v).
+template <> struct Model<1> {
+    static constexpr int D = 2, NQ = 2, NX = 0, F = 51;
+    __device__ __forceinline__ static void coupled(const double (&x)[D], double (&f)[NQ])
+    {
+        f[0] = x[0];
+        f[1] = x[1];
+    }
+    __device__ __forceinline__ static void rhs(const ModelParams &P, int F_, const double (&fo)[NQ],
+                                               const int64_t (&qo)[NQ], const i128 (&W)[NQ],
+                                               const double *, double, double (&k)[D])
+    {
+        const double Cu = fixed_to_double(W[0] - (i128)qo[0] * P.wsize, F_);
+        const double Cv = fixed_to_double(W[1] - (i128)qo[1] * P.wsize, F_);
+        const double u = fo[0], v = fo[1];
+        k[0] = (u - u * u * u * (1.0 / 3.0) - v + P.c[2] * (P.c[3] * Cu + P.c[4] * Cv)) * P.c[0];
+        k[1] = u + P.c[1] + P.c[2] * (P.c[5] * Cu + P.c[6] * Cv);
+    }
+};
+
+// Hodgkin-Huxley, Eq. (1) as the classic neuron (V, m, h, n), textbook rates
+// (V in mV, rates in 1/ms, rest near -65 mV):
+//   Cm dV/dt = I_ext - gNa m^3 h (V-ENa) - gK n^4 (V-EK) - gL (V-EL) + (g/K) CV
+//   dx/dt    = alpha_x(V) (1-x) - beta_x(V) x,   x in {m, h, n}
+// with CV = sum_{j in W(i)} (V_j - V_i) = W_V - wsize * Q(V_i), exact in fixed point.
+// c = {1/Cm, gNa, gK, gL, ENa, EK, EL, g/K}.  Coupled quantity V; the gates are
+// local variables.
+__device__ __forceinline__ double x_over_1mexp(double x)
+{
+    return x == 0.0 ? 1.0 : x / -expm1(-x);
+}
+
+template <> struct Model<2> {
+    static constexpr int D = 4, NQ = 1, NX = 3, F = 46;
+    __device__ __forceinline__ static void coupled(const double (&x)[D], double (&f)[NQ])
+    {
+        f[0] = x[0];
+    }
+    __device__ __forceinline__ static void rhs(const ModelParams &P, int F_, const double (&fo)[NQ],
+                                               const int64_t (&qo)[NQ], const i128 (&W)[NQ],
+                                               const double *X, double Iext, double (&k)[D])
+    {
+        const double CV = fixed_to_double(W[0] - (i128)qo[0] * P.wsize, F_);
+        const double V = fo[0], m = X[0], h = X[1], n = X[2];
+        const double am = x_over_1mexp((V + 40.0) * 0.1);
+        const double bm = 4.0 * exp(-(V + 65.0) * (1.0 / 18.0));
+        const double ah = 0.07 * exp(-(V + 65.0) * 0.05);
+        const double bh = 1.0 / (1.0 + exp(-(V + 35.0) * 0.1));
+        const double an = 0.1 * x_over_1mexp((V + 55.0) * 0.1);
+        const double bn = 0.125 * exp(-(V + 65.0) * 0.0125);
+        const double m3h = m * m * m * h, n4 = (n * n) * (n * n);
+        const double I = Iext - P.c[1] * m3h * (V - P.c[4]) - P.c[2] * n4 * (V - P.c[5]) -
+                         P.c[3] * (V - P.c[6]) + P.c[7] * CV;
+        k[0] = I * P.c[0];
+        k[1] = am * (1.0 - m) - bm * m;
+        k[2] = ah * (1.0 - h) - bh * h;
+        k[3] = an * (1.0 - n) - bn * n;
+    }
+};
+
+} // namespace simk

@@ -1,0 +1,462 @@
+// C ABI of libsim: handles, argument validation, device buffers, the
+// CUDA-graph-captured step loop and error reporting (declared in include/sim.h).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+
+#include "internal.h"
+#include "sim.h"
+
+using namespace simk;
+
+namespace {
+
+thread_local std::string g_last_error = "no error";
+
+int fail(int status, const std::string &msg)
+{
+    g_last_error = msg;
+    return status;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(SIM_EDEVICE, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+constexpr int64_t kObsCap = 65536;
+constexpr int kGraphChunk = 16; // RK4 steps per captured graph
+
+size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
+
+int model_dim(int m) { return m == SIM_KS ? 1 : m == SIM_FHN ? 2 : m == SIM_HH ? 4 : 0; }
+int model_nq(int m) { return m == SIM_HH ? 1 : 2; }
+int model_nx(int m) { return m == SIM_HH ? 3 : 0; }
+int model_nparams(int m) { return m == SIM_KS ? 3 : m == SIM_FHN ? 4 : m == SIM_HH ? 8 : -1; }
+int ring_F(int m) { return m == SIM_KS ? Model<0>::F : m == SIM_FHN ? Model<1>::F : Model<2>::F; }
+
+int ceil_log2(uint64_t x)
+{
+    int r = 0;
+    while ((1ull << r) < x) ++r;
+    return r;
+}
+
+// Byte layout of a network's device block.  Each entry is an offset.
+struct Layout {
+    size_t total = 0;
+    size_t y, acc, xg0, xg1, npar, lam0, lam1, ofs0, ofs1, slots, f, sx, sxy, partial, ctrs, obs;
+};
+
+Layout layout_of(int model, int topo, int64_t N, int64_t R)
+{
+    Layout L{};
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o = align_up(o + bytes);
+        return at;
+    };
+    const int d = model_dim(model);
+    if (topo == SIM_RING) {
+        const int nq = model_nq(model), nx = model_nx(model);
+        const int64_t nsub = (N + kSubTile - 1) / kSubTile, nctas = (N + kRingTile - 1) / kRingTile;
+        L.y = take(sizeof(double) * d * N);
+        L.acc = take(sizeof(double) * d * N);
+        L.xg0 = take(sizeof(double) * nx * N);
+        L.xg1 = take(sizeof(double) * nx * N);
+        L.npar = take(model == SIM_HH ? sizeof(double) * N : 0);
+        L.lam0 = take(sizeof(int64_t) * nq * N);
+        L.lam1 = take(sizeof(int64_t) * nq * N);
+        L.ofs0 = take(sizeof(i128) * nq * (nsub + 1));
+        L.ofs1 = take(sizeof(i128) * nq * (nsub + 1));
+        L.slots = take(sizeof(LookbackSlot) * nctas);
+    } else {
+        const int64_t n = N * N * N;
+        const int64_t nblk = ((N + 127) / 128) * N;
+        L.y = take(sizeof(double) * n);
+        L.acc = take(sizeof(double) * n);
+        L.f = take(sizeof(double) * 2 * n);
+        L.sx = take(sizeof(int64_t) * 2 * n);
+        L.sxy = take(sizeof(int64_t) * 2 * n);
+        L.partial = take(sizeof(i128) * 2 * nblk);
+    }
+    L.ctrs = take(64);
+    L.obs = take(sizeof(double) * kObsCap);
+    L.total = o;
+    return L;
+}
+
+const char *validate(int model, int topo, int64_t N, int64_t R, const double *params, int n_params)
+{
+    if (model_dim(model) == 0) return "unknown model";
+    if (topo != SIM_RING && topo != SIM_CUBE3D) return "unknown topology";
+    if (topo == SIM_CUBE3D && model != SIM_KS) return "the cubic lattice supports the Kuramoto model only";
+    if (R < 1) return "radius must be >= 1";
+    if (N < 2 * R + 1) return "window does not fit: need 2*radius+1 <= N";
+    if (topo == SIM_RING && N > (int64_t(1) << 34)) return "ring too large";
+    if (topo == SIM_CUBE3D && N > 1024) return "cube edge N1 must be <= 1024";
+    if (n_params != model_nparams(model)) return "wrong number of parameters for this model";
+    if (!params) return "params is NULL";
+    for (int i = 0; i < n_params; ++i)
+        if (!std::isfinite(params[i])) return "non-finite parameter";
+    if (model == SIM_FHN && params[0] == 0.0) return "FHN eps must be non-zero";
+    if (model == SIM_HH && params[0] == 0.0) return "HH Cm must be non-zero";
+    return nullptr;
+}
+
+} // namespace
+
+struct sim_handle {
+    int model = 0, topo = 0, d = 0;
+    int64_t N = 0, R = 0, nodes = 0;
+    unsigned flags = 0;
+    cudaStream_t stream = nullptr;       // where work is issued
+    cudaStream_t cap_stream = nullptr;   // private stream used only for graph capture
+    void *block = nullptr;
+    size_t bytes = 0;
+    Layout L;
+    RingPlan ring{};
+    CubePlan cube{};
+    unsigned *err = nullptr;
+    unsigned long long *obs_ctr = nullptr;
+    double *obs = nullptr;
+    unsigned *h_err = nullptr;            // pinned
+    unsigned long long *h_ctr = nullptr;  // pinned
+    int64_t steps_done = 0;
+    int64_t obs_read = 0;
+    std::map<std::pair<double, int>, cudaGraphExec_t> graphs;
+};
+
+namespace {
+
+int check_device_error(sim_t h)
+{
+    cudaError_t e = cudaMemcpyAsync(h->h_err, h->err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "device work failed");
+    const unsigned w = *h->h_err;
+    if (w & ERR_TIMEOUT) return fail(SIM_ETIMEOUT, "a device-side wait exceeded its bound; results are invalid");
+    if (w & ERR_RANGE) return fail(SIM_ENONFINITE, "the state became non-finite or left the fixed-point range");
+    return SIM_OK;
+}
+
+cudaError_t launch_steps(sim_t h, int64_t n, double dt, cudaStream_t s)
+{
+    for (int64_t t = 0; t < n; ++t) {
+        const cudaError_t e = h->topo == SIM_RING ? ring_step(h->ring, dt, s) : cube_step(h->cube, dt, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+int get_graph(sim_t h, double dt, int chunk, cudaGraphExec_t *out)
+{
+    auto it = h->graphs.find({dt, chunk});
+    if (it != h->graphs.end()) {
+        *out = it->second;
+        return SIM_OK;
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+    const cudaError_t le = launch_steps(h, chunk, dt, h->cap_stream);
+    e = cudaStreamEndCapture(h->cap_stream, &g);
+    if (le != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(le, "kernel launch during capture");
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    h->graphs[{dt, chunk}] = ex;
+    *out = ex;
+    return SIM_OK;
+}
+
+int prologue(sim_t h)
+{
+    cudaError_t e = cudaMemsetAsync(h->obs_ctr, 0, sizeof(unsigned long long), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->err, 0, sizeof(unsigned), h->stream);
+    if (e == cudaSuccess) e = h->topo == SIM_RING ? ring_prologue(h->ring, h->stream) : cube_prologue(h->cube, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "prologue");
+    h->steps_done = 0;
+    h->obs_read = 0;
+    return SIM_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+size_t sim_workspace_bytes(int model, int topology, int64_t N, int64_t radius)
+{
+    double dummy[8] = {1, 1, 1, 1, 1, 1, 1, 1};
+    if (validate(model, topology, N, radius, dummy, model_nparams(model))) return 0;
+    return layout_of(model, topology, N, radius).total;
+}
+
+int sim_create(sim_t *out, int model, int topology, int64_t N, int64_t radius, const double *params,
+               int n_params, unsigned flags, void *stream)
+{
+    if (!out) return fail(SIM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (const char *msg = validate(model, topology, N, radius, params, n_params)) return fail(SIM_EINVAL, msg);
+    if (flags & ~SIM_FLAG_INCLUDE_SELF) return fail(SIM_EINVAL, "unknown flags");
+
+    sim_t h = new sim_handle();
+    h->model = model;
+    h->topo = topology;
+    h->d = model_dim(model);
+    h->N = N;
+    h->R = radius;
+    h->nodes = topology == SIM_CUBE3D ? N * N * N : N;
+    h->flags = flags;
+    h->stream = static_cast<cudaStream_t>(stream);
+    h->L = layout_of(model, topology, N, radius);
+    h->bytes = h->L.total;
+
+    cudaError_t e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&h->block, h->bytes);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        sim_destroy(h);
+        return fail(SIM_ENOMEM, "device allocation of " + std::to_string(h->bytes) + " bytes failed");
+    }
+    if (e == cudaSuccess) e = cudaMallocHost(&h->h_err, 64);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->block, 0, h->bytes, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        sim_destroy(h);
+        return cuda_fail(e, "sim_create");
+    }
+    h->h_ctr = reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(h->h_err) + 8);
+    char *b = static_cast<char *>(h->block);
+    const Layout &L = h->L;
+    unsigned long long *ctrs = reinterpret_cast<unsigned long long *>(b + L.ctrs);
+    h->err = reinterpret_cast<unsigned *>(ctrs + 0);
+    h->obs_ctr = ctrs + 1;
+    unsigned long long *ticket = ctrs + 2;
+    h->obs = reinterpret_cast<double *>(b + L.obs);
+
+    // Derived model constants (FP64 on the host).
+    ModelParams mp{};
+    const bool self = (flags & SIM_FLAG_INCLUDE_SELF) != 0;
+    mp.include_self = self ? 1 : 0;
+    mp.wsize = topology == SIM_RING ? 2 * radius + 1 : (2 * radius + 1) * (2 * radius + 1) * (2 * radius + 1);
+    const double K = (double)(self ? mp.wsize : mp.wsize - 1);
+    if (model == SIM_KS) {
+        mp.c[0] = params[0];
+        mp.c[1] = params[1] / K;
+        mp.c[2] = std::sin(params[2]);
+        mp.c[3] = std::cos(params[2]);
+    } else if (model == SIM_FHN) {
+        const double ph = params[3];
+        mp.c[0] = 1.0 / params[0];
+        mp.c[1] = params[1];
+        mp.c[2] = params[2] / K;
+        mp.c[3] = std::cos(ph);
+        mp.c[4] = std::sin(ph);
+        mp.c[5] = -std::sin(ph);
+        mp.c[6] = std::cos(ph);
+    } else {
+        mp.c[0] = 1.0 / params[0];
+        for (int i = 1; i < 7; ++i) mp.c[i] = params[i];
+        mp.c[7] = params[7] / K;
+    }
+
+    if (topology == SIM_RING) {
+        RingPlan &p = h->ring;
+        p.model = model;
+        p.N = N;
+        p.R = radius;
+        p.nsub = (N + kSubTile - 1) / kSubTile;
+        p.nctas = (N + kRingTile - 1) / kRingTile;
+        p.F = ring_F(model);
+        p.lim = 54 - p.F;
+        p.mp = mp;
+        p.y = reinterpret_cast<double *>(b + L.y);
+        p.acc = reinterpret_cast<double *>(b + L.acc);
+        p.xg[0] = reinterpret_cast<double *>(b + L.xg0);
+        p.xg[1] = reinterpret_cast<double *>(b + L.xg1);
+        p.node_param = model == SIM_HH ? reinterpret_cast<double *>(b + L.npar) : nullptr;
+        p.lam[0] = reinterpret_cast<int64_t *>(b + L.lam0);
+        p.lam[1] = reinterpret_cast<int64_t *>(b + L.lam1);
+        p.ofs[0] = reinterpret_cast<i128 *>(b + L.ofs0);
+        p.ofs[1] = reinterpret_cast<i128 *>(b + L.ofs1);
+        p.slots = reinterpret_cast<LookbackSlot *>(b + L.slots);
+        p.ticket = ticket;
+        p.err = h->err;
+        p.obs = h->obs;
+        p.obs_cap = kObsCap;
+        p.obs_ctr = h->obs_ctr;
+    } else {
+        CubePlan &p = h->cube;
+        p.N1 = N;
+        p.P = radius;
+        p.F = 61 - ceil_log2((uint64_t)mp.wsize);
+        p.mp = mp;
+        p.y = reinterpret_cast<double *>(b + L.y);
+        p.acc = reinterpret_cast<double *>(b + L.acc);
+        p.f = reinterpret_cast<double *>(b + L.f);
+        p.sx = reinterpret_cast<int64_t *>(b + L.sx);
+        p.sxy = reinterpret_cast<int64_t *>(b + L.sxy);
+        p.partial = reinterpret_cast<i128 *>(b + L.partial);
+        p.done_ctr = ticket;
+        p.err = h->err;
+        p.obs = h->obs;
+        p.obs_cap = kObsCap;
+        p.obs_ctr = h->obs_ctr;
+        if ((e = cube_configure()) != cudaSuccess) {
+            sim_destroy(h);
+            return cuda_fail(e, "cube kernel configuration");
+        }
+    }
+    const int st = prologue(h);
+    if (st != SIM_OK) {
+        sim_destroy(h);
+        return st;
+    }
+    *out = h;
+    return SIM_OK;
+}
+
+int64_t sim_nodes(sim_t h) { return h ? h->nodes : 0; }
+int sim_dim(sim_t h) { return h ? h->d : 0; }
+
+static int set_state_impl(sim_t h, const double *src, int64_t n_values, cudaMemcpyKind kind)
+{
+    if (!h || !src) return fail(SIM_EINVAL, "NULL handle or buffer");
+    if (n_values != (int64_t)h->d * h->nodes) return fail(SIM_EINVAL, "n_values must equal dim * nodes");
+    double *y = h->topo == SIM_RING ? h->ring.y : h->cube.y;
+    cudaError_t e = cudaMemcpyAsync(y, src, sizeof(double) * n_values, kind, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "state copy");
+    return prologue(h);
+}
+
+int sim_set_state(sim_t h, const double *host_soa, int64_t n_values)
+{
+    return set_state_impl(h, host_soa, n_values, cudaMemcpyHostToDevice);
+}
+
+int sim_set_state_device(sim_t h, const double *dev_soa, int64_t n_values)
+{
+    return set_state_impl(h, dev_soa, n_values, cudaMemcpyDeviceToDevice);
+}
+
+int sim_set_node_param(sim_t h, int which, const double *host, int64_t n)
+{
+    if (!h || !host) return fail(SIM_EINVAL, "NULL handle or buffer");
+    if (h->model != SIM_HH || which != 0) return fail(SIM_EINVAL, "only the HH external current (which = 0) is a node parameter");
+    if (n != h->nodes) return fail(SIM_EINVAL, "n must equal the number of nodes");
+    cudaError_t e = cudaMemcpyAsync(const_cast<double *>(h->ring.node_param), host, sizeof(double) * n,
+                                    cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "node parameter copy");
+    return SIM_OK;
+}
+
+int sim_step(sim_t h, int64_t n_steps, double dt)
+{
+    if (!h) return fail(SIM_EINVAL, "NULL handle");
+    if (n_steps < 0) return fail(SIM_EINVAL, "n_steps must be >= 0");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(SIM_EINVAL, "dt must be finite and > 0");
+    int64_t left = n_steps;
+    while (left > 0) {
+        const int chunk = left >= kGraphChunk ? kGraphChunk : 1;
+        cudaGraphExec_t ex;
+        const int st = get_graph(h, dt, chunk, &ex);
+        if (st != SIM_OK) return st;
+        const cudaError_t e = cudaGraphLaunch(ex, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+        left -= chunk;
+        h->steps_done += chunk;
+    }
+    return SIM_OK;
+}
+
+static int get_state_impl(sim_t h, double *dst, int64_t n_values, cudaMemcpyKind kind)
+{
+    if (!h || !dst) return fail(SIM_EINVAL, "NULL handle or buffer");
+    if (n_values != (int64_t)h->d * h->nodes) return fail(SIM_EINVAL, "n_values must equal dim * nodes");
+    const double *y = h->topo == SIM_RING ? h->ring.y : h->cube.y;
+    const cudaError_t e = cudaMemcpyAsync(dst, y, sizeof(double) * n_values, kind, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "state copy");
+    return SIM_OK;
+}
+
+int sim_get_state(sim_t h, double *host_soa, int64_t n_values)
+{
+    const int st = get_state_impl(h, host_soa, n_values, cudaMemcpyDeviceToHost);
+    if (st != SIM_OK) return st;
+    return check_device_error(h);
+}
+
+int sim_get_state_device(sim_t h, double *dev_soa, int64_t n_values)
+{
+    return get_state_impl(h, dev_soa, n_values, cudaMemcpyDeviceToDevice);
+}
+
+int sim_rhs(sim_t h, double *host_k, int64_t n_values)
+{
+    if (!h || !host_k) return fail(SIM_EINVAL, "NULL handle or buffer");
+    if (n_values != (int64_t)h->d * h->nodes) return fail(SIM_EINVAL, "n_values must equal dim * nodes");
+    cudaError_t e = h->topo == SIM_RING ? ring_rhs(h->ring, h->stream) : cube_rhs(h->cube, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "rhs launch");
+    const double *acc = h->topo == SIM_RING ? h->ring.acc : h->cube.acc;
+    e = cudaMemcpyAsync(host_k, acc, sizeof(double) * n_values, cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "rhs copy");
+    return check_device_error(h);
+}
+
+int sim_observables(sim_t h, double *host_R, int64_t max_values, int64_t *n_written)
+{
+    if (!h || !n_written || (max_values > 0 && !host_R)) return fail(SIM_EINVAL, "NULL argument");
+    *n_written = 0;
+    if (h->model != SIM_KS) return check_device_error(h);
+    cudaError_t e = cudaMemcpyAsync(h->h_ctr, h->obs_ctr, sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "observable counter copy");
+    const int64_t have = (int64_t)*h->h_ctr;
+    if (have - h->obs_read > kObsCap) h->obs_read = have - kObsCap;
+    int64_t n = have - h->obs_read;
+    if (n > max_values) n = max_values;
+    int64_t done = 0;
+    while (done < n) {
+        const int64_t start = (h->obs_read + done) % kObsCap;
+        int64_t len = n - done;
+        if (start + len > kObsCap) len = kObsCap - start;
+        e = cudaMemcpyAsync(host_R + done, h->obs + start, sizeof(double) * len, cudaMemcpyDeviceToHost, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "observable copy");
+        done += len;
+    }
+    h->obs_read += n;
+    *n_written = n;
+    return check_device_error(h);
+}
+
+int sim_sync(sim_t h)
+{
+    if (!h) return fail(SIM_EINVAL, "NULL handle");
+    return check_device_error(h);
+}
+
+int64_t sim_steps_done(sim_t h) { return h ? h->steps_done : 0; }
+
+const char *sim_last_error(void) { return g_last_error.c_str(); }
+
+void sim_destroy(sim_t h)
+{
+    if (!h) return;
+    if (h->stream || h->block) cudaStreamSynchronize(h->stream);
+    for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
+    if (h->block) cudaFree(h->block);
+    if (h->h_err) cudaFreeHost(h->h_err);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    delete h;
+}
+
+} // extern "C"

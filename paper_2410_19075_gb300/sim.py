@@ -1,0 +1,118 @@
+"""Thin Python binding of the C ABI in include/sim.h (argument marshalling only).
+
+Every step of the time integration runs in the CUDA kernels of libsim.so; this
+module only converts arguments.  PyTorch supplies streams and device tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from ._lib import check, lib
+
+KS, FHN, HH = 0, 1, 2
+RING, CUBE3D = 0, 1
+FLAG_INCLUDE_SELF = 1
+DIM = {KS: 1, FHN: 2, HH: 4}
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)  # torch.cuda.Stream
+
+
+def workspace_bytes(model, topology, N, radius) -> int:
+    return int(lib().sim_workspace_bytes(model, topology, N, radius))
+
+
+class Network:
+    """One network on the GPU: ``sim_create`` ... ``sim_destroy``."""
+
+    def __init__(self, model: int, topology: int, N: int, radius: int, params, include_self: bool = False,
+                 stream=None):
+        p = np.ascontiguousarray(params, dtype=np.float64)
+        h = ctypes.c_void_p()
+        flags = FLAG_INCLUDE_SELF if include_self else 0
+        check(lib().sim_create(ctypes.byref(h), model, topology, int(N), int(radius),
+                               p.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), p.size, flags,
+                               _stream_ptr(stream)))
+        self._h = h
+        self.model, self.topology, self.N, self.radius = model, topology, int(N), int(radius)
+        self.nodes = int(lib().sim_nodes(h))
+        self.dim = int(lib().sim_dim(h))
+
+    @property
+    def n_values(self):
+        return self.nodes * self.dim
+
+    def _handle(self):
+        if self._h is None:
+            raise RuntimeError("network is closed")
+        return self._h
+
+    def set_state(self, state):
+        """Host numpy array (SoA, dim*nodes doubles) or a CUDA float64 tensor."""
+        if hasattr(state, "is_cuda") and state.is_cuda:
+            t = state.contiguous()
+            check(lib().sim_set_state_device(self._handle(), t.data_ptr(), t.numel()))
+            return
+        a = np.ascontiguousarray(state, dtype=np.float64)
+        check(lib().sim_set_state(self._handle(), a.ctypes.data, a.size))
+
+    def set_node_param(self, values, which: int = 0):
+        a = np.ascontiguousarray(values, dtype=np.float64)
+        check(lib().sim_set_node_param(self._handle(), which, a.ctypes.data, a.size))
+
+    def step(self, n_steps: int, dt: float):
+        check(lib().sim_step(self._handle(), int(n_steps), float(dt)))
+
+    def get_state(self, out: np.ndarray | None = None) -> np.ndarray:
+        if out is None:
+            out = np.empty(self.n_values, dtype=np.float64)
+        check(lib().sim_get_state(self._handle(), out.ctypes.data, out.size))
+        return out
+
+    def get_state_device(self, out):
+        """Copy the state into a CUDA float64 tensor (asynchronous)."""
+        check(lib().sim_get_state_device(self._handle(), out.data_ptr(), out.numel()))
+        return out
+
+    def rhs(self) -> np.ndarray:
+        """Right-hand side f(y) at the current state (SoA, host)."""
+        out = np.empty(self.n_values, dtype=np.float64)
+        check(lib().sim_rhs(self._handle(), out.ctypes.data, out.size))
+        return out
+
+    def observables(self, max_values: int = 1 << 16) -> np.ndarray:
+        buf = np.empty(max_values, dtype=np.float64)
+        n = ctypes.c_int64(0)
+        check(lib().sim_observables(self._handle(), buf.ctypes.data, max_values, ctypes.byref(n)))
+        return buf[: n.value].copy()
+
+    def sync(self):
+        check(lib().sim_sync(self._handle()))
+
+    @property
+    def steps_done(self) -> int:
+        return int(lib().sim_steps_done(self._handle()))
+
+    def close(self):
+        if self._h is not None:
+            lib().sim_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,83 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds, loads and
+exports every entry point include/sim.h declares; argument validation rejects
+bad networks before touching the device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", h)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"\b(sim_\w+|srv_\w+)\s*\(", text)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2410_19075_gb300 import build
+    build.build()
+    from paper_2410_19075_gb300 import _lib
+    return _lib.lib()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared_functions()
+    assert "sim_create" in names and "sim_step" in names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_declares_every_symbol():
+    from paper_2410_19075_gb300 import _lib
+    assert set(_declared_functions()) <= set(_lib.SIGNATURES)
+
+
+def test_workspace_bytes(lib):
+    from paper_2410_19075_gb300 import workspace_bytes
+    small = workspace_bytes(0, 0, 1000, 350)
+    big = workspace_bytes(1, 0, 10 ** 6, 350000)
+    assert 0 < small < big
+    # FHN ring: y, acc (16 B each per node) + two prefix buffers (16 B each) dominate
+    assert 60 * 10 ** 6 < big < 80 * 10 ** 6
+    cube = workspace_bytes(0, 1, 464, 92)
+    assert 6.0e9 < cube < 7.0e9  # 64 B per lattice node
+    assert workspace_bytes(0, 0, 10, 5) == 0  # 2R+1 > N
+    assert workspace_bytes(1, 1, 10, 2) == 0  # cube is Kuramoto only
+
+
+@pytest.mark.parametrize("model,topo,N,R,params", [
+    (0, 0, 10, 5, [0, 1, 1]),       # window does not fit
+    (0, 0, 10, 0, [0, 1, 1]),       # radius < 1
+    (0, 0, 10, 2, [0, 1]),          # wrong param count
+    (0, 0, 10, 2, [0, np.nan, 1]),  # non-finite param
+    (1, 1, 9, 2, [0.05, 0.5, 0.1, 1.4]),  # FHN on the cube
+    (3, 0, 10, 2, [0, 1, 1]),       # unknown model
+    (0, 2, 10, 2, [0, 1, 1]),       # unknown topology
+    (0, 1, 2000, 2, [0, 1, 1]),     # cube edge too large
+])
+def test_create_rejects_invalid_arguments(lib, model, topo, N, R, params):
+    from paper_2410_19075_gb300._lib import SIM_EINVAL
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    h = ctypes.c_void_p()
+    st = lib.sim_create(ctypes.byref(h), model, topo, N, R, p.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                        p.size, 0, None)
+    assert st == SIM_EINVAL
+    assert not h.value
+    assert len(lib.sim_last_error()) > 0
+
+
+def test_null_handle_calls_fail_cleanly(lib):
+    from paper_2410_19075_gb300._lib import SIM_EINVAL
+    assert lib.sim_step(None, 1, 0.01) == SIM_EINVAL
+    assert lib.sim_sync(None) == SIM_EINVAL
+    lib.sim_destroy(None)
