@@ -1,0 +1,336 @@
+"""Benchmark: FP64 node-steps/s of the fused RK4 stage kernels on one GB300.
+
+Default workload: FitzHugh-Nagumo ring with rotational coupling, N = 10^6 nodes,
+R = 350000 (r = 0.35), eps = 0.05, a = 0.5, sigma = 0.1, phi = pi/2 - 0.1,
+(u, v) uniform on the circle of radius 2, RK4 at dt = 0.01.  One bench step is one
+RK4 step of the whole network (4 fused stage kernels).  Timed iterations are
+chunks of --chunk RK4 steps; L2 is flushed (a 512 MiB write) between them.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on the
+host cores instead (bounded samples of the same workload).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2410_19075_gb300 import inputs as I  # noqa: E402
+
+MODEL_NAMES = {0: "Kuramoto-Sakaguchi", 1: "FitzHugh-Nagumo", 2: "Hodgkin-Huxley"}
+
+# Algorithmic bytes per node-step (4 stages) of the fused ring stage kernel:
+# per stage it reads the node's own prefix entry (nq * 8), the two shifted window
+# entries (2 * nq * 8), y (d * 8), acc (d * 8, stages 2-4), local stage
+# variables (nx * 8) and the node parameter, and writes the next prefix entry
+# (nq * 8), acc or y (d * 8) and the next local stage variables (nx * 8).
+RING_BYTES = {0: 344, 1: 432, 2: 704}
+# FP64 flops per node-step (DFMA = 2, DADD/DMUL = 1) of the arithmetic the method
+# needs, from the kernels' expressions; a library sincos counts 50 and a library
+# exp/expm1 34 (their measured cost in DFMA equivalents, x2).  Tally in the design doc.
+RING_FLOPS = {0: 4 * (50 + 13) + 14, 1: 4 * 15 + 3 * 8 + 6, 2: 4 * (6 * 34 + 40) + 3 * 16 + 12}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=100)
+    ap.add_argument("--chunk", type=int, default=100, help="RK4 steps per timed iteration")
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--model", type=int, default=1)
+    ap.add_argument("--N", type=int, default=10 ** 6)
+    ap.add_argument("--r", type=float, default=0.35)
+    ap.add_argument("--dt", type=float, default=0.01)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def workload(args):
+    N = args.N
+    R = max(1, min((N - 1) // 2, int(math.floor(args.r * N))))
+    params = {0: I.ks_params(alpha=1.46), 1: I.fhn_params(), 2: I.hh_params()}[args.model]
+    return N, R, params
+
+
+def config_of(args, N, R):
+    return {
+        "workload": f"{MODEL_NAMES[args.model]} ring, N={N}, R={R}, RK4 dt={args.dt}",
+        "N": N, "R": R, "dt": args.dt,
+        "rk4_steps_per_iteration": args.chunk,
+        "l2": "flushed (512 MiB write) between timed iterations; within an iteration the network "
+              "state is reused across consecutive RK4 steps as in a real run",
+        "parallelism": "replicas" if args.gpus > 1 else "single",
+    }
+
+
+# ----------------------------------------------------------------------------- distributed
+def dist_init(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if args.impl == "native" else "gloo")
+    return rank, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.idx = gpu_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- CPU baseline
+def cpu_baseline(args, N, R, params, seconds):
+    """Oracle throughput on the host cores: brute-force RHS of a bounded sample of
+    nodes for the 4 stages of one RK4 step, extrapolated per node-step."""
+    import oracle
+    cores = os.cpu_count() or 1
+    y0 = I.initial_state(args.model, 2412, 0, N)
+    npar = I.hh_iext(2412, 0, N) if args.model == 2 else None
+    # calibrate on a small sample, then size the sample to the time budget
+    rng = np.random.default_rng(0)
+    n = 16
+    while True:
+        q = np.sort(rng.choice(N, n, replace=False))
+        t0 = time.perf_counter()
+        for _ in range(4):
+            oracle.rhs_sampled(args.model, 0, N, R, params, y0, q, node_param=npar, threads=cores)
+        dt = time.perf_counter() - t0
+        if dt > seconds / 4 or n >= N:
+            break
+        n = min(N, max(n * 2, int(n * (seconds / 4) / max(dt, 1e-3))))
+    return {"value": n / dt, "unit": "node-steps/s", "cores": cores, "kind": "oracle",
+            "sample": f"brute-force RHS of {n} sampled nodes x 4 RK4 stages on the {N}-node network "
+                      f"({2 * R} links each), extrapolated per node-step"}
+
+
+def run_reference(args):
+    rank, world = dist_init(args)
+    N, R, params = workload(args)
+    if rank != 0:
+        return
+    import oracle
+    cores = os.cpu_count() or 1
+    y0 = I.initial_state(args.model, 2412, 0, N)
+    npar = I.hh_iext(2412, 0, N) if args.model == 2 else None
+    budget = 120.0  # seconds for the whole timed run
+    per_step_nodes = max(1, int(2.0e9 / (4 * 2 * R) * budget / max(1, args.steps + args.warmup) / 10))
+    rng = np.random.default_rng(1)
+    def one_step():
+        q = np.sort(rng.choice(N, min(N, per_step_nodes), replace=False))
+        for _ in range(4):
+            oracle.rhs_sampled(args.model, 0, N, R, params, y0, q, node_param=npar, threads=cores)
+        return q.size
+    for _ in range(args.warmup):
+        one_step()
+    t0 = time.perf_counter()
+    done = 0
+    for _ in range(args.steps):
+        done += one_step()
+    el = time.perf_counter() - t0
+    v = done / el
+    line = {"impl": "reference", "metric": "FP64 node-steps/s", "value": v, "unit": "node-steps/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_of(args, N, R),
+            "cpu_baseline": {"value": v, "unit": "node-steps/s", "cores": cores, "kind": "oracle",
+                             "sample": f"each step: brute-force RHS of {per_step_nodes} sampled nodes x 4 "
+                                       f"stages of the {N}-node network"},
+            "e2e": {"value": v, "unit": "node-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- native
+def run_native(args):
+    import torch
+    rank, world = dist_init(args)
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    from paper_2410_19075_gb300 import Network
+
+    N, R, params = workload(args)
+    d = {0: 1, 1: 2, 2: 4}[args.model]
+    stream = torch.cuda.current_stream()
+    y0_host = I.initial_state(args.model, 2412, rank, N)
+    npar = I.hh_iext(2412, rank, N) if args.model == 2 else None
+    y0_dev = torch.from_numpy(y0_host).cuda()
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    net = Network(args.model, 0, N, R, params, stream=stream)
+    if npar is not None:
+        net.set_node_param(npar)
+    net.set_state(y0_dev)
+
+    chunks = []
+    left = args.steps
+    while left > 0:
+        c = min(args.chunk, left)
+        chunks.append(c)
+        left -= c
+
+    # warm-up (also captures the CUDA graphs)
+    w = args.warmup
+    while w > 0:
+        c = min(args.chunk, w)
+        net.step(c, args.dt)
+        w -= c
+    for c in set(chunks):
+        net.step(c, args.dt)
+    net.set_state(y0_dev)
+    net.sync()
+
+    # --- device-resident timing: K RK4 steps in chunks, L2 flushed between chunks
+    clocks = ClockSampler(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in chunks]
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    for (a, b), c in zip(ev, chunks):
+        flush.zero_()
+        a.record(stream)
+        net.step(c, args.dt)
+        b.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier(world)
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    ms = max_over_ranks(ms, world)
+    y_check = net.get_state()  # surfaces any device error
+    assert np.isfinite(y_check).all()
+    node_steps = float(N) * args.steps * world
+    value = node_steps / (ms * 1e-3)
+
+    # --- end to end through the public API with host buffers: each iteration
+    # loads its input state from pinned host memory, steps, reads the result back
+    pin_in = torch.from_numpy(y0_host).pin_memory()
+    pin_out = torch.empty(d * N, dtype=torch.float64).pin_memory()
+    e2e_chunks = chunks[: max(1, min(len(chunks), 10))]
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for c in e2e_chunks:
+        net.set_state(pin_in.numpy())
+        net.step(c, args.dt)
+        net.get_state(pin_out.numpy())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+    e2e_steps = sum(e2e_chunks)
+    e2e_value = float(N) * e2e_steps * world / e2e_s
+    state_bytes = 8 * d * N
+
+    # --- dominant kernel: the ring stage kernel (4 launches per RK4 step)
+    launches = 4 * args.steps
+    avg_launch_s = ms * 1e-3 / launches
+    alg_bytes_launch = RING_BYTES[args.model] / 4 * N
+    alg_flops_launch = RING_FLOPS[args.model] / 4 * N
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except OSError:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    fp64_peak_gflops = 2 * 504.3  # measured DFMA rate x 2 flops
+    achieved_gflops = alg_flops_launch / avg_launch_s / 1e9
+    achieved_gbs = alg_bytes_launch / avg_launch_s / 1e9
+    roofline = {"bound": "alu", "achieved": achieved_gflops, "peak": fp64_peak_gflops, "unit": "GFLOP/s",
+                "frac": achieved_gflops / fp64_peak_gflops, "traffic": None,
+                "hbm_achieved_gbs": achieved_gbs, "hbm_peak_gbs": hbm_peak,
+                "hbm_frac": achieved_gbs / hbm_peak,
+                "note": "FP64 pipe of measured DFMA throughput; HBM fraction from algorithmic bytes"}
+
+    line = {"metric": "FP64 node-steps/s", "value": value, "unit": "node-steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_of(args, N, R),
+            "e2e": {"value": e2e_value, "unit": "node-steps/s",
+                    "h2d_bytes_per_step": state_bytes / max(1, e2e_chunks[0]),
+                    "d2h_bytes_per_step": state_bytes / max(1, e2e_chunks[0])},
+            "gpu_launches": launches, "roofline": roofline, "clocks": clk}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args, N, R, params, args.cpu_seconds)
+    net.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,7 +1,5 @@
 // Device helpers shared by the stage kernels: fixed-point conversions, warp
-// scans of 64-bit integers, and the single-pass decoupled look-back over exact
-// 128-bit tile sums (Merrill & Garland, "Single-pass Parallel Prefix Scan with
-// Decoupled Look-back", NVIDIA TR 2016).
+// scans of 64-bit integers, and the exact cross-CTA prefix of tile sums.
 //
 // Why fixed point: GB300 executes FP64 at about 1/68 of its FP32 rate, while
 // 64-bit integer adds run on the integer pipes.  A coupled quantity f (sin/cos
@@ -23,9 +21,6 @@ typedef unsigned __int128 u128;
 
 // Device error word bits (mapped to sim_status on the host).
 enum : unsigned { ERR_TIMEOUT = 1u, ERR_RANGE = 2u };
-
-// Bound on spin iterations of any cross-CTA wait (~1 s with the back-off).
-constexpr int kSpinLimit = 1 << 22;
 
 __device__ __forceinline__ void raise_error(unsigned *err, unsigned bit)
 {
@@ -105,37 +100,19 @@ __device__ __forceinline__ int64_t warp_incl_scan(int64_t v)
 }
 
 // ---------------------------------------------------------------------------
-// Decoupled look-back over CTA tiles with exact 128-bit payloads.
-//
-// Tickets: every CTA of a launch draws ticket = atomicAdd(counter, 1); with
-// exactly nctas CTAs per launch, tile = ticket % nctas and the launch epoch is
-// ticket / nctas + 1.  Tiles are therefore processed in ticket order (a CTA only
-// waits for tiles whose CTAs have already started), and flags carry the epoch,
-// so the slots never need resetting between launches.
-struct LookbackSlot {
-    unsigned long long flag; // epoch * 4 + status (1 = aggregate, 2 = inclusive)
-    unsigned long long pad;
-    i128 agg[2];
-    i128 inc[2];
-};
-
-__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long *p)
-{
-    unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void st_release(unsigned long long *p, unsigned long long v)
-{
-    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
+// Cross-CTA prefix without waiting: every CTA publishes its sub-tile totals,
+// and the last CTA of the launch to finish (a monotonically increasing done
+// counter, taken modulo the grid size, so it never needs resetting) scans
+// them.  No CTA ever waits for another, so nothing can hang.
 
 __device__ __forceinline__ i128 ld_cg_i128(const i128 *p)
 {
     const longlong2 v = __ldcg(reinterpret_cast<const longlong2 *>(p));
     return (i128)(u128)(unsigned long long)v.x | ((i128)v.y << 64);
 }
+
+__device__ __forceinline__ i128 ld_cg(const int64_t *p) { return (i128)__ldcg(p); }
+__device__ __forceinline__ i128 ld_cg(const i128 *p) { return ld_cg_i128(p); }
 
 __device__ __forceinline__ void st_i128(i128 *p, i128 v)
 {
@@ -145,49 +122,76 @@ __device__ __forceinline__ void st_i128(i128 *p, i128 v)
     *reinterpret_cast<longlong2 *>(p) = w;
 }
 
-// Called by one thread.  Publishes this tile's aggregate, looks back for the
-// exclusive prefix, publishes the inclusive prefix, and returns the exclusive
-// prefix in excl[0..NQ).  On a wait that exceeds kSpinLimit it raises
-// ERR_TIMEOUT and carries on with what it has (results are then invalid, but
-// every CTA terminates).
-template <int NQ>
-__device__ void lookback(LookbackSlot *slots, long long tile, unsigned long long epoch,
-                         const i128 (&agg)[NQ], i128 (&excl)[NQ], unsigned *err)
+__device__ __forceinline__ i128 shfl_up_i128(i128 v, int o)
 {
+    const long long lo = (long long)(unsigned long long)(u128)v, hi = (long long)(v >> 64);
+    const long long l2 = __shfl_up_sync(0xffffffffu, lo, o), h2 = __shfl_up_sync(0xffffffffu, hi, o);
+    return (i128)(u128)(unsigned long long)l2 | ((i128)h2 << 64);
+}
+
+// Called by every thread of one CTA (blockDim.x a multiple of 32).  Writes the
+// exclusive prefix of in[0..n) to out[0..n] (out[n] = total) and returns the
+// total.  in is read through L2 (it was written by other CTAs of this launch).
+template <int E, typename T>
+__device__ i128 block_exclusive_scan(const T *in, i128 *out, int64_t n)
+{
+    __shared__ i128 s_w[32];
+    __shared__ i128 s_carry;
+    const int t = threadIdx.x, nt = blockDim.x, lane = t & 31, warp = t >> 5, nw = nt >> 5;
+    if (t == 0) s_carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < n; base += (int64_t)nt * E) {
+        const int64_t b0 = base + (int64_t)t * E;
+        i128 v[E];
+        i128 run = 0;
 #pragma unroll
-    for (int c = 0; c < NQ; ++c) excl[c] = 0;
-    LookbackSlot *me = slots + tile;
-    if (tile > 0) {
-#pragma unroll
-        for (int c = 0; c < NQ; ++c) st_i128(&me->agg[c], agg[c]);
-        __threadfence();
-        st_release(&me->flag, epoch * 4ull + 1ull);
-        for (long long p = tile - 1; p >= 0; --p) {
-            const LookbackSlot *s = slots + p;
-            unsigned long long f = ld_acquire(&s->flag);
-            int spins = 0;
-            while ((f >> 2) != epoch || (f & 3ull) == 0ull) {
-                if (++spins > kSpinLimit) {
-                    raise_error(err, ERR_TIMEOUT);
-                    break;
-                }
-                __nanosleep(spins < 64 ? 20 : 200);
-                f = ld_acquire(&s->flag);
-            }
-            if ((f >> 2) != epoch) break; // timed out
-            if ((f & 3ull) == 2ull) {
-#pragma unroll
-                for (int c = 0; c < NQ; ++c) excl[c] += ld_cg_i128(&s->inc[c]);
-                break;
-            }
-#pragma unroll
-            for (int c = 0; c < NQ; ++c) excl[c] += ld_cg_i128(&s->agg[c]);
+        for (int e = 0; e < E; ++e) {
+            v[e] = (b0 + e < n) ? ld_cg(in + b0 + e) : (i128)0;
+            run += v[e];
         }
-    }
+        i128 x = run;
 #pragma unroll
-    for (int c = 0; c < NQ; ++c) st_i128(&me->inc[c], excl[c] + agg[c]);
-    __threadfence();
-    st_release(&me->flag, epoch * 4ull + 2ull);
+        for (int o = 1; o < 32; o <<= 1) {
+            const i128 y = shfl_up_i128(x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_w[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            i128 w = lane < nw ? s_w[lane] : (i128)0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const i128 y = shfl_up_i128(w, o);
+                if (lane >= o) w += y;
+            }
+            if (lane < nw) s_w[lane] = w;
+        }
+        __syncthreads();
+        i128 acc = s_carry + (warp ? s_w[warp - 1] : (i128)0) + (x - run);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            if (b0 + e < n) st_i128(out + b0 + e, acc);
+            acc += v[e];
+        }
+        __syncthreads();
+        if (t == 0) s_carry += s_w[nw - 1];
+        __syncthreads();
+    }
+    const i128 total = s_carry;
+    if (t == 0) st_i128(out + n, total);
+    return total;
+}
+
+// Called by one thread after it made its global writes visible (__threadfence).
+// Returns true for the last of `count` arrivals on a monotonically increasing
+// counter; the counter never needs resetting because every launch adds exactly
+// `count` arrivals to it.
+__device__ __forceinline__ bool last_arrival(unsigned long long *ctr, unsigned long long count)
+{
+    const unsigned long long done = atomicAdd(ctr, 1ull);
+    const bool last = ((done + 1ull) % count) == 0ull;
+    if (last) __threadfence();
+    return last;
 }
 
 } // namespace simk

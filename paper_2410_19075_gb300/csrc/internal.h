@@ -9,18 +9,18 @@
 
 namespace simk {
 
-constexpr int kRingThreads = 256;       // threads per CTA
-constexpr int kRingNodesPerThread = 4;  // consecutive nodes per thread
-constexpr int kRingTile = kRingThreads * kRingNodesPerThread; // nodes per CTA
-constexpr int kSubTile = 256;           // nodes per exact-prefix sub-tile
+constexpr int kRingThreads = 256;       // threads per CTA, one node each
+constexpr int kSubTile = 256;           // nodes per CTA = exact-prefix sub-tile
 constexpr int kSubLog2 = 8;
+constexpr int kGroup = 64;              // sub-tiles per prefix group
+constexpr int kGroupLog2 = 6;
 
 // Device buffers and sizes of one ring network (plain path).
 struct RingPlan {
     int model;
     int64_t N, R;
-    int64_t nsub;  // ceil(N / kSubTile)
-    int64_t nctas; // ceil(N / kRingTile)
+    int64_t nsub;    // ceil(N / kSubTile) = CTAs per stage launch
+    int64_t ngroups; // ceil(nsub / kGroup)
     int F, lim;    // fixed-point grid 2^-F, range |f| < 2^lim
     ModelParams mp;
     double *y;          // D * N, the state y_n
@@ -28,9 +28,12 @@ struct RingPlan {
     double *xg[2];      // NX * N each, local stage-input variables (HH gates)
     const double *node_param; // N (HH I_ext) or nullptr
     int64_t *lam[2];    // NQ * N each: inclusive prefix of Q(f) inside each sub-tile
-    i128 *ofs[2];       // NQ * (nsub + 1) each: exclusive prefix at sub-tile starts
-    LookbackSlot *slots; // nctas
-    unsigned long long *ticket;
+    i128 *ingrp[2];     // NQ * nsub each: exclusive prefix of each sub-tile inside its group
+    i128 *grpofs[2];    // NQ * (ngroups + 1) each: exclusive prefix at group starts, then the total
+    int64_t *subtot;    // NQ * nsub: sub-tile totals (scratch of the launch)
+    i128 *grptot;       // NQ * ngroups: group totals (scratch of the launch)
+    unsigned long long *grp_ctr; // ngroups arrival counters
+    unsigned long long *top_ctr; // arrival counter of the groups
     unsigned *err;
     double *obs;        // order-parameter ring buffer
     int64_t obs_cap;

@@ -49,7 +49,9 @@ template <> struct Model<0> {
 //   du/dt = (u - u^3/3 - v + (sigma/K) [b00 Cu + b01 Cv]) / eps
 //   dv/dt =  u + a        + (sigma/K) [b10 Cu + b11 Cv]
 // with Cu = sum_{j in W(i)} (u_j - u_i) = W_u - wsize * Q(u_i), exact in fixed point.
-// c = {1/eps, a, sigma/K, b00, b01, b10, b11}.  Coupled quantity (u, v).
+// c = {1/eps, a, (sigma/K) b00/eps, (sigma/K) b01/eps, (sigma/K) b10, (sigma/K) b11}
+// (constants folded on the host so that the RHS costs 9 FP64 instructions).
+// Coupled quantity (u, v).
 template <> struct Model<1> {
     static constexpr int D = 2, NQ = 2, NX = 0, F = 51;
     __device__ __forceinline__ static void coupled(const double (&x)[D], double (&f)[NQ])
@@ -64,8 +66,10 @@ template <> struct Model<1> {
         const double Cu = fixed_to_double(W[0] - (i128)qo[0] * P.wsize, F_);
         const double Cv = fixed_to_double(W[1] - (i128)qo[1] * P.wsize, F_);
         const double u = fo[0], v = fo[1];
-        k[0] = (u - u * u * u * (1.0 / 3.0) - v + P.c[2] * (P.c[3] * Cu + P.c[4] * Cv)) * P.c[0];
-        k[1] = u + P.c[1] + P.c[2] * (P.c[5] * Cu + P.c[6] * Cv);
+        const double w = fma(u * u, -1.0 / 3.0, 1.0);      // 1 - u^2/3
+        const double local = fma(u, w, -v);                // u - u^3/3 - v
+        k[0] = fma(P.c[0], local, fma(P.c[2], Cu, P.c[3] * Cv));
+        k[1] = fma(P.c[4], Cu, fma(P.c[5], Cv, u + P.c[1]));
     }
 };
 

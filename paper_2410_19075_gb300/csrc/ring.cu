@@ -9,8 +9,9 @@
 //   a5  RK4 accumulate acc += b_s k_s (stage 4: y <- y + dt/6 (acc + k_4));
 //   a1  next stage input x_{s+1} = y + c_{s+1} dt k_s;
 //   a2  coupled quantity f(x_{s+1}), its exact prefix inside each 256-node
-//       sub-tile, and the prefix at sub-tile starts through a single-pass
-//       decoupled look-back across CTAs;
+//       sub-tile (one CTA), and, without any CTA waiting for another, the exact
+//       prefix at every sub-tile start: the last CTA to finish in each group of
+//       64 sub-tiles scans that group, and the last group scans the groups;
 //   a6  (stage 4) the Kuramoto order parameter of y_{n+1} from the global totals.
 // The prologue kernel does a1/a2/a6 for the initial state.
 #include "internal.h"
@@ -21,9 +22,9 @@ struct RingStageArgs {
     RingPlan p;
     double dt;
     const int64_t *lam_in;
-    const i128 *ofs_in;
+    const i128 *ingrp_in, *grpofs_in;
     int64_t *lam_out;
-    i128 *ofs_out;
+    i128 *ingrp_out, *grpofs_out;
     const double *x_in; // local stage-input variables of this stage (HH gates)
     double *x_out;      // local stage-input variables of the next stage
 };
@@ -34,8 +35,21 @@ __device__ __forceinline__ i128 ldg_i128(const i128 *p)
     return (i128)(u128)(unsigned long long)v.x | ((i128)v.y << 64);
 }
 
-// P(p) = sum_{j<p} Q(f_j) over the periodic extension of the ring, p in [-N, 2N).
-__device__ __forceinline__ i128 prefix_at(const int64_t *lam, const i128 *ofs, int64_t N, int64_t p, i128 tot)
+__device__ __forceinline__ i128 warp_incl_scan_i128(i128 v)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const i128 t = shfl_up_i128(v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// P(p) = sum_{j<p} Q(f_j) over the periodic extension of the ring, p in [-N, 2N):
+// group offset + sub-tile offset inside the group + prefix inside the sub-tile.
+__device__ __forceinline__ i128 prefix_at(const int64_t *lam, const i128 *ingrp, const i128 *grpofs, int64_t N,
+                                          int64_t p, i128 tot)
 {
     i128 add = 0;
     if (p < 0) {
@@ -45,59 +59,56 @@ __device__ __forceinline__ i128 prefix_at(const int64_t *lam, const i128 *ofs, i
         p -= N;
         add = tot;
     }
-    i128 v = ldg_i128(ofs + (p >> kSubLog2)) + add;
+    const int64_t sub = p >> kSubLog2;
+    i128 v = ldg_i128(grpofs + (sub >> kGroupLog2)) + ldg_i128(ingrp + sub) + add;
     if (p & (kSubTile - 1)) v += (i128)__ldg(lam + p - 1);
     return v;
 }
 
+template <int M> struct MinBlocks { static constexpr int value = 4; };
+template <> struct MinBlocks<2> { static constexpr int value = 2; };
+
+// One 256-node sub-tile per CTA, one node per thread.
 template <int M, int STAGE>
-__global__ void __launch_bounds__(kRingThreads) ring_stage_kernel(const RingStageArgs a)
+__global__ void __launch_bounds__(kRingThreads, MinBlocks<M>::value) ring_stage_kernel(const RingStageArgs a)
 {
     using Mo = Model<M>;
-    constexpr int D = Mo::D, NQ = Mo::NQ, NX = Mo::NX, V = kRingNodesPerThread;
+    constexpr int D = Mo::D, NQ = Mo::NQ, NX = Mo::NX;
     constexpr int XOFF = D - NX; // first local (non-coupled) state variable
+    constexpr int NW = kRingThreads / 32;
     const RingPlan &P = a.p;
-    __shared__ unsigned long long s_ticket;
-    __shared__ int64_t s_wtot[kRingThreads / 32][NQ];
-    __shared__ i128 s_excl[NQ];
+    __shared__ int64_t s_wtot[NW][NQ];
+    __shared__ int s_last;
 
-    if (threadIdx.x == 0) s_ticket = atomicAdd(P.ticket, 1ull);
-    __syncthreads();
-    const unsigned long long ticket = s_ticket;
-    const long long tile = (long long)(ticket % (unsigned long long)P.nctas);
-    const unsigned long long epoch = ticket / (unsigned long long)P.nctas + 1ull;
-    const int64_t N = P.N;
-    const int64_t base = (int64_t)tile * kRingTile + (int64_t)threadIdx.x * V;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t N = P.N, nsub = P.nsub, ngroups = P.ngroups;
+    const int64_t sub = blockIdx.x;
+    const int64_t i = sub * kSubTile + tid;
 
-    double xn[V][D];
-    if (STAGE == 0) {
+    int64_t qv[NQ];
+    bool ok = true;
 #pragma unroll
-        for (int q = 0; q < V; ++q)
+    for (int c = 0; c < NQ; ++c) qv[c] = 0;
+    if (i < N) {
+        double xn[D];
+        if (STAGE == 0) {
 #pragma unroll
-            for (int v = 0; v < D; ++v) xn[q][v] = (base + q < N) ? P.y[v * N + base + q] : 0.0;
-    } else {
-        i128 tot[NQ];
-#pragma unroll
-        for (int c = 0; c < NQ; ++c) tot[c] = ldg_i128(a.ofs_in + c * (P.nsub + 1) + P.nsub);
-#pragma unroll
-        for (int q = 0; q < V; ++q) {
-            const int64_t i = base + q;
-            if (i >= N) {
-#pragma unroll
-                for (int v = 0; v < D; ++v) xn[q][v] = 0.0;
-                continue;
-            }
+            for (int v = 0; v < D; ++v) xn[v] = P.y[v * N + i];
+        } else {
             int64_t qo[NQ];
             double fo[NQ];
             i128 W[NQ];
 #pragma unroll
             for (int c = 0; c < NQ; ++c) {
                 const int64_t *lam = a.lam_in + c * N;
-                const i128 *ofs = a.ofs_in + c * (P.nsub + 1);
+                const i128 *ingrp = a.ingrp_in + c * nsub;
+                const i128 *grpofs = a.grpofs_in + c * (ngroups + 1);
+                const i128 tot = ldg_i128(grpofs + ngroups);
                 const int64_t l = __ldg(lam + i);
-                qo[c] = (i & (kSubTile - 1)) ? l - __ldg(lam + i - 1) : l;
+                qo[c] = tid ? l - __ldg(lam + i - 1) : l; // tid = position in the sub-tile
                 fo[c] = fixed_to_double(qo[c], P.F);
-                W[c] = prefix_at(lam, ofs, N, i + P.R + 1, tot[c]) - prefix_at(lam, ofs, N, i - P.R, tot[c]);
+                W[c] = prefix_at(lam, ingrp, grpofs, N, i + P.R + 1, tot) -
+                       prefix_at(lam, ingrp, grpofs, N, i - P.R, tot);
             }
             double X[NX > 0 ? NX : 1];
 #pragma unroll
@@ -110,99 +121,92 @@ __global__ void __launch_bounds__(kRingThreads) ring_stage_kernel(const RingStag
                 const double yv = P.y[v * N + i];
                 if (STAGE == 1) {
                     P.acc[v * N + i] = k[v];
-                    xn[q][v] = yv + (0.5 * a.dt) * k[v];
+                    xn[v] = yv + (0.5 * a.dt) * k[v];
                 } else if (STAGE == 2) {
                     P.acc[v * N + i] = P.acc[v * N + i] + 2.0 * k[v];
-                    xn[q][v] = yv + (0.5 * a.dt) * k[v];
+                    xn[v] = yv + (0.5 * a.dt) * k[v];
                 } else if (STAGE == 3) {
                     P.acc[v * N + i] = P.acc[v * N + i] + 2.0 * k[v];
-                    xn[q][v] = yv + a.dt * k[v];
+                    xn[v] = yv + a.dt * k[v];
                 } else {
                     const double yn = yv + (a.dt / 6.0) * (P.acc[v * N + i] + k[v]);
                     P.y[v * N + i] = yn;
-                    xn[q][v] = yn;
+                    xn[v] = yn;
                 }
             }
             if (NX > 0 && STAGE >= 1 && STAGE <= 3) {
 #pragma unroll
-                for (int g = 0; g < NX; ++g) a.x_out[g * N + i] = xn[q][XOFF + g];
+                for (int g = 0; g < NX; ++g) a.x_out[g * N + i] = xn[XOFF + g];
             }
         }
-    }
-
-    // a2: coupled quantity of the next stage input on the fixed-point grid.
-    int64_t qv[V][NQ];
-    bool ok = true;
-#pragma unroll
-    for (int q = 0; q < V; ++q) {
+        // a2: coupled quantity of the next stage input on the fixed-point grid
         double f[NQ];
-        Mo::coupled(xn[q], f);
+        Mo::coupled(xn, f);
 #pragma unroll
-        for (int c = 0; c < NQ; ++c) qv[q][c] = (base + q < N) ? to_fixed(f[c], P.F, P.lim, ok) : 0;
+        for (int c = 0; c < NQ; ++c) qv[c] = to_fixed(f[c], P.F, P.lim, ok);
     }
     if (!ok) raise_error(P.err, ERR_RANGE);
 
-    // Exact inclusive prefix inside each 256-node sub-tile (= 2 warps).
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int64_t tsum[NQ], incl[NQ];
+    // Exact inclusive prefix inside the sub-tile (warp scans + preceding warps).
 #pragma unroll
     for (int c = 0; c < NQ; ++c) {
-        int64_t run = 0;
-#pragma unroll
-        for (int q = 0; q < V; ++q) {
-            run += qv[q][c];
-            qv[q][c] = run;
-        }
-        tsum[c] = run;
-        incl[c] = warp_incl_scan(run);
-        if (lane == 31) s_wtot[warp][c] = incl[c];
+        qv[c] = warp_incl_scan(qv[c]);
+        if (lane == 31) s_wtot[warp][c] = qv[c];
     }
     __syncthreads();
 #pragma unroll
     for (int c = 0; c < NQ; ++c) {
-        const int64_t off = incl[c] - tsum[c] + ((warp & 1) ? s_wtot[warp - 1][c] : 0);
-#pragma unroll
-        for (int q = 0; q < V; ++q)
-            if (base + q < N) a.lam_out[c * N + base + q] = off + qv[q][c];
+        int64_t off = 0;
+        for (int w = 0; w < warp; ++w) off += s_wtot[w][c];
+        if (i < N) a.lam_out[c * N + i] = off + qv[c];
     }
 
-    // Exclusive prefix of this CTA's tile across the ring.
-    if (threadIdx.x == 0) {
-        i128 agg[NQ], excl[NQ];
+    // Level 1: the last CTA of each group of 64 sub-tiles scans the group.
+    const int64_t g = sub >> kGroupLog2, s0 = g << kGroupLog2;
+    const int64_t gsize = nsub - s0 < kGroup ? nsub - s0 : kGroup;
+    if (tid == 0) {
 #pragma unroll
         for (int c = 0; c < NQ; ++c) {
-            agg[c] = 0;
-            for (int w = 0; w < kRingThreads / 32; ++w) agg[c] += (i128)s_wtot[w][c];
+            int64_t t = 0;
+            for (int w = 0; w < NW; ++w) t += s_wtot[w][c];
+            P.subtot[c * nsub + sub] = t;
         }
-        lookback<NQ>(P.slots, tile, epoch, agg, excl, P.err);
-#pragma unroll
-        for (int c = 0; c < NQ; ++c) s_excl[c] = excl[c];
-        if (tile == P.nctas - 1) {
-            // Global totals: the last prefix entry, and the order parameter.
-#pragma unroll
-            for (int c = 0; c < NQ; ++c) a.ofs_out[c * (P.nsub + 1) + P.nsub] = excl[c] + agg[c];
-            if (M == 0 && (STAGE == 0 || STAGE == 4)) {
-                const double S = fixed_to_double(excl[0] + agg[0], P.F);
-                const double C = fixed_to_double(excl[NQ - 1] + agg[NQ - 1], P.F);
-                const unsigned long long n = *P.obs_ctr;
-                P.obs[n % (unsigned long long)P.obs_cap] = sqrt(S * S + C * C) / (double)N;
-                *P.obs_ctr = n + 1;
-            }
-        }
+        __threadfence();
+        s_last = last_arrival(P.grp_ctr + g, (unsigned long long)gsize);
     }
     __syncthreads();
-    constexpr int kSubPerCta = kRingTile / kSubTile;
-    if (threadIdx.x < kSubPerCta) {
-        const int s = threadIdx.x;
-        const int64_t sub = (int64_t)tile * kSubPerCta + s;
-        if (sub < P.nsub) {
+    if (!s_last) return;
+    if (warp == 0) {
 #pragma unroll
-            for (int c = 0; c < NQ; ++c) {
-                i128 v = s_excl[c];
-                for (int t = 0; t < s; ++t) v += (i128)s_wtot[2 * t][c] + (i128)s_wtot[2 * t + 1][c];
-                a.ofs_out[c * (P.nsub + 1) + sub] = v;
-            }
+        for (int c = 0; c < NQ; ++c) {
+            const int64_t *st = P.subtot + c * nsub + s0;
+            const i128 v0 = 2 * lane < gsize ? (i128)__ldcg(st + 2 * lane) : (i128)0;
+            const i128 v1 = 2 * lane + 1 < gsize ? (i128)__ldcg(st + 2 * lane + 1) : (i128)0;
+            const i128 x = warp_incl_scan_i128(v0 + v1);
+            const i128 ex = x - v0 - v1;
+            i128 *ig = a.ingrp_out + c * nsub + s0;
+            if (2 * lane < gsize) st_i128(ig + 2 * lane, ex);
+            if (2 * lane + 1 < gsize) st_i128(ig + 2 * lane + 1, ex + v0);
+            if (lane == 31) st_i128(P.grptot + c * ngroups + g, x);
         }
+        __threadfence();
+    }
+    __syncthreads();
+    if (tid == 0) s_last = last_arrival(P.top_ctr, (unsigned long long)ngroups);
+    __syncthreads();
+    if (!s_last) return;
+
+    // Level 2: the last group scans the group totals (and records the totals).
+    i128 total[NQ];
+#pragma unroll
+    for (int c = 0; c < NQ; ++c)
+        total[c] = block_exclusive_scan<8>(P.grptot + c * ngroups, a.grpofs_out + c * (ngroups + 1), ngroups);
+    if (M == 0 && (STAGE == 0 || STAGE == 4) && tid == 0) {
+        const double S = fixed_to_double(total[0], P.F);
+        const double C = fixed_to_double(total[NQ - 1], P.F);
+        const unsigned long long n = *P.obs_ctr;
+        P.obs[n % (unsigned long long)P.obs_cap] = sqrt(S * S + C * C) / (double)N;
+        *P.obs_ctr = n + 1;
     }
 }
 
@@ -214,10 +218,13 @@ static cudaError_t launch_stage(int stage, const RingPlan &p, double dt, cudaStr
     a.p = p;
     a.dt = dt;
     const int in = (stage + 1) & 1, out = stage & 1; // stage 0 writes buffer 0
+    const int o = stage == 0 ? 0 : out;
     a.lam_in = stage ? p.lam[in] : nullptr;
-    a.ofs_in = stage ? p.ofs[in] : nullptr;
-    a.lam_out = p.lam[stage == 0 ? 0 : out];
-    a.ofs_out = p.ofs[stage == 0 ? 0 : out];
+    a.ingrp_in = stage ? p.ingrp[in] : nullptr;
+    a.grpofs_in = stage ? p.grpofs[in] : nullptr;
+    a.lam_out = p.lam[o];
+    a.ingrp_out = p.ingrp[o];
+    a.grpofs_out = p.grpofs[o];
     a.x_in = nullptr;
     a.x_out = nullptr;
     if (NX > 0) {
@@ -226,7 +233,7 @@ static cudaError_t launch_stage(int stage, const RingPlan &p, double dt, cudaStr
         a.x_in = src[stage];
         a.x_out = dst[stage];
     }
-    const dim3 grid((unsigned)p.nctas), block(kRingThreads);
+    const dim3 grid((unsigned)p.nsub), block(kRingThreads);
     switch (stage) {
     case 0: ring_stage_kernel<M, 0><<<grid, block, 0, s>>>(a); break;
     case 1: ring_stage_kernel<M, 1><<<grid, block, 0, s>>>(a); break;

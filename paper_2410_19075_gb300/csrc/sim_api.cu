@@ -47,7 +47,8 @@ int ceil_log2(uint64_t x)
 // Byte layout of a network's device block.  Each entry is an offset.
 struct Layout {
     size_t total = 0;
-    size_t y, acc, xg0, xg1, npar, lam0, lam1, ofs0, ofs1, slots, f, sx, sxy, partial, ctrs, obs;
+    size_t y, acc, xg0, xg1, npar, lam0, lam1, ingrp0, ingrp1, grpofs0, grpofs1, subtot, grptot, grpctr;
+    size_t f, sx, sxy, partial, ctrs, obs;
 };
 
 Layout layout_of(int model, int topo, int64_t N, int64_t R)
@@ -62,7 +63,7 @@ Layout layout_of(int model, int topo, int64_t N, int64_t R)
     const int d = model_dim(model);
     if (topo == SIM_RING) {
         const int nq = model_nq(model), nx = model_nx(model);
-        const int64_t nsub = (N + kSubTile - 1) / kSubTile, nctas = (N + kRingTile - 1) / kRingTile;
+        const int64_t nsub = (N + kSubTile - 1) / kSubTile, ngroups = (nsub + kGroup - 1) / kGroup;
         L.y = take(sizeof(double) * d * N);
         L.acc = take(sizeof(double) * d * N);
         L.xg0 = take(sizeof(double) * nx * N);
@@ -70,9 +71,13 @@ Layout layout_of(int model, int topo, int64_t N, int64_t R)
         L.npar = take(model == SIM_HH ? sizeof(double) * N : 0);
         L.lam0 = take(sizeof(int64_t) * nq * N);
         L.lam1 = take(sizeof(int64_t) * nq * N);
-        L.ofs0 = take(sizeof(i128) * nq * (nsub + 1));
-        L.ofs1 = take(sizeof(i128) * nq * (nsub + 1));
-        L.slots = take(sizeof(LookbackSlot) * nctas);
+        L.ingrp0 = take(sizeof(i128) * nq * nsub);
+        L.ingrp1 = take(sizeof(i128) * nq * nsub);
+        L.grpofs0 = take(sizeof(i128) * nq * (ngroups + 1));
+        L.grpofs1 = take(sizeof(i128) * nq * (ngroups + 1));
+        L.subtot = take(sizeof(int64_t) * nq * nsub);
+        L.grptot = take(sizeof(i128) * nq * ngroups);
+        L.grpctr = take(sizeof(unsigned long long) * ngroups);
     } else {
         const int64_t n = N * N * N;
         const int64_t nblk = ((N + 127) / 128) * N;
@@ -255,14 +260,13 @@ int sim_create(sim_t *out, int model, int topology, int64_t N, int64_t radius, c
         mp.c[2] = std::sin(params[2]);
         mp.c[3] = std::cos(params[2]);
     } else if (model == SIM_FHN) {
-        const double ph = params[3];
-        mp.c[0] = 1.0 / params[0];
+        const double ph = params[3], inv_eps = 1.0 / params[0], sK = params[2] / K;
+        mp.c[0] = inv_eps;
         mp.c[1] = params[1];
-        mp.c[2] = params[2] / K;
-        mp.c[3] = std::cos(ph);
-        mp.c[4] = std::sin(ph);
-        mp.c[5] = -std::sin(ph);
-        mp.c[6] = std::cos(ph);
+        mp.c[2] = sK * std::cos(ph) * inv_eps;  // (sigma/K) B00 / eps
+        mp.c[3] = sK * std::sin(ph) * inv_eps;  // (sigma/K) B01 / eps
+        mp.c[4] = -sK * std::sin(ph);           // (sigma/K) B10
+        mp.c[5] = sK * std::cos(ph);            // (sigma/K) B11
     } else {
         mp.c[0] = 1.0 / params[0];
         for (int i = 1; i < 7; ++i) mp.c[i] = params[i];
@@ -275,7 +279,7 @@ int sim_create(sim_t *out, int model, int topology, int64_t N, int64_t radius, c
         p.N = N;
         p.R = radius;
         p.nsub = (N + kSubTile - 1) / kSubTile;
-        p.nctas = (N + kRingTile - 1) / kRingTile;
+        p.ngroups = (p.nsub + kGroup - 1) / kGroup;
         p.F = ring_F(model);
         p.lim = 54 - p.F;
         p.mp = mp;
@@ -286,10 +290,14 @@ int sim_create(sim_t *out, int model, int topology, int64_t N, int64_t radius, c
         p.node_param = model == SIM_HH ? reinterpret_cast<double *>(b + L.npar) : nullptr;
         p.lam[0] = reinterpret_cast<int64_t *>(b + L.lam0);
         p.lam[1] = reinterpret_cast<int64_t *>(b + L.lam1);
-        p.ofs[0] = reinterpret_cast<i128 *>(b + L.ofs0);
-        p.ofs[1] = reinterpret_cast<i128 *>(b + L.ofs1);
-        p.slots = reinterpret_cast<LookbackSlot *>(b + L.slots);
-        p.ticket = ticket;
+        p.ingrp[0] = reinterpret_cast<i128 *>(b + L.ingrp0);
+        p.ingrp[1] = reinterpret_cast<i128 *>(b + L.ingrp1);
+        p.grpofs[0] = reinterpret_cast<i128 *>(b + L.grpofs0);
+        p.grpofs[1] = reinterpret_cast<i128 *>(b + L.grpofs1);
+        p.subtot = reinterpret_cast<int64_t *>(b + L.subtot);
+        p.grptot = reinterpret_cast<i128 *>(b + L.grptot);
+        p.grp_ctr = reinterpret_cast<unsigned long long *>(b + L.grpctr);
+        p.top_ctr = ticket;
         p.err = h->err;
         p.obs = h->obs;
         p.obs_cap = kObsCap;
