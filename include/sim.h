@@ -133,6 +133,13 @@ int sim_sync(sim_t h);
 /* Steps completed (issued) since the last sim_set_state. */
 int64_t sim_steps_done(sim_t h);
 
+/* Evaluate the library's device elementary functions on n arguments (host
+ * buffers; synchronous), for accuracy checks: fn 0 = sin, 1 = cos, 2 = exp,
+ * 3 = reciprocal 1/x, 4 = x / (1 - exp(-x)).  These are the table-driven FP64
+ * routines the node right-hand sides use (Kuramoto phases, Hodgkin-Huxley
+ * rates of Eq. (1)).  Allocates and frees its own device buffers. */
+int sim_math_eval(int fn, const double *host_x, double *host_out, int64_t n);
+
 /* Message of the last non-OK status returned on this thread (never NULL). */
 const char *sim_last_error(void);
 

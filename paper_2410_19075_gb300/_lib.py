@@ -40,6 +40,7 @@ SIGNATURES = {
     "sim_rhs": (_int, [_vp, _vp, _i64]),
     "sim_observables": (_int, [_vp, _vp, _i64, ctypes.POINTER(_i64)]),
     "sim_sync": (_int, [_vp]),
+    "sim_math_eval": (_int, [_int, _vp, _vp, _i64]),
     "sim_steps_done": (_i64, [_vp]),
     "sim_last_error": (ctypes.c_char_p, []),
     "sim_destroy": (None, [_vp]),

@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(kCubeColThreads) cube_z_kernel(CubePlan p, dou
                 s1 += a1[kin * plane] - a1[kout * plane];
             }
             double sn, cn;
-            sincos(x, &sn, &cn);
+            fast_sincos(x, p.mp.tab, sn, cn);
             p.f[n] = sn;
             p.f[nodes + n] = cn;
             if (STAGE == 0 || STAGE == 4) {

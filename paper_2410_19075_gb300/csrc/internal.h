@@ -70,4 +70,7 @@ cudaError_t cube_prologue(const CubePlan &p, cudaStream_t s);
 cudaError_t cube_step(const CubePlan &p, double dt, cudaStream_t s);
 cudaError_t cube_rhs(const CubePlan &p, cudaStream_t s); // acc <- f(y)
 
+// Host-side values of the fast-math tables (long double, rounded to double).
+void fill_math_tables(double *sincos /* 2 * kSinTab */, double *exp2j /* kExpTab */);
+
 } // namespace simk

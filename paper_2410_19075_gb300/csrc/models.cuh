@@ -6,12 +6,14 @@
 // fixed-point integers, and a local right-hand side.
 #pragma once
 #include "common.cuh"
+#include "fastmath.cuh"
 
 namespace simk {
 
 // Derived constants, computed once on the host in FP64.
 struct ModelParams {
     double c[8];
+    MathTables tab;   // device tables of the fast elementary functions
     int64_t wsize;    // window size including the node itself (2R+1 or (2P+1)^3)
     int include_self; // 1: the node is one of its own links
 };
@@ -26,9 +28,9 @@ template <int M> struct Model;
 // c = {omega, mu/K, sin alpha, cos alpha}.  Coupled quantity (sin phi, cos phi).
 template <> struct Model<0> {
     static constexpr int D = 1, NQ = 2, NX = 0, F = 53;
-    __device__ __forceinline__ static void coupled(const double (&x)[D], double (&f)[NQ])
+    __device__ __forceinline__ static void coupled(const ModelParams &P, const double (&x)[D], double (&f)[NQ])
     {
-        sincos(x[0], &f[0], &f[1]);
+        fast_sincos(x[0], P.tab, f[0], f[1]);
     }
     __device__ __forceinline__ static void rhs(const ModelParams &P, int F_, const double (&fo)[NQ],
                                                const int64_t (&qo)[NQ], const i128 (&W)[NQ],
@@ -54,7 +56,7 @@ template <> struct Model<0> {
 // Coupled quantity (u, v).
 template <> struct Model<1> {
     static constexpr int D = 2, NQ = 2, NX = 0, F = 51;
-    __device__ __forceinline__ static void coupled(const double (&x)[D], double (&f)[NQ])
+    __device__ __forceinline__ static void coupled(const ModelParams &, const double (&x)[D], double (&f)[NQ])
     {
         f[0] = x[0];
         f[1] = x[1];
@@ -79,15 +81,10 @@ template <> struct Model<1> {
 //   dx/dt    = alpha_x(V) (1-x) - beta_x(V) x,   x in {m, h, n}
 // with CV = sum_{j in W(i)} (V_j - V_i) = W_V - wsize * Q(V_i), exact in fixed point.
 // c = {1/Cm, gNa, gK, gL, ENa, EK, EL, g/K}.  Coupled quantity V; the gates are
-// local variables.
-__device__ __forceinline__ double x_over_1mexp(double x)
-{
-    return x == 0.0 ? 1.0 : x / -expm1(-x);
-}
-
+// local variables.  Rates use the table-driven exp and reciprocal of fastmath.cuh.
 template <> struct Model<2> {
     static constexpr int D = 4, NQ = 1, NX = 3, F = 46;
-    __device__ __forceinline__ static void coupled(const double (&x)[D], double (&f)[NQ])
+    __device__ __forceinline__ static void coupled(const ModelParams &, const double (&x)[D], double (&f)[NQ])
     {
         f[0] = x[0];
     }
@@ -97,12 +94,13 @@ template <> struct Model<2> {
     {
         const double CV = fixed_to_double(W[0] - (i128)qo[0] * P.wsize, F_);
         const double V = fo[0], m = X[0], h = X[1], n = X[2];
-        const double am = x_over_1mexp((V + 40.0) * 0.1);
-        const double bm = 4.0 * exp(-(V + 65.0) * (1.0 / 18.0));
-        const double ah = 0.07 * exp(-(V + 65.0) * 0.05);
-        const double bh = 1.0 / (1.0 + exp(-(V + 35.0) * 0.1));
-        const double an = 0.1 * x_over_1mexp((V + 55.0) * 0.1);
-        const double bn = 0.125 * exp(-(V + 65.0) * 0.0125);
+        const MathTables &T = P.tab;
+        const double am = fast_x_over_1mexp(fma(V, 0.1, 4.0), T);                    // (V+40)/10
+        const double bm = 4.0 * fast_exp(fma(V, -1.0 / 18.0, -65.0 / 18.0), T);     // -(V+65)/18
+        const double ah = 0.07 * fast_exp(fma(V, -0.05, -3.25), T);                 // -(V+65)/20
+        const double bh = fast_rcp(1.0 + fast_exp(fma(V, -0.1, -3.5), T));          // -(V+35)/10
+        const double an = 0.1 * fast_x_over_1mexp(fma(V, 0.1, 5.5), T);             // (V+55)/10
+        const double bn = 0.125 * fast_exp(fma(V, -0.0125, -0.8125), T);            // -(V+65)/80
         const double m3h = m * m * m * h, n4 = (n * n) * (n * n);
         const double I = Iext - P.c[1] * m3h * (V - P.c[4]) - P.c[2] * n4 * (V - P.c[5]) -
                          P.c[3] * (V - P.c[6]) + P.c[7] * CV;

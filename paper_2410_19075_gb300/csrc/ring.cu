@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(kRingThreads, MinBlocks<M>::value) ring_stage_
         }
         // a2: coupled quantity of the next stage input on the fixed-point grid
         double f[NQ];
-        Mo::coupled(xn, f);
+        Mo::coupled(P.mp, xn, f);
 #pragma unroll
         for (int c = 0; c < NQ; ++c) qv[c] = to_fixed(f[c], P.F, P.lim, ok);
     }

@@ -5,6 +5,7 @@
 #include <cstring>
 #include <map>
 #include <string>
+#include <vector>
 
 #include "internal.h"
 #include "sim.h"
@@ -48,7 +49,7 @@ int ceil_log2(uint64_t x)
 struct Layout {
     size_t total = 0;
     size_t y, acc, xg0, xg1, npar, lam0, lam1, ingrp0, ingrp1, grpofs0, grpofs1, subtot, grptot, grpctr;
-    size_t f, sx, sxy, partial, ctrs, obs;
+    size_t f, sx, sxy, partial, ctrs, obs, tabs;
 };
 
 Layout layout_of(int model, int topo, int64_t N, int64_t R)
@@ -90,6 +91,7 @@ Layout layout_of(int model, int topo, int64_t N, int64_t R)
     }
     L.ctrs = take(64);
     L.obs = take(sizeof(double) * kObsCap);
+    L.tabs = take(sizeof(double) * (2 * kSinTab + kExpTab));
     L.total = o;
     return L;
 }
@@ -248,8 +250,21 @@ int sim_create(sim_t *out, int model, int topology, int64_t N, int64_t radius, c
     unsigned long long *ticket = ctrs + 2;
     h->obs = reinterpret_cast<double *>(b + L.obs);
 
+    // Tables of the fast elementary functions.
+    {
+        std::vector<double> tab(2 * kSinTab + kExpTab);
+        fill_math_tables(tab.data(), tab.data() + 2 * kSinTab);
+        e = cudaMemcpyAsync(b + L.tabs, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) {
+            sim_destroy(h);
+            return cuda_fail(e, "table upload");
+        }
+    }
     // Derived model constants (FP64 on the host).
     ModelParams mp{};
+    mp.tab.sincos = reinterpret_cast<const double2 *>(b + L.tabs);
+    mp.tab.exp2j = reinterpret_cast<const double *>(b + L.tabs) + 2 * kSinTab;
     const bool self = (flags & SIM_FLAG_INCLUDE_SELF) != 0;
     mp.include_self = self ? 1 : 0;
     mp.wsize = topology == SIM_RING ? 2 * radius + 1 : (2 * radius + 1) * (2 * radius + 1) * (2 * radius + 1);

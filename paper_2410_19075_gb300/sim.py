@@ -25,6 +25,14 @@ def _stream_ptr(stream):
     return int(stream.cuda_stream)  # torch.cuda.Stream
 
 
+def math_eval(fn: int, x) -> np.ndarray:
+    """Device elementary functions (0 sin, 1 cos, 2 exp, 3 1/x, 4 x/(1-exp(-x)))."""
+    a = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.empty_like(a)
+    check(lib().sim_math_eval(fn, a.ctypes.data, out.ctypes.data, a.size))
+    return out
+
+
 def workspace_bytes(model, topology, N, radius) -> int:
     return int(lib().sim_workspace_bytes(model, topology, N, radius))
 
