@@ -133,6 +133,31 @@ int sim_sync(sim_t h);
 /* Steps completed (issued) since the last sim_set_state. */
 int64_t sim_steps_done(sim_t h);
 
+/* RK4 steps of a ring network with no device allocation at all.
+ *
+ * The paper has no counterpart; this entry point is for callers that cannot
+ * allocate device memory while they run (for example a plugin inside an
+ * application that owns all device memory through its own fixed arena, or a
+ * service whose device footprint must not change after start-up).  The caller
+ * passes the state as a device buffer (dev_state: d * N doubles, SoA, updated in
+ * place) and, for SIM_HH, dev_node_param (N doubles of I_ext, or NULL for 0).
+ * Every other buffer lives in one static device array of this library (8 MiB,
+ * held by each GPU that loads the library until the process exits), so the
+ * ring must have N <= 65536 nodes; larger N returns SIM_EINVAL.  Arguments and
+ * model parameters are as for sim_create with topology SIM_RING.
+ * The work is issued on `stream` (a cudaStream_t, NULL = legacy default) and the
+ * call synchronises that stream before it returns, so that it can report
+ * SIM_ENONFINITE.  It calls no cudaMalloc, cudaFree or other allocator.
+ * The first call on each device does a one-time set-up with that device
+ * current (it looks up the static array's device address and copies the
+ * fast-math tables into it); make that first call before any stream capture.
+ * All calls share the static array: calls whose work overlaps on the GPU (other
+ * streams or host threads) race with each other and must be serialised by the
+ * caller. */
+int sim_ring_step_noalloc(int model, int64_t N, int64_t radius, const double *params, int n_params,
+                          unsigned flags, double *dev_state, const double *dev_node_param, int64_t n_steps,
+                          double dt, void *stream);
+
 /* Evaluate the library's device elementary functions on n arguments (host
  * buffers; synchronous), for accuracy checks: fn 0 = sin, 1 = cos, 2 = exp,
  * 3 = reciprocal 1/x, 4 = x / (1 - exp(-x)).  These are the table-driven FP64

@@ -41,6 +41,7 @@ SIGNATURES = {
     "sim_observables": (_int, [_vp, _vp, _i64, ctypes.POINTER(_i64)]),
     "sim_sync": (_int, [_vp]),
     "sim_math_eval": (_int, [_int, _vp, _vp, _i64]),
+    "sim_ring_step_noalloc": (_int, [_int, _i64, _i64, _dp, _int, _uint, _vp, _vp, _i64, _dbl, _vp]),
     "sim_steps_done": (_i64, [_vp]),
     "sim_last_error": (ctypes.c_char_p, []),
     "sim_destroy": (None, [_vp]),
