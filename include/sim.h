@@ -133,6 +133,40 @@ int sim_sync(sim_t h);
 /* Steps completed (issued) since the last sim_set_state. */
 int64_t sim_steps_done(sim_t h);
 
+/* ---------------------------------------------------------------------------
+ * Batches: many independent networks advanced together (the paper's "large
+ * number of small unconnected subnets within a single run", Section III.C, and
+ * its parameter and multistability studies, Section IV).  Ring members of the
+ * same model are stepped by one launch per RK4 stage whose CTAs are
+ * (member, 256-node sub-tile) work items; cube members by their own kernels.
+ * Every member keeps its own state, prefix buffers and observables, so results
+ * are bit-for-bit those of sim_step on each member alone.
+ */
+typedef struct sim_batch_handle *sim_batch_t;
+
+/* Group existing networks into a batch.  The batch does not own the members;
+ * they must outlive it and must not be stepped on their own streams while the
+ * batch's work is in flight.  stream: where the batch issues work (NULL =
+ * legacy default).  Errors: SIM_EINVAL (no members, NULL or duplicate member),
+ * SIM_ENOMEM, SIM_EDEVICE. */
+int sim_batch_create(sim_batch_t *out, const sim_t *members, int n_members, void *stream);
+
+/* Per-member step budgets (n_members values): a ring member with budget b stops
+ * after b more RK4 steps of the following sim_batch_step calls (its state then
+ * stays as it is); -1 = unlimited (the default).  Cube members take -1 only.
+ * Synchronises the batch stream. */
+int sim_batch_set_budgets(sim_batch_t b, const int64_t *steps);
+
+/* Advance every member by n_steps RK4 steps of size dt (asynchronous; CUDA
+ * graphs of 16 steps).  sim_steps_done() of each member is updated. */
+int sim_batch_step(sim_batch_t b, int64_t n_steps, double dt);
+
+/* Wait for the batch's work and report the first device error of any member. */
+int sim_batch_sync(sim_batch_t b);
+
+/* Free the batch's own tables (synchronises first); members are untouched. */
+void sim_batch_destroy(sim_batch_t b);
+
 /* RK4 steps of a ring network with no device allocation at all.
  *
  * The paper has no counterpart; this entry point is for callers that cannot

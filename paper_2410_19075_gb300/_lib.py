@@ -40,6 +40,11 @@ SIGNATURES = {
     "sim_rhs": (_int, [_vp, _vp, _i64]),
     "sim_observables": (_int, [_vp, _vp, _i64, ctypes.POINTER(_i64)]),
     "sim_sync": (_int, [_vp]),
+    "sim_batch_create": (_int, [ctypes.POINTER(_vp), ctypes.POINTER(_vp), _int, _vp]),
+    "sim_batch_set_budgets": (_int, [_vp, ctypes.POINTER(_i64)]),
+    "sim_batch_step": (_int, [_vp, _i64, _dbl]),
+    "sim_batch_sync": (_int, [_vp]),
+    "sim_batch_destroy": (None, [_vp]),
     "sim_math_eval": (_int, [_int, _vp, _vp, _i64]),
     "sim_ring_step_noalloc": (_int, [_int, _i64, _i64, _dp, _int, _uint, _vp, _vp, _i64, _dbl, _vp]),
     "sim_steps_done": (_i64, [_vp]),

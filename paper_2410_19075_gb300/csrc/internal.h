@@ -38,7 +38,21 @@ struct RingPlan {
     double *obs;        // order-parameter ring buffer
     int64_t obs_cap;
     unsigned long long *obs_ctr;
+    long long *steps_left; // batched runs with a step budget: steps still to do (else nullptr)
 };
+
+// Ring members of one model in a batch: device tables of the batched launch.
+struct RingBatchGroup {
+    int model;
+    int n_inst;
+    int64_t n_items;        // sum of the members' sub-tile counts = CTAs per launch
+    const RingPlan *plans;  // n_inst plans (device)
+    const int *inst_of_item; // n_items (device)
+    const int64_t *item_base; // n_inst: first item of each member (device)
+};
+
+// Batched ring stage kernels: one RK4 step of every member of the group.
+cudaError_t ring_batch_step(const RingBatchGroup &g, double dt, cudaStream_t s);
 
 // Ring: f(y) -> lam[0], ofs[0] and the order parameter of y (Kuramoto).
 cudaError_t ring_prologue(const RingPlan &p, cudaStream_t s);

@@ -18,9 +18,8 @@
 
 namespace simk {
 
-struct RingStageArgs {
-    RingPlan p;
-    double dt;
+// Buffers one stage reads and writes (chosen by the stage's parity).
+struct RingStageIO {
     const int64_t *lam_in;
     const i128 *ingrp_in, *grpofs_in;
     int64_t *lam_out;
@@ -28,6 +27,29 @@ struct RingStageArgs {
     const double *x_in; // local stage-input variables of this stage (HH gates)
     double *x_out;      // local stage-input variables of the next stage
 };
+
+// Stage 0 (prologue) writes buffer 0; stage s reads buffer (s+1)&1 and writes
+// s&1, so stage 4 leaves f(y_{n+1}) in buffer 0 for the next step.
+template <int M, int STAGE>
+__host__ __device__ __forceinline__ RingStageIO stage_io(const RingPlan &p)
+{
+    constexpr int D = Model<M>::D, NX = Model<M>::NX;
+    constexpr int in = (STAGE + 1) & 1, out = STAGE == 0 ? 0 : (STAGE & 1);
+    RingStageIO a;
+    a.lam_in = STAGE ? p.lam[in] : nullptr;
+    a.ingrp_in = STAGE ? p.ingrp[in] : nullptr;
+    a.grpofs_in = STAGE ? p.grpofs[in] : nullptr;
+    a.lam_out = p.lam[out];
+    a.ingrp_out = p.ingrp[out];
+    a.grpofs_out = p.grpofs[out];
+    a.x_in = nullptr;
+    a.x_out = nullptr;
+    if (NX > 0) {
+        a.x_in = STAGE == 1 ? p.y + (int64_t)(D - NX) * p.N : STAGE == 3 ? p.xg[1] : STAGE ? p.xg[0] : nullptr;
+        a.x_out = STAGE == 1 || STAGE == 3 ? p.xg[0] : STAGE == 2 ? p.xg[1] : nullptr;
+    }
+    return a;
+}
 
 __device__ __forceinline__ i128 ldg_i128(const i128 *p)
 {
@@ -68,21 +90,19 @@ __device__ __forceinline__ i128 prefix_at(const int64_t *lam, const i128 *ingrp,
 template <int M> struct MinBlocks { static constexpr int value = 4; };
 template <> struct MinBlocks<2> { static constexpr int value = 2; };
 
-// One 256-node sub-tile per CTA, one node per thread.
+// One 256-node sub-tile `sub` of ring P, one node per thread (the whole CTA).
 template <int M, int STAGE>
-__global__ void __launch_bounds__(kRingThreads, MinBlocks<M>::value) ring_stage_kernel(const RingStageArgs a)
+__device__ __forceinline__ void ring_stage_body(const RingPlan &P, const RingStageIO &a, double dt, int64_t sub)
 {
     using Mo = Model<M>;
     constexpr int D = Mo::D, NQ = Mo::NQ, NX = Mo::NX;
     constexpr int XOFF = D - NX; // first local (non-coupled) state variable
     constexpr int NW = kRingThreads / 32;
-    const RingPlan &P = a.p;
     __shared__ int64_t s_wtot[NW][NQ];
     __shared__ int s_last;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t N = P.N, nsub = P.nsub, ngroups = P.ngroups;
-    const int64_t sub = blockIdx.x;
     const int64_t i = sub * kSubTile + tid;
 
     int64_t qv[NQ];
@@ -121,15 +141,15 @@ __global__ void __launch_bounds__(kRingThreads, MinBlocks<M>::value) ring_stage_
                 const double yv = P.y[v * N + i];
                 if (STAGE == 1) {
                     P.acc[v * N + i] = k[v];
-                    xn[v] = yv + (0.5 * a.dt) * k[v];
+                    xn[v] = yv + (0.5 * dt) * k[v];
                 } else if (STAGE == 2) {
                     P.acc[v * N + i] = P.acc[v * N + i] + 2.0 * k[v];
-                    xn[v] = yv + (0.5 * a.dt) * k[v];
+                    xn[v] = yv + (0.5 * dt) * k[v];
                 } else if (STAGE == 3) {
                     P.acc[v * N + i] = P.acc[v * N + i] + 2.0 * k[v];
-                    xn[v] = yv + a.dt * k[v];
+                    xn[v] = yv + dt * k[v];
                 } else {
-                    const double yn = yv + (a.dt / 6.0) * (P.acc[v * N + i] + k[v]);
+                    const double yn = yv + (dt / 6.0) * (P.acc[v * N + i] + k[v]);
                     P.y[v * N + i] = yn;
                     xn[v] = yn;
                 }
@@ -208,38 +228,41 @@ __global__ void __launch_bounds__(kRingThreads, MinBlocks<M>::value) ring_stage_
         P.obs[n % (unsigned long long)P.obs_cap] = sqrt(S * S + C * C) / (double)N;
         *P.obs_ctr = n + 1;
     }
+    if (STAGE == 4 && tid == 0 && P.steps_left) *P.steps_left -= 1;
+}
+
+// Plain path: one ring, one sub-tile per CTA.
+template <int M, int STAGE>
+__global__ void __launch_bounds__(kRingThreads, MinBlocks<M>::value) ring_stage_kernel(const RingPlan p, double dt)
+{
+    ring_stage_body<M, STAGE>(p, stage_io<M, STAGE>(p), dt, blockIdx.x);
+}
+
+// Batched path: CTA b works on sub-tile b - item_base[inst] of ring inst =
+// inst_of_item[b]; every ring keeps its own exact prefix hierarchy.  A ring whose
+// step budget (steps_left) is used up is skipped whole, so its arrival counters
+// stay consistent.
+template <int M, int STAGE>
+__global__ void __launch_bounds__(kRingThreads, MinBlocks<M>::value)
+    ring_batch_stage_kernel(const RingPlan *__restrict__ plans, const int *__restrict__ inst_of_item,
+                            const int64_t *__restrict__ item_base, double dt)
+{
+    const int inst = inst_of_item[blockIdx.x];
+    const RingPlan &p = plans[inst];
+    if (p.steps_left && *(volatile long long *)p.steps_left <= 0) return;
+    ring_stage_body<M, STAGE>(p, stage_io<M, STAGE>(p), dt, (int64_t)blockIdx.x - item_base[inst]);
 }
 
 template <int M>
 static cudaError_t launch_stage(int stage, const RingPlan &p, double dt, cudaStream_t s)
 {
-    constexpr int D = Model<M>::D, NX = Model<M>::NX;
-    RingStageArgs a;
-    a.p = p;
-    a.dt = dt;
-    const int in = (stage + 1) & 1, out = stage & 1; // stage 0 writes buffer 0
-    const int o = stage == 0 ? 0 : out;
-    a.lam_in = stage ? p.lam[in] : nullptr;
-    a.ingrp_in = stage ? p.ingrp[in] : nullptr;
-    a.grpofs_in = stage ? p.grpofs[in] : nullptr;
-    a.lam_out = p.lam[o];
-    a.ingrp_out = p.ingrp[o];
-    a.grpofs_out = p.grpofs[o];
-    a.x_in = nullptr;
-    a.x_out = nullptr;
-    if (NX > 0) {
-        const double *src[5] = {nullptr, p.y + (int64_t)(D - NX) * p.N, p.xg[0], p.xg[1], p.xg[0]};
-        double *dst[5] = {nullptr, p.xg[0], p.xg[1], p.xg[0], nullptr};
-        a.x_in = src[stage];
-        a.x_out = dst[stage];
-    }
     const dim3 grid((unsigned)p.nsub), block(kRingThreads);
     switch (stage) {
-    case 0: ring_stage_kernel<M, 0><<<grid, block, 0, s>>>(a); break;
-    case 1: ring_stage_kernel<M, 1><<<grid, block, 0, s>>>(a); break;
-    case 2: ring_stage_kernel<M, 2><<<grid, block, 0, s>>>(a); break;
-    case 3: ring_stage_kernel<M, 3><<<grid, block, 0, s>>>(a); break;
-    default: ring_stage_kernel<M, 4><<<grid, block, 0, s>>>(a); break;
+    case 0: ring_stage_kernel<M, 0><<<grid, block, 0, s>>>(p, dt); break;
+    case 1: ring_stage_kernel<M, 1><<<grid, block, 0, s>>>(p, dt); break;
+    case 2: ring_stage_kernel<M, 2><<<grid, block, 0, s>>>(p, dt); break;
+    case 3: ring_stage_kernel<M, 3><<<grid, block, 0, s>>>(p, dt); break;
+    default: ring_stage_kernel<M, 4><<<grid, block, 0, s>>>(p, dt); break;
     }
     return cudaGetLastError();
 }
@@ -251,6 +274,34 @@ static cudaError_t launch_any(int stage, const RingPlan &p, double dt, cudaStrea
     case 1: return launch_stage<1>(stage, p, dt, s);
     default: return launch_stage<2>(stage, p, dt, s);
     }
+}
+
+template <int M>
+static cudaError_t launch_batch_stage(int stage, const RingBatchGroup &g, double dt, cudaStream_t s)
+{
+    const dim3 grid((unsigned)g.n_items), block(kRingThreads);
+    switch (stage) {
+    case 1: ring_batch_stage_kernel<M, 1><<<grid, block, 0, s>>>(g.plans, g.inst_of_item, g.item_base, dt); break;
+    case 2: ring_batch_stage_kernel<M, 2><<<grid, block, 0, s>>>(g.plans, g.inst_of_item, g.item_base, dt); break;
+    case 3: ring_batch_stage_kernel<M, 3><<<grid, block, 0, s>>>(g.plans, g.inst_of_item, g.item_base, dt); break;
+    default: ring_batch_stage_kernel<M, 4><<<grid, block, 0, s>>>(g.plans, g.inst_of_item, g.item_base, dt); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t ring_batch_step(const RingBatchGroup &g, double dt, cudaStream_t s)
+{
+    if (g.n_items == 0) return cudaSuccess;
+    for (int stage = 1; stage <= 4; ++stage) {
+        cudaError_t e;
+        switch (g.model) {
+        case 0: e = launch_batch_stage<0>(stage, g, dt, s); break;
+        case 1: e = launch_batch_stage<1>(stage, g, dt, s); break;
+        default: e = launch_batch_stage<2>(stage, g, dt, s); break;
+        }
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t ring_prologue(const RingPlan &p, cudaStream_t s)

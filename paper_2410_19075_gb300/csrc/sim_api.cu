@@ -471,6 +471,259 @@ int64_t sim_steps_done(sim_t h) { return h ? h->steps_done : 0; }
 
 const char *sim_last_error(void) { return g_last_error.c_str(); }
 
+// ---------------------------------------------------------------------------
+// Batches: many networks advanced together, ring members of one model in one
+// launch per RK4 stage.
+
+} // extern "C"
+
+struct sim_batch_handle {
+    cudaStream_t stream = nullptr, cap_stream = nullptr;
+    std::vector<sim_t> members;
+    std::vector<int> ring_slot;      // member -> index of its plan in the group tables (or -1)
+    std::vector<RingBatchGroup> groups;
+    std::vector<sim_t> cubes;
+    void *block = nullptr;           // device tables
+    long long *budgets = nullptr;    // device: steps left per ring member (budgeted mode)
+    std::vector<long long> host_budget; // host shadow, -1 = unlimited
+    unsigned **err_ptrs = nullptr;   // device: every member's error word
+    unsigned *err_out = nullptr;     // device: OR of the members' error words
+    unsigned *h_err = nullptr;       // pinned
+    bool budgeted = false;
+    std::map<std::pair<double, int>, cudaGraphExec_t> graphs;
+};
+
+namespace {
+
+__global__ void batch_error_kernel(unsigned *const *errs, int n, unsigned *out)
+{
+    __shared__ unsigned acc;
+    if (threadIdx.x == 0) acc = 0;
+    __syncthreads();
+    unsigned v = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) v |= *errs[i];
+    atomicOr(&acc, v);
+    __syncthreads();
+    if (threadIdx.x == 0) *out = acc;
+}
+
+cudaError_t batch_launch_steps(sim_batch_t b, int64_t n, double dt, cudaStream_t s)
+{
+    for (int64_t t = 0; t < n; ++t) {
+        for (const RingBatchGroup &g : b->groups) {
+            const cudaError_t e = ring_batch_step(g, dt, s);
+            if (e != cudaSuccess) return e;
+        }
+        for (sim_t c : b->cubes) {
+            const cudaError_t e = cube_step(c->cube, dt, s);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    return cudaSuccess;
+}
+
+int batch_graph(sim_batch_t b, double dt, int chunk, cudaGraphExec_t *out)
+{
+    auto it = b->graphs.find({dt, chunk});
+    if (it != b->graphs.end()) {
+        *out = it->second;
+        return SIM_OK;
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+    const cudaError_t le = batch_launch_steps(b, chunk, dt, b->cap_stream);
+    e = cudaStreamEndCapture(b->cap_stream, &g);
+    if (le != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(le, "kernel launch during capture");
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    b->graphs[{dt, chunk}] = ex;
+    *out = ex;
+    return SIM_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+int sim_batch_create(sim_batch_t *out, const sim_t *members, int n_members, void *stream)
+{
+    if (!out) return fail(SIM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n_members < 1 || !members) return fail(SIM_EINVAL, "a batch needs at least one member");
+    for (int i = 0; i < n_members; ++i) {
+        if (!members[i]) return fail(SIM_EINVAL, "NULL member");
+        for (int j = 0; j < i; ++j)
+            if (members[j] == members[i]) return fail(SIM_EINVAL, "a network appears twice in the batch");
+    }
+    sim_batch_t b = new sim_batch_handle();
+    b->stream = static_cast<cudaStream_t>(stream);
+    b->members.assign(members, members + n_members);
+    b->ring_slot.assign(n_members, -1);
+    b->host_budget.assign(n_members, -1);
+
+    // Group ring members by model; host copies of the device tables.
+    std::vector<std::vector<int>> by_model(3);
+    for (int i = 0; i < n_members; ++i) {
+        if (members[i]->topo == SIM_RING) by_model[members[i]->model].push_back(i);
+        else b->cubes.push_back(members[i]);
+    }
+    std::vector<RingPlan> plans;
+    std::vector<int> inst_of_item;
+    std::vector<int64_t> item_base;
+    struct GroupSpan { int model, plan0, n; int64_t item0, n_items; };
+    std::vector<GroupSpan> spans;
+    for (int m = 0; m < 3; ++m) {
+        if (by_model[m].empty()) continue;
+        GroupSpan gs{m, (int)plans.size(), (int)by_model[m].size(), (int64_t)inst_of_item.size(), 0};
+        for (int k = 0; k < (int)by_model[m].size(); ++k) {
+            const sim_t h = members[by_model[m][k]];
+            b->ring_slot[by_model[m][k]] = (int)plans.size();
+            item_base.push_back(gs.n_items);
+            for (int64_t t = 0; t < h->ring.nsub; ++t) inst_of_item.push_back(k);
+            gs.n_items += h->ring.nsub;
+            plans.push_back(h->ring);
+        }
+        spans.push_back(gs);
+    }
+    if (inst_of_item.size() > (size_t)0x7fffffff) {
+        delete b;
+        return fail(SIM_EINVAL, "batch too large");
+    }
+    const size_t nplan = plans.size(), nitem = inst_of_item.size();
+    size_t o = 0;
+    auto take = [&](size_t bytes) { const size_t at = o; o = align_up(o + bytes); return at; };
+    const size_t o_plans = take(sizeof(RingPlan) * nplan), o_items = take(sizeof(int) * nitem);
+    const size_t o_base = take(sizeof(int64_t) * nplan), o_budget = take(sizeof(long long) * nplan);
+    const size_t o_errs = take(sizeof(unsigned *) * n_members), o_eout = take(64);
+    cudaError_t e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&b->block, o);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_err, 64);
+    if (e != cudaSuccess) {
+        sim_batch_destroy(b);
+        return e == cudaErrorMemoryAllocation ? fail(SIM_ENOMEM, "batch tables") : cuda_fail(e, "sim_batch_create");
+    }
+    char *blk = static_cast<char *>(b->block);
+    b->budgets = reinterpret_cast<long long *>(blk + o_budget);
+    b->err_ptrs = reinterpret_cast<unsigned **>(blk + o_errs);
+    b->err_out = reinterpret_cast<unsigned *>(blk + o_eout);
+    // plans carry a step-budget pointer; unlimited budgets start at INT64_MAX
+    for (size_t k = 0; k < nplan; ++k) plans[k].steps_left = b->budgets + k;
+    std::vector<long long> budgets(nplan, (long long)0x7fffffffffffffffLL);
+    std::vector<unsigned *> errs(n_members);
+    for (int i = 0; i < n_members; ++i) errs[i] = members[i]->err;
+    if (nplan) e = cudaMemcpyAsync(blk + o_plans, plans.data(), sizeof(RingPlan) * nplan, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess && nitem)
+        e = cudaMemcpyAsync(blk + o_items, inst_of_item.data(), sizeof(int) * nitem, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess && nplan)
+        e = cudaMemcpyAsync(blk + o_base, item_base.data(), sizeof(int64_t) * nplan, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess && nplan)
+        e = cudaMemcpyAsync(b->budgets, budgets.data(), sizeof(long long) * nplan, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->err_ptrs, errs.data(), sizeof(unsigned *) * n_members, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) {
+        sim_batch_destroy(b);
+        return cuda_fail(e, "batch table upload");
+    }
+    for (const GroupSpan &gs : spans) {
+        RingBatchGroup g;
+        g.model = gs.model;
+        g.n_inst = gs.n;
+        g.n_items = gs.n_items;
+        g.plans = reinterpret_cast<const RingPlan *>(blk + o_plans) + gs.plan0;
+        g.inst_of_item = reinterpret_cast<const int *>(blk + o_items) + gs.item0;
+        g.item_base = reinterpret_cast<const int64_t *>(blk + o_base) + gs.plan0;
+        b->groups.push_back(g);
+    }
+    *out = b;
+    return SIM_OK;
+}
+
+int sim_batch_set_budgets(sim_batch_t b, const int64_t *steps)
+{
+    if (!b || !steps) return fail(SIM_EINVAL, "NULL argument");
+    const int n = (int)b->members.size();
+    for (int i = 0; i < n; ++i) {
+        if (steps[i] < -1) return fail(SIM_EINVAL, "budgets must be >= 0, or -1 for unlimited");
+        if (b->members[i]->topo != SIM_RING && steps[i] != -1)
+            return fail(SIM_EINVAL, "step budgets apply to ring members only");
+    }
+    std::vector<long long> dev;
+    for (int i = 0; i < n; ++i) {
+        b->host_budget[i] = steps[i];
+        if (b->ring_slot[i] >= 0) {
+            if ((int)dev.size() <= b->ring_slot[i]) dev.resize(b->ring_slot[i] + 1);
+            dev[b->ring_slot[i]] = steps[i] < 0 ? (long long)0x7fffffffffffffffLL : steps[i];
+        }
+    }
+    if (!dev.empty()) {
+        const cudaError_t e = cudaMemcpyAsync(b->budgets, dev.data(), sizeof(long long) * dev.size(),
+                                              cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) cudaStreamSynchronize(b->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "budget upload");
+    }
+    return SIM_OK;
+}
+
+int sim_batch_step(sim_batch_t b, int64_t n_steps, double dt)
+{
+    if (!b) return fail(SIM_EINVAL, "NULL batch");
+    if (n_steps < 0) return fail(SIM_EINVAL, "n_steps must be >= 0");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(SIM_EINVAL, "dt must be finite and > 0");
+    int64_t left = n_steps;
+    while (left > 0) {
+        const int chunk = left >= kGraphChunk ? kGraphChunk : 1;
+        cudaGraphExec_t ex;
+        const int st = batch_graph(b, dt, chunk, &ex);
+        if (st != SIM_OK) return st;
+        const cudaError_t e = cudaGraphLaunch(ex, b->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+        left -= chunk;
+    }
+    for (size_t i = 0; i < b->members.size(); ++i) {
+        long long &bud = b->host_budget[i];
+        int64_t done = n_steps;
+        if (bud >= 0) {
+            done = n_steps < bud ? n_steps : bud;
+            bud -= done;
+        }
+        b->members[i]->steps_done += done;
+    }
+    return SIM_OK;
+}
+
+int sim_batch_sync(sim_batch_t b)
+{
+    if (!b) return fail(SIM_EINVAL, "NULL batch");
+    batch_error_kernel<<<1, 256, 0, b->stream>>>(b->err_ptrs, (int)b->members.size(), b->err_out);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->h_err, b->err_out, sizeof(unsigned), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "batch work failed");
+    const unsigned w = *b->h_err;
+    if (w & ERR_TIMEOUT) return fail(SIM_ETIMEOUT, "a device-side wait exceeded its bound; results are invalid");
+    if (w & ERR_RANGE) return fail(SIM_ENONFINITE, "a member's state became non-finite or left the fixed-point range");
+    return SIM_OK;
+}
+
+void sim_batch_destroy(sim_batch_t b)
+{
+    if (!b) return;
+    if (b->block) cudaStreamSynchronize(b->stream);
+    for (auto &kv : b->graphs) cudaGraphExecDestroy(kv.second);
+    if (b->block) cudaFree(b->block);
+    if (b->h_err) cudaFreeHost(b->h_err);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    delete b;
+}
+
 void sim_destroy(sim_t h)
 {
     if (!h) return;

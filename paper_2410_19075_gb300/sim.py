@@ -124,3 +124,42 @@ class Network:
             self.close()
         except Exception:
             pass
+
+
+class Batch:
+    """Several networks advanced together (``sim_batch_*``).  The batch does not
+    own its members; keep them open while the batch exists."""
+
+    def __init__(self, members, stream=None):
+        self.members = list(members)
+        arr = (ctypes.c_void_p * len(self.members))(*[m._handle().value for m in self.members])
+        h = ctypes.c_void_p()
+        check(lib().sim_batch_create(ctypes.byref(h), arr, len(self.members), _stream_ptr(stream)))
+        self._h = h
+
+    def set_budgets(self, steps):
+        a = (ctypes.c_int64 * len(self.members))(*[int(s) for s in steps])
+        check(lib().sim_batch_set_budgets(self._h, a))
+
+    def step(self, n_steps: int, dt: float):
+        check(lib().sim_batch_step(self._h, int(n_steps), float(dt)))
+
+    def sync(self):
+        check(lib().sim_batch_sync(self._h))
+
+    def close(self):
+        if self._h is not None:
+            lib().sim_batch_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,116 @@
+"""Batched stepping: many networks of uneven size in one launch per RK4 stage.
+
+Exact integer window sums make every member's result independent of how the
+work is tiled, so a member stepped in a batch must equal, bit for bit, the same
+network stepped alone with sim_step.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2410_19075_gb300 import inputs as I
+from _common import ORDER_TOL, STATE_TOL
+
+pytestmark = pytest.mark.gpu
+
+
+def _members(specs):
+    from paper_2410_19075_gb300 import Network
+    nets, inits = [], []
+    for k, (model, topo, N, R, params) in enumerate(specs):
+        n = N ** 3 if topo == 1 else N
+        y0 = I.initial_state(model, 900 + k, 0, n)
+        net = Network(model, topo, N, R, params)
+        if model == 2:
+            net.set_node_param(I.hh_iext(900 + k, 0, n))
+        net.set_state(y0)
+        nets.append(net)
+        inits.append(y0)
+    return nets, inits
+
+
+def _alone(model, topo, N, R, params, y0, steps, npar=None):
+    from paper_2410_19075_gb300 import Network
+    with Network(model, topo, N, R, params) as net:
+        if npar is not None:
+            net.set_node_param(npar)
+        net.set_state(y0)
+        net.step(steps, 0.01)
+        return net.get_state(), net.observables()
+
+
+def _sweep_specs(n, seed):
+    out = []
+    for s in I.batched_sweep(n_inst=n, seed=seed, n_hi=20000):
+        out.append((0, 0, s.N, s.R, I.ks_params(alpha=s.alpha)))
+    return out
+
+
+def test_batched_kuramoto_sweep_equals_plain_bitwise():
+    from paper_2410_19075_gb300 import Batch
+    specs = _sweep_specs(24, 77)
+    nets, inits = _members(specs)
+    with Batch(nets) as b:
+        b.step(40, 0.01)
+        b.sync()
+    for (model, topo, N, R, params), net, y0 in zip(specs, nets, inits):
+        y, order = net.get_state(), net.observables()
+        ya, oa = _alone(model, topo, N, R, params, y0, 40)
+        assert np.array_equal(y, ya), (N, R)
+        assert np.array_equal(order, oa)
+        assert net.steps_done == 40
+        net.close()
+
+
+def test_batched_mixed_models_and_cube_equal_plain():
+    from paper_2410_19075_gb300 import Batch
+    specs = [(0, 0, 1000, 350, I.ks_params()), (1, 0, 3001, 1050, I.fhn_params()),
+             (2, 0, 1500, 450, I.hh_params()), (0, 1, 12, 2, I.ks_params(alpha=1.52)),
+             (1, 0, 300, 7, I.fhn_params()), (0, 0, 257, 128, I.ks_params(alpha=1.3))]
+    nets, inits = _members(specs)
+    with Batch(nets) as b:
+        b.step(33, 0.01)
+        b.sync()
+    for k, ((model, topo, N, R, params), net, y0) in enumerate(zip(specs, nets, inits)):
+        npar = I.hh_iext(900 + k, 0, N) if model == 2 else None
+        ya, _ = _alone(model, topo, N, R, params, y0, 33, npar)
+        assert np.array_equal(net.get_state(), ya), (model, topo, N)
+        net.close()
+
+
+def test_batched_member_matches_oracle():
+    """One batched member against the CPU oracle (the bitwise tests above tie
+    every other member to the plain path, which the ring tests tie to the oracle)."""
+    from paper_2410_19075_gb300 import Batch
+    specs = _sweep_specs(6, 78)
+    nets, inits = _members(specs)
+    with Batch(nets) as b:
+        b.step(200, 0.01)
+        b.sync()
+    model, topo, N, R, params = specs[0]
+    ref, ref_order = oracle.rk4(0, 0, N, R, params, inits[0], 200, 0.01, record_order=True)
+    assert np.abs(nets[0].get_state() - ref).max() <= STATE_TOL
+    assert np.abs(nets[0].observables() - ref_order).max() <= ORDER_TOL
+    for n in nets:
+        n.close()
+
+
+def test_step_budgets_stop_members_exactly():
+    from paper_2410_19075_gb300 import Batch
+    specs = _sweep_specs(5, 79)
+    budgets = [0, 7, 16, 23, -1]
+    nets, inits = _members(specs)
+    with Batch(nets) as b:
+        b.set_budgets(budgets)
+        b.step(20, 0.01)
+        b.step(5, 0.01)
+        b.sync()
+    for (model, topo, N, R, params), net, y0, bud in zip(specs, nets, inits, budgets):
+        steps = 25 if bud < 0 else bud
+        ya, oa = _alone(model, topo, N, R, params, y0, steps)
+        assert np.array_equal(net.get_state(), ya), (bud, N)
+        assert np.array_equal(net.observables(), oa)
+        assert net.steps_done == steps
+        net.close()
