@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--dt", type=float, default=0.01)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-sweep comparison")
+    ap.add_argument("--no-served", action="store_true", help="skip the served-mix comparison")
+    ap.add_argument("--batched-only", action="store_true")
     return ap.parse_args()
 
 
@@ -209,6 +212,108 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------- batched sweep
+def bench_batched(args, flush, stream, n_inst=4096, steps=2000, plain_steps=20):
+    """Multistability sweep: n_inst Kuramoto rings, N log-uniform in [100, 50000],
+    R = floor(r N), r ~ U[0.05, 0.45], alpha ~ U[1.3, 1.57], seeded phases; all
+    advanced together (one launch per RK4 stage) versus the plain path run
+    network by network (timed on every network for plain_steps steps)."""
+    import torch
+    from paper_2410_19075_gb300 import Batch, Network
+    sweep = I.batched_sweep(n_inst=n_inst, seed=2414)
+    nets = []
+    for s in sweep:
+        net = Network(0, 0, s.N, s.R, I.ks_params(alpha=s.alpha), stream=stream)
+        net.set_state(I.ks_phases(s.seed, s.instance, s.N))
+        nets.append(net)
+    total_nodes = sum(s.N for s in sweep)
+    batch = Batch(nets, stream=stream)
+    batch.step(args.warmup, args.dt)
+    batch.step(100, args.dt)
+    batch.step(1, args.dt)
+    batch.sync()
+    chunks = [min(100, steps - k) for k in range(0, steps, 100)]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in chunks]
+    torch.cuda.synchronize()
+    for (a, b), c in zip(ev, chunks):
+        flush.zero_()
+        a.record(stream)
+        batch.step(c, args.dt)
+        b.record(stream)
+    torch.cuda.synchronize()
+    batch.sync()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    value = total_nodes * steps / (ms * 1e-3)
+    # plain path: every network alone (its own graphs), plain_steps steps each
+    for net in nets:
+        net.step(plain_steps, args.dt)  # graphs captured, warm
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush.zero_()
+    a.record(stream)
+    for net in nets:
+        net.step(plain_steps, args.dt)
+    b.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = a.elapsed_time(b)
+    plain_value = total_nodes * plain_steps / (plain_ms * 1e-3)
+    batch.close()
+    for net in nets:
+        net.close()
+    return {"workload": f"{n_inst} Kuramoto rings, N log-uniform in [100, 50000] (total {total_nodes} nodes), "
+                        f"r ~ U[0.05, 0.45], alpha ~ U[1.3, 1.57], RK4 dt={args.dt}",
+            "steps": steps, "value": value, "unit": "node-steps/s", "ms": ms,
+            "plain_value": plain_value, "plain_steps_timed": plain_steps,
+            "speedup_vs_plain": value / plain_value,
+            "gpu_launches": 4 * steps * 1}
+
+
+# ----------------------------------------------------------------------------- served mix
+def serve_trace(jobs, inits, slots, budget, chunk, stream):
+    from paper_2410_19075_gb300 import Server
+    with Server(budget, max_slots=slots, chunk_steps=chunk, stream=stream) as srv:
+        t0 = time.perf_counter()
+        ids = []
+        for job, y0 in zip(jobs, inits):
+            delay = t0 + job.arrival - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            ids.append(srv.submit(job.model, job.topo, job.N, job.R, job.params, y0, job.n_steps, 0.01,
+                                  node_param=job.node_param))
+        srv.wait_idle()
+        times = []
+        for jid in ids:
+            r = srv.poll(jid)
+            times.append(r[2])
+        stats = srv.stats()
+    t = np.array(times)
+    lat = t[:, 2] - t[:, 0]
+    span = t[:, 2].max() - t[:, 0].min()
+    return {"p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+            "mean_queue_wait_s": float(np.mean(t[:, 1] - t[:, 0])),
+            "value": stats["node_steps"] / span, "unit": "node-steps/s", "span_s": span,
+            "batches_formed": stats["batches_formed"]}
+
+
+def bench_served(args, stream, n_jobs=400, rate=200.0, size_scale=0.05, steps_scale=0.1):
+    """Poisson arrivals (rate jobs/s) of the mixed trace: 40% Kuramoto rings, 30%
+    FHN rings, 20% HH rings, 10% 3D Kuramoto lattices, horizons log-uniform in
+    [1e3, 1e4] steps; sizes and horizons scaled by size_scale and steps_scale so
+    that the trace runs in seconds.  Continuous batching versus one job at a time
+    on the plain path."""
+    jobs = I.served_trace(n_jobs=n_jobs, rate=rate, seed=2415, size_scale=size_scale, steps_scale=steps_scale)
+    inits = [I.initial_state(j.model, j.seed, j.job_id + 1, j.N ** 3 if j.topo == 1 else j.N) for j in jobs]
+    node_steps = sum((j.N ** 3 if j.topo == 1 else j.N) * j.n_steps for j in jobs)
+    budget = 64 << 30
+    batched = serve_trace(jobs, inits, 4096, budget, 32, stream)
+    plain = serve_trace(jobs, inits, 1, budget, 32, stream)
+    return {"workload": f"{n_jobs} jobs, Poisson {rate:g} jobs/s, 40/30/20/10 KS ring/FHN ring/HH ring/KS cube, "
+                        f"sizes x{size_scale:g}, horizons x{steps_scale:g}, dt=0.01, HBM budget {budget >> 30} GiB",
+            "total_node_steps": node_steps, "batched": batched, "plain_one_at_a_time": plain,
+            "speedup_vs_plain": batched["value"] / plain["value"],
+            "p99_latency_ratio_plain_over_batched": plain["p99_latency_s"] / batched["p99_latency_s"]}
+
+
 # ----------------------------------------------------------------------------- native
 def run_native(args):
     import torch
@@ -316,6 +421,10 @@ def run_native(args):
             "gpu_launches": launches, "roofline": roofline, "clocks": clk}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, N, R, params, args.cpu_seconds)
+    if not args.no_batched:
+        line["batched"] = bench_batched(args, flush, stream)
+    if not args.no_served:
+        line["served"] = bench_served(args, stream)
     net.close()
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -84,6 +84,15 @@ size_t sim_workspace_bytes(int model, int topology, int64_t N, int64_t radius);
 int sim_create(sim_t *out, int model, int topology, int64_t N, int64_t radius,
                const double *params, int n_params, unsigned flags, void *stream);
 
+/* Same as sim_create, but the network lives in caller-provided device memory
+ * (dev_workspace: at least sim_workspace_bytes() bytes, 256-byte aligned, for
+ * example a slice of a PyTorch tensor or of a caller's arena).  The handle does
+ * not free it; sim_destroy() synchronises the stream so the memory can be
+ * reused afterwards.  Errors: as sim_create, plus SIM_EINVAL for a NULL,
+ * misaligned or too small workspace. */
+int sim_create_in(sim_t *out, int model, int topology, int64_t N, int64_t radius, const double *params,
+                  int n_params, unsigned flags, void *dev_workspace, size_t workspace_bytes, void *stream);
+
 /* Number of nodes (N or N1^3) and of state variables per node. */
 int64_t sim_nodes(sim_t h);
 int sim_dim(sim_t h);
@@ -166,6 +175,51 @@ int sim_batch_sync(sim_batch_t b);
 
 /* Free the batch's own tables (synchronises first); members are untouched. */
 void sim_batch_destroy(sim_batch_t b);
+
+/* ---------------------------------------------------------------------------
+ * Serving: a request loop with continuous batching.  Jobs (one network each)
+ * are submitted at any time; a worker thread admits them in arrival order while
+ * the resident jobs' device memory (sim_workspace_bytes each) stays within
+ * hbm_budget_bytes and fewer than max_slots are resident, keeps their state on
+ * the device, advances all resident jobs together (sim_batch_* in chunks of
+ * chunk_steps RK4 steps, each job stopped exactly at its horizon by a step
+ * budget) and retires finished jobs (final state and Kuramoto order
+ * parameters copied to host memory, device memory released).  A job's result is
+ * bit-for-bit the same alone and in any mix.  max_slots = 1 runs one job at a
+ * time on the plain path (sim_step): the baseline.
+ */
+typedef struct srv_handle *srv_t;
+
+/* Start a server (and its worker thread) on the current device.  stream: where
+ * its work is issued (NULL = legacy default). */
+int srv_create(srv_t *out, size_t hbm_budget_bytes, int max_slots, int64_t chunk_steps, void *stream);
+
+/* Queue one job (arguments as sim_create / sim_set_state / sim_set_node_param;
+ * host buffers are copied before the call returns).  n_steps RK4 steps of dt.
+ * Writes the job id.  SIM_ENOMEM if the job alone exceeds the HBM budget. */
+int srv_submit(srv_t s, int model, int topology, int64_t N, int64_t radius, const double *params, int n_params,
+               const double *host_init_state, const double *host_node_param, int64_t n_steps, double dt,
+               int64_t *job_id);
+
+/* *done = 1 once the job has finished.  Then copies its final state
+ * (n_values = d * nodes doubles, or host_state_out = NULL), up to max_order
+ * order-parameter values (t = 0 and every step; Kuramoto only) with their count
+ * in *n_order, and times_out[0..2] = submit, admission and completion times
+ * (seconds, steady clock; may be NULL), releases the job and returns its
+ * status.  While not done it returns SIM_OK with *done = 0.  SIM_EINVAL for an
+ * unknown (or already collected) id. */
+int srv_poll(srv_t s, int64_t job_id, int *done, double *host_state_out, int64_t n_values, double *host_order_out,
+             int64_t max_order, int64_t *n_order, double *times_out);
+
+/* Block until every submitted job has finished. */
+int srv_wait_idle(srv_t s);
+
+/* out6 = {completed jobs, jobs not yet finished, queued (not admitted) jobs,
+ * node-steps done, batches formed, device bytes in use}. */
+int srv_stats(srv_t s, int64_t *out6);
+
+/* Stop the worker (unfinished jobs are dropped) and free everything. */
+void srv_destroy(srv_t s);
 
 /* RK4 steps of a ring network with no device allocation at all.
  *

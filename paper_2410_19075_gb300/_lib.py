@@ -29,6 +29,7 @@ _dp = ctypes.POINTER(ctypes.c_double)
 SIGNATURES = {
     "sim_workspace_bytes": (_sz, [_int, _int, _i64, _i64]),
     "sim_create": (_int, [ctypes.POINTER(_vp), _int, _int, _i64, _i64, _dp, _int, _uint, _vp]),
+    "sim_create_in": (_int, [ctypes.POINTER(_vp), _int, _int, _i64, _i64, _dp, _int, _uint, _vp, _sz, _vp]),
     "sim_nodes": (_i64, [_vp]),
     "sim_dim": (_int, [_vp]),
     "sim_set_state": (_int, [_vp, _vp, _i64]),
@@ -45,6 +46,12 @@ SIGNATURES = {
     "sim_batch_step": (_int, [_vp, _i64, _dbl]),
     "sim_batch_sync": (_int, [_vp]),
     "sim_batch_destroy": (None, [_vp]),
+    "srv_create": (_int, [ctypes.POINTER(_vp), _sz, _int, _i64, _vp]),
+    "srv_submit": (_int, [_vp, _int, _int, _i64, _i64, _dp, _int, _vp, _vp, _i64, _dbl, ctypes.POINTER(_i64)]),
+    "srv_poll": (_int, [_vp, _i64, ctypes.POINTER(_int), _vp, _i64, _vp, _i64, ctypes.POINTER(_i64), _vp]),
+    "srv_wait_idle": (_int, [_vp]),
+    "srv_stats": (_int, [_vp, ctypes.POINTER(_i64)]),
+    "srv_destroy": (None, [_vp]),
     "sim_math_eval": (_int, [_int, _vp, _vp, _i64]),
     "sim_ring_step_noalloc": (_int, [_int, _i64, _i64, _dp, _int, _uint, _vp, _vp, _i64, _dbl, _vp]),
     "sim_steps_done": (_i64, [_vp]),

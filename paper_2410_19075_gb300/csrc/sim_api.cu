@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -130,8 +131,9 @@ struct sim_handle {
     unsigned *err = nullptr;
     unsigned long long *obs_ctr = nullptr;
     double *obs = nullptr;
-    unsigned *h_err = nullptr;            // pinned
-    unsigned long long *h_ctr = nullptr;  // pinned
+    bool owns_block = true;               // false: caller's workspace (sim_create_in)
+    unsigned h_err = 0;                   // host copies of device words
+    unsigned long long h_ctr = 0;
     int64_t steps_done = 0;
     int64_t obs_read = 0;
     std::map<std::pair<double, int>, cudaGraphExec_t> graphs;
@@ -141,10 +143,10 @@ namespace {
 
 int check_device_error(sim_t h)
 {
-    cudaError_t e = cudaMemcpyAsync(h->h_err, h->err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream);
+    cudaError_t e = cudaMemcpyAsync(&h->h_err, h->err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "device work failed");
-    const unsigned w = *h->h_err;
+    const unsigned w = h->h_err;
     if (w & ERR_TIMEOUT) return fail(SIM_ETIMEOUT, "a device-side wait exceeded its bound; results are invalid");
     if (w & ERR_RANGE) return fail(SIM_ENONFINITE, "the state became non-finite or left the fixed-point range");
     return SIM_OK;
@@ -167,7 +169,10 @@ int get_graph(sim_t h, double dt, int chunk, cudaGraphExec_t *out)
         return SIM_OK;
     }
     cudaGraph_t g = nullptr;
-    cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+    cudaError_t e = cudaSuccess;
+    if (!h->cap_stream && (e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+        return cuda_fail(e, "capture stream");
+    e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
     const cudaError_t le = launch_steps(h, chunk, dt, h->cap_stream);
     e = cudaStreamEndCapture(h->cap_stream, &g);
@@ -207,8 +212,16 @@ size_t sim_workspace_bytes(int model, int topology, int64_t N, int64_t radius)
     return layout_of(model, topology, N, radius).total;
 }
 
-int sim_create(sim_t *out, int model, int topology, int64_t N, int64_t radius, const double *params,
-               int n_params, unsigned flags, void *stream)
+static const double *host_tables()
+{
+    static double tab[2 * kSinTab + kExpTab];
+    static std::once_flag once;
+    std::call_once(once, [] { fill_math_tables(tab, tab + 2 * kSinTab); });
+    return tab;
+}
+
+static int create_impl(sim_t *out, int model, int topology, int64_t N, int64_t radius, const double *params,
+                       int n_params, unsigned flags, void *workspace, size_t workspace_bytes, void *stream)
 {
     if (!out) return fail(SIM_EINVAL, "out is NULL");
     *out = nullptr;
@@ -227,21 +240,28 @@ int sim_create(sim_t *out, int model, int topology, int64_t N, int64_t radius, c
     h->L = layout_of(model, topology, N, radius);
     h->bytes = h->L.total;
 
-    cudaError_t e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaMalloc(&h->block, h->bytes);
-    if (e == cudaErrorMemoryAllocation) {
-        cudaGetLastError();
-        sim_destroy(h);
-        return fail(SIM_ENOMEM, "device allocation of " + std::to_string(h->bytes) + " bytes failed");
+    cudaError_t e = cudaSuccess;
+    if (workspace) {
+        if (workspace_bytes < h->bytes || (reinterpret_cast<uintptr_t>(workspace) & 255u)) {
+            delete h;
+            return fail(SIM_EINVAL, "workspace smaller than sim_workspace_bytes() or not 256-byte aligned");
+        }
+        h->block = workspace;
+        h->owns_block = false;
+    } else {
+        e = cudaMalloc(&h->block, h->bytes);
+        if (e == cudaErrorMemoryAllocation) {
+            cudaGetLastError();
+            h->block = nullptr;
+            sim_destroy(h);
+            return fail(SIM_ENOMEM, "device allocation of " + std::to_string(h->bytes) + " bytes failed");
+        }
     }
-    if (e == cudaSuccess) e = cudaMallocHost(&h->h_err, 64);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->block, 0, h->bytes, h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) {
         sim_destroy(h);
         return cuda_fail(e, "sim_create");
     }
-    h->h_ctr = reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(h->h_err) + 8);
     char *b = static_cast<char *>(h->block);
     const Layout &L = h->L;
     unsigned long long *ctrs = reinterpret_cast<unsigned long long *>(b + L.ctrs);
@@ -250,16 +270,13 @@ int sim_create(sim_t *out, int model, int topology, int64_t N, int64_t radius, c
     unsigned long long *ticket = ctrs + 2;
     h->obs = reinterpret_cast<double *>(b + L.obs);
 
-    // Tables of the fast elementary functions.
-    {
-        std::vector<double> tab(2 * kSinTab + kExpTab);
-        fill_math_tables(tab.data(), tab.data() + 2 * kSinTab);
-        e = cudaMemcpyAsync(b + L.tabs, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, h->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-        if (e != cudaSuccess) {
-            sim_destroy(h);
-            return cuda_fail(e, "table upload");
-        }
+    // Tables of the fast elementary functions (from a static host copy, so the
+    // copy needs no synchronisation).
+    e = cudaMemcpyAsync(b + L.tabs, host_tables(), sizeof(double) * (2 * kSinTab + kExpTab), cudaMemcpyHostToDevice,
+                        h->stream);
+    if (e != cudaSuccess) {
+        sim_destroy(h);
+        return cuda_fail(e, "table upload");
     }
     // Derived model constants (FP64 on the host).
     ModelParams mp{};
@@ -346,6 +363,20 @@ int sim_create(sim_t *out, int model, int topology, int64_t N, int64_t radius, c
     }
     *out = h;
     return SIM_OK;
+}
+
+int sim_create(sim_t *out, int model, int topology, int64_t N, int64_t radius, const double *params,
+               int n_params, unsigned flags, void *stream)
+{
+    return create_impl(out, model, topology, N, radius, params, n_params, flags, nullptr, 0, stream);
+}
+
+int sim_create_in(sim_t *out, int model, int topology, int64_t N, int64_t radius, const double *params,
+                  int n_params, unsigned flags, void *dev_workspace, size_t workspace_bytes, void *stream)
+{
+    if (!dev_workspace) return fail(SIM_EINVAL, "workspace is NULL");
+    return create_impl(out, model, topology, N, radius, params, n_params, flags, dev_workspace, workspace_bytes,
+                       stream);
 }
 
 int64_t sim_nodes(sim_t h) { return h ? h->nodes : 0; }
@@ -440,10 +471,10 @@ int sim_observables(sim_t h, double *host_R, int64_t max_values, int64_t *n_writ
     if (!h || !n_written || (max_values > 0 && !host_R)) return fail(SIM_EINVAL, "NULL argument");
     *n_written = 0;
     if (h->model != SIM_KS) return check_device_error(h);
-    cudaError_t e = cudaMemcpyAsync(h->h_ctr, h->obs_ctr, sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream);
+    cudaError_t e = cudaMemcpyAsync(&h->h_ctr, h->obs_ctr, sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "observable counter copy");
-    const int64_t have = (int64_t)*h->h_ctr;
+    const int64_t have = (int64_t)h->h_ctr;
     if (have - h->obs_read > kObsCap) h->obs_read = have - kObsCap;
     int64_t n = have - h->obs_read;
     if (n > max_values) n = max_values;
@@ -488,9 +519,15 @@ struct sim_batch_handle {
     std::vector<long long> host_budget; // host shadow, -1 = unlimited
     unsigned **err_ptrs = nullptr;   // device: every member's error word
     unsigned *err_out = nullptr;     // device: OR of the members' error words
-    unsigned *h_err = nullptr;       // pinned
+    unsigned h_err = 0;              // host copy of err_out
     bool budgeted = false;
     std::map<std::pair<double, int>, cudaGraphExec_t> graphs;
+    std::map<std::pair<double, int>, int> uses; // launches per (dt, chunk) before capturing a graph
+    // independent branches (one per model group, cubes spread over a few) run
+    // concurrently on side streams, forked from and joined to the main stream
+    std::vector<cudaStream_t> side;
+    cudaEvent_t ev_fork = nullptr;
+    std::vector<cudaEvent_t> ev_join;
 };
 
 namespace {
@@ -507,19 +544,55 @@ __global__ void batch_error_kernel(unsigned *const *errs, int n, unsigned *out)
     if (threadIdx.x == 0) *out = acc;
 }
 
-cudaError_t batch_launch_steps(sim_batch_t b, int64_t n, double dt, cudaStream_t s)
+constexpr int kCubeBranches = 4;
+
+int n_branches(sim_batch_t b)
 {
+    const int nc = (int)b->cubes.size();
+    return (int)b->groups.size() + (nc < kCubeBranches ? nc : kCubeBranches);
+}
+
+// n steps of branch k (a ring group, or every kCubeBranches-th cube) on stream s.
+cudaError_t branch_steps(sim_batch_t b, int k, int64_t n, double dt, cudaStream_t s)
+{
+    const int ng = (int)b->groups.size();
     for (int64_t t = 0; t < n; ++t) {
-        for (const RingBatchGroup &g : b->groups) {
-            const cudaError_t e = ring_batch_step(g, dt, s);
+        if (k < ng) {
+            const cudaError_t e = ring_batch_step(b->groups[k], dt, s);
             if (e != cudaSuccess) return e;
-        }
-        for (sim_t c : b->cubes) {
-            const cudaError_t e = cube_step(c->cube, dt, s);
-            if (e != cudaSuccess) return e;
+        } else {
+            for (size_t c = (size_t)(k - ng); c < b->cubes.size(); c += kCubeBranches) {
+                const cudaError_t e = cube_step(b->cubes[c]->cube, dt, s);
+                if (e != cudaSuccess) return e;
+            }
         }
     }
     return cudaSuccess;
+}
+
+cudaError_t batch_launch_steps(sim_batch_t b, int64_t n, double dt, cudaStream_t s)
+{
+    const int nb = n_branches(b);
+    if (nb <= 1) return nb ? branch_steps(b, 0, n, dt, s) : cudaSuccess;
+    cudaError_t e = cudaSuccess;
+    if (b->side.empty()) {
+        b->side.resize(nb, nullptr);
+        b->ev_join.resize(nb, nullptr);
+        e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+        for (int k = 0; k < nb && e == cudaSuccess; ++k) {
+            e = cudaStreamCreateWithFlags(&b->side[k], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join[k], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) return e;
+    }
+    e = cudaEventRecord(b->ev_fork, s);
+    for (int k = 0; k < nb && e == cudaSuccess; ++k) {
+        e = cudaStreamWaitEvent(b->side[k], b->ev_fork, 0);
+        if (e == cudaSuccess) e = branch_steps(b, k, n, dt, b->side[k]);
+        if (e == cudaSuccess) e = cudaEventRecord(b->ev_join[k], b->side[k]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->ev_join[k], 0);
+    }
+    return e;
 }
 
 int batch_graph(sim_batch_t b, double dt, int chunk, cudaGraphExec_t *out)
@@ -530,7 +603,10 @@ int batch_graph(sim_batch_t b, double dt, int chunk, cudaGraphExec_t *out)
         return SIM_OK;
     }
     cudaGraph_t g = nullptr;
-    cudaError_t e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
+    cudaError_t e = cudaSuccess;
+    if (!b->cap_stream && (e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+        return cuda_fail(e, "capture stream");
+    e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
     const cudaError_t le = batch_launch_steps(b, chunk, dt, b->cap_stream);
     e = cudaStreamEndCapture(b->cap_stream, &g);
@@ -602,10 +678,11 @@ int sim_batch_create(sim_batch_t *out, const sim_t *members, int n_members, void
     const size_t o_plans = take(sizeof(RingPlan) * nplan), o_items = take(sizeof(int) * nitem);
     const size_t o_base = take(sizeof(int64_t) * nplan), o_budget = take(sizeof(long long) * nplan);
     const size_t o_errs = take(sizeof(unsigned *) * n_members), o_eout = take(64);
-    cudaError_t e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaMalloc(&b->block, o);
-    if (e == cudaSuccess) e = cudaMallocHost(&b->h_err, 64);
+    // stream-ordered allocation: no device-wide synchronisation when batches are
+    // formed and dropped often (the serving loop re-forms them as jobs come and go)
+    cudaError_t e = cudaMallocAsync(&b->block, o, b->stream);
     if (e != cudaSuccess) {
+        b->block = nullptr;
         sim_batch_destroy(b);
         return e == cudaErrorMemoryAllocation ? fail(SIM_ENOMEM, "batch tables") : cuda_fail(e, "sim_batch_create");
     }
@@ -627,7 +704,6 @@ int sim_batch_create(sim_batch_t *out, const sim_t *members, int n_members, void
         e = cudaMemcpyAsync(b->budgets, budgets.data(), sizeof(long long) * nplan, cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->err_ptrs, errs.data(), sizeof(unsigned *) * n_members, cudaMemcpyHostToDevice, b->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) {
         sim_batch_destroy(b);
         return cuda_fail(e, "batch table upload");
@@ -664,9 +740,9 @@ int sim_batch_set_budgets(sim_batch_t b, const int64_t *steps)
         }
     }
     if (!dev.empty()) {
+        // from pageable memory: the call returns once the values are staged
         const cudaError_t e = cudaMemcpyAsync(b->budgets, dev.data(), sizeof(long long) * dev.size(),
                                               cudaMemcpyHostToDevice, b->stream);
-        if (e == cudaSuccess) cudaStreamSynchronize(b->stream);
         if (e != cudaSuccess) return cuda_fail(e, "budget upload");
     }
     return SIM_OK;
@@ -680,11 +756,20 @@ int sim_batch_step(sim_batch_t b, int64_t n_steps, double dt)
     int64_t left = n_steps;
     while (left > 0) {
         const int chunk = left >= kGraphChunk ? kGraphChunk : 1;
-        cudaGraphExec_t ex;
-        const int st = batch_graph(b, dt, chunk, &ex);
-        if (st != SIM_OK) return st;
-        const cudaError_t e = cudaGraphLaunch(ex, b->stream);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+        // A graph pays off only when reused: the first launches of a (dt, chunk)
+        // go out directly (a serving loop re-forms batches often).
+        int &uses = b->uses[{dt, chunk}];
+        if (uses < 2 && !b->graphs.count({dt, chunk})) {
+            ++uses;
+            const cudaError_t e = batch_launch_steps(b, chunk, dt, b->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "batched launch");
+        } else {
+            cudaGraphExec_t ex;
+            const int st = batch_graph(b, dt, chunk, &ex);
+            if (st != SIM_OK) return st;
+            const cudaError_t e = cudaGraphLaunch(ex, b->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+        }
         left -= chunk;
     }
     for (size_t i = 0; i < b->members.size(); ++i) {
@@ -704,10 +789,10 @@ int sim_batch_sync(sim_batch_t b)
     if (!b) return fail(SIM_EINVAL, "NULL batch");
     batch_error_kernel<<<1, 256, 0, b->stream>>>(b->err_ptrs, (int)b->members.size(), b->err_out);
     cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaMemcpyAsync(b->h_err, b->err_out, sizeof(unsigned), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&b->h_err, b->err_out, sizeof(unsigned), cudaMemcpyDeviceToHost, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return cuda_fail(e, "batch work failed");
-    const unsigned w = *b->h_err;
+    const unsigned w = b->h_err;
     if (w & ERR_TIMEOUT) return fail(SIM_ETIMEOUT, "a device-side wait exceeded its bound; results are invalid");
     if (w & ERR_RANGE) return fail(SIM_ENONFINITE, "a member's state became non-finite or left the fixed-point range");
     return SIM_OK;
@@ -716,21 +801,24 @@ int sim_batch_sync(sim_batch_t b)
 void sim_batch_destroy(sim_batch_t b)
 {
     if (!b) return;
-    if (b->block) cudaStreamSynchronize(b->stream);
+    cudaStreamSynchronize(b->stream); // the batch's graphs may still be running
     for (auto &kv : b->graphs) cudaGraphExecDestroy(kv.second);
-    if (b->block) cudaFree(b->block);
-    if (b->h_err) cudaFreeHost(b->h_err);
+    if (b->block) cudaFreeAsync(b->block, b->stream);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    for (cudaStream_t x : b->side)
+        if (x) cudaStreamDestroy(x);
+    for (cudaEvent_t x : b->ev_join)
+        if (x) cudaEventDestroy(x);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
     delete b;
 }
 
 void sim_destroy(sim_t h)
 {
     if (!h) return;
-    if (h->stream || h->block) cudaStreamSynchronize(h->stream);
+    if (h->block) cudaStreamSynchronize(h->stream);
     for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
-    if (h->block) cudaFree(h->block);
-    if (h->h_err) cudaFreeHost(h->h_err);
+    if (h->block && h->owns_block) cudaFree(h->block);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     delete h;
 }

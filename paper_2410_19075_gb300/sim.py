@@ -163,3 +163,69 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Server:
+    """Request loop with continuous batching (``srv_*``)."""
+
+    def __init__(self, hbm_budget_bytes: int, max_slots: int = 1024, chunk_steps: int = 64, stream=None):
+        h = ctypes.c_void_p()
+        check(lib().srv_create(ctypes.byref(h), int(hbm_budget_bytes), int(max_slots), int(chunk_steps),
+                               _stream_ptr(stream)))
+        self._h = h
+        self._shape = {}
+
+    def submit(self, model, topology, N, radius, params, init_state, n_steps, dt, node_param=None) -> int:
+        p = np.ascontiguousarray(params, dtype=np.float64)
+        y = np.ascontiguousarray(init_state, dtype=np.float64)
+        npar = np.ascontiguousarray(node_param, dtype=np.float64) if node_param is not None else None
+        jid = ctypes.c_int64(0)
+        check(lib().srv_submit(self._h, model, topology, int(N), int(radius),
+                               p.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), p.size, y.ctypes.data,
+                               npar.ctypes.data if npar is not None else None, int(n_steps), float(dt),
+                               ctypes.byref(jid)))
+        self._shape[jid.value] = (y.size, int(n_steps) + 1)
+        return jid.value
+
+    def poll(self, job_id: int):
+        """None while running; else (state, order, (t_submit, t_admit, t_done))."""
+        n_values, n_ord = self._shape[job_id]
+        done = ctypes.c_int(0)
+        state = np.empty(n_values)
+        order = np.empty(n_ord)
+        n = ctypes.c_int64(0)
+        times = np.empty(3)
+        st = lib().srv_poll(self._h, job_id, ctypes.byref(done), state.ctypes.data, n_values, order.ctypes.data,
+                            n_ord, ctypes.byref(n), times.ctypes.data)
+        if not done.value:
+            check(st)
+            return None
+        del self._shape[job_id]
+        check(st)
+        return state, order[: n.value].copy(), tuple(times)
+
+    def wait_idle(self):
+        check(lib().srv_wait_idle(self._h))
+
+    def stats(self):
+        a = (ctypes.c_int64 * 6)()
+        check(lib().srv_stats(self._h, a))
+        keys = ("completed", "pending", "queued", "node_steps", "batches_formed", "bytes_in_use")
+        return dict(zip(keys, list(a)))
+
+    def close(self):
+        if self._h is not None:
+            lib().srv_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
