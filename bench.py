@@ -39,6 +39,10 @@ RING_BYTES = {0: 344, 1: 432, 2: 704}
 # needs, from the kernels' expressions; a library sincos counts 50 and a library
 # exp/expm1 34 (their measured cost in DFMA equivalents, x2).  Tally in the design doc.
 RING_FLOPS = {0: 4 * (50 + 13) + 14, 1: 4 * 15 + 3 * 8 + 6, 2: 4 * (6 * 34 + 40) + 3 * 16 + 12}
+# Cube (Kuramoto): per stage the x, y and z passes move 32 + 32 + 72 bytes per
+# node; FP64 flops as the Kuramoto ring.
+CUBE_BYTES = 544
+CUBE_FLOPS = RING_FLOPS[0]
 
 
 def parse():
@@ -49,6 +53,7 @@ def parse():
     ap.add_argument("--chunk", type=int, default=100, help="RK4 steps per timed iteration")
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--model", type=int, default=1)
+    ap.add_argument("--topo", type=int, default=0, help="0 ring, 1 periodic cubic lattice (Kuramoto; N = edge)")
     ap.add_argument("--N", type=int, default=10 ** 6)
     ap.add_argument("--r", type=float, default=0.35)
     ap.add_argument("--dt", type=float, default=0.01)
@@ -63,13 +68,21 @@ def parse():
 def workload(args):
     N = args.N
     R = max(1, min((N - 1) // 2, int(math.floor(args.r * N))))
+    if args.topo == 1:
+        return N, R, I.ks_params(alpha=1.52)
     params = {0: I.ks_params(alpha=1.46), 1: I.fhn_params(), 2: I.hh_params()}[args.model]
     return N, R, params
 
 
+def nodes_of(args, N):
+    return N ** 3 if args.topo == 1 else N
+
+
 def config_of(args, N, R):
+    name = (f"Kuramoto-Sakaguchi periodic cubic lattice, N1={N} ({N ** 3} nodes), P={R}, RK4 dt={args.dt}"
+            if args.topo == 1 else f"{MODEL_NAMES[args.model]} ring, N={N}, R={R}, RK4 dt={args.dt}")
     return {
-        "workload": f"{MODEL_NAMES[args.model]} ring, N={N}, R={R}, RK4 dt={args.dt}",
+        "workload": name,
         "N": N, "R": R, "dt": args.dt,
         "rk4_steps_per_iteration": args.chunk,
         "l2": "flushed (512 MiB write) between timed iterations; within an iteration the network "
@@ -322,14 +335,17 @@ def run_native(args):
     torch.cuda.set_device(local)
     from paper_2410_19075_gb300 import Network
 
+    if args.topo == 1:
+        args.model = 0
     N, R, params = workload(args)
+    nodes = nodes_of(args, N)
     d = {0: 1, 1: 2, 2: 4}[args.model]
     stream = torch.cuda.current_stream()
-    y0_host = I.initial_state(args.model, 2412, rank, N)
+    y0_host = I.initial_state(args.model, 2412, rank, nodes)
     npar = I.hh_iext(2412, rank, N) if args.model == 2 else None
     y0_dev = torch.from_numpy(y0_host).cuda()
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
-    net = Network(args.model, 0, N, R, params, stream=stream)
+    net = Network(args.model, args.topo, N, R, params, stream=stream)
     if npar is not None:
         net.set_node_param(npar)
     net.set_state(y0_dev)
@@ -370,13 +386,13 @@ def run_native(args):
     ms = max_over_ranks(ms, world)
     y_check = net.get_state()  # surfaces any device error
     assert np.isfinite(y_check).all()
-    node_steps = float(N) * args.steps * world
+    node_steps = float(nodes) * args.steps * world
     value = node_steps / (ms * 1e-3)
 
     # --- end to end through the public API with host buffers: each iteration
     # loads its input state from pinned host memory, steps, reads the result back
     pin_in = torch.from_numpy(y0_host).pin_memory()
-    pin_out = torch.empty(d * N, dtype=torch.float64).pin_memory()
+    pin_out = torch.empty(d * nodes, dtype=torch.float64).pin_memory()
     e2e_chunks = chunks[: max(1, min(len(chunks), 10))]
     barrier(world)
     torch.cuda.synchronize()
@@ -387,14 +403,17 @@ def run_native(args):
         net.get_state(pin_out.numpy())
     e2e_s = max_over_ranks(time.perf_counter() - t0, world)
     e2e_steps = sum(e2e_chunks)
-    e2e_value = float(N) * e2e_steps * world / e2e_s
-    state_bytes = 8 * d * N
+    e2e_value = float(nodes) * e2e_steps * world / e2e_s
+    state_bytes = 8 * d * nodes
 
-    # --- dominant kernel: the ring stage kernel (4 launches per RK4 step)
+    # --- dominant kernel: the ring stage kernel (4 launches per RK4 step); for
+    # the cube the three passes of a stage are counted together as one launch
     launches = 4 * args.steps
     avg_launch_s = ms * 1e-3 / launches
-    alg_bytes_launch = RING_BYTES[args.model] / 4 * N
-    alg_flops_launch = RING_FLOPS[args.model] / 4 * N
+    bytes_ns = CUBE_BYTES if args.topo == 1 else RING_BYTES[args.model]
+    flops_ns = CUBE_FLOPS if args.topo == 1 else RING_FLOPS[args.model]
+    alg_bytes_launch = bytes_ns / 4 * nodes
+    alg_flops_launch = flops_ns / 4 * nodes
     peaks = {}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -418,8 +437,8 @@ def run_native(args):
             "e2e": {"value": e2e_value, "unit": "node-steps/s",
                     "h2d_bytes_per_step": state_bytes / max(1, e2e_chunks[0]),
                     "d2h_bytes_per_step": state_bytes / max(1, e2e_chunks[0])},
-            "gpu_launches": launches, "roofline": roofline, "clocks": clk}
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            "gpu_launches": launches * (3 if args.topo == 1 else 1), "roofline": roofline, "clocks": clk}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.topo == 0:
         line["cpu_baseline"] = cpu_baseline(args, N, R, params, args.cpu_seconds)
     if not args.no_batched:
         line["batched"] = bench_batched(args, flush, stream)
