@@ -82,9 +82,57 @@ __device__ __forceinline__ double fixed_to_double(i128 x, int F)
     return __longlong_as_double((long long)bits);
 }
 
+// int64 version (no 128-bit shifts).
 __device__ __forceinline__ double fixed_to_double(int64_t x, int F)
 {
-    return fixed_to_double((i128)x, F);
+    if (x == 0) return 0.0;
+    const uint64_t sign = (uint64_t)x & (1ull << 63);
+    uint64_t u = x < 0 ? (uint64_t)(-x) : (uint64_t)x;
+    const int lz = __clzll((long long)u);
+    u <<= lz; // leading one at bit 63
+    uint64_t mant = u >> 11;
+    const uint64_t rbit = (u >> 10) & 1ull;
+    const bool sticky = (u & 0x3FFull) != 0;
+    if (rbit && (sticky || (mant & 1ull))) mant += 1;
+    int ex = 63 - lz - F;
+    if (mant >> 53) {
+        mant >>= 1;
+        ex += 1;
+    }
+    return __longlong_as_double((long long)(sign | ((uint64_t)(ex + 1023) << 52) | (mant & 0xFFFFFFFFFFFFFull)));
+}
+
+// Correctly rounded double of x * 2^-F for 128-bit x, with 64-bit shifts only.
+__device__ __forceinline__ double fixed_to_double_wide(i128 x, int F)
+{
+    const int64_t hi_s = (int64_t)(x >> 64);
+    const uint64_t lo_s = (uint64_t)x;
+    if (hi_s == ((int64_t)lo_s >> 63)) return fixed_to_double((int64_t)lo_s, F); // fits in int64
+    const uint64_t sign = (uint64_t)hi_s & (1ull << 63);
+    const u128 ua = x < 0 ? (u128)(-x) : (u128)x; // |x| >= 2^63 here
+    const uint64_t hi = (uint64_t)(ua >> 64), lo = (uint64_t)ua;
+    int lz;
+    uint64_t top; // the top 64 bits of |x|, leading one at bit 63
+    bool low_rest;
+    if (hi == 0) { // 2^63 <= |x| < 2^64
+        lz = 64;
+        top = lo;
+        low_rest = false;
+    } else {
+        lz = __clzll((long long)hi);
+        top = lz ? (hi << lz) | (lo >> (64 - lz)) : hi;
+        low_rest = lz ? (lo << lz) != 0 : lo != 0;
+    }
+    uint64_t mant = top >> 11;
+    const uint64_t rbit = (top >> 10) & 1ull;
+    const bool sticky = ((top & 0x3FFull) != 0) || low_rest;
+    if (rbit && (sticky || (mant & 1ull))) mant += 1;
+    int ex = 127 - lz - F;
+    if (mant >> 53) {
+        mant >>= 1;
+        ex += 1;
+    }
+    return __longlong_as_double((long long)(sign | ((uint64_t)(ex + 1023) << 52) | (mant & 0xFFFFFFFFFFFFFull)));
 }
 
 // Inclusive warp scan of int64 (Hillis-Steele over shuffles).

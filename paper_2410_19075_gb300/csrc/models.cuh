@@ -38,7 +38,7 @@ template <> struct Model<0> {
     {
         const i128 ss = P.include_self ? W[0] : W[0] - (i128)qo[0];
         const i128 sc = P.include_self ? W[1] : W[1] - (i128)qo[1];
-        const double Ss = fixed_to_double(ss, F_), Sc = fixed_to_double(sc, F_);
+        const double Ss = fixed_to_double_wide(ss, F_), Sc = fixed_to_double_wide(sc, F_);
         const double s = fo[0], c = fo[1];
         const double sxa = s * P.c[3] + c * P.c[2]; // sin(phi + alpha)
         const double cxa = c * P.c[3] - s * P.c[2]; // cos(phi + alpha)
@@ -65,8 +65,8 @@ template <> struct Model<1> {
                                                const int64_t (&qo)[NQ], const i128 (&W)[NQ],
                                                const double *, double, double (&k)[D])
     {
-        const double Cu = fixed_to_double(W[0] - (i128)qo[0] * P.wsize, F_);
-        const double Cv = fixed_to_double(W[1] - (i128)qo[1] * P.wsize, F_);
+        const double Cu = fixed_to_double_wide(W[0] - (i128)qo[0] * P.wsize, F_);
+        const double Cv = fixed_to_double_wide(W[1] - (i128)qo[1] * P.wsize, F_);
         const double u = fo[0], v = fo[1];
         const double w = fma(u * u, -1.0 / 3.0, 1.0);      // 1 - u^2/3
         const double local = fma(u, w, -v);                // u - u^3/3 - v
@@ -92,7 +92,7 @@ template <> struct Model<2> {
                                                const int64_t (&qo)[NQ], const i128 (&W)[NQ],
                                                const double *X, double Iext, double (&k)[D])
     {
-        const double CV = fixed_to_double(W[0] - (i128)qo[0] * P.wsize, F_);
+        const double CV = fixed_to_double_wide(W[0] - (i128)qo[0] * P.wsize, F_);
         const double V = fo[0], m = X[0], h = X[1], n = X[2];
         const MathTables &T = P.tab;
         const double am = fast_x_over_1mexp(fma(V, 0.1, 4.0), T);                    // (V+40)/10

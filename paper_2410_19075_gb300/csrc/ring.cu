@@ -68,26 +68,11 @@ __device__ __forceinline__ i128 warp_incl_scan_i128(i128 v)
     return v;
 }
 
-// P(p) = sum_{j<p} Q(f_j) over the periodic extension of the ring, p in [-N, 2N):
-// group offset + sub-tile offset inside the group + prefix inside the sub-tile.
-__device__ __forceinline__ i128 prefix_at(const int64_t *lam, const i128 *ingrp, const i128 *grpofs, int64_t N,
-                                          int64_t p, i128 tot)
-{
-    i128 add = 0;
-    if (p < 0) {
-        p += N;
-        add = -tot;
-    } else if (p >= N) {
-        p -= N;
-        add = tot;
-    }
-    const int64_t sub = p >> kSubLog2;
-    i128 v = ldg_i128(grpofs + (sub >> kGroupLog2)) + ldg_i128(ingrp + sub) + add;
-    if (p & (kSubTile - 1)) v += (i128)__ldg(lam + p - 1);
-    return v;
-}
-
-template <int M> struct MinBlocks { static constexpr int value = 4; };
+// Resident CTAs per SM the register allocation is sized for (256 threads each).
+#ifndef SIM_RING_MIN_BLOCKS
+#define SIM_RING_MIN_BLOCKS 6
+#endif
+template <int M> struct MinBlocks { static constexpr int value = SIM_RING_MIN_BLOCKS; };
 template <> struct MinBlocks<2> { static constexpr int value = 2; };
 
 // One 256-node sub-tile `sub` of ring P, one node per thread (the whole CTA).
@@ -105,6 +90,48 @@ __device__ __forceinline__ void ring_stage_body(const RingPlan &P, const RingSta
     const int64_t N = P.N, nsub = P.nsub, ngroups = P.ngroups;
     const int64_t i = sub * kSubTile + tid;
 
+    // Window bases of this CTA: the right ends b = i+R+1 (side 0) and left ends
+    // a = i-R (side 1) of its nodes are consecutive, and each side covers at most
+    // three pieces (split at a sub-tile start and at N).  Per piece: its first
+    // position on the periodic extension, the multiple of N to subtract, and the
+    // exact prefix at its sub-tile's start (+ q * total).  Then every node needs
+    // one in-sub-tile prefix load per end.
+    __shared__ i128 s_base[2][3][NQ];
+    __shared__ int64_t s_start[2][3], s_qn[2][3];
+    if (STAGE > 0) {
+        if (tid < 2) {
+            const int side = tid;
+            const int64_t nvalid = N - sub * kSubTile < kSubTile ? N - sub * kSubTile : kSubTile;
+            const int64_t p0 = side == 0 ? sub * kSubTile + P.R + 1 : sub * kSubTile - P.R;
+            const int64_t p1 = p0 + nvalid - 1; // in [-N, 2N)
+            int64_t p = p0;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                if (p > p1) {
+                    s_start[side][k] = INT64_MAX;
+                    s_qn[side][k] = 0;
+                    continue;
+                }
+                const int q = p < 0 ? -1 : (p >= N ? 1 : 0);
+                const int64_t qn = q * N, pp = p - qn;
+                const int64_t st = pp >> kSubLog2;
+                int64_t end = ((st + 1) << kSubLog2) - 1;
+                if (end > N - 1) end = N - 1;
+#pragma unroll
+                for (int c = 0; c < NQ; ++c) {
+                    const i128 *grpofs = a.grpofs_in + c * (ngroups + 1);
+                    const i128 tot = ldg_i128(grpofs + ngroups);
+                    s_base[side][k][c] = ldg_i128(grpofs + (st >> kGroupLog2)) + ldg_i128(a.ingrp_in + c * nsub + st) +
+                                         (q < 0 ? -tot : (q > 0 ? tot : (i128)0));
+                }
+                s_start[side][k] = p;
+                s_qn[side][k] = qn;
+                p = end + qn + 1;
+            }
+        }
+        __syncthreads();
+    }
+
     int64_t qv[NQ];
     bool ok = true;
 #pragma unroll
@@ -115,20 +142,22 @@ __device__ __forceinline__ void ring_stage_body(const RingPlan &P, const RingSta
 #pragma unroll
             for (int v = 0; v < D; ++v) xn[v] = P.y[v * N + i];
         } else {
+            const int64_t b = i + P.R + 1, am = i - P.R;
+            const int kb = (b >= s_start[0][1]) + (b >= s_start[0][2]);
+            const int ka = (am >= s_start[1][1]) + (am >= s_start[1][2]);
+            const int64_t bp = b - s_qn[0][kb], ap = am - s_qn[1][ka];
             int64_t qo[NQ];
             double fo[NQ];
             i128 W[NQ];
 #pragma unroll
             for (int c = 0; c < NQ; ++c) {
                 const int64_t *lam = a.lam_in + c * N;
-                const i128 *ingrp = a.ingrp_in + c * nsub;
-                const i128 *grpofs = a.grpofs_in + c * (ngroups + 1);
-                const i128 tot = ldg_i128(grpofs + ngroups);
                 const int64_t l = __ldg(lam + i);
                 qo[c] = tid ? l - __ldg(lam + i - 1) : l; // tid = position in the sub-tile
                 fo[c] = fixed_to_double(qo[c], P.F);
-                W[c] = prefix_at(lam, ingrp, grpofs, N, i + P.R + 1, tot) -
-                       prefix_at(lam, ingrp, grpofs, N, i - P.R, tot);
+                const int64_t lb = (bp & (kSubTile - 1)) ? __ldg(lam + bp - 1) : 0;
+                const int64_t la = (ap & (kSubTile - 1)) ? __ldg(lam + ap - 1) : 0;
+                W[c] = (s_base[0][kb][c] - s_base[1][ka][c]) + (i128)(lb - la);
             }
             double X[NX > 0 ? NX : 1];
 #pragma unroll
