@@ -71,6 +71,8 @@ typedef enum {
 
 /* Creation flags. */
 #define SIM_FLAG_INCLUDE_SELF 1u /* count the node itself as one of its links */
+#define SIM_FLAG_STREAMING 2u    /* rings of <= 4096 nodes: use the multi-launch streaming kernels
+                                    instead of the thread-block-cluster kernel (same results) */
 
 /* Bytes of device memory sim_create() allocates for this network (for
  * admission control).  Returns 0 for invalid arguments. */

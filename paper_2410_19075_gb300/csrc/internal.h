@@ -56,6 +56,13 @@ cudaError_t ring_batch_step(const RingBatchGroup &g, double dt, cudaStream_t s);
 
 // Ring: f(y) -> lam[0], ofs[0] and the order parameter of y (Kuramoto).
 cudaError_t ring_prologue(const RingPlan &p, cudaStream_t s);
+// Small rings (N <= kClusterMaxNodes): all stages of n_steps RK4 steps in one
+// thread-block-cluster launch (ring_cluster.cu).  Same results as ring_step.
+constexpr int64_t kClusterMaxNodes = 4096;
+cudaError_t ring_cluster_configure(); // per device, before the first cluster launch
+int cluster_size_for(int64_t N);      // CTAs of the cluster for a ring of N nodes (0: not eligible)
+cudaError_t ring_cluster_steps(const RingPlan &p, double dt, int64_t n_steps, cudaStream_t s);
+
 // Ring: stage 1 only with dt = 0, so acc receives f(y) and y is untouched.
 cudaError_t ring_rhs(const RingPlan &p, cudaStream_t s);
 // Ring: one RK4 step, 4 fused stage kernels.

@@ -152,8 +152,14 @@ int check_device_error(sim_t h)
     return SIM_OK;
 }
 
+bool use_cluster(sim_t h)
+{
+    return h->topo == SIM_RING && !(h->flags & SIM_FLAG_STREAMING) && cluster_size_for(h->N) > 0;
+}
+
 cudaError_t launch_steps(sim_t h, int64_t n, double dt, cudaStream_t s)
 {
+    if (use_cluster(h)) return n > 0 ? ring_cluster_steps(h->ring, dt, n, s) : cudaSuccess;
     for (int64_t t = 0; t < n; ++t) {
         const cudaError_t e = h->topo == SIM_RING ? ring_step(h->ring, dt, s) : cube_step(h->cube, dt, s);
         if (e != cudaSuccess) return e;
@@ -226,7 +232,7 @@ static int create_impl(sim_t *out, int model, int topology, int64_t N, int64_t r
     if (!out) return fail(SIM_EINVAL, "out is NULL");
     *out = nullptr;
     if (const char *msg = validate(model, topology, N, radius, params, n_params)) return fail(SIM_EINVAL, msg);
-    if (flags & ~SIM_FLAG_INCLUDE_SELF) return fail(SIM_EINVAL, "unknown flags");
+    if (flags & ~(SIM_FLAG_INCLUDE_SELF | SIM_FLAG_STREAMING)) return fail(SIM_EINVAL, "unknown flags");
 
     sim_t h = new sim_handle();
     h->model = model;
@@ -334,6 +340,12 @@ static int create_impl(sim_t *out, int model, int topology, int64_t N, int64_t r
         p.obs = h->obs;
         p.obs_cap = kObsCap;
         p.obs_ctr = h->obs_ctr;
+        if (N <= kClusterMaxNodes && !(flags & SIM_FLAG_STREAMING)) {
+            static std::once_flag cl_once;
+            static cudaError_t cl_err = cudaSuccess;
+            std::call_once(cl_once, [] { cl_err = ring_cluster_configure(); });
+            if (cl_err != cudaSuccess) h->flags |= SIM_FLAG_STREAMING; // fall back to the streaming kernels
+        }
     } else {
         CubePlan &p = h->cube;
         p.N1 = N;

@@ -14,6 +14,7 @@ from ._lib import check, lib
 KS, FHN, HH = 0, 1, 2
 RING, CUBE3D = 0, 1
 FLAG_INCLUDE_SELF = 1
+FLAG_STREAMING = 2
 DIM = {KS: 1, FHN: 2, HH: 4}
 
 
@@ -41,10 +42,10 @@ class Network:
     """One network on the GPU: ``sim_create`` ... ``sim_destroy``."""
 
     def __init__(self, model: int, topology: int, N: int, radius: int, params, include_self: bool = False,
-                 stream=None):
+                 stream=None, streaming: bool = False):
         p = np.ascontiguousarray(params, dtype=np.float64)
         h = ctypes.c_void_p()
-        flags = FLAG_INCLUDE_SELF if include_self else 0
+        flags = (FLAG_INCLUDE_SELF if include_self else 0) | (FLAG_STREAMING if streaming else 0)
         check(lib().sim_create(ctypes.byref(h), model, topology, int(N), int(radius),
                                p.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), p.size, flags,
                                _stream_ptr(stream)))

@@ -174,3 +174,27 @@ def test_nonfinite_state_reported():
         net.set_state(I.fhn_state(3, 0, 100))
         net.step(2, 0.01)
         net.get_state()
+
+
+@pytest.mark.parametrize("model", [0, 1, 2])
+@pytest.mark.parametrize("N,R", [(3, 1), (257, 128), (1000, 350), (2048, 700), (4096, 1)])
+def test_cluster_path_equals_streaming_path_bitwise(model, N, R):
+    """Rings of <= 4096 nodes run all steps of a call in one thread-block cluster;
+    the multi-launch streaming kernels (SIM_FLAG_STREAMING) must give the same bits,
+    and either path can continue the other's run."""
+    from paper_2410_19075_gb300 import Network
+    params = PARAMS[model]()
+    y0, npar = inputs_for(model, 0, N, 3 + N)
+    outs = []
+    for streaming in (False, True):
+        with Network(model, 0, N, R, params, streaming=streaming) as net:
+            if npar is not None:
+                net.set_node_param(npar)
+            net.set_state(y0)
+            net.step(37, 0.01)
+            k = net.rhs()
+            net.step(5, 0.01)
+            outs.append((net.get_state(), net.observables(), k))
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert np.array_equal(outs[0][1], outs[1][1])
+    assert np.array_equal(outs[0][2], outs[1][2])
