@@ -12,39 +12,59 @@
 
 namespace simk {
 
-constexpr int kCubeRowWarps = 4;      // x pass: one warp per row, 4 rows per CTA
+constexpr int kCubeRowWarps = 8;      // x pass: one warp per row, 8 rows per CTA
 constexpr int kCubeMaxN1 = 1024;      // x-pass shared-memory row buffer
 constexpr int kCubeColThreads = 128;  // y and z passes: threads per CTA along i
 
 // x pass: one warp per (j, k) row.  pre(p) = sum_{m<p} Q(f(m)) for p in [0, N1]
-// is built in shared memory; SX(i) = Pe(i+P+1) - Pe(i-P) on the periodic
-// extension Pe(p) = pre(p mod N1) + floor(p / N1) * pre(N1).
+// is built in shared memory (row stride N1 + 1 per component, sized at launch);
+// SX(i) = Pe(i+P+1) - Pe(i-P) on the periodic extension
+// Pe(p) = pre(p mod N1) + floor(p / N1) * pre(N1).  Rows are read and written
+// with coalesced accesses; the scan runs on the shared-memory copy.
 __global__ void __launch_bounds__(32 * kCubeRowWarps) cube_x_kernel(CubePlan p)
 {
     extern __shared__ int64_t smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t N1 = p.N1, P = p.P, nodes = N1 * N1 * N1;
-    int64_t *pre0 = smem + (int64_t)warp * 2 * (kCubeMaxN1 + 1);
-    int64_t *pre1 = pre0 + (kCubeMaxN1 + 1);
-    const int per = (int)((N1 + 31) / 32); // contiguous chunk per lane
+    const int64_t N1 = p.N1, P = p.P, nodes = N1 * N1 * N1, stride = N1 + 1;
+    int64_t *pre0 = smem + (int64_t)warp * 2 * stride;
+    int64_t *pre1 = pre0 + stride;
+    const int per = (int)((N1 + 31) / 32); // contiguous chunk per lane in the scan
     bool ok = true;
     for (int64_t row = (int64_t)blockIdx.x * kCubeRowWarps + warp; row < N1 * N1;
          row += (int64_t)gridDim.x * kCubeRowWarps) {
-        const double *fs = p.f + row * N1, *fc = p.f + nodes + row * N1;
-        // serial prefix of each lane's chunk, then a warp scan of chunk totals
+        const double *__restrict__ fs = p.f + row * N1;
+        const double *__restrict__ fc = p.f + nodes + row * N1;
+        // coalesced loads, 8 per lane in flight before they are used
+        for (int64_t mb = lane; mb < N1; mb += 32 * 8) {
+            double vs[8], vc[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int64_t m = mb + 32 * u;
+                vs[u] = m < N1 ? __ldg(fs + m) : 0.0;
+                vc[u] = m < N1 ? __ldg(fc + m) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int64_t m = mb + 32 * u;
+                if (m < N1) {
+                    pre0[m + 1] = to_fixed(vs[u], p.F, 1, ok);
+                    pre1[m + 1] = to_fixed(vc[u], p.F, 1, ok);
+                }
+            }
+        }
+        __syncwarp();
         const int m0 = lane * per;
         int64_t r0 = 0, r1 = 0;
         for (int t = 0; t < per; ++t) {
             const int m = m0 + t;
             if (m < N1) {
-                r0 += to_fixed(fs[m], p.F, 1, ok);
-                r1 += to_fixed(fc[m], p.F, 1, ok);
+                r0 += pre0[m + 1];
+                r1 += pre1[m + 1];
                 pre0[m + 1] = r0;
                 pre1[m + 1] = r1;
             }
         }
         const int64_t e0 = warp_incl_scan(r0) - r0, e1 = warp_incl_scan(r1) - r1;
-        __syncwarp();
         for (int t = 0; t < per; ++t) {
             const int m = m0 + t;
             if (m < N1) {
@@ -58,7 +78,8 @@ __global__ void __launch_bounds__(32 * kCubeRowWarps) cube_x_kernel(CubePlan p)
         }
         __syncwarp();
         const int64_t t0 = pre0[N1], t1 = pre1[N1];
-        int64_t *o0 = p.sx + row * N1, *o1 = p.sx + nodes + row * N1;
+        int64_t *__restrict__ o0 = p.sx + row * N1;
+        int64_t *__restrict__ o1 = p.sx + nodes + row * N1;
         for (int64_t i = lane; i < N1; i += 32) {
             int64_t b = i + P + 1, a = i - P;
             int64_t s0 = 0, s1 = 0;
@@ -73,29 +94,50 @@ __global__ void __launch_bounds__(32 * kCubeRowWarps) cube_x_kernel(CubePlan p)
 }
 
 // y pass: one thread per (i, k) column, sliding window along j (exact int64).
+// The loop runs in blocks of 8 rows whose 16 window loads per component are
+// issued together, so each thread keeps several loads in flight.
 __global__ void __launch_bounds__(kCubeColThreads) cube_y_kernel(CubePlan p)
 {
+    constexpr int U = 8;
     const int64_t N1 = p.N1, P = p.P, nodes = N1 * N1 * N1;
     const int64_t i = (int64_t)blockIdx.x * kCubeColThreads + threadIdx.x;
     const int64_t k = blockIdx.y;
     if (i >= N1) return;
     const int64_t col = k * N1 * N1 + i; // + j * N1
-    const int64_t *a0 = p.sx + col, *a1 = p.sx + nodes + col;
-    int64_t *o0 = p.sxy + col, *o1 = p.sxy + nodes + col;
+    const int64_t *__restrict__ a0 = p.sx + col;
+    const int64_t *__restrict__ a1 = p.sx + nodes + col;
+    int64_t *__restrict__ o0 = p.sxy + col;
+    int64_t *__restrict__ o1 = p.sxy + nodes + col;
     int64_t s0 = 0, s1 = 0;
     for (int64_t d = -P; d <= P; ++d) {
         const int64_t j = d < 0 ? d + N1 : d;
-        s0 += a0[j * N1];
-        s1 += a1[j * N1];
+        s0 += __ldg(a0 + j * N1);
+        s1 += __ldg(a1 + j * N1);
     }
-    for (int64_t j = 0; j < N1; ++j) {
-        o0[j * N1] = s0;
-        o1[j * N1] = s1;
-        int64_t jin = j + P + 1, jout = j - P;
-        if (jin >= N1) jin -= N1;
-        if (jout < 0) jout += N1;
-        s0 += a0[jin * N1] - a0[jout * N1];
-        s1 += a1[jin * N1] - a1[jout * N1];
+    for (int64_t j0 = 0; j0 < N1; j0 += U) {
+        int64_t in0[U], out0[U], in1[U], out1[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t j = j0 + u;
+            int64_t jin = j + P + 1, jout = j - P;
+            if (jin >= N1) jin -= N1;
+            if (jout < 0) jout += N1;
+            const bool live = j < N1;
+            in0[u] = live ? __ldg(a0 + jin * N1) : 0;
+            out0[u] = live ? __ldg(a0 + jout * N1) : 0;
+            in1[u] = live ? __ldg(a1 + jin * N1) : 0;
+            out1[u] = live ? __ldg(a1 + jout * N1) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t j = j0 + u;
+            if (j < N1) {
+                o0[j * N1] = s0;
+                o1[j * N1] = s1;
+            }
+            s0 += in0[u] - out0[u];
+            s1 += in1[u] - out1[u];
+        }
     }
 }
 
@@ -209,7 +251,7 @@ static dim3 col_grid(int64_t N1)
     return dim3((unsigned)((N1 + kCubeColThreads - 1) / kCubeColThreads), (unsigned)N1);
 }
 
-constexpr size_t kCubeXSmem = (size_t)kCubeRowWarps * 2 * (kCubeMaxN1 + 1) * sizeof(int64_t);
+constexpr size_t kCubeXSmem = (size_t)kCubeRowWarps * 2 * (kCubeMaxN1 + 1) * sizeof(int64_t); // largest N1
 
 cudaError_t cube_configure()
 {
@@ -218,10 +260,10 @@ cudaError_t cube_configure()
 
 static cudaError_t launch_x(const CubePlan &p, cudaStream_t s)
 {
-    const size_t smem = kCubeXSmem;
+    const size_t smem = (size_t)kCubeRowWarps * 2 * (size_t)(p.N1 + 1) * sizeof(int64_t);
     const int64_t rows = p.N1 * p.N1;
     const int64_t want = (rows + kCubeRowWarps - 1) / kCubeRowWarps;
-    const unsigned grid = (unsigned)(want < 152 * 8 ? want : 152 * 8);
+    const unsigned grid = (unsigned)(want < 152 * 16 ? want : 152 * 16);
     cube_x_kernel<<<grid, 32 * kCubeRowWarps, smem, s>>>(p);
     return cudaGetLastError();
 }
