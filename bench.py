@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-sweep comparison")
     ap.add_argument("--no-served", action="store_true", help="skip the served-mix comparison")
+    ap.add_argument("--no-extra", action="store_true", help="skip the small-ring and lattice lines")
     ap.add_argument("--batched-only", action="store_true")
     return ap.parse_args()
 
@@ -281,6 +282,57 @@ def bench_batched(args, flush, stream, n_inst=4096, steps=2000, plain_steps=20):
             "gpu_launches": 4 * steps * 1}
 
 
+# ----------------------------------------------------------------------------- c1 and c3
+def bench_small_ring(args, stream, flush, steps=200, reps=5):
+    """Kuramoto ring N=1000, R=350, alpha=1.46: latency of one RK4 step (the whole
+    200-step run per timed iteration, median of reps, L2 flushed between)."""
+    import torch
+    from paper_2410_19075_gb300 import Network
+    N, R = 1000, 350
+    net = Network(0, 0, N, R, I.ks_params(alpha=1.46), stream=stream)
+    y0 = torch.from_numpy(I.ks_phases(2411, 0, N)).cuda()
+    net.set_state(y0)
+    net.step(steps, args.dt)
+    times = []
+    for _ in range(reps):
+        net.set_state(y0)
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        net.step(steps, args.dt)
+        b.record(stream)
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    net.close()
+    ms = statistics.median(times)
+    return {"workload": f"Kuramoto ring N={N}, R={R}, alpha=1.46, {steps} RK4 steps (cluster-resident kernel)",
+            "us_per_step": 1e3 * ms / steps, "value": N * steps / (ms * 1e-3), "unit": "node-steps/s"}
+
+
+def bench_cube(args, stream, flush, N1=464, P=92, steps=20):
+    """Kuramoto periodic cubic lattice 464^3 (99.9 million nodes), P=92 box,
+    alpha=1.52: separable exact box sums, steps RK4 steps per timed iteration."""
+    import torch
+    from paper_2410_19075_gb300 import Network
+    net = Network(0, 1, N1, P, I.ks_params(alpha=1.52), stream=stream)
+    net.set_state(torch.from_numpy(I.ks_phases(2413, 0, N1 ** 3)).cuda())
+    net.step(3, args.dt)
+    net.sync()
+    flush.zero_()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    net.step(steps, args.dt)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    net.sync()
+    net.close()
+    nodes = N1 ** 3
+    return {"workload": f"Kuramoto periodic cubic lattice N1={N1} ({nodes} nodes), P={P}, alpha=1.52",
+            "steps": steps, "ms_per_step": ms / steps, "value": nodes * steps / (ms * 1e-3),
+            "unit": "node-steps/s", "hbm_gbs_algorithmic": CUBE_BYTES * nodes * steps / (ms * 1e-3) / 1e9}
+
+
 # ----------------------------------------------------------------------------- served mix
 def serve_trace(jobs, inits, slots, budget, chunk, stream):
     from paper_2410_19075_gb300 import Server
@@ -440,6 +492,9 @@ def run_native(args):
             "gpu_launches": launches * (3 if args.topo == 1 else 1), "roofline": roofline, "clocks": clk}
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.topo == 0:
         line["cpu_baseline"] = cpu_baseline(args, N, R, params, args.cpu_seconds)
+    if not args.no_extra and args.topo == 0 and world == 1:
+        line["small_ring"] = bench_small_ring(args, stream, flush)
+        line["cube"] = bench_cube(args, stream, flush)
     if not args.no_batched:
         line["batched"] = bench_batched(args, flush, stream)
     if not args.no_served:
