@@ -23,11 +23,11 @@ import numpy as np
 
 from .build import build as _build
 
-KS, FHN, HH = 0, 1, 2
-RING, CUBE = 0, 1
+KS, FHN, HH, KSI = 0, 1, 2, 3
+RING, CUBE, BALL, DISK = 0, 1, 2, 3
 REVERSE, INCLUDE_SELF = 1, 2
-_DIM = {KS: 1, FHN: 2, HH: 4}
-_NPARAM = {KS: 3, FHN: 4, HH: 8}
+_DIM = {KS: 1, FHN: 2, HH: 4, KSI: 2}
+_NPARAM = {KS: 3, FHN: 4, HH: 8, KSI: 4}
 
 _lib = None
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -43,6 +43,8 @@ def lib():
         _lib.orc_rk4.argtypes = [c_int, c_int, i64, i64, _dp, c_int, _dp, _dp, i64, c_double, _dp, c_int, c_int]
         _lib.orc_window_sum.argtypes = [c_int, i64, i64, _dp, i64, _ip, _dp, c_int]
         _lib.orc_rhs_sampled.argtypes = [c_int, c_int, i64, i64, _dp, c_int, _dp, _dp, i64, _ip, _dp, c_int, c_int]
+        _lib.orc_links.argtypes = [c_int, i64, i64, c_int]
+        _lib.orc_links.restype = i64
         _lib.orc_order_parameter.argtypes = [i64, _dp]
         _lib.orc_order_parameter.restype = c_double
         for name in ("orc_hh_alpha_m", "orc_hh_beta_m", "orc_hh_alpha_h", "orc_hh_beta_h",
@@ -65,7 +67,16 @@ def _arr(a, n=None):
 
 
 def nodes_of(topo, N):
-    return N ** 3 if topo == CUBE else N
+    if topo in (CUBE, BALL):
+        return N ** 3
+    if topo == DISK:
+        return N ** 2
+    return N
+
+
+def links(topo, N, R, include_self=False):
+    """Number of links of a node (window size) as the oracle enumerates it."""
+    return int(lib().orc_links(topo, N, R, 1 if include_self else 0))
 
 
 def _check(st, what):
@@ -103,7 +114,7 @@ def rk4(model, topo, N, R, params, y0, n_steps, dt, node_param=None, flags=0, th
     y = _arr(y0, nodes_of(topo, N) * _DIM[model]).copy()
     p = _arr(params)
     npar = _arr(node_param, nodes_of(topo, N)) if node_param is not None else None
-    order = np.empty(n_steps + 1) if (record_order and model == KS) else None
+    order = np.empty(n_steps + 1) if (record_order and model in (KS, KSI)) else None
     _check(lib().orc_rk4(model, topo, N, R, _d(p), p.size, _d(npar), _d(y), n_steps, float(dt),
                          _d(order), flags, threads), "rk4")
     return y, order

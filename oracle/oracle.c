@@ -24,6 +24,8 @@
  *     node index k*N1^2 + j*N1 + i (Section IV, 3D networks), coupled to the
  *     (2P+1)^3 box around it.  Self is excluded unless ORC_INCLUDE_SELF.
  *   - Classic fixed-step fourth-order Runge-Kutta.
+ *   - Kuramoto-Sakaguchi with inertia, Eq. (3) with m != 0, as phi' = psi,
+ *     psi' = ((mu/K) sum_j sin(phi_j - phi_i - alpha) - eps psi) / m.
  *   - Kuramoto order parameter |sum_j exp(i phi_j)| / n.
  *
  * Build: gcc -O2 -std=c11 -ffp-contract=off -fopenmp -shared -fPIC (see build.py).
@@ -38,8 +40,8 @@
 #include <omp.h>
 #endif
 
-enum { ORC_KS = 0, ORC_FHN = 1, ORC_HH = 2 };
-enum { ORC_RING = 0, ORC_CUBE = 1 };
+enum { ORC_KS = 0, ORC_FHN = 1, ORC_HH = 2, ORC_KSI = 3 };
+enum { ORC_RING = 0, ORC_CUBE = 1, ORC_BALL = 2, ORC_DISK = 3 };
 enum { ORC_REVERSE = 1, ORC_INCLUDE_SELF = 2 };
 enum { ORC_OK = 0, ORC_EINVAL = -1, ORC_ENOMEM = -2 };
 
@@ -50,14 +52,18 @@ int orc_dim(int model)
     case ORC_KS: return 1;
     case ORC_FHN: return 2;
     case ORC_HH: return 4;
+    case ORC_KSI: return 2;
     default: return 0;
     }
 }
 
-/* Number of nodes: N for the ring, N^3 for the cube (N is the edge N1). */
+/* Number of nodes: N for the ring, N1^3 for the cube and the ball, N1^2 for the
+ * disk (N is the edge N1). */
 int64_t orc_nodes(int topo, int64_t N)
 {
-    return topo == ORC_CUBE ? N * N * N : N;
+    if (topo == ORC_CUBE || topo == ORC_BALL) return N * N * N;
+    if (topo == ORC_DISK) return N * N;
+    return N;
 }
 
 static int n_params_of(int model)
@@ -66,6 +72,7 @@ static int n_params_of(int model)
     case ORC_KS: return 3;  /* omega, mu, alpha */
     case ORC_FHN: return 4; /* eps, a, sigma, phi */
     case ORC_HH: return 8;  /* Cm, gNa, gK, gL, ENa, EK, EL, g */
+    case ORC_KSI: return 4; /* m, eps, mu, alpha */
     default: return -1;
     }
 }
@@ -73,17 +80,21 @@ static int n_params_of(int model)
 int orc_validate(int model, int topo, int64_t N, int64_t R, int n_params)
 {
     if (orc_dim(model) == 0) return ORC_EINVAL;
-    if (topo != ORC_RING && topo != ORC_CUBE) return ORC_EINVAL;
+    if (topo < ORC_RING || topo > ORC_DISK) return ORC_EINVAL;
     if (n_params != n_params_of(model)) return ORC_EINVAL;
     if (R < 1 || N < 2 * R + 1) return ORC_EINVAL;
-    if (topo == ORC_CUBE && model != ORC_KS) return ORC_EINVAL;
+    if (topo != ORC_RING && model != ORC_KS && model != ORC_KSI) return ORC_EINVAL;
     return ORC_OK;
 }
 
 /* ------------------------------------------------------------------------- */
 /* Neighbour enumeration.  The window of node `node` is listed into `nb` in
- * increasing offset order (ring: d = -R..R; cube: dz, then dy, then dx, each
- * -P..P), skipping the node itself unless include_self.  Returns the count. */
+ * increasing offset order (ring: d = -R..R; lattices: dz, then dy, then dx,
+ * each -P..P), skipping the node itself unless include_self.  The cube keeps
+ * every offset of the (2P+1)^3 box; the ball keeps dx^2 + dy^2 + dz^2 <= P^2
+ * (Section IV, 3D networks: the sphere of radius P, index k N1^2 + j N1 + i);
+ * the disk keeps dx^2 + dy^2 <= P^2 (Section IV, 2D networks, index j N1 + i).
+ * Returns the count. */
 static int64_t wrap(int64_t a, int64_t n)
 {
     int64_t r = a % n;
@@ -98,11 +109,20 @@ static int64_t list_window(int topo, int64_t N, int64_t R, int64_t node, int inc
             if (d == 0 && !include_self) continue;
             nb[c++] = wrap(node + d, N);
         }
+    } else if (topo == ORC_DISK) {
+        int64_t i = node % N, j = node / N;
+        for (int64_t dy = -R; dy <= R; ++dy)
+            for (int64_t dx = -R; dx <= R; ++dx) {
+                if (dx * dx + dy * dy > R * R) continue;
+                if (dx == 0 && dy == 0 && !include_self) continue;
+                nb[c++] = wrap(j + dy, N) * N + wrap(i + dx, N);
+            }
     } else {
         int64_t i = node % N, j = (node / N) % N, k = node / (N * N);
         for (int64_t dz = -R; dz <= R; ++dz)
             for (int64_t dy = -R; dy <= R; ++dy)
                 for (int64_t dx = -R; dx <= R; ++dx) {
+                    if (topo == ORC_BALL && dx * dx + dy * dy + dz * dz > R * R) continue;
                     if (dx == 0 && dy == 0 && dz == 0 && !include_self) continue;
                     nb[c++] = wrap(k + dz, N) * N * N + wrap(j + dy, N) * N + wrap(i + dx, N);
                 }
@@ -110,11 +130,23 @@ static int64_t list_window(int topo, int64_t N, int64_t R, int64_t node, int inc
     return c;
 }
 
+/* An upper bound of the window size (the enclosing box). */
 static int64_t window_size(int topo, int64_t R, int include_self)
 {
     int64_t w = 2 * R + 1;
-    int64_t full = topo == ORC_RING ? w : w * w * w;
+    int64_t full = topo == ORC_RING ? w : (topo == ORC_DISK ? w * w : w * w * w);
     return include_self ? full : full - 1;
+}
+
+/* Links of a node (the window size): used by tests against the paper's counts. */
+int64_t orc_links(int topo, int64_t N, int64_t R, int include_self)
+{
+    if (R < 1 || N < 2 * R + 1) return -1;
+    int64_t *nb = malloc(sizeof(int64_t) * (size_t)window_size(topo, R, 1));
+    if (!nb) return -1;
+    int64_t c = list_window(topo, N, R, 0, include_self, nb);
+    free(nb);
+    return c;
 }
 
 /* ------------------------------------------------------------------------- */
@@ -154,6 +186,16 @@ static void rhs_node(int model, int topo, int64_t N, int64_t R, const double *p,
         for (int64_t t = first; t != last; t += step)
             sum += sin(phi_i - x[nb[t]] + alpha);
         k[0] = omega - (mu / K) * sum;
+    } else if (model == ORC_KSI) {
+        /* Eq. (3) with inertia: m phi'' + eps phi' = (mu/K) sum_j sin(phi_j - phi_i - alpha),
+         * as the first-order system phi' = psi, psi' = ((mu/K) sum_j ... - eps psi) / m. */
+        double m = p[0], eps = p[1], mu = p[2], alpha = p[3];
+        const double *phi = x, *psi = x + nodes;
+        double phi_i = phi[i], sum = 0.0;
+        for (int64_t t = first; t != last; t += step)
+            sum += sin(phi[nb[t]] - phi_i - alpha);
+        k[0] = psi[i];
+        k[1] = ((mu / K) * sum - eps * psi[i]) / m;
     } else if (model == ORC_FHN) {
         double eps = p[0], a = p[1], sigma = p[2], phi = p[3];
         double buu = cos(phi), buv = sin(phi), bvu = -sin(phi), bvv = cos(phi);
@@ -259,7 +301,8 @@ int orc_rk4(int model, int topo, int64_t N, int64_t R, const double *params, int
         return ORC_ENOMEM;
     }
     int nt = set_threads(nthreads);
-    if (order_out && model == ORC_KS) order_out[0] = orc_order_parameter(nodes, y);
+    int has_order = model == ORC_KS || model == ORC_KSI; /* phases are the first variable */
+    if (order_out && has_order) order_out[0] = orc_order_parameter(nodes, y);
     for (int64_t s = 0; s < n_steps && st == ORC_OK; ++s) {
         st = orc_rhs(model, topo, N, R, params, n_params, node_param, y, k1, flags, nt);
         for (int64_t q = 0; q < len; ++q) tmp[q] = y[q] + dt / 2.0 * k1[q];
@@ -270,7 +313,7 @@ int orc_rk4(int model, int topo, int64_t N, int64_t R, const double *params, int
         if (st == ORC_OK) st = orc_rhs(model, topo, N, R, params, n_params, node_param, tmp, k4, flags, nt);
         for (int64_t q = 0; q < len; ++q)
             y[q] = y[q] + dt / 6.0 * (k1[q] + 2.0 * k2[q] + 2.0 * k3[q] + k4[q]);
-        if (order_out && model == ORC_KS) order_out[s + 1] = orc_order_parameter(nodes, y);
+        if (order_out && has_order) order_out[s + 1] = orc_order_parameter(nodes, y);
     }
     free(k1); free(k2); free(k3); free(k4); free(tmp);
     return st;

@@ -410,3 +410,137 @@ def test_invalid_arguments_rejected():
         oracle.rk4(oracle.FHN, oracle.CUBE, 5, 1, I.fhn_params(), np.zeros(250), 1, 0.01)
     with pytest.raises(ValueError):
         oracle.rk4(oracle.KS, oracle.RING, 10, 2, I.ks_params(), np.zeros(10), 1, 0.0)
+
+
+# ---------------------------------------------------------------- lattices of the paper
+def test_ball_and_disk_link_counts_match_the_paper():
+    with open(os.path.join(GOLDEN, "lattice_link_counts.txt")) as fh:
+        rows = [ln.split() for ln in fh if ln.strip() and not ln.startswith("#")]
+    for topo_name, P, count in rows:
+        topo = {"ball": oracle.BALL, "disk": oracle.DISK}[topo_name]
+        N1 = 2 * int(P) + 3
+        assert oracle.links(topo, N1, int(P), include_self=True) == int(count), (topo_name, P)
+        assert oracle.links(topo, N1, int(P)) == int(count) - 1
+
+
+def _ball_member(N1, P, a, b, dims, include_self=False):
+    ca = [(a // N1 ** d) % N1 for d in range(dims)]
+    cb = [(b // N1 ** d) % N1 for d in range(dims)]
+    ds = []
+    for x, y in zip(ca, cb):
+        d = abs(x - y) % N1
+        ds.append(min(d, N1 - d))
+    return sum(d * d for d in ds) <= P * P and (include_self or any(ds))
+
+
+@pytest.mark.parametrize("topo,dims,N1,P", [(oracle.BALL, 3, 5, 2), (oracle.BALL, 3, 7, 3), (oracle.DISK, 2, 5, 2),
+                                            (oracle.DISK, 2, 9, 4), (oracle.DISK, 2, 6, 1)])
+def test_ball_disk_window_sums_from_geometry(topo, dims, N1, P):
+    n = N1 ** dims
+    f = I.uniform(20, 0, 0, n, -1, 1)
+    got = oracle.window_sum(topo, N1, P, f)
+    for i in range(n):
+        e = sum(f[j] for j in range(n) if _ball_member(N1, P, i, j, dims))
+        assert abs(got[i] - e) < 1e-12
+
+
+def _inertia_constant_coupling_solution(m, eps, c, phi0, psi0, t):
+    """psi' = (c - eps psi)/m with constant c: psi(t) = psi_inf + (psi0 - psi_inf) e^{-eps t/m}."""
+    pinf = c / eps
+    e = math.exp(-eps * t / m)
+    return phi0 + pinf * t + (psi0 - pinf) * (m / eps) * (1 - e), pinf + (psi0 - pinf) * e
+
+
+@pytest.mark.parametrize("topo,N", [(oracle.RING, 21), (oracle.CUBE, 7), (oracle.BALL, 7), (oracle.DISK, 9)])
+def test_inertia_in_phase_state_closed_form(topo, N):
+    """All phases equal: the mean coupling is sin(-alpha), and psi relaxes
+    exponentially to -mu sin(alpha)/eps (Eq. 3 with m != 0)."""
+    m, eps, mu, alpha = 1.0, 0.05, 0.8, 0.45
+    R = 2 if topo != oracle.RING else 6
+    n = oracle.nodes_of(topo, N)
+    y0 = np.concatenate([np.full(n, 0.3), np.full(n, 0.2)])
+    T = 500
+    y, order = oracle.rk4(oracle.KSI, topo, N, R, [m, eps, mu, alpha], y0, T, 0.01, record_order=True)
+    phi, psi = _inertia_constant_coupling_solution(m, eps, -mu * math.sin(alpha), 0.3, 0.2, T * 0.01)
+    assert np.abs(y[:n] - phi).max() < 1e-10
+    assert np.abs(y[n:] - psi).max() < 1e-10
+    assert np.abs(order - 1).max() < 1e-14
+
+
+@pytest.mark.parametrize("topo,dims,N1,P,q", [(oracle.BALL, 3, 9, 2, 1), (oracle.BALL, 3, 11, 3, 2),
+                                              (oracle.DISK, 2, 12, 4, 1), (oracle.RING, 1, 40, 9, 3)])
+def test_inertia_plane_wave_closed_form(topo, dims, N1, P, q):
+    """phi = kappa i_x: every node sees the same mean coupling
+    -(sin alpha / K) (sum over its window of cos(kappa dx)), counted here from the
+    geometry, so psi relaxes exponentially as for a constant drive."""
+    m, eps, mu, alpha = 1.0, 0.05, 1.0, 0.45
+    kap = 2 * math.pi * q / N1
+    offs = []
+    rng_ = range(-P, P + 1)
+    if dims == 1:
+        offs = [d for d in rng_ if d != 0]
+    elif dims == 2:
+        offs = [dx for dx in rng_ for dy in rng_ if dx * dx + dy * dy <= P * P and (dx, dy) != (0, 0)]
+    else:
+        offs = [dx for dx in rng_ for dy in rng_ for dz in rng_
+                if dx * dx + dy * dy + dz * dz <= P * P and (dx, dy, dz) != (0, 0, 0)]
+    K = len(offs)
+    c = -mu * math.sin(alpha) * sum(math.cos(kap * d) for d in offs) / K
+    n = N1 ** dims
+    ix = np.arange(n) % N1
+    phi0 = kap * ix
+    y0 = np.concatenate([phi0, np.full(n, -0.1)])
+    T = 300
+    y, _ = oracle.rk4(oracle.KSI, topo, N1, P, [m, eps, mu, alpha], y0, T, 0.01)
+    dphi, psi = _inertia_constant_coupling_solution(m, eps, c, 0.0, -0.1, T * 0.01)
+    assert np.abs(y[:n] - phi0 - dphi).max() < 1e-10
+    assert np.abs(y[n:] - psi).max() < 1e-10
+
+
+@pytest.mark.parametrize("topo,dims,N,R", [(oracle.RING, 1, 11, 3), (oracle.BALL, 3, 5, 2), (oracle.DISK, 2, 6, 2)])
+def test_inertia_jacobian_matches_equation(topo, dims, N, R):
+    m, eps, mu, alpha = 1.3, 0.05, 0.7, 0.45
+    n = oracle.nodes_of(topo, N)
+    x = np.concatenate([I.ks_phases(21, 0, n), I.uniform(21, 0, 5, n, -1, 1)])
+    J = _fd_jacobian(oracle.KSI, topo, N, R, [m, eps, mu, alpha], x)
+    member = (lambda N_, R_, a, b: ring_member(N_, R_, a, b)) if topo == oracle.RING else \
+        (lambda N_, R_, a, b: _ball_member(N_, R_, a, b, dims))
+    K = sum(1 for j in range(n) if member(N, R, 0, j))
+    phi = x[:n]
+    for i in range(n):
+        diag = 0.0
+        for j in range(n):
+            if j == i:
+                continue
+            e = (mu / (m * K)) * math.cos(phi[j] - phi[i] - alpha) if member(N, R, i, j) else 0.0
+            diag -= e
+            assert abs(J[n + i, j] - e) < 1e-8
+            assert abs(J[i, j]) < 1e-12 and abs(J[i, n + j]) < 1e-12 and abs(J[n + i, n + j]) < 1e-12
+        assert abs(J[n + i, i] - diag) < 1e-8
+        assert abs(J[i, n + i] - 1.0) < 1e-9
+        assert abs(J[n + i, n + i] + eps / m) < 1e-8
+
+
+@pytest.mark.parametrize("topo,dims", [(oracle.BALL, 3), (oracle.DISK, 2)])
+def test_ball_disk_roll_equivariance(topo, dims):
+    N1, P = 7, 2
+    shape = (N1,) * dims
+    x = I.ks_phases(22, 0, N1 ** dims).reshape(shape)
+    v = I.uniform(22, 0, 5, N1 ** dims, -0.5, 0.5).reshape(shape)
+    p = [1.0, 0.05, 1.0, 0.45]
+    y1, _ = oracle.rk4(oracle.KSI, topo, N1, P, p, np.concatenate([x.ravel(), v.ravel()]), 20, 0.01)
+    for axis in range(dims):
+        y2, _ = oracle.rk4(oracle.KSI, topo, N1, P, p,
+                           np.concatenate([np.roll(x, 3, axis=axis).ravel(), np.roll(v, 3, axis=axis).ravel()]), 20, 0.01)
+        n = N1 ** dims
+        for part in (slice(0, n), slice(n, 2 * n)):
+            assert np.abs(np.roll(y1[part].reshape(shape), 3, axis=axis) - y2[part].reshape(shape)).max() < 1e-12
+
+
+def test_inertia_rk4_fourth_order():
+    N, R = 30, 6
+    p = [1.0, 0.05, 1.0, 0.45]
+    x = np.concatenate([I.ks_phases(23, 0, N), I.uniform(23, 0, 5, N, -1, 1)])
+    sols = [oracle.rk4(oracle.KSI, oracle.RING, N, R, p, x, int(round(2.0 / dt)), dt)[0] for dt in (0.04, 0.02, 0.01)]
+    e1, e2 = np.abs(sols[0] - sols[1]).max(), np.abs(sols[1] - sols[2]).max()
+    assert 12 < e1 / e2 < 20
