@@ -27,7 +27,8 @@ sys.path.insert(0, ROOT)
 
 from paper_2410_19075_gb300 import inputs as I  # noqa: E402
 
-MODEL_NAMES = {0: "Kuramoto-Sakaguchi", 1: "FitzHugh-Nagumo", 2: "Hodgkin-Huxley"}
+MODEL_NAMES = {0: "Kuramoto-Sakaguchi", 1: "FitzHugh-Nagumo", 2: "Hodgkin-Huxley", 3: "Kuramoto with inertia"}
+TOPO_NAMES = {1: "periodic cubic lattice", 2: "periodic 3D lattice, ball window", 3: "periodic 2D lattice, disk window"}
 
 # Algorithmic bytes per node-step (4 stages) of the fused ring stage kernel:
 # per stage it reads the node's own prefix entry (nq * 8), the two shifted window
@@ -43,6 +44,13 @@ RING_FLOPS = {0: 4 * (50 + 13) + 14, 1: 4 * 15 + 3 * 8 + 6, 2: 4 * (6 * 34 + 40)
 # node; FP64 flops as the Kuramoto ring.
 CUBE_BYTES = 544
 CUBE_FLOPS = RING_FLOPS[0]
+# Ball / disk lattices: per stage the x pass reads (sin, cos) and writes the row
+# prefixes (32 B per node); the gather reads each prefix once from HBM (16 B; the
+# chord reads re-hit L1/L2), the stage-input (sin, cos) (16 B), y, acc and the
+# local stage variables, and writes acc or y, the local variables and the next
+# (sin, cos).  Kuramoto with inertia (d = 2, one local variable): 120 + 2 * 144 +
+# 136 B per node-step; Kuramoto (d = 1): 96 + 2 * 104 + 104 B.
+LATTICE_BYTES = {0: 408, 3: 544}
 
 
 def parse():
@@ -309,6 +317,50 @@ def bench_small_ring(args, stream, flush, steps=200, reps=5):
             "us_per_step": 1e3 * ms / steps, "value": N * steps / (ms * 1e-3), "unit": "node-steps/s"}
 
 
+def bench_lattice(args, stream, flush, model, topo, N1, P, params, steps=100):
+    """One lattice workload: steps RK4 steps per timed iteration after 3 warm-up
+    steps, L2 flushed before the timed region."""
+    import torch
+    from paper_2410_19075_gb300 import Network
+    nodes = N1 ** 3 if topo in (1, 2) else N1 * N1
+    net = Network(model, topo, N1, P, params, stream=stream)
+    net.set_state(torch.from_numpy(I.initial_state(model, 2413, 0, nodes)).cuda())
+    net.step(3, args.dt)
+    net.step(steps, args.dt)
+    net.sync()
+    times = []
+    for _ in range(3):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        net.step(steps, args.dt)
+        b.record(stream)
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    y = net.get_state()
+    assert np.isfinite(y).all()
+    net.close()
+    ms = statistics.median(times)
+    links = {1: (2 * P + 1) ** 3 - 1}.get(topo)
+    if links is None:
+        r = range(-P, P + 1)
+        links = (sum(1 for a in r for b in r for c in r if a * a + b * b + c * c <= P * P) if topo == 2
+                 else sum(1 for a in r for b in r if a * a + b * b <= P * P)) - 1
+    per_byte = CUBE_BYTES if topo == 1 else LATTICE_BYTES[model]
+    return {"workload": f"{MODEL_NAMES[model]} {TOPO_NAMES[topo]}, N1={N1} ({nodes} nodes), P={P} "
+                        f"({links} links per node), params={list(map(float, params))}",
+            "steps": steps, "ms_per_step": ms / steps, "value": nodes * steps / (ms * 1e-3),
+            "unit": "node-steps/s", "links_per_s": nodes * links * steps / (ms * 1e-3),
+            "hbm_gbs_algorithmic": per_byte * nodes * steps / (ms * 1e-3) / 1e9}
+
+
+def bench_ball(args, stream, flush):
+    """The paper's performance-test network: 3D Kuramoto with inertia (m = 1,
+    eps = 0.05, mu = 0.01, alpha = 0.45), N1 = 100 (10^6 nodes), ball window of
+    radius P = 2, 4, 6."""
+    return [bench_lattice(args, stream, flush, 3, 2, 100, P, I.ksi_params(), steps=200) for P in (2, 4, 6)]
+
+
 def bench_cube(args, stream, flush, N1=464, P=92, steps=20):
     """Kuramoto periodic cubic lattice 464^3 (99.9 million nodes), P=92 box,
     alpha=1.52: separable exact box sums, steps RK4 steps per timed iteration."""
@@ -495,6 +547,7 @@ def run_native(args):
     if not args.no_extra and args.topo == 0 and world == 1:
         line["small_ring"] = bench_small_ring(args, stream, flush)
         line["cube"] = bench_cube(args, stream, flush)
+        line["ball3d_inertia"] = bench_ball(args, stream, flush)
     if not args.no_batched:
         line["batched"] = bench_batched(args, flush, stream)
     if not args.no_served:

@@ -16,8 +16,8 @@
  *     call.  The handle owns every device buffer it allocates and frees it in
  *     sim_destroy().
  *   - State layout: variable-major (SoA), FP64, little-endian.  Variable v of
- *     node i is at [v * nodes + i].  Ring: node i in [0, N).  Cube: node
- *     k*N1^2 + j*N1 + i (Section IV, 3D networks).
+ *     node i is at [v * nodes + i].  Ring: node i in [0, N).  Cube and ball:
+ *     node k*N1^2 + j*N1 + i; disk: node j*N1 + i (Section IV, 3D networks).
  *   - Work is issued asynchronously on the handle's CUDA stream (the stream
  *     given at creation; NULL means the legacy default stream).  Device errors
  *     from earlier asynchronous work surface at the next call that synchronises.
@@ -49,15 +49,27 @@ typedef struct sim_handle *sim_t;
  *         + g (mean_{j in W(i)} V_j - V_i).  4 variables.
  *         params = {Cm, gNa, gK, gL, ENa, EK, EL, g}; I_ext per node via
  *         sim_set_node_param (default 0).
- * K is the number of links of a node: 2R on the ring, (2P+1)^3 - 1 on the cube
- * (one more of each with SIM_FLAG_INCLUDE_SELF). */
-typedef enum { SIM_KS = 0, SIM_FHN = 1, SIM_HH = 2 } sim_model;
+ * SIM_KSI Kuramoto with inertia, Eq. (3) with m != 0 (Section IV.C, 3D chimeras):
+ *         m phi_i'' + eps phi_i' = (mu/K) sum_{j in W(i)} sin(phi_j - phi_i - alpha),
+ *         integrated as phi' = psi, psi' = ((mu/K) sum_j ... - eps psi) / m.
+ *         2 variables (phi, psi), stored phi block then psi block.
+ *         params = {m, eps, mu, alpha}; m must be non-zero.
+ * K is the number of links of a node: 2R on the ring, (2P+1)^3 - 1 on the cube,
+ * the lattice-point count of the ball or disk of radius P minus one (one more
+ * of each with SIM_FLAG_INCLUDE_SELF). */
+typedef enum { SIM_KS = 0, SIM_FHN = 1, SIM_HH = 2, SIM_KSI = 3 } sim_model;
 
 /* Topologies (Section IV).
  * SIM_RING    node i couples to i-R..i+R (mod N), R = radius, 2R+1 <= N.
- * SIM_CUBE3D  periodic N1^3 lattice (N = N1), node couples to the (2P+1)^3 box
- *             around it, P = radius, 2P+1 <= N1.  Kuramoto only. */
-typedef enum { SIM_RING = 0, SIM_CUBE3D = 1 } sim_topology;
+ * SIM_CUBE3D  periodic N1^3 lattice (N = N1, N1 <= 1024), node couples to the
+ *             (2P+1)^3 box around it, P = radius, 2P+1 <= N1.
+ * SIM_BALL3D  periodic N1^3 lattice (N1 <= 1024), node couples to every node at
+ *             offset (dx, dy, dz) with dx^2 + dy^2 + dz^2 <= P^2 (the nonlocal
+ *             3D coupling of Section IV.C), 2P+1 <= N1.
+ * SIM_DISK2D  periodic N1^2 lattice (N1 <= 8192), dx^2 + dy^2 <= P^2, 2P+1 <= N1.
+ * Lattice nodes are numbered k N1^2 + j N1 + i (x = i fastest).  The lattices
+ * take the Kuramoto models (SIM_KS, SIM_KSI) only. */
+typedef enum { SIM_RING = 0, SIM_CUBE3D = 1, SIM_BALL3D = 2, SIM_DISK2D = 3 } sim_topology;
 
 typedef enum {
     SIM_OK = 0,
@@ -95,7 +107,7 @@ int sim_create(sim_t *out, int model, int topology, int64_t N, int64_t radius,
 int sim_create_in(sim_t *out, int model, int topology, int64_t N, int64_t radius, const double *params,
                   int n_params, unsigned flags, void *dev_workspace, size_t workspace_bytes, void *stream);
 
-/* Number of nodes (N or N1^3) and of state variables per node. */
+/* Number of nodes (N, N1^3 or N1^2) and of state variables per node. */
 int64_t sim_nodes(sim_t h);
 int sim_dim(sim_t h);
 
@@ -135,7 +147,8 @@ int sim_rhs(sim_t h, double *host_k, int64_t n_values);
 /* Kuramoto order parameter |mean_j exp(i phi_j)| at t = 0 and after every step
  * since the last call (synchronises).  Writes at most max_values values to
  * host_R and their count to *n_written.  Values not yet read are kept for the
- * most recent 65536 steps; older ones are dropped.  Other models write 0 values. */
+ * most recent 65536 steps; older ones are dropped.  Recorded for SIM_KS and
+ * SIM_KSI (phases = variable 0); other models write 0 values. */
 int sim_observables(sim_t h, double *host_R, int64_t max_values, int64_t *n_written);
 
 /* Wait for all work issued on the handle's stream and report device errors. */
@@ -149,7 +162,7 @@ int64_t sim_steps_done(sim_t h);
  * number of small unconnected subnets within a single run", Section III.C, and
  * its parameter and multistability studies, Section IV).  Ring members of the
  * same model are stepped by one launch per RK4 stage whose CTAs are
- * (member, 256-node sub-tile) work items; cube members by their own kernels.
+ * (member, 256-node sub-tile) work items; lattice members by their own kernels.
  * Every member keeps its own state, prefix buffers and observables, so results
  * are bit-for-bit those of sim_step on each member alone.
  */

@@ -68,28 +68,33 @@ cudaError_t ring_rhs(const RingPlan &p, cudaStream_t s);
 // Ring: one RK4 step, 4 fused stage kernels.
 cudaError_t ring_step(const RingPlan &p, double dt, cudaStream_t s);
 
-// Device buffers of one periodic cubic lattice (Kuramoto only).
-struct CubePlan {
-    int64_t N1, P;
-    int F;            // fixed-point grid of the box sums
+// Device buffers of one periodic lattice (cube, ball or disk; Kuramoto models 0
+// and 3).  topo: 1 cube, 2 ball, 3 disk.
+struct LatticePlan {
+    int model, topo, dims;
+    int64_t N1, P, nodes;
+    int F;            // fixed-point grid of the window sums
     ModelParams mp;
-    double *y, *acc;  // N1^3
-    double *f;        // 2 * N1^3: sin, cos of the current stage input
-    int64_t *sx;      // 2 * N1^3: window sums along x
-    int64_t *sxy;     // 2 * N1^3: box sums over x and y
+    double *y, *acc;  // D * nodes
+    double *f;        // 2 * nodes: sin, cos of the current stage-input phase
+    double *xs;       // NX * nodes: local stage-input variables (psi of model 3)
+    int64_t *sx;      // 2 * nodes: cube window sums along x, or row prefixes (ball, disk)
+    int64_t *sxy;     // 2 * nodes: cube box sums over x and y
     i128 *partial;    // per-CTA partial sums of the order parameter
     unsigned long long *done_ctr;
     unsigned *err;
     double *obs;
     int64_t obs_cap;
     unsigned long long *obs_ctr;
-    int zgrid;        // CTAs of the z pass
+    const int4 *chords; // ball/disk: (dy, dz, w, 0) chords of the window
+    int nchords;
 };
 
-cudaError_t cube_configure(); // once per process, before the first launch
-cudaError_t cube_prologue(const CubePlan &p, cudaStream_t s);
-cudaError_t cube_step(const CubePlan &p, double dt, cudaStream_t s);
-cudaError_t cube_rhs(const CubePlan &p, cudaStream_t s); // acc <- f(y)
+cudaError_t lattice_configure(); // once per process, before the first launch
+int64_t lattice_order_blocks(int topo, int64_t N1); // CTAs of the order-parameter passes
+cudaError_t lattice_prologue(const LatticePlan &p, cudaStream_t s);
+cudaError_t lattice_step(const LatticePlan &p, double dt, cudaStream_t s);
+cudaError_t lattice_rhs(const LatticePlan &p, cudaStream_t s); // acc <- f(y)
 
 // Host-side values of the fast-math tables (long double, rounded to double).
 void fill_math_tables(double *sincos /* 2 * kSinTab */, double *exp2j /* kExpTab */);

@@ -1,0 +1,428 @@
+// Periodic lattices of Kuramoto nodes (with or without inertia), Section IV:
+//   cube  N1^3 nodes, index k N1^2 + j N1 + i, the (2P+1)^3 box around a node;
+//   ball  N1^3 nodes, the sphere dx^2 + dy^2 + dz^2 <= P^2 (3D networks);
+//   disk  N1^2 nodes, index j N1 + i, the circle dx^2 + dy^2 <= P^2 (2D networks).
+// f = (sin, cos) of the stage-input phase, rounded onto the grid 2^-F (F chosen
+// so that a full window sum fits in int64), so every window sum is exact.
+//
+// Cube, per RK4 stage (the box is separable):
+//   x pass  SX(i,j,k)  = sum_{|dx|<=P} Q(f(i+dx,j,k))      (row prefix in shared memory)
+//   y pass  SXY(i,j,k) = sum_{|dy|<=P} SX(i,j+dy,k)        (sliding window along j)
+//   z pass  W(i,j,k)   = sum_{|dz|<=P} SXY(i,j,k+dz)       (sliding window along k)
+//           fused with the right-hand side, the RK4 update and the next (sin, cos).
+// Ball and disk, per RK4 stage:
+//   x pass  the inclusive prefix of Q(f) along every row (wrapping int64);
+//   gather  W = sum over the chords of the window, one per (dy, dz) (ball) or dy
+//           (disk): the row segment |dx| <= w = floor(sqrt(P^2 - dy^2 - dz^2)),
+//           each read as a difference of two row prefixes (O(P^2) resp. O(P)
+//           reads per node), fused with the right-hand side and RK4 update.
+#include "internal.h"
+
+namespace simk {
+
+constexpr int kRowWarpsMax = 8;       // x pass: one warp per row
+constexpr int kColThreads = 128;      // cube y and z passes: threads per CTA along i
+constexpr int kGatherThreads = 256;   // ball/disk gather: one node per thread
+constexpr size_t kRowSmemMax = 220 * 1024;
+
+static int row_warps(int64_t N1)
+{
+    const size_t per_warp = 2 * (size_t)(N1 + 1) * sizeof(int64_t);
+    int w = (int)(kRowSmemMax / per_warp);
+    return w < 1 ? 1 : (w > kRowWarpsMax ? kRowWarpsMax : w);
+}
+
+// x pass: one warp per row.  pre(p) = sum_{m<p} Q(f(m)) for p in [0, N1] is built
+// in shared memory (stride N1 + 1 per component).  PREFIX = false (cube) writes
+// the window sums SX(i) = Pe(i+P+1) - Pe(i-P) on the periodic extension
+// Pe(p) = pre(p mod N1) + floor(p / N1) pre(N1); PREFIX = true (ball, disk) writes
+// the inclusive prefix pre(i+1), modulo 2^64.
+template <bool PREFIX>
+__global__ void __launch_bounds__(32 * kRowWarpsMax) lattice_x_kernel(LatticePlan p)
+{
+    extern __shared__ int64_t smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    const int64_t N1 = p.N1, P = p.P, nodes = p.nodes, stride = N1 + 1, rows = nodes / N1;
+    int64_t *pre0 = smem + (int64_t)warp * 2 * stride;
+    int64_t *pre1 = pre0 + stride;
+    const int per = (int)((N1 + 31) / 32);
+    bool ok = true;
+    for (int64_t row = (int64_t)blockIdx.x * nwarps + warp; row < rows; row += (int64_t)gridDim.x * nwarps) {
+        const double *__restrict__ fs = p.f + row * N1;
+        const double *__restrict__ fc = p.f + nodes + row * N1;
+        for (int64_t mb = lane; mb < N1; mb += 32 * 8) { // coalesced, 8 loads in flight per lane
+            double vs[8], vc[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int64_t m = mb + 32 * u;
+                vs[u] = m < N1 ? __ldg(fs + m) : 0.0;
+                vc[u] = m < N1 ? __ldg(fc + m) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int64_t m = mb + 32 * u;
+                if (m < N1) {
+                    pre0[m + 1] = to_fixed(vs[u], p.F, 1, ok);
+                    pre1[m + 1] = to_fixed(vc[u], p.F, 1, ok);
+                }
+            }
+        }
+        __syncwarp();
+        const int m0 = lane * per;
+        uint64_t r0 = 0, r1 = 0; // wrapping sums
+        for (int t = 0; t < per; ++t) {
+            const int m = m0 + t;
+            if (m < N1) {
+                r0 += (uint64_t)pre0[m + 1];
+                r1 += (uint64_t)pre1[m + 1];
+                pre0[m + 1] = (int64_t)r0;
+                pre1[m + 1] = (int64_t)r1;
+            }
+        }
+        const uint64_t e0 = (uint64_t)warp_incl_scan((int64_t)r0) - r0;
+        const uint64_t e1 = (uint64_t)warp_incl_scan((int64_t)r1) - r1;
+        for (int t = 0; t < per; ++t) {
+            const int m = m0 + t;
+            if (m < N1) {
+                pre0[m + 1] = (int64_t)((uint64_t)pre0[m + 1] + e0);
+                pre1[m + 1] = (int64_t)((uint64_t)pre1[m + 1] + e1);
+            }
+        }
+        if (lane == 0) {
+            pre0[0] = 0;
+            pre1[0] = 0;
+        }
+        __syncwarp();
+        int64_t *__restrict__ o0 = p.sx + row * N1;
+        int64_t *__restrict__ o1 = p.sx + nodes + row * N1;
+        if (PREFIX) {
+            for (int64_t i = lane; i < N1; i += 32) {
+                o0[i] = pre0[i + 1];
+                o1[i] = pre1[i + 1];
+            }
+        } else {
+            const int64_t t0 = pre0[N1], t1 = pre1[N1];
+            for (int64_t i = lane; i < N1; i += 32) {
+                int64_t b = i + P + 1, a = i - P;
+                int64_t s0 = 0, s1 = 0;
+                if (b > N1) { b -= N1; s0 += t0; s1 += t1; }
+                if (a < 0) { a += N1; s0 += t0; s1 += t1; } // Pe(a) = pre(a+N1) - total
+                o0[i] = s0 + pre0[b] - pre0[a];
+                o1[i] = s1 + pre1[b] - pre1[a];
+            }
+        }
+        __syncwarp();
+    }
+    if (!ok) raise_error(p.err, ERR_RANGE);
+}
+
+// cube y pass: one thread per (i, k) column, sliding window along j (exact int64),
+// 8 rows of window loads issued together.
+__global__ void __launch_bounds__(kColThreads) cube_y_kernel(LatticePlan p)
+{
+    constexpr int U = 8;
+    const int64_t N1 = p.N1, P = p.P, nodes = p.nodes;
+    const int64_t i = (int64_t)blockIdx.x * kColThreads + threadIdx.x;
+    const int64_t k = blockIdx.y;
+    if (i >= N1) return;
+    const int64_t col = k * N1 * N1 + i; // + j * N1
+    const int64_t *__restrict__ a0 = p.sx + col;
+    const int64_t *__restrict__ a1 = p.sx + nodes + col;
+    int64_t *__restrict__ o0 = p.sxy + col;
+    int64_t *__restrict__ o1 = p.sxy + nodes + col;
+    int64_t s0 = 0, s1 = 0;
+    for (int64_t d = -P; d <= P; ++d) {
+        const int64_t j = d < 0 ? d + N1 : d;
+        s0 += __ldg(a0 + j * N1);
+        s1 += __ldg(a1 + j * N1);
+    }
+    for (int64_t j0 = 0; j0 < N1; j0 += U) {
+        int64_t in0[U], out0[U], in1[U], out1[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t j = j0 + u;
+            int64_t jin = j + P + 1, jout = j - P;
+            if (jin >= N1) jin -= N1;
+            if (jout < 0) jout += N1;
+            const bool live = j < N1;
+            in0[u] = live ? __ldg(a0 + jin * N1) : 0;
+            out0[u] = live ? __ldg(a0 + jout * N1) : 0;
+            in1[u] = live ? __ldg(a1 + jin * N1) : 0;
+            out1[u] = live ? __ldg(a1 + jout * N1) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t j = j0 + u;
+            if (j < N1) {
+                o0[j * N1] = s0;
+                o1[j * N1] = s1;
+            }
+            s0 += in0[u] - out0[u];
+            s1 += in1[u] - out1[u];
+        }
+    }
+}
+
+// Deterministic order parameter of the new state: per-CTA partial sums of the
+// fixed-point (sin, cos), and the last CTA to finish sums every partial in index
+// order and records R.
+__device__ void lattice_record_order(const LatticePlan &p, int64_t ps, int64_t pc)
+{
+    __shared__ int64_t s_s[256], s_c[256];
+    __shared__ bool s_last;
+    s_s[threadIdx.x] = ps;
+    s_c[threadIdx.x] = pc;
+    __syncthreads();
+    const unsigned nblk = gridDim.x * gridDim.y;
+    const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x;
+    if (threadIdx.x == 0) {
+        i128 ts = 0, tc = 0;
+        for (unsigned t = 0; t < blockDim.x; ++t) {
+            ts += s_s[t];
+            tc += s_c[t];
+        }
+        p.partial[2 * bid] = ts;
+        p.partial[2 * bid + 1] = tc;
+        __threadfence();
+        s_last = last_arrival(p.done_ctr, nblk);
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+        i128 ts = 0, tc = 0;
+        for (unsigned b = 0; b < nblk; ++b) {
+            ts += ld_cg_i128(p.partial + 2 * b);
+            tc += ld_cg_i128(p.partial + 2 * b + 1);
+        }
+        const double S = fixed_to_double(ts, p.F), C = fixed_to_double(tc, p.F);
+        const unsigned long long n = *p.obs_ctr;
+        p.obs[n % (unsigned long long)p.obs_cap] = sqrt(S * S + C * C) / (double)p.nodes;
+        *p.obs_ctr = n + 1;
+    }
+}
+
+// One node's RK4 stage: right-hand side from the window sums (W0, W1) and its own
+// stage input, the RK4 update, the next stage input's local variables and (sin,
+// cos).  STAGE 0 (prologue) only computes (sin, cos) of y.
+template <int M, int STAGE>
+__device__ __forceinline__ void lattice_node(const LatticePlan &p, int64_t n, int64_t W0, int64_t W1, double dt,
+                                             bool &ok, int64_t &ps, int64_t &pc)
+{
+    constexpr int D = Model<M>::D, NX = Model<M>::NX, XOFF = D - NX;
+    const int64_t nodes = p.nodes;
+    double xn[D];
+    if (STAGE == 0) {
+#pragma unroll
+        for (int v = 0; v < D; ++v) xn[v] = p.y[v * nodes + n];
+    } else {
+        const double fo[2] = {p.f[n], p.f[nodes + n]};
+        const int64_t qo[2] = {to_fixed(fo[0], p.F, 1, ok), to_fixed(fo[1], p.F, 1, ok)};
+        const i128 W[2] = {(i128)W0, (i128)W1};
+        double X[NX > 0 ? NX : 1];
+#pragma unroll
+        for (int g = 0; g < NX; ++g) X[g] = STAGE == 1 ? p.y[(XOFF + g) * nodes + n] : p.xs[g * nodes + n];
+        double k[D];
+        Model<M>::rhs(p.mp, p.F, fo, qo, W, X, 0.0, k);
+#pragma unroll
+        for (int v = 0; v < D; ++v) {
+            const double yv = p.y[v * nodes + n];
+            if (STAGE == 1) {
+                p.acc[v * nodes + n] = k[v];
+                xn[v] = yv + (0.5 * dt) * k[v];
+            } else if (STAGE == 2) {
+                p.acc[v * nodes + n] = p.acc[v * nodes + n] + 2.0 * k[v];
+                xn[v] = yv + (0.5 * dt) * k[v];
+            } else if (STAGE == 3) {
+                p.acc[v * nodes + n] = p.acc[v * nodes + n] + 2.0 * k[v];
+                xn[v] = yv + dt * k[v];
+            } else {
+                xn[v] = yv + (dt / 6.0) * (p.acc[v * nodes + n] + k[v]);
+                p.y[v * nodes + n] = xn[v];
+            }
+        }
+        if (NX > 0 && STAGE <= 3) {
+#pragma unroll
+            for (int g = 0; g < NX; ++g) p.xs[g * nodes + n] = xn[XOFF + g];
+        }
+    }
+    double sn, cn;
+    fast_sincos(xn[0], p.mp.tab, sn, cn);
+    p.f[n] = sn;
+    p.f[nodes + n] = cn;
+    if (STAGE == 0 || STAGE == 4) {
+        ps += to_fixed(sn, p.F, 1, ok);
+        pc += to_fixed(cn, p.F, 1, ok);
+    }
+}
+
+// cube z pass: one thread per (i, j) column, sliding window along k, fused with
+// the node update.  Also the prologue of every lattice (STAGE 0, no window).
+template <int M, int STAGE>
+__global__ void __launch_bounds__(kColThreads) cube_z_kernel(LatticePlan p, double dt)
+{
+    const int64_t N1 = p.N1, P = p.P, nodes = p.nodes, plane = N1 * N1;
+    const int64_t i = (int64_t)blockIdx.x * kColThreads + threadIdx.x;
+    const int64_t j = blockIdx.y;
+    int64_t ps = 0, pc = 0;
+    bool ok = true;
+    if (i < N1) {
+        const int64_t col = j * N1 + i; // + k * plane
+        const int64_t *__restrict__ a0 = p.sxy + col;
+        const int64_t *__restrict__ a1 = p.sxy + nodes + col;
+        int64_t s0 = 0, s1 = 0;
+        if (STAGE > 0) {
+            for (int64_t d = -P; d <= P; ++d) {
+                const int64_t k = d < 0 ? d + N1 : d;
+                s0 += __ldg(a0 + k * plane);
+                s1 += __ldg(a1 + k * plane);
+            }
+        }
+        for (int64_t k = 0; k < N1; ++k) {
+            lattice_node<M, STAGE>(p, col + k * plane, s0, s1, dt, ok, ps, pc);
+            if (STAGE > 0) {
+                int64_t kin = k + P + 1, kout = k - P;
+                if (kin >= N1) kin -= N1;
+                if (kout < 0) kout += N1;
+                s0 += __ldg(a0 + kin * plane) - __ldg(a0 + kout * plane);
+                s1 += __ldg(a1 + kin * plane) - __ldg(a1 + kout * plane);
+            }
+        }
+    }
+    if (!ok) raise_error(p.err, ERR_RANGE);
+    if (STAGE == 0 || STAGE == 4) lattice_record_order(p, ps, pc);
+}
+
+// Sum of Q(f) over the row segment [a, b] (b - a < N1, a > -N1, b < 2 N1) from the
+// row's inclusive prefix I (wrapping arithmetic; the segment sum itself is exact).
+__device__ __forceinline__ uint64_t chord_sum(const int64_t *__restrict__ I, int64_t N1, int64_t a, int64_t b)
+{
+    const uint64_t tot = (uint64_t)__ldg(I + N1 - 1);
+    if (a < 0) return tot - (uint64_t)__ldg(I + a + N1 - 1) + (uint64_t)__ldg(I + b);
+    if (b >= N1) return tot - (a ? (uint64_t)__ldg(I + a - 1) : 0ull) + (uint64_t)__ldg(I + b - N1);
+    return (uint64_t)__ldg(I + b) - (a ? (uint64_t)__ldg(I + a - 1) : 0ull);
+}
+
+// ball / disk gather: one node per thread; the window is the union of the chords
+// (dy, dz, w) of the plan's table.
+template <int M, int STAGE>
+__global__ void __launch_bounds__(kGatherThreads) lattice_gather_kernel(LatticePlan p, double dt)
+{
+    const int64_t N1 = p.N1, nodes = p.nodes;
+    const int64_t n = (int64_t)blockIdx.x * kGatherThreads + threadIdx.x;
+    int64_t ps = 0, pc = 0;
+    bool ok = true;
+    if (n < nodes) {
+        const int64_t i = n % N1, j = (n / N1) % N1, k = p.dims == 3 ? n / (N1 * N1) : 0;
+        uint64_t w0 = 0, w1 = 0;
+        if (STAGE > 0) {
+            for (int c = 0; c < p.nchords; ++c) {
+                const int4 ch = __ldg(p.chords + c); // (dy, dz, w, 0)
+                int64_t jj = j + ch.x, kk = k + ch.y;
+                if (jj < 0) jj += N1; else if (jj >= N1) jj -= N1;
+                if (kk < 0) kk += N1; else if (kk >= N1) kk -= N1;
+                const int64_t row = (kk * N1 + jj) * N1;
+                w0 += chord_sum(p.sx + row, N1, i - ch.z, i + ch.z);
+                w1 += chord_sum(p.sx + nodes + row, N1, i - ch.z, i + ch.z);
+            }
+        }
+        lattice_node<M, STAGE>(p, n, (int64_t)w0, (int64_t)w1, dt, ok, ps, pc);
+    }
+    if (!ok) raise_error(p.err, ERR_RANGE);
+    if (STAGE == 0 || STAGE == 4) lattice_record_order(p, ps, pc);
+}
+
+// ---------------------------------------------------------------------------
+static dim3 col_grid(int64_t N1)
+{
+    return dim3((unsigned)((N1 + kColThreads - 1) / kColThreads), (unsigned)N1);
+}
+
+static unsigned gather_grid(const LatticePlan &p)
+{
+    return (unsigned)((p.nodes + kGatherThreads - 1) / kGatherThreads);
+}
+
+int64_t lattice_order_blocks(int topo, int64_t N1)
+{
+    if (topo == 1) return ((N1 + kColThreads - 1) / kColThreads) * N1;
+    const int64_t nodes = topo == 3 ? N1 * N1 : N1 * N1 * N1;
+    return (nodes + kGatherThreads - 1) / kGatherThreads;
+}
+
+cudaError_t lattice_configure()
+{
+    cudaError_t e = cudaFuncSetAttribute(lattice_x_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kRowSmemMax);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(lattice_x_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kRowSmemMax);
+    return e;
+}
+
+static cudaError_t launch_x(const LatticePlan &p, cudaStream_t s)
+{
+    const int w = row_warps(p.N1);
+    const size_t smem = (size_t)w * 2 * (size_t)(p.N1 + 1) * sizeof(int64_t);
+    const int64_t rows = p.nodes / p.N1;
+    const int64_t want = (rows + w - 1) / w;
+    const unsigned grid = (unsigned)(want < 152 * 16 ? want : 152 * 16);
+    if (p.topo == 1) lattice_x_kernel<false><<<grid, 32 * w, smem, s>>>(p);
+    else lattice_x_kernel<true><<<grid, 32 * w, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <int M, int STAGE>
+static cudaError_t launch_node_pass(const LatticePlan &p, double dt, cudaStream_t s)
+{
+    if (p.topo == 1) cube_z_kernel<M, STAGE><<<col_grid(p.N1), kColThreads, 0, s>>>(p, dt);
+    else lattice_gather_kernel<M, STAGE><<<gather_grid(p), kGatherThreads, 0, s>>>(p, dt);
+    return cudaGetLastError();
+}
+
+template <int M>
+static cudaError_t launch_stage(int stage, const LatticePlan &p, double dt, cudaStream_t s)
+{
+    if (stage == 0) {
+        // prologue: (sin, cos) of y and its order parameter, no window
+        return p.topo == 1 ? (cube_z_kernel<M, 0><<<col_grid(p.N1), kColThreads, 0, s>>>(p, 0.0), cudaGetLastError())
+                           : (lattice_gather_kernel<M, 0><<<gather_grid(p), kGatherThreads, 0, s>>>(p, 0.0),
+                              cudaGetLastError());
+    }
+    cudaError_t e = launch_x(p, s);
+    if (e != cudaSuccess) return e;
+    if (p.topo == 1) {
+        cube_y_kernel<<<col_grid(p.N1), kColThreads, 0, s>>>(p);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    switch (stage) {
+    case 1: return launch_node_pass<M, 1>(p, dt, s);
+    case 2: return launch_node_pass<M, 2>(p, dt, s);
+    case 3: return launch_node_pass<M, 3>(p, dt, s);
+    default: return launch_node_pass<M, 4>(p, dt, s);
+    }
+}
+
+static cudaError_t launch_any(int stage, const LatticePlan &p, double dt, cudaStream_t s)
+{
+    return p.model == 3 ? launch_stage<3>(stage, p, dt, s) : launch_stage<0>(stage, p, dt, s);
+}
+
+cudaError_t lattice_prologue(const LatticePlan &p, cudaStream_t s)
+{
+    return launch_any(0, p, 0.0, s);
+}
+
+cudaError_t lattice_rhs(const LatticePlan &p, cudaStream_t s)
+{
+    return launch_any(1, p, 0.0, s);
+}
+
+cudaError_t lattice_step(const LatticePlan &p, double dt, cudaStream_t s)
+{
+    for (int stage = 1; stage <= 4; ++stage) {
+        const cudaError_t e = launch_any(stage, p, dt, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+} // namespace simk

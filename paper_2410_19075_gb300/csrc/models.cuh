@@ -111,4 +111,30 @@ template <> struct Model<2> {
     }
 };
 
+// Kuramoto-Sakaguchi with inertia, Eq. (3) with m != 0, as a first-order system:
+//   dphi/dt = psi,   dpsi/dt = ((mu/K) sum_{j in W(i)} sin(phi_j - phi_i - alpha) - eps psi) / m
+// with sum_j sin(phi_j - phi_i - alpha) = cos(phi_i+alpha) S_sin - sin(phi_i+alpha) S_cos.
+// c = {mu/(m K), eps/m, sin alpha, cos alpha}.  Coupled quantity (sin phi, cos phi);
+// psi is a local variable.
+template <> struct Model<3> {
+    static constexpr int D = 2, NQ = 2, NX = 1, F = 53;
+    __device__ __forceinline__ static void coupled(const ModelParams &P, const double (&x)[D], double (&f)[NQ])
+    {
+        fast_sincos(x[0], P.tab, f[0], f[1]);
+    }
+    __device__ __forceinline__ static void rhs(const ModelParams &P, int F_, const double (&fo)[NQ],
+                                               const int64_t (&qo)[NQ], const i128 (&W)[NQ],
+                                               const double *X, double, double (&k)[D])
+    {
+        const i128 ss = P.include_self ? W[0] : W[0] - (i128)qo[0];
+        const i128 sc = P.include_self ? W[1] : W[1] - (i128)qo[1];
+        const double Ss = fixed_to_double_wide(ss, F_), Sc = fixed_to_double_wide(sc, F_);
+        const double s = fo[0], c = fo[1], psi = X[0];
+        const double sxa = s * P.c[3] + c * P.c[2]; // sin(phi + alpha)
+        const double cxa = c * P.c[3] - s * P.c[2]; // cos(phi + alpha)
+        k[0] = psi;
+        k[1] = fma(P.c[0], cxa * Ss - sxa * Sc, -P.c[1] * psi);
+    }
+};
+
 } // namespace simk

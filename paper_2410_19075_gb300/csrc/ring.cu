@@ -250,7 +250,7 @@ __device__ __forceinline__ void ring_stage_body(const RingPlan &P, const RingSta
 #pragma unroll
     for (int c = 0; c < NQ; ++c)
         total[c] = block_exclusive_scan<8>(P.grptot + c * ngroups, a.grpofs_out + c * (ngroups + 1), ngroups);
-    if (M == 0 && (STAGE == 0 || STAGE == 4) && tid == 0) {
+    if ((M == 0 || M == 3) && (STAGE == 0 || STAGE == 4) && tid == 0) {
         const double S = fixed_to_double(total[0], P.F);
         const double C = fixed_to_double(total[NQ - 1], P.F);
         const unsigned long long n = *P.obs_ctr;
@@ -301,7 +301,8 @@ static cudaError_t launch_any(int stage, const RingPlan &p, double dt, cudaStrea
     switch (p.model) {
     case 0: return launch_stage<0>(stage, p, dt, s);
     case 1: return launch_stage<1>(stage, p, dt, s);
-    default: return launch_stage<2>(stage, p, dt, s);
+    case 2: return launch_stage<2>(stage, p, dt, s);
+    default: return launch_stage<3>(stage, p, dt, s);
     }
 }
 
@@ -326,7 +327,8 @@ cudaError_t ring_batch_step(const RingBatchGroup &g, double dt, cudaStream_t s)
         switch (g.model) {
         case 0: e = launch_batch_stage<0>(stage, g, dt, s); break;
         case 1: e = launch_batch_stage<1>(stage, g, dt, s); break;
-        default: e = launch_batch_stage<2>(stage, g, dt, s); break;
+        case 2: e = launch_batch_stage<2>(stage, g, dt, s); break;
+        default: e = launch_batch_stage<3>(stage, g, dt, s); break;
         }
         if (e != cudaSuccess) return e;
     }

@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
         return v;
     };
     auto record_order = [&]() {
-        if (M == 0 && rank == 0 && tid == 0) {
+        if ((M == 0 || M == 3) && rank == 0 && tid == 0) {
             const double S = fixed_to_double(bofs[nb], P.F);
             const double C = fixed_to_double(bofs[(NQ - 1) * (nb + 1) + nb], P.F);
             const unsigned long long n = *P.obs_ctr;
@@ -274,6 +274,7 @@ cudaError_t ring_cluster_configure()
     cudaError_t e = configure_one<0>(kClusterMaxNodes);
     if (e == cudaSuccess) e = configure_one<1>(kClusterMaxNodes);
     if (e == cudaSuccess) e = configure_one<2>(kClusterMaxNodes);
+    if (e == cudaSuccess) e = configure_one<3>(kClusterMaxNodes);
     if (e != cudaSuccess) return e;
     // largest cluster the device can co-schedule with the largest shared-memory use
     cudaLaunchConfig_t cfg = {};
@@ -320,7 +321,8 @@ cudaError_t ring_cluster_steps(const RingPlan &p, double dt, int64_t n_steps, cu
     switch (p.model) {
     case 0: return launch_cluster<0>(p, dt, n_steps, cl, s);
     case 1: return launch_cluster<1>(p, dt, n_steps, cl, s);
-    default: return launch_cluster<2>(p, dt, n_steps, cl, s);
+    case 2: return launch_cluster<2>(p, dt, n_steps, cl, s);
+    default: return launch_cluster<3>(p, dt, n_steps, cl, s);
     }
 }
 

@@ -137,8 +137,11 @@ struct srv_handle {
 
 namespace {
 
-int64_t nodes_of(const Job &j) { return j.topo == SIM_CUBE3D ? j.N * j.N * j.N : j.N; }
-int dim_of(int model) { return model == SIM_KS ? 1 : model == SIM_FHN ? 2 : 4; }
+int64_t nodes_of(const Job &j)
+{
+    return j.topo == SIM_RING ? j.N : j.topo == SIM_DISK2D ? j.N * j.N : j.N * j.N * j.N;
+}
+int dim_of(int model) { return model == SIM_KS ? 1 : model == SIM_HH ? 4 : 2; }
 
 void destroy_batches(srv_t s)
 {
@@ -172,7 +175,7 @@ void retire(srv_t s, Job *j)
 {
     j->result.resize((size_t)dim_of(j->model) * nodes_of(*j));
     int st = sim_get_state(j->h, j->result.data(), (int64_t)j->result.size());
-    if (st == SIM_OK && j->model == SIM_KS) {
+    if (st == SIM_OK && (j->model == SIM_KS || j->model == SIM_KSI)) {
         j->order.resize((size_t)j->steps + 1);
         int64_t n = 0;
         st = sim_observables(j->h, j->order.data(), (int64_t)j->order.size(), &n);
@@ -273,7 +276,7 @@ void worker_loop(srv_t s)
             // the shortest cube horizon
             int64_t n = s->chunk;
             for (Job *j : s->resident)
-                if (j->topo == SIM_CUBE3D && j->left < n) n = j->left;
+                if (j->topo != SIM_RING && j->left < n) n = j->left;
             for (auto &kv : s->batches) {
                 int st = sim_batch_step(kv.second, n, kv.first);
                 if (st == SIM_OK) st = sim_batch_sync(kv.second);
@@ -360,7 +363,7 @@ int srv_submit(srv_t s, int model, int topology, int64_t N, int64_t radius, cons
     j->steps = n_steps;
     j->dt = dt;
     j->params.assign(params, params + n_params);
-    const int64_t n = dim_of(model) * (topology == SIM_CUBE3D ? N * N * N : N);
+    const int64_t n = dim_of(model) * (topology == SIM_RING ? N : topology == SIM_DISK2D ? N * N : N * N * N);
     j->init.assign(host_init_state, host_init_state + n);
     if (host_node_param && model == SIM_HH) j->npar.assign(host_node_param, host_node_param + N);
     j->bytes = bytes;

@@ -33,11 +33,50 @@ constexpr int kGraphChunk = 16; // RK4 steps per captured graph
 
 size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
 
-int model_dim(int m) { return m == SIM_KS ? 1 : m == SIM_FHN ? 2 : m == SIM_HH ? 4 : 0; }
+int model_dim(int m) { return m == SIM_KS ? 1 : m == SIM_FHN ? 2 : m == SIM_HH ? 4 : m == SIM_KSI ? 2 : 0; }
 int model_nq(int m) { return m == SIM_HH ? 1 : 2; }
-int model_nx(int m) { return m == SIM_HH ? 3 : 0; }
-int model_nparams(int m) { return m == SIM_KS ? 3 : m == SIM_FHN ? 4 : m == SIM_HH ? 8 : -1; }
-int ring_F(int m) { return m == SIM_KS ? Model<0>::F : m == SIM_FHN ? Model<1>::F : Model<2>::F; }
+int model_nx(int m) { return m == SIM_HH ? 3 : m == SIM_KSI ? 1 : 0; }
+int model_nparams(int m) { return m == SIM_KS ? 3 : m == SIM_FHN ? 4 : m == SIM_HH ? 8 : m == SIM_KSI ? 4 : -1; }
+int ring_F(int m)
+{
+    return m == SIM_KS ? Model<0>::F : m == SIM_FHN ? Model<1>::F : m == SIM_HH ? Model<2>::F : Model<3>::F;
+}
+bool is_lattice(int topo) { return topo == SIM_CUBE3D || topo == SIM_BALL3D || topo == SIM_DISK2D; }
+int64_t nodes_of(int topo, int64_t N)
+{
+    return topo == SIM_RING ? N : topo == SIM_DISK2D ? N * N : N * N * N;
+}
+
+// Chords (dy, dz, w) of a ball (dims 3) or disk (dims 2) window of radius P:
+// for every (dy, dz) with dy^2 + dz^2 <= P^2, the row segment |dx| <= w with
+// w = floor(sqrt(P^2 - dy^2 - dz^2)).  Also returns the window size.
+std::vector<int4> chords_of(int topo, int64_t P, int64_t *count)
+{
+    std::vector<int4> out;
+    int64_t c = 0;
+    const int64_t zr = topo == SIM_BALL3D ? P : 0;
+    for (int64_t dz = -zr; dz <= zr; ++dz)
+        for (int64_t dy = -P; dy <= P; ++dy) {
+            const int64_t r2 = P * P - dy * dy - dz * dz;
+            if (r2 < 0) continue;
+            int64_t w = (int64_t)std::sqrt((double)r2);
+            while ((w + 1) * (w + 1) <= r2) ++w;
+            while (w * w > r2) --w;
+            out.push_back(make_int4((int)dy, (int)dz, (int)w, 0));
+            c += 2 * w + 1;
+        }
+    *count = c;
+    return out;
+}
+
+int64_t window_of(int topo, int64_t R)
+{
+    if (topo == SIM_RING) return 2 * R + 1;
+    if (topo == SIM_CUBE3D) return (2 * R + 1) * (2 * R + 1) * (2 * R + 1);
+    int64_t c = 0;
+    chords_of(topo, R, &c);
+    return c;
+}
 
 int ceil_log2(uint64_t x)
 {
@@ -50,7 +89,7 @@ int ceil_log2(uint64_t x)
 struct Layout {
     size_t total = 0;
     size_t y, acc, xg0, xg1, npar, lam0, lam1, ingrp0, ingrp1, grpofs0, grpofs1, subtot, grptot, grpctr;
-    size_t f, sx, sxy, partial, ctrs, obs, tabs;
+    size_t f, xs, sx, sxy, partial, chords, ctrs, obs, tabs;
 };
 
 Layout layout_of(int model, int topo, int64_t N, int64_t R)
@@ -81,14 +120,16 @@ Layout layout_of(int model, int topo, int64_t N, int64_t R)
         L.grptot = take(sizeof(i128) * nq * ngroups);
         L.grpctr = take(sizeof(unsigned long long) * ngroups);
     } else {
-        const int64_t n = N * N * N;
-        const int64_t nblk = ((N + 127) / 128) * N;
-        L.y = take(sizeof(double) * n);
-        L.acc = take(sizeof(double) * n);
+        const int64_t n = nodes_of(topo, N);
+        const int64_t nblk = lattice_order_blocks(topo, N);
+        L.y = take(sizeof(double) * d * n);
+        L.acc = take(sizeof(double) * d * n);
         L.f = take(sizeof(double) * 2 * n);
+        L.xs = take(sizeof(double) * model_nx(model) * n);
         L.sx = take(sizeof(int64_t) * 2 * n);
-        L.sxy = take(sizeof(int64_t) * 2 * n);
+        L.sxy = take(topo == SIM_CUBE3D ? sizeof(int64_t) * 2 * n : 0);
         L.partial = take(sizeof(i128) * 2 * nblk);
+        L.chords = take(topo == SIM_CUBE3D ? 0 : sizeof(int4) * (2 * R + 1) * (2 * R + 1));
     }
     L.ctrs = take(64);
     L.obs = take(sizeof(double) * kObsCap);
@@ -100,18 +141,21 @@ Layout layout_of(int model, int topo, int64_t N, int64_t R)
 const char *validate(int model, int topo, int64_t N, int64_t R, const double *params, int n_params)
 {
     if (model_dim(model) == 0) return "unknown model";
-    if (topo != SIM_RING && topo != SIM_CUBE3D) return "unknown topology";
-    if (topo == SIM_CUBE3D && model != SIM_KS) return "the cubic lattice supports the Kuramoto model only";
+    if (topo != SIM_RING && !is_lattice(topo)) return "unknown topology";
+    if (is_lattice(topo) && model != SIM_KS && model != SIM_KSI)
+        return "the lattices support the Kuramoto models (with or without inertia) only";
     if (R < 1) return "radius must be >= 1";
     if (N < 2 * R + 1) return "window does not fit: need 2*radius+1 <= N";
     if (topo == SIM_RING && N > (int64_t(1) << 34)) return "ring too large";
-    if (topo == SIM_CUBE3D && N > 1024) return "cube edge N1 must be <= 1024";
+    if ((topo == SIM_CUBE3D || topo == SIM_BALL3D) && N > 1024) return "3D lattice edge N1 must be <= 1024";
+    if (topo == SIM_DISK2D && N > 8192) return "disk lattice edge N1 must be <= 8192";
     if (n_params != model_nparams(model)) return "wrong number of parameters for this model";
     if (!params) return "params is NULL";
     for (int i = 0; i < n_params; ++i)
         if (!std::isfinite(params[i])) return "non-finite parameter";
     if (model == SIM_FHN && params[0] == 0.0) return "FHN eps must be non-zero";
     if (model == SIM_HH && params[0] == 0.0) return "HH Cm must be non-zero";
+    if (model == SIM_KSI && params[0] == 0.0) return "the mass m must be non-zero";
     return nullptr;
 }
 
@@ -127,7 +171,8 @@ struct sim_handle {
     size_t bytes = 0;
     Layout L;
     RingPlan ring{};
-    CubePlan cube{};
+    LatticePlan lat{};
+    std::vector<int4> chords; // host copy (the upload reads it asynchronously)
     unsigned *err = nullptr;
     unsigned long long *obs_ctr = nullptr;
     double *obs = nullptr;
@@ -161,7 +206,7 @@ cudaError_t launch_steps(sim_t h, int64_t n, double dt, cudaStream_t s)
 {
     if (use_cluster(h)) return n > 0 ? ring_cluster_steps(h->ring, dt, n, s) : cudaSuccess;
     for (int64_t t = 0; t < n; ++t) {
-        const cudaError_t e = h->topo == SIM_RING ? ring_step(h->ring, dt, s) : cube_step(h->cube, dt, s);
+        const cudaError_t e = h->topo == SIM_RING ? ring_step(h->ring, dt, s) : lattice_step(h->lat, dt, s);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -200,7 +245,7 @@ int prologue(sim_t h)
 {
     cudaError_t e = cudaMemsetAsync(h->obs_ctr, 0, sizeof(unsigned long long), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->err, 0, sizeof(unsigned), h->stream);
-    if (e == cudaSuccess) e = h->topo == SIM_RING ? ring_prologue(h->ring, h->stream) : cube_prologue(h->cube, h->stream);
+    if (e == cudaSuccess) e = h->topo == SIM_RING ? ring_prologue(h->ring, h->stream) : lattice_prologue(h->lat, h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "prologue");
     h->steps_done = 0;
     h->obs_read = 0;
@@ -240,7 +285,7 @@ static int create_impl(sim_t *out, int model, int topology, int64_t N, int64_t r
     h->d = model_dim(model);
     h->N = N;
     h->R = radius;
-    h->nodes = topology == SIM_CUBE3D ? N * N * N : N;
+    h->nodes = nodes_of(topology, N);
     h->flags = flags;
     h->stream = static_cast<cudaStream_t>(stream);
     h->L = layout_of(model, topology, N, radius);
@@ -290,13 +335,18 @@ static int create_impl(sim_t *out, int model, int topology, int64_t N, int64_t r
     mp.tab.exp2j = reinterpret_cast<const double *>(b + L.tabs) + 2 * kSinTab;
     const bool self = (flags & SIM_FLAG_INCLUDE_SELF) != 0;
     mp.include_self = self ? 1 : 0;
-    mp.wsize = topology == SIM_RING ? 2 * radius + 1 : (2 * radius + 1) * (2 * radius + 1) * (2 * radius + 1);
+    mp.wsize = window_of(topology, radius);
     const double K = (double)(self ? mp.wsize : mp.wsize - 1);
     if (model == SIM_KS) {
         mp.c[0] = params[0];
         mp.c[1] = params[1] / K;
         mp.c[2] = std::sin(params[2]);
         mp.c[3] = std::cos(params[2]);
+    } else if (model == SIM_KSI) {
+        mp.c[0] = params[2] / (params[0] * K); // mu / (m K)
+        mp.c[1] = params[1] / params[0];       // eps / m
+        mp.c[2] = std::sin(params[3]);
+        mp.c[3] = std::cos(params[3]);
     } else if (model == SIM_FHN) {
         const double ph = params[3], inv_eps = 1.0 / params[0], sK = params[2] / K;
         mp.c[0] = inv_eps;
@@ -347,14 +397,19 @@ static int create_impl(sim_t *out, int model, int topology, int64_t N, int64_t r
             if (cl_err != cudaSuccess) h->flags |= SIM_FLAG_STREAMING; // fall back to the streaming kernels
         }
     } else {
-        CubePlan &p = h->cube;
+        LatticePlan &p = h->lat;
+        p.model = model;
+        p.topo = topology;
+        p.dims = topology == SIM_DISK2D ? 2 : 3;
         p.N1 = N;
         p.P = radius;
+        p.nodes = h->nodes;
         p.F = 61 - ceil_log2((uint64_t)mp.wsize);
         p.mp = mp;
         p.y = reinterpret_cast<double *>(b + L.y);
         p.acc = reinterpret_cast<double *>(b + L.acc);
         p.f = reinterpret_cast<double *>(b + L.f);
+        p.xs = reinterpret_cast<double *>(b + L.xs);
         p.sx = reinterpret_cast<int64_t *>(b + L.sx);
         p.sxy = reinterpret_cast<int64_t *>(b + L.sxy);
         p.partial = reinterpret_cast<i128 *>(b + L.partial);
@@ -363,9 +418,24 @@ static int create_impl(sim_t *out, int model, int topology, int64_t N, int64_t r
         p.obs = h->obs;
         p.obs_cap = kObsCap;
         p.obs_ctr = h->obs_ctr;
-        if ((e = cube_configure()) != cudaSuccess) {
+        p.chords = nullptr;
+        p.nchords = 0;
+        if (topology != SIM_CUBE3D) {
+            int64_t cnt = 0;
+            const std::vector<int4> ch = chords_of(topology, radius, &cnt);
+            h->chords = ch;
+            p.chords = reinterpret_cast<const int4 *>(b + L.chords);
+            p.nchords = (int)ch.size();
+            e = cudaMemcpyAsync(b + L.chords, h->chords.data(), sizeof(int4) * ch.size(), cudaMemcpyHostToDevice,
+                                h->stream);
+        }
+        static std::once_flag lat_once;
+        static cudaError_t lat_err = cudaSuccess;
+        std::call_once(lat_once, [] { lat_err = lattice_configure(); });
+        if (e == cudaSuccess) e = lat_err;
+        if (e != cudaSuccess) {
             sim_destroy(h);
-            return cuda_fail(e, "cube kernel configuration");
+            return cuda_fail(e, "lattice set-up");
         }
     }
     const int st = prologue(h);
@@ -398,7 +468,7 @@ static int set_state_impl(sim_t h, const double *src, int64_t n_values, cudaMemc
 {
     if (!h || !src) return fail(SIM_EINVAL, "NULL handle or buffer");
     if (n_values != (int64_t)h->d * h->nodes) return fail(SIM_EINVAL, "n_values must equal dim * nodes");
-    double *y = h->topo == SIM_RING ? h->ring.y : h->cube.y;
+    double *y = h->topo == SIM_RING ? h->ring.y : h->lat.y;
     cudaError_t e = cudaMemcpyAsync(y, src, sizeof(double) * n_values, kind, h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "state copy");
     return prologue(h);
@@ -448,7 +518,7 @@ static int get_state_impl(sim_t h, double *dst, int64_t n_values, cudaMemcpyKind
 {
     if (!h || !dst) return fail(SIM_EINVAL, "NULL handle or buffer");
     if (n_values != (int64_t)h->d * h->nodes) return fail(SIM_EINVAL, "n_values must equal dim * nodes");
-    const double *y = h->topo == SIM_RING ? h->ring.y : h->cube.y;
+    const double *y = h->topo == SIM_RING ? h->ring.y : h->lat.y;
     const cudaError_t e = cudaMemcpyAsync(dst, y, sizeof(double) * n_values, kind, h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "state copy");
     return SIM_OK;
@@ -470,9 +540,9 @@ int sim_rhs(sim_t h, double *host_k, int64_t n_values)
 {
     if (!h || !host_k) return fail(SIM_EINVAL, "NULL handle or buffer");
     if (n_values != (int64_t)h->d * h->nodes) return fail(SIM_EINVAL, "n_values must equal dim * nodes");
-    cudaError_t e = h->topo == SIM_RING ? ring_rhs(h->ring, h->stream) : cube_rhs(h->cube, h->stream);
+    cudaError_t e = h->topo == SIM_RING ? ring_rhs(h->ring, h->stream) : lattice_rhs(h->lat, h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "rhs launch");
-    const double *acc = h->topo == SIM_RING ? h->ring.acc : h->cube.acc;
+    const double *acc = h->topo == SIM_RING ? h->ring.acc : h->lat.acc;
     e = cudaMemcpyAsync(host_k, acc, sizeof(double) * n_values, cudaMemcpyDeviceToHost, h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "rhs copy");
     return check_device_error(h);
@@ -482,7 +552,7 @@ int sim_observables(sim_t h, double *host_R, int64_t max_values, int64_t *n_writ
 {
     if (!h || !n_written || (max_values > 0 && !host_R)) return fail(SIM_EINVAL, "NULL argument");
     *n_written = 0;
-    if (h->model != SIM_KS) return check_device_error(h);
+    if (h->model != SIM_KS && h->model != SIM_KSI) return check_device_error(h);
     cudaError_t e = cudaMemcpyAsync(&h->h_ctr, h->obs_ctr, sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "observable counter copy");
@@ -525,7 +595,7 @@ struct sim_batch_handle {
     std::vector<sim_t> members;
     std::vector<int> ring_slot;      // member -> index of its plan in the group tables (or -1)
     std::vector<RingBatchGroup> groups;
-    std::vector<sim_t> cubes;
+    std::vector<sim_t> lattices;
     void *block = nullptr;           // device tables
     long long *budgets = nullptr;    // device: steps left per ring member (budgeted mode)
     std::vector<long long> host_budget; // host shadow, -1 = unlimited
@@ -535,7 +605,7 @@ struct sim_batch_handle {
     bool budgeted = false;
     std::map<std::pair<double, int>, cudaGraphExec_t> graphs;
     std::map<std::pair<double, int>, int> uses; // launches per (dt, chunk) before capturing a graph
-    // independent branches (one per model group, cubes spread over a few) run
+    // independent branches (one per model group, lattices spread over a few) run
     // concurrently on side streams, forked from and joined to the main stream
     std::vector<cudaStream_t> side;
     cudaEvent_t ev_fork = nullptr;
@@ -556,15 +626,15 @@ __global__ void batch_error_kernel(unsigned *const *errs, int n, unsigned *out)
     if (threadIdx.x == 0) *out = acc;
 }
 
-constexpr int kCubeBranches = 4;
+constexpr int kLatticeBranches = 4;
 
 int n_branches(sim_batch_t b)
 {
-    const int nc = (int)b->cubes.size();
-    return (int)b->groups.size() + (nc < kCubeBranches ? nc : kCubeBranches);
+    const int nc = (int)b->lattices.size();
+    return (int)b->groups.size() + (nc < kLatticeBranches ? nc : kLatticeBranches);
 }
 
-// n steps of branch k (a ring group, or every kCubeBranches-th cube) on stream s.
+// n steps of branch k (a ring group, or every kLatticeBranches-th lattice) on stream s.
 cudaError_t branch_steps(sim_batch_t b, int k, int64_t n, double dt, cudaStream_t s)
 {
     const int ng = (int)b->groups.size();
@@ -573,8 +643,8 @@ cudaError_t branch_steps(sim_batch_t b, int k, int64_t n, double dt, cudaStream_
             const cudaError_t e = ring_batch_step(b->groups[k], dt, s);
             if (e != cudaSuccess) return e;
         } else {
-            for (size_t c = (size_t)(k - ng); c < b->cubes.size(); c += kCubeBranches) {
-                const cudaError_t e = cube_step(b->cubes[c]->cube, dt, s);
+            for (size_t c = (size_t)(k - ng); c < b->lattices.size(); c += kLatticeBranches) {
+                const cudaError_t e = lattice_step(b->lattices[c]->lat, dt, s);
                 if (e != cudaSuccess) return e;
             }
         }
@@ -657,17 +727,17 @@ int sim_batch_create(sim_batch_t *out, const sim_t *members, int n_members, void
     b->host_budget.assign(n_members, -1);
 
     // Group ring members by model; host copies of the device tables.
-    std::vector<std::vector<int>> by_model(3);
+    std::vector<std::vector<int>> by_model(4);
     for (int i = 0; i < n_members; ++i) {
         if (members[i]->topo == SIM_RING) by_model[members[i]->model].push_back(i);
-        else b->cubes.push_back(members[i]);
+        else b->lattices.push_back(members[i]);
     }
     std::vector<RingPlan> plans;
     std::vector<int> inst_of_item;
     std::vector<int64_t> item_base;
     struct GroupSpan { int model, plan0, n; int64_t item0, n_items; };
     std::vector<GroupSpan> spans;
-    for (int m = 0; m < 3; ++m) {
+    for (int m = 0; m < 4; ++m) {
         if (by_model[m].empty()) continue;
         GroupSpan gs{m, (int)plans.size(), (int)by_model[m].size(), (int64_t)inst_of_item.size(), 0};
         for (int k = 0; k < (int)by_model[m].size(); ++k) {
@@ -741,7 +811,7 @@ int sim_batch_set_budgets(sim_batch_t b, const int64_t *steps)
     for (int i = 0; i < n; ++i) {
         if (steps[i] < -1) return fail(SIM_EINVAL, "budgets must be >= 0, or -1 for unlimited");
         if (b->members[i]->topo != SIM_RING && steps[i] != -1)
-            return fail(SIM_EINVAL, "step budgets apply to ring members only");
+            return fail(SIM_EINVAL, "step budgets apply to ring members only (lattices take -1)");
     }
     std::vector<long long> dev;
     for (int i = 0; i < n; ++i) {

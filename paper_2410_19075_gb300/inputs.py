@@ -13,6 +13,7 @@ double in [0, 1) takes its top 53 bits.
 Workload shapes (the paper's networks start from random initial conditions,
 Section IV):
   * Kuramoto phases  phi ~ U[-pi, pi)
+  * Kuramoto with inertia: phi ~ U[-pi, pi), phase velocity psi ~ U[-0.1, 0.1]
   * FitzHugh-Nagumo (u, v) uniform on the circle of radius 2
   * Hodgkin-Huxley V ~ U[-70, -60] mV, gates near their resting values,
     external current I_ext ~ U[9, 11] per node
@@ -34,7 +35,7 @@ _MASK = (1 << 64) - 1
 _CHUNK = 1 << 22
 
 # Variable ids of the streams (part of the key).
-VAR_PHASE, VAR_U, VAR_V, VAR_M, VAR_H, VAR_N, VAR_IEXT, VAR_INST = range(8)
+VAR_PHASE, VAR_U, VAR_V, VAR_M, VAR_H, VAR_N, VAR_IEXT, VAR_INST, VAR_PSI = range(9)
 
 
 def _mix_int(z: int) -> int:
@@ -81,6 +82,13 @@ def ks_phases(seed: int, instance: int, nodes: int) -> np.ndarray:
     return uniform(seed, instance, VAR_PHASE, nodes, -math.pi, math.pi)
 
 
+def ksi_state(seed: int, instance: int, nodes: int, psi_max: float = 0.1) -> np.ndarray:
+    """Kuramoto with inertia (phi, psi = dphi/dt); SoA (2*nodes).  The phases are
+    the same stream as ``ks_phases``."""
+    return np.concatenate([ks_phases(seed, instance, nodes),
+                           uniform(seed, instance, VAR_PSI, nodes, -psi_max, psi_max)])
+
+
 def fhn_state(seed: int, instance: int, nodes: int, radius: float = 2.0) -> np.ndarray:
     """FitzHugh-Nagumo (u, v), uniform on the circle of the given radius; SoA (2*nodes)."""
     theta = uniform(seed, instance, VAR_U, nodes, 0.0, 2.0 * math.pi)
@@ -113,6 +121,12 @@ def ks_params(omega=0.0, mu=1.0, alpha=1.46):
     return np.array([omega, mu, alpha], dtype=np.float64)
 
 
+def ksi_params(m=1.0, eps=0.05, mu=0.01, alpha=0.45):
+    """Kuramoto with inertia; the defaults are the scroll-toroid chimera
+    parameters of the paper's performance test (Fig. 6c)."""
+    return np.array([m, eps, mu, alpha], dtype=np.float64)
+
+
 def fhn_params(eps=0.05, a=0.5, sigma=0.1, phi=math.pi / 2 - 0.1):
     return np.array([eps, a, sigma, phi], dtype=np.float64)
 
@@ -122,13 +136,16 @@ def hh_params(Cm=1.0, gNa=120.0, gK=36.0, gL=0.3, ENa=50.0, EK=-77.0, EL=-54.4, 
 
 
 def initial_state(model: int, seed: int, instance: int, nodes: int) -> np.ndarray:
-    """Seeded initial state for model 0 (Kuramoto), 1 (FHN) or 2 (HH)."""
+    """Seeded initial state for model 0 (Kuramoto), 1 (FHN), 2 (HH) or 3
+    (Kuramoto with inertia)."""
     if model == 0:
         return ks_phases(seed, instance, nodes)
     if model == 1:
         return fhn_state(seed, instance, nodes)
     if model == 2:
         return hh_state(seed, instance, nodes)
+    if model == 3:
+        return ksi_state(seed, instance, nodes)
     raise ValueError(f"unknown model {model}")
 
 

@@ -11,11 +11,11 @@ import numpy as np
 
 from ._lib import check, lib
 
-KS, FHN, HH = 0, 1, 2
-RING, CUBE3D = 0, 1
+KS, FHN, HH, KSI = 0, 1, 2, 3
+RING, CUBE3D, BALL3D, DISK2D = 0, 1, 2, 3
 FLAG_INCLUDE_SELF = 1
 FLAG_STREAMING = 2
-DIM = {KS: 1, FHN: 2, HH: 4}
+DIM = {KS: 1, FHN: 2, HH: 4, KSI: 2}
 
 
 def _stream_ptr(stream):

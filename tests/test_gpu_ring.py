@@ -24,7 +24,7 @@ def _check(model, N, R, steps, seed, dt=0.01, include_self=False, tol=STATE_TOL,
     ref, ref_order = oracle_run(model, 0, N, R, params, y0, steps, dt, npar, include_self, threads)
     err = np.abs(y - ref).max()
     assert err <= tol, (model, N, R, err)
-    if model == 0:
+    if model in (0, 3):
         assert order.size == steps + 1
         assert np.abs(order - ref_order).max() <= ORDER_TOL
     else:
@@ -43,7 +43,7 @@ def test_ks_ring_config1_1000_steps():
     _check(0, 1000, 350, 1000, 2411)
 
 
-@pytest.mark.parametrize("model", [0, 1, 2])
+@pytest.mark.parametrize("model", [0, 1, 2, 3])
 @pytest.mark.parametrize("N", [3, 4, 5, 7, 16, 33])
 def test_ring_tiny_every_radius(model, N):
     """Every radius with 2R+1 <= N, including the full-wrap edge 2R+1 = N."""
@@ -51,7 +51,7 @@ def test_ring_tiny_every_radius(model, N):
         _check(model, N, R, 30, 100 + N + R, tol=1e-12)
 
 
-@pytest.mark.parametrize("model", [0, 1, 2])
+@pytest.mark.parametrize("model", [0, 1, 2, 3])
 @pytest.mark.parametrize("R", [1, 2, 100, 777, 1574])
 def test_ring_several_tiles_ragged_tail(model, R):
     """N = 3*1024 + 77 spans 4 CTA tiles and 13 sub-tiles with a ragged tail."""
@@ -60,6 +60,33 @@ def test_ring_several_tiles_ragged_tail(model, R):
 
 def test_ks_ring_include_self():
     _check(0, 500, 60, 200, 31, include_self=True)
+
+
+def test_ksi_ring_1000_steps():
+    """Kuramoto with inertia (m = 1, eps = 0.05, mu = 0.01, alpha = 0.45) on a
+    ring of 1000 nodes, R = 350, 1000 RK4 steps of dt = 0.01."""
+    _check(3, 1000, 350, 1000, 2416)
+
+
+def test_ksi_ring_strong_coupling_include_self():
+    _check(3, 777, 100, 300, 2417, include_self=True)
+
+
+def test_ksi_twisted_state_closed_form_on_gpu():
+    """A twisted state phi_i = 2 pi q i / N with phase velocity psi = Om, the
+    terminal velocity Om = (mu/K) S / eps of its constant coupling sum S, is an
+    exact uniformly rotating solution: after T the phases moved by Om T and psi
+    is unchanged."""
+    N, R, q = 4096 + 123, 1000, 3
+    m, eps, mu, alpha = 0.7, 0.05, 1.0, 0.45
+    k = 2 * math.pi * q / N
+    S = -math.sin(alpha) * (2 * math.sin(R * k / 2) * math.cos((R + 1) * k / 2) / math.sin(k / 2))
+    Om = (mu / (2 * R)) * S / eps
+    y0 = np.concatenate([2 * math.pi * q * np.arange(N) / N, np.full(N, Om)])
+    y, order = gpu_run(3, 0, N, R, [m, eps, mu, alpha], y0, 100, 0.01)
+    assert np.abs(y[:N] - y0[:N] - Om).max() < 1e-11
+    assert np.abs(y[N:] - Om).max() < 1e-12
+    assert np.abs(order).max() < 1e-13
 
 
 def test_fhn_ring_scaled_config2_1000_steps():
@@ -84,7 +111,7 @@ def test_ks_twisted_state_closed_form_on_gpu():
     assert np.abs(order).max() < 1e-13
 
 
-@pytest.mark.parametrize("model", [0, 1, 2])
+@pytest.mark.parametrize("model", [0, 1, 2, 3])
 def test_rhs_matches_oracle_sampled_at_full_size(model):
     """Full-size networks (N = 10^6, r = 0.35; HH at 10^5, r = 0.3): the GPU
     right-hand side at the seeded state and after 100 steps, checked at 256
@@ -176,7 +203,7 @@ def test_nonfinite_state_reported():
         net.get_state()
 
 
-@pytest.mark.parametrize("model", [0, 1, 2])
+@pytest.mark.parametrize("model", [0, 1, 2, 3])
 @pytest.mark.parametrize("N,R", [(3, 1), (257, 128), (1000, 350), (2048, 700), (4096, 1)])
 def test_cluster_path_equals_streaming_path_bitwise(model, N, R):
     """Rings of <= 4096 nodes run all steps of a call in one thread-block cluster;

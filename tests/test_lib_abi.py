@@ -53,6 +53,11 @@ def test_workspace_bytes(lib):
     assert 6.0e9 < cube < 7.0e9  # 64 B per lattice node
     assert workspace_bytes(0, 0, 10, 5) == 0  # 2R+1 > N
     assert workspace_bytes(1, 1, 10, 2) == 0  # cube is Kuramoto only
+    assert workspace_bytes(2, 2, 10, 2) == 0  # so is the ball
+    ball = workspace_bytes(3, 2, 100, 4)      # 3D Kuramoto with inertia, ball of radius 4
+    assert 0 < ball < 100 * 10 ** 6
+    disk = workspace_bytes(0, 3, 1000, 30)
+    assert 0 < disk < 100 * 10 ** 6
 
 
 @pytest.mark.parametrize("model,topo,N,R,params", [
@@ -61,9 +66,15 @@ def test_workspace_bytes(lib):
     (0, 0, 10, 2, [0, 1]),          # wrong param count
     (0, 0, 10, 2, [0, np.nan, 1]),  # non-finite param
     (1, 1, 9, 2, [0.05, 0.5, 0.1, 1.4]),  # FHN on the cube
-    (3, 0, 10, 2, [0, 1, 1]),       # unknown model
-    (0, 2, 10, 2, [0, 1, 1]),       # unknown topology
+    (4, 0, 10, 2, [0, 1, 1]),       # unknown model
+    (0, 4, 10, 2, [0, 1, 1]),       # unknown topology
     (0, 1, 2000, 2, [0, 1, 1]),     # cube edge too large
+    (0, 2, 1025, 2, [0, 1, 1]),     # ball edge too large
+    (0, 3, 8193, 2, [0, 1, 1]),     # disk edge too large
+    (0, 2, 10, 5, [0, 1, 1]),       # ball window does not fit
+    (2, 3, 50, 2, [1, 120, 36, 0.3, 50, -77, -54.4, 0.1]),  # HH on the disk
+    (3, 0, 10, 2, [0, 0.05, 1, 0.45]),  # inertia model with m = 0
+    (3, 2, 10, 2, [1, 0.05, 1]),    # inertia model, wrong param count
 ])
 def test_create_rejects_invalid_arguments(lib, model, topo, N, R, params):
     from paper_2410_19075_gb300._lib import SIM_EINVAL
