@@ -177,6 +177,20 @@ __device__ __forceinline__ i128 shfl_up_i128(i128 v, int o)
     return (i128)(u128)(unsigned long long)l2 | ((i128)h2 << 64);
 }
 
+// Sum over the 32 lanes of a warp (every lane gets the total; exact).
+__device__ __forceinline__ i128 warp_sum_i128(i128 v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long lo = (unsigned long long)(u128)v;
+        const unsigned long long hi = (unsigned long long)(u128)(v >> 64);
+        const unsigned long long l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+        const unsigned long long h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+        v += (i128)(((u128)h2 << 64) | (u128)l2);
+    }
+    return v;
+}
+
 // Called by every thread of one CTA (blockDim.x a multiple of 32).  Writes the
 // exclusive prefix of in[0..n) to out[0..n] (out[n] = total) and returns the
 // total.  in is read through L2 (it was written by other CTAs of this launch).

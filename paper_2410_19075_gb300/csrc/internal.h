@@ -78,7 +78,10 @@ struct LatticePlan {
     double *y, *acc;  // D * nodes
     double *f;        // 2 * nodes: sin, cos of the current stage-input phase
     double *xs;       // NX * nodes: local stage-input variables (psi of model 3)
-    int64_t *sx;      // 2 * nodes: cube window sums along x, or row prefixes (ball, disk)
+    int64_t *sx;      // cube: 2 * nodes window sums along x (SoA); ball, disk: per row,
+                      // rs (sin, cos) pairs of the periodically extended inclusive
+                      // prefix E(x), x in [-P-1, N1+P-1], stored at x + P + 1
+    int64_t rs;       // ball, disk: row stride of sx in (sin, cos) pairs, N1 + 2P + 1
     int64_t *sxy;     // 2 * nodes: cube box sums over x and y
     i128 *partial;    // per-CTA partial sums of the order parameter
     unsigned long long *done_ctr;
@@ -92,6 +95,7 @@ struct LatticePlan {
 
 cudaError_t lattice_configure(); // once per process, before the first launch
 int64_t lattice_order_blocks(int topo, int64_t N1); // CTAs of the order-parameter passes
+int64_t lattice_sx_elems(int topo, int64_t N1, int64_t P); // int64 elements of sx
 cudaError_t lattice_prologue(const LatticePlan &p, cudaStream_t s);
 cudaError_t lattice_step(const LatticePlan &p, double dt, cudaStream_t s);
 cudaError_t lattice_rhs(const LatticePlan &p, cudaStream_t s); // acc <- f(y)

@@ -11,11 +11,14 @@
 //   z pass  W(i,j,k)   = sum_{|dz|<=P} SXY(i,j,k+dz)       (sliding window along k)
 //           fused with the right-hand side, the RK4 update and the next (sin, cos).
 // Ball and disk, per RK4 stage:
-//   x pass  the inclusive prefix of Q(f) along every row (wrapping int64);
+//   x pass  the inclusive prefix E(x) of Q(f) along every row, extended
+//           periodically by P + 1 entries on the left and P on the right, with
+//           sin and cos interleaved (wrapping int64);
 //   gather  W = sum over the chords of the window, one per (dy, dz) (ball) or dy
 //           (disk): the row segment |dx| <= w = floor(sqrt(P^2 - dy^2 - dz^2)),
-//           each read as a difference of two row prefixes (O(P^2) resp. O(P)
-//           reads per node), fused with the right-hand side and RK4 update.
+//           read as E(i + w) - E(i - w - 1), one 16-byte load per end (O(P^2)
+//           resp. O(P) reads per node), fused with the right-hand side and RK4
+//           update.
 #include "internal.h"
 
 namespace simk {
@@ -93,14 +96,28 @@ __global__ void __launch_bounds__(32 * kRowWarpsMax) lattice_x_kernel(LatticePla
             pre1[0] = 0;
         }
         __syncwarp();
-        int64_t *__restrict__ o0 = p.sx + row * N1;
-        int64_t *__restrict__ o1 = p.sx + nodes + row * N1;
         if (PREFIX) {
-            for (int64_t i = lane; i < N1; i += 32) {
-                o0[i] = pre0[i + 1];
-                o1[i] = pre1[i + 1];
+            // E(x) = Pe(x + 1) for x in [-P-1, N1+P-1], at slot x + P + 1
+            const uint64_t t0 = (uint64_t)pre0[N1], t1 = (uint64_t)pre1[N1];
+            longlong2 *__restrict__ o = reinterpret_cast<longlong2 *>(p.sx) + row * p.rs;
+            for (int64_t e = lane; e < p.rs; e += 32) {
+                int64_t q = e - P; // = x + 1, in [-P, N1 + P]
+                uint64_t v0, v1;
+                if (q < 0) {
+                    v0 = (uint64_t)pre0[q + N1] - t0;
+                    v1 = (uint64_t)pre1[q + N1] - t1;
+                } else if (q > N1) {
+                    v0 = (uint64_t)pre0[q - N1] + t0;
+                    v1 = (uint64_t)pre1[q - N1] + t1;
+                } else {
+                    v0 = (uint64_t)pre0[q];
+                    v1 = (uint64_t)pre1[q];
+                }
+                o[e] = make_longlong2((long long)v0, (long long)v1);
             }
         } else {
+            int64_t *__restrict__ o0 = p.sx + row * N1;
+            int64_t *__restrict__ o1 = p.sx + nodes + row * N1;
             const int64_t t0 = pre0[N1], t1 = pre1[N1];
             for (int64_t i = lane; i < N1; i += 32) {
                 int64_t b = i + P + 1, a = i - P;
@@ -164,34 +181,54 @@ __global__ void __launch_bounds__(kColThreads) cube_y_kernel(LatticePlan p)
 }
 
 // Deterministic order parameter of the new state: per-CTA partial sums of the
-// fixed-point (sin, cos), and the last CTA to finish sums every partial in index
-// order and records R.
-__device__ void lattice_record_order(const LatticePlan &p, int64_t ps, int64_t pc)
+// fixed-point (sin, cos) (exact i128, so the reduction order does not matter),
+// and the last CTA to finish sums every partial and records R.
+__device__ void lattice_record_order(const LatticePlan &p, i128 ps, i128 pc)
 {
-    __shared__ int64_t s_s[256], s_c[256];
+    __shared__ i128 s_ws[32], s_wc[32];
     __shared__ bool s_last;
-    s_s[threadIdx.x] = ps;
-    s_c[threadIdx.x] = pc;
-    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const unsigned nblk = gridDim.x * gridDim.y;
     const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x;
+    ps = warp_sum_i128(ps);
+    pc = warp_sum_i128(pc);
+    if (lane == 0) {
+        s_ws[warp] = ps;
+        s_wc[warp] = pc;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
         i128 ts = 0, tc = 0;
-        for (unsigned t = 0; t < blockDim.x; ++t) {
-            ts += s_s[t];
-            tc += s_c[t];
+        for (int w = 0; w < nw; ++w) {
+            ts += s_ws[w];
+            tc += s_wc[w];
         }
-        p.partial[2 * bid] = ts;
-        p.partial[2 * bid + 1] = tc;
+        st_i128(p.partial + 2 * bid, ts);
+        st_i128(p.partial + 2 * bid + 1, tc);
         __threadfence();
         s_last = last_arrival(p.done_ctr, nblk);
     }
     __syncthreads();
-    if (s_last && threadIdx.x == 0) {
-        i128 ts = 0, tc = 0;
-        for (unsigned b = 0; b < nblk; ++b) {
-            ts += ld_cg_i128(p.partial + 2 * b);
-            tc += ld_cg_i128(p.partial + 2 * b + 1);
+    if (!s_last) return;
+    i128 ts = 0, tc = 0;
+    for (unsigned b = threadIdx.x; b < nblk; b += blockDim.x) {
+        ts += ld_cg_i128(p.partial + 2 * b);
+        tc += ld_cg_i128(p.partial + 2 * b + 1);
+    }
+    ts = warp_sum_i128(ts);
+    tc = warp_sum_i128(tc);
+    __syncthreads();
+    if (lane == 0) {
+        s_ws[warp] = ts;
+        s_wc[warp] = tc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ts = 0;
+        tc = 0;
+        for (int w = 0; w < nw; ++w) {
+            ts += s_ws[w];
+            tc += s_wc[w];
         }
         const double S = fixed_to_double(ts, p.F), C = fixed_to_double(tc, p.F);
         const unsigned long long n = *p.obs_ctr;
@@ -205,7 +242,7 @@ __device__ void lattice_record_order(const LatticePlan &p, int64_t ps, int64_t p
 // cos).  STAGE 0 (prologue) only computes (sin, cos) of y.
 template <int M, int STAGE>
 __device__ __forceinline__ void lattice_node(const LatticePlan &p, int64_t n, int64_t W0, int64_t W1, double dt,
-                                             bool &ok, int64_t &ps, int64_t &pc)
+                                             bool &ok, i128 &ps, i128 &pc)
 {
     constexpr int D = Model<M>::D, NX = Model<M>::NX, XOFF = D - NX;
     const int64_t nodes = p.nodes;
@@ -262,7 +299,7 @@ __global__ void __launch_bounds__(kColThreads) cube_z_kernel(LatticePlan p, doub
     const int64_t N1 = p.N1, P = p.P, nodes = p.nodes, plane = N1 * N1;
     const int64_t i = (int64_t)blockIdx.x * kColThreads + threadIdx.x;
     const int64_t j = blockIdx.y;
-    int64_t ps = 0, pc = 0;
+    i128 ps = 0, pc = 0;
     bool ok = true;
     if (i < N1) {
         const int64_t col = j * N1 + i; // + k * plane
@@ -291,37 +328,36 @@ __global__ void __launch_bounds__(kColThreads) cube_z_kernel(LatticePlan p, doub
     if (STAGE == 0 || STAGE == 4) lattice_record_order(p, ps, pc);
 }
 
-// Sum of Q(f) over the row segment [a, b] (b - a < N1, a > -N1, b < 2 N1) from the
-// row's inclusive prefix I (wrapping arithmetic; the segment sum itself is exact).
-__device__ __forceinline__ uint64_t chord_sum(const int64_t *__restrict__ I, int64_t N1, int64_t a, int64_t b)
-{
-    const uint64_t tot = (uint64_t)__ldg(I + N1 - 1);
-    if (a < 0) return tot - (uint64_t)__ldg(I + a + N1 - 1) + (uint64_t)__ldg(I + b);
-    if (b >= N1) return tot - (a ? (uint64_t)__ldg(I + a - 1) : 0ull) + (uint64_t)__ldg(I + b - N1);
-    return (uint64_t)__ldg(I + b) - (a ? (uint64_t)__ldg(I + a - 1) : 0ull);
-}
-
 // ball / disk gather: one node per thread; the window is the union of the chords
-// (dy, dz, w) of the plan's table.
+// (dy, dz, w) of the plan's table, each the difference of two extended-prefix
+// entries of one row (wrapping arithmetic; every chord sum and the window sum
+// itself are exact).
 template <int M, int STAGE>
 __global__ void __launch_bounds__(kGatherThreads) lattice_gather_kernel(LatticePlan p, double dt)
 {
     const int64_t N1 = p.N1, nodes = p.nodes;
     const int64_t n = (int64_t)blockIdx.x * kGatherThreads + threadIdx.x;
-    int64_t ps = 0, pc = 0;
+    i128 ps = 0, pc = 0;
     bool ok = true;
     if (n < nodes) {
-        const int64_t i = n % N1, j = (n / N1) % N1, k = p.dims == 3 ? n / (N1 * N1) : 0;
+        const int i = (int)(n % N1), j = (int)((n / N1) % N1), k = p.dims == 3 ? (int)(n / (N1 * N1)) : 0;
+        const int n1 = (int)N1;
         uint64_t w0 = 0, w1 = 0;
         if (STAGE > 0) {
-            for (int c = 0; c < p.nchords; ++c) {
+            const longlong2 *__restrict__ E = reinterpret_cast<const longlong2 *>(p.sx) + (i + p.P + 1);
+            const int nch = p.nchords;
+#pragma unroll 4
+            for (int c = 0; c < nch; ++c) {
                 const int4 ch = __ldg(p.chords + c); // (dy, dz, w, 0)
-                int64_t jj = j + ch.x, kk = k + ch.y;
-                if (jj < 0) jj += N1; else if (jj >= N1) jj -= N1;
-                if (kk < 0) kk += N1; else if (kk >= N1) kk -= N1;
-                const int64_t row = (kk * N1 + jj) * N1;
-                w0 += chord_sum(p.sx + row, N1, i - ch.z, i + ch.z);
-                w1 += chord_sum(p.sx + nodes + row, N1, i - ch.z, i + ch.z);
+                int jj = j + ch.x, kk = k + ch.y;
+                jj += jj < 0 ? n1 : 0;
+                jj -= jj >= n1 ? n1 : 0;
+                kk += kk < 0 ? n1 : 0;
+                kk -= kk >= n1 ? n1 : 0;
+                const longlong2 *r = E + (int64_t)(kk * n1 + jj) * p.rs;
+                const longlong2 b = __ldg(r + ch.z), a = __ldg(r - ch.z - 1);
+                w0 += (uint64_t)b.x - (uint64_t)a.x;
+                w1 += (uint64_t)b.y - (uint64_t)a.y;
             }
         }
         lattice_node<M, STAGE>(p, n, (int64_t)w0, (int64_t)w1, dt, ok, ps, pc);
@@ -339,6 +375,13 @@ static dim3 col_grid(int64_t N1)
 static unsigned gather_grid(const LatticePlan &p)
 {
     return (unsigned)((p.nodes + kGatherThreads - 1) / kGatherThreads);
+}
+
+int64_t lattice_sx_elems(int topo, int64_t N1, int64_t P)
+{
+    if (topo == 1) return 2 * N1 * N1 * N1;
+    const int64_t rows = topo == 3 ? N1 : N1 * N1;
+    return 2 * rows * (N1 + 2 * P + 1);
 }
 
 int64_t lattice_order_blocks(int topo, int64_t N1)

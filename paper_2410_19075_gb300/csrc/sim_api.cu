@@ -126,7 +126,7 @@ Layout layout_of(int model, int topo, int64_t N, int64_t R)
         L.acc = take(sizeof(double) * d * n);
         L.f = take(sizeof(double) * 2 * n);
         L.xs = take(sizeof(double) * model_nx(model) * n);
-        L.sx = take(sizeof(int64_t) * 2 * n);
+        L.sx = take(sizeof(int64_t) * lattice_sx_elems(topo, N, R));
         L.sxy = take(topo == SIM_CUBE3D ? sizeof(int64_t) * 2 * n : 0);
         L.partial = take(sizeof(i128) * 2 * nblk);
         L.chords = take(topo == SIM_CUBE3D ? 0 : sizeof(int4) * (2 * R + 1) * (2 * R + 1));
@@ -411,6 +411,7 @@ static int create_impl(sim_t *out, int model, int topology, int64_t N, int64_t r
         p.f = reinterpret_cast<double *>(b + L.f);
         p.xs = reinterpret_cast<double *>(b + L.xs);
         p.sx = reinterpret_cast<int64_t *>(b + L.sx);
+        p.rs = N + 2 * radius + 1;
         p.sxy = reinterpret_cast<int64_t *>(b + L.sxy);
         p.partial = reinterpret_cast<i128 *>(b + L.partial);
         p.done_ctr = ticket;

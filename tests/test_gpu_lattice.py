@@ -180,3 +180,21 @@ def test_batch_of_lattices_equals_solo_runs():
     finally:
         for net in nets:
             net.close()
+
+
+@pytest.mark.parametrize("topo,N1,P", [(CUBE, 300, 1), (BALL, 300, 1), (DISK, 4000, 1)])
+def test_order_parameter_of_large_lattices_with_small_windows(topo, N1, P):
+    """Small windows give the finest fixed-point grid (2^-58 for the radius-1
+    ball), so the lattice-wide sums of the order parameter need 128 bits: check
+    R at t = 0 and after 3 steps against the oracle's plain sum."""
+    from paper_2410_19075_gb300 import Network
+    n = nodes_of(topo, N1)
+    y0 = I.ks_phases(2422, 0, n)
+    with Network(0, topo, N1, P, I.ks_params()) as net:
+        net.set_state(y0)
+        net.step(3, 0.01)
+        y = net.get_state()
+        order = net.observables()
+    assert order.size == 4
+    assert abs(order[0] - oracle.order_parameter(y0)) <= ORDER_TOL
+    assert abs(order[-1] - oracle.order_parameter(y)) <= ORDER_TOL
