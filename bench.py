@@ -35,15 +35,15 @@ TOPO_NAMES = {1: "periodic cubic lattice", 2: "periodic 3D lattice, ball window"
 # entries (2 * nq * 8), y (d * 8), acc (d * 8, stages 2-4), local stage
 # variables (nx * 8) and the node parameter, and writes the next prefix entry
 # (nq * 8), acc or y (d * 8) and the next local stage variables (nx * 8).
-RING_BYTES = {0: 344, 1: 432, 2: 704}
+RING_BYTES = {0: 344, 1: 432, 2: 704, 3: 480}
 # FP64 flops per node-step (DFMA = 2, DADD/DMUL = 1) of the arithmetic the method
 # needs, from the kernels' expressions; a library sincos counts 50 and a library
 # exp/expm1 34 (their measured cost in DFMA equivalents, x2).  Tally in the design doc.
-RING_FLOPS = {0: 4 * (50 + 13) + 14, 1: 4 * 15 + 3 * 8 + 6, 2: 4 * (6 * 34 + 40) + 3 * 16 + 12}
+RING_FLOPS = {0: 4 * (50 + 13) + 14, 1: 4 * 15 + 3 * 8 + 6, 2: 4 * (6 * 34 + 40) + 3 * 16 + 12,
+              3: 4 * (50 + 16) + 3 * 8 + 6}
 # Cube (Kuramoto): per stage the x, y and z passes move 32 + 32 + 72 bytes per
 # node; FP64 flops as the Kuramoto ring.
 CUBE_BYTES = 544
-CUBE_FLOPS = RING_FLOPS[0]
 # Ball / disk lattices: per stage the x pass reads (sin, cos) and writes the row
 # prefixes (32 B per node); the gather reads each prefix once from HBM (16 B; the
 # chord reads re-hit L1/L2), the stage-input (sin, cos) (16 B), y, acc and the
@@ -61,7 +61,8 @@ def parse():
     ap.add_argument("--chunk", type=int, default=100, help="RK4 steps per timed iteration")
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--model", type=int, default=1)
-    ap.add_argument("--topo", type=int, default=0, help="0 ring, 1 periodic cubic lattice (Kuramoto; N = edge)")
+    ap.add_argument("--topo", type=int, default=0,
+                    help="0 ring; lattices (Kuramoto models, N = edge N1, radius floor(r N1)): 1 cube, 2 ball, 3 disk")
     ap.add_argument("--N", type=int, default=10 ** 6)
     ap.add_argument("--r", type=float, default=0.35)
     ap.add_argument("--dt", type=float, default=0.01)
@@ -77,19 +78,22 @@ def parse():
 def workload(args):
     N = args.N
     R = max(1, min((N - 1) // 2, int(math.floor(args.r * N))))
-    if args.topo == 1:
+    if args.model == 3:
+        return N, R, I.ksi_params()
+    if args.topo != 0:
         return N, R, I.ks_params(alpha=1.52)
     params = {0: I.ks_params(alpha=1.46), 1: I.fhn_params(), 2: I.hh_params()}[args.model]
     return N, R, params
 
 
 def nodes_of(args, N):
-    return N ** 3 if args.topo == 1 else N
+    return N ** 3 if args.topo in (1, 2) else N * N if args.topo == 3 else N
 
 
 def config_of(args, N, R):
-    name = (f"Kuramoto-Sakaguchi periodic cubic lattice, N1={N} ({N ** 3} nodes), P={R}, RK4 dt={args.dt}"
-            if args.topo == 1 else f"{MODEL_NAMES[args.model]} ring, N={N}, R={R}, RK4 dt={args.dt}")
+    name = (f"{MODEL_NAMES[args.model]} {TOPO_NAMES[args.topo]}, N1={N} ({nodes_of(args, N)} nodes), P={R}, "
+            f"RK4 dt={args.dt}" if args.topo != 0 else
+            f"{MODEL_NAMES[args.model]} ring, N={N}, R={R}, RK4 dt={args.dt}")
     return {
         "workload": name,
         "N": N, "R": R, "dt": args.dt,
@@ -439,11 +443,11 @@ def run_native(args):
     torch.cuda.set_device(local)
     from paper_2410_19075_gb300 import Network
 
-    if args.topo == 1:
+    if args.topo != 0 and args.model not in (0, 3):
         args.model = 0
     N, R, params = workload(args)
     nodes = nodes_of(args, N)
-    d = {0: 1, 1: 2, 2: 4}[args.model]
+    d = {0: 1, 1: 2, 2: 4, 3: 2}[args.model]
     stream = torch.cuda.current_stream()
     y0_host = I.initial_state(args.model, 2412, rank, nodes)
     npar = I.hh_iext(2412, rank, N) if args.model == 2 else None
@@ -511,11 +515,11 @@ def run_native(args):
     state_bytes = 8 * d * nodes
 
     # --- dominant kernel: the ring stage kernel (4 launches per RK4 step); for
-    # the cube the three passes of a stage are counted together as one launch
+    # the lattices the passes of a stage are counted together as one launch
     launches = 4 * args.steps
     avg_launch_s = ms * 1e-3 / launches
-    bytes_ns = CUBE_BYTES if args.topo == 1 else RING_BYTES[args.model]
-    flops_ns = CUBE_FLOPS if args.topo == 1 else RING_FLOPS[args.model]
+    bytes_ns = {0: RING_BYTES.get(args.model), 1: CUBE_BYTES}.get(args.topo, LATTICE_BYTES.get(args.model))
+    flops_ns = RING_FLOPS[args.model]
     alg_bytes_launch = bytes_ns / 4 * nodes
     alg_flops_launch = flops_ns / 4 * nodes
     peaks = {}
@@ -541,7 +545,7 @@ def run_native(args):
             "e2e": {"value": e2e_value, "unit": "node-steps/s",
                     "h2d_bytes_per_step": state_bytes / max(1, e2e_chunks[0]),
                     "d2h_bytes_per_step": state_bytes / max(1, e2e_chunks[0])},
-            "gpu_launches": launches * (3 if args.topo == 1 else 1), "roofline": roofline, "clocks": clk}
+            "gpu_launches": launches * {0: 1, 1: 3}.get(args.topo, 2), "roofline": roofline, "clocks": clk}
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.topo == 0:
         line["cpu_baseline"] = cpu_baseline(args, N, R, params, args.cpu_seconds)
     if not args.no_extra and args.topo == 0 and world == 1:

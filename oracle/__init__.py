@@ -10,6 +10,9 @@ What it computes (each function cites the passage it follows):
                     Algorithm 1; FitzHugh-Nagumo Eq. (2) with a rotational coupling
                     matrix; Hodgkin-Huxley Eq. (1) as the classic 4-variable neuron.
   * ``rk4``      -- classic fixed-step fourth-order Runge-Kutta over the network.
+  * ``dp5``      -- adaptive Dormand-Prince 5(4) (the paper's default solver,
+                    Section III.A) with the textbook step-size controller and cubic
+                    Hermite dense output of the order parameter (Section V).
   * ``order_parameter`` -- Kuramoto order parameter |mean exp(i phi)| (the
                     synchronization analysis of Section V).
   * ``window_sum`` -- brute-force window sums of one quantity (ring: R neighbours
@@ -45,6 +48,11 @@ def lib():
         _lib.orc_rhs_sampled.argtypes = [c_int, c_int, i64, i64, _dp, c_int, _dp, _dp, i64, _ip, _dp, c_int, c_int]
         _lib.orc_links.argtypes = [c_int, i64, i64, c_int]
         _lib.orc_links.restype = i64
+        _lib.orc_dp5.argtypes = [c_int, c_int, i64, i64, _dp, c_int, _dp, _dp, c_double, c_double, c_double,
+                                 c_double, c_double, c_double, c_double, i64, _dp, _ip, _dp, c_int, c_int]
+        _lib.orc_dp5_tableau.argtypes = [_dp, _dp, _dp, _dp]
+        _lib.orc_dp5_n_out.argtypes = [c_double, c_double, c_double]
+        _lib.orc_dp5_n_out.restype = i64
         _lib.orc_order_parameter.argtypes = [i64, _dp]
         _lib.orc_order_parameter.restype = c_double
         for name in ("orc_hh_alpha_m", "orc_hh_beta_m", "orc_hh_alpha_h", "orc_hh_beta_h",
@@ -118,6 +126,39 @@ def rk4(model, topo, N, R, params, y0, n_steps, dt, node_param=None, flags=0, th
     _check(lib().orc_rk4(model, topo, N, R, _d(p), p.size, _d(npar), _d(y), n_steps, float(dt),
                          _d(order), flags, threads), "rk4")
     return y, order
+
+
+def dp5(model, topo, N, R, params, y0, t0, t_end, rtol, atol, h0, h_max=0.0, out_dt=0.0,
+        max_attempts=10 ** 6, node_param=None, flags=0, threads=0):
+    """Adaptive Dormand-Prince 5(4) from t0 to t_end.  Returns (y, order, stats):
+    order holds R(t0) and R at t0 + k out_dt (Kuramoto models with out_dt > 0,
+    else None); stats = dict(accepted, rejected, t, h_next, status).  A status
+    of -3 (attempt budget) or -4 (step too small) is reported, not raised."""
+    y = _arr(y0, nodes_of(topo, N) * _DIM[model]).copy()
+    p = _arr(params)
+    npar = _arr(node_param, nodes_of(topo, N)) if node_param is not None else None
+    n_out = lib().orc_dp5_n_out(float(t0), float(t_end), float(out_dt))
+    order = np.empty(n_out + 1) if model in (KS, KSI) else None
+    si = np.zeros(2, dtype=np.int64)
+    sd = np.zeros(2)
+    st = lib().orc_dp5(model, topo, N, R, _d(p), p.size, _d(npar), _d(y), float(t0), float(t_end), float(rtol),
+                       float(atol), float(h0), float(h_max), float(out_dt), int(max_attempts), _d(order),
+                       si.ctypes.data_as(_ip), _d(sd), flags, threads)
+    if st not in (0, -3, -4):
+        _check(st, "dp5")
+    return y, order, {"accepted": int(si[0]), "rejected": int(si[1]), "t": float(sd[0]), "h_next": float(sd[1]),
+                      "status": int(st)}
+
+
+def dp5_tableau():
+    """(A 7x7, b, bhat, c) of the Dormand-Prince 5(4) pair the oracle uses."""
+    a, b, bh, c = np.zeros(49), np.zeros(7), np.zeros(7), np.zeros(7)
+    lib().orc_dp5_tableau(_d(a), _d(b), _d(bh), _d(c))
+    return a.reshape(7, 7), b, bh, c
+
+
+def dp5_n_out(t0, t_end, out_dt):
+    return int(lib().orc_dp5_n_out(float(t0), float(t_end), float(out_dt)))
 
 
 def window_sum(topo, N, R, f, query=None, flags=0):

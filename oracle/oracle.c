@@ -27,6 +27,11 @@
  *   - Kuramoto-Sakaguchi with inertia, Eq. (3) with m != 0, as phi' = psi,
  *     psi' = ((mu/K) sum_j sin(phi_j - phi_i - alpha) - eps psi) / m.
  *   - Kuramoto order parameter |sum_j exp(i phi_j)| / n.
+ *   - Adaptive Dormand-Prince 5(4) (the paper's default solver, Section III.A):
+ *     the published RK5(4)7M tableau, the mixed error norm and step-size
+ *     controller of the textbook, and cubic Hermite dense output (the paper
+ *     interpolates its dense output and analyses synchronisation at every
+ *     output, Section V).
  *
  * Build: gcc -O2 -std=c11 -ffp-contract=off -fopenmp -shared -fPIC (see build.py).
  * Parallelism: OpenMP over nodes only; every node's sum is computed by one thread
@@ -43,7 +48,7 @@
 enum { ORC_KS = 0, ORC_FHN = 1, ORC_HH = 2, ORC_KSI = 3 };
 enum { ORC_RING = 0, ORC_CUBE = 1, ORC_BALL = 2, ORC_DISK = 3 };
 enum { ORC_REVERSE = 1, ORC_INCLUDE_SELF = 2 };
-enum { ORC_OK = 0, ORC_EINVAL = -1, ORC_ENOMEM = -2 };
+enum { ORC_OK = 0, ORC_EINVAL = -1, ORC_ENOMEM = -2, ORC_ESTEPS = -3, ORC_ESMALL = -4 };
 
 /* Number of state variables per node. */
 int orc_dim(int model)
@@ -367,4 +372,190 @@ int orc_rhs_sampled(int model, int topo, int64_t N, int64_t R, const double *par
         free(nb);
     }
     return failed ? ORC_ENOMEM : ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Dormand-Prince 5(4) (J. R. Dormand and P. J. Prince, "A family of embedded
+ * Runge-Kutta formulae", J. Comput. Appl. Math. 6 (1980) 19-26; the RK5(4)7M
+ * pair).  Seven stages, c_7 = 1 and a_7j = b_j, so the last stage is f(y_{n+1})
+ * and serves as the first stage of the next step (first same as last). */
+static const double DP_C[7] = {0.0, 1.0 / 5.0, 3.0 / 10.0, 4.0 / 5.0, 8.0 / 9.0, 1.0, 1.0};
+static const double DP_A[7][6] = {
+    {0, 0, 0, 0, 0, 0},
+    {1.0 / 5.0, 0, 0, 0, 0, 0},
+    {3.0 / 40.0, 9.0 / 40.0, 0, 0, 0, 0},
+    {44.0 / 45.0, -56.0 / 15.0, 32.0 / 9.0, 0, 0, 0},
+    {19372.0 / 6561.0, -25360.0 / 2187.0, 64448.0 / 6561.0, -212.0 / 729.0, 0, 0},
+    {9017.0 / 3168.0, -355.0 / 33.0, 46732.0 / 5247.0, 49.0 / 176.0, -5103.0 / 18656.0, 0},
+    {35.0 / 384.0, 0.0, 500.0 / 1113.0, 125.0 / 192.0, -2187.0 / 6784.0, 11.0 / 84.0}};
+/* fifth-order weights (= the last row of A, b_7 = 0) and the embedded fourth-order ones */
+static const double DP_B[7] = {35.0 / 384.0, 0.0, 500.0 / 1113.0, 125.0 / 192.0, -2187.0 / 6784.0, 11.0 / 84.0, 0.0};
+static const double DP_BHAT[7] = {5179.0 / 57600.0, 0.0, 7571.0 / 16695.0, 393.0 / 640.0, -92097.0 / 339200.0,
+                                  187.0 / 2100.0, 1.0 / 40.0};
+
+/* The tableau, for checks of the order conditions: a is 7 x 7 row-major. */
+void orc_dp5_tableau(double *a, double *b, double *bhat, double *c)
+{
+    for (int i = 0; i < 7; ++i) {
+        for (int j = 0; j < 7; ++j) a[7 * i + j] = j < 6 ? DP_A[i][j] : 0.0;
+        b[i] = DP_B[i];
+        bhat[i] = DP_BHAT[i];
+        c[i] = DP_C[i];
+    }
+}
+
+/* Cubic Hermite interpolant on [t, t + h] from y0, y1 and the slopes f0, f1 at
+ * both ends, at theta = (s - t) / h (textbook dense output of order 3). */
+static double hermite(double y0, double y1, double f0, double f1, double h, double th)
+{
+    return (1.0 - th) * y0 + th * y1 +
+           th * (th - 1.0) * ((1.0 - 2.0 * th) * (y1 - y0) + (th - 1.0) * h * f0 + th * h * f1);
+}
+
+/* Step-size controller constants (textbook values): safety factor, smallest and
+ * largest factor per step, and the error exponent 1/5 of a 5(4) pair. */
+#define DP_SAFE 0.9
+#define DP_FACMIN 0.2
+#define DP_FACMAX 10.0
+/* At most this many dense outputs inside one step: the step is capped at
+ * DP_MAX_OUT * out_dt. */
+#define DP_MAX_OUT 8
+
+/* Number of dense-output times t0 + k out_dt, k = 1..n, with t0 + k out_dt <= t_end
+ * (up to a relative 1e-12 of the span, so that an end point on the grid counts). */
+int64_t orc_dp5_n_out(double t0, double t_end, double out_dt)
+{
+    if (!(out_dt > 0.0)) return 0;
+    return (int64_t)floor((t_end - t0) / out_dt * (1.0 + 1e-12));
+}
+
+/* Integrate y (d * nodes doubles, SoA) from t0 to t_end with the adaptive
+ * Dormand-Prince 5(4) pair.
+ *   Error of an attempted step of size h: e = h sum_j (b_j - bhat_j) k_j and
+ *     err = sqrt(mean_q (e_q / sc_q)^2),  sc_q = atol + rtol max(|y_q|, |y_new,q|);
+ *   the step is accepted when err <= 1 (a non-finite err is a rejection with
+ *   factor 0.2).  New step h * clamp(0.9 err^(-1/5), 0.2, 10),
+ *   not larger than h after a rejected attempt, and at most h_max (if > 0) and
+ *   DP_MAX_OUT * out_dt (if out_dt > 0).  The attempt that reaches t_end is cut
+ *   to t_end - t and ends exactly at t_end.
+ *   Dense output (Kuramoto models): order_out[0] = R(t0) and order_out[k] = the
+ *   order parameter of the Hermite-interpolated phases at t0 + k out_dt,
+ *   k = 1..orc_dp5_n_out(t0, t_end, out_dt).
+ *   stats (may be NULL): accepted, rejected attempts, final t, the next proposed
+ *   step (before any cut at t_end).
+ * Returns ORC_ESTEPS if max_attempts attempts did not reach t_end, ORC_ESMALL if
+ * the step fell below 1e-14 (|t| + h), leaving y at the last accepted step. */
+int orc_dp5(int model, int topo, int64_t N, int64_t R, const double *params, int n_params,
+            const double *node_param, double *y, double t0, double t_end, double rtol, double atol,
+            double h0, double h_max, double out_dt, int64_t max_attempts, double *order_out,
+            int64_t *stats_i, double *stats_d, int flags, int nthreads)
+{
+    int st = orc_validate(model, topo, N, R, n_params);
+    if (st != ORC_OK) return st;
+    if (!(t_end > t0) || !(h0 > 0.0) || rtol < 0.0 || atol < 0.0 || !(rtol > 0.0 || atol > 0.0) ||
+        h_max < 0.0 || out_dt < 0.0 || max_attempts < 1)
+        return ORC_EINVAL;
+    const int64_t nodes = orc_nodes(topo, N);
+    const int64_t len = nodes * orc_dim(model);
+    double *k[7], *tmp = malloc(sizeof(double) * (size_t)len), *ynew = malloc(sizeof(double) * (size_t)len);
+    double *phi = malloc(sizeof(double) * (size_t)nodes);
+    int bad = !tmp || !ynew || !phi;
+    for (int s = 0; s < 7; ++s) {
+        k[s] = malloc(sizeof(double) * (size_t)len);
+        bad |= !k[s];
+    }
+    if (bad) {
+        for (int s = 0; s < 7; ++s) free(k[s]);
+        free(tmp); free(ynew); free(phi);
+        return ORC_ENOMEM;
+    }
+    const int nt = set_threads(nthreads);
+    const int has_order = model == ORC_KS || model == ORC_KSI;
+    const int64_t n_out = orc_dp5_n_out(t0, t_end, out_dt);
+    double hcap = h_max > 0.0 ? h_max : INFINITY;
+    if (out_dt > 0.0 && DP_MAX_OUT * out_dt < hcap) hcap = DP_MAX_OUT * out_dt;
+    if (order_out && has_order) order_out[0] = orc_order_parameter(nodes, y);
+
+    double t = t0, h = h0 < hcap ? h0 : hcap;
+    int64_t n_acc = 0, n_rej = 0, next_out = 1;
+    int last_rejected = 0;
+    st = orc_rhs(model, topo, N, R, params, n_params, node_param, y, k[0], flags, nt);
+    while (st == ORC_OK) {
+        if (n_acc + n_rej >= max_attempts) {
+            st = ORC_ESTEPS;
+            break;
+        }
+        const int last = t_end - t <= h;
+        const double hs = last ? t_end - t : h;
+        if (!(hs > 1e-14 * (fabs(t) + hs))) {
+            st = ORC_ESMALL;
+            break;
+        }
+        /* stages 2..7: stage input y + hs sum_{j<s} a_sj k_j */
+        for (int s = 1; s < 7 && st == ORC_OK; ++s) {
+            double *xin = s == 6 ? ynew : tmp;
+            for (int64_t q = 0; q < len; ++q) {
+                double acc = 0.0;
+                for (int j = 0; j < s; ++j) acc += DP_A[s][j] * k[j][q];
+                xin[q] = y[q] + hs * acc;
+            }
+            st = orc_rhs(model, topo, N, R, params, n_params, node_param, xin, k[s], flags, nt);
+        }
+        if (st != ORC_OK) break;
+        /* error norm */
+        double sum = 0.0;
+        for (int64_t q = 0; q < len; ++q) {
+            double e = 0.0;
+            for (int j = 0; j < 7; ++j) e += (DP_B[j] - DP_BHAT[j]) * k[j][q];
+            e *= hs;
+            const double sc = atol + rtol * fmax(fabs(y[q]), fabs(ynew[q]));
+            sum += (e / sc) * (e / sc);
+        }
+        const double err = sqrt(sum / (double)len);
+        /* a non-finite error (the attempt overflowed) is a rejection with the
+         * smallest factor; a zero error takes the largest */
+        double fac = !isfinite(err) ? DP_FACMIN : err > 0.0 ? DP_SAFE * pow(err, -0.2) : DP_FACMAX;
+        fac = fac < DP_FACMIN ? DP_FACMIN : (fac > DP_FACMAX ? DP_FACMAX : fac);
+        if (err <= 1.0) {
+            /* dense output inside (t, t + hs] */
+            if (order_out && has_order) {
+                while (next_out <= n_out) {
+                    const double to = t0 + (double)next_out * out_dt;
+                    if (!last && to > t + hs) break;
+                    double th = (to - t) / hs;
+                    th = th > 1.0 ? 1.0 : th;
+                    for (int64_t q = 0; q < nodes; ++q) phi[q] = hermite(y[q], ynew[q], k[0][q], k[6][q], hs, th);
+                    order_out[next_out] = orc_order_parameter(nodes, phi);
+                    ++next_out;
+                }
+            }
+            memcpy(y, ynew, sizeof(double) * (size_t)len);
+            memcpy(k[0], k[6], sizeof(double) * (size_t)len);
+            ++n_acc;
+            double hn = h * fac;
+            if (last_rejected && hn > h) hn = h;
+            h = hn < hcap ? hn : hcap;
+            last_rejected = 0;
+            if (last) {
+                t = t_end;
+                break;
+            }
+            t = t + hs;
+        } else {
+            ++n_rej;
+            h = hs * fac;
+            last_rejected = 1;
+        }
+    }
+    if (stats_i) {
+        stats_i[0] = n_acc;
+        stats_i[1] = n_rej;
+    }
+    if (stats_d) {
+        stats_d[0] = t;
+        stats_d[1] = h;
+    }
+    for (int s = 0; s < 7; ++s) free(k[s]);
+    free(tmp); free(ynew); free(phi);
+    return st;
 }

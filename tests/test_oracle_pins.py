@@ -544,3 +544,107 @@ def test_inertia_rk4_fourth_order():
     sols = [oracle.rk4(oracle.KSI, oracle.RING, N, R, p, x, int(round(2.0 / dt)), dt)[0] for dt in (0.04, 0.02, 0.01)]
     e1, e2 = np.abs(sols[0] - sols[1]).max(), np.abs(sols[1] - sols[2]).max()
     assert 12 < e1 / e2 < 20
+
+
+# ---------------------------------------------------------------- Dormand-Prince 5(4)
+def test_dp5_tableau_satisfies_the_order_conditions():
+    """Row sums give c; the fifth-order weights satisfy all 17 order conditions of
+    order <= 5 (one per rooted tree), the embedded weights the 8 of order <= 4 but
+    not all of order 5; the last stage is the new solution (first same as last)."""
+    A, b, bh, c = oracle.dp5_tableau()
+    assert np.abs(A.sum(axis=1) - c).max() < 1e-15
+    Ac = A @ c
+    conds = [
+        (lambda w: w.sum(), 1.0), (lambda w: w @ c, 1 / 2),
+        (lambda w: w @ c ** 2, 1 / 3), (lambda w: w @ Ac, 1 / 6),
+        (lambda w: w @ c ** 3, 1 / 4), (lambda w: w @ (c * Ac), 1 / 8), (lambda w: w @ (A @ c ** 2), 1 / 12),
+        (lambda w: w @ (A @ Ac), 1 / 24),
+        (lambda w: w @ c ** 4, 1 / 5), (lambda w: w @ (c ** 2 * Ac), 1 / 10), (lambda w: w @ (c * (A @ c ** 2)), 1 / 15),
+        (lambda w: w @ (c * (A @ Ac)), 1 / 30), (lambda w: w @ Ac ** 2, 1 / 20), (lambda w: w @ (A @ c ** 3), 1 / 20),
+        (lambda w: w @ (A @ (c * Ac)), 1 / 40), (lambda w: w @ (A @ (A @ c ** 2)), 1 / 60),
+        (lambda w: w @ (A @ (A @ Ac)), 1 / 120),
+    ]
+    for f, v in conds:
+        assert abs(f(b) - v) < 1e-14
+    for f, v in conds[:8]:
+        assert abs(f(bh) - v) < 1e-14
+    assert max(abs(f(bh) - v) for f, v in conds[8:]) > 1e-4
+    assert np.abs(A[6, :6] - b[:6]).max() == 0 and b[6] == 0 and c[6] == 1
+
+
+def test_dp5_constant_drift_is_exact_and_steps_grow_tenfold():
+    """mu = 0: phi' = omega exactly; the error estimate vanishes, so every accepted
+    step grows by the largest factor (10) until the last one is cut at t_end."""
+    N, R = 40, 5
+    y0 = I.ks_phases(30, 0, N)
+    y, order, st = oracle.dp5(oracle.KS, oracle.RING, N, R, [0.7, 0.0, 1.46], y0, 0.0, 100.0, 1e-9, 1e-9, 0.01)
+    assert np.abs(y - (y0 + 70.0)).max() < 1e-12
+    # steps 0.01, 0.1, 1, 10, then the rest (88.89) cut at t_end
+    assert st == {"accepted": 5, "rejected": 0, "t": 100.0, "h_next": 1000.0, "status": 0}
+
+
+def test_dp5_damped_rotation_closed_form_and_dense_output():
+    """Inertia model with mu = 0: psi' = -(eps/m) psi, so psi = psi0 e^{-eps t/m},
+    phi = phi0 + psi0 (m/eps)(1 - e^{-eps t/m}); the dense-output order parameter
+    at t = k/2 matches the one of the exact phases."""
+    N, R = 64, 3
+    m, eps = 1.0, 0.5
+    y0 = np.concatenate([I.ks_phases(31, 0, N), I.uniform(31, 0, 5, N, -1, 1)])
+    y, order, st = oracle.dp5(oracle.KSI, oracle.RING, N, R, [m, eps, 0.0, 0.45], y0, 0.0, 6.0, 1e-11, 1e-11, 0.05,
+                              out_dt=0.5)
+    assert st["status"] == 0 and st["t"] == 6.0
+    ex = lambda t: (y0[:N] + y0[N:] * (m / eps) * (1 - math.exp(-eps * t / m)), y0[N:] * math.exp(-eps * t / m))
+    phi, psi = ex(6.0)
+    assert np.abs(y[:N] - phi).max() < 1e-9 and np.abs(y[N:] - psi).max() < 1e-9
+    assert order.size == 13
+    for k in range(13):
+        assert abs(order[k] - oracle.order_parameter(ex(0.5 * k)[0])) < 1e-8
+
+
+def test_dp5_agrees_with_fine_rk4():
+    N, R = 60, 12
+    params = I.ks_params(omega=0.2, alpha=1.3)
+    y0 = I.ks_phases(32, 0, N)
+    y, _, st = oracle.dp5(oracle.KS, oracle.RING, N, R, params, y0, 0.0, 5.0, 1e-12, 1e-12, 0.01)
+    ref, _ = oracle.rk4(oracle.KS, oracle.RING, N, R, params, y0, 5000, 1e-3)
+    assert st["status"] == 0 and st["rejected"] == 0
+    assert np.abs(y - ref).max() < 1e-9
+
+
+def test_dp5_rejects_oversized_steps_and_stays_accurate():
+    """A first trial step far too large for the FitzHugh-Nagumo ring (eps = 0.05)
+    is rejected and shrunk; the result still matches a fine RK4 run."""
+    N, R = 50, 10
+    params = I.fhn_params()
+    y0 = I.fhn_state(33, 0, N)
+    y, _, st = oracle.dp5(oracle.FHN, oracle.RING, N, R, params, y0, 0.0, 2.0, 1e-10, 1e-10, 1.0)
+    ref, _ = oracle.rk4(oracle.FHN, oracle.RING, N, R, params, y0, 20000, 1e-4)
+    assert st["status"] == 0 and st["rejected"] >= 1
+    assert np.abs(y - ref).max() < 1e-7
+
+
+def test_dp5_tolerance_controls_the_error():
+    """Global error shrinks with the tolerance (tol^(4/5)-like for a 5(4) pair)."""
+    N, R = 40, 8
+    params = I.hh_params()
+    y0 = I.hh_state(34, 0, N)
+    iext = I.hh_iext(34, 0, N)
+    ref, _, _ = oracle.dp5(oracle.HH, oracle.RING, N, R, params, y0, 0.0, 10.0, 1e-13, 1e-13, 0.001, node_param=iext)
+    errs = []
+    for tol in (1e-6, 1e-8, 1e-10):
+        y, _, st = oracle.dp5(oracle.HH, oracle.RING, N, R, params, y0, 0.0, 10.0, tol, tol, 0.001, node_param=iext)
+        assert st["status"] == 0
+        errs.append(np.abs(y - ref).max())
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[2] < 1e-6
+
+
+def test_dp5_attempt_budget_and_bad_arguments():
+    y0 = I.ks_phases(35, 0, 30)
+    y, _, st = oracle.dp5(oracle.KS, oracle.RING, 30, 5, I.ks_params(), y0, 0.0, 50.0, 1e-10, 1e-10, 0.001,
+                          max_attempts=3)
+    assert st["status"] == -3 and st["accepted"] == 3 and 0 < st["t"] < 50.0
+    with pytest.raises(ValueError):
+        oracle.dp5(oracle.KS, oracle.RING, 30, 5, I.ks_params(), y0, 1.0, 1.0, 1e-10, 1e-10, 0.01)
+    with pytest.raises(ValueError):
+        oracle.dp5(oracle.KS, oracle.RING, 30, 5, I.ks_params(), y0, 0.0, 1.0, 0.0, 0.0, 0.01)
