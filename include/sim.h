@@ -78,7 +78,9 @@ typedef enum {
     SIM_EDEVICE = -3,     /* a CUDA call failed; the message says which */
     SIM_ETIMEOUT = -4,    /* a bounded device-side wait gave up; results are invalid */
     SIM_ENONFINITE = -5,  /* the state left the representable range (NaN, Inf or overflow) */
-    SIM_EBUSY = -6        /* the handle is in use (e.g. captured) */
+    SIM_EBUSY = -6,       /* the handle is in use (e.g. captured) */
+    SIM_ESTEPS = -7,      /* Dormand-Prince: the attempt budget ran out before t_end */
+    SIM_ESMALL = -8       /* Dormand-Prince: the step size fell below the resolution of t */
 } sim_status;
 
 /* Creation flags. */
@@ -158,6 +160,49 @@ int sim_sync(sim_t h);
 int64_t sim_steps_done(sim_t h);
 
 /* ---------------------------------------------------------------------------
+ * Adaptive Dormand-Prince 5(4) (Section III.A: the paper's default solver is a
+ * Dormand-Prince method with step-size control; Section V: the solution is
+ * interpolated for dense output and synchronisation is analysed at every
+ * output).  Ring networks only (every model).
+ *
+ * Method: the RK5(4)7M pair of Dormand and Prince (1980), first same as last
+ * (six right-hand sides per attempted step).  Error of an attempt of size h:
+ * e = h sum_j (b_j - bhat_j) k_j, err = sqrt(mean over all d * N values of
+ * (e / sc)^2) with sc = atol + rtol max(|y_n|, |y_n+1|).  Accepted when err <= 1
+ * (a non-finite err is a rejection).  Next step h * clamp(0.9 err^(-1/5), 0.2, 10),
+ * not growing right after a rejection, and at most h_max and 8 * out_dt.  The
+ * attempt that reaches t_end is cut to end there exactly.  Every decision is
+ * taken on the device; the host only waits for the run to end.
+ * Dense output (SIM_KS, SIM_KSI): the order parameter of the cubic Hermite
+ * interpolant of the phases (from y_n, y_n+1 and their slopes) at
+ * t0 + k out_dt, k = 1 .. floor((t_end - t0) / out_dt (1 + 1e-12)); together with
+ * R(t0) these values are appended to the record sim_observables() returns.
+ * The state is integrated in place: after the call the handle holds y(t), t as
+ * reported in the stats.  The first call on a handle allocates its
+ * Dormand-Prince buffers (7 d N doubles and per-sub-tile sums). */
+typedef struct {
+    double t0, t_end;   /* integrate from t0 to t_end > t0 */
+    double rtol, atol;  /* >= 0, not both 0 */
+    double h0;          /* first trial step, > 0 */
+    double h_max;       /* largest step; 0 = no limit */
+    double out_dt;      /* dense-output interval; 0 = none */
+    int64_t max_attempts; /* accepted + rejected attempts allowed, >= 1 */
+} sim_dp5_opts;
+
+typedef struct {
+    int64_t accepted, rejected;
+    double t;       /* time reached: t_end unless status != 0 */
+    double h_next;  /* the next proposed step size (before any cut at t_end) */
+    int status;     /* SIM_OK, SIM_ESTEPS or SIM_ESMALL */
+} sim_dp5_stats;
+
+/* One ring network.  Returns SIM_OK, the run's SIM_ESTEPS / SIM_ESMALL (the state
+ * is then that of the last accepted step, stats->t), SIM_EINVAL (not a ring,
+ * invalid options), SIM_ENOMEM, or a device error.  stats may be NULL.
+ * Synchronises the handle's stream. */
+int sim_dp5(sim_t h, const sim_dp5_opts *opts, sim_dp5_stats *stats);
+
+/* ---------------------------------------------------------------------------
  * Batches: many independent networks advanced together (the paper's "large
  * number of small unconnected subnets within a single run", Section III.C, and
  * its parameter and multistability studies, Section IV).  Ring members of the
@@ -184,6 +229,14 @@ int sim_batch_set_budgets(sim_batch_t b, const int64_t *steps);
 /* Advance every member by n_steps RK4 steps of size dt (asynchronous; CUDA
  * graphs of 16 steps).  sim_steps_done() of each member is updated. */
 int sim_batch_step(sim_batch_t b, int64_t n_steps, double dt);
+
+/* Dormand-Prince runs of every member (all must be rings), each with its own
+ * options opts[i], tolerances, step sizes and decisions; every attempt of every
+ * unfinished member is one set of launches per model group.  stats[i] gets each
+ * member's outcome (status SIM_OK, SIM_ESTEPS or SIM_ESMALL).  Returns SIM_OK
+ * unless the arguments, an allocation or the device failed.  Results are those
+ * of sim_dp5 on each member alone. */
+int sim_batch_dp5(sim_batch_t b, const sim_dp5_opts *opts, sim_dp5_stats *stats);
 
 /* Wait for the batch's work and report the first device error of any member. */
 int sim_batch_sync(sim_batch_t b);

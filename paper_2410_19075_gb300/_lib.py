@@ -11,8 +11,20 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsim.so")
 
 SIM_OK, SIM_EINVAL, SIM_ENOMEM, SIM_EDEVICE, SIM_ETIMEOUT, SIM_ENONFINITE, SIM_EBUSY = 0, -1, -2, -3, -4, -5, -6
+SIM_ESTEPS, SIM_ESMALL = -7, -8
 STATUS_NAMES = {0: "SIM_OK", -1: "SIM_EINVAL", -2: "SIM_ENOMEM", -3: "SIM_EDEVICE", -4: "SIM_ETIMEOUT",
-                -5: "SIM_ENONFINITE", -6: "SIM_EBUSY"}
+                -5: "SIM_ENONFINITE", -6: "SIM_EBUSY", -7: "SIM_ESTEPS", -8: "SIM_ESMALL"}
+
+
+class DP5Opts(ctypes.Structure):
+    _fields_ = [("t0", ctypes.c_double), ("t_end", ctypes.c_double), ("rtol", ctypes.c_double),
+                ("atol", ctypes.c_double), ("h0", ctypes.c_double), ("h_max", ctypes.c_double),
+                ("out_dt", ctypes.c_double), ("max_attempts", ctypes.c_int64)]
+
+
+class DP5Stats(ctypes.Structure):
+    _fields_ = [("accepted", ctypes.c_int64), ("rejected", ctypes.c_int64), ("t", ctypes.c_double),
+                ("h_next", ctypes.c_double), ("status", ctypes.c_int)]
 
 
 class SimError(RuntimeError):
@@ -55,6 +67,8 @@ SIGNATURES = {
     "sim_math_eval": (_int, [_int, _vp, _vp, _i64]),
     "sim_ring_step_noalloc": (_int, [_int, _i64, _i64, _dp, _int, _uint, _vp, _vp, _i64, _dbl, _vp]),
     "sim_steps_done": (_i64, [_vp]),
+    "sim_dp5": (_int, [_vp, ctypes.POINTER(DP5Opts), ctypes.POINTER(DP5Stats)]),
+    "sim_batch_dp5": (_int, [_vp, ctypes.POINTER(DP5Opts), ctypes.POINTER(DP5Stats)]),
     "sim_last_error": (ctypes.c_char_p, []),
     "sim_destroy": (None, [_vp]),
 }

@@ -54,6 +54,53 @@ struct RingBatchGroup {
 // Batched ring stage kernels: one RK4 step of every member of the group.
 cudaError_t ring_batch_step(const RingBatchGroup &g, double dt, cudaStream_t s);
 
+// Adaptive Dormand-Prince 5(4) on rings (dp5.cu), per instance in a batch.
+constexpr int kDpMaxOut = 16; // dense outputs handled inside one step (the step is capped at 8 of them)
+constexpr int kDpStatusSteps = -7, kDpStatusSmall = -8; // = SIM_ESTEPS, SIM_ESMALL
+
+// Step control of one instance (device memory; written by the host before a
+// run and by the deciding CTA of every attempt).
+struct DpCtl {
+    double t, t_end, t0, out_dt;
+    double h;      // proposed step
+    double h_att;  // step of the current attempt (h, or t_end - t for the last one)
+    double hcap;   // largest step: h_max and 8 out_dt
+    double rtol, atol;
+    long long n_acc, n_rej, max_att, n_out, next_out;
+    int last;      // the current attempt ends at t_end
+    int last_rej;  // the previous attempt was rejected
+    int cur;       // which of the two state / first-stage buffers holds y_n, k_1
+    int done;      // 1: finished (t_end reached or status set)
+    int status;    // 0, or the sim_status that ended the run
+    int bad;       // a stage input of the current attempt left the fixed-point range
+};
+
+struct DpPlan {
+    RingPlan r;              // prefix buffers, local-variable buffers, observables; r.y = ybuf[0]
+    double *ybuf[2];         // D * N each: y_n and the candidate y_{n+1}
+    double *k[7];            // D * N each: k[0], k[1] first-same-as-last pair, k[2..6] stages 2..6
+    DpCtl *ctl;
+    double *err_part;        // nsub: per-sub-tile sums of (e / sc)^2
+    long long *out_part;     // nsub * kDpMaxOut * 2: per-sub-tile fixed-point sums of the dense sin, cos
+    unsigned long long *dp_ctr; // arrival counter of the decision
+    int *remaining;          // instances of the run not done yet (shared by the run)
+};
+
+struct DpGroup {
+    int model;
+    int n_inst;
+    int64_t n_items;
+    const DpPlan *plans;
+    const int *inst_of_item;
+    const int64_t *item_base;
+};
+
+// Kernel ds of one attempt for every instance of the group: 1 = first right-hand
+// side of a run and the input of stage 2; 2..6 = stages 2..6; 7 = stage 7, the
+// error norm, dense output and the decision; 0 = the input of stage 2 of the
+// next attempt.
+cudaError_t dp_launch(int ds, const DpGroup &g, cudaStream_t s);
+
 // Ring: f(y) -> lam[0], ofs[0] and the order parameter of y (Kuramoto).
 cudaError_t ring_prologue(const RingPlan &p, cudaStream_t s);
 // Small rings (N <= kClusterMaxNodes): all stages of n_steps RK4 steps in one

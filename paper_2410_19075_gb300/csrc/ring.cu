@@ -14,7 +14,7 @@
 //       64 sub-tiles scans that group, and the last group scans the groups;
 //   a6  (stage 4) the Kuramoto order parameter of y_{n+1} from the global totals.
 // The prologue kernel does a1/a2/a6 for the initial state.
-#include "internal.h"
+#include "ring_parts.cuh"
 
 namespace simk {
 
@@ -51,30 +51,6 @@ __host__ __device__ __forceinline__ RingStageIO stage_io(const RingPlan &p)
     return a;
 }
 
-__device__ __forceinline__ i128 ldg_i128(const i128 *p)
-{
-    const longlong2 v = __ldg(reinterpret_cast<const longlong2 *>(p));
-    return (i128)(u128)(unsigned long long)v.x | ((i128)v.y << 64);
-}
-
-__device__ __forceinline__ i128 warp_incl_scan_i128(i128 v)
-{
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const i128 t = shfl_up_i128(v, o);
-        if (lane >= o) v += t;
-    }
-    return v;
-}
-
-// Resident CTAs per SM the register allocation is sized for (256 threads each).
-#ifndef SIM_RING_MIN_BLOCKS
-#define SIM_RING_MIN_BLOCKS 6
-#endif
-template <int M> struct MinBlocks { static constexpr int value = SIM_RING_MIN_BLOCKS; };
-template <> struct MinBlocks<2> { static constexpr int value = 2; };
-
 // One 256-node sub-tile `sub` of ring P, one node per thread (the whole CTA).
 template <int M, int STAGE>
 __device__ __forceinline__ void ring_stage_body(const RingPlan &P, const RingStageIO &a, double dt, int64_t sub)
@@ -82,55 +58,12 @@ __device__ __forceinline__ void ring_stage_body(const RingPlan &P, const RingSta
     using Mo = Model<M>;
     constexpr int D = Mo::D, NQ = Mo::NQ, NX = Mo::NX;
     constexpr int XOFF = D - NX; // first local (non-coupled) state variable
-    constexpr int NW = kRingThreads / 32;
-    __shared__ int64_t s_wtot[NW][NQ];
-    __shared__ int s_last;
+    __shared__ RingBases<NQ> s_bases;
 
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t N = P.N, nsub = P.nsub, ngroups = P.ngroups;
+    const int tid = threadIdx.x;
+    const int64_t N = P.N;
     const int64_t i = sub * kSubTile + tid;
-
-    // Window bases of this CTA: the right ends b = i+R+1 (side 0) and left ends
-    // a = i-R (side 1) of its nodes are consecutive, and each side covers at most
-    // three pieces (split at a sub-tile start and at N).  Per piece: its first
-    // position on the periodic extension, the multiple of N to subtract, and the
-    // exact prefix at its sub-tile's start (+ q * total).  Then every node needs
-    // one in-sub-tile prefix load per end.
-    __shared__ i128 s_base[2][3][NQ];
-    __shared__ int64_t s_start[2][3], s_qn[2][3];
-    if (STAGE > 0) {
-        if (tid < 2) {
-            const int side = tid;
-            const int64_t nvalid = N - sub * kSubTile < kSubTile ? N - sub * kSubTile : kSubTile;
-            const int64_t p0 = side == 0 ? sub * kSubTile + P.R + 1 : sub * kSubTile - P.R;
-            const int64_t p1 = p0 + nvalid - 1; // in [-N, 2N)
-            int64_t p = p0;
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                if (p > p1) {
-                    s_start[side][k] = INT64_MAX;
-                    s_qn[side][k] = 0;
-                    continue;
-                }
-                const int q = p < 0 ? -1 : (p >= N ? 1 : 0);
-                const int64_t qn = q * N, pp = p - qn;
-                const int64_t st = pp >> kSubLog2;
-                int64_t end = ((st + 1) << kSubLog2) - 1;
-                if (end > N - 1) end = N - 1;
-#pragma unroll
-                for (int c = 0; c < NQ; ++c) {
-                    const i128 *grpofs = a.grpofs_in + c * (ngroups + 1);
-                    const i128 tot = ldg_i128(grpofs + ngroups);
-                    s_base[side][k][c] = ldg_i128(grpofs + (st >> kGroupLog2)) + ldg_i128(a.ingrp_in + c * nsub + st) +
-                                         (q < 0 ? -tot : (q > 0 ? tot : (i128)0));
-                }
-                s_start[side][k] = p;
-                s_qn[side][k] = qn;
-                p = end + qn + 1;
-            }
-        }
-        __syncthreads();
-    }
+    if (STAGE > 0) ring_load_bases<NQ>(P, a.ingrp_in, a.grpofs_in, sub, s_bases);
 
     int64_t qv[NQ];
     bool ok = true;
@@ -142,23 +75,10 @@ __device__ __forceinline__ void ring_stage_body(const RingPlan &P, const RingSta
 #pragma unroll
             for (int v = 0; v < D; ++v) xn[v] = P.y[v * N + i];
         } else {
-            const int64_t b = i + P.R + 1, am = i - P.R;
-            const int kb = (b >= s_start[0][1]) + (b >= s_start[0][2]);
-            const int ka = (am >= s_start[1][1]) + (am >= s_start[1][2]);
-            const int64_t bp = b - s_qn[0][kb], ap = am - s_qn[1][ka];
             int64_t qo[NQ];
             double fo[NQ];
             i128 W[NQ];
-#pragma unroll
-            for (int c = 0; c < NQ; ++c) {
-                const int64_t *lam = a.lam_in + c * N;
-                const int64_t l = __ldg(lam + i);
-                qo[c] = tid ? l - __ldg(lam + i - 1) : l; // tid = position in the sub-tile
-                fo[c] = fixed_to_double(qo[c], P.F);
-                const int64_t lb = (bp & (kSubTile - 1)) ? __ldg(lam + bp - 1) : 0;
-                const int64_t la = (ap & (kSubTile - 1)) ? __ldg(lam + ap - 1) : 0;
-                W[c] = (s_base[0][kb][c] - s_base[1][ka][c]) + (i128)(lb - la);
-            }
+            ring_window<NQ>(P, a.lam_in, s_bases, tid, i, qo, fo, W);
             double X[NX > 0 ? NX : 1];
 #pragma unroll
             for (int g = 0; g < NX; ++g) X[g] = a.x_in[g * N + i];
@@ -195,69 +115,8 @@ __device__ __forceinline__ void ring_stage_body(const RingPlan &P, const RingSta
         for (int c = 0; c < NQ; ++c) qv[c] = to_fixed(f[c], P.F, P.lim, ok);
     }
     if (!ok) raise_error(P.err, ERR_RANGE);
-
-    // Exact inclusive prefix inside the sub-tile (warp scans + preceding warps).
-#pragma unroll
-    for (int c = 0; c < NQ; ++c) {
-        qv[c] = warp_incl_scan(qv[c]);
-        if (lane == 31) s_wtot[warp][c] = qv[c];
-    }
-    __syncthreads();
-#pragma unroll
-    for (int c = 0; c < NQ; ++c) {
-        int64_t off = 0;
-        for (int w = 0; w < warp; ++w) off += s_wtot[w][c];
-        if (i < N) a.lam_out[c * N + i] = off + qv[c];
-    }
-
-    // Level 1: the last CTA of each group of 64 sub-tiles scans the group.
-    const int64_t g = sub >> kGroupLog2, s0 = g << kGroupLog2;
-    const int64_t gsize = nsub - s0 < kGroup ? nsub - s0 : kGroup;
-    if (tid == 0) {
-#pragma unroll
-        for (int c = 0; c < NQ; ++c) {
-            int64_t t = 0;
-            for (int w = 0; w < NW; ++w) t += s_wtot[w][c];
-            P.subtot[c * nsub + sub] = t;
-        }
-        __threadfence();
-        s_last = last_arrival(P.grp_ctr + g, (unsigned long long)gsize);
-    }
-    __syncthreads();
-    if (!s_last) return;
-    if (warp == 0) {
-#pragma unroll
-        for (int c = 0; c < NQ; ++c) {
-            const int64_t *st = P.subtot + c * nsub + s0;
-            const i128 v0 = 2 * lane < gsize ? (i128)__ldcg(st + 2 * lane) : (i128)0;
-            const i128 v1 = 2 * lane + 1 < gsize ? (i128)__ldcg(st + 2 * lane + 1) : (i128)0;
-            const i128 x = warp_incl_scan_i128(v0 + v1);
-            const i128 ex = x - v0 - v1;
-            i128 *ig = a.ingrp_out + c * nsub + s0;
-            if (2 * lane < gsize) st_i128(ig + 2 * lane, ex);
-            if (2 * lane + 1 < gsize) st_i128(ig + 2 * lane + 1, ex + v0);
-            if (lane == 31) st_i128(P.grptot + c * ngroups + g, x);
-        }
-        __threadfence();
-    }
-    __syncthreads();
-    if (tid == 0) s_last = last_arrival(P.top_ctr, (unsigned long long)ngroups);
-    __syncthreads();
-    if (!s_last) return;
-
-    // Level 2: the last group scans the group totals (and records the totals).
-    i128 total[NQ];
-#pragma unroll
-    for (int c = 0; c < NQ; ++c)
-        total[c] = block_exclusive_scan<8>(P.grptot + c * ngroups, a.grpofs_out + c * (ngroups + 1), ngroups);
-    if ((M == 0 || M == 3) && (STAGE == 0 || STAGE == 4) && tid == 0) {
-        const double S = fixed_to_double(total[0], P.F);
-        const double C = fixed_to_double(total[NQ - 1], P.F);
-        const unsigned long long n = *P.obs_ctr;
-        P.obs[n % (unsigned long long)P.obs_cap] = sqrt(S * S + C * C) / (double)N;
-        *P.obs_ctr = n + 1;
-    }
-    if (STAGE == 4 && tid == 0 && P.steps_left) *P.steps_left -= 1;
+    ring_prefix_tail<NQ, (M == 0 || M == 3) && (STAGE == 0 || STAGE == 4), STAGE == 4>(P, a.lam_out, a.ingrp_out,
+                                                                                     a.grpofs_out, sub, i, qv);
 }
 
 // Plain path: one ring, one sub-tile per CTA.

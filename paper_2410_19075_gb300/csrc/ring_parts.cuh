@@ -1,0 +1,196 @@
+// Building blocks of the ring stage kernels (RK4 in ring.cu, Dormand-Prince in
+// dp5.cu): one CTA works on one 256-node sub-tile of a ring.
+//
+//   ring_load_bases   per-CTA window bases: the exact prefix at the start of
+//                     every piece (split at sub-tile starts and at N) that the
+//                     window ends of this CTA's nodes fall in;
+//   ring_window       one node's exact window sums W = P(i+R+1) - P(i-R) and its
+//                     own fixed-point coupled quantity, from the prefix arrays the
+//                     previous kernel wrote (two shifted in-sub-tile reads);
+//   ring_prefix_tail  the exact prefix of the next coupled quantity inside the
+//                     sub-tile and, without any CTA waiting for another, at every
+//                     sub-tile start: the last CTA to finish in each group of 64
+//                     sub-tiles scans that group, and the last group scans the
+//                     groups (and may record the Kuramoto order parameter).
+#pragma once
+#include "internal.h"
+
+namespace simk {
+
+__device__ __forceinline__ i128 ldg_i128(const i128 *p)
+{
+    const longlong2 v = __ldg(reinterpret_cast<const longlong2 *>(p));
+    return (i128)(u128)(unsigned long long)v.x | ((i128)v.y << 64);
+}
+
+__device__ __forceinline__ i128 warp_incl_scan_i128(i128 v)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const i128 t = shfl_up_i128(v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// Resident CTAs per SM the register allocation is sized for (256 threads each).
+#ifndef SIM_RING_MIN_BLOCKS
+#define SIM_RING_MIN_BLOCKS 6
+#endif
+template <int M> struct MinBlocks { static constexpr int value = SIM_RING_MIN_BLOCKS; };
+template <> struct MinBlocks<2> { static constexpr int value = 2; };
+
+// Window bases of one CTA: the right ends b = i+R+1 (side 0) and left ends
+// a = i-R (side 1) of its nodes are consecutive, and each side covers at most
+// three pieces (split at a sub-tile start and at N).  Per piece: its first
+// position on the periodic extension, the multiple of N to subtract, and the
+// exact prefix at its sub-tile's start (+ q * total).  Then every node needs one
+// in-sub-tile prefix load per end.
+template <int NQ> struct RingBases {
+    i128 base[2][3][NQ];
+    int64_t start[2][3], qn[2][3];
+};
+
+// Called by every thread of the CTA (contains a __syncthreads).
+template <int NQ>
+__device__ __forceinline__ void ring_load_bases(const RingPlan &P, const i128 *ingrp_in, const i128 *grpofs_in,
+                                                int64_t sub, RingBases<NQ> &B)
+{
+    const int tid = threadIdx.x;
+    const int64_t N = P.N, nsub = P.nsub, ngroups = P.ngroups;
+    if (tid < 2) {
+        const int side = tid;
+        const int64_t nvalid = N - sub * kSubTile < kSubTile ? N - sub * kSubTile : kSubTile;
+        const int64_t p0 = side == 0 ? sub * kSubTile + P.R + 1 : sub * kSubTile - P.R;
+        const int64_t p1 = p0 + nvalid - 1; // in [-N, 2N)
+        int64_t p = p0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            if (p > p1) {
+                B.start[side][k] = INT64_MAX;
+                B.qn[side][k] = 0;
+                continue;
+            }
+            const int q = p < 0 ? -1 : (p >= N ? 1 : 0);
+            const int64_t qn = q * N, pp = p - qn;
+            const int64_t st = pp >> kSubLog2;
+            int64_t end = ((st + 1) << kSubLog2) - 1;
+            if (end > N - 1) end = N - 1;
+#pragma unroll
+            for (int c = 0; c < NQ; ++c) {
+                const i128 *grpofs = grpofs_in + c * (ngroups + 1);
+                const i128 tot = ldg_i128(grpofs + ngroups);
+                B.base[side][k][c] = ldg_i128(grpofs + (st >> kGroupLog2)) + ldg_i128(ingrp_in + c * nsub + st) +
+                                     (q < 0 ? -tot : (q > 0 ? tot : (i128)0));
+            }
+            B.start[side][k] = p;
+            B.qn[side][k] = qn;
+            p = end + qn + 1;
+        }
+    }
+    __syncthreads();
+}
+
+// Node i (position tid in its sub-tile): its own coupled quantity (fixed point
+// qo and its double fo) and the exact window sums W of every coupled quantity.
+template <int NQ>
+__device__ __forceinline__ void ring_window(const RingPlan &P, const int64_t *lam_in, const RingBases<NQ> &B, int tid,
+                                            int64_t i, int64_t (&qo)[NQ], double (&fo)[NQ], i128 (&W)[NQ])
+{
+    const int64_t N = P.N;
+    const int64_t b = i + P.R + 1, am = i - P.R;
+    const int kb = (b >= B.start[0][1]) + (b >= B.start[0][2]);
+    const int ka = (am >= B.start[1][1]) + (am >= B.start[1][2]);
+    const int64_t bp = b - B.qn[0][kb], ap = am - B.qn[1][ka];
+#pragma unroll
+    for (int c = 0; c < NQ; ++c) {
+        const int64_t *lam = lam_in + c * N;
+        const int64_t l = __ldg(lam + i);
+        qo[c] = tid ? l - __ldg(lam + i - 1) : l;
+        fo[c] = fixed_to_double(qo[c], P.F);
+        const int64_t lb = (bp & (kSubTile - 1)) ? __ldg(lam + bp - 1) : 0;
+        const int64_t la = (ap & (kSubTile - 1)) ? __ldg(lam + ap - 1) : 0;
+        W[c] = (B.base[0][kb][c] - B.base[1][ka][c]) + (i128)(lb - la);
+    }
+}
+
+// Exact prefix of the fixed-point values qv (one per node, 0 past the ring's
+// end) into lam_out / ingrp_out / grpofs_out.  RECORD: the last CTA records the
+// Kuramoto order parameter from the totals (if P.obs is set); DEC_STEPS: it also
+// decrements the step budget.  Called by every thread of the CTA.
+template <int NQ, bool RECORD, bool DEC_STEPS>
+__device__ __forceinline__ void ring_prefix_tail(const RingPlan &P, int64_t *lam_out, i128 *ingrp_out,
+                                                 i128 *grpofs_out, int64_t sub, int64_t i, int64_t (&qv)[NQ])
+{
+    constexpr int NW = kRingThreads / 32;
+    __shared__ int64_t s_wtot[NW][NQ];
+    __shared__ int s_last;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t N = P.N, nsub = P.nsub, ngroups = P.ngroups;
+
+    // Exact inclusive prefix inside the sub-tile (warp scans + preceding warps).
+#pragma unroll
+    for (int c = 0; c < NQ; ++c) {
+        qv[c] = warp_incl_scan(qv[c]);
+        if (lane == 31) s_wtot[warp][c] = qv[c];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < NQ; ++c) {
+        int64_t off = 0;
+        for (int w = 0; w < warp; ++w) off += s_wtot[w][c];
+        if (i < N) lam_out[c * N + i] = off + qv[c];
+    }
+
+    // Level 1: the last CTA of each group of 64 sub-tiles scans the group.
+    const int64_t g = sub >> kGroupLog2, s0 = g << kGroupLog2;
+    const int64_t gsize = nsub - s0 < kGroup ? nsub - s0 : kGroup;
+    if (tid == 0) {
+#pragma unroll
+        for (int c = 0; c < NQ; ++c) {
+            int64_t t = 0;
+            for (int w = 0; w < NW; ++w) t += s_wtot[w][c];
+            P.subtot[c * nsub + sub] = t;
+        }
+        __threadfence();
+        s_last = last_arrival(P.grp_ctr + g, (unsigned long long)gsize);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    if (warp == 0) {
+#pragma unroll
+        for (int c = 0; c < NQ; ++c) {
+            const int64_t *st = P.subtot + c * nsub + s0;
+            const i128 v0 = 2 * lane < gsize ? (i128)__ldcg(st + 2 * lane) : (i128)0;
+            const i128 v1 = 2 * lane + 1 < gsize ? (i128)__ldcg(st + 2 * lane + 1) : (i128)0;
+            const i128 x = warp_incl_scan_i128(v0 + v1);
+            const i128 ex = x - v0 - v1;
+            i128 *ig = ingrp_out + c * nsub + s0;
+            if (2 * lane < gsize) st_i128(ig + 2 * lane, ex);
+            if (2 * lane + 1 < gsize) st_i128(ig + 2 * lane + 1, ex + v0);
+            if (lane == 31) st_i128(P.grptot + c * ngroups + g, x);
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    if (tid == 0) s_last = last_arrival(P.top_ctr, (unsigned long long)ngroups);
+    __syncthreads();
+    if (!s_last) return;
+
+    // Level 2: the last group scans the group totals (and records the totals).
+    i128 total[NQ];
+#pragma unroll
+    for (int c = 0; c < NQ; ++c)
+        total[c] = block_exclusive_scan<8>(P.grptot + c * ngroups, grpofs_out + c * (ngroups + 1), ngroups);
+    if (RECORD && tid == 0 && P.obs) {
+        const double S = fixed_to_double(total[0], P.F);
+        const double C = fixed_to_double(total[NQ - 1], P.F);
+        const unsigned long long n = *P.obs_ctr;
+        P.obs[n % (unsigned long long)P.obs_cap] = sqrt(S * S + C * C) / (double)N;
+        *P.obs_ctr = n + 1;
+    }
+    if (DEC_STEPS && tid == 0 && P.steps_left) *P.steps_left -= 1;
+}
+
+} // namespace simk

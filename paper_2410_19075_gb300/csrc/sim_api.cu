@@ -182,6 +182,8 @@ struct sim_handle {
     int64_t steps_done = 0;
     int64_t obs_read = 0;
     std::map<std::pair<double, int>, cudaGraphExec_t> graphs;
+    void *dp_block = nullptr;             // Dormand-Prince buffers (allocated on first use)
+    DpPlan dp{};
 };
 
 namespace {
@@ -901,9 +903,265 @@ void sim_destroy(sim_t h)
     if (!h) return;
     if (h->block) cudaStreamSynchronize(h->stream);
     for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
+    if (h->dp_block) cudaFree(h->dp_block);
     if (h->block && h->owns_block) cudaFree(h->block);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     delete h;
 }
 
 } // extern "C"
+
+// ---------------------------------------------------------------------------
+// Adaptive Dormand-Prince 5(4) on rings (kernels in dp5.cu).
+static_assert(kDpStatusSteps == SIM_ESTEPS && kDpStatusSmall == SIM_ESMALL, "status codes");
+
+namespace {
+
+constexpr int kDpGraphAttempts = 16; // attempted steps per captured graph
+constexpr int kDpMaxOutPerStep = 8;  // the step is capped at this many output intervals
+
+int64_t dp_n_out(double t0, double t_end, double out_dt)
+{
+    if (!(out_dt > 0.0)) return 0;
+    return (int64_t)std::floor((t_end - t0) / out_dt * (1.0 + 1e-12));
+}
+
+const char *dp_check(sim_t h, const sim_dp5_opts &o)
+{
+    if (h->topo != SIM_RING) return "Dormand-Prince runs take ring networks";
+    const double v[] = {o.t0, o.t_end, o.rtol, o.atol, o.h0, o.h_max, o.out_dt};
+    for (double x : v)
+        if (!std::isfinite(x)) return "non-finite option";
+    if (!(o.t_end > o.t0)) return "t_end must be after t0";
+    if (!(o.h0 > 0.0)) return "h0 must be positive";
+    if (o.rtol < 0.0 || o.atol < 0.0 || !(o.rtol > 0.0 || o.atol > 0.0)) return "tolerances must be >= 0, not both 0";
+    if (o.h_max < 0.0 || o.out_dt < 0.0) return "h_max and out_dt must be >= 0";
+    if (o.max_attempts < 1) return "max_attempts must be >= 1";
+    return nullptr;
+}
+
+int dp_ensure(sim_t h)
+{
+    if (h->dp_block) return SIM_OK;
+    const int64_t n = (int64_t)h->d * h->N, nsub = h->ring.nsub;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off += align_up(bytes);
+        return o;
+    };
+    const size_t oy1 = take(sizeof(double) * n);
+    size_t ok[7] = {};
+    for (int s = 0; s < 7; ++s)
+        if (s != 2) ok[s] = take(sizeof(double) * n);
+    const size_t oerr = take(sizeof(double) * nsub);
+    const size_t oout = take(sizeof(long long) * nsub * kDpMaxOut * 2);
+    const size_t octl = take(sizeof(DpCtl));
+    const size_t octr = take(sizeof(unsigned long long));
+    cudaError_t e = cudaMalloc(&h->dp_block, off);
+    if (e != cudaSuccess) {
+        h->dp_block = nullptr;
+        return fail(SIM_ENOMEM, "device allocation of the Dormand-Prince buffers failed");
+    }
+    char *b = static_cast<char *>(h->dp_block);
+    e = cudaMemsetAsync(b + octr, 0, sizeof(unsigned long long), h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "Dormand-Prince set-up");
+    DpPlan &Q = h->dp;
+    Q.r = h->ring;
+    Q.r.steps_left = nullptr;
+    Q.ybuf[0] = h->ring.y;
+    Q.ybuf[1] = reinterpret_cast<double *>(b + oy1);
+    for (int s = 0; s < 7; ++s) Q.k[s] = s == 2 ? h->ring.acc : reinterpret_cast<double *>(b + ok[s]);
+    Q.ctl = reinterpret_cast<DpCtl *>(b + octl);
+    Q.err_part = reinterpret_cast<double *>(b + oerr);
+    Q.out_part = reinterpret_cast<long long *>(b + oout);
+    Q.dp_ctr = reinterpret_cast<unsigned long long *>(b + octr);
+    Q.remaining = nullptr;
+    return SIM_OK;
+}
+
+// Integrate every member from its opts.t0 to opts.t_end on stream s.  Returns a
+// machinery or device status; per-member outcomes are in stats.
+int dp_run(const std::vector<sim_t> &mem, const sim_dp5_opts *opts, sim_dp5_stats *stats, cudaStream_t s)
+{
+    const int n = (int)mem.size();
+    for (int i = 0; i < n; ++i)
+        if (const char *why = dp_check(mem[i], opts[i])) return fail(SIM_EINVAL, why);
+    for (int i = 0; i < n; ++i) {
+        const int st = dp_ensure(mem[i]);
+        if (st != SIM_OK) return st;
+        mem[i]->dp.r = mem[i]->ring; // picks up a node parameter set since the last run
+        mem[i]->dp.r.steps_left = nullptr;
+    }
+    // Step control of every member, and the first attempt.
+    std::vector<DpCtl> ctl(n);
+    int remaining = 0;
+    for (int i = 0; i < n; ++i) {
+        const sim_dp5_opts &o = opts[i];
+        DpCtl c{};
+        c.t = o.t0;
+        c.t_end = o.t_end;
+        c.t0 = o.t0;
+        c.out_dt = o.out_dt;
+        c.rtol = o.rtol;
+        c.atol = o.atol;
+        c.hcap = o.h_max > 0.0 ? o.h_max : INFINITY;
+        if (o.out_dt > 0.0 && kDpMaxOutPerStep * o.out_dt < c.hcap) c.hcap = kDpMaxOutPerStep * o.out_dt;
+        c.h = o.h0 < c.hcap ? o.h0 : c.hcap;
+        c.max_att = o.max_attempts;
+        c.n_out = dp_n_out(o.t0, o.t_end, o.out_dt);
+        c.next_out = 1;
+        c.last = o.t_end - c.t <= c.h;
+        c.h_att = c.last ? o.t_end - c.t : c.h;
+        if (!(c.h_att > 1e-14 * (std::fabs(c.t) + c.h_att))) {
+            c.done = 1;
+            c.status = SIM_ESMALL;
+        }
+        remaining += c.done ? 0 : 1;
+        ctl[i] = c;
+    }
+    // Device tables of the run: plans, work items per model group, the counter.
+    std::vector<std::vector<int>> by_model(4);
+    for (int i = 0; i < n; ++i) by_model[mem[i]->model].push_back(i);
+    std::vector<DpPlan> plans;
+    std::vector<int> inst_of_item;
+    std::vector<int64_t> item_base;
+    struct Span { int model, first_plan, n_inst; int64_t first_item, n_items; };
+    std::vector<Span> spans;
+    for (int m = 0; m < 4; ++m) {
+        if (by_model[m].empty()) continue;
+        Span sp{m, (int)plans.size(), (int)by_model[m].size(), (int64_t)inst_of_item.size(), 0};
+        for (int k = 0; k < sp.n_inst; ++k) {
+            const sim_t h = mem[by_model[m][k]];
+            plans.push_back(h->dp);
+            item_base.push_back(sp.n_items);
+            for (int64_t t = 0; t < h->ring.nsub; ++t) inst_of_item.push_back(k);
+            sp.n_items += h->ring.nsub;
+        }
+        spans.push_back(sp);
+    }
+    const size_t o_plans = 0, o_items = align_up(sizeof(DpPlan) * plans.size());
+    const size_t o_base = o_items + align_up(sizeof(int) * inst_of_item.size());
+    const size_t o_rem = o_base + align_up(sizeof(int64_t) * item_base.size());
+    const size_t total = o_rem + align_up(sizeof(int));
+    void *tab = nullptr;
+    cudaError_t e = cudaMalloc(&tab, total);
+    if (e != cudaSuccess) return fail(SIM_ENOMEM, "device allocation of the run tables failed");
+    char *tb = static_cast<char *>(tab);
+    int *d_rem = reinterpret_cast<int *>(tb + o_rem);
+    for (DpPlan &q : plans) q.remaining = d_rem;
+    std::vector<DpGroup> groups;
+    for (const Span &sp : spans)
+        groups.push_back(DpGroup{sp.model, sp.n_inst, sp.n_items,
+                                 reinterpret_cast<const DpPlan *>(tb + o_plans) + sp.first_plan,
+                                 reinterpret_cast<const int *>(tb + o_items) + sp.first_item,
+                                 reinterpret_cast<const int64_t *>(tb + o_base) + sp.first_plan});
+    cudaGraphExec_t ex = nullptr;
+    cudaStream_t cap = nullptr;
+    int status = SIM_OK;
+    auto finish = [&](int st) {
+        if (ex) cudaGraphExecDestroy(ex);
+        cudaStreamSynchronize(s);
+        if (cap) cudaStreamDestroy(cap);
+        cudaFree(tab);
+        return st;
+    };
+    e = cudaMemcpyAsync(tb + o_plans, plans.data(), sizeof(DpPlan) * plans.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(tb + o_items, inst_of_item.data(), sizeof(int) * inst_of_item.size(),
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(tb + o_base, item_base.data(), sizeof(int64_t) * item_base.size(),
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_rem, &remaining, sizeof(int), cudaMemcpyHostToDevice, s);
+    for (int i = 0; i < n && e == cudaSuccess; ++i)
+        e = cudaMemcpyAsync(mem[i]->dp.ctl, &ctl[i], sizeof(DpCtl), cudaMemcpyHostToDevice, s);
+    // f(y_n) prefix and R(t0) of every member, then the first right-hand side.
+    for (int i = 0; i < n && e == cudaSuccess; ++i) e = ring_prologue(mem[i]->ring, s);
+    for (const DpGroup &g : groups)
+        if (e == cudaSuccess) e = dp_launch(1, g, s);
+    if (e != cudaSuccess) return finish(cuda_fail(e, "Dormand-Prince start"));
+    // Attempts in captured graphs until every member is done.
+    if (remaining > 0) {
+        e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return finish(cuda_fail(e, "Dormand-Prince capture"));
+        cudaError_t le = cudaSuccess;
+        for (int a = 0; a < kDpGraphAttempts && le == cudaSuccess; ++a)
+            for (int ds : {2, 3, 4, 5, 6, 7, 0})
+                for (const DpGroup &g : groups)
+                    if (le == cudaSuccess) le = dp_launch(ds, g, cap);
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(cap, &graph);
+        if (le != cudaSuccess || e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return finish(cuda_fail(le != cudaSuccess ? le : e, "Dormand-Prince capture"));
+        }
+        e = cudaGraphInstantiate(&ex, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return finish(cuda_fail(e, "cudaGraphInstantiate"));
+        long long max_att = 0;
+        for (int i = 0; i < n; ++i) max_att = opts[i].max_attempts > max_att ? opts[i].max_attempts : max_att;
+        const long long max_replays = max_att / kDpGraphAttempts + 2;
+        int h_rem = remaining;
+        for (long long r = 0; r < max_replays && h_rem > 0; ++r) {
+            e = cudaGraphLaunch(ex, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&h_rem, d_rem, sizeof(int), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) return finish(cuda_fail(e, "Dormand-Prince attempts"));
+        }
+        if (h_rem > 0) status = fail(SIM_EDEVICE, "Dormand-Prince run did not finish within its attempt budget");
+    }
+    // Results: control words, the state back in the handle's buffer, and the
+    // prefix of f(y) for the RK4 path (without recording another R).
+    for (int i = 0; i < n && e == cudaSuccess; ++i)
+        e = cudaMemcpyAsync(&ctl[i], mem[i]->dp.ctl, sizeof(DpCtl), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+        const sim_t h = mem[i];
+        if (ctl[i].cur == 1)
+            e = cudaMemcpyAsync(h->ring.y, h->dp.ybuf[1], sizeof(double) * h->d * h->N, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) {
+            RingPlan quiet = h->ring;
+            quiet.obs = nullptr;
+            e = ring_prologue(quiet, s);
+        }
+    }
+    if (e != cudaSuccess) return finish(cuda_fail(e, "Dormand-Prince results"));
+    for (int i = 0; i < n; ++i) {
+        if (!stats) break;
+        stats[i].accepted = ctl[i].n_acc;
+        stats[i].rejected = ctl[i].n_rej;
+        stats[i].t = ctl[i].t;
+        stats[i].h_next = ctl[i].h;
+        stats[i].status = ctl[i].status;
+    }
+    status = finish(status);
+    for (int i = 0; i < n && status == SIM_OK; ++i) status = check_device_error(mem[i]);
+    return status;
+}
+
+} // namespace
+
+extern "C" {
+
+int sim_dp5(sim_t h, const sim_dp5_opts *opts, sim_dp5_stats *stats)
+{
+    if (!h || !opts) return fail(SIM_EINVAL, "NULL argument");
+    sim_dp5_stats st{};
+    const int r = dp_run({h}, opts, &st, h->stream);
+    if (stats) *stats = st;
+    if (r != SIM_OK) return r;
+    if (st.status == SIM_ESTEPS) return fail(SIM_ESTEPS, "the attempt budget ran out before t_end");
+    if (st.status == SIM_ESMALL) return fail(SIM_ESMALL, "the step size fell below the resolution of t");
+    return SIM_OK;
+}
+
+int sim_batch_dp5(sim_batch_t b, const sim_dp5_opts *opts, sim_dp5_stats *stats)
+{
+    if (!b || !opts) return fail(SIM_EINVAL, "NULL argument");
+    return dp_run(b->members, opts, stats, b->stream);
+}
+
+} // extern "C"
+

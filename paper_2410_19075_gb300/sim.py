@@ -9,7 +9,7 @@ import ctypes
 
 import numpy as np
 
-from ._lib import check, lib
+from ._lib import DP5Opts, DP5Stats, SIM_ESMALL, SIM_ESTEPS, check, lib
 
 KS, FHN, HH, KSI = 0, 1, 2, 3
 RING, CUBE3D, BALL3D, DISK2D = 0, 1, 2, 3
@@ -32,6 +32,16 @@ def math_eval(fn: int, x) -> np.ndarray:
     out = np.empty_like(a)
     check(lib().sim_math_eval(fn, a.ctypes.data, out.ctypes.data, a.size))
     return out
+
+
+def _dp5_opts(t_end, rtol, atol, h0, t0=0.0, h_max=0.0, out_dt=0.0, max_attempts=10 ** 6):
+    return DP5Opts(float(t0), float(t_end), float(rtol), float(atol), float(h0), float(h_max), float(out_dt),
+                   int(max_attempts))
+
+
+def _dp5_stats(s):
+    return {"accepted": int(s.accepted), "rejected": int(s.rejected), "t": float(s.t), "h_next": float(s.h_next),
+            "status": int(s.status)}
 
 
 def workspace_bytes(model, topology, N, radius) -> int:
@@ -78,6 +88,17 @@ class Network:
 
     def step(self, n_steps: int, dt: float):
         check(lib().sim_step(self._handle(), int(n_steps), float(dt)))
+
+    def dp5(self, t_end, rtol, atol, h0, t0=0.0, h_max=0.0, out_dt=0.0, max_attempts=10 ** 6):
+        """Adaptive Dormand-Prince 5(4) from t0 to t_end (``sim_dp5``).  Returns the
+        stats as a dict; an exhausted attempt budget or a vanishing step is
+        reported in ``status`` instead of raising."""
+        o = _dp5_opts(t_end, rtol, atol, h0, t0, h_max, out_dt, max_attempts)
+        st = DP5Stats()
+        r = lib().sim_dp5(self._handle(), ctypes.byref(o), ctypes.byref(st))
+        if r not in (0, SIM_ESTEPS, SIM_ESMALL):
+            check(r)
+        return _dp5_stats(st)
 
     def get_state(self, out: np.ndarray | None = None) -> np.ndarray:
         if out is None:
@@ -147,6 +168,14 @@ class Batch:
 
     def sync(self):
         check(lib().sim_batch_sync(self._h))
+
+    def dp5(self, opts):
+        """Dormand-Prince runs of every member; opts is one dict per member with the
+        keyword arguments of ``Network.dp5``.  Returns one stats dict per member."""
+        arr = (DP5Opts * len(self.members))(*[_dp5_opts(**o) for o in opts])
+        st = (DP5Stats * len(self.members))()
+        check(lib().sim_batch_dp5(self._h, arr, st))
+        return [_dp5_stats(x) for x in st]
 
     def close(self):
         if self._h is not None:

@@ -1,0 +1,177 @@
+"""GPU parity of the adaptive Dormand-Prince 5(4) path (Section III.A) against
+the oracle's dp5 on the same seeded inputs: the same accepted and rejected
+attempts, the final state within the state tolerance, the dense-output order
+parameters within the order tolerance; batches equal solo runs bit for bit."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2410_19075_gb300 import inputs as I
+from _common import ORDER_TOL, PARAMS, STATE_TOL, inputs_for
+
+pytestmark = pytest.mark.gpu
+
+
+def _gpu_dp5(model, N, R, params, y0, npar=None, **opts):
+    from paper_2410_19075_gb300 import Network
+    with Network(model, 0, N, R, params) as net:
+        if npar is not None:
+            net.set_node_param(npar)
+        net.set_state(y0)
+        net.observables()  # drop R(t0) of set_state; the run records its own
+        st = net.dp5(**opts)
+        return net.get_state(), net.observables(), st
+
+
+def _check(model, N, R, seed, t_end, tol, h0, out_dt=0.0, params=None, **kw):
+    params = PARAMS[model]() if params is None else params
+    y0, npar = inputs_for(model, 0, N, seed)
+    y, order, st = _gpu_dp5(model, N, R, params, y0, npar, t_end=t_end, rtol=tol, atol=tol, h0=h0, out_dt=out_dt, **kw)
+    ref, ref_order, ref_st = oracle.dp5(model, 0, N, R, params, y0, 0.0, t_end, tol, tol, h0, out_dt=out_dt,
+                                        node_param=npar, **kw)
+    assert (st["accepted"], st["rejected"], st["status"]) == (ref_st["accepted"], ref_st["rejected"],
+                                                              ref_st["status"])
+    assert st["t"] == ref_st["t"]
+    # the error norm is a small difference of stage slopes, so rounding-level
+    # differences of the states move the proposed step at the 1e-7 level
+    assert abs(st["h_next"] - ref_st["h_next"]) <= 1e-6 * ref_st["h_next"]
+    assert np.abs(y - ref).max() <= STATE_TOL
+    if model in (0, 3):
+        assert order.size == ref_order.size
+        assert np.abs(order - ref_order).max() <= ORDER_TOL
+    else:
+        assert order.size == 0
+    return st
+
+
+@pytest.mark.parametrize("model", [0, 1, 2, 3])
+@pytest.mark.parametrize("N,R", [(7, 2), (1000, 350), (3 * 1024 + 77, 777)])
+def test_dp5_matches_oracle(model, N, R):
+    """Every model on rings from one sub-tile to several with a ragged tail."""
+    t_end = {0: 10.0, 1: 2.0, 2: 5.0, 3: 10.0}[model]
+    st = _check(model, N, R, 40 + N, t_end, 1e-9, 0.01, out_dt=0.5 if model in (0, 3) else 0.0)
+    assert st["accepted"] > 5
+
+
+def test_dp5_rejections_match_oracle():
+    """An oversized first step on the Kuramoto ring is rejected and shrunk the
+    same way on both sides."""
+    st = _check(0, 2000, 600, 41, 20.0, 1e-10, 5.0, out_dt=1.0, params=I.ks_params(omega=0.3, alpha=1.3))
+    assert st["rejected"] >= 1
+
+
+def test_dp5_range_failure_is_a_rejection():
+    """FitzHugh-Nagumo with a first trial step of 1 (eps = 0.05): the attempt
+    leaves the fixed-point range of the window sums and must be rejected, not
+    reported; the run then matches a fine RK4 solution."""
+    from paper_2410_19075_gb300 import Network
+    N, R = 1000, 300
+    y0 = I.fhn_state(42, 0, N)
+    with Network(1, 0, N, R, I.fhn_params()) as net:
+        net.set_state(y0)
+        st = net.dp5(t_end=1.0, rtol=1e-10, atol=1e-10, h0=1.0)
+        y = net.get_state()
+    ref, _ = oracle.rk4(1, 0, N, R, I.fhn_params(), y0, 10000, 1e-4)
+    assert st["status"] == 0 and st["rejected"] >= 1
+    assert np.abs(y - ref).max() < 1e-7
+
+
+def test_dp5_attempt_budget():
+    from paper_2410_19075_gb300 import Network
+    from paper_2410_19075_gb300._lib import SIM_ESTEPS
+    y0 = I.ks_phases(43, 0, 500)
+    with Network(0, 0, 500, 100, I.ks_params()) as net:
+        net.set_state(y0)
+        st = net.dp5(t_end=100.0, rtol=1e-10, atol=1e-10, h0=0.001, max_attempts=3)
+        y = net.get_state()
+    ref, _, ref_st = oracle.dp5(0, 0, 500, 100, I.ks_params(), y0, 0.0, 100.0, 1e-10, 1e-10, 0.001, max_attempts=3)
+    assert st["status"] == SIM_ESTEPS and ref_st["status"] == -3  # the oracle's code for the same outcome
+    assert st["accepted"] == 3 and abs(st["t"] - ref_st["t"]) <= 1e-9 * ref_st["t"]
+    assert np.abs(y - ref).max() <= STATE_TOL
+
+
+def test_dp5_then_rk4_continues_from_the_dp5_state():
+    """After a run the handle holds y(t_end) and the RK4 path continues from it."""
+    from paper_2410_19075_gb300 import Network
+    N, R = 3000, 900
+    params = I.ks_params()
+    y0 = I.ks_phases(44, 0, N)
+    with Network(0, 0, N, R, params) as net:
+        net.set_state(y0)
+        net.dp5(t_end=3.0, rtol=1e-10, atol=1e-10, h0=0.01)
+        mid = net.get_state()
+        net.step(50, 0.01)
+        after = net.get_state()
+    ref, _ = oracle.rk4(0, 0, N, R, params, mid, 50, 0.01)
+    assert np.abs(after - ref).max() <= STATE_TOL
+
+
+def test_batch_dp5_equals_solo_runs_bitwise():
+    """Members of every model and size, each with its own span, tolerance and
+    output grid, give in one batch what each gives alone."""
+    from paper_2410_19075_gb300 import Batch, Network
+    cases = [(0, 1000, 350, dict(t_end=5.0, rtol=1e-9, atol=1e-9, h0=0.01, out_dt=0.25)),
+             (0, 300, 40, dict(t_end=8.0, rtol=1e-7, atol=1e-7, h0=0.1, out_dt=1.0)),
+             (1, 2000, 700, dict(t_end=1.5, rtol=1e-8, atol=1e-8, h0=0.001)),
+             (2, 500, 150, dict(t_end=4.0, rtol=1e-8, atol=1e-8, h0=0.01)),
+             (3, 777, 200, dict(t_end=6.0, rtol=1e-9, atol=1e-9, h0=0.05, out_dt=0.5)),
+             (0, 5000, 1700, dict(t_end=0.5, rtol=1e-10, atol=1e-10, h0=0.5, max_attempts=4))]
+    solo, nets = [], []
+    for idx, (model, N, R, o) in enumerate(cases):
+        y0, npar = inputs_for(model, 0, N, 700 + idx)
+        solo.append(_gpu_dp5(model, N, R, PARAMS[model](), y0, npar, **o))
+        net = Network(model, 0, N, R, PARAMS[model]())
+        if npar is not None:
+            net.set_node_param(npar)
+        net.set_state(y0)
+        net.observables()
+        nets.append(net)
+    try:
+        with Batch(nets) as b:
+            stats = b.dp5([o for *_, o in cases])
+        for net, (y, order, st), bst in zip(nets, solo, stats):
+            assert bst == st
+            assert np.array_equal(net.get_state(), y)
+            assert np.array_equal(net.observables(), order)
+    finally:
+        for net in nets:
+            net.close()
+
+
+def test_dp5_full_size_fhn_ring_agrees_with_rk4():
+    """The 10^6-node FitzHugh-Nagumo ring (R = 350000): Dormand-Prince at 1e-9
+    and RK4 at dt = 0.001 reach the same state at t = 1 (sampled nodes checked
+    against the oracle's right-hand side afterwards)."""
+    from paper_2410_19075_gb300 import Network
+    N, R = 10 ** 6, 350000
+    params = I.fhn_params()
+    y0 = I.fhn_state(2412, 0, N)
+    with Network(1, 0, N, R, params) as net:
+        net.set_state(y0)
+        st = net.dp5(t_end=1.0, rtol=1e-9, atol=1e-9, h0=0.001)
+        a = net.get_state()
+        k = net.rhs().reshape(2, N)
+    with Network(1, 0, N, R, params) as net:
+        net.set_state(y0)
+        net.step(1000, 0.001)
+        b = net.get_state()
+    assert st["status"] == 0
+    assert np.abs(a - b).max() < 1e-7
+    q = np.random.default_rng(9).choice(N, 32, replace=False)
+    ref = oracle.rhs_sampled(1, 0, N, R, params, a, q)
+    assert np.abs(k[:, q] - ref).max() < 1e-12
+
+
+def test_dp5_rejects_lattices_and_bad_options():
+    from paper_2410_19075_gb300 import Network
+    from paper_2410_19075_gb300._lib import SimError
+    with Network(0, 2, 8, 2, I.ks_params()) as net:
+        net.set_state(I.ks_phases(1, 0, 512))
+        with pytest.raises(SimError):
+            net.dp5(t_end=1.0, rtol=1e-8, atol=1e-8, h0=0.01)
+    with Network(0, 0, 100, 10, I.ks_params()) as net:
+        net.set_state(I.ks_phases(1, 0, 100))
+        for bad in (dict(t_end=0.0, rtol=1e-8, atol=1e-8, h0=0.01), dict(t_end=1.0, rtol=0, atol=0, h0=0.01),
+                    dict(t_end=1.0, rtol=1e-8, atol=1e-8, h0=0.0)):
+            with pytest.raises(SimError):
+                net.dp5(**bad)
