@@ -294,6 +294,61 @@ def bench_batched(args, flush, stream, n_inst=4096, steps=2000, plain_steps=20):
             "gpu_launches": 4 * steps * 1}
 
 
+def bench_dp5_sweep(args, n_inst=4096, N=1000, t_end=100.0, tol=1e-8, plain_inst=32):
+    """Adaptive Dormand-Prince 5(4) parameter sweep in the shape of the paper's
+    1D chimera study (Section IV): n_inst Kuramoto rings of N nodes with
+    r ~ U[0.05, 0.45] and alpha ~ U[1.3, 1.57], each integrated to t_end with its
+    own step control (rtol = atol = tol) and the order parameter recorded every
+    time unit; one sim_batch_dp5 call, wall time of the call.  Beside it, the
+    first plain_inst networks integrated one at a time with sim_dp5."""
+    from paper_2410_19075_gb300 import Batch, Network
+    sweep = I.batched_sweep(n_inst=n_inst, seed=2416, n_lo=N, n_hi=N)
+    opts = dict(t_end=t_end, rtol=tol, atol=tol, h0=0.01, out_dt=1.0)
+
+    def make(ss):
+        nets = []
+        for s in ss:
+            net = Network(0, 0, s.N, s.R, I.ks_params(alpha=s.alpha))
+            net.set_state(I.ks_phases(s.seed, s.instance, s.N))
+            nets.append(net)
+        return nets
+
+    # warm-up run on a few members (graph capture paths, allocations)
+    warm = make(sweep[:8])
+    with Batch(warm) as b:
+        b.dp5([dict(opts, t_end=1.0)] * len(warm))
+    for net in warm:
+        net.close()
+    nets = make(sweep)
+    batch = Batch(nets)
+    t0 = time.perf_counter()
+    stats = batch.dp5([opts] * n_inst)
+    wall = time.perf_counter() - t0
+    batch.close()
+    assert all(st["status"] == 0 for st in stats)
+    acc = sum(st["accepted"] for st in stats)
+    att = acc + sum(st["rejected"] for st in stats)
+    node_steps = float(N) * acc
+    for net in nets:
+        net.close()
+    plain = make(sweep[:plain_inst])
+    t0 = time.perf_counter()
+    pst = [net.dp5(**opts) for net in plain]
+    plain_wall = time.perf_counter() - t0
+    for net in plain:
+        net.close()
+    plain_value = float(N) * sum(st["accepted"] for st in pst) / plain_wall
+    value = node_steps / wall
+    return {"workload": f"{n_inst} Kuramoto rings of N={N}, r ~ U[0.05, 0.45], alpha ~ U[1.3, 1.57], "
+                        f"Dormand-Prince 5(4) to t={t_end} at rtol=atol={tol}, R recorded every time unit",
+            "value": value, "unit": "accepted node-steps/s", "wall_s": wall,
+            "accepted_steps": acc, "attempted_steps": att,
+            "rhs_node_evals_per_s": 6.0 * N * att / wall,
+            "plain_value": plain_value, "plain_instances_timed": plain_inst,
+            "speedup_vs_plain": value / plain_value,
+            "gpu_launches": 7 * (att // n_inst + 1)}
+
+
 # ----------------------------------------------------------------------------- c1 and c3
 def bench_small_ring(args, stream, flush, steps=200, reps=5):
     """Kuramoto ring N=1000, R=350, alpha=1.46: latency of one RK4 step (the whole
@@ -554,6 +609,7 @@ def run_native(args):
         line["ball3d_inertia"] = bench_ball(args, stream, flush)
     if not args.no_batched:
         line["batched"] = bench_batched(args, flush, stream)
+        line["batched_dp5"] = bench_dp5_sweep(args)
     if not args.no_served:
         line["served"] = bench_served(args, stream)
     net.close()

@@ -19,7 +19,10 @@
 //           attempt whose stage inputs left the fixed-point range of the window
 //           sums is rejected with the smallest step factor (as a non-finite
 //           error is), not reported as a failure.
-// ds 1 starts a run: k1 = f(y_n) from the prefix of y_n, then as ds 0.
+// ds 8 starts a run: the prefix of f(y_n) and R(t0); ds 1 then computes
+// k1 = f(y_n) from it and continues as ds 0.  ds 9 ends a run: the state moves
+// back to the first buffer if needed and the prefix of f(y) is rebuilt for the
+// RK4 kernels (without recording R).
 // An instance that is done skips every kernel whole (its arrival counters stay
 // consistent); accepting swaps the roles of the two state buffers and of the
 // two first-stage buffers instead of copying.
@@ -124,8 +127,9 @@ __global__ void __launch_bounds__(kRingThreads, DpMinBlocks<M>::value)
     using Mo = Model<M>;
     constexpr int D = Mo::D, NQ = Mo::NQ, NX = Mo::NX, XOFF = D - NX;
     constexpr bool KURAMOTO = M == 0 || M == 3;
-    constexpr int pin = (DS + 1) & 1;             // prefix buffer read (ds >= 1)
-    constexpr int pout = DS <= 1 ? 1 : (DS & 1);  // prefix buffer written (ds <= 6)
+    constexpr bool EDGE = DS >= 8;                // run start (8) or end (9)
+    constexpr int pin = (DS + 1) & 1;             // prefix buffer read (ds 1..7)
+    constexpr int pout = EDGE ? 0 : (DS <= 1 ? 1 : (DS & 1)); // prefix buffer written
     constexpr int NW = kRingThreads / 32;
     __shared__ RingBases<NQ> s_bases;
 
@@ -133,7 +137,7 @@ __global__ void __launch_bounds__(kRingThreads, DpMinBlocks<M>::value)
     const DpPlan &Q = plans[inst];
     const RingPlan &P = Q.r;
     const DpCtl *ctl = Q.ctl;
-    if (*(const volatile int *)&ctl->done) return;
+    if (!EDGE && *(const volatile int *)&ctl->done) return;
     const int64_t sub = (int64_t)blockIdx.x - item_base[inst];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t N = P.N;
@@ -143,7 +147,7 @@ __global__ void __launch_bounds__(kRingThreads, DpMinBlocks<M>::value)
     const double *__restrict__ y = Q.ybuf[cur];
     double *__restrict__ y5 = Q.ybuf[cur ^ 1];
     const double *k1 = Q.k[cur];
-    if (DS >= 1) ring_load_bases<NQ>(P, P.ingrp[pin], P.grpofs[pin], sub, s_bases);
+    if (DS >= 1 && DS <= 7) ring_load_bases<NQ>(P, P.ingrp[pin], P.grpofs[pin], sub, s_bases);
 
     int64_t qv[NQ];
     bool ok = true;
@@ -151,6 +155,24 @@ __global__ void __launch_bounds__(kRingThreads, DpMinBlocks<M>::value)
     for (int c = 0; c < NQ; ++c) qv[c] = 0;
     double err_acc = 0.0;
     double k[D];
+    if (EDGE && i < N) {
+        double xn[D];
+#pragma unroll
+        for (int v = 0; v < D; ++v) {
+            const int64_t q = v * N + i;
+            xn[v] = y[q];
+            if (DS == 9 && cur == 1) Q.ybuf[0][q] = xn[v];
+        }
+        double f[NQ];
+        Mo::coupled(P.mp, xn, f);
+#pragma unroll
+        for (int c = 0; c < NQ; ++c) qv[c] = to_fixed(f[c], P.F, P.lim, ok);
+    }
+    if (EDGE) {
+        if (!ok) raise_error(P.err, ERR_RANGE);
+        ring_prefix_tail<NQ, DS == 8 && KURAMOTO, false>(P, P.lam[0], P.ingrp[0], P.grpofs[0], sub, i, qv);
+        return;
+    }
     if (i < N) {
         if (DS >= 1) {
             int64_t qo[NQ];
@@ -332,7 +354,9 @@ static cudaError_t launch_m(int ds, const DpGroup &g, cudaStream_t s)
     case 4: dp_stage_kernel<M, 4><<<grid, block, 0, s>>>(g.plans, g.inst_of_item, g.item_base); break;
     case 5: dp_stage_kernel<M, 5><<<grid, block, 0, s>>>(g.plans, g.inst_of_item, g.item_base); break;
     case 6: dp_stage_kernel<M, 6><<<grid, block, 0, s>>>(g.plans, g.inst_of_item, g.item_base); break;
-    default: dp_stage_kernel<M, 7><<<grid, block, 0, s>>>(g.plans, g.inst_of_item, g.item_base); break;
+    case 7: dp_stage_kernel<M, 7><<<grid, block, 0, s>>>(g.plans, g.inst_of_item, g.item_base); break;
+    case 8: dp_stage_kernel<M, 8><<<grid, block, 0, s>>>(g.plans, g.inst_of_item, g.item_base); break;
+    default: dp_stage_kernel<M, 9><<<grid, block, 0, s>>>(g.plans, g.inst_of_item, g.item_base); break;
     }
     return cudaGetLastError();
 }

@@ -95,10 +95,11 @@ struct DpGroup {
     const int64_t *item_base;
 };
 
-// Kernel ds of one attempt for every instance of the group: 1 = first right-hand
-// side of a run and the input of stage 2; 2..6 = stages 2..6; 7 = stage 7, the
-// error norm, dense output and the decision; 0 = the input of stage 2 of the
-// next attempt.
+// Kernel ds for every instance of the group: 8 = run start (prefix of f(y_n),
+// R(t0)); 1 = first right-hand side of a run and the input of stage 2;
+// 2..6 = stages 2..6; 7 = stage 7, the error norm, dense output and the
+// decision; 0 = the input of stage 2 of the next attempt; 9 = run end (state
+// back in the first buffer, prefix of f(y) for the RK4 kernels).
 cudaError_t dp_launch(int ds, const DpGroup &g, cudaStream_t s);
 
 // Ring: f(y) -> lam[0], ofs[0] and the order parameter of y (Kuramoto).

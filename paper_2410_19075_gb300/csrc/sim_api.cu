@@ -956,7 +956,6 @@ int dp_ensure(sim_t h)
         if (s != 2) ok[s] = take(sizeof(double) * n);
     const size_t oerr = take(sizeof(double) * nsub);
     const size_t oout = take(sizeof(long long) * nsub * kDpMaxOut * 2);
-    const size_t octl = take(sizeof(DpCtl));
     const size_t octr = take(sizeof(unsigned long long));
     cudaError_t e = cudaMalloc(&h->dp_block, off);
     if (e != cudaSuccess) {
@@ -965,18 +964,17 @@ int dp_ensure(sim_t h)
     }
     char *b = static_cast<char *>(h->dp_block);
     e = cudaMemsetAsync(b + octr, 0, sizeof(unsigned long long), h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "Dormand-Prince set-up");
     DpPlan &Q = h->dp;
-    Q.r = h->ring;
-    Q.r.steps_left = nullptr;
     Q.ybuf[0] = h->ring.y;
     Q.ybuf[1] = reinterpret_cast<double *>(b + oy1);
     for (int s = 0; s < 7; ++s) Q.k[s] = s == 2 ? h->ring.acc : reinterpret_cast<double *>(b + ok[s]);
-    Q.ctl = reinterpret_cast<DpCtl *>(b + octl);
     Q.err_part = reinterpret_cast<double *>(b + oerr);
     Q.out_part = reinterpret_cast<long long *>(b + oout);
     Q.dp_ctr = reinterpret_cast<unsigned long long *>(b + octr);
-    Q.remaining = nullptr;
+    Q.ctl = nullptr;       // set per run (the run's control table)
+    Q.remaining = nullptr; // set per run
     return SIM_OK;
 }
 
@@ -990,7 +988,7 @@ int dp_run(const std::vector<sim_t> &mem, const sim_dp5_opts *opts, sim_dp5_stat
     for (int i = 0; i < n; ++i) {
         const int st = dp_ensure(mem[i]);
         if (st != SIM_OK) return st;
-        mem[i]->dp.r = mem[i]->ring; // picks up a node parameter set since the last run
+        mem[i]->dp.r = mem[i]->ring;
         mem[i]->dp.r.steps_left = nullptr;
     }
     // Step control of every member, and the first attempt.
@@ -1020,11 +1018,12 @@ int dp_run(const std::vector<sim_t> &mem, const sim_dp5_opts *opts, sim_dp5_stat
         remaining += c.done ? 0 : 1;
         ctl[i] = c;
     }
-    // Device tables of the run: plans, work items per model group, the counter.
+    // Device tables of the run: plans, work items per model group, control
+    // words, the members' error words and the counter of unfinished members.
     std::vector<std::vector<int>> by_model(4);
     for (int i = 0; i < n; ++i) by_model[mem[i]->model].push_back(i);
     std::vector<DpPlan> plans;
-    std::vector<int> inst_of_item;
+    std::vector<int> inst_of_item, plan_member;
     std::vector<int64_t> item_base;
     struct Span { int model, first_plan, n_inst; int64_t first_item, n_items; };
     std::vector<Span> spans;
@@ -1034,22 +1033,33 @@ int dp_run(const std::vector<sim_t> &mem, const sim_dp5_opts *opts, sim_dp5_stat
         for (int k = 0; k < sp.n_inst; ++k) {
             const sim_t h = mem[by_model[m][k]];
             plans.push_back(h->dp);
+            plan_member.push_back(by_model[m][k]);
             item_base.push_back(sp.n_items);
             for (int64_t t = 0; t < h->ring.nsub; ++t) inst_of_item.push_back(k);
             sp.n_items += h->ring.nsub;
         }
         spans.push_back(sp);
     }
+    std::vector<unsigned *> errs(n);
+    for (int i = 0; i < n; ++i) errs[i] = mem[i]->err;
     const size_t o_plans = 0, o_items = align_up(sizeof(DpPlan) * plans.size());
     const size_t o_base = o_items + align_up(sizeof(int) * inst_of_item.size());
-    const size_t o_rem = o_base + align_up(sizeof(int64_t) * item_base.size());
-    const size_t total = o_rem + align_up(sizeof(int));
+    const size_t o_ctl = o_base + align_up(sizeof(int64_t) * item_base.size());
+    const size_t o_errs = o_ctl + align_up(sizeof(DpCtl) * n);
+    const size_t o_rem = o_errs + align_up(sizeof(unsigned *) * n);
+    const size_t o_eout = o_rem + align_up(sizeof(int));
+    const size_t total = o_eout + align_up(sizeof(unsigned));
     void *tab = nullptr;
     cudaError_t e = cudaMalloc(&tab, total);
     if (e != cudaSuccess) return fail(SIM_ENOMEM, "device allocation of the run tables failed");
     char *tb = static_cast<char *>(tab);
     int *d_rem = reinterpret_cast<int *>(tb + o_rem);
-    for (DpPlan &q : plans) q.remaining = d_rem;
+    DpCtl *d_ctl = reinterpret_cast<DpCtl *>(tb + o_ctl);
+    unsigned *d_eout = reinterpret_cast<unsigned *>(tb + o_eout);
+    for (size_t q = 0; q < plans.size(); ++q) {
+        plans[q].remaining = d_rem;
+        plans[q].ctl = d_ctl + plan_member[q];
+    }
     std::vector<DpGroup> groups;
     for (const Span &sp : spans)
         groups.push_back(DpGroup{sp.model, sp.n_inst, sp.n_items,
@@ -1073,13 +1083,14 @@ int dp_run(const std::vector<sim_t> &mem, const sim_dp5_opts *opts, sim_dp5_stat
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(tb + o_base, item_base.data(), sizeof(int64_t) * item_base.size(),
                             cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_ctl, ctl.data(), sizeof(DpCtl) * n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(tb + o_errs, errs.data(), sizeof(unsigned *) * n, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_rem, &remaining, sizeof(int), cudaMemcpyHostToDevice, s);
-    for (int i = 0; i < n && e == cudaSuccess; ++i)
-        e = cudaMemcpyAsync(mem[i]->dp.ctl, &ctl[i], sizeof(DpCtl), cudaMemcpyHostToDevice, s);
-    // f(y_n) prefix and R(t0) of every member, then the first right-hand side.
-    for (int i = 0; i < n && e == cudaSuccess; ++i) e = ring_prologue(mem[i]->ring, s);
-    for (const DpGroup &g : groups)
-        if (e == cudaSuccess) e = dp_launch(1, g, s);
+    // prefix of f(y_n) and R(t0) of every member, then the first right-hand side
+    for (int ds : {8, 1})
+        for (const DpGroup &g : groups)
+            if (e == cudaSuccess) e = dp_launch(ds, g, s);
     if (e != cudaSuccess) return finish(cuda_fail(e, "Dormand-Prince start"));
     // Attempts in captured graphs until every member is done.
     if (remaining > 0) {
@@ -1112,24 +1123,20 @@ int dp_run(const std::vector<sim_t> &mem, const sim_dp5_opts *opts, sim_dp5_stat
         }
         if (h_rem > 0) status = fail(SIM_EDEVICE, "Dormand-Prince run did not finish within its attempt budget");
     }
-    // Results: control words, the state back in the handle's buffer, and the
-    // prefix of f(y) for the RK4 path (without recording another R).
-    for (int i = 0; i < n && e == cudaSuccess; ++i)
-        e = cudaMemcpyAsync(&ctl[i], mem[i]->dp.ctl, sizeof(DpCtl), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    for (int i = 0; i < n && e == cudaSuccess; ++i) {
-        const sim_t h = mem[i];
-        if (ctl[i].cur == 1)
-            e = cudaMemcpyAsync(h->ring.y, h->dp.ybuf[1], sizeof(double) * h->d * h->N, cudaMemcpyDeviceToDevice, s);
-        if (e == cudaSuccess) {
-            RingPlan quiet = h->ring;
-            quiet.obs = nullptr;
-            e = ring_prologue(quiet, s);
-        }
+    // State back in the handles' buffers with the prefix of f(y) for the RK4
+    // path, the control words and the OR of the members' error words.
+    for (const DpGroup &g : groups)
+        if (e == cudaSuccess) e = dp_launch(9, g, s);
+    if (e == cudaSuccess) {
+        batch_error_kernel<<<1, 256, 0, s>>>(reinterpret_cast<unsigned *const *>(tb + o_errs), n, d_eout);
+        e = cudaGetLastError();
     }
+    unsigned h_eout = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ctl.data(), d_ctl, sizeof(DpCtl) * n, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_eout, d_eout, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return finish(cuda_fail(e, "Dormand-Prince results"));
-    for (int i = 0; i < n; ++i) {
-        if (!stats) break;
+    for (int i = 0; i < n && stats; ++i) {
         stats[i].accepted = ctl[i].n_acc;
         stats[i].rejected = ctl[i].n_rej;
         stats[i].t = ctl[i].t;
@@ -1137,7 +1144,10 @@ int dp_run(const std::vector<sim_t> &mem, const sim_dp5_opts *opts, sim_dp5_stat
         stats[i].status = ctl[i].status;
     }
     status = finish(status);
-    for (int i = 0; i < n && status == SIM_OK; ++i) status = check_device_error(mem[i]);
+    if (status == SIM_OK && (h_eout & ERR_TIMEOUT))
+        status = fail(SIM_ETIMEOUT, "a device-side wait exceeded its bound; results are invalid");
+    if (status == SIM_OK && (h_eout & ERR_RANGE))
+        status = fail(SIM_ENONFINITE, "the state became non-finite or left the fixed-point range");
     return status;
 }
 
