@@ -51,6 +51,10 @@ CUBE_BYTES = 544
 # (sin, cos).  Kuramoto with inertia (d = 2, one local variable): 120 + 2 * 144 +
 # 136 B per node-step; Kuramoto (d = 1): 96 + 2 * 104 + 104 B.
 LATTICE_BYTES = {0: 408, 3: 544}
+# DRAM bytes per stage launch (dram__bytes_read.sum + dram__bytes_write.sum, mean
+# over the four stages) from an ncu capture of the current ring stage kernel on
+# the FitzHugh-Nagumo ring N = 10^6, R = 350000; reported only for that workload.
+MEASURED_TRAFFIC = {(0, 1, 10 ** 6, 350000): 44.23e6}
 
 
 def parse():
@@ -587,8 +591,9 @@ def run_native(args):
     fp64_peak_gflops = 2 * 504.3  # measured DFMA rate x 2 flops
     achieved_gflops = alg_flops_launch / avg_launch_s / 1e9
     achieved_gbs = alg_bytes_launch / avg_launch_s / 1e9
+    traffic = MEASURED_TRAFFIC.get((args.topo, args.model, N, R))
     roofline = {"bound": "alu", "achieved": achieved_gflops, "peak": fp64_peak_gflops, "unit": "GFLOP/s",
-                "frac": achieved_gflops / fp64_peak_gflops, "traffic": None,
+                "frac": achieved_gflops / fp64_peak_gflops, "traffic": traffic,
                 "hbm_achieved_gbs": achieved_gbs, "hbm_peak_gbs": hbm_peak,
                 "hbm_frac": achieved_gbs / hbm_peak,
                 "note": "FP64 pipe of measured DFMA throughput; HBM fraction from algorithmic bytes"}
