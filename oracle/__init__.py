@@ -27,7 +27,7 @@ import numpy as np
 from .build import build as _build
 
 KS, FHN, HH, KSI = 0, 1, 2, 3
-RING, CUBE, BALL, DISK = 0, 1, 2, 3
+RING, CUBE, BALL, DISK, GRAPH = 0, 1, 2, 3, 4
 REVERSE, INCLUDE_SELF = 1, 2
 _DIM = {KS: 1, FHN: 2, HH: 4, KSI: 2}
 _NPARAM = {KS: 3, FHN: 4, HH: 8, KSI: 4}
@@ -53,6 +53,11 @@ def lib():
         _lib.orc_dp5_tableau.argtypes = [_dp, _dp, _dp, _dp]
         _lib.orc_dp5_n_out.argtypes = [c_double, c_double, c_double]
         _lib.orc_dp5_n_out.restype = i64
+        _lib.orc_set_graph.argtypes = [i64, _ip, _ip]
+        _lib.orc_compress.argtypes = [i64, _ip, _ip, ctypes.POINTER(i64), _ip, _ip, _ip, _ip]
+        _lib.orc_compress.restype = i64
+        _lib.orc_extract.argtypes = [i64, i64, i64, _ip, _ip, _ip, _ip, _ip]
+        _lib.orc_extract.restype = i64
         _lib.orc_order_parameter.argtypes = [i64, _dp]
         _lib.orc_order_parameter.restype = c_double
         for name in ("orc_hh_alpha_m", "orc_hh_beta_m", "orc_hh_alpha_h", "orc_hh_beta_h",
@@ -75,6 +80,8 @@ def _arr(a, n=None):
 
 
 def nodes_of(topo, N):
+    if topo == GRAPH:
+        return N
     if topo in (CUBE, BALL):
         return N ** 3
     if topo == DISK:
@@ -168,6 +175,57 @@ def window_sum(topo, N, R, f, query=None, flags=0):
     out = np.empty(q.size)
     _check(lib().orc_window_sum(topo, N, R, _d(f), q.size, q.ctypes.data_as(_ip), _d(out), flags), "window_sum")
     return out
+
+
+_graph_keep = None
+
+
+def set_graph(N, row_ptr, col):
+    """Use the link matrix given by rows (CSR: the links of node i are
+    col[row_ptr[i]:row_ptr[i+1]]) as topology GRAPH (then pass N and any R)."""
+    global _graph_keep
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    cl = np.ascontiguousarray(col, dtype=np.int64)
+    if rp.size != N + 1 or rp[-1] != cl.size:
+        raise ValueError("bad CSR")
+    if lib().orc_set_graph(N, rp.ctypes.data_as(_ip), cl.ctypes.data_as(_ip) if cl.size else None) != 0:
+        raise ValueError("bad CSR")
+    _graph_keep = (rp, cl)
+
+
+def compress(N, row_ptr, col):
+    """Algorithm 2 COMPRESS: returns (V, d_ptr, d_pos, C)."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    cl = np.ascontiguousarray(col, dtype=np.int64)
+    nv = ctypes.c_int64(0)
+    cptr = cl.ctypes.data_as(_ip) if cl.size else None
+    ne = lib().orc_compress(N, rp.ctypes.data_as(_ip), cptr, ctypes.byref(nv), None, None, None, None)
+    if ne < 0:
+        raise ValueError("compress failed")
+    # second pass with outputs sized from the first (the table of a pass never
+    # exceeds the input size)
+    v = np.empty(max(nv.value, 1), dtype=np.int64)
+    d_ptr = np.empty(ne + 1, dtype=np.int64)
+    d_pos = np.empty(max(int(cl.size) + N * max(nv.value, 1), 1), dtype=np.int64)
+    c = np.empty(N, dtype=np.int64)
+    ne2 = lib().orc_compress(N, rp.ctypes.data_as(_ip), cptr, ctypes.byref(nv), v.ctypes.data_as(_ip),
+                             d_ptr.ctypes.data_as(_ip), d_pos.ctypes.data_as(_ip), c.ctypes.data_as(_ip))
+    assert ne2 == ne
+    return v[: nv.value], d_ptr, d_pos[: d_ptr[-1]], c
+
+
+def extract(N, i, v, d_ptr, d_pos, c):
+    """Algorithm 2 EXTRACT: the sorted links of row i."""
+    v = np.ascontiguousarray(v, dtype=np.int64)
+    d_ptr = np.ascontiguousarray(d_ptr, dtype=np.int64)
+    d_pos = np.ascontiguousarray(d_pos, dtype=np.int64)
+    c = np.ascontiguousarray(c, dtype=np.int64)
+    e = int(c[i])
+    row = np.empty(v.size + int(d_ptr[e + 1] - d_ptr[e]) + 1, dtype=np.int64)
+    n = lib().orc_extract(N, i, v.size, v.ctypes.data_as(_ip), d_ptr.ctypes.data_as(_ip),
+                          d_pos.ctypes.data_as(_ip) if d_pos.size else None, c.ctypes.data_as(_ip),
+                          row.ctypes.data_as(_ip))
+    return row[:n]
 
 
 def order_parameter(phi):

@@ -27,6 +27,9 @@
  *   - Kuramoto-Sakaguchi with inertia, Eq. (3) with m != 0, as phi' = psi,
  *     psi' = ((mu/K) sum_j sin(phi_j - phi_i - alpha) - eps psi) / m.
  *   - Kuramoto order parameter |sum_j exp(i phi_j)| / n.
+ *   - A general link matrix given by rows (Section III.C), every model, each node
+ *     normalised by its own link count; and the differential compression of
+ *     the link matrix, Algorithm 2 (COMPRESS and EXTRACT).
  *   - Adaptive Dormand-Prince 5(4) (the paper's default solver, Section III.A):
  *     the published RK5(4)7M tableau, the mixed error norm and step-size
  *     controller of the textbook, and cubic Hermite dense output (the paper
@@ -46,7 +49,28 @@
 #endif
 
 enum { ORC_KS = 0, ORC_FHN = 1, ORC_HH = 2, ORC_KSI = 3 };
-enum { ORC_RING = 0, ORC_CUBE = 1, ORC_BALL = 2, ORC_DISK = 3 };
+enum { ORC_RING = 0, ORC_CUBE = 1, ORC_BALL = 2, ORC_DISK = 3, ORC_GRAPH = 4 };
+
+/* A general link matrix (Section III.C: L_ij = 1 when oscillator j influences
+ * oscillator i), given by rows: the links of node i are col[row_ptr[i] ..
+ * row_ptr[i+1]).  Set with orc_set_graph before using topology ORC_GRAPH (N is
+ * then the number of nodes and R is ignored).  The oracle keeps a pointer to the
+ * caller's arrays; they must stay valid while it is used. */
+static int64_t g_graph_n = 0;
+static const int64_t *g_graph_ptr = NULL, *g_graph_col = NULL;
+
+int orc_set_graph(int64_t n, const int64_t *row_ptr, const int64_t *col)
+{
+    if (n < 1 || !row_ptr || (row_ptr[n] > 0 && !col)) return -1;
+    for (int64_t i = 0; i < n; ++i)
+        if (row_ptr[i + 1] < row_ptr[i]) return -1;
+    for (int64_t t = 0; t < row_ptr[n]; ++t)
+        if (col[t] < 0 || col[t] >= n) return -1;
+    g_graph_n = n;
+    g_graph_ptr = row_ptr;
+    g_graph_col = col;
+    return 0;
+}
 enum { ORC_REVERSE = 1, ORC_INCLUDE_SELF = 2 };
 enum { ORC_OK = 0, ORC_EINVAL = -1, ORC_ENOMEM = -2, ORC_ESTEPS = -3, ORC_ESMALL = -4 };
 
@@ -68,7 +92,7 @@ int64_t orc_nodes(int topo, int64_t N)
 {
     if (topo == ORC_CUBE || topo == ORC_BALL) return N * N * N;
     if (topo == ORC_DISK) return N * N;
-    return N;
+    return N; /* ring, graph */
 }
 
 static int n_params_of(int model)
@@ -85,8 +109,9 @@ static int n_params_of(int model)
 int orc_validate(int model, int topo, int64_t N, int64_t R, int n_params)
 {
     if (orc_dim(model) == 0) return ORC_EINVAL;
-    if (topo < ORC_RING || topo > ORC_DISK) return ORC_EINVAL;
+    if (topo < ORC_RING || topo > ORC_GRAPH) return ORC_EINVAL;
     if (n_params != n_params_of(model)) return ORC_EINVAL;
+    if (topo == ORC_GRAPH) return (g_graph_ptr && N == g_graph_n) ? ORC_OK : ORC_EINVAL;
     if (R < 1 || N < 2 * R + 1) return ORC_EINVAL;
     if (topo != ORC_RING && model != ORC_KS && model != ORC_KSI) return ORC_EINVAL;
     return ORC_OK;
@@ -109,7 +134,10 @@ static int64_t wrap(int64_t a, int64_t n)
 static int64_t list_window(int topo, int64_t N, int64_t R, int64_t node, int include_self, int64_t *nb)
 {
     int64_t c = 0;
-    if (topo == ORC_RING) {
+    if (topo == ORC_GRAPH) { /* the row of the link matrix, as given (self only if listed) */
+        (void)include_self;
+        for (int64_t t = g_graph_ptr[node]; t < g_graph_ptr[node + 1]; ++t) nb[c++] = g_graph_col[t];
+    } else if (topo == ORC_RING) {
         for (int64_t d = -R; d <= R; ++d) {
             if (d == 0 && !include_self) continue;
             nb[c++] = wrap(node + d, N);
@@ -138,6 +166,12 @@ static int64_t list_window(int topo, int64_t N, int64_t R, int64_t node, int inc
 /* An upper bound of the window size (the enclosing box). */
 static int64_t window_size(int topo, int64_t R, int include_self)
 {
+    if (topo == ORC_GRAPH) {
+        int64_t m = 1;
+        for (int64_t i = 0; i < g_graph_n; ++i)
+            if (g_graph_ptr[i + 1] - g_graph_ptr[i] > m) m = g_graph_ptr[i + 1] - g_graph_ptr[i];
+        return m;
+    }
     int64_t w = 2 * R + 1;
     int64_t full = topo == ORC_RING ? w : (topo == ORC_DISK ? w * w : w * w * w);
     return include_self ? full : full - 1;
@@ -182,6 +216,7 @@ static void rhs_node(int model, int topo, int64_t N, int64_t R, const double *p,
     int include_self = (flags & ORC_INCLUDE_SELF) != 0;
     int64_t cnt = list_window(topo, N, R, i, include_self, nb);
     double K = (double)cnt;
+    /* cnt = 0 (a node without links, only on a graph): no coupling term */
     int64_t first = 0, last = cnt, step = 1;
     if (flags & ORC_REVERSE) { first = cnt - 1; last = -1; step = -1; }
 
@@ -190,7 +225,7 @@ static void rhs_node(int model, int topo, int64_t N, int64_t R, const double *p,
         double phi_i = x[i], sum = 0.0;
         for (int64_t t = first; t != last; t += step)
             sum += sin(phi_i - x[nb[t]] + alpha);
-        k[0] = omega - (mu / K) * sum;
+        k[0] = cnt > 0 ? omega - (mu / K) * sum : omega;
     } else if (model == ORC_KSI) {
         /* Eq. (3) with inertia: m phi'' + eps phi' = (mu/K) sum_j sin(phi_j - phi_i - alpha),
          * as the first-order system phi' = psi, psi' = ((mu/K) sum_j ... - eps psi) / m. */
@@ -200,7 +235,7 @@ static void rhs_node(int model, int topo, int64_t N, int64_t R, const double *p,
         for (int64_t t = first; t != last; t += step)
             sum += sin(phi[nb[t]] - phi_i - alpha);
         k[0] = psi[i];
-        k[1] = ((mu / K) * sum - eps * psi[i]) / m;
+        k[1] = ((cnt > 0 ? (mu / K) * sum : 0.0) - eps * psi[i]) / m;
     } else if (model == ORC_FHN) {
         double eps = p[0], a = p[1], sigma = p[2], phi = p[3];
         double buu = cos(phi), buv = sin(phi), bvu = -sin(phi), bvv = cos(phi);
@@ -211,8 +246,9 @@ static void rhs_node(int model, int topo, int64_t N, int64_t R, const double *p,
             cu += buu * (u[j] - ui) + buv * (v[j] - vi);
             cv += bvu * (u[j] - ui) + bvv * (v[j] - vi);
         }
-        k[0] = (ui - ui * ui * ui / 3.0 - vi + (sigma / K) * cu) / eps;
-        k[1] = ui + a + (sigma / K) * cv;
+        const double sK = cnt > 0 ? sigma / K : 0.0;
+        k[0] = (ui - ui * ui * ui / 3.0 - vi + sK * cu) / eps;
+        k[1] = ui + a + sK * cv;
     } else { /* ORC_HH */
         double Cm = p[0], gNa = p[1], gK = p[2], gL = p[3];
         double ENa = p[4], EK = p[5], EL = p[6], g = p[7];
@@ -220,7 +256,7 @@ static void rhs_node(int model, int topo, int64_t N, int64_t R, const double *p,
         double Vi = V[i], mi = m[i], hi = h[i], ni = n[i];
         double sumV = 0.0;
         for (int64_t t = first; t != last; t += step) sumV += V[nb[t]];
-        double coupling = g * (sumV / K - Vi);
+        double coupling = cnt > 0 ? g * (sumV / K - Vi) : 0.0;
         double Iext = node_param ? node_param[i] : 0.0;
         double INa = gNa * mi * mi * mi * hi * (Vi - ENa);
         double IK = gK * ni * ni * ni * ni * (Vi - EK);
@@ -558,4 +594,107 @@ int orc_dp5(int model, int topo, int64_t N, int64_t R, const double *params, int
     for (int s = 0; s < 7; ++s) free(k[s]);
     free(tmp); free(ynew); free(phi);
     return st;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Algorithm 2 (Section III.C): differential compression of the link matrix.
+ * A row is the sorted set of positions of its set bits.  ROL by i moves bit p to
+ * (p - i) mod N; XOR of two rows is the symmetric difference of the sets.
+ *   COMPRESS: V = row 0; for each row i, d = XOR(ROL(row_i, i), V); C_i is the
+ *   index of d in the difference table D (d is appended if new).
+ *   EXTRACT(i) = ROR(XOR(V, D[C_i]), i), ROR by i moving bit p to (p + i) mod N.
+ * Outputs (caller-allocated, sizes from a first call with NULL outputs):
+ *   v[n_v], the sorted set V; d_ptr[n_d + 1] and d_pos[d_ptr[n_d]], the table D;
+ *   c[n] the entry of every row.  Returns n_d, or -1 on invalid input. */
+static int cmp_i64(const void *a, const void *b)
+{
+    const int64_t x = *(const int64_t *)a, y = *(const int64_t *)b;
+    return x < y ? -1 : (x > y);
+}
+
+/* symmetric difference of two sorted sets; returns its size */
+static int64_t sym_diff(const int64_t *a, int64_t na, const int64_t *b, int64_t nb, int64_t *out)
+{
+    int64_t i = 0, j = 0, c = 0;
+    while (i < na || j < nb) {
+        if (j >= nb || (i < na && a[i] < b[j])) out[c++] = a[i++];
+        else if (i >= na || b[j] < a[i]) out[c++] = b[j++];
+        else { ++i; ++j; }
+    }
+    return c;
+}
+
+int64_t orc_compress(int64_t n, const int64_t *row_ptr, const int64_t *col, int64_t *n_v, int64_t *v,
+                     int64_t *d_ptr, int64_t *d_pos, int64_t *c)
+{
+    if (n < 1) return -1;
+    int64_t maxrow = 0;
+    for (int64_t i = 0; i < n; ++i)
+        if (row_ptr[i + 1] - row_ptr[i] > maxrow) maxrow = row_ptr[i + 1] - row_ptr[i];
+    const int64_t nv = row_ptr[1] - row_ptr[0];
+    int64_t *V = malloc(sizeof(int64_t) * (size_t)(nv + 1));
+    int64_t *sh = malloc(sizeof(int64_t) * (size_t)(maxrow + 1));
+    int64_t *d = malloc(sizeof(int64_t) * (size_t)(maxrow + nv + 1));
+    /* the difference table, grown as needed */
+    int64_t cap_e = 16, cap_p = 1024, ne = 0;
+    int64_t *eptr = malloc(sizeof(int64_t) * (size_t)(cap_e + 1));
+    int64_t *epos = malloc(sizeof(int64_t) * (size_t)cap_p);
+    if (!V || !sh || !d || !eptr || !epos) {
+        free(V); free(sh); free(d); free(eptr); free(epos);
+        return -1;
+    }
+    for (int64_t t = 0; t < nv; ++t) V[t] = col[row_ptr[0] + t];
+    qsort(V, (size_t)nv, sizeof(int64_t), cmp_i64);
+    eptr[0] = 0;
+    int64_t result = 0;
+    for (int64_t i = 0; i < n && result >= 0; ++i) {
+        const int64_t len = row_ptr[i + 1] - row_ptr[i];
+        for (int64_t t = 0; t < len; ++t) sh[t] = wrap(col[row_ptr[i] + t] - i, n); /* ROL by i */
+        qsort(sh, (size_t)len, sizeof(int64_t), cmp_i64);
+        const int64_t nd = sym_diff(sh, len, V, nv, d); /* XOR with V */
+        int64_t found = -1;
+        for (int64_t e = 0; e < ne && found < 0; ++e) /* FIND in the table */
+            if (eptr[e + 1] - eptr[e] == nd && memcmp(epos + eptr[e], d, sizeof(int64_t) * (size_t)nd) == 0)
+                found = e;
+        if (found < 0) {
+            if (ne == cap_e) {
+                cap_e *= 2;
+                int64_t *q = realloc(eptr, sizeof(int64_t) * (size_t)(cap_e + 1));
+                if (!q) { result = -1; break; }
+                eptr = q;
+            }
+            while (eptr[ne] + nd > cap_p) {
+                cap_p *= 2;
+                int64_t *q = realloc(epos, sizeof(int64_t) * (size_t)cap_p);
+                if (!q) { result = -1; break; }
+                epos = q;
+            }
+            if (result < 0) break;
+            memcpy(epos + eptr[ne], d, sizeof(int64_t) * (size_t)nd);
+            eptr[ne + 1] = eptr[ne] + nd;
+            found = ne++;
+        }
+        if (c) c[i] = found;
+    }
+    if (result >= 0) {
+        *n_v = nv;
+        if (v) memcpy(v, V, sizeof(int64_t) * (size_t)nv);
+        if (d_ptr) memcpy(d_ptr, eptr, sizeof(int64_t) * (size_t)(ne + 1));
+        if (d_pos) memcpy(d_pos, epos, sizeof(int64_t) * (size_t)eptr[ne]);
+        result = ne;
+    }
+    free(V); free(sh); free(d); free(eptr); free(epos);
+    return result;
+}
+
+/* EXTRACT(i): writes the sorted links of row i into row (at most n_v plus the
+ * entry's size values) and returns their count. */
+int64_t orc_extract(int64_t n, int64_t i, int64_t n_v, const int64_t *v, const int64_t *d_ptr,
+                    const int64_t *d_pos, const int64_t *c, int64_t *row)
+{
+    const int64_t e = c[i];
+    const int64_t cnt = sym_diff(v, n_v, d_pos + d_ptr[e], d_ptr[e + 1] - d_ptr[e], row); /* XOR */
+    for (int64_t t = 0; t < cnt; ++t) row[t] = wrap(row[t] + i, n); /* ROR by i */
+    qsort(row, (size_t)cnt, sizeof(int64_t), cmp_i64);
+    return cnt;
 }

@@ -648,3 +648,119 @@ def test_dp5_attempt_budget_and_bad_arguments():
         oracle.dp5(oracle.KS, oracle.RING, 30, 5, I.ks_params(), y0, 1.0, 1.0, 1e-10, 1e-10, 0.01)
     with pytest.raises(ValueError):
         oracle.dp5(oracle.KS, oracle.RING, 30, 5, I.ks_params(), y0, 0.0, 1.0, 0.0, 0.0, 0.01)
+
+
+# ---------------------------------------------------------------- general link matrix, Algorithm 2
+def _csr(rows):
+    rp = np.cumsum([0] + [len(r) for r in rows]).astype(np.int64)
+    col = np.concatenate([np.asarray(r, dtype=np.int64) for r in rows]) if rp[-1] else np.zeros(0, np.int64)
+    return rp, col
+
+
+def _random_rows(N, p, seed, self_loops=False):
+    u = I.uniform(seed, 0, 0, N * N).reshape(N, N)
+    rows = []
+    for i in range(N):
+        r = [j for j in range(N) if u[i, j] < p and (self_loops or j != i)]
+        rows.append(r)
+    return rows
+
+
+def _small_world_rows(N, R, p, seed):
+    """Ring of radius R with each link rewired to a uniform target with probability p."""
+    u = I.uniform(seed, 0, 1, N * 2 * R).reshape(N, 2 * R)
+    t = I.uniform(seed, 0, 2, N * 2 * R).reshape(N, 2 * R)
+    rows = []
+    for i in range(N):
+        r = set()
+        for k, d in enumerate([d for d in range(-R, R + 1) if d]):
+            j = (i + d) % N
+            if u[i, k] < p:
+                j = int(t[i, k] * N) % N
+            if j != i:
+                r.add(j)
+        rows.append(sorted(r))
+    return rows
+
+
+@pytest.mark.parametrize("kind", ["erdos_renyi", "self_loops", "small_world", "ring", "star", "empty_rows"])
+def test_algorithm2_extract_inverts_compress(kind):
+    N = 97
+    rows = {"erdos_renyi": lambda: _random_rows(N, 0.06, 50),
+            "self_loops": lambda: _random_rows(N, 0.1, 51, self_loops=True),
+            "small_world": lambda: _small_world_rows(N, 4, 0.1, 52),
+            "ring": lambda: [[(i + d) % N for d in range(-5, 6) if d] for i in range(N)],
+            "star": lambda: [list(range(1, N))] + [[0] for _ in range(1, N)],
+            "empty_rows": lambda: [[] if i % 7 == 0 else [(i + 1) % N] for i in range(N)]}[kind]()
+    rp, col = _csr(rows)
+    V, dp, dpos, C = oracle.compress(N, rp, col)
+    for i in range(N):
+        assert list(oracle.extract(N, i, V, dp, dpos, C)) == sorted(rows[i])
+
+
+def test_algorithm2_ring_and_full_mesh():
+    """A ring: every shifted row equals row 0, so one empty difference entry;
+    the full mesh (every bit set) gives V = all ones and one empty entry, as the
+    paper states for it."""
+    N, R = 100, 7
+    rp, col = _csr([[(i + d) % N for d in range(-R, R + 1) if d] for i in range(N)])
+    V, dp, dpos, C = oracle.compress(N, rp, col)
+    assert list(V) == list(range(1, R + 1)) + list(range(N - R, N))
+    assert list(dp) == [0, 0] and np.all(C == 0)
+    rp, col = _csr([list(range(N)) for _ in range(N)])
+    V, dp, dpos, C = oracle.compress(N, rp, col)
+    assert list(V) == list(range(N)) and list(dp) == [0, 0] and np.all(C == 0)
+
+
+def test_algorithm2_ball_lattice_has_one_entry_per_xy_boundary_class():
+    """The periodic ball lattice in the paper's linear index k N1^2 + j N1 + i:
+    shifted rows differ only where the window wraps in x or y (a wrap in z moves
+    the linear offset by N1^3 = N, invisible mod N), so the table has
+    (2P+1)^2 entries; interior rows map to the empty entry."""
+    N1, P = 12, 2
+    n = N1 ** 3
+    rows = []
+    for node in range(n):
+        i, j, k = node % N1, (node // N1) % N1, node // (N1 * N1)
+        r = sorted(((k + dz) % N1) * N1 * N1 + ((j + dy) % N1) * N1 + (i + dx) % N1
+                   for dz in range(-P, P + 1) for dy in range(-P, P + 1) for dx in range(-P, P + 1)
+                   if dx * dx + dy * dy + dz * dz <= P * P and (dx, dy, dz) != (0, 0, 0))
+        rows.append(r)
+    rp, col = _csr(rows)
+    V, dp, dpos, C = oracle.compress(n, rp, col)
+    assert dp.size - 1 == (2 * P + 1) ** 2
+    center = (N1 // 2) * N1 * N1 + (N1 // 2) * N1 + N1 // 2
+    assert dp[C[center] + 1] - dp[C[center]] == 0 or C[center] == C[center + N1 * N1]
+    for node in (0, center, n - 1, 5 * N1 + 1):
+        assert list(oracle.extract(n, node, V, dp, dpos, C)) == rows[node]
+
+
+@pytest.mark.parametrize("model", [0, 1, 2, 3])
+def test_graph_rows_of_a_ring_give_the_ring_bit_for_bit(model):
+    """The ring written as a link matrix (rows in the ring's offset order) gives
+    the ring's right-hand side exactly: per-node normalisation by the row length
+    and the self handling agree with the ring path."""
+    N, R = 60, 9
+    rows = [[(i + d) % N for d in range(-R, R + 1) if d] for i in range(N)]
+    rp, col = _csr(rows)
+    oracle.set_graph(N, rp, col)
+    params = [I.ks_params, I.fhn_params, I.hh_params, I.ksi_params][model]()
+    y0 = I.initial_state(model, 53, 0, N)
+    npar = I.hh_iext(53, 0, N) if model == 2 else None
+    a = oracle.rhs(model, oracle.GRAPH, N, 0, params, y0, node_param=npar)
+    b = oracle.rhs(model, oracle.RING, N, R, params, y0, node_param=npar)
+    assert np.array_equal(a, b)
+
+
+def test_graph_in_phase_rotation_with_uneven_degrees():
+    """All phases equal on a star with isolated nodes: every node with links
+    rotates at omega - mu sin(alpha) whatever its degree (per-node mean), an
+    isolated node at omega."""
+    N = 40
+    rows = [list(range(1, 30))] + [[0] for _ in range(1, 30)] + [[] for _ in range(30, N)]
+    rp, col = _csr(rows)
+    oracle.set_graph(N, rp, col)
+    omega, mu, alpha = 0.3, 0.8, 1.2
+    k = oracle.rhs(oracle.KS, oracle.GRAPH, N, 0, [omega, mu, alpha], np.full(N, 0.7))
+    assert np.abs(k[:30] - (omega - mu * math.sin(alpha))).max() < 1e-15
+    assert np.all(k[30:] == omega)
