@@ -69,7 +69,9 @@ typedef enum { SIM_KS = 0, SIM_FHN = 1, SIM_HH = 2, SIM_KSI = 3 } sim_model;
  * SIM_DISK2D  periodic N1^2 lattice (N1 <= 8192), dx^2 + dy^2 <= P^2, 2P+1 <= N1.
  * Lattice nodes are numbered k N1^2 + j N1 + i (x = i fastest).  The lattices
  * take the Kuramoto models (SIM_KS, SIM_KSI) only. */
-typedef enum { SIM_RING = 0, SIM_CUBE3D = 1, SIM_BALL3D = 2, SIM_DISK2D = 3 } sim_topology;
+typedef enum { SIM_RING = 0, SIM_CUBE3D = 1, SIM_BALL3D = 2, SIM_DISK2D = 3, SIM_GRAPH = 4 } sim_topology;
+/* SIM_GRAPH   a general link matrix (Section III.C), created with
+ *             sim_create_graph, not sim_create. */
 
 typedef enum {
     SIM_OK = 0,
@@ -108,6 +110,29 @@ int sim_create(sim_t *out, int model, int topology, int64_t N, int64_t radius,
  * misaligned or too small workspace. */
 int sim_create_in(sim_t *out, int model, int topology, int64_t N, int64_t radius, const double *params,
                   int n_params, unsigned flags, void *dev_workspace, size_t workspace_bytes, void *stream);
+
+/* A network on a general link matrix (Section III.C: L_ij = 1 when node j
+ * influences node i), every model.  Host arrays, read during the call only:
+ * row_ptr[N + 1] (row_ptr[0] = 0, non-decreasing) and col[row_ptr[N]]; the links
+ * of node i are col[row_ptr[i] .. row_ptr[i+1]), each in [0, N), no duplicates
+ * within a row (a self link is allowed and counts as a link).  The coupling of
+ * node i is normalised by its own link count K_i (the mean over its links, as
+ * Algorithm 1 does with links_amount); a node without links has no coupling
+ * term.  The matrix is compressed with Algorithm 2 (common vector V = row 0,
+ * difference table of XOR(ROL(row_i, i), V), one entry index per node) and the
+ * device evaluates each node's sum as runs of V read from an exact prefix of
+ * the coupled quantity plus its entry's signed links: O(runs of V + entry size)
+ * reads per node instead of one per link.  3 <= N < 2^31.  The network then
+ * steps with sim_step (RK4) and supports every call taking a sim_t except
+ * sim_dp5, budgets and the server.  Errors: SIM_EINVAL (invalid matrix, model
+ * or parameters; the message says which), SIM_ENOMEM, SIM_EDEVICE. */
+int sim_create_graph(sim_t *out, int model, int64_t N, const int64_t *row_ptr, const int64_t *col,
+                     const double *params, int n_params, void *stream);
+
+/* Size of the compressed link matrix of a SIM_GRAPH network: difference-table
+ * entries, runs of the common vector, device bytes of the tables.  Any output
+ * may be NULL.  SIM_EINVAL for other networks. */
+int sim_graph_info(sim_t h, int64_t *n_entries, int64_t *n_runs, size_t *device_bytes);
 
 /* Number of nodes (N, N1^3 or N1^2) and of state variables per node. */
 int64_t sim_nodes(sim_t h);

@@ -4,5 +4,5 @@ The hot path (the fused RK4 stage kernels) lives in libsim.so behind the C ABI o
 include/sim.h; ``sim`` is its thin Python binding, ``inputs`` the seeded
 synthetic workloads.
 """
-from .sim import (BALL3D, CUBE3D, DISK2D, FHN, HH, KS, KSI, RING, Batch, Network, Server,  # noqa: F401
+from .sim import (BALL3D, CUBE3D, DISK2D, FHN, GRAPH, HH, KS, KSI, RING, Batch, Network, Server,  # noqa: F401
                   workspace_bytes)

@@ -68,6 +68,8 @@ SIGNATURES = {
     "sim_ring_step_noalloc": (_int, [_int, _i64, _i64, _dp, _int, _uint, _vp, _vp, _i64, _dbl, _vp]),
     "sim_steps_done": (_i64, [_vp]),
     "sim_dp5": (_int, [_vp, ctypes.POINTER(DP5Opts), ctypes.POINTER(DP5Stats)]),
+    "sim_create_graph": (_int, [ctypes.POINTER(_vp), _int, _i64, _vp, _vp, _dp, _int, _vp]),
+    "sim_graph_info": (_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_sz)]),
     "sim_batch_dp5": (_int, [_vp, ctypes.POINTER(DP5Opts), ctypes.POINTER(DP5Stats)]),
     "sim_last_error": (ctypes.c_char_p, []),
     "sim_destroy": (None, [_vp]),

@@ -1,0 +1,130 @@
+// General link matrices (Section III.C) stepped with RK4 through the compressed
+// form of Algorithm 2.
+//
+// COMPRESS (on the host, sim_api.cu) keeps the common vector V = row 0 and, for
+// every row i, a reference C_i to the difference entry D = XOR(ROL(row_i, i), V);
+// EXTRACT gives row i = ROR(XOR(V, D_{C_i}), i).  So the coupling sum of node i is
+//   W(i) = sum_{p in V} Q(x_{i+p}) + sum_{p in D_{C_i}} s_p Q(x_{i+p})   (indices mod N)
+// with s_p = -1 where p is in V (the XOR clears that bit) and +1 elsewhere.  Here
+// V is stored as runs of consecutive offsets [a, a + len), and the sum over a run
+// is the difference of two entries of the exact prefix of Q in node order,
+//   P(i + a + len) - P(i + a),
+// the same exact fixed-point prefix the ring stage kernels build (P over the
+// periodic extension).  A node therefore costs O(number of runs + size of its
+// difference entry) reads instead of one per link: a ring is two runs and the
+// empty entry, a periodic lattice a few runs per row of its window plus the
+// wrapped links near the boundary.  The degree of the node (its link count, which
+// normalises the coupling) comes with its entry.
+#include "ring_parts.cuh"
+
+namespace simk {
+
+// Exact prefix P(pos) = sum_{m < pos} Q_m of component c on the periodic
+// extension, pos in [0, 2N).
+__device__ __forceinline__ i128 graph_prefix_at(const RingPlan &P, const RingStageIO &a, int c, int64_t pos)
+{
+    const int64_t N = P.N;
+    const i128 *grpofs = a.grpofs_in + c * (P.ngroups + 1);
+    i128 base = 0;
+    if (pos >= N) {
+        pos -= N;
+        base = ldg_i128(grpofs + P.ngroups);
+    }
+    if (pos == 0) return base;
+    const int64_t s = (pos - 1) >> kSubLog2;
+    return base + ldg_i128(grpofs + (s >> kGroupLog2)) + ldg_i128(a.ingrp_in + c * P.nsub + s) +
+           (i128)__ldg(a.lam_in + c * N + pos - 1);
+}
+
+template <int NQ> struct GraphGather {
+    const GraphPlan &G;
+    const RingStageIO &a;
+    __device__ __forceinline__ void operator()(int tid, int64_t i, int64_t (&qo)[NQ], double (&fo)[NQ],
+                                               i128 (&W)[NQ], int64_t &wsize, double &cs) const
+    {
+        const RingPlan &P = G.r;
+        const int64_t N = P.N;
+#pragma unroll
+        for (int c = 0; c < NQ; ++c) {
+            const int64_t *lam = a.lam_in + c * N;
+            const int64_t l = __ldg(lam + i);
+            qo[c] = tid ? l - __ldg(lam + i - 1) : l;
+            fo[c] = fixed_to_double(qo[c], P.F);
+            W[c] = 0;
+        }
+        // the common vector: runs of consecutive offsets
+        for (int r = 0; r < G.nruns; ++r) {
+            const int2 run = __ldg(G.runs + r); // (a, len), a + len <= N
+            const int64_t lo = i + run.x, hi = lo + run.y;
+#pragma unroll
+            for (int c = 0; c < NQ; ++c) W[c] += graph_prefix_at(P, a, c, hi) - graph_prefix_at(P, a, c, lo);
+        }
+        // the node's difference entry: signed single links
+        const int e = __ldg(G.ent + i);
+        const int64_t t0 = __ldg(G.dptr + e), t1 = __ldg(G.dptr + e + 1);
+        for (int64_t t = t0; t < t1; ++t) {
+            const int2 d = __ldg(G.dpos + t); // (offset, sign)
+            int64_t j = i + d.x;
+            j -= j >= N ? N : 0;
+#pragma unroll
+            for (int c = 0; c < NQ; ++c) {
+                const int64_t *lam = a.lam_in + c * N;
+                const int64_t q = (j & (kSubTile - 1)) ? __ldg(lam + j) - __ldg(lam + j - 1) : __ldg(lam + j);
+                W[c] += d.y > 0 ? (i128)q : -(i128)q;
+            }
+        }
+        wsize = __ldg(G.ek + e);
+        cs = __ldg(G.ecs + e);
+    }
+};
+
+// the run loop and 128-bit window sums need more registers than the ring kernel
+template <int M> struct GraphMinBlocks { static constexpr int value = 3; };
+template <> struct GraphMinBlocks<2> { static constexpr int value = 2; };
+
+template <int M, int STAGE>
+__global__ void __launch_bounds__(kRingThreads, GraphMinBlocks<M>::value)
+    graph_stage_kernel(const GraphPlan g, double dt)
+{
+    const RingStageIO a = stage_io<M, STAGE>(g.r);
+    stage_body<M, STAGE>(g.r, a, dt, blockIdx.x, GraphGather<Model<M>::NQ>{g, a});
+}
+
+template <int M>
+static cudaError_t launch_stage(int stage, const GraphPlan &g, double dt, cudaStream_t s)
+{
+    const dim3 grid((unsigned)g.r.nsub), block(kRingThreads);
+    switch (stage) {
+    case 1: graph_stage_kernel<M, 1><<<grid, block, 0, s>>>(g, dt); break;
+    case 2: graph_stage_kernel<M, 2><<<grid, block, 0, s>>>(g, dt); break;
+    case 3: graph_stage_kernel<M, 3><<<grid, block, 0, s>>>(g, dt); break;
+    default: graph_stage_kernel<M, 4><<<grid, block, 0, s>>>(g, dt); break;
+    }
+    return cudaGetLastError();
+}
+
+static cudaError_t launch_any(int stage, const GraphPlan &g, double dt, cudaStream_t s)
+{
+    switch (g.r.model) {
+    case 0: return launch_stage<0>(stage, g, dt, s);
+    case 1: return launch_stage<1>(stage, g, dt, s);
+    case 2: return launch_stage<2>(stage, g, dt, s);
+    default: return launch_stage<3>(stage, g, dt, s);
+    }
+}
+
+cudaError_t graph_rhs(const GraphPlan &g, cudaStream_t s)
+{
+    return launch_any(1, g, 0.0, s);
+}
+
+cudaError_t graph_step(const GraphPlan &g, double dt, cudaStream_t s)
+{
+    for (int stage = 1; stage <= 4; ++stage) {
+        const cudaError_t e = launch_any(stage, g, dt, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+} // namespace simk

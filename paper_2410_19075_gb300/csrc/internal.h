@@ -54,6 +54,21 @@ struct RingBatchGroup {
 // Batched ring stage kernels: one RK4 step of every member of the group.
 cudaError_t ring_batch_step(const RingBatchGroup &g, double dt, cudaStream_t s);
 
+// General link matrix in the compressed form of Algorithm 2 (graph.cu): the ring
+// buffers (exact prefix in node order, states, observables) plus the tables.
+struct GraphPlan {
+    RingPlan r;            // r.R is unused; r.mp carries K = 1 and include_self = 1
+    const int2 *runs;      // the common vector V as runs (first offset, length), first + length <= N
+    int nruns;
+    const int *ent;        // N: difference-table entry of every node
+    const int64_t *dptr;   // entries + 1: start of every entry in dpos
+    const int2 *dpos;      // (offset p, sign): -1 where p is in V (the bit is cleared), +1 elsewhere
+    const int64_t *ek;     // per entry: the link count K = |V| + sum of its signs
+    const double *ecs;     // per entry: 1 / K (0 for a node without links)
+};
+cudaError_t graph_rhs(const GraphPlan &g, cudaStream_t s);             // acc <- f(y), stage 1 with dt = 0
+cudaError_t graph_step(const GraphPlan &g, double dt, cudaStream_t s); // one RK4 step
+
 // Adaptive Dormand-Prince 5(4) on rings (dp5.cu), per instance in a batch.
 constexpr int kDpMaxOut = 16; // dense outputs handled inside one step (the step is capped at 8 of them)
 constexpr int kDpStatusSteps = -7, kDpStatusSmall = -8; // = SIM_ESTEPS, SIM_ESMALL

@@ -10,6 +10,11 @@
 
 namespace simk {
 
+// Every rhs() takes the node's window sums W; on a general link matrix it also
+// takes the node's link count (wsize, the FHN/HH self-term multiplier; -1 = the
+// network's) and a coupling scale cs = 1/K_i applied to the converted sums (the
+// constants c then carry K = 1).  The ring and lattice paths use the defaults.
+
 // Derived constants, computed once on the host in FP64.
 struct ModelParams {
     double c[8];
@@ -34,11 +39,12 @@ template <> struct Model<0> {
     }
     __device__ __forceinline__ static void rhs(const ModelParams &P, int F_, const double (&fo)[NQ],
                                                const int64_t (&qo)[NQ], const i128 (&W)[NQ],
-                                               const double *, double, double (&k)[D])
+                                               const double *X, double Iext, double (&k)[D],
+                                               int64_t = 0, double cs = 1.0)
     {
         const i128 ss = P.include_self ? W[0] : W[0] - (i128)qo[0];
         const i128 sc = P.include_self ? W[1] : W[1] - (i128)qo[1];
-        const double Ss = fixed_to_double_wide(ss, F_), Sc = fixed_to_double_wide(sc, F_);
+        const double Ss = cs * fixed_to_double_wide(ss, F_), Sc = cs * fixed_to_double_wide(sc, F_);
         const double s = fo[0], c = fo[1];
         const double sxa = s * P.c[3] + c * P.c[2]; // sin(phi + alpha)
         const double cxa = c * P.c[3] - s * P.c[2]; // cos(phi + alpha)
@@ -63,10 +69,12 @@ template <> struct Model<1> {
     }
     __device__ __forceinline__ static void rhs(const ModelParams &P, int F_, const double (&fo)[NQ],
                                                const int64_t (&qo)[NQ], const i128 (&W)[NQ],
-                                               const double *, double, double (&k)[D])
+                                               const double *X, double Iext, double (&k)[D],
+                                               int64_t wsize = -1, double cs = 1.0)
     {
-        const double Cu = fixed_to_double_wide(W[0] - (i128)qo[0] * P.wsize, F_);
-        const double Cv = fixed_to_double_wide(W[1] - (i128)qo[1] * P.wsize, F_);
+        const int64_t ws = wsize < 0 ? P.wsize : wsize;
+        const double Cu = cs * fixed_to_double_wide(W[0] - (i128)qo[0] * ws, F_);
+        const double Cv = cs * fixed_to_double_wide(W[1] - (i128)qo[1] * ws, F_);
         const double u = fo[0], v = fo[1];
         const double w = fma(u * u, -1.0 / 3.0, 1.0);      // 1 - u^2/3
         const double local = fma(u, w, -v);                // u - u^3/3 - v
@@ -90,9 +98,11 @@ template <> struct Model<2> {
     }
     __device__ __forceinline__ static void rhs(const ModelParams &P, int F_, const double (&fo)[NQ],
                                                const int64_t (&qo)[NQ], const i128 (&W)[NQ],
-                                               const double *X, double Iext, double (&k)[D])
+                                               const double *X, double Iext, double (&k)[D],
+                                               int64_t wsize = -1, double cs = 1.0)
     {
-        const double CV = fixed_to_double_wide(W[0] - (i128)qo[0] * P.wsize, F_);
+        const int64_t ws = wsize < 0 ? P.wsize : wsize;
+        const double CV = cs * fixed_to_double_wide(W[0] - (i128)qo[0] * ws, F_);
         const double V = fo[0], m = X[0], h = X[1], n = X[2];
         const MathTables &T = P.tab;
         const double am = fast_x_over_1mexp(fma(V, 0.1, 4.0), T);                    // (V+40)/10
@@ -124,11 +134,12 @@ template <> struct Model<3> {
     }
     __device__ __forceinline__ static void rhs(const ModelParams &P, int F_, const double (&fo)[NQ],
                                                const int64_t (&qo)[NQ], const i128 (&W)[NQ],
-                                               const double *X, double, double (&k)[D])
+                                               const double *X, double Iext, double (&k)[D],
+                                               int64_t = 0, double cs = 1.0)
     {
         const i128 ss = P.include_self ? W[0] : W[0] - (i128)qo[0];
         const i128 sc = P.include_self ? W[1] : W[1] - (i128)qo[1];
-        const double Ss = fixed_to_double_wide(ss, F_), Sc = fixed_to_double_wide(sc, F_);
+        const double Ss = cs * fixed_to_double_wide(ss, F_), Sc = cs * fixed_to_double_wide(sc, F_);
         const double s = fo[0], c = fo[1], psi = X[0];
         const double sxa = s * P.c[3] + c * P.c[2]; // sin(phi + alpha)
         const double cxa = c * P.c[3] - s * P.c[2]; // cos(phi + alpha)

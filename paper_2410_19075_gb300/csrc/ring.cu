@@ -18,105 +18,28 @@
 
 namespace simk {
 
-// Buffers one stage reads and writes (chosen by the stage's parity).
-struct RingStageIO {
+// Ring window: the node's two window ends read through the per-CTA bases.
+template <int NQ> struct RingGather {
+    const RingPlan &P;
     const int64_t *lam_in;
-    const i128 *ingrp_in, *grpofs_in;
-    int64_t *lam_out;
-    i128 *ingrp_out, *grpofs_out;
-    const double *x_in; // local stage-input variables of this stage (HH gates)
-    double *x_out;      // local stage-input variables of the next stage
-};
-
-// Stage 0 (prologue) writes buffer 0; stage s reads buffer (s+1)&1 and writes
-// s&1, so stage 4 leaves f(y_{n+1}) in buffer 0 for the next step.
-template <int M, int STAGE>
-__host__ __device__ __forceinline__ RingStageIO stage_io(const RingPlan &p)
-{
-    constexpr int D = Model<M>::D, NX = Model<M>::NX;
-    constexpr int in = (STAGE + 1) & 1, out = STAGE == 0 ? 0 : (STAGE & 1);
-    RingStageIO a;
-    a.lam_in = STAGE ? p.lam[in] : nullptr;
-    a.ingrp_in = STAGE ? p.ingrp[in] : nullptr;
-    a.grpofs_in = STAGE ? p.grpofs[in] : nullptr;
-    a.lam_out = p.lam[out];
-    a.ingrp_out = p.ingrp[out];
-    a.grpofs_out = p.grpofs[out];
-    a.x_in = nullptr;
-    a.x_out = nullptr;
-    if (NX > 0) {
-        a.x_in = STAGE == 1 ? p.y + (int64_t)(D - NX) * p.N : STAGE == 3 ? p.xg[1] : STAGE ? p.xg[0] : nullptr;
-        a.x_out = STAGE == 1 || STAGE == 3 ? p.xg[0] : STAGE == 2 ? p.xg[1] : nullptr;
+    const RingBases<NQ> &B;
+    __device__ __forceinline__ void operator()(int tid, int64_t i, int64_t (&qo)[NQ], double (&fo)[NQ],
+                                               i128 (&W)[NQ], int64_t &wsize, double &cs) const
+    {
+        ring_window<NQ>(P, lam_in, B, tid, i, qo, fo, W);
+        wsize = -1; // the network's window size
+        cs = 1.0;
     }
-    return a;
-}
+};
 
 // One 256-node sub-tile `sub` of ring P, one node per thread (the whole CTA).
 template <int M, int STAGE>
 __device__ __forceinline__ void ring_stage_body(const RingPlan &P, const RingStageIO &a, double dt, int64_t sub)
 {
-    using Mo = Model<M>;
-    constexpr int D = Mo::D, NQ = Mo::NQ, NX = Mo::NX;
-    constexpr int XOFF = D - NX; // first local (non-coupled) state variable
+    constexpr int NQ = Model<M>::NQ;
     __shared__ RingBases<NQ> s_bases;
-
-    const int tid = threadIdx.x;
-    const int64_t N = P.N;
-    const int64_t i = sub * kSubTile + tid;
     if (STAGE > 0) ring_load_bases<NQ>(P, a.ingrp_in, a.grpofs_in, sub, s_bases);
-
-    int64_t qv[NQ];
-    bool ok = true;
-#pragma unroll
-    for (int c = 0; c < NQ; ++c) qv[c] = 0;
-    if (i < N) {
-        double xn[D];
-        if (STAGE == 0) {
-#pragma unroll
-            for (int v = 0; v < D; ++v) xn[v] = P.y[v * N + i];
-        } else {
-            int64_t qo[NQ];
-            double fo[NQ];
-            i128 W[NQ];
-            ring_window<NQ>(P, a.lam_in, s_bases, tid, i, qo, fo, W);
-            double X[NX > 0 ? NX : 1];
-#pragma unroll
-            for (int g = 0; g < NX; ++g) X[g] = a.x_in[g * N + i];
-            const double Iext = (M == 2 && P.node_param) ? P.node_param[i] : 0.0;
-            double k[D];
-            Mo::rhs(P.mp, P.F, fo, qo, W, X, Iext, k);
-#pragma unroll
-            for (int v = 0; v < D; ++v) {
-                const double yv = P.y[v * N + i];
-                if (STAGE == 1) {
-                    P.acc[v * N + i] = k[v];
-                    xn[v] = yv + (0.5 * dt) * k[v];
-                } else if (STAGE == 2) {
-                    P.acc[v * N + i] = P.acc[v * N + i] + 2.0 * k[v];
-                    xn[v] = yv + (0.5 * dt) * k[v];
-                } else if (STAGE == 3) {
-                    P.acc[v * N + i] = P.acc[v * N + i] + 2.0 * k[v];
-                    xn[v] = yv + dt * k[v];
-                } else {
-                    const double yn = yv + (dt / 6.0) * (P.acc[v * N + i] + k[v]);
-                    P.y[v * N + i] = yn;
-                    xn[v] = yn;
-                }
-            }
-            if (NX > 0 && STAGE >= 1 && STAGE <= 3) {
-#pragma unroll
-                for (int g = 0; g < NX; ++g) a.x_out[g * N + i] = xn[XOFF + g];
-            }
-        }
-        // a2: coupled quantity of the next stage input on the fixed-point grid
-        double f[NQ];
-        Mo::coupled(P.mp, xn, f);
-#pragma unroll
-        for (int c = 0; c < NQ; ++c) qv[c] = to_fixed(f[c], P.F, P.lim, ok);
-    }
-    if (!ok) raise_error(P.err, ERR_RANGE);
-    ring_prefix_tail<NQ, (M == 0 || M == 3) && (STAGE == 0 || STAGE == 4), STAGE == 4>(P, a.lam_out, a.ingrp_out,
-                                                                                     a.grpofs_out, sub, i, qv);
+    stage_body<M, STAGE>(P, a, dt, sub, RingGather<NQ>{P, a.lam_in, s_bases});
 }
 
 // Plain path: one ring, one sub-tile per CTA.

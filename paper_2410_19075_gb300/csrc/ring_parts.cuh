@@ -11,7 +11,9 @@
 //                     sub-tile and, without any CTA waiting for another, at every
 //                     sub-tile start: the last CTA to finish in each group of 64
 //                     sub-tiles scans that group, and the last group scans the
-//                     groups (and may record the Kuramoto order parameter).
+//                     groups (and may record the Kuramoto order parameter);
+//   stage_body        one fused RK4 stage around a gather of the window sums
+//                     (ring windows here, general link matrices in graph.cu).
 #pragma once
 #include "internal.h"
 
@@ -191,6 +193,111 @@ __device__ __forceinline__ void ring_prefix_tail(const RingPlan &P, int64_t *lam
         *P.obs_ctr = n + 1;
     }
     if (DEC_STEPS && tid == 0 && P.steps_left) *P.steps_left -= 1;
+}
+
+// Buffers one stage reads and writes (chosen by the stage's parity).
+struct RingStageIO {
+    const int64_t *lam_in;
+    const i128 *ingrp_in, *grpofs_in;
+    int64_t *lam_out;
+    i128 *ingrp_out, *grpofs_out;
+    const double *x_in; // local stage-input variables of this stage (HH gates)
+    double *x_out;      // local stage-input variables of the next stage
+};
+
+// Stage 0 (prologue) writes buffer 0; stage s reads buffer (s+1)&1 and writes
+// s&1, so stage 4 leaves f(y_{n+1}) in buffer 0 for the next step.
+template <int M, int STAGE>
+__host__ __device__ __forceinline__ RingStageIO stage_io(const RingPlan &p)
+{
+    constexpr int D = Model<M>::D, NX = Model<M>::NX;
+    constexpr int in = (STAGE + 1) & 1, out = STAGE == 0 ? 0 : (STAGE & 1);
+    RingStageIO a;
+    a.lam_in = STAGE ? p.lam[in] : nullptr;
+    a.ingrp_in = STAGE ? p.ingrp[in] : nullptr;
+    a.grpofs_in = STAGE ? p.grpofs[in] : nullptr;
+    a.lam_out = p.lam[out];
+    a.ingrp_out = p.ingrp[out];
+    a.grpofs_out = p.grpofs[out];
+    a.x_in = nullptr;
+    a.x_out = nullptr;
+    if (NX > 0) {
+        a.x_in = STAGE == 1 ? p.y + (int64_t)(D - NX) * p.N : STAGE == 3 ? p.xg[1] : STAGE ? p.xg[0] : nullptr;
+        a.x_out = STAGE == 1 || STAGE == 3 ? p.xg[0] : STAGE == 2 ? p.xg[1] : nullptr;
+    }
+    return a;
+}
+
+// RK4 stage s of node-parallel networks whose coupling is a sum over exact
+// prefixes of the coupled quantity in node order (rings and general link
+// matrices): one 256-node sub-tile `sub` per CTA, one node per thread.  gather
+// gives node i's own fixed-point coupled quantity and its window sums W, plus
+// its link count and coupling scale for the model (see models.cuh).
+template <int M, int STAGE, class Gather>
+__device__ __forceinline__ void stage_body(const RingPlan &P, const RingStageIO &a, double dt, int64_t sub,
+                                           const Gather &gather)
+{
+    using Mo = Model<M>;
+    constexpr int D = Mo::D, NQ = Mo::NQ, NX = Mo::NX;
+    constexpr int XOFF = D - NX; // first local (non-coupled) state variable
+    const int tid = threadIdx.x;
+    const int64_t N = P.N;
+    const int64_t i = sub * kSubTile + tid;
+
+    int64_t qv[NQ];
+    bool ok = true;
+#pragma unroll
+    for (int c = 0; c < NQ; ++c) qv[c] = 0;
+    if (i < N) {
+        double xn[D];
+        if (STAGE == 0) {
+#pragma unroll
+            for (int v = 0; v < D; ++v) xn[v] = P.y[v * N + i];
+        } else {
+            int64_t qo[NQ];
+            double fo[NQ];
+            i128 W[NQ];
+            int64_t wsize;
+            double cs;
+            gather(tid, i, qo, fo, W, wsize, cs);
+            double X[NX > 0 ? NX : 1];
+#pragma unroll
+            for (int g = 0; g < NX; ++g) X[g] = a.x_in[g * N + i];
+            const double Iext = (M == 2 && P.node_param) ? P.node_param[i] : 0.0;
+            double k[D];
+            Mo::rhs(P.mp, P.F, fo, qo, W, X, Iext, k, wsize, cs);
+#pragma unroll
+            for (int v = 0; v < D; ++v) {
+                const double yv = P.y[v * N + i];
+                if (STAGE == 1) {
+                    P.acc[v * N + i] = k[v];
+                    xn[v] = yv + (0.5 * dt) * k[v];
+                } else if (STAGE == 2) {
+                    P.acc[v * N + i] = P.acc[v * N + i] + 2.0 * k[v];
+                    xn[v] = yv + (0.5 * dt) * k[v];
+                } else if (STAGE == 3) {
+                    P.acc[v * N + i] = P.acc[v * N + i] + 2.0 * k[v];
+                    xn[v] = yv + dt * k[v];
+                } else {
+                    const double yn = yv + (dt / 6.0) * (P.acc[v * N + i] + k[v]);
+                    P.y[v * N + i] = yn;
+                    xn[v] = yn;
+                }
+            }
+            if (NX > 0 && STAGE >= 1 && STAGE <= 3) {
+#pragma unroll
+                for (int g = 0; g < NX; ++g) a.x_out[g * N + i] = xn[XOFF + g];
+            }
+        }
+        // a2: coupled quantity of the next stage input on the fixed-point grid
+        double f[NQ];
+        Mo::coupled(P.mp, xn, f);
+#pragma unroll
+        for (int c = 0; c < NQ; ++c) qv[c] = to_fixed(f[c], P.F, P.lim, ok);
+    }
+    if (!ok) raise_error(P.err, ERR_RANGE);
+    ring_prefix_tail<NQ, (M == 0 || M == 3) && (STAGE == 0 || STAGE == 4), STAGE == 4>(P, a.lam_out, a.ingrp_out,
+                                                                                     a.grpofs_out, sub, i, qv);
 }
 
 } // namespace simk

@@ -3,9 +3,12 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
+#include <iterator>
 #include <map>
 #include <mutex>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "internal.h"
@@ -141,6 +144,7 @@ Layout layout_of(int model, int topo, int64_t N, int64_t R)
 const char *validate(int model, int topo, int64_t N, int64_t R, const double *params, int n_params)
 {
     if (model_dim(model) == 0) return "unknown model";
+    if (topo == SIM_GRAPH) return "link-matrix networks are created with sim_create_graph";
     if (topo != SIM_RING && !is_lattice(topo)) return "unknown topology";
     if (is_lattice(topo) && model != SIM_KS && model != SIM_KSI)
         return "the lattices support the Kuramoto models (with or without inertia) only";
@@ -184,9 +188,16 @@ struct sim_handle {
     std::map<std::pair<double, int>, cudaGraphExec_t> graphs;
     void *dp_block = nullptr;             // Dormand-Prince buffers (allocated on first use)
     DpPlan dp{};
+    void *graph_block = nullptr;          // compressed link matrix (general topology)
+    GraphPlan graph{};
+    int64_t graph_entries = 0;            // difference-table entries
+    size_t graph_bytes = 0;               // device bytes of the compressed matrix
 };
 
 namespace {
+
+// rings and general link matrices share the node-order buffers and prologue
+bool ring_like(sim_t h) { return h->topo == SIM_RING || h->topo == SIM_GRAPH; }
 
 int check_device_error(sim_t h)
 {
@@ -208,7 +219,9 @@ cudaError_t launch_steps(sim_t h, int64_t n, double dt, cudaStream_t s)
 {
     if (use_cluster(h)) return n > 0 ? ring_cluster_steps(h->ring, dt, n, s) : cudaSuccess;
     for (int64_t t = 0; t < n; ++t) {
-        const cudaError_t e = h->topo == SIM_RING ? ring_step(h->ring, dt, s) : lattice_step(h->lat, dt, s);
+        const cudaError_t e = h->topo == SIM_RING    ? ring_step(h->ring, dt, s)
+                              : h->topo == SIM_GRAPH ? graph_step(h->graph, dt, s)
+                                                     : lattice_step(h->lat, dt, s);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -247,7 +260,8 @@ int prologue(sim_t h)
 {
     cudaError_t e = cudaMemsetAsync(h->obs_ctr, 0, sizeof(unsigned long long), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->err, 0, sizeof(unsigned), h->stream);
-    if (e == cudaSuccess) e = h->topo == SIM_RING ? ring_prologue(h->ring, h->stream) : lattice_prologue(h->lat, h->stream);
+    if (e == cudaSuccess)
+        e = ring_like(h) ? ring_prologue(h->ring, h->stream) : lattice_prologue(h->lat, h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "prologue");
     h->steps_done = 0;
     h->obs_read = 0;
@@ -271,6 +285,34 @@ static const double *host_tables()
     static std::once_flag once;
     std::call_once(once, [] { fill_math_tables(tab, tab + 2 * kSinTab); });
     return tab;
+}
+
+// Derived model constants for K links per node (FP64 on the host).
+static void model_constants(int model, const double *params, double K, ModelParams &mp)
+{
+    if (model == SIM_KS) {
+        mp.c[0] = params[0];
+        mp.c[1] = params[1] / K;
+        mp.c[2] = std::sin(params[2]);
+        mp.c[3] = std::cos(params[2]);
+    } else if (model == SIM_KSI) {
+        mp.c[0] = params[2] / (params[0] * K); // mu / (m K)
+        mp.c[1] = params[1] / params[0];       // eps / m
+        mp.c[2] = std::sin(params[3]);
+        mp.c[3] = std::cos(params[3]);
+    } else if (model == SIM_FHN) {
+        const double ph = params[3], inv_eps = 1.0 / params[0], sK = params[2] / K;
+        mp.c[0] = inv_eps;
+        mp.c[1] = params[1];
+        mp.c[2] = sK * std::cos(ph) * inv_eps;  // (sigma/K) B00 / eps
+        mp.c[3] = sK * std::sin(ph) * inv_eps;  // (sigma/K) B01 / eps
+        mp.c[4] = -sK * std::sin(ph);           // (sigma/K) B10
+        mp.c[5] = sK * std::cos(ph);            // (sigma/K) B11
+    } else {
+        mp.c[0] = 1.0 / params[0];
+        for (int i = 1; i < 7; ++i) mp.c[i] = params[i];
+        mp.c[7] = params[7] / K;
+    }
 }
 
 static int create_impl(sim_t *out, int model, int topology, int64_t N, int64_t radius, const double *params,
@@ -338,30 +380,7 @@ static int create_impl(sim_t *out, int model, int topology, int64_t N, int64_t r
     const bool self = (flags & SIM_FLAG_INCLUDE_SELF) != 0;
     mp.include_self = self ? 1 : 0;
     mp.wsize = window_of(topology, radius);
-    const double K = (double)(self ? mp.wsize : mp.wsize - 1);
-    if (model == SIM_KS) {
-        mp.c[0] = params[0];
-        mp.c[1] = params[1] / K;
-        mp.c[2] = std::sin(params[2]);
-        mp.c[3] = std::cos(params[2]);
-    } else if (model == SIM_KSI) {
-        mp.c[0] = params[2] / (params[0] * K); // mu / (m K)
-        mp.c[1] = params[1] / params[0];       // eps / m
-        mp.c[2] = std::sin(params[3]);
-        mp.c[3] = std::cos(params[3]);
-    } else if (model == SIM_FHN) {
-        const double ph = params[3], inv_eps = 1.0 / params[0], sK = params[2] / K;
-        mp.c[0] = inv_eps;
-        mp.c[1] = params[1];
-        mp.c[2] = sK * std::cos(ph) * inv_eps;  // (sigma/K) B00 / eps
-        mp.c[3] = sK * std::sin(ph) * inv_eps;  // (sigma/K) B01 / eps
-        mp.c[4] = -sK * std::sin(ph);           // (sigma/K) B10
-        mp.c[5] = sK * std::cos(ph);            // (sigma/K) B11
-    } else {
-        mp.c[0] = 1.0 / params[0];
-        for (int i = 1; i < 7; ++i) mp.c[i] = params[i];
-        mp.c[7] = params[7] / K;
-    }
+    model_constants(model, params, (double)(self ? mp.wsize : mp.wsize - 1), mp);
 
     if (topology == SIM_RING) {
         RingPlan &p = h->ring;
@@ -450,6 +469,74 @@ static int create_impl(sim_t *out, int model, int topology, int64_t N, int64_t r
     return SIM_OK;
 }
 
+// Algorithm 2 (Section III.C) on the host: the common vector V = row 0 as runs
+// of consecutive offsets, and for every row i the entry of the difference table
+// holding XOR(ROL(row_i, i), V) (ROL by i maps link j to (j - i) mod N; XOR is the
+// symmetric difference of the sorted offset sets), found through a hash of the
+// entry's offsets.  Each entry keeps its offsets with the sign they carry in the
+// coupling sum and the link count of its rows.
+struct CompressedLinks {
+    std::vector<int2> runs;
+    std::vector<int> ent;
+    std::vector<int64_t> dptr{0};
+    std::vector<int2> dpos;
+    std::vector<int64_t> ek;
+    std::vector<double> ecs;
+};
+
+static const char *compress_links(int64_t N, const int64_t *row_ptr, const int64_t *col, CompressedLinks &T)
+{
+    if (row_ptr[0] != 0) return "row_ptr[0] must be 0";
+    for (int64_t i = 0; i < N; ++i)
+        if (row_ptr[i + 1] < row_ptr[i]) return "row_ptr must not decrease";
+    if (row_ptr[N] > 0 && !col) return "col is NULL";
+    std::vector<int64_t> V(col + row_ptr[0], col + row_ptr[1]);
+    for (int64_t j : V)
+        if (j < 0 || j >= N) return "a link index is outside [0, N)";
+    std::sort(V.begin(), V.end());
+    if (std::adjacent_find(V.begin(), V.end()) != V.end()) return "a row lists the same link twice";
+    for (size_t t = 0; t < V.size();) { // runs of consecutive offsets
+        size_t u = t + 1;
+        while (u < V.size() && V[u] == V[u - 1] + 1) ++u;
+        T.runs.push_back(make_int2((int)V[t], (int)(u - t)));
+        t = u;
+    }
+    T.ent.resize(N);
+    std::unordered_map<std::string, int> index;
+    std::vector<int64_t> sh, d;
+    for (int64_t i = 0; i < N; ++i) {
+        sh.clear();
+        for (int64_t t = row_ptr[i]; t < row_ptr[i + 1]; ++t) {
+            const int64_t j = col[t];
+            if (j < 0 || j >= N) return "a link index is outside [0, N)";
+            sh.push_back(j >= i ? j - i : j - i + N);
+        }
+        std::sort(sh.begin(), sh.end());
+        if (std::adjacent_find(sh.begin(), sh.end()) != sh.end()) return "a row lists the same link twice";
+        d.clear();
+        std::set_symmetric_difference(sh.begin(), sh.end(), V.begin(), V.end(), std::back_inserter(d));
+        std::string key(reinterpret_cast<const char *>(d.data()), d.size() * sizeof(int64_t));
+        auto it = index.find(key);
+        if (it != index.end()) {
+            T.ent[i] = it->second;
+            continue;
+        }
+        const int e = (int)index.size();
+        index.emplace(std::move(key), e);
+        T.ent[i] = e;
+        int64_t K = (int64_t)V.size();
+        for (int64_t p : d) {
+            const int sign = std::binary_search(V.begin(), V.end(), p) ? -1 : 1;
+            T.dpos.push_back(make_int2((int)p, sign));
+            K += sign;
+        }
+        T.dptr.push_back((int64_t)T.dpos.size());
+        T.ek.push_back(K);
+        T.ecs.push_back(K > 0 ? 1.0 / (double)K : 0.0);
+    }
+    return nullptr;
+}
+
 int sim_create(sim_t *out, int model, int topology, int64_t N, int64_t radius, const double *params,
                int n_params, unsigned flags, void *stream)
 {
@@ -464,6 +551,78 @@ int sim_create_in(sim_t *out, int model, int topology, int64_t N, int64_t radius
                        stream);
 }
 
+int sim_create_graph(sim_t *out, int model, int64_t N, const int64_t *row_ptr, const int64_t *col,
+                     const double *params, int n_params, void *stream)
+{
+    if (!out) return fail(SIM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (N < 3 || N > INT32_MAX) return fail(SIM_EINVAL, "a link matrix needs 3 <= N < 2^31 nodes");
+    if (!row_ptr) return fail(SIM_EINVAL, "row_ptr is NULL");
+    CompressedLinks T;
+    if (const char *why = compress_links(N, row_ptr, col, T)) return fail(SIM_EINVAL, why);
+    // The node-order buffers of a ring of N nodes (radius 1 only sizes its window
+    // bases, which a link matrix does not use), streaming kernels.
+    sim_t h = nullptr;
+    int st = create_impl(&h, model, SIM_RING, N, 1, params, n_params, SIM_FLAG_STREAMING, nullptr, 0, stream);
+    if (st != SIM_OK) return st;
+    h->topo = SIM_GRAPH;
+    h->R = 0;
+    // constants for K = 1: every node's coupling is scaled by 1 / K_i on the device
+    model_constants(model, params, 1.0, h->ring.mp);
+    h->ring.mp.include_self = 1; // the link sums are exact; a self link is just one of the links
+    h->ring.mp.wsize = 1;
+    // device tables
+    const size_t o_runs = 0, o_ent = align_up(sizeof(int2) * (T.runs.size() + 1));
+    const size_t o_dptr = o_ent + align_up(sizeof(int) * T.ent.size());
+    const size_t o_dpos = o_dptr + align_up(sizeof(int64_t) * T.dptr.size());
+    const size_t o_ek = o_dpos + align_up(sizeof(int2) * (T.dpos.size() + 1));
+    const size_t o_ecs = o_ek + align_up(sizeof(int64_t) * T.ek.size());
+    const size_t total = o_ecs + align_up(sizeof(double) * T.ecs.size());
+    cudaError_t e = cudaMalloc(&h->graph_block, total);
+    if (e != cudaSuccess) {
+        h->graph_block = nullptr;
+        sim_destroy(h);
+        return fail(SIM_ENOMEM, "device allocation of the compressed link matrix failed");
+    }
+    char *b = static_cast<char *>(h->graph_block);
+    auto up = [&](size_t off, const void *src, size_t bytes) {
+        if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(b + off, src, bytes, cudaMemcpyHostToDevice, h->stream);
+    };
+    up(o_runs, T.runs.data(), sizeof(int2) * T.runs.size());
+    up(o_ent, T.ent.data(), sizeof(int) * T.ent.size());
+    up(o_dptr, T.dptr.data(), sizeof(int64_t) * T.dptr.size());
+    up(o_dpos, T.dpos.data(), sizeof(int2) * T.dpos.size());
+    up(o_ek, T.ek.data(), sizeof(int64_t) * T.ek.size());
+    up(o_ecs, T.ecs.data(), sizeof(double) * T.ecs.size());
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream); // the host tables go out of scope
+    if (e != cudaSuccess) {
+        sim_destroy(h);
+        return cuda_fail(e, "link matrix upload");
+    }
+    GraphPlan &g = h->graph;
+    g.r = h->ring;
+    g.runs = reinterpret_cast<const int2 *>(b + o_runs);
+    g.nruns = (int)T.runs.size();
+    g.ent = reinterpret_cast<const int *>(b + o_ent);
+    g.dptr = reinterpret_cast<const int64_t *>(b + o_dptr);
+    g.dpos = reinterpret_cast<const int2 *>(b + o_dpos);
+    g.ek = reinterpret_cast<const int64_t *>(b + o_ek);
+    g.ecs = reinterpret_cast<const double *>(b + o_ecs);
+    h->graph_entries = (int64_t)T.ek.size();
+    h->graph_bytes = total;
+    *out = h;
+    return SIM_OK;
+}
+
+int sim_graph_info(sim_t h, int64_t *n_entries, int64_t *n_runs, size_t *device_bytes)
+{
+    if (!h || h->topo != SIM_GRAPH) return fail(SIM_EINVAL, "not a link-matrix network");
+    if (n_entries) *n_entries = h->graph_entries;
+    if (n_runs) *n_runs = h->graph.nruns;
+    if (device_bytes) *device_bytes = h->graph_bytes;
+    return SIM_OK;
+}
+
 int64_t sim_nodes(sim_t h) { return h ? h->nodes : 0; }
 int sim_dim(sim_t h) { return h ? h->d : 0; }
 
@@ -471,7 +630,7 @@ static int set_state_impl(sim_t h, const double *src, int64_t n_values, cudaMemc
 {
     if (!h || !src) return fail(SIM_EINVAL, "NULL handle or buffer");
     if (n_values != (int64_t)h->d * h->nodes) return fail(SIM_EINVAL, "n_values must equal dim * nodes");
-    double *y = h->topo == SIM_RING ? h->ring.y : h->lat.y;
+    double *y = ring_like(h) ? h->ring.y : h->lat.y;
     cudaError_t e = cudaMemcpyAsync(y, src, sizeof(double) * n_values, kind, h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "state copy");
     return prologue(h);
@@ -521,7 +680,7 @@ static int get_state_impl(sim_t h, double *dst, int64_t n_values, cudaMemcpyKind
 {
     if (!h || !dst) return fail(SIM_EINVAL, "NULL handle or buffer");
     if (n_values != (int64_t)h->d * h->nodes) return fail(SIM_EINVAL, "n_values must equal dim * nodes");
-    const double *y = h->topo == SIM_RING ? h->ring.y : h->lat.y;
+    const double *y = ring_like(h) ? h->ring.y : h->lat.y;
     const cudaError_t e = cudaMemcpyAsync(dst, y, sizeof(double) * n_values, kind, h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "state copy");
     return SIM_OK;
@@ -543,9 +702,11 @@ int sim_rhs(sim_t h, double *host_k, int64_t n_values)
 {
     if (!h || !host_k) return fail(SIM_EINVAL, "NULL handle or buffer");
     if (n_values != (int64_t)h->d * h->nodes) return fail(SIM_EINVAL, "n_values must equal dim * nodes");
-    cudaError_t e = h->topo == SIM_RING ? ring_rhs(h->ring, h->stream) : lattice_rhs(h->lat, h->stream);
+    cudaError_t e = h->topo == SIM_RING    ? ring_rhs(h->ring, h->stream)
+                    : h->topo == SIM_GRAPH ? graph_rhs(h->graph, h->stream)
+                                           : lattice_rhs(h->lat, h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "rhs launch");
-    const double *acc = h->topo == SIM_RING ? h->ring.acc : h->lat.acc;
+    const double *acc = ring_like(h) ? h->ring.acc : h->lat.acc;
     e = cudaMemcpyAsync(host_k, acc, sizeof(double) * n_values, cudaMemcpyDeviceToHost, h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "rhs copy");
     return check_device_error(h);
@@ -598,7 +759,7 @@ struct sim_batch_handle {
     std::vector<sim_t> members;
     std::vector<int> ring_slot;      // member -> index of its plan in the group tables (or -1)
     std::vector<RingBatchGroup> groups;
-    std::vector<sim_t> lattices;
+    std::vector<sim_t> lattices;     // members stepped by their own kernels (lattices, link matrices)
     void *block = nullptr;           // device tables
     long long *budgets = nullptr;    // device: steps left per ring member (budgeted mode)
     std::vector<long long> host_budget; // host shadow, -1 = unlimited
@@ -647,7 +808,8 @@ cudaError_t branch_steps(sim_batch_t b, int k, int64_t n, double dt, cudaStream_
             if (e != cudaSuccess) return e;
         } else {
             for (size_t c = (size_t)(k - ng); c < b->lattices.size(); c += kLatticeBranches) {
-                const cudaError_t e = lattice_step(b->lattices[c]->lat, dt, s);
+                const sim_t m = b->lattices[c];
+                const cudaError_t e = m->topo == SIM_GRAPH ? graph_step(m->graph, dt, s) : lattice_step(m->lat, dt, s);
                 if (e != cudaSuccess) return e;
             }
         }
@@ -904,6 +1066,7 @@ void sim_destroy(sim_t h)
     if (h->block) cudaStreamSynchronize(h->stream);
     for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
     if (h->dp_block) cudaFree(h->dp_block);
+    if (h->graph_block) cudaFree(h->graph_block);
     if (h->block && h->owns_block) cudaFree(h->block);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     delete h;

@@ -20,6 +20,9 @@ Section IV):
   * batched sweep: N log-uniform in [100, 50000], R = floor(r N), r ~ U[0.05, 0.45],
     alpha ~ U[1.3, 1.57]
   * served trace: Poisson arrivals and a fixed model mix (see ``served_trace``)
+  * link matrices by rows: a small-world ring (each of the 2R ring links rewired
+    to a uniform node with probability p) and random directed graphs (each node
+    draws its links uniformly)
 """
 from __future__ import annotations
 
@@ -35,7 +38,7 @@ _MASK = (1 << 64) - 1
 _CHUNK = 1 << 22
 
 # Variable ids of the streams (part of the key).
-VAR_PHASE, VAR_U, VAR_V, VAR_M, VAR_H, VAR_N, VAR_IEXT, VAR_INST, VAR_PSI = range(9)
+VAR_PHASE, VAR_U, VAR_V, VAR_M, VAR_H, VAR_N, VAR_IEXT, VAR_INST, VAR_PSI, VAR_LINK, VAR_LINK2 = range(11)
 
 
 def _mix_int(z: int) -> int:
@@ -224,3 +227,35 @@ def served_trace(n_jobs: int = 2000, rate: float = 200.0, seed: int = 2415,
             job = Job(i, t, 0, 1, N1, P, ks_params(alpha=1.52), steps, seed)
         jobs.append(job)
     return jobs
+
+
+# --------------------------------------------------------------------------
+def _rows_from_pairs(N: int, src: np.ndarray, dst: np.ndarray):
+    """CSR (row_ptr, col) of the links dst -> src (row src lists dst), without
+    self links or duplicates, columns sorted within each row."""
+    keep = src != dst
+    key = np.unique(src[keep].astype(np.int64) * N + dst[keep].astype(np.int64))
+    rows, cols = key // N, key % N
+    row_ptr = np.zeros(N + 1, dtype=np.int64)
+    np.add.at(row_ptr, rows + 1, 1)
+    return np.cumsum(row_ptr), cols.astype(np.int64)
+
+
+def small_world_links(N: int, R: int, p: float, seed: int):
+    """Ring of radius R whose links are each rewired to a uniform node with
+    probability p (Watts-Strogatz style); returns (row_ptr, col)."""
+    offs = np.array([d for d in range(-R, R + 1) if d], dtype=np.int64)
+    src = np.repeat(np.arange(N, dtype=np.int64), offs.size)
+    dst = (src + np.tile(offs, N)) % N
+    u = uniform(seed, 0, VAR_LINK, src.size)
+    t = np.minimum((uniform(seed, 0, VAR_LINK2, src.size) * N).astype(np.int64), N - 1)
+    dst = np.where(u < p, t, dst)
+    return _rows_from_pairs(N, src, dst)
+
+
+def random_links(N: int, k: int, seed: int):
+    """Random directed graph: every node draws k links uniformly (duplicates and
+    self links dropped); returns (row_ptr, col)."""
+    src = np.repeat(np.arange(N, dtype=np.int64), k)
+    dst = np.minimum((uniform(seed, 0, VAR_LINK, src.size) * N).astype(np.int64), N - 1)
+    return _rows_from_pairs(N, src, dst)

@@ -12,7 +12,7 @@ import numpy as np
 from ._lib import DP5Opts, DP5Stats, SIM_ESMALL, SIM_ESTEPS, check, lib
 
 KS, FHN, HH, KSI = 0, 1, 2, 3
-RING, CUBE3D, BALL3D, DISK2D = 0, 1, 2, 3
+RING, CUBE3D, BALL3D, DISK2D, GRAPH = 0, 1, 2, 3, 4
 FLAG_INCLUDE_SELF = 1
 FLAG_STREAMING = 2
 DIM = {KS: 1, FHN: 2, HH: 4, KSI: 2}
@@ -63,6 +63,29 @@ class Network:
         self.model, self.topology, self.N, self.radius = model, topology, int(N), int(radius)
         self.nodes = int(lib().sim_nodes(h))
         self.dim = int(lib().sim_dim(h))
+
+    @classmethod
+    def from_links(cls, model: int, N: int, row_ptr, col, params, stream=None):
+        """A network on a general link matrix given by rows (``sim_create_graph``):
+        the links of node i are col[row_ptr[i]:row_ptr[i+1]]."""
+        rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+        cl = np.ascontiguousarray(col, dtype=np.int64)
+        p = np.ascontiguousarray(params, dtype=np.float64)
+        h = ctypes.c_void_p()
+        check(lib().sim_create_graph(ctypes.byref(h), model, int(N), rp.ctypes.data, cl.ctypes.data if cl.size else None,
+                                     p.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), p.size, _stream_ptr(stream)))
+        self = cls.__new__(cls)
+        self._h = h
+        self.model, self.topology, self.N, self.radius = model, GRAPH, int(N), 0
+        self.nodes = int(lib().sim_nodes(h))
+        self.dim = int(lib().sim_dim(h))
+        return self
+
+    def graph_info(self):
+        """(difference-table entries, runs of the common vector, device bytes)."""
+        e, r, b = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_size_t(0)
+        check(lib().sim_graph_info(self._handle(), ctypes.byref(e), ctypes.byref(r), ctypes.byref(b)))
+        return int(e.value), int(r.value), int(b.value)
 
     @property
     def n_values(self):
