@@ -76,6 +76,8 @@ def parse():
     ap.add_argument("--no-served", action="store_true", help="skip the served-mix comparison")
     ap.add_argument("--no-extra", action="store_true", help="skip the small-ring and lattice lines")
     ap.add_argument("--batched-only", action="store_true")
+    ap.add_argument("--graph-ball", action="store_true",
+                    help="also time the 100^3 ball lattice (P = 6) as a compressed link matrix (~25 s set-up)")
     return ap.parse_args()
 
 
@@ -353,6 +355,66 @@ def bench_dp5_sweep(args, n_inst=4096, N=1000, t_end=100.0, tol=1e-8, plain_inst
             "gpu_launches": 7 * (att // n_inst + 1)}
 
 
+def ball_links(N1, P):
+    """Rows of the periodic ball lattice (index k N1^2 + j N1 + i, self excluded)."""
+    offs = np.array([(dx, dy, dz) for dz in range(-P, P + 1) for dy in range(-P, P + 1) for dx in range(-P, P + 1)
+                     if dx * dx + dy * dy + dz * dz <= P * P and (dx, dy, dz) != (0, 0, 0)], dtype=np.int64)
+    n, K = N1 ** 3, len(offs)
+    col = np.empty(n * K, dtype=np.int64)
+    for s0 in range(0, n, 50000):
+        idx = np.arange(s0, min(n, s0 + 50000), dtype=np.int64)
+        i, j, k = idx % N1, (idx // N1) % N1, idx // (N1 * N1)
+        nb = (((k[:, None] + offs[None, :, 2]) % N1) * N1 * N1 + ((j[:, None] + offs[None, :, 1]) % N1) * N1
+              + (i[:, None] + offs[None, :, 0]) % N1)
+        col[s0 * K:(s0 + idx.size) * K] = nb.ravel()
+    return np.arange(0, n * K + 1, K, dtype=np.int64), col
+
+
+def bench_graph(args, stream, flush, ball=False, steps=100):
+    """General link matrices through Algorithm 2: a small-world ring of 10^6
+    Kuramoto nodes (10 links each, 1% rewired) and, with --graph-ball, the
+    paper's compressed-matrix example, the 100^3 ball lattice with P = 6 written
+    as a link matrix (Kuramoto with inertia), beside its lattice kernel."""
+    import torch
+    from paper_2410_19075_gb300 import Network
+
+    def timed(net, model, n):
+        net.set_state(torch.from_numpy(I.initial_state(model, 2417, 0, n)).cuda())
+        net.step(3, args.dt)
+        net.sync()
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        net.step(steps, args.dt)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / steps
+
+    out = []
+    cases = [("small-world ring, 10 links per node, 1% rewired", 0, 10 ** 6,
+              lambda: I.small_world_links(10 ** 6, 5, 0.01, 2417))]
+    if ball:
+        cases.append(("periodic 100^3 ball lattice, P = 6 (924 links per node) as a link matrix", 3, 10 ** 6,
+                      lambda: ball_links(100, 6)))
+    for name, model, n, make in cases:
+        rp, col = make()
+        t0 = time.perf_counter()
+        net = Network.from_links(model, n, rp, col, I.ksi_params() if model == 3 else I.ks_params(),
+                                 stream=stream)
+        compress_s = time.perf_counter() - t0
+        links = int(rp[-1])
+        del rp, col
+        entries, runs, nbytes = net.graph_info()
+        ms = timed(net, model, n)
+        net.close()
+        out.append({"workload": f"{MODEL_NAMES[model]} on a {name}, N={n}", "links": links,
+                    "compressed": {"entries": entries, "runs_of_common_vector": runs, "device_bytes": nbytes,
+                                   "host_compress_s": compress_s},
+                    "ms_per_step": ms, "value": n * steps / (ms * steps * 1e-3), "unit": "node-steps/s",
+                    "links_per_s": links / (ms * 1e-3)})
+    return out
+
+
 # ----------------------------------------------------------------------------- c1 and c3
 def bench_small_ring(args, stream, flush, steps=200, reps=5):
     """Kuramoto ring N=1000, R=350, alpha=1.46: latency of one RK4 step (the whole
@@ -612,6 +674,7 @@ def run_native(args):
         line["small_ring"] = bench_small_ring(args, stream, flush)
         line["cube"] = bench_cube(args, stream, flush)
         line["ball3d_inertia"] = bench_ball(args, stream, flush)
+        line["graph"] = bench_graph(args, stream, flush, ball=args.graph_ball)
     if not args.no_batched:
         line["batched"] = bench_batched(args, flush, stream)
         line["batched_dp5"] = bench_dp5_sweep(args)

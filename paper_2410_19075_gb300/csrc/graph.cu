@@ -1,7 +1,8 @@
 // General link matrices (Section III.C) stepped with RK4 through the compressed
 // form of Algorithm 2.
 //
-// COMPRESS (on the host, sim_api.cu) keeps the common vector V = row 0 and, for
+// COMPRESS (on the host, sim_api.cu) keeps a common vector V (the most frequent
+// shifted row; the paper takes row 0) and, for
 // every row i, a reference C_i to the difference entry D = XOR(ROL(row_i, i), V);
 // EXTRACT gives row i = ROR(XOR(V, D_{C_i}), i).  So the coupling sum of node i is
 //   W(i) = sum_{p in V} Q(x_{i+p}) + sum_{p in D_{C_i}} s_p Q(x_{i+p})   (indices mod N)
@@ -12,9 +13,11 @@
 // the same exact fixed-point prefix the ring stage kernels build (P over the
 // periodic extension).  A node therefore costs O(number of runs + size of its
 // difference entry) reads instead of one per link: a ring is two runs and the
-// empty entry, a periodic lattice a few runs per row of its window plus the
-// wrapped links near the boundary.  The degree of the node (its link count, which
-// normalises the coupling) comes with its entry.
+// empty entry, a periodic lattice one run per row of its window plus the
+// wrapped links near the boundary.  As in the ring kernel, the exact prefix at
+// the pieces the CTA's run ends fall in is computed once per CTA, so a run costs
+// a node one load per end and component.  The degree of the node (its link
+// count, which normalises the coupling) comes with its entry.
 #include "ring_parts.cuh"
 
 namespace simk {
@@ -36,9 +39,61 @@ __device__ __forceinline__ i128 graph_prefix_at(const RingPlan &P, const RingSta
            (i128)__ldg(a.lam_in + c * N + pos - 1);
 }
 
+// Per-CTA bases of the run ends: for run r, end 2r is i + a (the run's first
+// offset) and end 2r+1 is i + a + len; over the CTA's consecutive nodes each end
+// covers at most three pieces (split at sub-tile starts and at N), whose exact
+// prefix at the piece start is computed once, so a node needs one in-sub-tile
+// prefix load per end.  Runs past kGraphSmemRuns use graph_prefix_at.
+constexpr int kGraphSmemRuns = 128;
+template <int NQ> struct GraphBases {
+    i128 base[2 * kGraphSmemRuns][3][NQ];
+    int64_t start[2 * kGraphSmemRuns][3], qn[2 * kGraphSmemRuns][3];
+};
+
+template <int NQ>
+__device__ __forceinline__ void graph_load_bases(const GraphPlan &G, const RingStageIO &a, int64_t sub, int nb,
+                                                 GraphBases<NQ> &B)
+{
+    const RingPlan &P = G.r;
+    const int64_t N = P.N, nsub = P.nsub, ngroups = P.ngroups;
+    const int64_t nvalid = N - sub * kSubTile < kSubTile ? N - sub * kSubTile : kSubTile;
+    for (int e = threadIdx.x; e < 2 * nb; e += blockDim.x) {
+        const int2 run = __ldg(G.runs + (e >> 1));
+        const int64_t p0 = sub * kSubTile + run.x + ((e & 1) ? run.y : 0);
+        const int64_t p1 = p0 + nvalid - 1; // in [0, 2N)
+        int64_t p = p0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            if (p > p1) {
+                B.start[e][k] = INT64_MAX;
+                B.qn[e][k] = 0;
+                continue;
+            }
+            const int64_t qn = p >= N ? N : 0, pp = p - qn;
+            const int64_t st = pp >> kSubLog2;
+            int64_t end = ((st + 1) << kSubLog2) - 1;
+            if (end > N - 1) end = N - 1;
+#pragma unroll
+            for (int c = 0; c < NQ; ++c) {
+                const i128 *grpofs = a.grpofs_in + c * (ngroups + 1);
+                const i128 tot = ldg_i128(grpofs + ngroups);
+                // st == nsub only for pp == N (never: pp < N here)
+                B.base[e][k][c] = ldg_i128(grpofs + (st >> kGroupLog2)) + ldg_i128(a.ingrp_in + c * nsub + st) +
+                                  (qn ? tot : (i128)0);
+            }
+            B.start[e][k] = p;
+            B.qn[e][k] = qn;
+            p = end + qn + 1;
+        }
+    }
+    __syncthreads();
+}
+
 template <int NQ> struct GraphGather {
     const GraphPlan &G;
     const RingStageIO &a;
+    const GraphBases<NQ> &B;
+    int nb; // runs with per-CTA bases
     __device__ __forceinline__ void operator()(int tid, int64_t i, int64_t (&qo)[NQ], double (&fo)[NQ],
                                                i128 (&W)[NQ], int64_t &wsize, double &cs) const
     {
@@ -52,8 +107,23 @@ template <int NQ> struct GraphGather {
             fo[c] = fixed_to_double(qo[c], P.F);
             W[c] = 0;
         }
-        // the common vector: runs of consecutive offsets
-        for (int r = 0; r < G.nruns; ++r) {
+        // the common vector: runs of consecutive offsets, through the CTA's bases
+        for (int r = 0; r < nb; ++r) {
+            const int2 run = __ldg(G.runs + r);
+            const int64_t lo = i + run.x, hi = lo + run.y;
+            const int el = 2 * r, eh = 2 * r + 1;
+            const int kl = (lo >= B.start[el][1]) + (lo >= B.start[el][2]);
+            const int kh = (hi >= B.start[eh][1]) + (hi >= B.start[eh][2]);
+            const int64_t pl = lo - B.qn[el][kl], ph = hi - B.qn[eh][kh];
+#pragma unroll
+            for (int c = 0; c < NQ; ++c) {
+                const int64_t *lam = a.lam_in + c * N;
+                const int64_t ll = (pl & (kSubTile - 1)) ? __ldg(lam + pl - 1) : 0;
+                const int64_t lh = (ph & (kSubTile - 1)) ? __ldg(lam + ph - 1) : 0;
+                W[c] += (B.base[eh][kh][c] - B.base[el][kl][c]) + (i128)(lh - ll);
+            }
+        }
+        for (int r = nb; r < G.nruns; ++r) {
             const int2 run = __ldg(G.runs + r); // (a, len), a + len <= N
             const int64_t lo = i + run.x, hi = lo + run.y;
 #pragma unroll
@@ -86,8 +156,12 @@ template <int M, int STAGE>
 __global__ void __launch_bounds__(kRingThreads, GraphMinBlocks<M>::value)
     graph_stage_kernel(const GraphPlan g, double dt)
 {
+    constexpr int NQ = Model<M>::NQ;
+    __shared__ GraphBases<NQ> s_bases;
     const RingStageIO a = stage_io<M, STAGE>(g.r);
-    stage_body<M, STAGE>(g.r, a, dt, blockIdx.x, GraphGather<Model<M>::NQ>{g, a});
+    const int nb = g.nruns < kGraphSmemRuns ? g.nruns : kGraphSmemRuns;
+    graph_load_bases<NQ>(g, a, blockIdx.x, nb, s_bases);
+    stage_body<M, STAGE>(g.r, a, dt, blockIdx.x, GraphGather<NQ>{g, a, s_bases, nb});
 }
 
 template <int M>

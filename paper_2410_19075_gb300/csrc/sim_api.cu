@@ -469,12 +469,16 @@ static int create_impl(sim_t *out, int model, int topology, int64_t N, int64_t r
     return SIM_OK;
 }
 
-// Algorithm 2 (Section III.C) on the host: the common vector V = row 0 as runs
-// of consecutive offsets, and for every row i the entry of the difference table
-// holding XOR(ROL(row_i, i), V) (ROL by i maps link j to (j - i) mod N; XOR is the
-// symmetric difference of the sorted offset sets), found through a hash of the
-// entry's offsets.  Each entry keeps its offsets with the sign they carry in the
-// coupling sum and the link count of its rows.
+// Algorithm 2 (Section III.C) on the host.  ROL by i maps link j of row i to
+// offset (j - i) mod N; XOR is the symmetric difference of sorted offset sets.
+// Every row i is stored as the entry of the difference table holding
+// XOR(ROL(row_i, i), V), found through a hash of its offsets, and V is kept as
+// runs of consecutive offsets.  The paper takes V = row 0; here V is the most
+// frequent shifted row (row 0 among equals), so that the rows of a periodic
+// lattice, whose node 0 is a corner with wrapped links, map to the empty entry
+// except near the boundary.  EXTRACT is unchanged: row_i = ROR(XOR(V, D), i).
+// Each entry keeps its offsets with the sign they carry in the coupling sum and
+// the link count of its rows.
 struct CompressedLinks {
     std::vector<int2> runs;
     std::vector<int> ent;
@@ -484,38 +488,62 @@ struct CompressedLinks {
     std::vector<double> ecs;
 };
 
+static std::string offsets_key(const std::vector<int64_t> &v)
+{
+    return std::string(reinterpret_cast<const char *>(v.data()), v.size() * sizeof(int64_t));
+}
+
+// Shifted row i (sorted); nullptr or the reason it is invalid.
+static const char *shifted_row(int64_t N, const int64_t *row_ptr, const int64_t *col, int64_t i,
+                               std::vector<int64_t> &sh)
+{
+    sh.clear();
+    for (int64_t t = row_ptr[i]; t < row_ptr[i + 1]; ++t) {
+        const int64_t j = col[t];
+        if (j < 0 || j >= N) return "a link index is outside [0, N)";
+        sh.push_back(j >= i ? j - i : j - i + N);
+    }
+    std::sort(sh.begin(), sh.end());
+    if (std::adjacent_find(sh.begin(), sh.end()) != sh.end()) return "a row lists the same link twice";
+    return nullptr;
+}
+
 static const char *compress_links(int64_t N, const int64_t *row_ptr, const int64_t *col, CompressedLinks &T)
 {
     if (row_ptr[0] != 0) return "row_ptr[0] must be 0";
     for (int64_t i = 0; i < N; ++i)
         if (row_ptr[i + 1] < row_ptr[i]) return "row_ptr must not decrease";
     if (row_ptr[N] > 0 && !col) return "col is NULL";
-    std::vector<int64_t> V(col + row_ptr[0], col + row_ptr[1]);
-    for (int64_t j : V)
-        if (j < 0 || j >= N) return "a link index is outside [0, N)";
-    std::sort(V.begin(), V.end());
-    if (std::adjacent_find(V.begin(), V.end()) != V.end()) return "a row lists the same link twice";
+    // pass 1: the most frequent shifted row becomes V
+    std::vector<int64_t> sh, d, V;
+    {
+        std::unordered_map<std::string, std::pair<int64_t, int64_t>> count; // key -> (count, first row)
+        int64_t best = -1, best_row = 0;
+        for (int64_t i = 0; i < N; ++i) {
+            if (const char *why = shifted_row(N, row_ptr, col, i, sh)) return why;
+            auto &c = count[offsets_key(sh)];
+            if (c.first++ == 0) c.second = i;
+            if (c.first > best || (c.first == best && c.second < best_row)) {
+                best = c.first;
+                best_row = c.second;
+            }
+        }
+        shifted_row(N, row_ptr, col, best_row, V);
+    }
     for (size_t t = 0; t < V.size();) { // runs of consecutive offsets
         size_t u = t + 1;
         while (u < V.size() && V[u] == V[u - 1] + 1) ++u;
         T.runs.push_back(make_int2((int)V[t], (int)(u - t)));
         t = u;
     }
+    // pass 2: the difference table
     T.ent.resize(N);
     std::unordered_map<std::string, int> index;
-    std::vector<int64_t> sh, d;
     for (int64_t i = 0; i < N; ++i) {
-        sh.clear();
-        for (int64_t t = row_ptr[i]; t < row_ptr[i + 1]; ++t) {
-            const int64_t j = col[t];
-            if (j < 0 || j >= N) return "a link index is outside [0, N)";
-            sh.push_back(j >= i ? j - i : j - i + N);
-        }
-        std::sort(sh.begin(), sh.end());
-        if (std::adjacent_find(sh.begin(), sh.end()) != sh.end()) return "a row lists the same link twice";
+        shifted_row(N, row_ptr, col, i, sh);
         d.clear();
         std::set_symmetric_difference(sh.begin(), sh.end(), V.begin(), V.end(), std::back_inserter(d));
-        std::string key(reinterpret_cast<const char *>(d.data()), d.size() * sizeof(int64_t));
+        std::string key = offsets_key(d);
         auto it = index.find(key);
         if (it != index.end()) {
             T.ent[i] = it->second;
