@@ -154,14 +154,14 @@ template <> struct GraphMinBlocks<2> { static constexpr int value = 2; };
 
 template <int M, int STAGE>
 __global__ void __launch_bounds__(kRingThreads, GraphMinBlocks<M>::value)
-    graph_stage_kernel(const GraphPlan g, double dt)
+    graph_stage_kernel(const GraphPlan g, const StepSize h)
 {
     constexpr int NQ = Model<M>::NQ;
     __shared__ GraphBases<NQ> s_bases;
     const RingStageIO a = stage_io<M, STAGE>(g.r);
     const int nb = g.nruns < kGraphSmemRuns ? g.nruns : kGraphSmemRuns;
     graph_load_bases<NQ>(g, a, blockIdx.x, nb, s_bases);
-    stage_body<M, STAGE>(g.r, a, dt, blockIdx.x, GraphGather<NQ>{g, a, s_bases, nb});
+    stage_body<M, STAGE>(g.r, a, h, blockIdx.x, GraphGather<NQ>{g, a, s_bases, nb});
 }
 
 template <int M>
@@ -169,10 +169,10 @@ static cudaError_t launch_stage(int stage, const GraphPlan &g, double dt, cudaSt
 {
     const dim3 grid((unsigned)g.r.nsub), block(kRingThreads);
     switch (stage) {
-    case 1: graph_stage_kernel<M, 1><<<grid, block, 0, s>>>(g, dt); break;
-    case 2: graph_stage_kernel<M, 2><<<grid, block, 0, s>>>(g, dt); break;
-    case 3: graph_stage_kernel<M, 3><<<grid, block, 0, s>>>(g, dt); break;
-    default: graph_stage_kernel<M, 4><<<grid, block, 0, s>>>(g, dt); break;
+    case 1: graph_stage_kernel<M, 1><<<grid, block, 0, s>>>(g, step_size(dt)); break;
+    case 2: graph_stage_kernel<M, 2><<<grid, block, 0, s>>>(g, step_size(dt)); break;
+    case 3: graph_stage_kernel<M, 3><<<grid, block, 0, s>>>(g, step_size(dt)); break;
+    default: graph_stage_kernel<M, 4><<<grid, block, 0, s>>>(g, step_size(dt)); break;
     }
     return cudaGetLastError();
 }

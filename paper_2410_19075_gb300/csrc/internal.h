@@ -15,6 +15,14 @@ constexpr int kSubLog2 = 8;
 constexpr int kGroup = 64;              // sub-tiles per prefix group
 constexpr int kGroupLog2 = 6;
 
+// RK4 step size and the multiples the stage updates use, computed once on the
+// host (IEEE division: the same bits as on the device), so that no thread
+// divides.
+struct StepSize {
+    double dt, half, sixth; // dt, dt / 2, dt / 6
+};
+inline StepSize step_size(double dt) { return StepSize{dt, 0.5 * dt, dt / 6.0}; }
+
 // Device buffers and sizes of one ring network (plain path).
 struct RingPlan {
     int model;

@@ -241,7 +241,7 @@ __device__ void lattice_record_order(const LatticePlan &p, i128 ps, i128 pc)
 // stage input, the RK4 update, the next stage input's local variables and (sin,
 // cos).  STAGE 0 (prologue) only computes (sin, cos) of y.
 template <int M, int STAGE>
-__device__ __forceinline__ void lattice_node(const LatticePlan &p, int64_t n, int64_t W0, int64_t W1, double dt,
+__device__ __forceinline__ void lattice_node(const LatticePlan &p, int64_t n, int64_t W0, int64_t W1, const StepSize &h,
                                              bool &ok, i128 &ps, i128 &pc)
 {
     constexpr int D = Model<M>::D, NX = Model<M>::NX, XOFF = D - NX;
@@ -264,15 +264,15 @@ __device__ __forceinline__ void lattice_node(const LatticePlan &p, int64_t n, in
             const double yv = p.y[v * nodes + n];
             if (STAGE == 1) {
                 p.acc[v * nodes + n] = k[v];
-                xn[v] = yv + (0.5 * dt) * k[v];
+                xn[v] = yv + h.half * k[v];
             } else if (STAGE == 2) {
                 p.acc[v * nodes + n] = p.acc[v * nodes + n] + 2.0 * k[v];
-                xn[v] = yv + (0.5 * dt) * k[v];
+                xn[v] = yv + h.half * k[v];
             } else if (STAGE == 3) {
                 p.acc[v * nodes + n] = p.acc[v * nodes + n] + 2.0 * k[v];
-                xn[v] = yv + dt * k[v];
+                xn[v] = yv + h.dt * k[v];
             } else {
-                xn[v] = yv + (dt / 6.0) * (p.acc[v * nodes + n] + k[v]);
+                xn[v] = yv + h.sixth * (p.acc[v * nodes + n] + k[v]);
                 p.y[v * nodes + n] = xn[v];
             }
         }
@@ -294,7 +294,7 @@ __device__ __forceinline__ void lattice_node(const LatticePlan &p, int64_t n, in
 // cube z pass: one thread per (i, j) column, sliding window along k, fused with
 // the node update.  Also the prologue of every lattice (STAGE 0, no window).
 template <int M, int STAGE>
-__global__ void __launch_bounds__(kColThreads) cube_z_kernel(LatticePlan p, double dt)
+__global__ void __launch_bounds__(kColThreads) cube_z_kernel(LatticePlan p, const StepSize h)
 {
     const int64_t N1 = p.N1, P = p.P, nodes = p.nodes, plane = N1 * N1;
     const int64_t i = (int64_t)blockIdx.x * kColThreads + threadIdx.x;
@@ -314,7 +314,7 @@ __global__ void __launch_bounds__(kColThreads) cube_z_kernel(LatticePlan p, doub
             }
         }
         for (int64_t k = 0; k < N1; ++k) {
-            lattice_node<M, STAGE>(p, col + k * plane, s0, s1, dt, ok, ps, pc);
+            lattice_node<M, STAGE>(p, col + k * plane, s0, s1, h, ok, ps, pc);
             if (STAGE > 0) {
                 int64_t kin = k + P + 1, kout = k - P;
                 if (kin >= N1) kin -= N1;
@@ -333,7 +333,7 @@ __global__ void __launch_bounds__(kColThreads) cube_z_kernel(LatticePlan p, doub
 // entries of one row (wrapping arithmetic; every chord sum and the window sum
 // itself are exact).
 template <int M, int STAGE>
-__global__ void __launch_bounds__(kGatherThreads) lattice_gather_kernel(LatticePlan p, double dt)
+__global__ void __launch_bounds__(kGatherThreads) lattice_gather_kernel(LatticePlan p, const StepSize h)
 {
     const int64_t N1 = p.N1, nodes = p.nodes;
     const int64_t n = (int64_t)blockIdx.x * kGatherThreads + threadIdx.x;
@@ -360,7 +360,7 @@ __global__ void __launch_bounds__(kGatherThreads) lattice_gather_kernel(LatticeP
                 w1 += (uint64_t)b.y - (uint64_t)a.y;
             }
         }
-        lattice_node<M, STAGE>(p, n, (int64_t)w0, (int64_t)w1, dt, ok, ps, pc);
+        lattice_node<M, STAGE>(p, n, (int64_t)w0, (int64_t)w1, h, ok, ps, pc);
     }
     if (!ok) raise_error(p.err, ERR_RANGE);
     if (STAGE == 0 || STAGE == 4) lattice_record_order(p, ps, pc);
@@ -416,8 +416,8 @@ static cudaError_t launch_x(const LatticePlan &p, cudaStream_t s)
 template <int M, int STAGE>
 static cudaError_t launch_node_pass(const LatticePlan &p, double dt, cudaStream_t s)
 {
-    if (p.topo == 1) cube_z_kernel<M, STAGE><<<col_grid(p.N1), kColThreads, 0, s>>>(p, dt);
-    else lattice_gather_kernel<M, STAGE><<<gather_grid(p), kGatherThreads, 0, s>>>(p, dt);
+    if (p.topo == 1) cube_z_kernel<M, STAGE><<<col_grid(p.N1), kColThreads, 0, s>>>(p, step_size(dt));
+    else lattice_gather_kernel<M, STAGE><<<gather_grid(p), kGatherThreads, 0, s>>>(p, step_size(dt));
     return cudaGetLastError();
 }
 
@@ -426,8 +426,9 @@ static cudaError_t launch_stage(int stage, const LatticePlan &p, double dt, cuda
 {
     if (stage == 0) {
         // prologue: (sin, cos) of y and its order parameter, no window
-        return p.topo == 1 ? (cube_z_kernel<M, 0><<<col_grid(p.N1), kColThreads, 0, s>>>(p, 0.0), cudaGetLastError())
-                           : (lattice_gather_kernel<M, 0><<<gather_grid(p), kGatherThreads, 0, s>>>(p, 0.0),
+        return p.topo == 1 ? (cube_z_kernel<M, 0><<<col_grid(p.N1), kColThreads, 0, s>>>(p, step_size(0.0)),
+                              cudaGetLastError())
+                           : (lattice_gather_kernel<M, 0><<<gather_grid(p), kGatherThreads, 0, s>>>(p, step_size(0.0)),
                               cudaGetLastError());
     }
     cudaError_t e = launch_x(p, s);

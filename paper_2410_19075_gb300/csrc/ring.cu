@@ -34,19 +34,20 @@ template <int NQ> struct RingGather {
 
 // One 256-node sub-tile `sub` of ring P, one node per thread (the whole CTA).
 template <int M, int STAGE>
-__device__ __forceinline__ void ring_stage_body(const RingPlan &P, const RingStageIO &a, double dt, int64_t sub)
+__device__ __forceinline__ void ring_stage_body(const RingPlan &P, const RingStageIO &a, const StepSize &h,
+                                                int64_t sub)
 {
     constexpr int NQ = Model<M>::NQ;
     __shared__ RingBases<NQ> s_bases;
     if (STAGE > 0) ring_load_bases<NQ>(P, a.ingrp_in, a.grpofs_in, sub, s_bases);
-    stage_body<M, STAGE>(P, a, dt, sub, RingGather<NQ>{P, a.lam_in, s_bases});
+    stage_body<M, STAGE>(P, a, h, sub, RingGather<NQ>{P, a.lam_in, s_bases});
 }
 
 // Plain path: one ring, one sub-tile per CTA.
 template <int M, int STAGE>
-__global__ void __launch_bounds__(kRingThreads, MinBlocks<M>::value) ring_stage_kernel(const RingPlan p, double dt)
+__global__ void __launch_bounds__(kRingThreads, MinBlocks<M>::value) ring_stage_kernel(const RingPlan p, const StepSize h)
 {
-    ring_stage_body<M, STAGE>(p, stage_io<M, STAGE>(p), dt, blockIdx.x);
+    ring_stage_body<M, STAGE>(p, stage_io<M, STAGE>(p), h, blockIdx.x);
 }
 
 // Batched path: CTA b works on sub-tile b - item_base[inst] of ring inst =
@@ -56,12 +57,12 @@ __global__ void __launch_bounds__(kRingThreads, MinBlocks<M>::value) ring_stage_
 template <int M, int STAGE>
 __global__ void __launch_bounds__(kRingThreads, MinBlocks<M>::value)
     ring_batch_stage_kernel(const RingPlan *__restrict__ plans, const int *__restrict__ inst_of_item,
-                            const int64_t *__restrict__ item_base, double dt)
+                            const int64_t *__restrict__ item_base, const StepSize h)
 {
     const int inst = inst_of_item[blockIdx.x];
     const RingPlan &p = plans[inst];
     if (p.steps_left && *(volatile long long *)p.steps_left <= 0) return;
-    ring_stage_body<M, STAGE>(p, stage_io<M, STAGE>(p), dt, (int64_t)blockIdx.x - item_base[inst]);
+    ring_stage_body<M, STAGE>(p, stage_io<M, STAGE>(p), h, (int64_t)blockIdx.x - item_base[inst]);
 }
 
 template <int M>
@@ -69,11 +70,11 @@ static cudaError_t launch_stage(int stage, const RingPlan &p, double dt, cudaStr
 {
     const dim3 grid((unsigned)p.nsub), block(kRingThreads);
     switch (stage) {
-    case 0: ring_stage_kernel<M, 0><<<grid, block, 0, s>>>(p, dt); break;
-    case 1: ring_stage_kernel<M, 1><<<grid, block, 0, s>>>(p, dt); break;
-    case 2: ring_stage_kernel<M, 2><<<grid, block, 0, s>>>(p, dt); break;
-    case 3: ring_stage_kernel<M, 3><<<grid, block, 0, s>>>(p, dt); break;
-    default: ring_stage_kernel<M, 4><<<grid, block, 0, s>>>(p, dt); break;
+    case 0: ring_stage_kernel<M, 0><<<grid, block, 0, s>>>(p, step_size(dt)); break;
+    case 1: ring_stage_kernel<M, 1><<<grid, block, 0, s>>>(p, step_size(dt)); break;
+    case 2: ring_stage_kernel<M, 2><<<grid, block, 0, s>>>(p, step_size(dt)); break;
+    case 3: ring_stage_kernel<M, 3><<<grid, block, 0, s>>>(p, step_size(dt)); break;
+    default: ring_stage_kernel<M, 4><<<grid, block, 0, s>>>(p, step_size(dt)); break;
     }
     return cudaGetLastError();
 }
@@ -93,10 +94,10 @@ static cudaError_t launch_batch_stage(int stage, const RingBatchGroup &g, double
 {
     const dim3 grid((unsigned)g.n_items), block(kRingThreads);
     switch (stage) {
-    case 1: ring_batch_stage_kernel<M, 1><<<grid, block, 0, s>>>(g.plans, g.inst_of_item, g.item_base, dt); break;
-    case 2: ring_batch_stage_kernel<M, 2><<<grid, block, 0, s>>>(g.plans, g.inst_of_item, g.item_base, dt); break;
-    case 3: ring_batch_stage_kernel<M, 3><<<grid, block, 0, s>>>(g.plans, g.inst_of_item, g.item_base, dt); break;
-    default: ring_batch_stage_kernel<M, 4><<<grid, block, 0, s>>>(g.plans, g.inst_of_item, g.item_base, dt); break;
+    case 1: ring_batch_stage_kernel<M, 1><<<grid, block, 0, s>>>(g.plans, g.inst_of_item, g.item_base, step_size(dt)); break;
+    case 2: ring_batch_stage_kernel<M, 2><<<grid, block, 0, s>>>(g.plans, g.inst_of_item, g.item_base, step_size(dt)); break;
+    case 3: ring_batch_stage_kernel<M, 3><<<grid, block, 0, s>>>(g.plans, g.inst_of_item, g.item_base, step_size(dt)); break;
+    default: ring_batch_stage_kernel<M, 4><<<grid, block, 0, s>>>(g.plans, g.inst_of_item, g.item_base, step_size(dt)); break;
     }
     return cudaGetLastError();
 }

@@ -234,7 +234,7 @@ __host__ __device__ __forceinline__ RingStageIO stage_io(const RingPlan &p)
 // gives node i's own fixed-point coupled quantity and its window sums W, plus
 // its link count and coupling scale for the model (see models.cuh).
 template <int M, int STAGE, class Gather>
-__device__ __forceinline__ void stage_body(const RingPlan &P, const RingStageIO &a, double dt, int64_t sub,
+__device__ __forceinline__ void stage_body(const RingPlan &P, const RingStageIO &a, const StepSize &h, int64_t sub,
                                            const Gather &gather)
 {
     using Mo = Model<M>;
@@ -271,15 +271,15 @@ __device__ __forceinline__ void stage_body(const RingPlan &P, const RingStageIO 
                 const double yv = P.y[v * N + i];
                 if (STAGE == 1) {
                     P.acc[v * N + i] = k[v];
-                    xn[v] = yv + (0.5 * dt) * k[v];
+                    xn[v] = yv + h.half * k[v];
                 } else if (STAGE == 2) {
                     P.acc[v * N + i] = P.acc[v * N + i] + 2.0 * k[v];
-                    xn[v] = yv + (0.5 * dt) * k[v];
+                    xn[v] = yv + h.half * k[v];
                 } else if (STAGE == 3) {
                     P.acc[v * N + i] = P.acc[v * N + i] + 2.0 * k[v];
-                    xn[v] = yv + dt * k[v];
+                    xn[v] = yv + h.dt * k[v];
                 } else {
-                    const double yn = yv + (dt / 6.0) * (P.acc[v * N + i] + k[v]);
+                    const double yn = yv + h.sixth * (P.acc[v * N + i] + k[v]);
                     P.y[v * N + i] = yn;
                     xn[v] = yn;
                 }
