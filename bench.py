@@ -75,7 +75,9 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-sweep comparison")
     ap.add_argument("--no-served", action="store_true", help="skip the served-mix comparison")
     ap.add_argument("--no-extra", action="store_true", help="skip the small-ring and lattice lines")
-    ap.add_argument("--batched-only", action="store_true")
+    ap.add_argument("--only", choices=["dp5", "graph"], default=None,
+                    help="run only one side line (for profiling): the Dormand-Prince sweep or the link matrices")
+    ap.add_argument("--instances", type=int, default=4096, help="networks in the Dormand-Prince sweep")
     ap.add_argument("--graph-ball", action="store_true",
                     help="also time the 100^3 ball lattice (P = 6) as a compressed link matrix (~25 s set-up)")
     return ap.parse_args()
@@ -677,7 +679,7 @@ def run_native(args):
         line["graph"] = bench_graph(args, stream, flush, ball=args.graph_ball)
     if not args.no_batched:
         line["batched"] = bench_batched(args, flush, stream)
-        line["batched_dp5"] = bench_dp5_sweep(args)
+        line["batched_dp5"] = bench_dp5_sweep(args, n_inst=args.instances)
     if not args.no_served:
         line["served"] = bench_served(args, stream)
     net.close()
@@ -688,8 +690,22 @@ def run_native(args):
         dist.destroy_process_group()
 
 
+def run_only(args):
+    import torch
+    torch.cuda.set_device(0)
+    if args.only == "dp5":
+        out = bench_dp5_sweep(args, n_inst=args.instances, plain_inst=min(32, args.instances))
+    else:
+        flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+        out = bench_graph(args, torch.cuda.current_stream(), flush, ball=args.graph_ball)
+    print(json.dumps({"only": args.only, "result": out}), flush=True)
+
+
 def main():
     args = parse()
+    if args.only:
+        run_only(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

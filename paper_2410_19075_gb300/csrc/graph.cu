@@ -90,20 +90,33 @@ __device__ __forceinline__ void graph_load_bases(const GraphPlan &G, const RingS
 }
 
 template <int NQ> struct GraphGather {
+    struct Pre {
+        int64_t l[NQ], lp[NQ];
+    };
     const GraphPlan &G;
     const RingStageIO &a;
-    const GraphBases<NQ> &B;
-    int nb; // runs with per-CTA bases
-    __device__ __forceinline__ void operator()(int tid, int64_t i, int64_t (&qo)[NQ], double (&fo)[NQ],
-                                               i128 (&W)[NQ], int64_t &wsize, double &cs) const
+    GraphBases<NQ> &B;
+    int nb;      // runs with per-CTA bases
+    int64_t sub; // the CTA's sub-tile
+    __device__ __forceinline__ void load(int tid, int64_t i, Pre &pre) const
+    {
+        const int64_t N = G.r.N;
+#pragma unroll
+        for (int c = 0; c < NQ; ++c) {
+            const int64_t *lam = a.lam_in + c * N;
+            pre.l[c] = __ldg(lam + i);
+            pre.lp[c] = tid ? __ldg(lam + i - 1) : 0;
+        }
+    }
+    __device__ __forceinline__ void sync() const { graph_load_bases<NQ>(G, a, sub, nb, B); }
+    __device__ __forceinline__ void finish(int tid, int64_t i, const Pre &pre, int64_t (&qo)[NQ], double (&fo)[NQ],
+                                           i128 (&W)[NQ], int64_t &wsize, double &cs) const
     {
         const RingPlan &P = G.r;
         const int64_t N = P.N;
 #pragma unroll
         for (int c = 0; c < NQ; ++c) {
-            const int64_t *lam = a.lam_in + c * N;
-            const int64_t l = __ldg(lam + i);
-            qo[c] = tid ? l - __ldg(lam + i - 1) : l;
+            qo[c] = pre.l[c] - pre.lp[c];
             fo[c] = fixed_to_double(qo[c], P.F);
             W[c] = 0;
         }
@@ -160,8 +173,7 @@ __global__ void __launch_bounds__(kRingThreads, GraphMinBlocks<M>::value)
     __shared__ GraphBases<NQ> s_bases;
     const RingStageIO a = stage_io<M, STAGE>(g.r);
     const int nb = g.nruns < kGraphSmemRuns ? g.nruns : kGraphSmemRuns;
-    graph_load_bases<NQ>(g, a, blockIdx.x, nb, s_bases);
-    stage_body<M, STAGE>(g.r, a, h, blockIdx.x, GraphGather<NQ>{g, a, s_bases, nb});
+    stage_body<M, STAGE>(g.r, a, h, blockIdx.x, GraphGather<NQ>{g, a, s_bases, nb, (int64_t)blockIdx.x});
 }
 
 template <int M>

@@ -18,15 +18,46 @@
 
 namespace simk {
 
-// Ring window: the node's two window ends read through the per-CTA bases.
+// Ring window in three phases.  load(): the node's own prefix entries and the
+// in-sub-tile prefix at both window ends, b = i+R+1 and a = i-R on the periodic
+// extension (a piece never straddles 0 or N, so the copy of the ring each end
+// falls in is known without the bases).  sync(): the bases threads 0 and 1
+// computed become visible.  finish(): W = base(b) - base(a) + the loaded parts,
+// exactly as ring_window computes it.
 template <int NQ> struct RingGather {
+    struct Pre {
+        int64_t l[NQ], lp[NQ], lb[NQ], la[NQ];
+    };
     const RingPlan &P;
     const int64_t *lam_in;
     const RingBases<NQ> &B;
-    __device__ __forceinline__ void operator()(int tid, int64_t i, int64_t (&qo)[NQ], double (&fo)[NQ],
-                                               i128 (&W)[NQ], int64_t &wsize, double &cs) const
+    __device__ __forceinline__ void load(int tid, int64_t i, Pre &pre) const
     {
-        ring_window<NQ>(P, lam_in, B, tid, i, qo, fo, W);
+        const int64_t N = P.N;
+        const int64_t b = i + P.R + 1, am = i - P.R;
+        const int64_t bp = b >= N ? b - N : b, ap = am < 0 ? am + N : am;
+#pragma unroll
+        for (int c = 0; c < NQ; ++c) {
+            const int64_t *lam = lam_in + c * N;
+            pre.l[c] = __ldg(lam + i);
+            pre.lp[c] = tid ? __ldg(lam + i - 1) : 0;
+            pre.lb[c] = (bp & (kSubTile - 1)) ? __ldg(lam + bp - 1) : 0;
+            pre.la[c] = (ap & (kSubTile - 1)) ? __ldg(lam + ap - 1) : 0;
+        }
+    }
+    __device__ __forceinline__ void sync() const { __syncthreads(); }
+    __device__ __forceinline__ void finish(int tid, int64_t i, const Pre &pre, int64_t (&qo)[NQ], double (&fo)[NQ],
+                                           i128 (&W)[NQ], int64_t &wsize, double &cs) const
+    {
+        const int64_t b = i + P.R + 1, am = i - P.R;
+        const int kb = (b >= B.start[0][1]) + (b >= B.start[0][2]);
+        const int ka = (am >= B.start[1][1]) + (am >= B.start[1][2]);
+#pragma unroll
+        for (int c = 0; c < NQ; ++c) {
+            qo[c] = pre.l[c] - pre.lp[c];
+            fo[c] = fixed_to_double(qo[c], P.F);
+            W[c] = (B.base[0][kb][c] - B.base[1][ka][c]) + (i128)(pre.lb[c] - pre.la[c]);
+        }
         wsize = -1; // the network's window size
         cs = 1.0;
     }
@@ -39,7 +70,7 @@ __device__ __forceinline__ void ring_stage_body(const RingPlan &P, const RingSta
 {
     constexpr int NQ = Model<M>::NQ;
     __shared__ RingBases<NQ> s_bases;
-    if (STAGE > 0) ring_load_bases<NQ>(P, a.ingrp_in, a.grpofs_in, sub, s_bases);
+    if (STAGE > 0) ring_compute_bases<NQ>(P, a.ingrp_in, a.grpofs_in, sub, s_bases);
     stage_body<M, STAGE>(P, a, h, sub, RingGather<NQ>{P, a.lam_in, s_bases});
 }
 

@@ -38,7 +38,7 @@ __device__ __forceinline__ i128 warp_incl_scan_i128(i128 v)
 
 // Resident CTAs per SM the register allocation is sized for (256 threads each).
 #ifndef SIM_RING_MIN_BLOCKS
-#define SIM_RING_MIN_BLOCKS 6
+#define SIM_RING_MIN_BLOCKS 5
 #endif
 template <int M> struct MinBlocks { static constexpr int value = SIM_RING_MIN_BLOCKS; };
 template <> struct MinBlocks<2> { static constexpr int value = 2; };
@@ -54,10 +54,10 @@ template <int NQ> struct RingBases {
     int64_t start[2][3], qn[2][3];
 };
 
-// Called by every thread of the CTA (contains a __syncthreads).
+// Threads 0 and 1 write the bases; the caller makes them visible with a barrier.
 template <int NQ>
-__device__ __forceinline__ void ring_load_bases(const RingPlan &P, const i128 *ingrp_in, const i128 *grpofs_in,
-                                                int64_t sub, RingBases<NQ> &B)
+__device__ __forceinline__ void ring_compute_bases(const RingPlan &P, const i128 *ingrp_in, const i128 *grpofs_in,
+                                                   int64_t sub, RingBases<NQ> &B)
 {
     const int tid = threadIdx.x;
     const int64_t N = P.N, nsub = P.nsub, ngroups = P.ngroups;
@@ -91,6 +91,14 @@ __device__ __forceinline__ void ring_load_bases(const RingPlan &P, const i128 *i
             p = end + qn + 1;
         }
     }
+}
+
+// Called by every thread of the CTA (contains a __syncthreads).
+template <int NQ>
+__device__ __forceinline__ void ring_load_bases(const RingPlan &P, const i128 *ingrp_in, const i128 *grpofs_in,
+                                                int64_t sub, RingBases<NQ> &B)
+{
+    ring_compute_bases<NQ>(P, ingrp_in, grpofs_in, sub, B);
     __syncthreads();
 }
 
@@ -230,9 +238,13 @@ __host__ __device__ __forceinline__ RingStageIO stage_io(const RingPlan &p)
 
 // RK4 stage s of node-parallel networks whose coupling is a sum over exact
 // prefixes of the coupled quantity in node order (rings and general link
-// matrices): one 256-node sub-tile `sub` per CTA, one node per thread.  gather
-// gives node i's own fixed-point coupled quantity and its window sums W, plus
-// its link count and coupling scale for the model (see models.cuh).
+// matrices): one 256-node sub-tile `sub` per CTA, one node per thread.  The
+// gather works in three phases: load() issues the node's own global loads (they
+// need nothing shared), sync() makes the CTA's shared window bases visible (a
+// barrier every thread reaches), finish() combines them into the node's own
+// fixed-point coupled quantity, its window sums W, its link count and coupling
+// scale (see models.cuh).  The node's state loads are issued before the barrier
+// as well, so the CTA's start latency overlaps the bases' computation.
 template <int M, int STAGE, class Gather>
 __device__ __forceinline__ void stage_body(const RingPlan &P, const RingStageIO &a, const StepSize &h, int64_t sub,
                                            const Gather &gather)
@@ -248,6 +260,23 @@ __device__ __forceinline__ void stage_body(const RingPlan &P, const RingStageIO 
     bool ok = true;
 #pragma unroll
     for (int c = 0; c < NQ; ++c) qv[c] = 0;
+    double yv[D], av[D], X[NX > 0 ? NX : 1];
+    double Iext = 0.0;
+    typename Gather::Pre pre;
+    if (STAGE > 0) {
+        if (i < N) {
+            gather.load(tid, i, pre);
+#pragma unroll
+            for (int v = 0; v < D; ++v) {
+                yv[v] = P.y[v * N + i];
+                av[v] = STAGE >= 2 ? P.acc[v * N + i] : 0.0;
+            }
+#pragma unroll
+            for (int g = 0; g < NX; ++g) X[g] = a.x_in[g * N + i];
+            if (M == 2 && P.node_param) Iext = P.node_param[i];
+        }
+        gather.sync();
+    }
     if (i < N) {
         double xn[D];
         if (STAGE == 0) {
@@ -259,27 +288,22 @@ __device__ __forceinline__ void stage_body(const RingPlan &P, const RingStageIO 
             i128 W[NQ];
             int64_t wsize;
             double cs;
-            gather(tid, i, qo, fo, W, wsize, cs);
-            double X[NX > 0 ? NX : 1];
-#pragma unroll
-            for (int g = 0; g < NX; ++g) X[g] = a.x_in[g * N + i];
-            const double Iext = (M == 2 && P.node_param) ? P.node_param[i] : 0.0;
+            gather.finish(tid, i, pre, qo, fo, W, wsize, cs);
             double k[D];
             Mo::rhs(P.mp, P.F, fo, qo, W, X, Iext, k, wsize, cs);
 #pragma unroll
             for (int v = 0; v < D; ++v) {
-                const double yv = P.y[v * N + i];
                 if (STAGE == 1) {
                     P.acc[v * N + i] = k[v];
-                    xn[v] = yv + h.half * k[v];
+                    xn[v] = yv[v] + h.half * k[v];
                 } else if (STAGE == 2) {
-                    P.acc[v * N + i] = P.acc[v * N + i] + 2.0 * k[v];
-                    xn[v] = yv + h.half * k[v];
+                    P.acc[v * N + i] = av[v] + 2.0 * k[v];
+                    xn[v] = yv[v] + h.half * k[v];
                 } else if (STAGE == 3) {
-                    P.acc[v * N + i] = P.acc[v * N + i] + 2.0 * k[v];
-                    xn[v] = yv + h.dt * k[v];
+                    P.acc[v * N + i] = av[v] + 2.0 * k[v];
+                    xn[v] = yv[v] + h.dt * k[v];
                 } else {
-                    const double yn = yv + h.sixth * (P.acc[v * N + i] + k[v]);
+                    const double yn = yv[v] + h.sixth * (av[v] + k[v]);
                     P.y[v * N + i] = yn;
                     xn[v] = yn;
                 }
