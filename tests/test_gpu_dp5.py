@@ -175,3 +175,8 @@ def test_dp5_rejects_lattices_and_bad_options():
                     dict(t_end=1.0, rtol=1e-8, atol=1e-8, h0=0.0)):
             with pytest.raises(SimError):
                 net.dp5(**bad)
+
+
+def test_dp5_several_prefix_groups():
+    """A ring of 2 groups of 64 sub-tiles plus a ragged tail."""
+    _check(0, 2 * 64 * 256 + 77, 100, 45, 3.0, 1e-9, 0.01, out_dt=0.5)

@@ -186,3 +186,10 @@ def test_invalid_link_matrices_rejected():
     with pytest.raises(SimError):
         net.dp5(t_end=1.0, rtol=1e-8, atol=1e-8, h0=0.01)
     net.close()
+
+
+def test_random_graph_several_prefix_groups():
+    """20,000 nodes (2 groups of 64 sub-tiles): every model."""
+    rp, col = I.random_links(20000, 6, 74)
+    for model in (0, 1, 2, 3):
+        _run(model, 20000, rp, col, 60, 75)

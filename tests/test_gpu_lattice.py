@@ -198,3 +198,25 @@ def test_order_parameter_of_large_lattices_with_small_windows(topo, N1, P):
     assert order.size == 4
     assert abs(order[0] - oracle.order_parameter(y0)) <= ORDER_TOL
     assert abs(order[-1] - oracle.order_parameter(y)) <= ORDER_TOL
+
+
+@pytest.mark.parametrize("topo,dims,N1,P", [(BALL, 3, 1024, 1), (DISK, 2, 8192, 3)])
+def test_largest_lattices_plane_wave_closed_form(topo, dims, N1, P):
+    """The largest lattices the API accepts (1024^3 = 1.07e9 nodes, 8192^2): a plane
+    wave along y has the same right-hand side at every node (the closed form
+    counted from the geometry), checked at every node, so every index of the
+    x pass and the gather past 2^31 is exercised."""
+    from paper_2410_19075_gb300 import Network
+    omega, mu, alpha, q = 0.2, 1.0, 1.3, 5
+    kap = 2 * math.pi * q / N1
+    offs = [o for o in _window_offsets(dims, P) if o != (0, 0, 0)]
+    Om = omega + mu * sum(math.sin(kap * o[1] - alpha) for o in offs) / len(offs)
+    row = np.repeat(kap * np.arange(N1, dtype=np.float64), N1)  # y index of one (x, y) plane
+    y0 = np.tile(row, N1) if dims == 3 else row
+    with Network(0, topo, N1, P, [omega, mu, alpha]) as net:
+        net.set_state(y0)
+        k = net.rhs()
+        order = net.observables()
+    assert k.size == N1 ** dims
+    assert np.abs(k - Om).max() < 1e-12
+    assert np.abs(order).max() < 1e-12

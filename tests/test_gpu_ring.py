@@ -225,3 +225,12 @@ def test_cluster_path_equals_streaming_path_bitwise(model, N, R):
     assert np.array_equal(outs[0][0], outs[1][0])
     assert np.array_equal(outs[0][1], outs[1][1])
     assert np.array_equal(outs[0][2], outs[1][2])
+
+
+@pytest.mark.parametrize("model,N,R,steps", [(1, 64 * 256, 700, 30), (1, 64 * 256 + 1, 700, 30),
+                                             (1, 3 * 64 * 256 + 1000, 1500, 10), (0, 3 * 64 * 256 + 1000, 50, 100),
+                                             (2, 2 * 64 * 256 + 5, 100, 50), (3, 2 * 64 * 256 + 255, 500, 20)])
+def test_ring_several_prefix_groups(model, N, R, steps):
+    """Exactly one group of 64 sub-tiles, one node more, and several groups with a
+    ragged last group and sub-tile: the exact prefix across groups (level 2)."""
+    _check(model, N, R, steps, 900 + N, threads=0)
