@@ -220,3 +220,19 @@ def test_largest_lattices_plane_wave_closed_form(topo, dims, N1, P):
     assert k.size == N1 ** dims
     assert np.abs(k - Om).max() < 1e-12
     assert np.abs(order).max() < 1e-12
+
+
+def test_largest_cube_plane_wave_closed_form():
+    """The 1024^3 cube (P = 1): a plane wave along z, closed form at every node."""
+    from paper_2410_19075_gb300 import Network
+    N1, P, q = 1024, 1, 7
+    omega, mu, alpha = 0.1, 1.0, 1.2
+    kap = 2 * math.pi * q / N1
+    offs = [(dx, dy, dz) for dx in range(-P, P + 1) for dy in range(-P, P + 1) for dz in range(-P, P + 1)
+            if (dx, dy, dz) != (0, 0, 0)]
+    Om = omega + mu * sum(math.sin(kap * o[2] - alpha) for o in offs) / len(offs)
+    y0 = np.repeat(kap * np.arange(N1, dtype=np.float64), N1 * N1)  # z index
+    with Network(0, CUBE, N1, P, [omega, mu, alpha]) as net:
+        net.set_state(y0)
+        k = net.rhs()
+    assert np.abs(k - Om).max() < 1e-12

@@ -234,3 +234,21 @@ def test_ring_several_prefix_groups(model, N, R, steps):
     """Exactly one group of 64 sub-tiles, one node more, and several groups with a
     ragged last group and sub-tile: the exact prefix across groups (level 2)."""
     _check(model, N, R, steps, 900 + N, threads=0)
+
+
+def test_ring_past_2_to_31_nodes_twisted_state():
+    """A Kuramoto ring of 2^31 + 12345 nodes (about 100 GB on the device): the
+    twisted state's closed-form rotation at every node, so node indices past the
+    32-bit range run through every part of the stage kernel and the prefix."""
+    from paper_2410_19075_gb300 import Network
+    N, R, q = 2 ** 31 + 12345, 1000, 3
+    omega, mu, alpha = 0.1, 1.0, 1.46
+    y0 = (2 * math.pi * q / N) * np.arange(N, dtype=np.float64)
+    k = 2 * math.pi * q / N
+    Om = omega - (mu / R) * math.sin(alpha) * math.sin(R * k / 2) * math.cos((R + 1) * k / 2) / math.sin(k / 2)
+    with Network(0, 0, N, R, [omega, mu, alpha]) as net:
+        net.set_state(y0)
+        del y0
+        kk = net.rhs()
+    assert kk.size == N
+    assert np.abs(kk - Om).max() < 1e-12
