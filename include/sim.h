@@ -89,9 +89,15 @@ typedef enum {
 #define SIM_FLAG_INCLUDE_SELF 1u /* count the node itself as one of its links */
 #define SIM_FLAG_STREAMING 2u    /* rings of <= 4096 nodes: use the multi-launch streaming kernels
                                     instead of the thread-block-cluster kernel (same results) */
+#define SIM_FLAG_LOW_MEMORY 4u   /* ball and disk lattices: keep one periodically extended row
+                                    prefix (about 16 B per node) instead of one x-window array
+                                    per chord half-width ((P+1) * 16 B per node, the default for
+                                    P >= 5 when it stays within 8 GiB), at two loads per chord
+                                    instead of one; the results are the same bits */
 
-/* Bytes of device memory sim_create() allocates for this network (for
- * admission control).  Returns 0 for invalid arguments. */
+/* Bytes of device memory sim_create() allocates for this network with flags 0
+ * (an upper bound for any flags; for admission control).  Returns 0 for invalid
+ * arguments. */
 size_t sim_workspace_bytes(int model, int topology, int64_t N, int64_t radius);
 
 /* Create a network.  params: n_params doubles in the model's order (above).

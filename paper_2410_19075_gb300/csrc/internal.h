@@ -153,6 +153,8 @@ struct LatticePlan {
                       // rs (sin, cos) pairs of the periodically extended inclusive
                       // prefix E(x), x in [-P-1, N1+P-1], stored at x + P + 1
     int64_t rs;       // ball, disk: row stride of sx in (sin, cos) pairs, N1 + 2P + 1
+    int wmode;        // ball, disk: sx holds, for w = 0..P, nodes (sin, cos) pairs of the
+                      // x-window sums S_w (one load per chord) instead of the row prefixes
     int64_t *sxy;     // 2 * nodes: cube box sums over x and y
     i128 *partial;    // per-CTA partial sums of the order parameter
     unsigned long long *done_ctr;
@@ -166,7 +168,8 @@ struct LatticePlan {
 
 cudaError_t lattice_configure(); // once per process, before the first launch
 int64_t lattice_order_blocks(int topo, int64_t N1); // CTAs of the order-parameter passes
-int64_t lattice_sx_elems(int topo, int64_t N1, int64_t P); // int64 elements of sx
+int64_t lattice_sx_elems(int topo, int64_t N1, int64_t P, bool wmode); // int64 elements of sx
+constexpr int64_t kLatticeWindowBudget = int64_t(8) << 30; // bytes of the per-w window arrays
 cudaError_t lattice_prologue(const LatticePlan &p, cudaStream_t s);
 cudaError_t lattice_step(const LatticePlan &p, double dt, cudaStream_t s);
 cudaError_t lattice_rhs(const LatticePlan &p, cudaStream_t s); // acc <- f(y)

@@ -11,14 +11,16 @@
 //   z pass  W(i,j,k)   = sum_{|dz|<=P} SXY(i,j,k+dz)       (sliding window along k)
 //           fused with the right-hand side, the RK4 update and the next (sin, cos).
 // Ball and disk, per RK4 stage:
-//   x pass  the inclusive prefix E(x) of Q(f) along every row, extended
-//           periodically by P + 1 entries on the left and P on the right, with
-//           sin and cos interleaved (wrapping int64);
+//   x pass  for every half-width w = 0..P the x-window sums S_w(i) of Q(f) along
+//           every row, sin and cos interleaved; or, when those P+1 arrays would
+//           exceed the memory budget (or SIM_FLAG_LOW_MEMORY), the inclusive row
+//           prefix E(x) extended periodically by P + 1 entries on the left and P
+//           on the right (wrapping int64);
 //   gather  W = sum over the chords of the window, one per (dy, dz) (ball) or dy
 //           (disk): the row segment |dx| <= w = floor(sqrt(P^2 - dy^2 - dz^2)),
-//           read as E(i + w) - E(i - w - 1), one 16-byte load per end (O(P^2)
-//           resp. O(P) reads per node), fused with the right-hand side and RK4
-//           update.
+//           read as S_w (one 16-byte load) or E(i + w) - E(i - w - 1) (two),
+//           O(P^2) resp. O(P) reads per node, fused with the right-hand side and
+//           RK4 update.
 #include "internal.h"
 
 namespace simk {
@@ -36,11 +38,15 @@ static int row_warps(int64_t N1)
 }
 
 // x pass: one warp per row.  pre(p) = sum_{m<p} Q(f(m)) for p in [0, N1] is built
-// in shared memory (stride N1 + 1 per component).  PREFIX = false (cube) writes
-// the window sums SX(i) = Pe(i+P+1) - Pe(i-P) on the periodic extension
-// Pe(p) = pre(p mod N1) + floor(p / N1) pre(N1); PREFIX = true (ball, disk) writes
-// the inclusive prefix pre(i+1), modulo 2^64.
-template <bool PREFIX>
+// in shared memory (stride N1 + 1 per component).  With Pe(p) = pre(p mod N1) +
+// floor(p / N1) pre(N1) the periodic extension:
+//   MODE 0 (cube)        SX(i) = Pe(i+P+1) - Pe(i-P), sin and cos in two arrays;
+//   MODE 1 (ball, disk,  the extended inclusive prefix E(x) = Pe(x+1),
+//           low memory)  x in [-P-1, N1+P-1], (sin, cos) pairs, modulo 2^64;
+//   MODE 2 (ball, disk)  for every half-width w = 0..P the window sums
+//                        S_w(i) = Pe(i+w+1) - Pe(i-w), (sin, cos) pairs, one
+//                        array of nodes pairs per w.
+template <int MODE>
 __global__ void __launch_bounds__(32 * kRowWarpsMax) lattice_x_kernel(LatticePlan p)
 {
     extern __shared__ int64_t smem[];
@@ -96,7 +102,19 @@ __global__ void __launch_bounds__(32 * kRowWarpsMax) lattice_x_kernel(LatticePla
             pre1[0] = 0;
         }
         __syncwarp();
-        if (PREFIX) {
+        if (MODE == 2) {
+            const int64_t t0 = pre0[N1], t1 = pre1[N1];
+            longlong2 *__restrict__ o = reinterpret_cast<longlong2 *>(p.sx) + row * N1;
+            for (int64_t w = 0; w <= P; ++w, o += nodes) {
+                for (int64_t i = lane; i < N1; i += 32) {
+                    int64_t b = i + w + 1, a = i - w;
+                    int64_t s0 = 0, s1 = 0;
+                    if (b > N1) { b -= N1; s0 += t0; s1 += t1; }
+                    if (a < 0) { a += N1; s0 += t0; s1 += t1; } // Pe(a) = pre(a+N1) - total
+                    o[i] = make_longlong2(s0 + pre0[b] - pre0[a], s1 + pre1[b] - pre1[a]);
+                }
+            }
+        } else if (MODE == 1) {
             // E(x) = Pe(x + 1) for x in [-P-1, N1+P-1], at slot x + P + 1
             const uint64_t t0 = (uint64_t)pre0[N1], t1 = (uint64_t)pre1[N1];
             longlong2 *__restrict__ o = reinterpret_cast<longlong2 *>(p.sx) + row * p.rs;
@@ -329,10 +347,11 @@ __global__ void __launch_bounds__(kColThreads) cube_z_kernel(LatticePlan p, cons
 }
 
 // ball / disk gather: one node per thread; the window is the union of the chords
-// (dy, dz, w) of the plan's table, each the difference of two extended-prefix
-// entries of one row (wrapping arithmetic; every chord sum and the window sum
-// itself are exact).
-template <int M, int STAGE>
+// (dy, dz, w) of the plan's table.  WMODE: one load per chord, the x-window sum
+// S_w of the chord's row; otherwise two, the difference of the row's extended
+// prefix at both ends (wrapping arithmetic; every chord sum and the window sum
+// itself are exact either way, so both give the same bits).
+template <int M, int STAGE, bool WMODE>
 __global__ void __launch_bounds__(kGatherThreads) lattice_gather_kernel(LatticePlan p, const StepSize h)
 {
     const int64_t N1 = p.N1, nodes = p.nodes;
@@ -344,7 +363,8 @@ __global__ void __launch_bounds__(kGatherThreads) lattice_gather_kernel(LatticeP
         const int n1 = (int)N1;
         uint64_t w0 = 0, w1 = 0;
         if (STAGE > 0) {
-            const longlong2 *__restrict__ E = reinterpret_cast<const longlong2 *>(p.sx) + (i + p.P + 1);
+            const longlong2 *__restrict__ E =
+                reinterpret_cast<const longlong2 *>(p.sx) + (WMODE ? (int64_t)i : (int64_t)(i + p.P + 1));
             const int nch = p.nchords;
 #pragma unroll 4
             for (int c = 0; c < nch; ++c) {
@@ -354,10 +374,16 @@ __global__ void __launch_bounds__(kGatherThreads) lattice_gather_kernel(LatticeP
                 jj -= jj >= n1 ? n1 : 0;
                 kk += kk < 0 ? n1 : 0;
                 kk -= kk >= n1 ? n1 : 0;
-                const longlong2 *r = E + (int64_t)(kk * n1 + jj) * p.rs;
-                const longlong2 b = __ldg(r + ch.z), a = __ldg(r - ch.z - 1);
-                w0 += (uint64_t)b.x - (uint64_t)a.x;
-                w1 += (uint64_t)b.y - (uint64_t)a.y;
+                if (WMODE) {
+                    const longlong2 v = __ldg(E + (int64_t)ch.z * nodes + (int64_t)(kk * n1 + jj) * N1);
+                    w0 += (uint64_t)v.x;
+                    w1 += (uint64_t)v.y;
+                } else {
+                    const longlong2 *r = E + (int64_t)(kk * n1 + jj) * p.rs;
+                    const longlong2 b = __ldg(r + ch.z), a = __ldg(r - ch.z - 1);
+                    w0 += (uint64_t)b.x - (uint64_t)a.x;
+                    w1 += (uint64_t)b.y - (uint64_t)a.y;
+                }
             }
         }
         lattice_node<M, STAGE>(p, n, (int64_t)w0, (int64_t)w1, h, ok, ps, pc);
@@ -377,11 +403,11 @@ static unsigned gather_grid(const LatticePlan &p)
     return (unsigned)((p.nodes + kGatherThreads - 1) / kGatherThreads);
 }
 
-int64_t lattice_sx_elems(int topo, int64_t N1, int64_t P)
+int64_t lattice_sx_elems(int topo, int64_t N1, int64_t P, bool wmode)
 {
     if (topo == 1) return 2 * N1 * N1 * N1;
     const int64_t rows = topo == 3 ? N1 : N1 * N1;
-    return 2 * rows * (N1 + 2 * P + 1);
+    return wmode ? 2 * (P + 1) * rows * N1 : 2 * rows * (N1 + 2 * P + 1);
 }
 
 int64_t lattice_order_blocks(int topo, int64_t N1)
@@ -393,10 +419,13 @@ int64_t lattice_order_blocks(int topo, int64_t N1)
 
 cudaError_t lattice_configure()
 {
-    cudaError_t e = cudaFuncSetAttribute(lattice_x_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(lattice_x_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kRowSmemMax);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(lattice_x_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(lattice_x_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kRowSmemMax);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(lattice_x_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kRowSmemMax);
     return e;
 }
@@ -408,8 +437,9 @@ static cudaError_t launch_x(const LatticePlan &p, cudaStream_t s)
     const int64_t rows = p.nodes / p.N1;
     const int64_t want = (rows + w - 1) / w;
     const unsigned grid = (unsigned)(want < 152 * 16 ? want : 152 * 16);
-    if (p.topo == 1) lattice_x_kernel<false><<<grid, 32 * w, smem, s>>>(p);
-    else lattice_x_kernel<true><<<grid, 32 * w, smem, s>>>(p);
+    if (p.topo == 1) lattice_x_kernel<0><<<grid, 32 * w, smem, s>>>(p);
+    else if (p.wmode) lattice_x_kernel<2><<<grid, 32 * w, smem, s>>>(p);
+    else lattice_x_kernel<1><<<grid, 32 * w, smem, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -417,7 +447,8 @@ template <int M, int STAGE>
 static cudaError_t launch_node_pass(const LatticePlan &p, double dt, cudaStream_t s)
 {
     if (p.topo == 1) cube_z_kernel<M, STAGE><<<col_grid(p.N1), kColThreads, 0, s>>>(p, step_size(dt));
-    else lattice_gather_kernel<M, STAGE><<<gather_grid(p), kGatherThreads, 0, s>>>(p, step_size(dt));
+    else if (p.wmode) lattice_gather_kernel<M, STAGE, true><<<gather_grid(p), kGatherThreads, 0, s>>>(p, step_size(dt));
+    else lattice_gather_kernel<M, STAGE, false><<<gather_grid(p), kGatherThreads, 0, s>>>(p, step_size(dt));
     return cudaGetLastError();
 }
 
@@ -428,7 +459,8 @@ static cudaError_t launch_stage(int stage, const LatticePlan &p, double dt, cuda
         // prologue: (sin, cos) of y and its order parameter, no window
         return p.topo == 1 ? (cube_z_kernel<M, 0><<<col_grid(p.N1), kColThreads, 0, s>>>(p, step_size(0.0)),
                               cudaGetLastError())
-                           : (lattice_gather_kernel<M, 0><<<gather_grid(p), kGatherThreads, 0, s>>>(p, step_size(0.0)),
+                           : (lattice_gather_kernel<M, 0, false><<<gather_grid(p), kGatherThreads, 0, s>>>(
+                                  p, step_size(0.0)),
                               cudaGetLastError());
     }
     cudaError_t e = launch_x(p, s);

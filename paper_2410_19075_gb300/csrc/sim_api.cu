@@ -95,7 +95,19 @@ struct Layout {
     size_t f, xs, sx, sxy, partial, chords, ctrs, obs, tabs;
 };
 
-Layout layout_of(int model, int topo, int64_t N, int64_t R)
+// Ball and disk: one x-window array per chord half-width (one load per chord
+// instead of two) for radii of 5 and more, when the arrays fit the budget.
+// Measured on the 100^3 ball: 8% faster at P = 6 and 19% on 200^3 at P = 8;
+// at P <= 4 the extra x-pass writes cost as much as the loads they save.
+constexpr int64_t kWindowMinRadius = 5;
+bool lattice_wmode(int topo, int64_t N, int64_t R, unsigned flags)
+{
+    if (topo != SIM_BALL3D && topo != SIM_DISK2D) return false;
+    if ((flags & SIM_FLAG_LOW_MEMORY) || R < kWindowMinRadius) return false;
+    return (R + 1) * 16 * nodes_of(topo, N) <= kLatticeWindowBudget;
+}
+
+Layout layout_of(int model, int topo, int64_t N, int64_t R, unsigned flags = 0)
 {
     Layout L{};
     size_t o = 0;
@@ -129,7 +141,7 @@ Layout layout_of(int model, int topo, int64_t N, int64_t R)
         L.acc = take(sizeof(double) * d * n);
         L.f = take(sizeof(double) * 2 * n);
         L.xs = take(sizeof(double) * model_nx(model) * n);
-        L.sx = take(sizeof(int64_t) * lattice_sx_elems(topo, N, R));
+        L.sx = take(sizeof(int64_t) * lattice_sx_elems(topo, N, R, lattice_wmode(topo, N, R, flags)));
         L.sxy = take(topo == SIM_CUBE3D ? sizeof(int64_t) * 2 * n : 0);
         L.partial = take(sizeof(i128) * 2 * nblk);
         L.chords = take(topo == SIM_CUBE3D ? 0 : sizeof(int4) * (2 * R + 1) * (2 * R + 1));
@@ -321,7 +333,8 @@ static int create_impl(sim_t *out, int model, int topology, int64_t N, int64_t r
     if (!out) return fail(SIM_EINVAL, "out is NULL");
     *out = nullptr;
     if (const char *msg = validate(model, topology, N, radius, params, n_params)) return fail(SIM_EINVAL, msg);
-    if (flags & ~(SIM_FLAG_INCLUDE_SELF | SIM_FLAG_STREAMING)) return fail(SIM_EINVAL, "unknown flags");
+    if (flags & ~(SIM_FLAG_INCLUDE_SELF | SIM_FLAG_STREAMING | SIM_FLAG_LOW_MEMORY))
+        return fail(SIM_EINVAL, "unknown flags");
 
     sim_t h = new sim_handle();
     h->model = model;
@@ -332,7 +345,7 @@ static int create_impl(sim_t *out, int model, int topology, int64_t N, int64_t r
     h->nodes = nodes_of(topology, N);
     h->flags = flags;
     h->stream = static_cast<cudaStream_t>(stream);
-    h->L = layout_of(model, topology, N, radius);
+    h->L = layout_of(model, topology, N, radius, flags);
     h->bytes = h->L.total;
 
     cudaError_t e = cudaSuccess;
@@ -433,6 +446,7 @@ static int create_impl(sim_t *out, int model, int topology, int64_t N, int64_t r
         p.xs = reinterpret_cast<double *>(b + L.xs);
         p.sx = reinterpret_cast<int64_t *>(b + L.sx);
         p.rs = N + 2 * radius + 1;
+        p.wmode = lattice_wmode(topology, N, radius, flags) ? 1 : 0;
         p.sxy = reinterpret_cast<int64_t *>(b + L.sxy);
         p.partial = reinterpret_cast<i128 *>(b + L.partial);
         p.done_ctr = ticket;

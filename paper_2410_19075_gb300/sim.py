@@ -15,6 +15,7 @@ KS, FHN, HH, KSI = 0, 1, 2, 3
 RING, CUBE3D, BALL3D, DISK2D, GRAPH = 0, 1, 2, 3, 4
 FLAG_INCLUDE_SELF = 1
 FLAG_STREAMING = 2
+FLAG_LOW_MEMORY = 4
 DIM = {KS: 1, FHN: 2, HH: 4, KSI: 2}
 
 
@@ -52,10 +53,11 @@ class Network:
     """One network on the GPU: ``sim_create`` ... ``sim_destroy``."""
 
     def __init__(self, model: int, topology: int, N: int, radius: int, params, include_self: bool = False,
-                 stream=None, streaming: bool = False):
+                 stream=None, streaming: bool = False, low_memory: bool = False):
         p = np.ascontiguousarray(params, dtype=np.float64)
         h = ctypes.c_void_p()
-        flags = (FLAG_INCLUDE_SELF if include_self else 0) | (FLAG_STREAMING if streaming else 0)
+        flags = ((FLAG_INCLUDE_SELF if include_self else 0) | (FLAG_STREAMING if streaming else 0)
+                 | (FLAG_LOW_MEMORY if low_memory else 0))
         check(lib().sim_create(ctypes.byref(h), model, topology, int(N), int(radius),
                                p.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), p.size, flags,
                                _stream_ptr(stream)))

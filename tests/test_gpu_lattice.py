@@ -236,3 +236,24 @@ def test_largest_cube_plane_wave_closed_form():
         net.set_state(y0)
         k = net.rhs()
     assert np.abs(k - Om).max() < 1e-12
+
+
+@pytest.mark.parametrize("topo,N1,P,model", [(BALL, 13, 6, 3), (BALL, 20, 4, 0), (DISK, 67, 20, 3), (DISK, 40, 6, 0)])
+def test_window_arrays_and_row_prefixes_give_the_same_bits(topo, N1, P, model):
+    """The default gather (one x-window array per chord half-width) and the
+    low-memory one (row prefixes, two loads per chord) sum the same integers:
+    identical trajectories and order parameters, and the oracle's within tolerance."""
+    from paper_2410_19075_gb300 import Network
+    y0, _ = inputs_for(model, topo, N1, 800 + N1)
+    out = []
+    for low in (False, True):
+        with Network(model, topo, N1, P, PARAMS[model](), low_memory=low) as net:
+            net.set_state(y0)
+            net.step(60, 0.01)
+            k = net.rhs()
+            out.append((net.get_state(), net.observables(), k))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
+    assert np.array_equal(out[0][2], out[1][2])
+    ref, _ = oracle_run(model, topo, N1, P, PARAMS[model](), y0, 60, 0.01)
+    assert np.abs(out[1][0] - ref).max() <= STATE_TOL

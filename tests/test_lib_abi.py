@@ -55,9 +55,9 @@ def test_workspace_bytes(lib):
     assert workspace_bytes(1, 1, 10, 2) == 0  # cube is Kuramoto only
     assert workspace_bytes(2, 2, 10, 2) == 0  # so is the ball
     ball = workspace_bytes(3, 2, 100, 4)      # 3D Kuramoto with inertia, ball of radius 4
-    assert 0 < ball < 100 * 10 ** 6
+    assert 0 < ball < 100 * 10 ** 6           # P = 4: one row-prefix array
     disk = workspace_bytes(0, 3, 1000, 30)
-    assert 0 < disk < 100 * 10 ** 6
+    assert 0 < disk < 600 * 10 ** 6           # 31 window arrays (P = 30) of 16 MB
 
 
 @pytest.mark.parametrize("model,topo,N,R,params", [
