@@ -74,6 +74,123 @@ __device__ __forceinline__ void ring_stage_body(const RingPlan &P, const RingSta
     stage_body<M, STAGE>(P, a, h, sub, RingGather<NQ>{P, a.lam_in, s_bases});
 }
 
+// Two adjacent nodes per thread, 128 threads per 256-node sub-tile: two
+// independent right-hand sides per thread and one warp scan per node pair.  The
+// same integers and FP64 expressions as ring_stage_body, so the same bits.
+constexpr int kRing2Threads = kSubTile / 2;
+#ifndef SIM_RING2_MIN_BLOCKS
+#define SIM_RING2_MIN_BLOCKS 8
+#endif
+
+template <int M, int STAGE>
+__device__ __forceinline__ void ring_stage_body2(const RingPlan &P, const RingStageIO &a, const StepSize &h,
+                                                 int64_t sub)
+{
+    using Mo = Model<M>;
+    constexpr int D = Mo::D, NQ = Mo::NQ, NX = Mo::NX;
+    constexpr int XOFF = D - NX;
+    __shared__ RingBases<NQ> s_bases;
+    const int tid = threadIdx.x;
+    const int64_t N = P.N;
+    const int64_t i0 = sub * kSubTile + 2 * tid;
+    if (STAGE > 0) ring_compute_bases<NQ>(P, a.ingrp_in, a.grpofs_in, sub, s_bases);
+
+    int64_t l[NQ][2], lp[NQ], lb[NQ][2], la[NQ][2];
+    double yv[2][D], av[2][D], X[2][NX > 0 ? NX : 1], Iext[2] = {0.0, 0.0};
+    if (STAGE > 0) {
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int64_t i = i0 + u;
+            if (i < N) {
+                const int64_t b = i + P.R + 1, am = i - P.R;
+                const int64_t bp = b >= N ? b - N : b, ap = am < 0 ? am + N : am;
+#pragma unroll
+                for (int c = 0; c < NQ; ++c) {
+                    const int64_t *lam = a.lam_in + c * N;
+                    l[c][u] = __ldg(lam + i);
+                    if (u == 0) lp[c] = tid ? __ldg(lam + i - 1) : 0;
+                    lb[c][u] = (bp & (kSubTile - 1)) ? __ldg(lam + bp - 1) : 0;
+                    la[c][u] = (ap & (kSubTile - 1)) ? __ldg(lam + ap - 1) : 0;
+                }
+#pragma unroll
+                for (int v = 0; v < D; ++v) {
+                    yv[u][v] = P.y[v * N + i];
+                    av[u][v] = STAGE >= 2 ? P.acc[v * N + i] : 0.0;
+                }
+#pragma unroll
+                for (int g = 0; g < NX; ++g) X[u][g] = a.x_in[g * N + i];
+                if (M == 2 && P.node_param) Iext[u] = P.node_param[i];
+            }
+        }
+        __syncthreads();
+    }
+
+    int64_t qv[NQ][2];
+    bool ok = true;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const int64_t i = i0 + u;
+#pragma unroll
+        for (int c = 0; c < NQ; ++c) qv[c][u] = 0;
+        if (i >= N) continue;
+        double xn[D];
+        if (STAGE == 0) {
+#pragma unroll
+            for (int v = 0; v < D; ++v) xn[v] = P.y[v * N + i];
+        } else {
+            const int64_t b = i + P.R + 1, am = i - P.R;
+            const int kb = (b >= s_bases.start[0][1]) + (b >= s_bases.start[0][2]);
+            const int ka = (am >= s_bases.start[1][1]) + (am >= s_bases.start[1][2]);
+            int64_t qo[NQ];
+            double fo[NQ];
+            i128 W[NQ];
+#pragma unroll
+            for (int c = 0; c < NQ; ++c) {
+                qo[c] = l[c][u] - (u == 0 ? lp[c] : l[c][0]);
+                fo[c] = fixed_to_double(qo[c], P.F);
+                W[c] = (s_bases.base[0][kb][c] - s_bases.base[1][ka][c]) + (i128)(lb[c][u] - la[c][u]);
+            }
+            double k[D];
+            Mo::rhs(P.mp, P.F, fo, qo, W, X[u], Iext[u], k);
+#pragma unroll
+            for (int v = 0; v < D; ++v) {
+                if (STAGE == 1) {
+                    P.acc[v * N + i] = k[v];
+                    xn[v] = yv[u][v] + h.half * k[v];
+                } else if (STAGE == 2) {
+                    P.acc[v * N + i] = av[u][v] + 2.0 * k[v];
+                    xn[v] = yv[u][v] + h.half * k[v];
+                } else if (STAGE == 3) {
+                    P.acc[v * N + i] = av[u][v] + 2.0 * k[v];
+                    xn[v] = yv[u][v] + h.dt * k[v];
+                } else {
+                    const double yn = yv[u][v] + h.sixth * (av[u][v] + k[v]);
+                    P.y[v * N + i] = yn;
+                    xn[v] = yn;
+                }
+            }
+            if (NX > 0 && STAGE >= 1 && STAGE <= 3) {
+#pragma unroll
+                for (int g = 0; g < NX; ++g) a.x_out[g * N + i] = xn[XOFF + g];
+            }
+        }
+        double f[NQ];
+        Mo::coupled(P.mp, xn, f);
+#pragma unroll
+        for (int c = 0; c < NQ; ++c) qv[c][u] = to_fixed(f[c], P.F, P.lim, ok);
+    }
+    if (!ok) raise_error(P.err, ERR_RANGE);
+    ring_prefix_tail_n<NQ, 2, (M == 0 || M == 3) && (STAGE == 0 || STAGE == 4), STAGE == 4>(
+        P, a.lam_out, a.ingrp_out, a.grpofs_out, sub, i0, qv);
+}
+
+template <int M, int STAGE>
+__global__ void __launch_bounds__(kRing2Threads, SIM_RING2_MIN_BLOCKS)
+    ring_stage_kernel2(const RingPlan p, const StepSize h)
+{
+    ring_stage_body2<M, STAGE>(p, stage_io<M, STAGE>(p), h, blockIdx.x);
+}
+
 // Plain path: one ring, one sub-tile per CTA.
 template <int M, int STAGE>
 __global__ void __launch_bounds__(kRingThreads, MinBlocks<M>::value) ring_stage_kernel(const RingPlan p, const StepSize h)
@@ -96,10 +213,25 @@ __global__ void __launch_bounds__(kRingThreads, MinBlocks<M>::value)
     ring_stage_body<M, STAGE>(p, stage_io<M, STAGE>(p), h, (int64_t)blockIdx.x - item_base[inst]);
 }
 
+#ifndef SIM_RING_NPT
+#define SIM_RING_NPT 2
+#endif
+
 template <int M>
 static cudaError_t launch_stage(int stage, const RingPlan &p, double dt, cudaStream_t s)
 {
     const dim3 grid((unsigned)p.nsub), block(kRingThreads);
+    if (SIM_RING_NPT == 2 && M != 2) {
+        const dim3 block2(kRing2Threads);
+        switch (stage) {
+        case 0: ring_stage_kernel2<M, 0><<<grid, block2, 0, s>>>(p, step_size(dt)); break;
+        case 1: ring_stage_kernel2<M, 1><<<grid, block2, 0, s>>>(p, step_size(dt)); break;
+        case 2: ring_stage_kernel2<M, 2><<<grid, block2, 0, s>>>(p, step_size(dt)); break;
+        case 3: ring_stage_kernel2<M, 3><<<grid, block2, 0, s>>>(p, step_size(dt)); break;
+        default: ring_stage_kernel2<M, 4><<<grid, block2, 0, s>>>(p, step_size(dt)); break;
+        }
+        return cudaGetLastError();
+    }
     switch (stage) {
     case 0: ring_stage_kernel<M, 0><<<grid, block, 0, s>>>(p, step_size(dt)); break;
     case 1: ring_stage_kernel<M, 1><<<grid, block, 0, s>>>(p, step_size(dt)); break;

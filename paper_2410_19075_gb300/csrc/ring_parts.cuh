@@ -203,6 +203,91 @@ __device__ __forceinline__ void ring_prefix_tail(const RingPlan &P, int64_t *lam
     if (DEC_STEPS && tid == 0 && P.steps_left) *P.steps_left -= 1;
 }
 
+// As ring_prefix_tail, with NPT adjacent nodes per thread (kSubTile / NPT
+// threads per CTA): node i0 + u of the thread holds qv[c][u].
+template <int NQ, int NPT, bool RECORD, bool DEC_STEPS>
+__device__ __forceinline__ void ring_prefix_tail_n(const RingPlan &P, int64_t *lam_out, i128 *ingrp_out,
+                                                   i128 *grpofs_out, int64_t sub, int64_t i0,
+                                                   const int64_t (&qv)[NQ][NPT])
+{
+    constexpr int NW = kSubTile / NPT / 32;
+    __shared__ int64_t s_wtot[NW][NQ];
+    __shared__ int s_last;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t N = P.N, nsub = P.nsub, ngroups = P.ngroups;
+
+    // Exact inclusive prefix inside the sub-tile: the thread's running sums, a
+    // warp scan of the thread totals and the preceding warps' totals.
+    int64_t run[NQ][NPT], ex[NQ];
+#pragma unroll
+    for (int c = 0; c < NQ; ++c) {
+        run[c][0] = qv[c][0];
+#pragma unroll
+        for (int u = 1; u < NPT; ++u) run[c][u] = run[c][u - 1] + qv[c][u];
+        const int64_t incl = warp_incl_scan(run[c][NPT - 1]);
+        ex[c] = incl - run[c][NPT - 1];
+        if (lane == 31) s_wtot[warp][c] = incl;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < NQ; ++c) {
+        int64_t off = ex[c];
+        for (int w = 0; w < warp; ++w) off += s_wtot[w][c];
+#pragma unroll
+        for (int u = 0; u < NPT; ++u)
+            if (i0 + u < N) lam_out[c * N + i0 + u] = off + run[c][u];
+    }
+
+    // Level 1: the last CTA of each group of 64 sub-tiles scans the group.
+    const int64_t g = sub >> kGroupLog2, s0 = g << kGroupLog2;
+    const int64_t gsize = nsub - s0 < kGroup ? nsub - s0 : kGroup;
+    if (tid == 0) {
+#pragma unroll
+        for (int c = 0; c < NQ; ++c) {
+            int64_t t = 0;
+            for (int w = 0; w < NW; ++w) t += s_wtot[w][c];
+            P.subtot[c * nsub + sub] = t;
+        }
+        __threadfence();
+        s_last = last_arrival(P.grp_ctr + g, (unsigned long long)gsize);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    if (warp == 0) {
+#pragma unroll
+        for (int c = 0; c < NQ; ++c) {
+            const int64_t *st = P.subtot + c * nsub + s0;
+            const i128 v0 = 2 * lane < gsize ? (i128)__ldcg(st + 2 * lane) : (i128)0;
+            const i128 v1 = 2 * lane + 1 < gsize ? (i128)__ldcg(st + 2 * lane + 1) : (i128)0;
+            const i128 x = warp_incl_scan_i128(v0 + v1);
+            const i128 e = x - v0 - v1;
+            i128 *ig = ingrp_out + c * nsub + s0;
+            if (2 * lane < gsize) st_i128(ig + 2 * lane, e);
+            if (2 * lane + 1 < gsize) st_i128(ig + 2 * lane + 1, e + v0);
+            if (lane == 31) st_i128(P.grptot + c * ngroups + g, x);
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    if (tid == 0) s_last = last_arrival(P.top_ctr, (unsigned long long)ngroups);
+    __syncthreads();
+    if (!s_last) return;
+
+    // Level 2: the last group scans the group totals (and records the totals).
+    i128 total[NQ];
+#pragma unroll
+    for (int c = 0; c < NQ; ++c)
+        total[c] = block_exclusive_scan<8>(P.grptot + c * ngroups, grpofs_out + c * (ngroups + 1), ngroups);
+    if (RECORD && tid == 0 && P.obs) {
+        const double S = fixed_to_double(total[0], P.F);
+        const double C = fixed_to_double(total[NQ - 1], P.F);
+        const unsigned long long n = *P.obs_ctr;
+        P.obs[n % (unsigned long long)P.obs_cap] = sqrt(S * S + C * C) / (double)N;
+        *P.obs_ctr = n + 1;
+    }
+    if (DEC_STEPS && tid == 0 && P.steps_left) *P.steps_left -= 1;
+}
+
 // Buffers one stage reads and writes (chosen by the stage's parity).
 struct RingStageIO {
     const int64_t *lam_in;
