@@ -213,6 +213,18 @@ __global__ void __launch_bounds__(kRingThreads, MinBlocks<M>::value)
     ring_stage_body<M, STAGE>(p, stage_io<M, STAGE>(p), h, (int64_t)blockIdx.x - item_base[inst]);
 }
 
+// The same with two adjacent nodes per thread (ring_stage_body2).
+template <int M, int STAGE>
+__global__ void __launch_bounds__(kRing2Threads, SIM_RING2_MIN_BLOCKS)
+    ring_batch_stage_kernel2(const RingPlan *__restrict__ plans, const int *__restrict__ inst_of_item,
+                             const int64_t *__restrict__ item_base, const StepSize h)
+{
+    const int inst = inst_of_item[blockIdx.x];
+    const RingPlan &p = plans[inst];
+    if (p.steps_left && *(volatile long long *)p.steps_left <= 0) return;
+    ring_stage_body2<M, STAGE>(p, stage_io<M, STAGE>(p), h, (int64_t)blockIdx.x - item_base[inst]);
+}
+
 #ifndef SIM_RING_NPT
 #define SIM_RING_NPT 2
 #endif
@@ -221,7 +233,7 @@ template <int M>
 static cudaError_t launch_stage(int stage, const RingPlan &p, double dt, cudaStream_t s)
 {
     const dim3 grid((unsigned)p.nsub), block(kRingThreads);
-    if (SIM_RING_NPT == 2 && M != 2) {
+    if constexpr (SIM_RING_NPT == 2 && M != 2) {
         const dim3 block2(kRing2Threads);
         switch (stage) {
         case 0: ring_stage_kernel2<M, 0><<<grid, block2, 0, s>>>(p, step_size(dt)); break;
@@ -256,11 +268,22 @@ template <int M>
 static cudaError_t launch_batch_stage(int stage, const RingBatchGroup &g, double dt, cudaStream_t s)
 {
     const dim3 grid((unsigned)g.n_items), block(kRingThreads);
+    const StepSize h = step_size(dt);
+    if constexpr (SIM_RING_NPT == 2 && M != 2) {
+        const dim3 block2(kRing2Threads);
+        switch (stage) {
+        case 1: ring_batch_stage_kernel2<M, 1><<<grid, block2, 0, s>>>(g.plans, g.inst_of_item, g.item_base, h); break;
+        case 2: ring_batch_stage_kernel2<M, 2><<<grid, block2, 0, s>>>(g.plans, g.inst_of_item, g.item_base, h); break;
+        case 3: ring_batch_stage_kernel2<M, 3><<<grid, block2, 0, s>>>(g.plans, g.inst_of_item, g.item_base, h); break;
+        default: ring_batch_stage_kernel2<M, 4><<<grid, block2, 0, s>>>(g.plans, g.inst_of_item, g.item_base, h); break;
+        }
+        return cudaGetLastError();
+    }
     switch (stage) {
-    case 1: ring_batch_stage_kernel<M, 1><<<grid, block, 0, s>>>(g.plans, g.inst_of_item, g.item_base, step_size(dt)); break;
-    case 2: ring_batch_stage_kernel<M, 2><<<grid, block, 0, s>>>(g.plans, g.inst_of_item, g.item_base, step_size(dt)); break;
-    case 3: ring_batch_stage_kernel<M, 3><<<grid, block, 0, s>>>(g.plans, g.inst_of_item, g.item_base, step_size(dt)); break;
-    default: ring_batch_stage_kernel<M, 4><<<grid, block, 0, s>>>(g.plans, g.inst_of_item, g.item_base, step_size(dt)); break;
+    case 1: ring_batch_stage_kernel<M, 1><<<grid, block, 0, s>>>(g.plans, g.inst_of_item, g.item_base, h); break;
+    case 2: ring_batch_stage_kernel<M, 2><<<grid, block, 0, s>>>(g.plans, g.inst_of_item, g.item_base, h); break;
+    case 3: ring_batch_stage_kernel<M, 3><<<grid, block, 0, s>>>(g.plans, g.inst_of_item, g.item_base, h); break;
+    default: ring_batch_stage_kernel<M, 4><<<grid, block, 0, s>>>(g.plans, g.inst_of_item, g.item_base, h); break;
     }
     return cudaGetLastError();
 }
