@@ -18,7 +18,7 @@ def _jobs(n, seed, scale):
 
 
 def _init(job):
-    n = job.N ** 3 if job.topo == 1 else job.N
+    n = job.N ** 3 if job.topo in (1, 2) else job.N * job.N if job.topo == 3 else job.N
     return I.initial_state(job.model, job.seed, job.job_id + 1, n)
 
 
@@ -81,6 +81,28 @@ def test_every_model_served_alongside_others():
     # and one of them against the oracle
     job = specs[0]
     ref, ref_order = oracle.rk4(0, 0, job.N, job.R, job.params, inits[0], job.n_steps, 0.01, record_order=True)
+    assert np.abs(served[0][0] - ref).max() <= STATE_TOL
+    assert np.abs(served[0][1] - ref_order).max() <= ORDER_TOL
+
+
+def test_inertia_model_and_ball_disk_lattices_served():
+    """Jobs of the paper's 3D inertia model on the ball, a Kuramoto disk, an
+    inertia ring and a cube, served together: each equals its solo run bit for
+    bit, and the ball job matches the oracle."""
+    from paper_2410_19075_gb300 import inputs as Ii
+    specs = [Ii.Job(0, 0.0, 3, 2, 10, 2, Ii.ksi_params(mu=1.0), 40, 6),
+             Ii.Job(1, 0.0, 0, 3, 40, 6, Ii.ks_params(alpha=1.3), 50, 6),
+             Ii.Job(2, 0.0, 3, 0, 1500, 400, Ii.ksi_params(), 70, 6),
+             Ii.Job(3, 0.0, 3, 1, 9, 2, Ii.ksi_params(mu=0.5), 30, 6)]
+    inits = [_init(j) for j in specs]
+    served, stats = _serve(specs, inits, chunk=9)
+    assert stats["completed"] == len(specs)
+    for job, y0 in zip(specs, inits):
+        ya, oa = _alone(job, y0)
+        assert np.array_equal(served[job.job_id][0], ya), (job.model, job.topo)
+        assert np.array_equal(served[job.job_id][1], oa), (job.model, job.topo)
+    job = specs[0]
+    ref, ref_order = oracle.rk4(3, 2, job.N, job.R, job.params, inits[0], job.n_steps, 0.01, record_order=True)
     assert np.abs(served[0][0] - ref).max() <= STATE_TOL
     assert np.abs(served[0][1] - ref_order).max() <= ORDER_TOL
 
