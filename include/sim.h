@@ -194,7 +194,8 @@ int64_t sim_steps_done(sim_t h);
  * Adaptive Dormand-Prince 5(4) (Section III.A: the paper's default solver is a
  * Dormand-Prince method with step-size control; Section V: the solution is
  * interpolated for dense output and synchronisation is analysed at every
- * output).  Ring networks only (every model).
+ * output).  Rings (every model) and the cube, ball and disk lattices (the
+ * Kuramoto models); not link matrices.
  *
  * Method: the RK5(4)7M pair of Dormand and Prince (1980), first same as last
  * (six right-hand sides per attempted step).  Error of an attempt of size h:
@@ -227,10 +228,12 @@ typedef struct {
     int status;     /* SIM_OK, SIM_ESTEPS or SIM_ESMALL */
 } sim_dp5_stats;
 
-/* One ring network.  Returns SIM_OK, the run's SIM_ESTEPS / SIM_ESMALL (the state
- * is then that of the last accepted step, stats->t), SIM_EINVAL (not a ring,
+/* One network.  Returns SIM_OK, the run's SIM_ESTEPS / SIM_ESMALL (the state is
+ * then that of the last accepted step, stats->t), SIM_EINVAL (a link matrix,
  * invalid options), SIM_ENOMEM, or a device error.  stats may be NULL.
- * Synchronises the handle's stream. */
+ * Synchronises the handle's stream.  A lattice run evaluates each stage with
+ * the lattice's own kernels (stage input, x pass, gather); a ring run with the
+ * fused ring stage kernels. */
 int sim_dp5(sim_t h, const sim_dp5_opts *opts, sim_dp5_stats *stats);
 
 /* ---------------------------------------------------------------------------
@@ -261,7 +264,7 @@ int sim_batch_set_budgets(sim_batch_t b, const int64_t *steps);
  * graphs of 16 steps).  sim_steps_done() of each member is updated. */
 int sim_batch_step(sim_batch_t b, int64_t n_steps, double dt);
 
-/* Dormand-Prince runs of every member (all must be rings), each with its own
+/* Dormand-Prince runs of every member (rings and lattices), each with its own
  * options opts[i], tolerances, step sizes and decisions; every attempt of every
  * unfinished member is one set of launches per model group.  stats[i] gets each
  * member's outcome (status SIM_OK, SIM_ESTEPS or SIM_ESMALL).  Returns SIM_OK

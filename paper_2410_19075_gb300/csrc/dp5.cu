@@ -26,27 +26,10 @@
 // An instance that is done skips every kernel whole (its arrival counters stay
 // consistent); accepting swaps the roles of the two state buffers and of the
 // two first-stage buffers instead of copying.
+#include "dp_control.cuh"
 #include "ring_parts.cuh"
 
 namespace simk {
-
-// Dormand and Prince (1980), the RK5(4)7M pair.  Row s (0-based stage) holds the
-// weights of k_1..k_s in the input of stage s + 1; row 6 is the fifth-order
-// solution.  c_dp_e = b - bhat (b the fifth-order weights, bhat the embedded
-// fourth-order ones).
-__constant__ double c_dp_a[7][6] = {
-    {0, 0, 0, 0, 0, 0},
-    {1.0 / 5.0, 0, 0, 0, 0, 0},
-    {3.0 / 40.0, 9.0 / 40.0, 0, 0, 0, 0},
-    {44.0 / 45.0, -56.0 / 15.0, 32.0 / 9.0, 0, 0, 0},
-    {19372.0 / 6561.0, -25360.0 / 2187.0, 64448.0 / 6561.0, -212.0 / 729.0, 0, 0},
-    {9017.0 / 3168.0, -355.0 / 33.0, 46732.0 / 5247.0, 49.0 / 176.0, -5103.0 / 18656.0, 0},
-    {35.0 / 384.0, 0.0, 500.0 / 1113.0, 125.0 / 192.0, -2187.0 / 6784.0, 11.0 / 84.0}};
-__constant__ double c_dp_e[7] = {71.0 / 57600.0, 0.0, -71.0 / 16695.0, 71.0 / 1920.0, -17253.0 / 339200.0,
-                                 22.0 / 525.0, -1.0 / 40.0};
-
-// Step-size controller: safety factor, smallest and largest factor per step.
-constexpr double kDpSafe = 0.9, kDpFacMin = 0.2, kDpFacMax = 10.0;
 
 template <int M> struct DpMinBlocks { static constexpr int value = 4; };
 template <> struct DpMinBlocks<2> { static constexpr int value = 2; };
@@ -63,60 +46,6 @@ __device__ __forceinline__ long long warp_sum_i64(long long v)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
-}
-
-// The decision of one attempt (one thread of the instance's last CTA).
-__device__ void dp_decide(const DpPlan &Q, double esum, int n_here, const i128 (*out_tot)[2])
-{
-    const RingPlan &P = Q.r;
-    const int D = P.model == 2 ? 4 : (P.model == 0 ? 1 : 2);
-    DpCtl c = *Q.ctl;
-    // an attempt whose stage inputs left the fixed-point range is rejected like
-    // one whose error is not finite
-    const double err = c.bad ? INFINITY : sqrt(esum / (double)(D * P.N));
-    c.bad = 0;
-    double fac = !isfinite(err) ? kDpFacMin : err > 0.0 ? kDpSafe * pow(err, -0.2) : kDpFacMax;
-    fac = fac < kDpFacMin ? kDpFacMin : (fac > kDpFacMax ? kDpFacMax : fac);
-    if (err <= 1.0) {
-        for (int o = 0; o < n_here && P.obs; ++o) {
-            const double S = fixed_to_double(out_tot[o][0], P.F), C = fixed_to_double(out_tot[o][1], P.F);
-            const unsigned long long n = *P.obs_ctr;
-            P.obs[n % (unsigned long long)P.obs_cap] = sqrt(S * S + C * C) / (double)P.N;
-            *P.obs_ctr = n + 1;
-        }
-        c.next_out += n_here;
-        c.cur ^= 1;
-        ++c.n_acc;
-        double hn = c.h * fac;
-        if (c.last_rej && hn > c.h) hn = c.h;
-        c.h = hn < c.hcap ? hn : c.hcap;
-        c.last_rej = 0;
-        if (c.last) {
-            c.t = c.t_end;
-            c.done = 1;
-        } else {
-            c.t = c.t + c.h_att;
-        }
-    } else {
-        ++c.n_rej;
-        c.h = c.h_att * fac;
-        c.last_rej = 1;
-    }
-    if (!c.done) {
-        if (c.n_acc + c.n_rej >= c.max_att) {
-            c.done = 1;
-            c.status = kDpStatusSteps;
-        } else {
-            c.last = c.t_end - c.t <= c.h;
-            c.h_att = c.last ? c.t_end - c.t : c.h;
-            if (!(c.h_att > 1e-14 * (fabs(c.t) + c.h_att))) {
-                c.done = 1;
-                c.status = kDpStatusSmall;
-            }
-        }
-    }
-    *Q.ctl = c;
-    if (c.done) atomicSub(Q.remaining, 1);
 }
 
 template <int M, int DS>
@@ -338,7 +267,9 @@ __global__ void __launch_bounds__(kRingThreads, DpMinBlocks<M>::value)
     if (tid == 0) {
         double tot = 0.0;
         for (int w = 0; w < NW; ++w) tot += s_err[w];
-        dp_decide(Q, tot, n_here, s_out);
+        const int D = P.model == 2 ? 4 : (P.model == 0 ? 1 : 2);
+        dp_decide_ctl(Q.ctl, Q.remaining, tot, (int64_t)D * P.N, n_here, s_out,
+                      DpRecord{P.obs, P.obs_cap, P.obs_ctr, P.F, P.N});
     }
 }
 

@@ -96,6 +96,7 @@ struct DpCtl {
     int done;      // 1: finished (t_end reached or status set)
     int status;    // 0, or the sim_status that ended the run
     int bad;       // a stage input of the current attempt left the fixed-point range
+    int acc_flag;  // the last decided attempt was accepted
 };
 
 struct DpPlan {
@@ -164,7 +165,26 @@ struct LatticePlan {
     unsigned long long *obs_ctr;
     const int4 *chords; // ball/disk: (dy, dz, w, 0) chords of the window
     int nchords;
+    const int *skip;    // if set and nonzero, the x, y and gather passes of stage 1 return at once
+                        // (a finished Dormand-Prince run); nullptr for every other use
 };
+
+// Adaptive Dormand-Prince 5(4) on a lattice (lattice_dp.cu): the lattice
+// right-hand side evaluates each stage (x pass, gather) from a stage-input buffer.
+struct LatDpPlan {
+    LatticePlan rhs;   // the network's plan with y = xbuf and skip = &ctl->done; acc set per stage
+    int model;         // 0 or 3
+    int64_t nodes, nblk; // nodes; CTAs of the elementwise kernels (256 nodes each)
+    double *y, *y5, *xbuf;
+    double *k[8];      // k[1..7]: the stage slopes (k[1] = f(y_n) kept from the last accepted step)
+    DpCtl *ctl;
+    int *remaining;
+    double *err_part;  // nblk
+    i128 *out_part;    // nblk * kDpMaxOut * 2
+    unsigned long long *dp_ctr;
+};
+cudaError_t lat_dp_start(const LatDpPlan &d, cudaStream_t s);   // k1 = f(y_n)
+cudaError_t lat_dp_attempt(const LatDpPlan &d, cudaStream_t s); // one attempted step
 
 cudaError_t lattice_configure(); // once per process, before the first launch
 int64_t lattice_order_blocks(int topo, int64_t N1); // CTAs of the order-parameter passes

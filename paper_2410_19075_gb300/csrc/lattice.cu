@@ -49,6 +49,7 @@ static int row_warps(int64_t N1)
 template <int MODE>
 __global__ void __launch_bounds__(32 * kRowWarpsMax) lattice_x_kernel(LatticePlan p)
 {
+    if (p.skip && *(const volatile int *)p.skip) return;
     extern __shared__ int64_t smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     const int64_t N1 = p.N1, P = p.P, nodes = p.nodes, stride = N1 + 1, rows = nodes / N1;
@@ -155,6 +156,7 @@ __global__ void __launch_bounds__(32 * kRowWarpsMax) lattice_x_kernel(LatticePla
 // 8 rows of window loads issued together.
 __global__ void __launch_bounds__(kColThreads) cube_y_kernel(LatticePlan p)
 {
+    if (p.skip && *(const volatile int *)p.skip) return;
     constexpr int U = 8;
     const int64_t N1 = p.N1, P = p.P, nodes = p.nodes;
     const int64_t i = (int64_t)blockIdx.x * kColThreads + threadIdx.x;
@@ -249,9 +251,11 @@ __device__ void lattice_record_order(const LatticePlan &p, i128 ps, i128 pc)
             tc += s_wc[w];
         }
         const double S = fixed_to_double(ts, p.F), C = fixed_to_double(tc, p.F);
-        const unsigned long long n = *p.obs_ctr;
-        p.obs[n % (unsigned long long)p.obs_cap] = sqrt(S * S + C * C) / (double)p.nodes;
-        *p.obs_ctr = n + 1;
+        if (p.obs) {
+            const unsigned long long n = *p.obs_ctr;
+            p.obs[n % (unsigned long long)p.obs_cap] = sqrt(S * S + C * C) / (double)p.nodes;
+            *p.obs_ctr = n + 1;
+        }
     }
 }
 
@@ -314,6 +318,7 @@ __device__ __forceinline__ void lattice_node(const LatticePlan &p, int64_t n, in
 template <int M, int STAGE>
 __global__ void __launch_bounds__(kColThreads) cube_z_kernel(LatticePlan p, const StepSize h)
 {
+    if (STAGE == 1 && p.skip && *(const volatile int *)p.skip) return; // stage 1 records nothing
     const int64_t N1 = p.N1, P = p.P, nodes = p.nodes, plane = N1 * N1;
     const int64_t i = (int64_t)blockIdx.x * kColThreads + threadIdx.x;
     const int64_t j = blockIdx.y;
@@ -354,6 +359,7 @@ __global__ void __launch_bounds__(kColThreads) cube_z_kernel(LatticePlan p, cons
 template <int M, int STAGE, bool WMODE>
 __global__ void __launch_bounds__(kGatherThreads) lattice_gather_kernel(LatticePlan p, const StepSize h)
 {
+    if (STAGE == 1 && p.skip && *(const volatile int *)p.skip) return; // stage 1 records nothing
     const int64_t N1 = p.N1, nodes = p.nodes;
     const int64_t n = (int64_t)blockIdx.x * kGatherThreads + threadIdx.x;
     i128 ps = 0, pc = 0;

@@ -200,6 +200,8 @@ struct sim_handle {
     std::map<std::pair<double, int>, cudaGraphExec_t> graphs;
     void *dp_block = nullptr;             // Dormand-Prince buffers (allocated on first use)
     DpPlan dp{};
+    void *ldp_block = nullptr;            // lattice Dormand-Prince buffers (allocated on first use)
+    LatDpPlan ldp{};
     void *graph_block = nullptr;          // compressed link matrix (general topology)
     GraphPlan graph{};
     int64_t graph_entries = 0;            // difference-table entries
@@ -1109,6 +1111,7 @@ void sim_destroy(sim_t h)
     for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
     if (h->dp_block) cudaFree(h->dp_block);
     if (h->graph_block) cudaFree(h->graph_block);
+    if (h->ldp_block) cudaFree(h->ldp_block);
     if (h->block && h->owns_block) cudaFree(h->block);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     delete h;
@@ -1133,7 +1136,7 @@ int64_t dp_n_out(double t0, double t_end, double out_dt)
 
 const char *dp_check(sim_t h, const sim_dp5_opts &o)
 {
-    if (h->topo != SIM_RING) return "Dormand-Prince runs take ring networks";
+    if (h->topo == SIM_GRAPH) return "Dormand-Prince runs take ring and lattice networks";
     const double v[] = {o.t0, o.t_end, o.rtol, o.atol, o.h0, o.h_max, o.out_dt};
     for (double x : v)
         if (!std::isfinite(x)) return "non-finite option";
@@ -1183,6 +1186,47 @@ int dp_ensure(sim_t h)
     return SIM_OK;
 }
 
+int ldp_ensure(sim_t h)
+{
+    if (h->ldp_block) return SIM_OK;
+    const int64_t n = (int64_t)h->d * h->nodes, nblk = (h->nodes + 255) / 256;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off += align_up(bytes);
+        return o;
+    };
+    const size_t oy5 = take(sizeof(double) * n), ox = take(sizeof(double) * n);
+    size_t ok[8] = {};
+    for (int j = 1; j <= 7; ++j)
+        if (j != 2) ok[j] = take(sizeof(double) * n);
+    const size_t oerr = take(sizeof(double) * nblk);
+    const size_t oout = take(sizeof(i128) * nblk * kDpMaxOut * 2);
+    const size_t octr = take(sizeof(unsigned long long));
+    cudaError_t e = cudaMalloc(&h->ldp_block, off);
+    if (e != cudaSuccess) {
+        h->ldp_block = nullptr;
+        return fail(SIM_ENOMEM, "device allocation of the Dormand-Prince buffers failed");
+    }
+    char *b = static_cast<char *>(h->ldp_block);
+    e = cudaMemsetAsync(b + octr, 0, sizeof(unsigned long long), h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "Dormand-Prince set-up");
+    LatDpPlan &Q = h->ldp;
+    Q.model = h->model;
+    Q.nodes = h->nodes;
+    Q.nblk = nblk;
+    Q.y = h->lat.y;
+    Q.y5 = reinterpret_cast<double *>(b + oy5);
+    Q.xbuf = reinterpret_cast<double *>(b + ox);
+    Q.k[0] = nullptr;
+    for (int j = 1; j <= 7; ++j) Q.k[j] = j == 2 ? h->lat.acc : reinterpret_cast<double *>(b + ok[j]);
+    Q.err_part = reinterpret_cast<double *>(b + oerr);
+    Q.out_part = reinterpret_cast<i128 *>(b + oout);
+    Q.dp_ctr = reinterpret_cast<unsigned long long *>(b + octr);
+    return SIM_OK;
+}
+
 // Integrate every member from its opts.t0 to opts.t_end on stream s.  Returns a
 // machinery or device status; per-member outcomes are in stats.
 int dp_run(const std::vector<sim_t> &mem, const sim_dp5_opts *opts, sim_dp5_stats *stats, cudaStream_t s)
@@ -1191,9 +1235,14 @@ int dp_run(const std::vector<sim_t> &mem, const sim_dp5_opts *opts, sim_dp5_stat
     for (int i = 0; i < n; ++i)
         if (const char *why = dp_check(mem[i], opts[i])) return fail(SIM_EINVAL, why);
     for (int i = 0; i < n; ++i) {
+        if (mem[i]->topo != SIM_RING) {
+            const int st = ldp_ensure(mem[i]);
+            if (st != SIM_OK) return st;
+            continue;
+        }
         const int st = dp_ensure(mem[i]);
         if (st != SIM_OK) return st;
-        mem[i]->dp.r = mem[i]->ring;
+        mem[i]->dp.r = mem[i]->ring; // picks up a node parameter set since the last run
         mem[i]->dp.r.steps_left = nullptr;
     }
     // Step control of every member, and the first attempt.
@@ -1226,7 +1275,11 @@ int dp_run(const std::vector<sim_t> &mem, const sim_dp5_opts *opts, sim_dp5_stat
     // Device tables of the run: plans, work items per model group, control
     // words, the members' error words and the counter of unfinished members.
     std::vector<std::vector<int>> by_model(4);
-    for (int i = 0; i < n; ++i) by_model[mem[i]->model].push_back(i);
+    std::vector<int> lat_members;
+    for (int i = 0; i < n; ++i) {
+        if (mem[i]->topo == SIM_RING) by_model[mem[i]->model].push_back(i);
+        else lat_members.push_back(i);
+    }
     std::vector<DpPlan> plans;
     std::vector<int> inst_of_item, plan_member;
     std::vector<int64_t> item_base;
@@ -1265,6 +1318,16 @@ int dp_run(const std::vector<sim_t> &mem, const sim_dp5_opts *opts, sim_dp5_stat
         plans[q].remaining = d_rem;
         plans[q].ctl = d_ctl + plan_member[q];
     }
+    std::vector<LatDpPlan> lplans;
+    for (int i : lat_members) {
+        LatDpPlan q = mem[i]->ldp;
+        q.rhs = mem[i]->lat;
+        q.rhs.y = q.xbuf;
+        q.rhs.skip = &(d_ctl + i)->done;
+        q.ctl = d_ctl + i;
+        q.remaining = d_rem;
+        lplans.push_back(q);
+    }
     std::vector<DpGroup> groups;
     for (const Span &sp : spans)
         groups.push_back(DpGroup{sp.model, sp.n_inst, sp.n_items,
@@ -1296,6 +1359,10 @@ int dp_run(const std::vector<sim_t> &mem, const sim_dp5_opts *opts, sim_dp5_stat
     for (int ds : {8, 1})
         for (const DpGroup &g : groups)
             if (e == cudaSuccess) e = dp_launch(ds, g, s);
+    for (size_t q = 0; q < lplans.size() && e == cudaSuccess; ++q) {
+        e = lattice_prologue(mem[lat_members[q]]->lat, s);
+        if (e == cudaSuccess) e = lat_dp_start(lplans[q], s);
+    }
     if (e != cudaSuccess) return finish(cuda_fail(e, "Dormand-Prince start"));
     // Attempts in captured graphs until every member is done.
     if (remaining > 0) {
@@ -1303,10 +1370,13 @@ int dp_run(const std::vector<sim_t> &mem, const sim_dp5_opts *opts, sim_dp5_stat
         if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return finish(cuda_fail(e, "Dormand-Prince capture"));
         cudaError_t le = cudaSuccess;
-        for (int a = 0; a < kDpGraphAttempts && le == cudaSuccess; ++a)
+        for (int a = 0; a < kDpGraphAttempts && le == cudaSuccess; ++a) {
             for (int ds : {2, 3, 4, 5, 6, 7, 0})
                 for (const DpGroup &g : groups)
                     if (le == cudaSuccess) le = dp_launch(ds, g, cap);
+            for (const LatDpPlan &q : lplans)
+                if (le == cudaSuccess) le = lat_dp_attempt(q, cap);
+        }
         cudaGraph_t graph = nullptr;
         e = cudaStreamEndCapture(cap, &graph);
         if (le != cudaSuccess || e != cudaSuccess) {
@@ -1332,6 +1402,11 @@ int dp_run(const std::vector<sim_t> &mem, const sim_dp5_opts *opts, sim_dp5_stat
     // path, the control words and the OR of the members' error words.
     for (const DpGroup &g : groups)
         if (e == cudaSuccess) e = dp_launch(9, g, s);
+    for (int i : lat_members) { // (sin, cos) of y for the RK4 kernels, without recording R
+        LatticePlan quiet = mem[i]->lat;
+        quiet.obs = nullptr;
+        if (e == cudaSuccess) e = lattice_prologue(quiet, s);
+    }
     if (e == cudaSuccess) {
         batch_error_kernel<<<1, 256, 0, s>>>(reinterpret_cast<unsigned *const *>(tb + o_errs), n, d_eout);
         e = cudaGetLastError();

@@ -162,19 +162,100 @@ def test_dp5_full_size_fhn_ring_agrees_with_rk4():
     assert np.abs(k[:, q] - ref).max() < 1e-12
 
 
-def test_dp5_rejects_lattices_and_bad_options():
+def test_dp5_rejects_link_matrices_and_bad_options():
     from paper_2410_19075_gb300 import Network
     from paper_2410_19075_gb300._lib import SimError
-    with Network(0, 2, 8, 2, I.ks_params()) as net:
-        net.set_state(I.ks_phases(1, 0, 512))
-        with pytest.raises(SimError):
-            net.dp5(t_end=1.0, rtol=1e-8, atol=1e-8, h0=0.01)
+    rp = np.array([0, 1, 2, 3], dtype=np.int64)
+    net = Network.from_links(0, 3, rp, np.array([1, 2, 0]), I.ks_params())
+    with pytest.raises(SimError):
+        net.dp5(t_end=1.0, rtol=1e-8, atol=1e-8, h0=0.01)
+    net.close()
     with Network(0, 0, 100, 10, I.ks_params()) as net:
         net.set_state(I.ks_phases(1, 0, 100))
         for bad in (dict(t_end=0.0, rtol=1e-8, atol=1e-8, h0=0.01), dict(t_end=1.0, rtol=0, atol=0, h0=0.01),
                     dict(t_end=1.0, rtol=1e-8, atol=1e-8, h0=0.0)):
             with pytest.raises(SimError):
                 net.dp5(**bad)
+
+
+def _check_lattice(model, topo, N1, seed, P, t_end, tol, h0, out_dt=0.0, params=None):
+    from paper_2410_19075_gb300 import Network
+    params = PARAMS[model]() if params is None else params
+    y0, _ = inputs_for(model, topo, N1, seed)
+    with Network(model, topo, N1, P, params) as net:
+        net.set_state(y0)
+        net.observables()
+        st = net.dp5(t_end=t_end, rtol=tol, atol=tol, h0=h0, out_dt=out_dt)
+        y, order = net.get_state(), net.observables()
+    ref, ref_order, ref_st = oracle.dp5(model, topo, N1, P, params, y0, 0.0, t_end, tol, tol, h0, out_dt=out_dt)
+    assert (st["accepted"], st["rejected"], st["status"]) == (ref_st["accepted"], ref_st["rejected"],
+                                                              ref_st["status"])
+    assert st["t"] == ref_st["t"]
+    assert np.abs(y - ref).max() <= STATE_TOL
+    assert order.size == ref_order.size
+    assert np.abs(order - ref_order).max() <= ORDER_TOL
+    return st
+
+
+@pytest.mark.parametrize("model,topo,N1,P", [(3, 2, 10, 2), (0, 2, 9, 3), (3, 1, 8, 2), (0, 1, 9, 2),
+                                             (0, 3, 30, 5), (3, 3, 40, 7), (3, 2, 13, 6)])
+def test_dp5_lattices_match_oracle(model, topo, N1, P):
+    """Dormand-Prince on the cube, ball and disk (both Kuramoto models, window
+    arrays at P >= 5 and row prefixes below) against the oracle's dp5."""
+    params = I.ksi_params(mu=1.0) if model == 3 else I.ks_params(omega=0.2, alpha=1.3)
+    st = _check_lattice(model, topo, N1, 60 + N1 + P, P, 4.0, 1e-9, 0.01, out_dt=0.5, params=params)
+    assert st["accepted"] > 3
+
+
+def test_dp5_paper_performance_network_agrees_with_rk4():
+    """The paper's performance test: Kuramoto with inertia on the 100^3 ball,
+    P = 2, mu = 0.01, alpha = 0.45 - Dormand-Prince at 1e-10 against RK4 at
+    dt = 0.002 to t = 2."""
+    from paper_2410_19075_gb300 import Network
+    y0 = I.ksi_state(2413, 0, 10 ** 6)
+    with Network(3, 2, 100, 2, I.ksi_params()) as net:
+        net.set_state(y0)
+        st = net.dp5(t_end=2.0, rtol=1e-10, atol=1e-10, h0=0.01)
+        a = net.get_state()
+        net.set_state(y0)
+        net.step(1000, 0.002)
+        b = net.get_state()
+    assert st["status"] == 0 and st["t"] == 2.0
+    assert np.abs(a - b).max() < 1e-8
+
+
+def test_batch_dp5_rings_and_lattices_equal_solo_runs():
+    from paper_2410_19075_gb300 import Batch, Network
+    cases = [(3, 2, 10, 2, dict(t_end=3.0, rtol=1e-9, atol=1e-9, h0=0.01, out_dt=0.5)),
+             (0, 0, 800, 200, dict(t_end=4.0, rtol=1e-8, atol=1e-8, h0=0.05, out_dt=1.0)),
+             (0, 3, 30, 5, dict(t_end=2.0, rtol=1e-10, atol=1e-10, h0=0.01)),
+             (3, 1, 8, 2, dict(t_end=5.0, rtol=1e-8, atol=1e-8, h0=0.1, max_attempts=7))]
+
+    def make(model, topo, N, R, seed):
+        params = I.ksi_params(mu=1.0) if model == 3 else I.ks_params()
+        y0, _ = inputs_for(model, topo, N, seed)
+        net = Network(model, topo, N, R, params)
+        net.set_state(y0)
+        net.observables()
+        return net
+
+    solo = []
+    for idx, (model, topo, N, R, o) in enumerate(cases):
+        net = make(model, topo, N, R, 900 + idx)
+        st = net.dp5(**o)
+        solo.append((net.get_state(), net.observables(), st))
+        net.close()
+    nets = [make(model, topo, N, R, 900 + idx) for idx, (model, topo, N, R, _) in enumerate(cases)]
+    try:
+        with Batch(nets) as b:
+            stats = b.dp5([o for *_, o in cases])
+        for net, (y, order, st), bst in zip(nets, solo, stats):
+            assert bst == st
+            assert np.array_equal(net.get_state(), y)
+            assert np.array_equal(net.observables(), order)
+    finally:
+        for net in nets:
+            net.close()
 
 
 def test_dp5_several_prefix_groups():
