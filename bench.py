@@ -481,6 +481,34 @@ def bench_lattice(args, stream, flush, model, topo, N1, P, params, steps=100):
             "hbm_gbs_algorithmic": per_byte * nodes * steps / (ms * 1e-3) / 1e9}
 
 
+def bench_ball_dp5(args, t_end=100.0, tol=1e-10):
+    """The paper's performance test as the paper runs it: the 100^3 ball with
+    inertia (Fig. 6c parameters) integrated by adaptive Dormand-Prince 5(4) over
+    100 time units (the span of its timing comparison, Section V) at
+    rtol = atol = tol, P = 2, 4, 6; wall time of one sim_dp5 call."""
+    import torch
+    from paper_2410_19075_gb300 import Network
+    out = []
+    n = 100 ** 3
+    y0 = torch.from_numpy(I.ksi_state(2413, 0, n)).cuda()
+    for P in (2, 4, 6):
+        with Network(3, 2, 100, P, I.ksi_params()) as net:
+            net.set_state(y0)
+            net.dp5(t_end=0.5, rtol=tol, atol=tol, h0=0.01)  # first run allocates its buffers
+            net.set_state(y0)
+            t0 = time.perf_counter()
+            st = net.dp5(t_end=t_end, rtol=tol, atol=tol, h0=0.01, out_dt=1.0)
+            wall = time.perf_counter() - t0
+        assert st["status"] == 0
+        out.append({"workload": f"Kuramoto with inertia, 100^3 ball, P={P}, Dormand-Prince 5(4) to t={t_end} at "
+                                f"rtol=atol={tol}, R every time unit",
+                    "wall_s": wall, "accepted_steps": st["accepted"], "rejected_steps": st["rejected"],
+                    "ms_per_accepted_step": 1e3 * wall / st["accepted"],
+                    "rhs_node_evals_per_s": 6.0 * n * (st["accepted"] + st["rejected"]) / wall,
+                    "value": n * st["accepted"] / wall, "unit": "accepted node-steps/s"})
+    return out
+
+
 def bench_ball(args, stream, flush):
     """The paper's performance-test network: 3D Kuramoto with inertia (m = 1,
     eps = 0.05, mu = 0.01, alpha = 0.45), N1 = 100 (10^6 nodes), ball window of
@@ -676,6 +704,7 @@ def run_native(args):
         line["small_ring"] = bench_small_ring(args, stream, flush)
         line["cube"] = bench_cube(args, stream, flush)
         line["ball3d_inertia"] = bench_ball(args, stream, flush)
+        line["ball3d_inertia_dp5"] = bench_ball_dp5(args)
         line["graph"] = bench_graph(args, stream, flush, ball=args.graph_ball)
     if not args.no_batched:
         line["batched"] = bench_batched(args, flush, stream)
