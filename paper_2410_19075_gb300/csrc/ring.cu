@@ -13,7 +13,10 @@
 //       prefix at every sub-tile start: the last CTA to finish in each group of
 //       64 sub-tiles scans that group, and the last group scans the groups;
 //   a6  (stage 4) the Kuramoto order parameter of y_{n+1} from the global totals.
-// The prologue kernel does a1/a2/a6 for the initial state.
+// The prologue kernel does a1/a2/a6 for the initial state.  The Kuramoto and
+// FHN rings run ring_stage_kernel2 (two adjacent nodes per thread); HH runs
+// ring_stage_kernel (one node per thread).  The building blocks are in
+// ring_parts.cuh.
 #include "ring_parts.cuh"
 
 namespace simk {

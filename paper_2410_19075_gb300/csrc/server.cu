@@ -8,7 +8,7 @@
 // in arrival order while the resident jobs' device memory stays within the HBM
 // budget and a slot is free, keeps their state on the device, advances every
 // resident job together through the batched stage kernels (one launch per RK4
-// stage for all ring jobs of a model; cube jobs by their own kernels) in chunks
+// stage for all ring jobs of a model; lattice jobs by their own kernels) in chunks
 // of chunk_steps, and retires a job as soon as its horizon is reached: its step
 // budget stops it exactly inside a chunk, its final state and order parameters
 // are copied to host memory and its device memory is released, which lets the
@@ -272,8 +272,8 @@ void worker_loop(srv_t s)
                 s->membership_changed = false;
                 s->batches_formed++;
             }
-            // cube jobs carry no device budget: step the chunk only as far as
-            // the shortest cube horizon
+            // lattice jobs carry no device budget: step the chunk only as far as
+            // the shortest lattice horizon
             int64_t n = s->chunk;
             for (Job *j : s->resident)
                 if (j->topo != SIM_RING && j->left < n) n = j->left;
