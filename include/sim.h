@@ -129,8 +129,8 @@ int sim_create_in(sim_t *out, int model, int topology, int64_t N, int64_t radius
  * device evaluates each node's sum as runs of V read from an exact prefix of
  * the coupled quantity plus its entry's signed links: O(runs of V + entry size)
  * reads per node instead of one per link.  3 <= N < 2^31.  The network then
- * steps with sim_step (RK4) and supports every call taking a sim_t except
- * sim_dp5, budgets and the server.  Errors: SIM_EINVAL (invalid matrix, model
+ * steps with sim_step (RK4) or sim_dp5 and supports every call taking a sim_t
+ * except step budgets and the server.  Errors: SIM_EINVAL (invalid matrix, model
  * or parameters; the message says which), SIM_ENOMEM, SIM_EDEVICE. */
 int sim_create_graph(sim_t *out, int model, int64_t N, const int64_t *row_ptr, const int64_t *col,
                      const double *params, int n_params, void *stream);
@@ -194,8 +194,8 @@ int64_t sim_steps_done(sim_t h);
  * Adaptive Dormand-Prince 5(4) (Section III.A: the paper's default solver is a
  * Dormand-Prince method with step-size control; Section V: the solution is
  * interpolated for dense output and synchronisation is analysed at every
- * output).  Rings (every model) and the cube, ball and disk lattices (the
- * Kuramoto models); not link matrices.
+ * output).  Every topology: rings and link matrices (every model), the cube,
+ * ball and disk lattices (the Kuramoto models).
  *
  * Method: the RK5(4)7M pair of Dormand and Prince (1980), first same as last
  * (six right-hand sides per attempted step).  Error of an attempt of size h:
@@ -229,11 +229,11 @@ typedef struct {
 } sim_dp5_stats;
 
 /* One network.  Returns SIM_OK, the run's SIM_ESTEPS / SIM_ESMALL (the state is
- * then that of the last accepted step, stats->t), SIM_EINVAL (a link matrix,
- * invalid options), SIM_ENOMEM, or a device error.  stats may be NULL.
- * Synchronises the handle's stream.  A lattice run evaluates each stage with
- * the lattice's own kernels (stage input, x pass, gather); a ring run with the
- * fused ring stage kernels. */
+ * then that of the last accepted step, stats->t), SIM_EINVAL (invalid options),
+ * SIM_ENOMEM, or a device error.  stats may be NULL.  Synchronises the handle's
+ * stream.  A ring run uses fused Dormand-Prince stage kernels; a lattice or
+ * link-matrix run evaluates each stage with the network's own right-hand-side
+ * kernels from a stage-input buffer. */
 int sim_dp5(sim_t h, const sim_dp5_opts *opts, sim_dp5_stats *stats);
 
 /* ---------------------------------------------------------------------------
@@ -264,7 +264,7 @@ int sim_batch_set_budgets(sim_batch_t b, const int64_t *steps);
  * graphs of 16 steps).  sim_steps_done() of each member is updated. */
 int sim_batch_step(sim_batch_t b, int64_t n_steps, double dt);
 
-/* Dormand-Prince runs of every member (rings and lattices), each with its own
+/* Dormand-Prince runs of every member, each with its own
  * options opts[i], tolerances, step sizes and decisions; every attempt of every
  * unfinished member is one set of launches per model group.  stats[i] gets each
  * member's outcome (status SIM_OK, SIM_ESTEPS or SIM_ESMALL).  Returns SIM_OK

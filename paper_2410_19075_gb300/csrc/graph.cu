@@ -169,6 +169,7 @@ template <int M, int STAGE>
 __global__ void __launch_bounds__(kRingThreads, GraphMinBlocks<M>::value)
     graph_stage_kernel(const GraphPlan g, const StepSize h)
 {
+    if (g.r.skip && *(const volatile int *)g.r.skip) return; // uniform over the launch
     constexpr int NQ = Model<M>::NQ;
     __shared__ GraphBases<NQ> s_bases;
     const RingStageIO a = stage_io<M, STAGE>(g.r);

@@ -47,6 +47,8 @@ struct RingPlan {
     int64_t obs_cap;
     unsigned long long *obs_ctr;
     long long *steps_left; // batched runs with a step budget: steps still to do (else nullptr)
+    const int *skip;       // if set and nonzero, the plain and link-matrix stage kernels return at
+                           // once (a finished Dormand-Prince run); nullptr for every other use
 };
 
 // Ring members of one model in a batch: device tables of the batched launch.
@@ -169,22 +171,39 @@ struct LatticePlan {
                         // (a finished Dormand-Prince run); nullptr for every other use
 };
 
-// Adaptive Dormand-Prince 5(4) on a lattice (lattice_dp.cu): the lattice
-// right-hand side evaluates each stage (x pass, gather) from a stage-input buffer.
-struct LatDpPlan {
-    LatticePlan rhs;   // the network's plan with y = xbuf and skip = &ctl->done; acc set per stage
-    int model;         // 0 or 3
+// Adaptive Dormand-Prince 5(4) on lattices and link matrices (lattice_dp.cu):
+// elementwise stage-input, error/decision and accept kernels around the
+// network's own right-hand side, evaluated from a stage-input buffer.
+struct ElemDpPlan {
+    int model;
     int64_t nodes, nblk; // nodes; CTAs of the elementwise kernels (256 nodes each)
     double *y, *y5, *xbuf;
-    double *k[8];      // k[1..7]: the stage slopes (k[1] = f(y_n) kept from the last accepted step)
+    double *k[8];        // k[1..7]: the stage slopes (k[1] = f(y_n) kept from the last accepted step)
     DpCtl *ctl;
     int *remaining;
-    double *err_part;  // nblk
-    i128 *out_part;    // nblk * kDpMaxOut * 2
+    double *err_part;    // nblk
+    i128 *out_part;      // nblk * kDpMaxOut * 2
     unsigned long long *dp_ctr;
+    double *f;           // lattices: (sin, cos) of the stage input's phase (else nullptr)
+    MathTables tab;
+    int F;               // fixed-point grid of the dense order-parameter sums
+    double *obs;
+    int64_t obs_cap;
+    unsigned long long *obs_ctr;
+    unsigned *err;
 };
-cudaError_t lat_dp_start(const LatDpPlan &d, cudaStream_t s);   // k1 = f(y_n)
-cudaError_t lat_dp_attempt(const LatDpPlan &d, cudaStream_t s); // one attempted step
+struct LatDpPlan {
+    ElemDpPlan e;
+    LatticePlan rhs;     // the network's plan with y = xbuf and skip = &ctl->done; acc set per stage
+};
+struct GraphDpPlan {
+    ElemDpPlan e;
+    GraphPlan rhs;       // the network's plan with r.y = xbuf, r.obs = nullptr, r.skip = &ctl->done
+};
+cudaError_t lat_dp_start(const LatDpPlan &d, cudaStream_t s);     // k1 = f(y_n)
+cudaError_t lat_dp_attempt(const LatDpPlan &d, cudaStream_t s);   // one attempted step
+cudaError_t graph_dp_start(const GraphDpPlan &d, cudaStream_t s);
+cudaError_t graph_dp_attempt(const GraphDpPlan &d, cudaStream_t s);
 
 cudaError_t lattice_configure(); // once per process, before the first launch
 int64_t lattice_order_blocks(int topo, int64_t N1); // CTAs of the order-parameter passes

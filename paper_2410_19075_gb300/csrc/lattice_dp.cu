@@ -1,11 +1,12 @@
 // Adaptive Dormand-Prince 5(4) on the lattices (cube, ball, disk; Kuramoto with
-// and without inertia), the solver of the paper's performance tests on the 3D
-// network with inertia (Sections III.A and V).
+// and without inertia; the solver of the paper's performance tests on the 3D
+// network with inertia, Sections III.A and V) and on link matrices (every model).
 //
 // Each stage s of an attempt of size h is
 //   input   x_s = y + h sum_{j<s} a_sj k_j into the stage-input buffer, and the
 //           (sin, cos) of its phase (x_7 is also kept as the candidate y_{n+1});
-//   slope   k_s = f(x_s): the lattice right-hand side (x pass, gather) on a plan
+//   slope   k_s = f(x_s): the network's own right-hand side (lattice: x pass and
+//           gather; link matrix: exact prefix and the graph kernel) on a plan
 //           whose state is the stage-input buffer and whose output is k_s;
 // then the error kernel forms e = h sum_j (b_j - bhat_j) k_j, the per-CTA sums of
 // (e / sc)^2 and of the (sin, cos) of the Hermite-interpolated phases at the
@@ -18,10 +19,10 @@ namespace simk {
 
 constexpr int kLdpThreads = 256;
 
-__device__ __forceinline__ bool ldp_done(const LatDpPlan &d) { return *(const volatile int *)&d.ctl->done; }
+__device__ __forceinline__ bool ldp_done(const ElemDpPlan &d) { return *(const volatile int *)&d.ctl->done; }
 
 template <int M, int S>
-__global__ void __launch_bounds__(kLdpThreads) lat_dp_input_kernel(const LatDpPlan d)
+__global__ void __launch_bounds__(kLdpThreads) lat_dp_input_kernel(const ElemDpPlan d)
 {
     constexpr int D = Model<M>::D;
     if (ldp_done(d)) return;
@@ -46,14 +47,16 @@ __global__ void __launch_bounds__(kLdpThreads) lat_dp_input_kernel(const LatDpPl
         if (S == 7) d.y5[q] = x;
         if (v == 0) phase = x;
     }
-    double sn, cn;
-    fast_sincos(phase, d.rhs.mp.tab, sn, cn);
-    d.rhs.f[n] = sn;
-    d.rhs.f[nodes + n] = cn;
+    if (d.f) { // lattices: the x pass reads the (sin, cos) of the phase
+        double sn, cn;
+        fast_sincos(phase, d.tab, sn, cn);
+        d.f[n] = sn;
+        d.f[nodes + n] = cn;
+    }
 }
 
 template <int M>
-__global__ void __launch_bounds__(kLdpThreads) lat_dp_error_kernel(const LatDpPlan d)
+__global__ void __launch_bounds__(kLdpThreads) lat_dp_error_kernel(const ElemDpPlan d)
 {
     constexpr int D = Model<M>::D;
     constexpr int NW = kLdpThreads / 32;
@@ -90,7 +93,7 @@ __global__ void __launch_bounds__(kLdpThreads) lat_dp_error_kernel(const LatDpPl
     const long long next_out = ctl->next_out, n_out = ctl->n_out;
     const int last = ctl->last;
     int n_here = 0;
-    if (odt > 0.0) {
+    if ((M == 0 || M == 3) && odt > 0.0) {
         while (n_here < kDpMaxOut && next_out + n_here <= n_out) {
             const double to = t0 + (double)(next_out + n_here) * odt;
             if (!last && to > t + h) break;
@@ -108,9 +111,9 @@ __global__ void __launch_bounds__(kLdpThreads) lat_dp_error_kernel(const LatDpPl
             const double ph = (1.0 - th) * a0 + th * a1 +
                               th * (th - 1.0) * ((1.0 - 2.0 * th) * (a1 - a0) + (th - 1.0) * h * f0 + th * h * f1);
             double sn, cn;
-            fast_sincos(ph, d.rhs.mp.tab, sn, cn);
-            ss = to_fixed(sn, d.rhs.F, 1, ok);
-            cc = to_fixed(cn, d.rhs.F, 1, ok);
+            fast_sincos(ph, d.tab, sn, cn);
+            ss = to_fixed(sn, d.F, 1, ok);
+            cc = to_fixed(cn, d.F, 1, ok);
         }
         ss = warp_sum_i128(ss);
         cc = warp_sum_i128(cc);
@@ -130,7 +133,7 @@ __global__ void __launch_bounds__(kLdpThreads) lat_dp_error_kernel(const LatDpPl
         }
         __syncthreads();
     }
-    if (!ok) raise_error(d.rhs.err, ERR_RANGE);
+    if (!ok) raise_error(d.err, ERR_RANGE);
     __syncthreads();
     if (tid == 0) {
         double a = 0.0;
@@ -178,14 +181,14 @@ __global__ void __launch_bounds__(kLdpThreads) lat_dp_error_kernel(const LatDpPl
         double tot = 0.0;
         for (int w = 0; w < NW; ++w) tot += s_err[w];
         dp_decide_ctl(d.ctl, d.remaining, tot, (int64_t)D * nodes, n_here, s_out,
-                      DpRecord{d.rhs.obs, d.rhs.obs_cap, d.rhs.obs_ctr, d.rhs.F, nodes});
+                      DpRecord{d.obs, d.obs_cap, d.obs_ctr, d.F, nodes});
     }
 }
 
 // An accepted attempt: y <- y_{n+1}, k_1 <- k_7 (idempotent, so repeating it after
 // the run ended changes nothing).
 template <int M>
-__global__ void __launch_bounds__(kLdpThreads) lat_dp_accept_kernel(const LatDpPlan d)
+__global__ void __launch_bounds__(kLdpThreads) lat_dp_accept_kernel(const ElemDpPlan d)
 {
     constexpr int D = Model<M>::D;
     if (!*(const volatile int *)&d.ctl->acc_flag) return;
@@ -199,41 +202,80 @@ __global__ void __launch_bounds__(kLdpThreads) lat_dp_accept_kernel(const LatDpP
     }
 }
 
-template <int M, int S>
-static cudaError_t stage(const LatDpPlan &d, cudaStream_t s)
+// Stage S: the stage input, then the network's right-hand side into k_S.
+template <int M, int S, class Rhs>
+static cudaError_t stage(const ElemDpPlan &e, const Rhs &rhs, cudaStream_t s)
 {
-    lat_dp_input_kernel<M, S><<<(unsigned)d.nblk, kLdpThreads, 0, s>>>(d);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    LatticePlan p = d.rhs;
-    p.acc = d.k[S];
-    return lattice_rhs(p, s);
+    lat_dp_input_kernel<M, S><<<(unsigned)e.nblk, kLdpThreads, 0, s>>>(e);
+    const cudaError_t err = cudaGetLastError();
+    return err != cudaSuccess ? err : rhs(e.k[S], s);
 }
 
-template <int M>
-static cudaError_t attempt(const LatDpPlan &d, cudaStream_t s)
+template <int M, class Rhs>
+static cudaError_t attempt(const ElemDpPlan &e, const Rhs &rhs, cudaStream_t s)
 {
-    cudaError_t e = stage<M, 2>(d, s);
-    if (e == cudaSuccess) e = stage<M, 3>(d, s);
-    if (e == cudaSuccess) e = stage<M, 4>(d, s);
-    if (e == cudaSuccess) e = stage<M, 5>(d, s);
-    if (e == cudaSuccess) e = stage<M, 6>(d, s);
-    if (e == cudaSuccess) e = stage<M, 7>(d, s);
-    if (e != cudaSuccess) return e;
-    lat_dp_error_kernel<M><<<(unsigned)d.nblk, kLdpThreads, 0, s>>>(d);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    lat_dp_accept_kernel<M><<<(unsigned)d.nblk, kLdpThreads, 0, s>>>(d);
+    cudaError_t err = stage<M, 2>(e, rhs, s);
+    if (err == cudaSuccess) err = stage<M, 3>(e, rhs, s);
+    if (err == cudaSuccess) err = stage<M, 4>(e, rhs, s);
+    if (err == cudaSuccess) err = stage<M, 5>(e, rhs, s);
+    if (err == cudaSuccess) err = stage<M, 6>(e, rhs, s);
+    if (err == cudaSuccess) err = stage<M, 7>(e, rhs, s);
+    if (err != cudaSuccess) return err;
+    lat_dp_error_kernel<M><<<(unsigned)e.nblk, kLdpThreads, 0, s>>>(e);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    lat_dp_accept_kernel<M><<<(unsigned)e.nblk, kLdpThreads, 0, s>>>(e);
     return cudaGetLastError();
 }
 
-cudaError_t lat_dp_start(const LatDpPlan &d, cudaStream_t s)
+// the right-hand sides: k <- f(stage-input buffer)
+struct LatticeRhs {
+    const LatticePlan &p;
+    cudaError_t operator()(double *k, cudaStream_t s) const
+    {
+        LatticePlan q = p;
+        q.acc = k;
+        return lattice_rhs(q, s);
+    }
+};
+struct GraphRhs {
+    const GraphPlan &g;
+    cudaError_t operator()(double *k, cudaStream_t s) const
+    {
+        GraphPlan q = g;
+        q.r.acc = k;
+        cudaError_t err = ring_prologue(q.r, s); // exact prefix of the stage input's coupled quantity
+        return err != cudaSuccess ? err : graph_rhs(q, s);
+    }
+};
+
+template <class Rhs>
+static cudaError_t start_any(const ElemDpPlan &e, const Rhs &rhs, cudaStream_t s)
 {
-    return d.model == 3 ? stage<3, 1>(d, s) : stage<0, 1>(d, s);
+    switch (e.model) {
+    case 0: return stage<0, 1>(e, rhs, s);
+    case 1: return stage<1, 1>(e, rhs, s);
+    case 2: return stage<2, 1>(e, rhs, s);
+    default: return stage<3, 1>(e, rhs, s);
+    }
 }
 
-cudaError_t lat_dp_attempt(const LatDpPlan &d, cudaStream_t s)
+template <class Rhs>
+static cudaError_t attempt_any(const ElemDpPlan &e, const Rhs &rhs, cudaStream_t s)
 {
-    return d.model == 3 ? attempt<3>(d, s) : attempt<0>(d, s);
+    switch (e.model) {
+    case 0: return attempt<0>(e, rhs, s);
+    case 1: return attempt<1>(e, rhs, s);
+    case 2: return attempt<2>(e, rhs, s);
+    default: return attempt<3>(e, rhs, s);
+    }
+}
+
+cudaError_t lat_dp_start(const LatDpPlan &d, cudaStream_t s) { return start_any(d.e, LatticeRhs{d.rhs}, s); }
+cudaError_t lat_dp_attempt(const LatDpPlan &d, cudaStream_t s) { return attempt_any(d.e, LatticeRhs{d.rhs}, s); }
+cudaError_t graph_dp_start(const GraphDpPlan &d, cudaStream_t s) { return start_any(d.e, GraphRhs{d.rhs}, s); }
+cudaError_t graph_dp_attempt(const GraphDpPlan &d, cudaStream_t s)
+{
+    return attempt_any(d.e, GraphRhs{d.rhs}, s);
 }
 
 } // namespace simk

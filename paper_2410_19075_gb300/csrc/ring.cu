@@ -191,6 +191,7 @@ template <int M, int STAGE>
 __global__ void __launch_bounds__(kRing2Threads, SIM_RING2_MIN_BLOCKS)
     ring_stage_kernel2(const RingPlan p, const StepSize h)
 {
+    if (p.skip && *(const volatile int *)p.skip) return; // uniform over the launch
     ring_stage_body2<M, STAGE>(p, stage_io<M, STAGE>(p), h, blockIdx.x);
 }
 
@@ -198,6 +199,7 @@ __global__ void __launch_bounds__(kRing2Threads, SIM_RING2_MIN_BLOCKS)
 template <int M, int STAGE>
 __global__ void __launch_bounds__(kRingThreads, MinBlocks<M>::value) ring_stage_kernel(const RingPlan p, const StepSize h)
 {
+    if (p.skip && *(const volatile int *)p.skip) return; // uniform over the launch
     ring_stage_body<M, STAGE>(p, stage_io<M, STAGE>(p), h, blockIdx.x);
 }
 

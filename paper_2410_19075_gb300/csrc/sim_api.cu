@@ -200,8 +200,8 @@ struct sim_handle {
     std::map<std::pair<double, int>, cudaGraphExec_t> graphs;
     void *dp_block = nullptr;             // Dormand-Prince buffers (allocated on first use)
     DpPlan dp{};
-    void *ldp_block = nullptr;            // lattice Dormand-Prince buffers (allocated on first use)
-    LatDpPlan ldp{};
+    void *edp_block = nullptr;            // lattice / link-matrix Dormand-Prince buffers (first use)
+    ElemDpPlan edp{};
     void *graph_block = nullptr;          // compressed link matrix (general topology)
     GraphPlan graph{};
     int64_t graph_entries = 0;            // difference-table entries
@@ -1111,7 +1111,7 @@ void sim_destroy(sim_t h)
     for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
     if (h->dp_block) cudaFree(h->dp_block);
     if (h->graph_block) cudaFree(h->graph_block);
-    if (h->ldp_block) cudaFree(h->ldp_block);
+    if (h->edp_block) cudaFree(h->edp_block);
     if (h->block && h->owns_block) cudaFree(h->block);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     delete h;
@@ -1136,7 +1136,6 @@ int64_t dp_n_out(double t0, double t_end, double out_dt)
 
 const char *dp_check(sim_t h, const sim_dp5_opts &o)
 {
-    if (h->topo == SIM_GRAPH) return "Dormand-Prince runs take ring and lattice networks";
     const double v[] = {o.t0, o.t_end, o.rtol, o.atol, o.h0, o.h_max, o.out_dt};
     for (double x : v)
         if (!std::isfinite(x)) return "non-finite option";
@@ -1186,9 +1185,11 @@ int dp_ensure(sim_t h)
     return SIM_OK;
 }
 
-int ldp_ensure(sim_t h)
+// Buffers of a lattice or link-matrix run: the candidate state, the stage
+// input, the seven slopes (k_2 in the network's own accumulator), per-CTA sums.
+int edp_ensure(sim_t h)
 {
-    if (h->ldp_block) return SIM_OK;
+    if (h->edp_block) return SIM_OK;
     const int64_t n = (int64_t)h->d * h->nodes, nblk = (h->nodes + 255) / 256;
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -1203,27 +1204,36 @@ int ldp_ensure(sim_t h)
     const size_t oerr = take(sizeof(double) * nblk);
     const size_t oout = take(sizeof(i128) * nblk * kDpMaxOut * 2);
     const size_t octr = take(sizeof(unsigned long long));
-    cudaError_t e = cudaMalloc(&h->ldp_block, off);
+    cudaError_t e = cudaMalloc(&h->edp_block, off);
     if (e != cudaSuccess) {
-        h->ldp_block = nullptr;
+        h->edp_block = nullptr;
         return fail(SIM_ENOMEM, "device allocation of the Dormand-Prince buffers failed");
     }
-    char *b = static_cast<char *>(h->ldp_block);
+    char *b = static_cast<char *>(h->edp_block);
     e = cudaMemsetAsync(b + octr, 0, sizeof(unsigned long long), h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "Dormand-Prince set-up");
-    LatDpPlan &Q = h->ldp;
+    const bool lat = h->topo != SIM_GRAPH;
+    ElemDpPlan &Q = h->edp;
     Q.model = h->model;
     Q.nodes = h->nodes;
     Q.nblk = nblk;
-    Q.y = h->lat.y;
+    Q.y = lat ? h->lat.y : h->ring.y;
     Q.y5 = reinterpret_cast<double *>(b + oy5);
     Q.xbuf = reinterpret_cast<double *>(b + ox);
     Q.k[0] = nullptr;
-    for (int j = 1; j <= 7; ++j) Q.k[j] = j == 2 ? h->lat.acc : reinterpret_cast<double *>(b + ok[j]);
+    for (int j = 1; j <= 7; ++j)
+        Q.k[j] = j == 2 ? (lat ? h->lat.acc : h->ring.acc) : reinterpret_cast<double *>(b + ok[j]);
     Q.err_part = reinterpret_cast<double *>(b + oerr);
     Q.out_part = reinterpret_cast<i128 *>(b + oout);
     Q.dp_ctr = reinterpret_cast<unsigned long long *>(b + octr);
+    Q.f = lat ? h->lat.f : nullptr;
+    Q.tab = lat ? h->lat.mp.tab : h->ring.mp.tab;
+    Q.F = lat ? h->lat.F : h->ring.F;
+    Q.obs = h->obs;
+    Q.obs_cap = kObsCap;
+    Q.obs_ctr = h->obs_ctr;
+    Q.err = h->err;
     return SIM_OK;
 }
 
@@ -1236,7 +1246,7 @@ int dp_run(const std::vector<sim_t> &mem, const sim_dp5_opts *opts, sim_dp5_stat
         if (const char *why = dp_check(mem[i], opts[i])) return fail(SIM_EINVAL, why);
     for (int i = 0; i < n; ++i) {
         if (mem[i]->topo != SIM_RING) {
-            const int st = ldp_ensure(mem[i]);
+            const int st = edp_ensure(mem[i]);
             if (st != SIM_OK) return st;
             continue;
         }
@@ -1318,15 +1328,30 @@ int dp_run(const std::vector<sim_t> &mem, const sim_dp5_opts *opts, sim_dp5_stat
         plans[q].remaining = d_rem;
         plans[q].ctl = d_ctl + plan_member[q];
     }
+    // lattices and link matrices: elementwise stage kernels around the network's
+    // own right-hand side, evaluated from the stage-input buffer
     std::vector<LatDpPlan> lplans;
+    std::vector<GraphDpPlan> gplans;
+    std::vector<int> lat_idx, graph_idx;
     for (int i : lat_members) {
-        LatDpPlan q = mem[i]->ldp;
-        q.rhs = mem[i]->lat;
-        q.rhs.y = q.xbuf;
-        q.rhs.skip = &(d_ctl + i)->done;
-        q.ctl = d_ctl + i;
-        q.remaining = d_rem;
-        lplans.push_back(q);
+        ElemDpPlan e = mem[i]->edp;
+        e.ctl = d_ctl + i;
+        e.remaining = d_rem;
+        if (mem[i]->topo == SIM_GRAPH) {
+            GraphDpPlan q{e, mem[i]->graph};
+            q.rhs.r.y = e.xbuf;
+            q.rhs.r.obs = nullptr;
+            q.rhs.r.skip = &(d_ctl + i)->done;
+            q.rhs.r.err = reinterpret_cast<unsigned *>(&(d_ctl + i)->bad); // out of range: reject
+            gplans.push_back(q);
+            graph_idx.push_back(i);
+        } else {
+            LatDpPlan q{e, mem[i]->lat};
+            q.rhs.y = e.xbuf;
+            q.rhs.skip = &(d_ctl + i)->done;
+            lplans.push_back(q);
+            lat_idx.push_back(i);
+        }
     }
     std::vector<DpGroup> groups;
     for (const Span &sp : spans)
@@ -1360,8 +1385,12 @@ int dp_run(const std::vector<sim_t> &mem, const sim_dp5_opts *opts, sim_dp5_stat
         for (const DpGroup &g : groups)
             if (e == cudaSuccess) e = dp_launch(ds, g, s);
     for (size_t q = 0; q < lplans.size() && e == cudaSuccess; ++q) {
-        e = lattice_prologue(mem[lat_members[q]]->lat, s);
+        e = lattice_prologue(mem[lat_idx[q]]->lat, s);
         if (e == cudaSuccess) e = lat_dp_start(lplans[q], s);
+    }
+    for (size_t q = 0; q < gplans.size() && e == cudaSuccess; ++q) {
+        e = ring_prologue(mem[graph_idx[q]]->ring, s); // R(t0)
+        if (e == cudaSuccess) e = graph_dp_start(gplans[q], s);
     }
     if (e != cudaSuccess) return finish(cuda_fail(e, "Dormand-Prince start"));
     // Attempts in captured graphs until every member is done.
@@ -1376,6 +1405,8 @@ int dp_run(const std::vector<sim_t> &mem, const sim_dp5_opts *opts, sim_dp5_stat
                     if (le == cudaSuccess) le = dp_launch(ds, g, cap);
             for (const LatDpPlan &q : lplans)
                 if (le == cudaSuccess) le = lat_dp_attempt(q, cap);
+            for (const GraphDpPlan &q : gplans)
+                if (le == cudaSuccess) le = graph_dp_attempt(q, cap);
         }
         cudaGraph_t graph = nullptr;
         e = cudaStreamEndCapture(cap, &graph);
@@ -1402,10 +1433,15 @@ int dp_run(const std::vector<sim_t> &mem, const sim_dp5_opts *opts, sim_dp5_stat
     // path, the control words and the OR of the members' error words.
     for (const DpGroup &g : groups)
         if (e == cudaSuccess) e = dp_launch(9, g, s);
-    for (int i : lat_members) { // (sin, cos) of y for the RK4 kernels, without recording R
+    for (int i : lat_idx) { // (sin, cos) of y for the RK4 kernels, without recording R
         LatticePlan quiet = mem[i]->lat;
         quiet.obs = nullptr;
         if (e == cudaSuccess) e = lattice_prologue(quiet, s);
+    }
+    for (int i : graph_idx) { // the prefix of f(y) for the RK4 kernels, without recording R
+        RingPlan quiet = mem[i]->ring;
+        quiet.obs = nullptr;
+        if (e == cudaSuccess) e = ring_prologue(quiet, s);
     }
     if (e == cudaSuccess) {
         batch_error_kernel<<<1, 256, 0, s>>>(reinterpret_cast<unsigned *const *>(tb + o_errs), n, d_eout);

@@ -162,20 +162,46 @@ def test_dp5_full_size_fhn_ring_agrees_with_rk4():
     assert np.abs(k[:, q] - ref).max() < 1e-12
 
 
-def test_dp5_rejects_link_matrices_and_bad_options():
+def test_dp5_rejects_bad_options():
     from paper_2410_19075_gb300 import Network
     from paper_2410_19075_gb300._lib import SimError
-    rp = np.array([0, 1, 2, 3], dtype=np.int64)
-    net = Network.from_links(0, 3, rp, np.array([1, 2, 0]), I.ks_params())
-    with pytest.raises(SimError):
-        net.dp5(t_end=1.0, rtol=1e-8, atol=1e-8, h0=0.01)
-    net.close()
     with Network(0, 0, 100, 10, I.ks_params()) as net:
         net.set_state(I.ks_phases(1, 0, 100))
         for bad in (dict(t_end=0.0, rtol=1e-8, atol=1e-8, h0=0.01), dict(t_end=1.0, rtol=0, atol=0, h0=0.01),
                     dict(t_end=1.0, rtol=1e-8, atol=1e-8, h0=0.0)):
             with pytest.raises(SimError):
                 net.dp5(**bad)
+
+
+@pytest.mark.parametrize("model", [0, 1, 2, 3])
+def test_dp5_link_matrices_match_oracle(model):
+    """Dormand-Prince on a small-world link matrix (every model) against the
+    oracle's dp5 on the same rows."""
+    from paper_2410_19075_gb300 import Network
+    N = 1500
+    rp, col = I.small_world_links(N, 8, 0.05, 80 + model)
+    params = PARAMS[model]()
+    y0, npar = inputs_for(model, 0, N, 81 + model)
+    t_end = {0: 6.0, 1: 1.5, 2: 4.0, 3: 6.0}[model]
+    out_dt = 0.5 if model in (0, 3) else 0.0
+    net = Network.from_links(model, N, rp, col, params)
+    try:
+        if npar is not None:
+            net.set_node_param(npar)
+        net.set_state(y0)
+        net.observables()
+        st = net.dp5(t_end=t_end, rtol=1e-9, atol=1e-9, h0=0.01, out_dt=out_dt)
+        y, order = net.get_state(), net.observables()
+    finally:
+        net.close()
+    oracle.set_graph(N, rp, col)
+    ref, ref_order, ref_st = oracle.dp5(model, oracle.GRAPH, N, 0, params, y0, 0.0, t_end, 1e-9, 1e-9, 0.01,
+                                        out_dt=out_dt, node_param=npar)
+    assert (st["accepted"], st["rejected"], st["status"]) == (ref_st["accepted"], ref_st["rejected"],
+                                                              ref_st["status"])
+    assert np.abs(y - ref).max() <= STATE_TOL
+    if model in (0, 3):
+        assert np.abs(order - ref_order).max() <= ORDER_TOL
 
 
 def _check_lattice(model, topo, N1, seed, P, t_end, tol, h0, out_dt=0.0, params=None):

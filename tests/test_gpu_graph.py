@@ -184,7 +184,7 @@ def test_invalid_link_matrices_rejected():
         Network.from_links(0, 2, good_rp[:3], good_col[:2], I.ks_params())
     net = Network.from_links(0, 3, good_rp, good_col, I.ks_params())
     with pytest.raises(SimError):
-        net.dp5(t_end=1.0, rtol=1e-8, atol=1e-8, h0=0.01)
+        net.set_state(np.zeros(4))  # wrong size
     net.close()
 
 
