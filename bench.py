@@ -186,28 +186,38 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- CPU baseline
-def cpu_baseline(args, N, R, params, seconds):
-    """Oracle throughput on the host cores: brute-force RHS of a bounded sample of
-    nodes for the 4 stages of one RK4 step, extrapolated per node-step."""
+def oracle_rate(model, topo, N, R, params, y, seconds, threads, node_param=None):
+    """Oracle throughput: brute-force RHS of a sample of nodes for the 4 stages of
+    one RK4 step, the sample grown until it takes about `seconds`; returns
+    (node-steps/s, sample size)."""
     import oracle
+    n_all = N ** 3 if topo in (1, 2) else N * N if topo == 3 else N
+    rng = np.random.default_rng(0)
+    n = 4
+    while True:
+        q = np.sort(rng.choice(n_all, n, replace=False))
+        t0 = time.perf_counter()
+        for _ in range(4):
+            oracle.rhs_sampled(model, topo, N, R, params, y, q, node_param=node_param, threads=threads)
+        dt = time.perf_counter() - t0
+        if dt > seconds / 4 or n >= n_all:
+            return n / dt, n
+        n = min(n_all, max(n * 2, int(n * (seconds / 4) / max(dt, 1e-3))))
+
+
+def cpu_baseline(args, N, R, params, seconds):
+    """Oracle throughput on the host cores (all of them, and one): brute-force RHS
+    of a bounded sample of nodes for the 4 stages of one RK4 step, extrapolated
+    per node-step."""
     cores = os.cpu_count() or 1
     y0 = I.initial_state(args.model, 2412, 0, N)
     npar = I.hh_iext(2412, 0, N) if args.model == 2 else None
-    # calibrate on a small sample, then size the sample to the time budget
-    rng = np.random.default_rng(0)
-    n = 16
-    while True:
-        q = np.sort(rng.choice(N, n, replace=False))
-        t0 = time.perf_counter()
-        for _ in range(4):
-            oracle.rhs_sampled(args.model, 0, N, R, params, y0, q, node_param=npar, threads=cores)
-        dt = time.perf_counter() - t0
-        if dt > seconds / 4 or n >= N:
-            break
-        n = min(N, max(n * 2, int(n * (seconds / 4) / max(dt, 1e-3))))
-    return {"value": n / dt, "unit": "node-steps/s", "cores": cores, "kind": "oracle",
-            "sample": f"brute-force RHS of {n} sampled nodes x 4 RK4 stages on the {N}-node network "
-                      f"({2 * R} links each), extrapolated per node-step"}
+    value, n = oracle_rate(args.model, 0, N, R, params, y0, seconds, cores, npar)
+    one, n1 = oracle_rate(args.model, 0, N, R, params, y0, seconds / 3, 1, npar)
+    return {"value": value, "unit": "node-steps/s", "cores": cores, "kind": "oracle",
+            "single_core_value": one,
+            "sample": f"brute-force RHS of {n} ({n1} on one core) sampled nodes x 4 RK4 stages on the "
+                      f"{N}-node network ({2 * R} links each), extrapolated per node-step"}
 
 
 def run_reference(args):
@@ -440,8 +450,14 @@ def bench_small_ring(args, stream, flush, steps=200, reps=5):
         times.append(a.elapsed_time(b))
     net.close()
     ms = statistics.median(times)
+    cores = os.cpu_count() or 1
+    y_host = I.ks_phases(2411, 0, N)
+    orc, _ = oracle_rate(0, 0, N, R, I.ks_params(alpha=1.46), y_host, 4.0, cores)
+    orc1, _ = oracle_rate(0, 0, N, R, I.ks_params(alpha=1.46), y_host, 2.0, 1)
     return {"workload": f"Kuramoto ring N={N}, R={R}, alpha=1.46, {steps} RK4 steps (cluster-resident kernel)",
-            "us_per_step": 1e3 * ms / steps, "value": N * steps / (ms * 1e-3), "unit": "node-steps/s"}
+            "us_per_step": 1e3 * ms / steps, "value": N * steps / (ms * 1e-3), "unit": "node-steps/s",
+            "oracle": {"value": orc, "single_core_value": orc1, "cores": cores, "unit": "node-steps/s",
+                       "sample": "brute-force RHS of every node (all 700 links), 4 stages"}}
 
 
 def bench_lattice(args, stream, flush, model, topo, N1, P, params, steps=100):
@@ -535,7 +551,16 @@ def bench_cube(args, stream, flush, N1=464, P=92, steps=20):
     net.sync()
     net.close()
     nodes = N1 ** 3
+    cores = os.cpu_count() or 1
+    y_host = I.ks_phases(2413, 0, nodes)
+    orc, n = oracle_rate(0, 1, N1, P, I.ks_params(alpha=1.52), y_host, 6.0, cores)
+    orc1, n1 = oracle_rate(0, 1, N1, P, I.ks_params(alpha=1.52), y_host, 3.0, 1)
+    del y_host
+    oracle_line = {"value": orc, "single_core_value": orc1, "cores": cores, "unit": "node-steps/s",
+                   "sample": f"brute-force RHS of {n} ({n1} on one core) sampled nodes x 4 stages, "
+                             f"{(2 * P + 1) ** 3 - 1} links each, extrapolated per node-step"}
     return {"workload": f"Kuramoto periodic cubic lattice N1={N1} ({nodes} nodes), P={P}, alpha=1.52",
+            "oracle": oracle_line,
             "steps": steps, "ms_per_step": ms / steps, "value": nodes * steps / (ms * 1e-3),
             "unit": "node-steps/s", "hbm_gbs_algorithmic": CUBE_BYTES * nodes * steps / (ms * 1e-3) / 1e9}
 
@@ -584,6 +609,24 @@ def bench_served(args, stream, n_jobs=400, rate=200.0, size_scale=0.05, steps_sc
             "total_node_steps": node_steps, "batched": batched, "plain_one_at_a_time": plain,
             "speedup_vs_plain": batched["value"] / plain["value"],
             "p99_latency_ratio_plain_over_batched": plain["p99_latency_s"] / batched["p99_latency_s"]}
+
+
+def bench_served_sweep(args, stream, rates=(10.0, 50.0, 200.0, 800.0, 3200.0)):
+    """The served mix at increasing offered rates (Poisson, same scaled trace
+    shape, about 5 s of arrivals, 60 to 400 jobs per rate), continuous batching:
+    where throughput stops following the offered load and latency grows (the
+    knee)."""
+    out = []
+    for rate in rates:
+        n_jobs = int(min(400, max(60, 5 * rate)))
+        jobs = I.served_trace(n_jobs=n_jobs, rate=rate, seed=2418, size_scale=0.05, steps_scale=0.1)
+        inits = [I.initial_state(j.model, j.seed, j.job_id + 1, j.N ** 3 if j.topo == 1 else j.N) for j in jobs]
+        offered = sum((j.N ** 3 if j.topo == 1 else j.N) * j.n_steps for j in jobs) / jobs[-1].arrival
+        r = serve_trace(jobs, inits, 4096, 64 << 30, 32, stream)
+        out.append({"rate_jobs_per_s": rate, "jobs": n_jobs, "offered_node_steps_per_s": offered, "value": r["value"],
+                    "p50_latency_s": r["p50_latency_s"], "p99_latency_s": r["p99_latency_s"],
+                    "mean_queue_wait_s": r["mean_queue_wait_s"]})
+    return out
 
 
 # ----------------------------------------------------------------------------- native
@@ -711,6 +754,7 @@ def run_native(args):
         line["batched_dp5"] = bench_dp5_sweep(args, n_inst=args.instances)
     if not args.no_served:
         line["served"] = bench_served(args, stream)
+        line["served_rate_sweep"] = bench_served_sweep(args, stream)
     net.close()
     if rank == 0:
         print(json.dumps(line), flush=True)

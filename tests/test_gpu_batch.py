@@ -114,3 +114,65 @@ def test_step_budgets_stop_members_exactly():
         assert np.array_equal(net.observables(), oa)
         assert net.steps_done == steps
         net.close()
+
+
+def test_batched_sweep_32_members_match_oracle():
+    """32 sweep members (N log-uniform in [100, 1000], plus the smallest and the
+    largest N of that range at the extreme radii) in one batch, 200 steps, every
+    member against the oracle."""
+    from paper_2410_19075_gb300 import Batch
+    specs = [(0, 0, s.N, s.R, I.ks_params(alpha=s.alpha))
+             for s in I.batched_sweep(n_inst=30, seed=81, n_lo=100, n_hi=1000)]
+    specs += [(0, 0, 100, 5, I.ks_params(alpha=1.3)), (0, 0, 1000, 450, I.ks_params(alpha=1.57))]
+    nets, inits = _members(specs)
+    try:
+        with Batch(nets) as b:
+            b.step(200, 0.01)
+            b.sync()
+        for (model, topo, N, R, params), net, y0 in zip(specs, nets, inits):
+            ref, ref_order = oracle.rk4(0, 0, N, R, params, y0, 200, 0.01, record_order=True)
+            assert np.abs(net.get_state() - ref).max() <= STATE_TOL, (N, R)
+            assert np.abs(net.observables() - ref_order).max() <= ORDER_TOL, (N, R)
+    finally:
+        for n in nets:
+            n.close()
+
+
+def test_full_size_sweep_sampled_members():
+    """The full-size sweep in the launch configuration the benchmark times: 4096
+    rings, N log-uniform in [100, 50000], one batch.  After 20 steps the smallest
+    member and 24 sampled members of N <= 600 match the oracle; the largest
+    member (N = 49779, too large for the oracle to step) equals its plain-path
+    run bit for bit and its right-hand side matches the oracle at 64 sampled
+    nodes."""
+    from paper_2410_19075_gb300 import Batch, Network
+    sweep = I.batched_sweep(n_inst=4096, seed=2414)
+    nets = []
+    try:
+        for s in sweep:
+            net = Network(0, 0, s.N, s.R, I.ks_params(alpha=s.alpha))
+            net.set_state(I.ks_phases(s.seed, s.instance, s.N))
+            nets.append(net)
+        with Batch(nets) as b:
+            b.step(20, 0.01)
+            b.sync()
+        sizes = np.array([s.N for s in sweep])
+        small = np.flatnonzero(sizes <= 600)
+        pick = set(np.random.default_rng(82).choice(small, 24, replace=False).tolist())
+        pick.add(int(np.argmin(sizes)))
+        for k in sorted(pick):
+            s = sweep[k]
+            ref = oracle.rk4(0, 0, s.N, s.R, I.ks_params(alpha=s.alpha), I.ks_phases(s.seed, s.instance, s.N),
+                             20, 0.01)[0]
+            assert np.abs(nets[k].get_state() - ref).max() <= STATE_TOL, (k, s.N, s.R)
+        k = int(np.argmax(sizes))
+        s = sweep[k]
+        params = I.ks_params(alpha=s.alpha)
+        y, _ = _alone(0, 0, s.N, s.R, params, I.ks_phases(s.seed, s.instance, s.N), 20)
+        assert np.array_equal(nets[k].get_state(), y)
+        rhs = nets[k].rhs().reshape(-1, s.N)
+        q = np.sort(np.random.default_rng(83).choice(s.N, 64, replace=False))
+        assert np.abs(rhs[:, q] - oracle.rhs_sampled(0, 0, s.N, s.R, params, y, q)).max() < 1e-12
+    finally:
+        for n in nets:
+            n.close()

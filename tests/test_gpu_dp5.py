@@ -287,3 +287,33 @@ def test_batch_dp5_rings_and_lattices_equal_solo_runs():
 def test_dp5_several_prefix_groups():
     """A ring of 2 groups of 64 sub-tiles plus a ragged tail."""
     _check(0, 2 * 64 * 256 + 77, 100, 45, 3.0, 1e-9, 0.01, out_dt=0.5)
+
+
+def test_batch_dp5_full_size_sweep_sampled_members():
+    """The adaptive sweep in the launch configuration the benchmark times: 4096
+    Kuramoto rings of N = 1000 in one sim_batch_dp5 call (rtol = atol = 1e-8,
+    the order parameter every time unit), over a shorter span; 8 sampled
+    members against the oracle's dp5."""
+    from paper_2410_19075_gb300 import Batch, Network
+    sweep = I.batched_sweep(n_inst=4096, seed=2416, n_lo=1000, n_hi=1000)
+    opts = dict(t_end=3.0, rtol=1e-8, atol=1e-8, h0=0.01, out_dt=1.0)
+    nets = []
+    try:
+        for s in sweep:
+            net = Network(0, 0, s.N, s.R, I.ks_params(alpha=s.alpha))
+            net.set_state(I.ks_phases(s.seed, s.instance, s.N))
+            net.observables()
+            nets.append(net)
+        with Batch(nets) as b:
+            stats = b.dp5([opts] * len(nets))
+        for k in np.random.default_rng(84).choice(len(sweep), 8, replace=False):
+            s = sweep[k]
+            ref, ref_order, ref_st = oracle.dp5(0, 0, s.N, s.R, I.ks_params(alpha=s.alpha),
+                                                I.ks_phases(s.seed, s.instance, s.N), 0.0, 3.0, 1e-8, 1e-8, 0.01,
+                                                out_dt=1.0)
+            assert (stats[k]["accepted"], stats[k]["rejected"]) == (ref_st["accepted"], ref_st["rejected"])
+            assert np.abs(nets[k].get_state() - ref).max() <= STATE_TOL
+            assert np.abs(nets[k].observables() - ref_order).max() <= ORDER_TOL
+    finally:
+        for n in nets:
+            n.close()
