@@ -583,13 +583,15 @@ def serve_trace(jobs, inits, slots, budget, chunk, stream):
             r = srv.poll(jid)
             times.append(r[2])
         stats = srv.stats()
+        phases = srv.timings()
     t = np.array(times)
     lat = t[:, 2] - t[:, 0]
     span = t[:, 2].max() - t[:, 0].min()
     return {"p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
             "mean_queue_wait_s": float(np.mean(t[:, 1] - t[:, 0])),
             "value": stats["node_steps"] / span, "unit": "node-steps/s", "span_s": span,
-            "batches_formed": stats["batches_formed"]}
+            "batches_formed": stats["batches_formed"],
+            "worker_seconds": {k: round(v, 4) for k, v in phases.items()}}
 
 
 def bench_served(args, stream, n_jobs=400, rate=200.0, size_scale=0.05, steps_scale=0.1):

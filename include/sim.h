@@ -320,6 +320,12 @@ int srv_wait_idle(srv_t s);
  * node-steps done, batches formed, device bytes in use}. */
 int srv_stats(srv_t s, int64_t *out6);
 
+/* out5 = the worker thread's cumulative time (seconds) in admission (network
+ * creation and state upload), batch formation, stepping (launches of each chunk
+ * and the wait for it), retirement (result download, release) and waiting for
+ * work.  Read while running or after srv_wait_idle. */
+int srv_timings(srv_t s, double *out5);
+
 /* Stop the worker (unfinished jobs are dropped) and free everything. */
 void srv_destroy(srv_t s);
 

@@ -63,6 +63,7 @@ SIGNATURES = {
     "srv_poll": (_int, [_vp, _i64, ctypes.POINTER(_int), _vp, _i64, _vp, _i64, ctypes.POINTER(_i64), _vp]),
     "srv_wait_idle": (_int, [_vp]),
     "srv_stats": (_int, [_vp, ctypes.POINTER(_i64)]),
+    "srv_timings": (_int, [_vp, _dp]),
     "srv_destroy": (None, [_vp]),
     "sim_math_eval": (_int, [_int, _vp, _vp, _i64]),
     "sim_ring_step_noalloc": (_int, [_int, _i64, _i64, _dp, _int, _uint, _vp, _vp, _i64, _dbl, _vp]),

@@ -27,6 +27,8 @@ namespace simk {
 
 constexpr int kRowWarpsMax = 8;       // x pass: one warp per row
 constexpr int kColThreads = 128;      // cube y and z passes: threads per CTA along i
+constexpr int64_t kColTarget = 152 * 1024; // cube y and z passes: columns are split into
+                                           // segments until about this many threads run
 constexpr int kGatherThreads = 256;   // ball/disk gather: one node per thread
 constexpr size_t kRowSmemMax = 220 * 1024;
 
@@ -152,8 +154,26 @@ __global__ void __launch_bounds__(32 * kRowWarpsMax) lattice_x_kernel(LatticePla
     if (!ok) raise_error(p.err, ERR_RANGE);
 }
 
-// cube y pass: one thread per (i, k) column, sliding window along j (exact int64),
-// 8 rows of window loads issued together.
+// Columns of the y and z passes are split into gridDim.z segments of
+// col_seg_len() nodes (small cubes would otherwise run a few thousand threads,
+// each walking its column serially); every segment starts its own sliding
+// window, so the window sums, being exact, do not depend on the split.
+__host__ __device__ inline int64_t col_segments(int64_t N1)
+{
+    const int64_t cols = N1 * N1;
+    int64_t nseg = (kColTarget + cols - 1) / cols;
+    if (nseg > N1) nseg = N1;
+    return nseg < 1 ? 1 : nseg;
+}
+
+__host__ __device__ inline int64_t col_seg_len(int64_t N1)
+{
+    const int64_t nseg = col_segments(N1);
+    return (N1 + nseg - 1) / nseg;
+}
+
+// cube y pass: one thread per segment of an (i, k) column, sliding window along
+// j (exact int64), 8 rows of window loads issued together.
 __global__ void __launch_bounds__(kColThreads) cube_y_kernel(LatticePlan p)
 {
     if (p.skip && *(const volatile int *)p.skip) return;
@@ -161,7 +181,9 @@ __global__ void __launch_bounds__(kColThreads) cube_y_kernel(LatticePlan p)
     const int64_t N1 = p.N1, P = p.P, nodes = p.nodes;
     const int64_t i = (int64_t)blockIdx.x * kColThreads + threadIdx.x;
     const int64_t k = blockIdx.y;
-    if (i >= N1) return;
+    const int64_t len = col_seg_len(N1), jb = (int64_t)blockIdx.z * len;
+    const int64_t je = jb + len < N1 ? jb + len : N1;
+    if (i >= N1 || jb >= N1) return;
     const int64_t col = k * N1 * N1 + i; // + j * N1
     const int64_t *__restrict__ a0 = p.sx + col;
     const int64_t *__restrict__ a1 = p.sx + nodes + col;
@@ -169,11 +191,13 @@ __global__ void __launch_bounds__(kColThreads) cube_y_kernel(LatticePlan p)
     int64_t *__restrict__ o1 = p.sxy + nodes + col;
     int64_t s0 = 0, s1 = 0;
     for (int64_t d = -P; d <= P; ++d) {
-        const int64_t j = d < 0 ? d + N1 : d;
+        int64_t j = jb + d;
+        j += j < 0 ? N1 : 0;
+        j -= j >= N1 ? N1 : 0;
         s0 += __ldg(a0 + j * N1);
         s1 += __ldg(a1 + j * N1);
     }
-    for (int64_t j0 = 0; j0 < N1; j0 += U) {
+    for (int64_t j0 = jb; j0 < je; j0 += U) {
         int64_t in0[U], out0[U], in1[U], out1[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -181,7 +205,7 @@ __global__ void __launch_bounds__(kColThreads) cube_y_kernel(LatticePlan p)
             int64_t jin = j + P + 1, jout = j - P;
             if (jin >= N1) jin -= N1;
             if (jout < 0) jout += N1;
-            const bool live = j < N1;
+            const bool live = j < je;
             in0[u] = live ? __ldg(a0 + jin * N1) : 0;
             out0[u] = live ? __ldg(a0 + jout * N1) : 0;
             in1[u] = live ? __ldg(a1 + jin * N1) : 0;
@@ -190,7 +214,7 @@ __global__ void __launch_bounds__(kColThreads) cube_y_kernel(LatticePlan p)
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int64_t j = j0 + u;
-            if (j < N1) {
+            if (j < je) {
                 o0[j * N1] = s0;
                 o1[j * N1] = s1;
             }
@@ -208,8 +232,8 @@ __device__ void lattice_record_order(const LatticePlan &p, i128 ps, i128 pc)
     __shared__ i128 s_ws[32], s_wc[32];
     __shared__ bool s_last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const unsigned nblk = gridDim.x * gridDim.y;
-    const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x;
+    const unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
+    const unsigned bid = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
     ps = warp_sum_i128(ps);
     pc = warp_sum_i128(pc);
     if (lane == 0) {
@@ -313,8 +337,9 @@ __device__ __forceinline__ void lattice_node(const LatticePlan &p, int64_t n, in
     }
 }
 
-// cube z pass: one thread per (i, j) column, sliding window along k, fused with
-// the node update.  Also the prologue of every lattice (STAGE 0, no window).
+// cube z pass: one thread per segment of an (i, j) column, sliding window along
+// k, fused with the node update.  Also the prologue of the cube (STAGE 0, no
+// window).
 template <int M, int STAGE>
 __global__ void __launch_bounds__(kColThreads) cube_z_kernel(LatticePlan p, const StepSize h)
 {
@@ -322,6 +347,8 @@ __global__ void __launch_bounds__(kColThreads) cube_z_kernel(LatticePlan p, cons
     const int64_t N1 = p.N1, P = p.P, nodes = p.nodes, plane = N1 * N1;
     const int64_t i = (int64_t)blockIdx.x * kColThreads + threadIdx.x;
     const int64_t j = blockIdx.y;
+    const int64_t len = col_seg_len(N1), kb = (int64_t)blockIdx.z * len;
+    const int64_t ke = kb + len < N1 ? kb + len : N1;
     i128 ps = 0, pc = 0;
     bool ok = true;
     if (i < N1) {
@@ -329,14 +356,16 @@ __global__ void __launch_bounds__(kColThreads) cube_z_kernel(LatticePlan p, cons
         const int64_t *__restrict__ a0 = p.sxy + col;
         const int64_t *__restrict__ a1 = p.sxy + nodes + col;
         int64_t s0 = 0, s1 = 0;
-        if (STAGE > 0) {
+        if (STAGE > 0 && kb < N1) {
             for (int64_t d = -P; d <= P; ++d) {
-                const int64_t k = d < 0 ? d + N1 : d;
+                int64_t k = kb + d;
+                k += k < 0 ? N1 : 0;
+                k -= k >= N1 ? N1 : 0;
                 s0 += __ldg(a0 + k * plane);
                 s1 += __ldg(a1 + k * plane);
             }
         }
-        for (int64_t k = 0; k < N1; ++k) {
+        for (int64_t k = kb; k < ke; ++k) {
             lattice_node<M, STAGE>(p, col + k * plane, s0, s1, h, ok, ps, pc);
             if (STAGE > 0) {
                 int64_t kin = k + P + 1, kout = k - P;
@@ -401,7 +430,7 @@ __global__ void __launch_bounds__(kGatherThreads) lattice_gather_kernel(LatticeP
 // ---------------------------------------------------------------------------
 static dim3 col_grid(int64_t N1)
 {
-    return dim3((unsigned)((N1 + kColThreads - 1) / kColThreads), (unsigned)N1);
+    return dim3((unsigned)((N1 + kColThreads - 1) / kColThreads), (unsigned)N1, (unsigned)col_segments(N1));
 }
 
 static unsigned gather_grid(const LatticePlan &p)
@@ -418,7 +447,7 @@ int64_t lattice_sx_elems(int topo, int64_t N1, int64_t P, bool wmode)
 
 int64_t lattice_order_blocks(int topo, int64_t N1)
 {
-    if (topo == 1) return ((N1 + kColThreads - 1) / kColThreads) * N1;
+    if (topo == 1) return ((N1 + kColThreads - 1) / kColThreads) * N1 * col_segments(N1);
     const int64_t nodes = topo == 3 ? N1 * N1 : N1 * N1 * N1;
     return (nodes + kGatherThreads - 1) / kGatherThreads;
 }

@@ -129,6 +129,9 @@ struct srv_handle {
     size_t used = 0;
     // statistics
     int64_t completed = 0, node_steps = 0, batches_formed = 0, ticks = 0;
+    // worker time by phase (seconds): admission, batch formation, stepping
+    // (launches and the wait for the chunk), retirement, waiting for work
+    double t_phase[5] = {0, 0, 0, 0, 0};
     // batch state (worker only)
     std::map<double, sim_batch_t> batches;
     bool membership_changed = true;
@@ -193,11 +196,16 @@ void worker_loop(srv_t s)
     for (;;) {
         // 1. admission: FIFO while a slot is free and the budget allows
         std::vector<Job *> to_admit;
+        double t0 = now_s();
         {
             std::unique_lock<std::mutex> lock(s->mu);
             if (s->stop) break;
-            if (s->resident.empty() && s->queue.empty())
+            if (s->resident.empty() && s->queue.empty()) {
                 s->cv_work.wait(lock, [&] { return s->stop || !s->queue.empty(); });
+                const double t = now_s();
+                s->t_phase[4] += t - t0;
+                t0 = t;
+            }
             if (s->stop) break;
             if (!s->queue.empty() && !s->arena.init(s->budget)) {
                 // the budget itself cannot be allocated: fail every queued job
@@ -223,6 +231,7 @@ void worker_loop(srv_t s)
         }
         for (Job *j : to_admit) {
             admit(s, j);
+
             if (j->h) {
                 s->resident.push_back(j);
                 s->membership_changed = true;
@@ -235,6 +244,8 @@ void worker_loop(srv_t s)
                 s->cv_done.notify_all();
             }
         }
+        double t1 = now_s();
+        s->t_phase[0] += t1 - t0;
         if (s->resident.empty()) continue;
 
         // 2. advance the resident jobs by one chunk
@@ -271,6 +282,9 @@ void worker_loop(srv_t s)
                 }
                 s->membership_changed = false;
                 s->batches_formed++;
+                const double t = now_s();
+                s->t_phase[1] += t - t1;
+                t1 = t;
             }
             // lattice jobs carry no device budget: step the chunk only as far as
             // the shortest lattice horizon
@@ -291,6 +305,8 @@ void worker_loop(srv_t s)
             }
         }
         s->ticks++;
+        const double t2 = now_s();
+        s->t_phase[2] += t2 - t1;
 
         // 3. retire finished jobs
         std::vector<Job *> still;
@@ -317,6 +333,7 @@ void worker_loop(srv_t s)
             }
             s->cv_done.notify_all();
         }
+        s->t_phase[3] += now_s() - t2;
     }
     destroy_batches(s);
     for (Job *j : s->resident)
@@ -419,6 +436,14 @@ int srv_wait_idle(srv_t s)
             if (!kv.second->done) return false;
         return true;
     });
+    return SIM_OK;
+}
+
+int srv_timings(srv_t s, double *out5)
+{
+    if (!s || !out5) return SIM_EINVAL;
+    std::lock_guard<std::mutex> lock(s->mu);
+    for (int k = 0; k < 5; ++k) out5[k] = s->t_phase[k];
     return SIM_OK;
 }
 

@@ -268,6 +268,12 @@ class Server:
         keys = ("completed", "pending", "queued", "node_steps", "batches_formed", "bytes_in_use")
         return dict(zip(keys, list(a)))
 
+    def timings(self):
+        """Worker time (s) by phase: admit, form (batches), step, retire, idle."""
+        a = (ctypes.c_double * 5)()
+        check(lib().srv_timings(self._h, a))
+        return dict(zip(("admit", "form", "step", "retire", "idle"), list(a)))
+
     def close(self):
         if self._h is not None:
             lib().srv_destroy(self._h)
