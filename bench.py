@@ -54,7 +54,7 @@ LATTICE_BYTES = {0: 408, 3: 544}
 # DRAM bytes per stage launch (dram__bytes_read.sum + dram__bytes_write.sum, mean
 # over the four stages) from an ncu capture of the current ring stage kernel on
 # the FitzHugh-Nagumo ring N = 10^6, R = 350000; reported only for that workload.
-MEASURED_TRAFFIC = {(0, 1, 10 ** 6, 350000): 44.25e6}
+MEASURED_TRAFFIC = {(0, 1, 10 ** 6, 350000): 44.20e6}
 
 
 def parse():

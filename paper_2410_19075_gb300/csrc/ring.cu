@@ -11,7 +11,9 @@
 //   a2  coupled quantity f(x_{s+1}), its exact prefix inside each 256-node
 //       sub-tile (one CTA), and, without any CTA waiting for another, the exact
 //       prefix at every sub-tile start: the last CTA to finish in each group of
-//       64 sub-tiles scans that group, and the last group scans the groups;
+//       64 sub-tiles scans that group, and the last group scans the groups; or,
+//       for rings of at most 64 groups (one-pass prefix, ring_parts.cuh), the
+//       sub-tile totals and group accumulators the next kernel sums itself;
 //   a6  (stage 4) the Kuramoto order parameter of y_{n+1} from the global totals.
 // The prologue kernel does a1/a2/a6 for the initial state.  The Kuramoto and
 // FHN rings run ring_stage_kernel2 (two adjacent nodes per thread); HH runs
@@ -96,7 +98,11 @@ __device__ __forceinline__ void ring_stage_body2(const RingPlan &P, const RingSt
     const int tid = threadIdx.x;
     const int64_t N = P.N;
     const int64_t i0 = sub * kSubTile + 2 * tid;
-    if (STAGE > 0) ring_compute_bases<NQ>(P, a.ingrp_in, a.grpofs_in, sub, s_bases);
+    const bool flat = P.flat != 0;
+    if (STAGE > 0) {
+        if (flat) ring_flat_bases<NQ>(P, a.fsub_in, a.facc_in, sub, s_bases);
+        else ring_compute_bases<NQ>(P, a.ingrp_in, a.grpofs_in, sub, s_bases);
+    }
 
     int64_t l[NQ][2], lp[NQ], lb[NQ][2], la[NQ][2];
     double yv[2][D], av[2][D], X[2][NX > 0 ? NX : 1], Iext[2] = {0.0, 0.0};
@@ -183,8 +189,10 @@ __device__ __forceinline__ void ring_stage_body2(const RingPlan &P, const RingSt
         for (int c = 0; c < NQ; ++c) qv[c][u] = to_fixed(f[c], P.F, P.lim, ok);
     }
     if (!ok) raise_error(P.err, ERR_RANGE);
+    // the prologue writes both prefix forms (a later kernel of either kind may read it)
     ring_prefix_tail_n<NQ, 2, (M == 0 || M == 3) && (STAGE == 0 || STAGE == 4), STAGE == 4>(
-        P, a.lam_out, a.ingrp_out, a.grpofs_out, sub, i0, qv);
+        P, a.lam_out, a.ingrp_out, a.grpofs_out, sub, i0, qv, flat, STAGE == 0 || !flat, a.fsub_out, a.facc_out,
+        a.facc_zero);
 }
 
 template <int M, int STAGE>
@@ -309,14 +317,26 @@ cudaError_t ring_batch_step(const RingBatchGroup &g, double dt, cudaStream_t s)
     return cudaSuccess;
 }
 
+static size_t flat_slot_bytes(const RingPlan &p)
+{
+    return sizeof(unsigned long long) * 2 * (size_t)Model<0>::NQ * (size_t)p.ngroups;
+}
+
 cudaError_t ring_prologue(const RingPlan &p, cudaStream_t s)
 {
+    if (p.flat) { // the four accumulator slots are contiguous; slot 0 must start from zero
+        const cudaError_t e = cudaMemsetAsync(p.facc[0], 0, 4 * flat_slot_bytes(p), s);
+        if (e != cudaSuccess) return e;
+    }
     return launch_any(0, p, 0.0, s);
 }
 
 cudaError_t ring_rhs(const RingPlan &p, cudaStream_t s)
 {
-    return launch_any(1, p, 0.0, s);
+    cudaError_t e = launch_any(1, p, 0.0, s);
+    // a stage 1 on its own leaves slot 1 filled; the next RK4 step adds into it
+    if (e == cudaSuccess && p.flat) e = cudaMemsetAsync(p.facc[1], 0, flat_slot_bytes(p), s);
+    return e;
 }
 
 cudaError_t ring_step(const RingPlan &p, double dt, cudaStream_t s)

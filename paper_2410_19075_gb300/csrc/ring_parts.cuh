@@ -12,6 +12,14 @@
 //                     sub-tile start: the last CTA to finish in each group of 64
 //                     sub-tiles scans that group, and the last group scans the
 //                     groups (and may record the Kuramoto order parameter);
+//   one-pass prefix   (RingPlan::flat, the RK4 kernels of rings of at most 64
+//                     groups) no scan at the end of a launch at all: each CTA
+//                     stores its sub-tile total and adds it into its group's
+//                     accumulator; two warps of each CTA of the next launch sum
+//                     the group totals and the sub-tile totals in front of its
+//                     window ends (ring_flat_bases).  The last CTA of a launch
+//                     used to run two dependent scans after everyone else had
+//                     finished, about 4 us each on GB300;
 //   stage_body        one fused RK4 stage around a gather of the window sums
 //                     (ring windows here, general link matrices in graph.cu).
 #pragma once
@@ -89,6 +97,112 @@ __device__ __forceinline__ void ring_compute_bases(const RingPlan &P, const i128
             B.start[side][k] = p;
             B.qn[side][k] = qn;
             p = end + qn + 1;
+        }
+    }
+}
+
+// Piece k (0..2) of window side `side` (0: right ends i+R+1, 1: left ends i-R)
+// of sub-tile `sub`, the same split as ring_compute_bases: its first position on
+// the periodic extension, the sub-tile it starts in and the copy of the ring it
+// lies in (q = -1, 0, 1).  False if the side has fewer pieces.
+__device__ __forceinline__ bool ring_piece(const RingPlan &P, int64_t sub, int side, int k, int64_t &start,
+                                           int64_t &st, int &q)
+{
+    const int64_t N = P.N;
+    const int64_t nvalid = N - sub * kSubTile < kSubTile ? N - sub * kSubTile : kSubTile;
+    const int64_t p0 = side == 0 ? sub * kSubTile + P.R + 1 : sub * kSubTile - P.R;
+    const int64_t p1 = p0 + nvalid - 1;
+    int64_t p = p0;
+    for (int j = 0; j < 3; ++j) {
+        if (p > p1) return false;
+        const int qq = p < 0 ? -1 : (p >= N ? 1 : 0);
+        const int64_t qn = qq * N, pp = p - qn;
+        const int64_t sp = pp >> kSubLog2;
+        if (j == k) {
+            start = p;
+            st = sp;
+            q = qq;
+            return true;
+        }
+        int64_t end = ((sp + 1) << kSubLog2) - 1;
+        if (end > N - 1) end = N - 1;
+        p = end + qn + 1;
+    }
+    return false;
+}
+
+// One-pass window bases (RingPlan::flat), the counterpart of ring_compute_bases:
+// warp `side` (0, 1) finds the exact prefix at the start of its first piece's
+// sub-tile st0 as the group totals in front of st0's group plus the sub-tile
+// totals in front of st0 inside that group, and the ring total, each as a pair
+// of 64-bit warp sums of the words t mod 2^32 and floor(t / 2^32) (no 128-bit
+// shuffles).  A later piece starts one sub-tile on (its prefix grows by that
+// sub-tile's total) or at sub-tile 0 of the next copy of the ring (prefix 0).
+// Lane 0 writes the bases; the caller's barrier makes them visible.  (One warp
+// doing both sides, reading the group totals once per CTA, measured slower.)
+template <int NQ>
+__device__ __forceinline__ void ring_flat_bases(const RingPlan &P, const int64_t *fsub_in,
+                                                const unsigned long long *facc_in, int64_t sub, RingBases<NQ> &B)
+{
+    const int lane = threadIdx.x & 31, side = threadIdx.x >> 5;
+    if (side > 1) return;
+    const int64_t N = P.N, ngroups = P.ngroups, nsub = P.nsub;
+    int64_t start[3] = {0, 0, 0}, st[3] = {0, 0, 0};
+    int q[3] = {0, 0, 0};
+    bool have[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) have[k] = ring_piece(P, sub, side, k, start[k], st[k], q[k]);
+    const int64_t g0 = st[0] >> kGroupLog2;
+#pragma unroll
+    for (int c = 0; c < NQ; ++c) {
+        const unsigned long long *acc = facc_in + c * ngroups * 2;
+        const int64_t *fs = fsub_in + c * nsub;
+        // the totals of the sub-tiles the later pieces follow (broadcast loads)
+        const int64_t f0 = have[1] ? __ldg(fs + st[0]) : 0, f1 = have[2] ? __ldg(fs + st[1]) : 0;
+        long long phi = 0, thi = 0;
+        unsigned long long plo = 0, tlo = 0;
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int64_t g = lane + 32 * e;
+            if (g < ngroups) {
+                const unsigned long long lo = __ldg(acc + 2 * g), hi = __ldg(acc + 2 * g + 1);
+                thi += (long long)hi;
+                tlo += lo;
+                if (g < g0) {
+                    phi += (long long)hi;
+                    plo += lo;
+                }
+            }
+            const int64_t sp = (g0 << kGroupLog2) + g;
+            if (sp < st[0]) {
+                const int64_t t = __ldg(fs + sp);
+                phi += t >> 32;
+                plo += (unsigned long long)(t & 0xffffffffll);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            phi += __shfl_xor_sync(0xffffffffu, phi, o);
+            plo += __shfl_xor_sync(0xffffffffu, plo, o);
+            thi += __shfl_xor_sync(0xffffffffu, thi, o);
+            tlo += __shfl_xor_sync(0xffffffffu, tlo, o);
+        }
+        if (lane == 0) {
+            const i128 T = ((i128)thi << 32) + (i128)tlo;
+            i128 pre = ((i128)phi << 32) + (i128)plo; // exact prefix at the start of st[k]
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                if (!have[k]) break;
+                if (k > 0) pre = st[k] == 0 ? (i128)0 : pre + (i128)(k == 1 ? f0 : f1);
+                B.base[side][k][c] = pre + (q[k] < 0 ? -T : (q[k] > 0 ? T : (i128)0));
+            }
+        }
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            B.start[side][k] = have[k] ? start[k] : INT64_MAX;
+            B.qn[side][k] = have[k] ? q[k] * N : 0;
         }
     }
 }
@@ -205,10 +319,17 @@ __device__ __forceinline__ void ring_prefix_tail(const RingPlan &P, int64_t *lam
 
 // As ring_prefix_tail, with NPT adjacent nodes per thread (kSubTile / NPT
 // threads per CTA): node i0 + u of the thread holds qv[c][u].
+//
+// One-pass output (flat): the sub-tile totals into fsub_out, their group
+// accumulators facc_out, and CTA 0 clears facc_zero (the accumulators the next
+// launch adds into).  tree: the two-level scan above as well (both only in the
+// prologue, whose output any later kernel may read).
 template <int NQ, int NPT, bool RECORD, bool DEC_STEPS>
 __device__ __forceinline__ void ring_prefix_tail_n(const RingPlan &P, int64_t *lam_out, i128 *ingrp_out,
                                                    i128 *grpofs_out, int64_t sub, int64_t i0,
-                                                   const int64_t (&qv)[NQ][NPT])
+                                                   const int64_t (&qv)[NQ][NPT], bool flat, bool tree,
+                                                   int64_t *fsub_out, unsigned long long *facc_out,
+                                                   unsigned long long *facc_zero)
 {
     constexpr int NW = kSubTile / NPT / 32;
     __shared__ int64_t s_wtot[NW][NQ];
@@ -236,6 +357,54 @@ __device__ __forceinline__ void ring_prefix_tail_n(const RingPlan &P, int64_t *l
 #pragma unroll
         for (int u = 0; u < NPT; ++u)
             if (i0 + u < N) lam_out[c * N + i0 + u] = off + run[c][u];
+    }
+
+    if (flat) {
+        const int64_t g = sub >> kGroupLog2;
+        if (tid == 0) {
+#pragma unroll
+            for (int c = 0; c < NQ; ++c) {
+                int64_t t = 0;
+                for (int w = 0; w < NW; ++w) t += s_wtot[w][c];
+                fsub_out[c * nsub + sub] = t;
+                unsigned long long *a = facc_out + (c * ngroups + g) * 2;
+                atomicAdd(a, (unsigned long long)(t & 0xffffffffll));
+                atomicAdd(a + 1, (unsigned long long)(t >> 32));
+            }
+        }
+        if (sub == 0)
+            for (int64_t w = tid; w < NQ * ngroups * 2; w += blockDim.x) facc_zero[w] = 0ull;
+        if (!tree) {
+            if ((RECORD && P.obs) || (DEC_STEPS && P.steps_left)) {
+                // the last CTA of the launch: totals from the accumulators
+                if (tid == 0) {
+                    __threadfence();
+                    s_last = last_arrival(P.flat_ctr, (unsigned long long)nsub);
+                }
+                __syncthreads();
+                if (s_last && warp == 0) {
+                    i128 total[NQ];
+#pragma unroll
+                    for (int c = 0; c < NQ; ++c) {
+                        i128 v = 0;
+                        for (int64_t gg = lane; gg < ngroups; gg += 32) {
+                            const unsigned long long *a = facc_out + (c * ngroups + gg) * 2;
+                            v += ((i128)(long long)__ldcg(a + 1) << 32) + (i128)__ldcg(a);
+                        }
+                        total[c] = warp_sum_i128(v);
+                    }
+                    if (RECORD && lane == 0 && P.obs) {
+                        const double S = fixed_to_double(total[0], P.F);
+                        const double C = fixed_to_double(total[NQ - 1], P.F);
+                        const unsigned long long n = *P.obs_ctr;
+                        P.obs[n % (unsigned long long)P.obs_cap] = sqrt(S * S + C * C) / (double)N;
+                        *P.obs_ctr = n + 1;
+                    }
+                    if (DEC_STEPS && lane == 0 && P.steps_left) *P.steps_left -= 1;
+                }
+            }
+            return;
+        }
     }
 
     // Level 1: the last CTA of each group of 64 sub-tiles scans the group.
@@ -294,12 +463,18 @@ struct RingStageIO {
     const i128 *ingrp_in, *grpofs_in;
     int64_t *lam_out;
     i128 *ingrp_out, *grpofs_out;
+    const int64_t *fsub_in; // one-pass prefix (RingPlan::flat)
+    const unsigned long long *facc_in;
+    int64_t *fsub_out;
+    unsigned long long *facc_out, *facc_zero;
     const double *x_in; // local stage-input variables of this stage (HH gates)
     double *x_out;      // local stage-input variables of the next stage
 };
 
 // Stage 0 (prologue) writes buffer 0; stage s reads buffer (s+1)&1 and writes
-// s&1, so stage 4 leaves f(y_{n+1}) in buffer 0 for the next step.
+// s&1, so stage 4 leaves f(y_{n+1}) in buffer 0 for the next step.  The
+// one-pass group accumulators rotate over four slots: stage s reads slot
+// (s-1)&3, adds into s&3 and clears (s+1)&3, which stage s-2 read last.
 template <int M, int STAGE>
 __host__ __device__ __forceinline__ RingStageIO stage_io(const RingPlan &p)
 {
@@ -312,6 +487,11 @@ __host__ __device__ __forceinline__ RingStageIO stage_io(const RingPlan &p)
     a.lam_out = p.lam[out];
     a.ingrp_out = p.ingrp[out];
     a.grpofs_out = p.grpofs[out];
+    a.fsub_in = STAGE ? p.fsub[in] : nullptr;
+    a.facc_in = STAGE ? p.facc[(STAGE - 1) & 3] : nullptr;
+    a.fsub_out = p.fsub[out];
+    a.facc_out = p.facc[STAGE & 3];
+    a.facc_zero = p.facc[(STAGE + 1) & 3];
     a.x_in = nullptr;
     a.x_out = nullptr;
     if (NX > 0) {

@@ -88,10 +88,18 @@ int ceil_log2(uint64_t x)
     return r;
 }
 
+// Rings whose RK4 stage kernels use the one-pass prefix: two nodes per thread
+// (not HH) and few enough groups for one warp to sum their totals.
+bool ring_flat_eligible(int model, int64_t ngroups)
+{
+    return model != SIM_HH && ngroups <= kFlatMaxGroups;
+}
+
 // Byte layout of a network's device block.  Each entry is an offset.
 struct Layout {
     size_t total = 0;
     size_t y, acc, xg0, xg1, npar, lam0, lam1, ingrp0, ingrp1, grpofs0, grpofs1, subtot, grptot, grpctr;
+    size_t fsub0, fsub1, facc; // one-pass prefix (rings of at most kFlatMaxGroups groups)
     size_t f, xs, sx, sxy, partial, chords, ctrs, obs, tabs;
 };
 
@@ -134,6 +142,10 @@ Layout layout_of(int model, int topo, int64_t N, int64_t R, unsigned flags = 0)
         L.subtot = take(sizeof(int64_t) * nq * nsub);
         L.grptot = take(sizeof(i128) * nq * ngroups);
         L.grpctr = take(sizeof(unsigned long long) * ngroups);
+        const bool flat = ring_flat_eligible(model, ngroups);
+        L.fsub0 = take(flat ? sizeof(int64_t) * nq * nsub : 0);
+        L.fsub1 = take(flat ? sizeof(int64_t) * nq * nsub : 0);
+        L.facc = take(flat ? sizeof(unsigned long long) * 4 * 2 * nq * ngroups : 0);
     } else {
         const int64_t n = nodes_of(topo, N);
         const int64_t nblk = lattice_order_blocks(topo, N);
@@ -206,6 +218,10 @@ struct sim_handle {
     GraphPlan graph{};
     int64_t graph_entries = 0;            // difference-table entries
     size_t graph_bytes = 0;               // device bytes of the compressed matrix
+    // Which prefix forms of f(y) in buffer 0 are current (rings): bit 0 the
+    // two-level scan (Dormand-Prince, cluster and link-matrix kernels read it),
+    // bit 1 the one-pass form (RK4 stage kernels of a flat ring).
+    int pfx = 3;
 };
 
 namespace {
@@ -270,6 +286,19 @@ int get_graph(sim_t h, double dt, int chunk, cudaGraphExec_t *out)
     return SIM_OK;
 }
 
+// Make the one-pass prefix of buffer 0 current again (after kernels that write
+// only the two-level form), without recording an order parameter.
+cudaError_t ring_refresh(sim_t h, cudaStream_t s)
+{
+    RingPlan quiet = h->ring;
+    quiet.obs = nullptr;
+    const cudaError_t e = ring_prologue(quiet, s);
+    if (e == cudaSuccess) h->pfx = 3;
+    return e;
+}
+
+bool ring_flat(sim_t h) { return h->topo == SIM_RING && h->ring.flat; }
+
 int prologue(sim_t h)
 {
     cudaError_t e = cudaMemsetAsync(h->obs_ctr, 0, sizeof(unsigned long long), h->stream);
@@ -279,6 +308,7 @@ int prologue(sim_t h)
     if (e != cudaSuccess) return cuda_fail(e, "prologue");
     h->steps_done = 0;
     h->obs_read = 0;
+    h->pfx = 3;
     return SIM_OK;
 }
 
@@ -426,6 +456,14 @@ static int create_impl(sim_t *out, int model, int topology, int64_t N, int64_t r
         p.obs = h->obs;
         p.obs_cap = kObsCap;
         p.obs_ctr = h->obs_ctr;
+        p.flat = ring_flat_eligible(model, p.ngroups) ? 1 : 0;
+        if (p.flat) {
+            const size_t slot = 2 * (size_t)model_nq(model) * p.ngroups;
+            p.fsub[0] = reinterpret_cast<int64_t *>(b + L.fsub0);
+            p.fsub[1] = reinterpret_cast<int64_t *>(b + L.fsub1);
+            for (int k = 0; k < 4; ++k) p.facc[k] = reinterpret_cast<unsigned long long *>(b + L.facc) + k * slot;
+            p.flat_ctr = ctrs + 3;
+        }
         if (N <= kClusterMaxNodes && !(flags & SIM_FLAG_STREAMING)) {
             static std::once_flag cl_once;
             static cudaError_t cl_err = cudaSuccess;
@@ -644,6 +682,7 @@ int sim_create_graph(sim_t *out, int model, int64_t N, const int64_t *row_ptr, c
         return cuda_fail(e, "link matrix upload");
     }
     GraphPlan &g = h->graph;
+    h->ring.flat = 0; // the link-matrix kernels read the two-level prefix
     g.r = h->ring;
     g.runs = reinterpret_cast<const int2 *>(b + o_runs);
     g.nruns = (int)T.runs.size();
@@ -706,6 +745,17 @@ int sim_step(sim_t h, int64_t n_steps, double dt)
     if (!h) return fail(SIM_EINVAL, "NULL handle");
     if (n_steps < 0) return fail(SIM_EINVAL, "n_steps must be >= 0");
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(SIM_EINVAL, "dt must be finite and > 0");
+    if (n_steps > 0 && ring_flat(h)) {
+        if (use_cluster(h)) {
+            h->pfx = 1; // the cluster kernel leaves the two-level form
+        } else {
+            if (!(h->pfx & 2)) {
+                const cudaError_t e = ring_refresh(h, h->stream);
+                if (e != cudaSuccess) return cuda_fail(e, "prefix refresh");
+            }
+            h->pfx = 2;
+        }
+    }
     int64_t left = n_steps;
     while (left > 0) {
         const int chunk = left >= kGraphChunk ? kGraphChunk : 1;
@@ -746,6 +796,10 @@ int sim_rhs(sim_t h, double *host_k, int64_t n_values)
 {
     if (!h || !host_k) return fail(SIM_EINVAL, "NULL handle or buffer");
     if (n_values != (int64_t)h->d * h->nodes) return fail(SIM_EINVAL, "n_values must equal dim * nodes");
+    if (ring_flat(h) && !(h->pfx & 2)) {
+        const cudaError_t e = ring_refresh(h, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "prefix refresh");
+    }
     cudaError_t e = h->topo == SIM_RING    ? ring_rhs(h->ring, h->stream)
                     : h->topo == SIM_GRAPH ? graph_rhs(h->graph, h->stream)
                                            : lattice_rhs(h->lat, h->stream);
@@ -956,6 +1010,10 @@ int sim_batch_create(sim_batch_t *out, const sim_t *members, int n_members, void
             for (int64_t t = 0; t < h->ring.nsub; ++t) inst_of_item.push_back(k);
             gs.n_items += h->ring.nsub;
             plans.push_back(h->ring);
+            // batched members keep the two-level scan: another member's work
+            // hides its end-of-launch scan, and the one-pass bases cost every
+            // CTA more than that (measured 3% on the 4096-ring sweep)
+            plans.back().flat = 0;
         }
         spans.push_back(gs);
     }
@@ -995,6 +1053,7 @@ int sim_batch_create(sim_batch_t *out, const sim_t *members, int n_members, void
         e = cudaMemcpyAsync(b->budgets, budgets.data(), sizeof(long long) * nplan, cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->err_ptrs, errs.data(), sizeof(unsigned *) * n_members, cudaMemcpyHostToDevice, b->stream);
+
     if (e != cudaSuccess) {
         sim_batch_destroy(b);
         return cuda_fail(e, "batch table upload");
@@ -1044,6 +1103,15 @@ int sim_batch_step(sim_batch_t b, int64_t n_steps, double dt)
     if (!b) return fail(SIM_EINVAL, "NULL batch");
     if (n_steps < 0) return fail(SIM_EINVAL, "n_steps must be >= 0");
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(SIM_EINVAL, "dt must be finite and > 0");
+    if (n_steps > 0)
+        for (sim_t h : b->members) {
+            if (!ring_flat(h)) continue;
+            if (!(h->pfx & 1)) { // the batched kernels read the two-level prefix
+                const cudaError_t e = ring_refresh(h, b->stream);
+                if (e != cudaSuccess) return cuda_fail(e, "prefix refresh");
+            }
+            h->pfx = 1;
+        }
     int64_t left = n_steps;
     while (left > 0) {
         const int chunk = left >= kGraphChunk ? kGraphChunk : 1;
@@ -1363,6 +1431,8 @@ int dp_run(const std::vector<sim_t> &mem, const sim_dp5_opts *opts, sim_dp5_stat
     cudaStream_t cap = nullptr;
     int status = SIM_OK;
     auto finish = [&](int st) {
+        for (sim_t h : mem)
+            if (h->topo == SIM_RING) h->pfx = 1; // the run leaves the two-level prefix of f(y)
         if (ex) cudaGraphExecDestroy(ex);
         cudaStreamSynchronize(s);
         if (cap) cudaStreamDestroy(cap);

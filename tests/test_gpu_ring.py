@@ -252,3 +252,46 @@ def test_ring_past_2_to_31_nodes_twisted_state():
         kk = net.rhs()
     assert kk.size == N
     assert np.abs(kk - Om).max() < 1e-12
+
+
+@pytest.mark.parametrize("model,N,R,steps", [(1, 4096 * 256, 5, 3), (1, 4096 * 256 + 1, 5, 3),
+                                             (0, 4096 * 256 - 100, 9, 3), (3, 4095 * 256 + 17, 40, 2)])
+def test_ring_one_pass_prefix_boundary(model, N, R, steps):
+    """The largest ring of the one-pass prefix (64 groups of 64 sub-tiles), one
+    node more (the two-level scan), and ragged rings just below: every node and
+    the order parameter against the oracle."""
+    _check(model, N, R, steps, 950 + N % 1000, threads=0)
+
+
+def test_prefix_forms_across_rhs_and_adaptive_runs():
+    """A ring of the one-pass prefix (20,000 nodes, stage kernels): a
+    right-hand side taken between steps changes no bit of the trajectory or of
+    its order parameters, and RK4 steps after an adaptive run (which leaves only
+    the two-level prefix) continue from its state like the oracle."""
+    from paper_2410_19075_gb300 import Network
+    N, R = 20000, 7000
+    params = I.ks_params()
+    y0 = I.ks_phases(46, 0, N)
+    with Network(0, 0, N, R, params) as a:
+        a.set_state(y0)
+        a.step(30, 0.01)
+        a.rhs()
+        a.step(30, 0.01)
+        ya, oa = a.get_state(), a.observables()
+    with Network(0, 0, N, R, params) as b:
+        b.set_state(y0)
+        b.step(60, 0.01)
+        yb, ob = b.get_state(), b.observables()
+    assert np.array_equal(ya, yb) and np.array_equal(oa, ob)
+    with Network(0, 0, N, R, params) as net:
+        net.set_state(y0)
+        net.step(20, 0.01)
+        mid = net.get_state()
+        net.dp5(t_end=1.0, rtol=1e-10, atol=1e-10, h0=0.01)
+        mid2 = net.get_state()
+        net.step(20, 0.01)
+        after = net.get_state()
+    ref, _ = oracle.rk4(0, 0, N, R, params, y0, 20, 0.01)
+    assert np.abs(mid - ref).max() <= STATE_TOL
+    ref2, _ = oracle.rk4(0, 0, N, R, params, mid2, 20, 0.01)
+    assert np.abs(after - ref2).max() <= STATE_TOL
