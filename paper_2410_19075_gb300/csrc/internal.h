@@ -50,17 +50,18 @@ struct RingPlan {
     const int *skip;       // if set and nonzero, the plain and link-matrix stage kernels return at
                            // once (a finished Dormand-Prince run); nullptr for every other use
     // One-pass prefix of the RK4 stage kernels (flat = 1; rings of at most
-    // kFlatMaxGroups groups): each CTA stores its sub-tile totals and adds them
-    // into per-group accumulators (exact: a total t is added as t mod 2^32 and
-    // floor(t / 2^32) into two words), and the next kernel's CTAs sum those
-    // themselves, so no CTA waits for the last one of its launch.
+    // kFlatMaxGroups groups): each CTA stores its sub-tile total t and adds it
+    // into its group's accumulator as four chunks (bits 0-17, 18-35, 36-53
+    // unsigned, and t >> 54 signed) in 32-bit words, exact because no sum of
+    // chunks over at most 8192 sub-tiles reaches 2^31; the next kernel's CTAs
+    // sum those themselves, so no CTA waits for the last one of its launch.
     int flat;
-    int64_t *fsub[2];              // NQ * nsub each: sub-tile totals (same parity as lam)
-    unsigned long long *facc[4];   // NQ * ngroups * 2 each: group accumulators (lo, hi) of stage slot s & 3
-    unsigned long long *flat_ctr;  // arrival counter of the one-pass kernels that record or count steps
+    int64_t *fsub[2];     // NQ * nsub each: sub-tile totals (same parity as lam)
+    unsigned *facc[4];    // NQ * ngroups * 4 each: group accumulators of stage slot s & 3
+    unsigned long long *flat_ctr; // arrival counter of the one-pass kernels that record or count steps
 };
 
-constexpr int kFlatMaxGroups = 64; // one warp sums the group totals, two per lane
+constexpr int kFlatMaxGroups = 128; // lanes sum four groups each; 8192 sub-tiles keep chunk sums below 2^31
 
 // Ring members of one model in a batch: device tables of the batched launch.
 struct RingBatchGroup {

@@ -319,7 +319,7 @@ cudaError_t ring_batch_step(const RingBatchGroup &g, double dt, cudaStream_t s)
 
 static size_t flat_slot_bytes(const RingPlan &p)
 {
-    return sizeof(unsigned long long) * 2 * (size_t)Model<0>::NQ * (size_t)p.ngroups;
+    return sizeof(unsigned) * 4 * (size_t)Model<0>::NQ * (size_t)p.ngroups;
 }
 
 cudaError_t ring_prologue(const RingPlan &p, cudaStream_t s)

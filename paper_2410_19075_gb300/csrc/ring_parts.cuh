@@ -12,12 +12,12 @@
 //                     sub-tile start: the last CTA to finish in each group of 64
 //                     sub-tiles scans that group, and the last group scans the
 //                     groups (and may record the Kuramoto order parameter);
-//   one-pass prefix   (RingPlan::flat, the RK4 kernels of rings of at most 64
+//   one-pass prefix   (RingPlan::flat, the RK4 kernels of rings of at most 128
 //                     groups) no scan at the end of a launch at all: each CTA
-//                     stores its sub-tile total and adds it into its group's
-//                     accumulator; two warps of each CTA of the next launch sum
-//                     the group totals and the sub-tile totals in front of its
-//                     window ends (ring_flat_bases).  The last CTA of a launch
+//                     stores its sub-tile total and adds its 18-bit chunks into
+//                     its group's 32-bit accumulators; two warps of each CTA of
+//                     the next launch sum the group totals and the sub-tile
+//                     totals in front of its window ends (ring_flat_bases).  The last CTA of a launch
 //                     used to run two dependent scans after everyone else had
 //                     finished, about 4 us each on GB300;
 //   stage_body        one fused RK4 stage around a gather of the window sums
@@ -101,95 +101,110 @@ __device__ __forceinline__ void ring_compute_bases(const RingPlan &P, const i128
     }
 }
 
-// Piece k (0..2) of window side `side` (0: right ends i+R+1, 1: left ends i-R)
-// of sub-tile `sub`, the same split as ring_compute_bases: its first position on
-// the periodic extension, the sub-tile it starts in and the copy of the ring it
-// lies in (q = -1, 0, 1).  False if the side has fewer pieces.
-__device__ __forceinline__ bool ring_piece(const RingPlan &P, int64_t sub, int side, int k, int64_t &start,
-                                           int64_t &st, int &q)
+// Chunks of a sub-tile total (|t| < 2^62) for the one-pass accumulators:
+// t = c0 + c1 2^18 + c2 2^36 + c3 2^54 with c0..c2 in [0, 2^18) and
+// c3 = floor(t / 2^54) in [-2^8, 2^8).  Over at most 8192 sub-tiles every chunk
+// sum stays below 2^31, so 32-bit words hold them exactly.
+__device__ __forceinline__ unsigned flat_chunk(int64_t t, int k)
 {
-    const int64_t N = P.N;
-    const int64_t nvalid = N - sub * kSubTile < kSubTile ? N - sub * kSubTile : kSubTile;
-    const int64_t p0 = side == 0 ? sub * kSubTile + P.R + 1 : sub * kSubTile - P.R;
-    const int64_t p1 = p0 + nvalid - 1;
-    int64_t p = p0;
-    for (int j = 0; j < 3; ++j) {
-        if (p > p1) return false;
-        const int qq = p < 0 ? -1 : (p >= N ? 1 : 0);
-        const int64_t qn = qq * N, pp = p - qn;
-        const int64_t sp = pp >> kSubLog2;
-        if (j == k) {
-            start = p;
-            st = sp;
-            q = qq;
-            return true;
-        }
-        int64_t end = ((sp + 1) << kSubLog2) - 1;
-        if (end > N - 1) end = N - 1;
-        p = end + qn + 1;
-    }
-    return false;
+    return k < 3 ? (unsigned)((t >> (18 * k)) & 0x3ffff) : (unsigned)(int)(t >> 54);
+}
+
+// The exact value of four chunk sums (the last one signed).
+__device__ __forceinline__ i128 flat_value(unsigned s0, unsigned s1, unsigned s2, unsigned s3)
+{
+    return (i128)s0 + ((i128)s1 << 18) + ((i128)s2 << 36) + ((i128)(int)s3 << 54);
+}
+
+// Per-lane chunk sums of group g: all groups into tk, those in front of group
+// g0 into pk.
+__device__ __forceinline__ void flat_group_add(const unsigned *acc, int g, int g0, unsigned (&pk)[4], unsigned (&tk)[4])
+{
+    const uint4 a = __ldg(reinterpret_cast<const uint4 *>(acc) + g);
+    const unsigned m = g < g0 ? 0xffffffffu : 0u;
+    tk[0] += a.x;
+    tk[1] += a.y;
+    tk[2] += a.z;
+    tk[3] += a.w;
+    pk[0] += a.x & m;
+    pk[1] += a.y & m;
+    pk[2] += a.z & m;
+    pk[3] += a.w & m;
 }
 
 // One-pass window bases (RingPlan::flat), the counterpart of ring_compute_bases:
 // warp `side` (0, 1) finds the exact prefix at the start of its first piece's
 // sub-tile st0 as the group totals in front of st0's group plus the sub-tile
-// totals in front of st0 inside that group, and the ring total, each as a pair
-// of 64-bit warp sums of the words t mod 2^32 and floor(t / 2^32) (no 128-bit
-// shuffles).  A later piece starts one sub-tile on (its prefix grows by that
-// sub-tile's total) or at sub-tile 0 of the next copy of the ring (prefix 0).
-// Lane 0 writes the bases; the caller's barrier makes them visible.  (One warp
-// doing both sides, reading the group totals once per CTA, measured slower.)
+// totals in front of st0 inside that group, and the ring total: every lane adds
+// the chunks of up to four groups and two sub-tiles, and each chunk sum is one
+// redux.sync over the warp.  A later piece starts one sub-tile on (its prefix
+// grows by that sub-tile's total) or at sub-tile 0 of the next copy of the ring
+// (prefix 0).  These rings have at most 2^21 nodes, so positions and indices
+// are 32-bit.  Lane 0 writes the bases; the caller's barrier makes them visible.
 template <int NQ>
-__device__ __forceinline__ void ring_flat_bases(const RingPlan &P, const int64_t *fsub_in,
-                                                const unsigned long long *facc_in, int64_t sub, RingBases<NQ> &B)
+__device__ __forceinline__ void ring_flat_bases(const RingPlan &P, const int64_t *fsub_in, const unsigned *facc_in,
+                                                int64_t sub, RingBases<NQ> &B)
 {
     const int lane = threadIdx.x & 31, side = threadIdx.x >> 5;
     if (side > 1) return;
-    const int64_t N = P.N, ngroups = P.ngroups, nsub = P.nsub;
-    int64_t start[3] = {0, 0, 0}, st[3] = {0, 0, 0};
-    int q[3] = {0, 0, 0};
+    const int N = (int)P.N, R = (int)P.R, ngroups = (int)P.ngroups, nsub = (int)P.nsub;
+    const int s0 = (int)sub * kSubTile;
+    const int nvalid = N - s0 < kSubTile ? N - s0 : kSubTile;
+    const int p0 = side == 0 ? s0 + R + 1 : s0 - R; // in [-N, 2N)
+    const int p1 = p0 + nvalid - 1;
+    // the pieces, split at sub-tile starts and at 0 and N (as in ring_compute_bases)
+    int start[3], st[3], q[3];
     bool have[3];
+    int p = p0;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) have[k] = ring_piece(P, sub, side, k, start[k], st[k], q[k]);
-    const int64_t g0 = st[0] >> kGroupLog2;
+    for (int k = 0; k < 3; ++k) {
+        have[k] = p <= p1;
+        const int qq = p < 0 ? -1 : (p >= N ? 1 : 0);
+        const int sp = (p - qq * N) >> kSubLog2;
+        start[k] = p;
+        st[k] = sp;
+        q[k] = qq;
+        int end = ((sp + 1) << kSubLog2) - 1;
+        end = end > N - 1 ? N - 1 : end;
+        p = end + qq * N + 1;
+    }
+    const int g0 = st[0] >> kGroupLog2;
 #pragma unroll
     for (int c = 0; c < NQ; ++c) {
-        const unsigned long long *acc = facc_in + c * ngroups * 2;
+        const unsigned *acc = facc_in + c * ngroups * 4;
         const int64_t *fs = fsub_in + c * nsub;
         // the totals of the sub-tiles the later pieces follow (broadcast loads)
         const int64_t f0 = have[1] ? __ldg(fs + st[0]) : 0, f1 = have[2] ? __ldg(fs + st[1]) : 0;
-        long long phi = 0, thi = 0;
-        unsigned long long plo = 0, tlo = 0;
+        unsigned pk[4] = {0, 0, 0, 0}, tk[4] = {0, 0, 0, 0};
+        // groups lane and lane + 32 with the sub-tiles of the same offsets in
+        // st0's group (this fixed, interleaved form measured fastest), then
+        // groups 64..127 on rings that have them
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
-            const int64_t g = lane + 32 * e;
-            if (g < ngroups) {
-                const unsigned long long lo = __ldg(acc + 2 * g), hi = __ldg(acc + 2 * g + 1);
-                thi += (long long)hi;
-                tlo += lo;
-                if (g < g0) {
-                    phi += (long long)hi;
-                    plo += lo;
-                }
-            }
-            const int64_t sp = (g0 << kGroupLog2) + g;
+            const int g = lane + 32 * e;
+            if (g < ngroups) flat_group_add(acc, g, g0, pk, tk);
+            const int sp = (g0 << kGroupLog2) + g;
             if (sp < st[0]) {
                 const int64_t t = __ldg(fs + sp);
-                phi += t >> 32;
-                plo += (unsigned long long)(t & 0xffffffffll);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) pk[k] += flat_chunk(t, k);
+            }
+        }
+        if (ngroups > 64) {
+#pragma unroll
+            for (int e = 2; e < kFlatMaxGroups / 32; ++e) {
+                const int g = lane + 32 * e;
+                if (g < ngroups) flat_group_add(acc, g, g0, pk, tk);
             }
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            phi += __shfl_xor_sync(0xffffffffu, phi, o);
-            plo += __shfl_xor_sync(0xffffffffu, plo, o);
-            thi += __shfl_xor_sync(0xffffffffu, thi, o);
-            tlo += __shfl_xor_sync(0xffffffffu, tlo, o);
+        for (int k = 0; k < 4; ++k) {
+            pk[k] = __reduce_add_sync(0xffffffffu, pk[k]);
+            tk[k] = __reduce_add_sync(0xffffffffu, tk[k]);
         }
         if (lane == 0) {
-            const i128 T = ((i128)thi << 32) + (i128)tlo;
-            i128 pre = ((i128)phi << 32) + (i128)plo; // exact prefix at the start of st[k]
+            const i128 T = flat_value(tk[0], tk[1], tk[2], tk[3]);
+            i128 pre = flat_value(pk[0], pk[1], pk[2], pk[3]); // exact prefix at the start of st[k]
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
                 if (!have[k]) break;
@@ -201,8 +216,8 @@ __device__ __forceinline__ void ring_flat_bases(const RingPlan &P, const int64_t
     if (lane == 0) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            B.start[side][k] = have[k] ? start[k] : INT64_MAX;
-            B.qn[side][k] = have[k] ? q[k] * N : 0;
+            B.start[side][k] = have[k] ? (int64_t)start[k] : INT64_MAX;
+            B.qn[side][k] = have[k] ? (int64_t)q[k] * N : 0;
         }
     }
 }
@@ -320,16 +335,15 @@ __device__ __forceinline__ void ring_prefix_tail(const RingPlan &P, int64_t *lam
 // As ring_prefix_tail, with NPT adjacent nodes per thread (kSubTile / NPT
 // threads per CTA): node i0 + u of the thread holds qv[c][u].
 //
-// One-pass output (flat): the sub-tile totals into fsub_out, their group
-// accumulators facc_out, and CTA 0 clears facc_zero (the accumulators the next
+// One-pass output (flat): the sub-tile totals into fsub_out, their chunks into
+// the group accumulators facc_out, and CTA 0 clears facc_zero (the accumulators the next
 // launch adds into).  tree: the two-level scan above as well (both only in the
 // prologue, whose output any later kernel may read).
 template <int NQ, int NPT, bool RECORD, bool DEC_STEPS>
 __device__ __forceinline__ void ring_prefix_tail_n(const RingPlan &P, int64_t *lam_out, i128 *ingrp_out,
                                                    i128 *grpofs_out, int64_t sub, int64_t i0,
                                                    const int64_t (&qv)[NQ][NPT], bool flat, bool tree,
-                                                   int64_t *fsub_out, unsigned long long *facc_out,
-                                                   unsigned long long *facc_zero)
+                                                   int64_t *fsub_out, unsigned *facc_out, unsigned *facc_zero)
 {
     constexpr int NW = kSubTile / NPT / 32;
     __shared__ int64_t s_wtot[NW][NQ];
@@ -367,13 +381,13 @@ __device__ __forceinline__ void ring_prefix_tail_n(const RingPlan &P, int64_t *l
                 int64_t t = 0;
                 for (int w = 0; w < NW; ++w) t += s_wtot[w][c];
                 fsub_out[c * nsub + sub] = t;
-                unsigned long long *a = facc_out + (c * ngroups + g) * 2;
-                atomicAdd(a, (unsigned long long)(t & 0xffffffffll));
-                atomicAdd(a + 1, (unsigned long long)(t >> 32));
+                unsigned *a = facc_out + (c * ngroups + g) * 4;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) atomicAdd(a + k, flat_chunk(t, k));
             }
         }
         if (sub == 0)
-            for (int64_t w = tid; w < NQ * ngroups * 2; w += blockDim.x) facc_zero[w] = 0ull;
+            for (int64_t w = tid; w < NQ * ngroups * 4; w += blockDim.x) facc_zero[w] = 0u;
         if (!tree) {
             if ((RECORD && P.obs) || (DEC_STEPS && P.steps_left)) {
                 // the last CTA of the launch: totals from the accumulators
@@ -386,12 +400,13 @@ __device__ __forceinline__ void ring_prefix_tail_n(const RingPlan &P, int64_t *l
                     i128 total[NQ];
 #pragma unroll
                     for (int c = 0; c < NQ; ++c) {
-                        i128 v = 0;
-                        for (int64_t gg = lane; gg < ngroups; gg += 32) {
-                            const unsigned long long *a = facc_out + (c * ngroups + gg) * 2;
-                            v += ((i128)(long long)__ldcg(a + 1) << 32) + (i128)__ldcg(a);
-                        }
-                        total[c] = warp_sum_i128(v);
+                        unsigned tk[4] = {0, 0, 0, 0};
+                        for (int64_t gg = lane; gg < ngroups; gg += 32)
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) tk[k] += __ldcg(facc_out + (c * ngroups + gg) * 4 + k);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) tk[k] = __reduce_add_sync(0xffffffffu, tk[k]);
+                        total[c] = flat_value(tk[0], tk[1], tk[2], tk[3]);
                     }
                     if (RECORD && lane == 0 && P.obs) {
                         const double S = fixed_to_double(total[0], P.F);
@@ -464,9 +479,9 @@ struct RingStageIO {
     int64_t *lam_out;
     i128 *ingrp_out, *grpofs_out;
     const int64_t *fsub_in; // one-pass prefix (RingPlan::flat)
-    const unsigned long long *facc_in;
+    const unsigned *facc_in;
     int64_t *fsub_out;
-    unsigned long long *facc_out, *facc_zero;
+    unsigned *facc_out, *facc_zero;
     const double *x_in; // local stage-input variables of this stage (HH gates)
     double *x_out;      // local stage-input variables of the next stage
 };

@@ -254,12 +254,14 @@ def test_ring_past_2_to_31_nodes_twisted_state():
     assert np.abs(kk - Om).max() < 1e-12
 
 
-@pytest.mark.parametrize("model,N,R,steps", [(1, 4096 * 256, 5, 3), (1, 4096 * 256 + 1, 5, 3),
-                                             (0, 4096 * 256 - 100, 9, 3), (3, 4095 * 256 + 17, 40, 2)])
+@pytest.mark.parametrize("model,N,R,steps", [(1, 8192 * 256, 5, 3), (1, 8192 * 256 + 1, 5, 3),
+                                             (0, 8192 * 256 - 100, 9, 3), (3, 4095 * 256 + 17, 40, 2),
+                                             (0, 64 * 64 * 256 + 300, 3000, 2)])
 def test_ring_one_pass_prefix_boundary(model, N, R, steps):
-    """The largest ring of the one-pass prefix (64 groups of 64 sub-tiles), one
-    node more (the two-level scan), and ragged rings just below: every node and
-    the order parameter against the oracle."""
+    """The largest ring of the one-pass prefix (128 groups of 64 sub-tiles), one
+    node more (the two-level scan), ragged rings below, and a ring whose groups
+    need more than two per lane: every node and the order parameter against
+    the oracle."""
     _check(model, N, R, steps, 950 + N % 1000, threads=0)
 
 
