@@ -37,10 +37,11 @@ TOPO_NAMES = {1: "periodic cubic lattice", 2: "periodic 3D lattice, ball window"
 # (nq * 8), acc or y (d * 8) and the next local stage variables (nx * 8).
 RING_BYTES = {0: 344, 1: 432, 2: 704, 3: 480}
 # FP64 flops per node-step (DFMA = 2, DADD/DMUL = 1) of the arithmetic the method
-# needs, from the kernels' expressions; a library sincos counts 50 and a library
-# exp/expm1 34 (their measured cost in DFMA equivalents, x2).  Tally in the design doc.
-RING_FLOPS = {0: 4 * (50 + 13) + 14, 1: 4 * 15 + 3 * 8 + 6, 2: 4 * (6 * 34 + 40) + 3 * 16 + 12,
-              3: 4 * (50 + 16) + 3 * 8 + 6}
+# needs, from the kernels' expressions; a sincos counts 25 and an exp 17, the
+# FP64 instructions of the kernels' table-driven routines (11 FMA + 3 MUL and
+# 8 FMA + 1 MUL).
+RING_FLOPS = {0: 4 * (25 + 13) + 14, 1: 4 * 15 + 3 * 8 + 6, 2: 4 * (6 * 17 + 40) + 3 * 16 + 12,
+              3: 4 * (25 + 16) + 3 * 8 + 6}
 # Cube (Kuramoto): per stage the x, y and z passes move 32 + 32 + 72 bytes per
 # node; FP64 flops as the Kuramoto ring.
 CUBE_BYTES = 544
@@ -460,6 +461,34 @@ def bench_small_ring(args, stream, flush, steps=200, reps=5):
                        "sample": "brute-force RHS of every node (all 700 links), 4 stages"}}
 
 
+def bench_roofline_sweep(args, stream, flush, steps=100):
+    """Kuramoto and FHN rings of 10^7 and 10^8 nodes, r = 0.35: steps RK4 steps
+    per timed iteration after 10 warm-up steps (L2 flushed before), with the FP64
+    and HBM fractions of the algorithmic flops and bytes."""
+    import torch
+    from paper_2410_19075_gb300 import Network
+    out = []
+    for model in (0, 1):
+        for N in (10 ** 7, 10 ** 8):
+            R = int(0.35 * N)
+            net = Network(model, 0, N, R, I.ks_params() if model == 0 else I.fhn_params(), stream=stream)
+            net.set_state(I.initial_state(model, 2419, 0, N))
+            net.step(10, args.dt)
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            net.step(steps, args.dt)
+            b.record(stream)
+            torch.cuda.synchronize()
+            net.close()
+            s_step = a.elapsed_time(b) * 1e-3 / steps
+            out.append({"workload": f"{MODEL_NAMES[model]} ring N={N}, R={R}", "steps": steps,
+                        "ms_per_step": s_step * 1e3, "value": N / s_step, "unit": "node-steps/s",
+                        "fp64_frac": RING_FLOPS[model] * N / s_step / 1e9 / (2 * 504.3),
+                        "hbm_frac": RING_BYTES[model] * N / s_step / 1e9 / 6693.8})
+    return out
+
+
 def bench_lattice(args, stream, flush, model, topo, N1, P, params, steps=100):
     """One lattice workload: steps RK4 steps per timed iteration after 3 warm-up
     steps, L2 flushed before the timed region."""
@@ -725,7 +754,7 @@ def run_native(args):
     except OSError:
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    fp64_peak_gflops = 2 * 504.3  # measured DFMA rate x 2 flops
+    fp64_peak_gflops = 2 * 504.3  # DFMA rate measured on GB300 (504.3 G/s), 2 flops each
     achieved_gflops = alg_flops_launch / avg_launch_s / 1e9
     achieved_gbs = alg_bytes_launch / avg_launch_s / 1e9
     traffic = MEASURED_TRAFFIC.get((args.topo, args.model, N, R))
@@ -751,6 +780,7 @@ def run_native(args):
         line["ball3d_inertia"] = bench_ball(args, stream, flush)
         line["ball3d_inertia_dp5"] = bench_ball_dp5(args)
         line["graph"] = bench_graph(args, stream, flush, ball=args.graph_ball)
+        line["roofline_sweep"] = bench_roofline_sweep(args, stream, flush)
     if not args.no_batched:
         line["batched"] = bench_batched(args, flush, stream)
         line["batched_dp5"] = bench_dp5_sweep(args, n_inst=args.instances)

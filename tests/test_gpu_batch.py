@@ -141,10 +141,11 @@ def test_batched_sweep_32_members_match_oracle():
 def test_full_size_sweep_sampled_members():
     """The full-size sweep in the launch configuration the benchmark times: 4096
     rings, N log-uniform in [100, 50000], one batch.  After 20 steps the smallest
-    member and 24 sampled members of N <= 600 match the oracle; the largest
-    member (N = 49779, too large for the oracle to step) equals its plain-path
-    run bit for bit and its right-hand side matches the oracle at 64 sampled
-    nodes."""
+    member and 24 sampled members of N <= 600 match the oracle; every member
+    equals its plain-path run bit for bit (the cluster kernel up to 4096 nodes,
+    the one-pass stage kernels above, against the batched two-level kernels);
+    the largest member's right-hand side (N = 49779, too large for the oracle
+    to step) matches the oracle at 64 sampled nodes."""
     from paper_2410_19075_gb300 import Batch, Network
     sweep = I.batched_sweep(n_inst=4096, seed=2414)
     nets = []
@@ -165,11 +166,13 @@ def test_full_size_sweep_sampled_members():
             ref = oracle.rk4(0, 0, s.N, s.R, I.ks_params(alpha=s.alpha), I.ks_phases(s.seed, s.instance, s.N),
                              20, 0.01)[0]
             assert np.abs(nets[k].get_state() - ref).max() <= STATE_TOL, (k, s.N, s.R)
+        for k, s in enumerate(sweep):
+            y, _ = _alone(0, 0, s.N, s.R, I.ks_params(alpha=s.alpha), I.ks_phases(s.seed, s.instance, s.N), 20)
+            assert np.array_equal(nets[k].get_state(), y), (k, s.N, s.R)
         k = int(np.argmax(sizes))
         s = sweep[k]
         params = I.ks_params(alpha=s.alpha)
-        y, _ = _alone(0, 0, s.N, s.R, params, I.ks_phases(s.seed, s.instance, s.N), 20)
-        assert np.array_equal(nets[k].get_state(), y)
+        y = nets[k].get_state()
         rhs = nets[k].rhs().reshape(-1, s.N)
         q = np.sort(np.random.default_rng(83).choice(s.N, 64, replace=False))
         assert np.abs(rhs[:, q] - oracle.rhs_sampled(0, 0, s.N, s.R, params, y, q)).max() < 1e-12
