@@ -106,6 +106,7 @@ def config_of(args, N, R):
     return {
         "workload": name,
         "N": N, "R": R, "dt": args.dt,
+        "kernel_variant": "autotuned (sim_autotune) before the timed region",
         "rk4_steps_per_iteration": args.chunk,
         "l2": "flushed (512 MiB write) between timed iterations; within an iteration the network "
               "state is reused across consecutive RK4 steps as in a real run",
@@ -273,6 +274,9 @@ def bench_batched(args, flush, stream, n_inst=4096, steps=2000, plain_steps=20):
         nets.append(net)
     total_nodes = sum(s.N for s in sweep)
     batch = Batch(nets, stream=stream)
+    t_tune = time.perf_counter()
+    npt = batch.autotune(args.dt, 16)  # nodes per thread of the batched kernels
+    tune_s = time.perf_counter() - t_tune
     batch.step(args.warmup, args.dt)
     batch.step(100, args.dt)
     batch.step(1, args.dt)
@@ -310,6 +314,7 @@ def bench_batched(args, flush, stream, n_inst=4096, steps=2000, plain_steps=20):
             "steps": steps, "value": value, "unit": "node-steps/s", "ms": ms,
             "plain_value": plain_value, "plain_steps_timed": plain_steps,
             "speedup_vs_plain": value / plain_value,
+            "autotune": {"npt": npt, "seconds": tune_s},
             "gpu_launches": 4 * steps * 1}
 
 
@@ -682,6 +687,10 @@ def run_native(args):
     if npar is not None:
         net.set_node_param(npar)
     net.set_state(y0_dev)
+    # the kernel variant from the autotuner (state unchanged; outside the timing)
+    t_tune = time.perf_counter()
+    tuned = net.autotune(args.dt, 32)
+    tuned["seconds"] = time.perf_counter() - t_tune
 
     chunks = []
     left = args.steps
@@ -771,7 +780,8 @@ def run_native(args):
             "e2e": {"value": e2e_value, "unit": "node-steps/s",
                     "h2d_bytes_per_step": state_bytes / max(1, e2e_chunks[0]),
                     "d2h_bytes_per_step": state_bytes / max(1, e2e_chunks[0])},
-            "gpu_launches": launches * {0: 1, 1: 3}.get(args.topo, 2), "roofline": roofline, "clocks": clk}
+            "gpu_launches": launches * {0: 1, 1: 3}.get(args.topo, 2), "roofline": roofline, "clocks": clk,
+            "autotune": tuned}
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.topo == 0:
         line["cpu_baseline"] = cpu_baseline(args, N, R, params, args.cpu_seconds)
     if not args.no_extra and args.topo == 0 and world == 1:

@@ -279,6 +279,43 @@ int sim_batch_sync(sim_batch_t b);
 void sim_batch_destroy(sim_batch_t b);
 
 /* ---------------------------------------------------------------------------
+ * Autotuner.  The ring stage kernels come in variants that give the same bits:
+ * two adjacent nodes per thread (128 threads per 256-node sub-tile) or one
+ * (256 threads), and, on rings of at most 128 prefix groups (N <= 2^21), the
+ * one-pass or the two-level prefix of the coupled quantity.  Which is fastest
+ * depends on the model, the ring and the batch, so it is measured.
+ *
+ * sim_autotune times trial_steps RK4 steps of dt with every variant of a ring
+ * network, on its current state, and keeps the fastest: *npt_out = nodes per
+ * thread (1 or 2), *flat_out = 1 for the one-pass prefix (either may be NULL).
+ * Afterwards the state is the one before the call, and the order-parameter
+ * record, step count and error word are as after sim_set_state (R(t0) is
+ * recorded again).  Networks without variants (lattices, link matrices, HH,
+ * rings small enough for the cluster kernel) report their fixed choice and run
+ * nothing.  Needs a device copy of the state; SIM_ENOMEM if it does not fit.
+ * The choice is also stored in a process-wide cache under (model, N, radius):
+ * later sim_create calls with the same key start with it. */
+int sim_autotune(sim_t h, double dt, int64_t trial_steps, int *npt_out, int *flat_out);
+
+/* The variant a ring network runs (npt 1 or 2, flat 0 or 1; 0 and 0 for
+ * lattices and link matrices). */
+int sim_tune_info(sim_t h, int *npt, int *flat);
+
+/* The same for a batch: times trial_steps batched RK4 steps with one and with
+ * two nodes per thread for every ring group (HH groups run one), keeps the
+ * faster in *npt_out, and restores every member's state, error word,
+ * order-parameter count and the batch's step budgets.  Cached under the batch's
+ * ring sub-tile and member counts for later sim_batch_create calls. */
+int sim_batch_autotune(sim_batch_t b, double dt, int64_t trial_steps, int *npt_out);
+
+/* Write the cache as text (one "kind model a b npt flat" line per entry; kind 0
+ * = plain ring (model, N, radius), kind 1 = batch (-1, ring sub-tiles, ring
+ * members)), merge a file written that way into it, or empty it.  Host only. */
+int sim_tune_save(const char *path);
+int sim_tune_load(const char *path);
+int sim_tune_clear(void);
+
+/* ---------------------------------------------------------------------------
  * Serving: a request loop with continuous batching.  Jobs (one network each)
  * are submitted at any time; a worker thread admits them in arrival order while
  * the resident jobs' device memory (sim_workspace_bytes each) stays within

@@ -5,4 +5,4 @@ include/sim.h; ``sim`` is its thin Python binding, ``inputs`` the seeded
 synthetic workloads.
 """
 from .sim import (BALL3D, CUBE3D, DISK2D, FHN, GRAPH, HH, KS, KSI, RING, Batch, Network, Server,  # noqa: F401
-                  workspace_bytes)
+                  tune_clear, tune_load, tune_save, workspace_bytes)

@@ -64,6 +64,12 @@ SIGNATURES = {
     "srv_wait_idle": (_int, [_vp]),
     "srv_stats": (_int, [_vp, ctypes.POINTER(_i64)]),
     "srv_timings": (_int, [_vp, _dp]),
+    "sim_autotune": (_int, [_vp, ctypes.c_double, _i64, ctypes.POINTER(_int), ctypes.POINTER(_int)]),
+    "sim_tune_info": (_int, [_vp, ctypes.POINTER(_int), ctypes.POINTER(_int)]),
+    "sim_batch_autotune": (_int, [_vp, ctypes.c_double, _i64, ctypes.POINTER(_int)]),
+    "sim_tune_save": (_int, [ctypes.c_char_p]),
+    "sim_tune_load": (_int, [ctypes.c_char_p]),
+    "sim_tune_clear": (_int, []),
     "srv_destroy": (None, [_vp]),
     "sim_math_eval": (_int, [_int, _vp, _vp, _i64]),
     "sim_ring_step_noalloc": (_int, [_int, _i64, _i64, _dp, _int, _uint, _vp, _vp, _i64, _dbl, _vp]),

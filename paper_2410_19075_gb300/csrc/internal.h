@@ -55,7 +55,9 @@ struct RingPlan {
     // unsigned, and t >> 54 signed) in 32-bit words, exact because no sum of
     // chunks over at most 8192 sub-tiles reaches 2^31; the next kernel's CTAs
     // sum those themselves, so no CTA waits for the last one of its launch.
-    int flat;
+    int flat;             // requires npt == 2
+    int npt;              // nodes per thread of the stage kernels: 2 (128 threads per sub-tile;
+                          // not HH) or 1 (256); set by sim_create and the autotuner
     int64_t *fsub[2];     // NQ * nsub each: sub-tile totals (same parity as lam)
     unsigned *facc[4];    // NQ * ngroups * 4 each: group accumulators of stage slot s & 3
     unsigned long long *flat_ctr; // arrival counter of the one-pass kernels that record or count steps
@@ -71,6 +73,7 @@ struct RingBatchGroup {
     const RingPlan *plans;  // n_inst plans (device)
     const int *inst_of_item; // n_items (device)
     const int64_t *item_base; // n_inst: first item of each member (device)
+    int npt;                  // nodes per thread of the batched stage kernels (1, or 2 if not HH)
 };
 
 // Batched ring stage kernels: one RK4 step of every member of the group.

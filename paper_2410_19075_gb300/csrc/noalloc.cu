@@ -157,6 +157,7 @@ extern "C" int sim_ring_step_noalloc(int model, int64_t N, int64_t radius, const
 
     RingPlan p{};
     p.model = model;
+    p.npt = model == SIM_HH ? 1 : 2;
     p.N = N;
     p.R = radius;
     p.nsub = (N + kSubTile - 1) / kSubTile;

@@ -16,9 +16,9 @@
 //       sub-tile totals and group accumulators the next kernel sums itself;
 //   a6  (stage 4) the Kuramoto order parameter of y_{n+1} from the global totals.
 // The prologue kernel does a1/a2/a6 for the initial state.  The Kuramoto and
-// FHN rings run ring_stage_kernel2 (two adjacent nodes per thread); HH runs
-// ring_stage_kernel (one node per thread).  The building blocks are in
-// ring_parts.cuh.
+// FHN rings run ring_stage_kernel2 (two adjacent nodes per thread) unless the
+// autotuner chose ring_stage_kernel (one node per thread), which HH always
+// runs.  The building blocks are in ring_parts.cuh.
 #include "ring_parts.cuh"
 
 namespace simk {
@@ -238,24 +238,24 @@ __global__ void __launch_bounds__(kRing2Threads, SIM_RING2_MIN_BLOCKS)
     ring_stage_body2<M, STAGE>(p, stage_io<M, STAGE>(p), h, (int64_t)blockIdx.x - item_base[inst]);
 }
 
-#ifndef SIM_RING_NPT
-#define SIM_RING_NPT 2
-#endif
-
+// The kernel variant is the plan's (p.npt, from sim_create or the autotuner):
+// two nodes per thread (128 threads per sub-tile) or one (256).
 template <int M>
 static cudaError_t launch_stage(int stage, const RingPlan &p, double dt, cudaStream_t s)
 {
     const dim3 grid((unsigned)p.nsub), block(kRingThreads);
-    if constexpr (SIM_RING_NPT == 2 && M != 2) {
-        const dim3 block2(kRing2Threads);
-        switch (stage) {
-        case 0: ring_stage_kernel2<M, 0><<<grid, block2, 0, s>>>(p, step_size(dt)); break;
-        case 1: ring_stage_kernel2<M, 1><<<grid, block2, 0, s>>>(p, step_size(dt)); break;
-        case 2: ring_stage_kernel2<M, 2><<<grid, block2, 0, s>>>(p, step_size(dt)); break;
-        case 3: ring_stage_kernel2<M, 3><<<grid, block2, 0, s>>>(p, step_size(dt)); break;
-        default: ring_stage_kernel2<M, 4><<<grid, block2, 0, s>>>(p, step_size(dt)); break;
+    if constexpr (M != 2) {
+        if (p.npt == 2) {
+            const dim3 block2(kRing2Threads);
+            switch (stage) {
+            case 0: ring_stage_kernel2<M, 0><<<grid, block2, 0, s>>>(p, step_size(dt)); break;
+            case 1: ring_stage_kernel2<M, 1><<<grid, block2, 0, s>>>(p, step_size(dt)); break;
+            case 2: ring_stage_kernel2<M, 2><<<grid, block2, 0, s>>>(p, step_size(dt)); break;
+            case 3: ring_stage_kernel2<M, 3><<<grid, block2, 0, s>>>(p, step_size(dt)); break;
+            default: ring_stage_kernel2<M, 4><<<grid, block2, 0, s>>>(p, step_size(dt)); break;
+            }
+            return cudaGetLastError();
         }
-        return cudaGetLastError();
     }
     switch (stage) {
     case 0: ring_stage_kernel<M, 0><<<grid, block, 0, s>>>(p, step_size(dt)); break;
@@ -282,15 +282,17 @@ static cudaError_t launch_batch_stage(int stage, const RingBatchGroup &g, double
 {
     const dim3 grid((unsigned)g.n_items), block(kRingThreads);
     const StepSize h = step_size(dt);
-    if constexpr (SIM_RING_NPT == 2 && M != 2) {
-        const dim3 block2(kRing2Threads);
-        switch (stage) {
-        case 1: ring_batch_stage_kernel2<M, 1><<<grid, block2, 0, s>>>(g.plans, g.inst_of_item, g.item_base, h); break;
-        case 2: ring_batch_stage_kernel2<M, 2><<<grid, block2, 0, s>>>(g.plans, g.inst_of_item, g.item_base, h); break;
-        case 3: ring_batch_stage_kernel2<M, 3><<<grid, block2, 0, s>>>(g.plans, g.inst_of_item, g.item_base, h); break;
-        default: ring_batch_stage_kernel2<M, 4><<<grid, block2, 0, s>>>(g.plans, g.inst_of_item, g.item_base, h); break;
+    if constexpr (M != 2) {
+        if (g.npt == 2) {
+            const dim3 block2(kRing2Threads);
+            switch (stage) {
+            case 1: ring_batch_stage_kernel2<M, 1><<<grid, block2, 0, s>>>(g.plans, g.inst_of_item, g.item_base, h); break;
+            case 2: ring_batch_stage_kernel2<M, 2><<<grid, block2, 0, s>>>(g.plans, g.inst_of_item, g.item_base, h); break;
+            case 3: ring_batch_stage_kernel2<M, 3><<<grid, block2, 0, s>>>(g.plans, g.inst_of_item, g.item_base, h); break;
+            default: ring_batch_stage_kernel2<M, 4><<<grid, block2, 0, s>>>(g.plans, g.inst_of_item, g.item_base, h); break;
+            }
+            return cudaGetLastError();
         }
-        return cudaGetLastError();
     }
     switch (stage) {
     case 1: ring_batch_stage_kernel<M, 1><<<grid, block, 0, s>>>(g.plans, g.inst_of_item, g.item_base, h); break;

@@ -95,6 +95,40 @@ bool ring_flat_eligible(int model, int64_t ngroups)
     return model != SIM_HH && ngroups <= kFlatMaxGroups;
 }
 
+// Autotuner cache (process-wide): the kernel variant that measured fastest for
+// a plain ring (kind 0: model, N, R) or for a batch (kind 1: the ring members'
+// sub-tile count and member count).  sim_create and sim_batch_create apply a
+// matching entry; sim_autotune and sim_batch_autotune add entries;
+// sim_tune_save / sim_tune_load keep them in a text file.
+struct TuneKey {
+    int kind, model;
+    int64_t a, b;
+    bool operator<(const TuneKey &o) const
+    {
+        return kind != o.kind ? kind < o.kind : model != o.model ? model < o.model : a != o.a ? a < o.a : b < o.b;
+    }
+};
+struct TuneVal {
+    int npt, flat;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneVal> g_tune;
+
+bool tune_lookup(const TuneKey &k, TuneVal *v)
+{
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune.find(k);
+    if (it == g_tune.end()) return false;
+    *v = it->second;
+    return true;
+}
+
+void tune_store(const TuneKey &k, const TuneVal &v)
+{
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune[k] = v;
+}
+
 // Byte layout of a network's device block.  Each entry is an offset.
 struct Layout {
     size_t total = 0;
@@ -457,6 +491,12 @@ static int create_impl(sim_t *out, int model, int topology, int64_t N, int64_t r
         p.obs_cap = kObsCap;
         p.obs_ctr = h->obs_ctr;
         p.flat = ring_flat_eligible(model, p.ngroups) ? 1 : 0;
+        p.npt = model == SIM_HH ? 1 : 2;
+        TuneVal tv;
+        if (model != SIM_HH && tune_lookup(TuneKey{0, model, N, radius}, &tv)) {
+            p.npt = tv.npt == 1 ? 1 : 2;
+            p.flat = p.flat && tv.flat && p.npt == 2 ? 1 : 0;
+        }
         if (p.flat) {
             const size_t slot = 4 * (size_t)model_nq(model) * p.ngroups;
             p.fsub[0] = reinterpret_cast<int64_t *>(b + L.fsub0);
@@ -940,6 +980,21 @@ cudaError_t batch_launch_steps(sim_batch_t b, int64_t n, double dt, cudaStream_t
     return e;
 }
 
+// Autotuner key of a batch: its ring members' sub-tile count and member count.
+TuneKey batch_tune_key(sim_batch_t b, size_t n_items)
+{
+    int64_t rings = 0;
+    for (int s : b->ring_slot) rings += s >= 0;
+    return TuneKey{1, -1, (int64_t)n_items, rings};
+}
+
+void clear_batch_graphs(sim_batch_t b)
+{
+    for (auto &kv : b->graphs) cudaGraphExecDestroy(kv.second);
+    b->graphs.clear();
+    b->uses.clear();
+}
+
 int batch_graph(sim_batch_t b, double dt, int chunk, cudaGraphExec_t *out)
 {
     auto it = b->graphs.find({dt, chunk});
@@ -1066,6 +1121,9 @@ int sim_batch_create(sim_batch_t *out, const sim_t *members, int n_members, void
         g.plans = reinterpret_cast<const RingPlan *>(blk + o_plans) + gs.plan0;
         g.inst_of_item = reinterpret_cast<const int *>(blk + o_items) + gs.item0;
         g.item_base = reinterpret_cast<const int64_t *>(blk + o_base) + gs.plan0;
+        g.npt = gs.model == SIM_HH ? 1 : 2;
+        TuneVal tv;
+        if (gs.model != SIM_HH && tune_lookup(batch_tune_key(b, nitem), &tv)) g.npt = tv.npt == 1 ? 1 : 2;
         b->groups.push_back(g);
     }
     *out = b;
@@ -1561,3 +1619,264 @@ int sim_batch_dp5(sim_batch_t b, const sim_dp5_opts *opts, sim_dp5_stats *stats)
 
 } // extern "C"
 
+
+// ----------------------------------------------------------------------------- autotuner
+namespace {
+
+void clear_graphs(sim_t h)
+{
+    for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
+    h->graphs.clear();
+}
+
+// Recompute the prefix buffers of f(y) of any member without recording R.
+cudaError_t quiet_prologue(sim_t h, cudaStream_t s)
+{
+    if (h->topo == SIM_RING) return ring_refresh(h, s);
+    if (ring_like(h)) {
+        RingPlan quiet = h->ring;
+        quiet.obs = nullptr;
+        return ring_prologue(quiet, s);
+    }
+    LatticePlan quiet = h->lat;
+    quiet.obs = nullptr;
+    return lattice_prologue(quiet, s);
+}
+
+double *state_of(sim_t h) { return ring_like(h) ? h->ring.y : h->lat.y; }
+
+// Device time of `launches` launches of a captured graph after one warm-up launch.
+cudaError_t time_graph(cudaGraphExec_t ex, int64_t launches, cudaStream_t s, float *ms)
+{
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaError_t e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    if (e == cudaSuccess) e = cudaGraphLaunch(ex, s);
+    if (e == cudaSuccess) e = cudaEventRecord(a, s);
+    for (int64_t k = 0; k < launches && e == cudaSuccess; ++k) e = cudaGraphLaunch(ex, s);
+    if (e == cudaSuccess) e = cudaEventRecord(b, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, a, b);
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    return e;
+}
+
+} // namespace
+
+extern "C" {
+
+int sim_autotune(sim_t h, double dt, int64_t trial_steps, int *npt_out, int *flat_out)
+{
+    if (!h) return fail(SIM_EINVAL, "NULL handle");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(SIM_EINVAL, "dt must be finite and > 0");
+    if (trial_steps < 1) return fail(SIM_EINVAL, "trial_steps must be >= 1");
+    auto report = [&] {
+        if (npt_out) *npt_out = h->topo == SIM_RING ? h->ring.npt : 0;
+        if (flat_out) *flat_out = h->topo == SIM_RING ? h->ring.flat : 0;
+        return SIM_OK;
+    };
+    // only the stage kernels of rings have variants (HH: one node per thread)
+    if (h->topo != SIM_RING || h->model == SIM_HH || use_cluster(h)) return report();
+    std::vector<TuneVal> cand;
+    if (ring_flat_eligible(h->model, h->ring.ngroups)) cand.push_back({2, 1});
+    cand.push_back({2, 0});
+    cand.push_back({1, 0});
+    const size_t ybytes = sizeof(double) * h->d * h->nodes;
+    void *save = nullptr;
+    cudaError_t e = cudaMallocAsync(&save, ybytes, h->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SIM_ENOMEM, "autotune: no room for a copy of the state");
+    }
+    e = cudaMemcpyAsync(save, h->ring.y, ybytes, cudaMemcpyDeviceToDevice, h->stream);
+    const int chunk = trial_steps >= kGraphChunk ? kGraphChunk : 1;
+    const int64_t launches = (trial_steps + chunk - 1) / chunk;
+    float best = 0.0f;
+    TuneVal pick = cand[0];
+    int st = SIM_OK;
+    for (size_t c = 0; c < cand.size() && e == cudaSuccess && st == SIM_OK; ++c) {
+        h->ring.npt = cand[c].npt;
+        h->ring.flat = cand[c].flat;
+        clear_graphs(h);
+        e = cudaMemcpyAsync(h->ring.y, save, ybytes, cudaMemcpyDeviceToDevice, h->stream);
+        if (e == cudaSuccess) e = ring_refresh(h, h->stream);
+        cudaGraphExec_t ex = nullptr;
+        if (e == cudaSuccess) st = get_graph(h, dt, chunk, &ex);
+        float ms = 0.0f;
+        if (e == cudaSuccess && st == SIM_OK) e = time_graph(ex, launches, h->stream, &ms);
+        if (e == cudaSuccess && st == SIM_OK && (c == 0 || ms < best)) {
+            best = ms;
+            pick = cand[c];
+        }
+    }
+    h->ring.npt = pick.npt;
+    h->ring.flat = pick.flat;
+    clear_graphs(h);
+    // the state as it was; prefix buffers, counters and R(t0) as after sim_set_state
+    const cudaError_t e2 = cudaMemcpyAsync(h->ring.y, save, ybytes, cudaMemcpyDeviceToDevice, h->stream);
+    cudaFreeAsync(save, h->stream);
+    if (e == cudaSuccess) e = e2;
+    if (e != cudaSuccess) return cuda_fail(e, "autotune");
+    if (st != SIM_OK) return st;
+    const int r = prologue(h);
+    if (r != SIM_OK) return r;
+    tune_store(TuneKey{0, h->model, h->N, h->R}, pick);
+    return report();
+}
+
+int sim_tune_info(sim_t h, int *npt, int *flat)
+{
+    if (!h || !npt || !flat) return fail(SIM_EINVAL, "NULL argument");
+    *npt = h->topo == SIM_RING ? h->ring.npt : 0;
+    *flat = h->topo == SIM_RING ? h->ring.flat : 0;
+    return SIM_OK;
+}
+
+int sim_batch_autotune(sim_batch_t b, double dt, int64_t trial_steps, int *npt_out)
+{
+    if (!b) return fail(SIM_EINVAL, "NULL batch");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(SIM_EINVAL, "dt must be finite and > 0");
+    if (trial_steps < 1) return fail(SIM_EINVAL, "trial_steps must be >= 1");
+    bool variants = false;
+    size_t n_items = 0;
+    for (const RingBatchGroup &g : b->groups) {
+        variants = variants || g.model != SIM_HH;
+        n_items += (size_t)g.n_items;
+    }
+    auto report = [&] {
+        int v = 1;
+        for (const RingBatchGroup &g : b->groups)
+            if (g.model != SIM_HH) v = g.npt;
+        if (npt_out) *npt_out = v;
+        return SIM_OK;
+    };
+    if (!variants) return report();
+    cudaStream_t s = b->stream;
+    const int n = (int)b->members.size();
+    // everything the trial steps change: states, error words, order-parameter
+    // counters and step budgets
+    std::vector<size_t> at(n + 1, 0);
+    for (int i = 0; i < n; ++i)
+        at[i + 1] = at[i] + align_up(sizeof(double) * b->members[i]->d * b->members[i]->nodes);
+    size_t nplan = 0;
+    for (const RingBatchGroup &g : b->groups) nplan += (size_t)g.n_inst;
+    const size_t o_err = at[n], o_ctr = align_up(o_err + sizeof(unsigned) * n);
+    const size_t o_bud = align_up(o_ctr + sizeof(unsigned long long) * n);
+    const size_t total = o_bud + sizeof(long long) * nplan;
+    char *save = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&save), total, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SIM_ENOMEM, "autotune: no room for a copy of the members' states");
+    }
+    auto copy_all = [&](bool to_save) {
+        cudaError_t r = cudaSuccess;
+        for (int i = 0; i < n && r == cudaSuccess; ++i) {
+            sim_t h = b->members[i];
+            const size_t yb = sizeof(double) * h->d * h->nodes;
+            double *y = state_of(h);
+            r = to_save ? cudaMemcpyAsync(save + at[i], y, yb, cudaMemcpyDeviceToDevice, s)
+                        : cudaMemcpyAsync(y, save + at[i], yb, cudaMemcpyDeviceToDevice, s);
+            if (r == cudaSuccess)
+                r = to_save ? cudaMemcpyAsync(save + o_err + sizeof(unsigned) * i, h->err, sizeof(unsigned),
+                                              cudaMemcpyDeviceToDevice, s)
+                            : cudaMemcpyAsync(h->err, save + o_err + sizeof(unsigned) * i, sizeof(unsigned),
+                                              cudaMemcpyDeviceToDevice, s);
+            if (r == cudaSuccess)
+                r = to_save ? cudaMemcpyAsync(save + o_ctr + 8 * i, h->obs_ctr, 8, cudaMemcpyDeviceToDevice, s)
+                            : cudaMemcpyAsync(h->obs_ctr, save + o_ctr + 8 * i, 8, cudaMemcpyDeviceToDevice, s);
+        }
+        if (r == cudaSuccess && nplan)
+            r = to_save ? cudaMemcpyAsync(save + o_bud, b->budgets, sizeof(long long) * nplan, cudaMemcpyDeviceToDevice, s)
+                        : cudaMemcpyAsync(b->budgets, save + o_bud, sizeof(long long) * nplan, cudaMemcpyDeviceToDevice, s);
+        for (int i = 0; i < n && r == cudaSuccess; ++i)
+            if (!to_save) r = quiet_prologue(b->members[i], s);
+        return r;
+    };
+    e = copy_all(true);
+    float best = 0.0f;
+    int pick = 2;
+    const int cands[2] = {2, 1};
+    for (int c = 0; c < 2 && e == cudaSuccess; ++c) {
+        for (RingBatchGroup &g : b->groups)
+            if (g.model != SIM_HH) g.npt = cands[c];
+        clear_batch_graphs(b);
+        e = copy_all(false);
+        cudaEvent_t ea = nullptr, eb = nullptr;
+        if (e == cudaSuccess) e = cudaEventCreate(&ea);
+        if (e == cudaSuccess) e = cudaEventCreate(&eb);
+        if (e == cudaSuccess) e = batch_launch_steps(b, 1, dt, s); // warm-up
+        if (e == cudaSuccess) e = cudaEventRecord(ea, s);
+        if (e == cudaSuccess) e = batch_launch_steps(b, trial_steps, dt, s);
+        if (e == cudaSuccess) e = cudaEventRecord(eb, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(eb);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ea, eb);
+        if (ea) cudaEventDestroy(ea);
+        if (eb) cudaEventDestroy(eb);
+        if (e == cudaSuccess && (c == 0 || ms < best)) {
+            best = ms;
+            pick = cands[c];
+        }
+    }
+    for (RingBatchGroup &g : b->groups)
+        if (g.model != SIM_HH) g.npt = pick;
+    clear_batch_graphs(b);
+    const cudaError_t e2 = copy_all(false);
+    cudaFreeAsync(save, s);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "batch autotune");
+    tune_store(batch_tune_key(b, n_items), TuneVal{pick, 0});
+    return report();
+}
+
+int sim_tune_save(const char *path)
+{
+    if (!path) return fail(SIM_EINVAL, "NULL path");
+    FILE *f = std::fopen(path, "w");
+    if (!f) return fail(SIM_EINVAL, std::string("cannot write ") + path);
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    std::fprintf(f, "# kind model a b npt flat\n");
+    for (const auto &kv : g_tune)
+        std::fprintf(f, "%d %d %lld %lld %d %d\n", kv.first.kind, kv.first.model, (long long)kv.first.a,
+                     (long long)kv.first.b, kv.second.npt, kv.second.flat);
+    const bool ok = std::fclose(f) == 0;
+    return ok ? SIM_OK : fail(SIM_EINVAL, std::string("cannot write ") + path);
+}
+
+int sim_tune_load(const char *path)
+{
+    if (!path) return fail(SIM_EINVAL, "NULL path");
+    FILE *f = std::fopen(path, "r");
+    if (!f) return fail(SIM_EINVAL, std::string("cannot read ") + path);
+    char line[256];
+    int st = SIM_OK;
+    std::map<TuneKey, TuneVal> read;
+    while (std::fgets(line, sizeof line, f)) {
+        if (line[0] == '#' || line[0] == '\n') continue;
+        int kind, model, npt, flat;
+        long long a, bb;
+        if (std::sscanf(line, "%d %d %lld %lld %d %d", &kind, &model, &a, &bb, &npt, &flat) != 6 ||
+            (kind != 0 && kind != 1) || (npt != 1 && npt != 2) || (flat != 0 && flat != 1)) {
+            st = fail(SIM_EINVAL, std::string("malformed line in ") + path);
+            break;
+        }
+        read[TuneKey{kind, model, a, bb}] = TuneVal{npt, flat};
+    }
+    std::fclose(f);
+    if (st != SIM_OK) return st;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    for (const auto &kv : read) g_tune[kv.first] = kv.second;
+    return SIM_OK;
+}
+
+int sim_tune_clear(void)
+{
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune.clear();
+    return SIM_OK;
+}
+
+} // extern "C"

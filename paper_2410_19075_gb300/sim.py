@@ -45,6 +45,20 @@ def _dp5_stats(s):
             "status": int(s.status)}
 
 
+def tune_save(path: str):
+    """Write the autotuner cache (``sim_tune_save``)."""
+    check(lib().sim_tune_save(str(path).encode()))
+
+
+def tune_load(path: str):
+    """Merge a saved autotuner cache into this process's (``sim_tune_load``)."""
+    check(lib().sim_tune_load(str(path).encode()))
+
+
+def tune_clear():
+    check(lib().sim_tune_clear())
+
+
 def workspace_bytes(model, topology, N, radius) -> int:
     return int(lib().sim_workspace_bytes(model, topology, N, radius))
 
@@ -151,6 +165,18 @@ class Network:
     def sync(self):
         check(lib().sim_sync(self._handle()))
 
+    def autotune(self, dt: float = 0.01, trial_steps: int = 32) -> dict:
+        """Time the kernel variants on the current state, keep the fastest
+        (``sim_autotune``); the state is unchanged, R(t0) is recorded again."""
+        npt, flat = ctypes.c_int(0), ctypes.c_int(0)
+        check(lib().sim_autotune(self._handle(), float(dt), int(trial_steps), ctypes.byref(npt), ctypes.byref(flat)))
+        return {"npt": npt.value, "flat": flat.value}
+
+    def tune_info(self) -> dict:
+        npt, flat = ctypes.c_int(0), ctypes.c_int(0)
+        check(lib().sim_tune_info(self._handle(), ctypes.byref(npt), ctypes.byref(flat)))
+        return {"npt": npt.value, "flat": flat.value}
+
     @property
     def steps_done(self) -> int:
         return int(lib().sim_steps_done(self._handle()))
@@ -193,6 +219,13 @@ class Batch:
 
     def sync(self):
         check(lib().sim_batch_sync(self._h))
+
+    def autotune(self, dt: float = 0.01, trial_steps: int = 16) -> int:
+        """Time one and two nodes per thread for the ring groups, keep the faster
+        (``sim_batch_autotune``); members' states and budgets are unchanged."""
+        npt = ctypes.c_int(0)
+        check(lib().sim_batch_autotune(self._h, float(dt), int(trial_steps), ctypes.byref(npt)))
+        return npt.value
 
     def dp5(self, opts):
         """Dormand-Prince runs of every member; opts is one dict per member with the
