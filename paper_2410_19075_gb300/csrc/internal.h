@@ -228,6 +228,23 @@ cudaError_t lattice_prologue(const LatticePlan &p, cudaStream_t s);
 cudaError_t lattice_step(const LatticePlan &p, double dt, cudaStream_t s);
 cudaError_t lattice_rhs(const LatticePlan &p, cudaStream_t s); // acc <- f(y)
 
+// Cube members of one model in a batch: device tables of the batched x, y and z
+// launches (lattice.cu).  x: CTA b does rows of member x_item[b] (w warps, one
+// row each, counted from x_base[member]); y and z: CTA b is the member's CTA
+// b - yz_base[member] of its single-network column grid.
+struct CubeBatchGroup {
+    int model;
+    int n_inst;
+    int w;                    // warps per x CTA (for the largest edge)
+    int64_t n1_max;           // largest edge (sizes the x pass's shared rows)
+    int64_t n_x, n_yz;        // CTAs of the x and of the y / z launches
+    const LatticePlan *plans; // n_inst (device)
+    const int *x_item, *yz_item;
+    const int64_t *x_base, *yz_base; // n_inst each
+};
+cudaError_t cube_batch_step(const CubeBatchGroup &g, double dt, cudaStream_t s); // one RK4 step of every member
+int lattice_row_warps(int64_t N1); // warps per CTA of the x pass for edge N1
+
 // Host-side values of the fast-math tables (long double, rounded to double).
 void fill_math_tables(double *sincos /* 2 * kSinTab */, double *exp2j /* kExpTab */);
 

@@ -48,109 +48,137 @@ static int row_warps(int64_t N1)
 //   MODE 2 (ball, disk)  for every half-width w = 0..P the window sums
 //                        S_w(i) = Pe(i+w+1) - Pe(i-w), (sin, cos) pairs, one
 //                        array of nodes pairs per w.
+// One row of the x pass (one warp; pre0/pre1 its shared prefix rows).
+template <int MODE>
+__device__ __forceinline__ void lattice_x_row(const LatticePlan &p, int64_t row, int64_t *pre0, int64_t *pre1,
+                                              bool &ok)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t N1 = p.N1, P = p.P, nodes = p.nodes;
+    const int per = (int)((N1 + 31) / 32);
+    const double *__restrict__ fs = p.f + row * N1;
+    const double *__restrict__ fc = p.f + nodes + row * N1;
+    for (int64_t mb = lane; mb < N1; mb += 32 * 8) { // coalesced, 8 loads in flight per lane
+        double vs[8], vc[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int64_t m = mb + 32 * u;
+            vs[u] = m < N1 ? __ldg(fs + m) : 0.0;
+            vc[u] = m < N1 ? __ldg(fc + m) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int64_t m = mb + 32 * u;
+            if (m < N1) {
+                pre0[m + 1] = to_fixed(vs[u], p.F, 1, ok);
+                pre1[m + 1] = to_fixed(vc[u], p.F, 1, ok);
+            }
+        }
+    }
+    __syncwarp();
+    const int m0 = lane * per;
+    uint64_t r0 = 0, r1 = 0; // wrapping sums
+    for (int t = 0; t < per; ++t) {
+        const int m = m0 + t;
+        if (m < N1) {
+            r0 += (uint64_t)pre0[m + 1];
+            r1 += (uint64_t)pre1[m + 1];
+            pre0[m + 1] = (int64_t)r0;
+            pre1[m + 1] = (int64_t)r1;
+        }
+    }
+    const uint64_t e0 = (uint64_t)warp_incl_scan((int64_t)r0) - r0;
+    const uint64_t e1 = (uint64_t)warp_incl_scan((int64_t)r1) - r1;
+    for (int t = 0; t < per; ++t) {
+        const int m = m0 + t;
+        if (m < N1) {
+            pre0[m + 1] = (int64_t)((uint64_t)pre0[m + 1] + e0);
+            pre1[m + 1] = (int64_t)((uint64_t)pre1[m + 1] + e1);
+        }
+    }
+    if (lane == 0) {
+        pre0[0] = 0;
+        pre1[0] = 0;
+    }
+    __syncwarp();
+    if (MODE == 2) {
+        const int64_t t0 = pre0[N1], t1 = pre1[N1];
+        longlong2 *__restrict__ o = reinterpret_cast<longlong2 *>(p.sx) + row * N1;
+        for (int64_t w = 0; w <= P; ++w, o += nodes) {
+            for (int64_t i = lane; i < N1; i += 32) {
+                int64_t b = i + w + 1, a = i - w;
+                int64_t s0 = 0, s1 = 0;
+                if (b > N1) { b -= N1; s0 += t0; s1 += t1; }
+                if (a < 0) { a += N1; s0 += t0; s1 += t1; } // Pe(a) = pre(a+N1) - total
+                o[i] = make_longlong2(s0 + pre0[b] - pre0[a], s1 + pre1[b] - pre1[a]);
+            }
+        }
+    } else if (MODE == 1) {
+        // E(x) = Pe(x + 1) for x in [-P-1, N1+P-1], at slot x + P + 1
+        const uint64_t t0 = (uint64_t)pre0[N1], t1 = (uint64_t)pre1[N1];
+        longlong2 *__restrict__ o = reinterpret_cast<longlong2 *>(p.sx) + row * p.rs;
+        for (int64_t e = lane; e < p.rs; e += 32) {
+            int64_t q = e - P; // = x + 1, in [-P, N1 + P]
+            uint64_t v0, v1;
+            if (q < 0) {
+                v0 = (uint64_t)pre0[q + N1] - t0;
+                v1 = (uint64_t)pre1[q + N1] - t1;
+            } else if (q > N1) {
+                v0 = (uint64_t)pre0[q - N1] + t0;
+                v1 = (uint64_t)pre1[q - N1] + t1;
+            } else {
+                v0 = (uint64_t)pre0[q];
+                v1 = (uint64_t)pre1[q];
+            }
+            o[e] = make_longlong2((long long)v0, (long long)v1);
+        }
+    } else {
+        int64_t *__restrict__ o0 = p.sx + row * N1;
+        int64_t *__restrict__ o1 = p.sx + nodes + row * N1;
+        const int64_t t0 = pre0[N1], t1 = pre1[N1];
+        for (int64_t i = lane; i < N1; i += 32) {
+            int64_t b = i + P + 1, a = i - P;
+            int64_t s0 = 0, s1 = 0;
+            if (b > N1) { b -= N1; s0 += t0; s1 += t1; }
+            if (a < 0) { a += N1; s0 += t0; s1 += t1; } // Pe(a) = pre(a+N1) - total
+            o0[i] = s0 + pre0[b] - pre0[a];
+            o1[i] = s1 + pre1[b] - pre1[a];
+        }
+    }
+    __syncwarp();
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(32 * kRowWarpsMax) lattice_x_kernel(LatticePlan p)
 {
     if (p.skip && *(const volatile int *)p.skip) return;
     extern __shared__ int64_t smem[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-    const int64_t N1 = p.N1, P = p.P, nodes = p.nodes, stride = N1 + 1, rows = nodes / N1;
+    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int64_t stride = p.N1 + 1, rows = p.nodes / p.N1;
     int64_t *pre0 = smem + (int64_t)warp * 2 * stride;
     int64_t *pre1 = pre0 + stride;
-    const int per = (int)((N1 + 31) / 32);
     bool ok = true;
-    for (int64_t row = (int64_t)blockIdx.x * nwarps + warp; row < rows; row += (int64_t)gridDim.x * nwarps) {
-        const double *__restrict__ fs = p.f + row * N1;
-        const double *__restrict__ fc = p.f + nodes + row * N1;
-        for (int64_t mb = lane; mb < N1; mb += 32 * 8) { // coalesced, 8 loads in flight per lane
-            double vs[8], vc[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int64_t m = mb + 32 * u;
-                vs[u] = m < N1 ? __ldg(fs + m) : 0.0;
-                vc[u] = m < N1 ? __ldg(fc + m) : 0.0;
-            }
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int64_t m = mb + 32 * u;
-                if (m < N1) {
-                    pre0[m + 1] = to_fixed(vs[u], p.F, 1, ok);
-                    pre1[m + 1] = to_fixed(vc[u], p.F, 1, ok);
-                }
-            }
-        }
-        __syncwarp();
-        const int m0 = lane * per;
-        uint64_t r0 = 0, r1 = 0; // wrapping sums
-        for (int t = 0; t < per; ++t) {
-            const int m = m0 + t;
-            if (m < N1) {
-                r0 += (uint64_t)pre0[m + 1];
-                r1 += (uint64_t)pre1[m + 1];
-                pre0[m + 1] = (int64_t)r0;
-                pre1[m + 1] = (int64_t)r1;
-            }
-        }
-        const uint64_t e0 = (uint64_t)warp_incl_scan((int64_t)r0) - r0;
-        const uint64_t e1 = (uint64_t)warp_incl_scan((int64_t)r1) - r1;
-        for (int t = 0; t < per; ++t) {
-            const int m = m0 + t;
-            if (m < N1) {
-                pre0[m + 1] = (int64_t)((uint64_t)pre0[m + 1] + e0);
-                pre1[m + 1] = (int64_t)((uint64_t)pre1[m + 1] + e1);
-            }
-        }
-        if (lane == 0) {
-            pre0[0] = 0;
-            pre1[0] = 0;
-        }
-        __syncwarp();
-        if (MODE == 2) {
-            const int64_t t0 = pre0[N1], t1 = pre1[N1];
-            longlong2 *__restrict__ o = reinterpret_cast<longlong2 *>(p.sx) + row * N1;
-            for (int64_t w = 0; w <= P; ++w, o += nodes) {
-                for (int64_t i = lane; i < N1; i += 32) {
-                    int64_t b = i + w + 1, a = i - w;
-                    int64_t s0 = 0, s1 = 0;
-                    if (b > N1) { b -= N1; s0 += t0; s1 += t1; }
-                    if (a < 0) { a += N1; s0 += t0; s1 += t1; } // Pe(a) = pre(a+N1) - total
-                    o[i] = make_longlong2(s0 + pre0[b] - pre0[a], s1 + pre1[b] - pre1[a]);
-                }
-            }
-        } else if (MODE == 1) {
-            // E(x) = Pe(x + 1) for x in [-P-1, N1+P-1], at slot x + P + 1
-            const uint64_t t0 = (uint64_t)pre0[N1], t1 = (uint64_t)pre1[N1];
-            longlong2 *__restrict__ o = reinterpret_cast<longlong2 *>(p.sx) + row * p.rs;
-            for (int64_t e = lane; e < p.rs; e += 32) {
-                int64_t q = e - P; // = x + 1, in [-P, N1 + P]
-                uint64_t v0, v1;
-                if (q < 0) {
-                    v0 = (uint64_t)pre0[q + N1] - t0;
-                    v1 = (uint64_t)pre1[q + N1] - t1;
-                } else if (q > N1) {
-                    v0 = (uint64_t)pre0[q - N1] + t0;
-                    v1 = (uint64_t)pre1[q - N1] + t1;
-                } else {
-                    v0 = (uint64_t)pre0[q];
-                    v1 = (uint64_t)pre1[q];
-                }
-                o[e] = make_longlong2((long long)v0, (long long)v1);
-            }
-        } else {
-            int64_t *__restrict__ o0 = p.sx + row * N1;
-            int64_t *__restrict__ o1 = p.sx + nodes + row * N1;
-            const int64_t t0 = pre0[N1], t1 = pre1[N1];
-            for (int64_t i = lane; i < N1; i += 32) {
-                int64_t b = i + P + 1, a = i - P;
-                int64_t s0 = 0, s1 = 0;
-                if (b > N1) { b -= N1; s0 += t0; s1 += t1; }
-                if (a < 0) { a += N1; s0 += t0; s1 += t1; } // Pe(a) = pre(a+N1) - total
-                o0[i] = s0 + pre0[b] - pre0[a];
-                o1[i] = s1 + pre1[b] - pre1[a];
-            }
-        }
-        __syncwarp();
-    }
+    for (int64_t row = (int64_t)blockIdx.x * nwarps + warp; row < rows; row += (int64_t)gridDim.x * nwarps)
+        lattice_x_row<MODE>(p, row, pre0, pre1, ok);
+    if (!ok) raise_error(p.err, ERR_RANGE);
+}
+
+// Batched cube x pass: CTA b works on rows (b - x_base[m]) * warps + warp of
+// member m = x_item[b]; shared memory is sized for the group's largest edge.
+__global__ void __launch_bounds__(32 * kRowWarpsMax)
+    cube_batch_x_kernel(const LatticePlan *__restrict__ plans, const int *__restrict__ x_item,
+                        const int64_t *__restrict__ x_base)
+{
+    const int inst = x_item[blockIdx.x];
+    const LatticePlan &p = plans[inst];
+    extern __shared__ int64_t smem[];
+    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int64_t stride = p.N1 + 1, rows = p.nodes / p.N1;
+    int64_t *pre0 = smem + (int64_t)warp * 2 * stride;
+    int64_t *pre1 = pre0 + stride;
+    const int64_t row = ((int64_t)blockIdx.x - x_base[inst]) * nwarps + warp;
+    bool ok = true;
+    if (row < rows) lattice_x_row<0>(p, row, pre0, pre1, ok); // uniform over the warp
     if (!ok) raise_error(p.err, ERR_RANGE);
 }
 
@@ -174,14 +202,11 @@ __host__ __device__ inline int64_t col_seg_len(int64_t N1)
 
 // cube y pass: one thread per segment of an (i, k) column, sliding window along
 // j (exact int64), 8 rows of window loads issued together.
-__global__ void __launch_bounds__(kColThreads) cube_y_kernel(LatticePlan p)
+__device__ __forceinline__ void cube_y_col(const LatticePlan &p, int64_t i, int64_t k, int64_t seg)
 {
-    if (p.skip && *(const volatile int *)p.skip) return;
     constexpr int U = 8;
     const int64_t N1 = p.N1, P = p.P, nodes = p.nodes;
-    const int64_t i = (int64_t)blockIdx.x * kColThreads + threadIdx.x;
-    const int64_t k = blockIdx.y;
-    const int64_t len = col_seg_len(N1), jb = (int64_t)blockIdx.z * len;
+    const int64_t len = col_seg_len(N1), jb = seg * len;
     const int64_t je = jb + len < N1 ? jb + len : N1;
     if (i >= N1 || jb >= N1) return;
     const int64_t col = k * N1 * N1 + i; // + j * N1
@@ -224,16 +249,43 @@ __global__ void __launch_bounds__(kColThreads) cube_y_kernel(LatticePlan p)
     }
 }
 
+__global__ void __launch_bounds__(kColThreads) cube_y_kernel(LatticePlan p)
+{
+    if (p.skip && *(const volatile int *)p.skip) return;
+    cube_y_col(p, (int64_t)blockIdx.x * kColThreads + threadIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// The (column block, plane, segment) of CTA b of a batched y or z pass: the
+// member's CTAs in the order of the single-network grid (x fastest).
+__device__ __forceinline__ void cube_col_item(const LatticePlan &p, int64_t lb, int64_t &bx, int64_t &plane,
+                                              int64_t &seg)
+{
+    const int64_t nbx = (p.N1 + kColThreads - 1) / kColThreads;
+    bx = lb % nbx;
+    plane = (lb / nbx) % p.N1;
+    seg = lb / (nbx * p.N1);
+}
+
+__global__ void __launch_bounds__(kColThreads)
+    cube_batch_y_kernel(const LatticePlan *__restrict__ plans, const int *__restrict__ yz_item,
+                        const int64_t *__restrict__ yz_base)
+{
+    const int inst = yz_item[blockIdx.x];
+    const LatticePlan &p = plans[inst];
+    int64_t bx, k, seg;
+    cube_col_item(p, (int64_t)blockIdx.x - yz_base[inst], bx, k, seg);
+    cube_y_col(p, bx * kColThreads + threadIdx.x, k, seg);
+}
+
 // Deterministic order parameter of the new state: per-CTA partial sums of the
 // fixed-point (sin, cos) (exact i128, so the reduction order does not matter),
-// and the last CTA to finish sums every partial and records R.
-__device__ void lattice_record_order(const LatticePlan &p, i128 ps, i128 pc)
+// and the last CTA to finish sums every partial and records R.  bid / nblk: the
+// CTA's index among the network's CTAs of this launch and their number.
+__device__ void lattice_record_order(const LatticePlan &p, i128 ps, i128 pc, unsigned bid, unsigned nblk)
 {
     __shared__ i128 s_ws[32], s_wc[32];
     __shared__ bool s_last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
-    const unsigned bid = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
     ps = warp_sum_i128(ps);
     pc = warp_sum_i128(pc);
     if (lane == 0) {
@@ -341,13 +393,12 @@ __device__ __forceinline__ void lattice_node(const LatticePlan &p, int64_t n, in
 // k, fused with the node update.  Also the prologue of the cube (STAGE 0, no
 // window).
 template <int M, int STAGE>
-__global__ void __launch_bounds__(kColThreads) cube_z_kernel(LatticePlan p, const StepSize h)
+__device__ __forceinline__ void cube_z_col(const LatticePlan &p, const StepSize &h, int64_t bx, int64_t j,
+                                           int64_t seg, unsigned bid, unsigned nblk)
 {
-    if (STAGE == 1 && p.skip && *(const volatile int *)p.skip) return; // stage 1 records nothing
     const int64_t N1 = p.N1, P = p.P, nodes = p.nodes, plane = N1 * N1;
-    const int64_t i = (int64_t)blockIdx.x * kColThreads + threadIdx.x;
-    const int64_t j = blockIdx.y;
-    const int64_t len = col_seg_len(N1), kb = (int64_t)blockIdx.z * len;
+    const int64_t i = bx * kColThreads + threadIdx.x;
+    const int64_t len = col_seg_len(N1), kb = seg * len;
     const int64_t ke = kb + len < N1 ? kb + len : N1;
     i128 ps = 0, pc = 0;
     bool ok = true;
@@ -377,7 +428,31 @@ __global__ void __launch_bounds__(kColThreads) cube_z_kernel(LatticePlan p, cons
         }
     }
     if (!ok) raise_error(p.err, ERR_RANGE);
-    if (STAGE == 0 || STAGE == 4) lattice_record_order(p, ps, pc);
+    if (STAGE == 0 || STAGE == 4) lattice_record_order(p, ps, pc, bid, nblk);
+}
+
+template <int M, int STAGE>
+__global__ void __launch_bounds__(kColThreads) cube_z_kernel(LatticePlan p, const StepSize h)
+{
+    if (STAGE == 1 && p.skip && *(const volatile int *)p.skip) return; // stage 1 records nothing
+    cube_z_col<M, STAGE>(p, h, blockIdx.x, blockIdx.y, blockIdx.z,
+                         (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x,
+                         gridDim.x * gridDim.y * gridDim.z);
+}
+
+// Batched cube z pass (stages 1-4): CTA b is CTA b - yz_base[m] of member m.
+template <int M, int STAGE>
+__global__ void __launch_bounds__(kColThreads)
+    cube_batch_z_kernel(const LatticePlan *__restrict__ plans, const int *__restrict__ yz_item,
+                        const int64_t *__restrict__ yz_base, const StepSize h)
+{
+    const int inst = yz_item[blockIdx.x];
+    const LatticePlan &p = plans[inst];
+    const int64_t lb = (int64_t)blockIdx.x - yz_base[inst];
+    int64_t bx, j, seg;
+    cube_col_item(p, lb, bx, j, seg);
+    const int64_t nbx = (p.N1 + kColThreads - 1) / kColThreads;
+    cube_z_col<M, STAGE>(p, h, bx, j, seg, (unsigned)lb, (unsigned)(nbx * p.N1 * col_segments(p.N1)));
 }
 
 // ball / disk gather: one node per thread; the window is the union of the chords
@@ -424,7 +499,7 @@ __global__ void __launch_bounds__(kGatherThreads) lattice_gather_kernel(LatticeP
         lattice_node<M, STAGE>(p, n, (int64_t)w0, (int64_t)w1, h, ok, ps, pc);
     }
     if (!ok) raise_error(p.err, ERR_RANGE);
-    if (STAGE == 0 || STAGE == 4) lattice_record_order(p, ps, pc);
+    if (STAGE == 0 || STAGE == 4) lattice_record_order(p, ps, pc, blockIdx.x, gridDim.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -462,7 +537,45 @@ cudaError_t lattice_configure()
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(lattice_x_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kRowSmemMax);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(cube_batch_x_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kRowSmemMax);
     return e;
+}
+
+int lattice_row_warps(int64_t N1) { return row_warps(N1); }
+
+// Batched cube members of one model: per RK4 stage one x, one y and one z
+// launch over all of them (each member with its own plan, prefix rows and
+// order-parameter counter), the same bits as lattice_step on each alone.
+template <int M>
+static cudaError_t cube_batch_stage(int stage, const CubeBatchGroup &g, double dt, cudaStream_t s)
+{
+    const size_t smem = (size_t)g.w * 2 * (size_t)(g.n1_max + 1) * sizeof(int64_t);
+    cube_batch_x_kernel<<<(unsigned)g.n_x, 32 * g.w, smem, s>>>(g.plans, g.x_item, g.x_base);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    cube_batch_y_kernel<<<(unsigned)g.n_yz, kColThreads, 0, s>>>(g.plans, g.yz_item, g.yz_base);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const StepSize h = step_size(dt);
+    const dim3 grid((unsigned)g.n_yz);
+    switch (stage) {
+    case 1: cube_batch_z_kernel<M, 1><<<grid, kColThreads, 0, s>>>(g.plans, g.yz_item, g.yz_base, h); break;
+    case 2: cube_batch_z_kernel<M, 2><<<grid, kColThreads, 0, s>>>(g.plans, g.yz_item, g.yz_base, h); break;
+    case 3: cube_batch_z_kernel<M, 3><<<grid, kColThreads, 0, s>>>(g.plans, g.yz_item, g.yz_base, h); break;
+    default: cube_batch_z_kernel<M, 4><<<grid, kColThreads, 0, s>>>(g.plans, g.yz_item, g.yz_base, h); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t cube_batch_step(const CubeBatchGroup &g, double dt, cudaStream_t s)
+{
+    if (g.n_x == 0) return cudaSuccess;
+    for (int stage = 1; stage <= 4; ++stage) {
+        const cudaError_t e = g.model == 3 ? cube_batch_stage<3>(stage, g, dt, s) : cube_batch_stage<0>(stage, g, dt, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 static cudaError_t launch_x(const LatticePlan &p, cudaStream_t s)

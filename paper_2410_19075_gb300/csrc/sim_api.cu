@@ -897,7 +897,8 @@ struct sim_batch_handle {
     std::vector<sim_t> members;
     std::vector<int> ring_slot;      // member -> index of its plan in the group tables (or -1)
     std::vector<RingBatchGroup> groups;
-    std::vector<sim_t> lattices;     // members stepped by their own kernels (lattices, link matrices)
+    std::vector<CubeBatchGroup> cube_groups; // cube members, by model
+    std::vector<sim_t> lattices;     // members stepped by their own kernels (ball, disk, link matrices)
     void *block = nullptr;           // device tables
     long long *budgets = nullptr;    // device: steps left per ring member (budgeted mode)
     std::vector<long long> host_budget; // host shadow, -1 = unlimited
@@ -933,19 +934,23 @@ constexpr int kLatticeBranches = 4;
 int n_branches(sim_batch_t b)
 {
     const int nc = (int)b->lattices.size();
-    return (int)b->groups.size() + (nc < kLatticeBranches ? nc : kLatticeBranches);
+    return (int)(b->groups.size() + b->cube_groups.size()) + (nc < kLatticeBranches ? nc : kLatticeBranches);
 }
 
-// n steps of branch k (a ring group, or every kLatticeBranches-th lattice) on stream s.
+// n steps of branch k (a ring group, a cube group, or every kLatticeBranches-th
+// other lattice) on stream s.
 cudaError_t branch_steps(sim_batch_t b, int k, int64_t n, double dt, cudaStream_t s)
 {
-    const int ng = (int)b->groups.size();
+    const int ng = (int)b->groups.size(), ncg = (int)b->cube_groups.size();
     for (int64_t t = 0; t < n; ++t) {
         if (k < ng) {
             const cudaError_t e = ring_batch_step(b->groups[k], dt, s);
             if (e != cudaSuccess) return e;
+        } else if (k < ng + ncg) {
+            const cudaError_t e = cube_batch_step(b->cube_groups[k - ng], dt, s);
+            if (e != cudaSuccess) return e;
         } else {
-            for (size_t c = (size_t)(k - ng); c < b->lattices.size(); c += kLatticeBranches) {
+            for (size_t c = (size_t)(k - ng - ncg); c < b->lattices.size(); c += kLatticeBranches) {
                 const sim_t m = b->lattices[c];
                 const cudaError_t e = m->topo == SIM_GRAPH ? graph_step(m->graph, dt, s) : lattice_step(m->lat, dt, s);
                 if (e != cudaSuccess) return e;
@@ -1045,10 +1050,36 @@ int sim_batch_create(sim_batch_t *out, const sim_t *members, int n_members, void
     b->host_budget.assign(n_members, -1);
 
     // Group ring members by model; host copies of the device tables.
-    std::vector<std::vector<int>> by_model(4);
+    std::vector<std::vector<int>> by_model(4), cubes(2); // cubes: Kuramoto, with inertia
     for (int i = 0; i < n_members; ++i) {
         if (members[i]->topo == SIM_RING) by_model[members[i]->model].push_back(i);
+        else if (members[i]->topo == SIM_CUBE3D) cubes[members[i]->model == SIM_KSI ? 1 : 0].push_back(i);
         else b->lattices.push_back(members[i]);
+    }
+    // cube members: one x, y and z launch per stage for each model (tables below)
+    std::vector<LatticePlan> cplans;
+    std::vector<int> cx_item, cyz_item;
+    std::vector<int64_t> cx_base, cyz_base;
+    struct CubeSpan { int model, plan0, n, w; int64_t n1_max, x0, nx, yz0, nyz; };
+    std::vector<CubeSpan> cspans;
+    for (int c = 0; c < 2; ++c) {
+        if (cubes[c].empty()) continue;
+        CubeSpan cs{c ? 3 : 0, (int)cplans.size(), (int)cubes[c].size(), 0, 0, (int64_t)cx_item.size(), 0,
+                    (int64_t)cyz_item.size(), 0};
+        for (int i : cubes[c]) cs.n1_max = std::max(cs.n1_max, members[i]->lat.N1);
+        cs.w = lattice_row_warps(cs.n1_max);
+        for (int k = 0; k < cs.n; ++k) {
+            const LatticePlan &lp = members[cubes[c][k]]->lat;
+            cplans.push_back(lp);
+            cx_base.push_back(cs.nx);
+            cyz_base.push_back(cs.nyz);
+            const int64_t nx = (lp.N1 * lp.N1 + cs.w - 1) / cs.w, nyz = lattice_order_blocks(SIM_CUBE3D, lp.N1);
+            cx_item.insert(cx_item.end(), (size_t)nx, k);
+            cyz_item.insert(cyz_item.end(), (size_t)nyz, k);
+            cs.nx += nx;
+            cs.nyz += nyz;
+        }
+        cspans.push_back(cs);
     }
     std::vector<RingPlan> plans;
     std::vector<int> inst_of_item;
@@ -1082,6 +1113,9 @@ int sim_batch_create(sim_batch_t *out, const sim_t *members, int n_members, void
     const size_t o_plans = take(sizeof(RingPlan) * nplan), o_items = take(sizeof(int) * nitem);
     const size_t o_base = take(sizeof(int64_t) * nplan), o_budget = take(sizeof(long long) * nplan);
     const size_t o_errs = take(sizeof(unsigned *) * n_members), o_eout = take(64);
+    const size_t o_cplans = take(sizeof(LatticePlan) * cplans.size());
+    const size_t o_cxi = take(sizeof(int) * cx_item.size()), o_cyi = take(sizeof(int) * cyz_item.size());
+    const size_t o_cxb = take(sizeof(int64_t) * cx_base.size()), o_cyb = take(sizeof(int64_t) * cyz_base.size());
     // stream-ordered allocation: no device-wide synchronisation when batches are
     // formed and dropped often (the serving loop re-forms them as jobs come and go)
     cudaError_t e = cudaMallocAsync(&b->block, o, b->stream);
@@ -1108,6 +1142,22 @@ int sim_batch_create(sim_batch_t *out, const sim_t *members, int n_members, void
         e = cudaMemcpyAsync(b->budgets, budgets.data(), sizeof(long long) * nplan, cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->err_ptrs, errs.data(), sizeof(unsigned *) * n_members, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess && !cplans.empty()) {
+        e = cudaMemcpyAsync(blk + o_cplans, cplans.data(), sizeof(LatticePlan) * cplans.size(), cudaMemcpyHostToDevice,
+                            b->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(blk + o_cxi, cx_item.data(), sizeof(int) * cx_item.size(), cudaMemcpyHostToDevice,
+                                b->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(blk + o_cyi, cyz_item.data(), sizeof(int) * cyz_item.size(), cudaMemcpyHostToDevice,
+                                b->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(blk + o_cxb, cx_base.data(), sizeof(int64_t) * cx_base.size(), cudaMemcpyHostToDevice,
+                                b->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(blk + o_cyb, cyz_base.data(), sizeof(int64_t) * cyz_base.size(),
+                                cudaMemcpyHostToDevice, b->stream);
+    }
 
     if (e != cudaSuccess) {
         sim_batch_destroy(b);
@@ -1125,6 +1175,21 @@ int sim_batch_create(sim_batch_t *out, const sim_t *members, int n_members, void
         TuneVal tv;
         if (gs.model != SIM_HH && tune_lookup(batch_tune_key(b, nitem), &tv)) g.npt = tv.npt == 1 ? 1 : 2;
         b->groups.push_back(g);
+    }
+    for (const CubeSpan &cs : cspans) {
+        CubeBatchGroup g;
+        g.model = cs.model;
+        g.n_inst = cs.n;
+        g.w = cs.w;
+        g.n1_max = cs.n1_max;
+        g.n_x = cs.nx;
+        g.n_yz = cs.nyz;
+        g.plans = reinterpret_cast<const LatticePlan *>(blk + o_cplans) + cs.plan0;
+        g.x_item = reinterpret_cast<const int *>(blk + o_cxi) + cs.x0;
+        g.yz_item = reinterpret_cast<const int *>(blk + o_cyi) + cs.yz0;
+        g.x_base = reinterpret_cast<const int64_t *>(blk + o_cxb) + cs.plan0;
+        g.yz_base = reinterpret_cast<const int64_t *>(blk + o_cyb) + cs.plan0;
+        b->cube_groups.push_back(g);
     }
     *out = b;
     return SIM_OK;

@@ -179,3 +179,42 @@ def test_full_size_sweep_sampled_members():
     finally:
         for n in nets:
             n.close()
+
+
+def test_batched_cubes_of_both_models_equal_plain():
+    """Cube members of both Kuramoto models and uneven edges (one x, y and z
+    launch per stage for each model), beside a ball and a ring: states and order
+    parameters equal each member stepped alone, bit for bit."""
+    from paper_2410_19075_gb300 import BALL3D, CUBE3D, KS, KSI, RING, Batch, Network
+    specs = [(KS, CUBE3D, 5, 2, I.ks_params(alpha=1.52)), (KS, CUBE3D, 24, 4, I.ks_params(alpha=1.3)),
+             (KSI, CUBE3D, 12, 3, I.ksi_params()), (KS, CUBE3D, 47, 9, I.ks_params(alpha=1.52)),
+             (KSI, CUBE3D, 33, 6, I.ksi_params(mu=1.0)), (KSI, BALL3D, 10, 3, I.ksi_params()),
+             (KS, RING, 2000, 600, I.ks_params())]
+    nodes = [N ** 3 if topo != RING else N for _, topo, N, _, _ in specs]
+    inits = [I.initial_state(m, 1200 + k, 0, n) for k, ((m, _, _, _, _), n) in enumerate(zip(specs, nodes))]
+
+    def make():
+        nets = []
+        for (m, topo, N, P, params), y0 in zip(specs, inits):
+            net = Network(m, topo, N, P, params)
+            net.set_state(y0)
+            nets.append(net)
+        return nets
+
+    solo = make()
+    for n in solo:
+        n.step(30, 0.01)
+    ref = [(n.get_state(), n.observables()) for n in solo]
+    for n in solo:
+        n.close()
+    nets = make()
+    try:
+        with Batch(nets) as b:
+            b.step(30, 0.01)
+            b.sync()
+        for net, (y, o), spec in zip(nets, ref, specs):
+            assert np.array_equal(net.get_state(), y), spec[:4]
+            assert np.array_equal(net.observables(), o), spec[:4]
+    finally:
+        for n in nets:
+            n.close()
