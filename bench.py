@@ -106,7 +106,6 @@ def config_of(args, N, R):
     return {
         "workload": name,
         "N": N, "R": R, "dt": args.dt,
-        "kernel_variant": "autotuned (sim_autotune) before the timed region",
         "rk4_steps_per_iteration": args.chunk,
         "l2": "flushed (512 MiB write) between timed iterations; within an iteration the network "
               "state is reused across consecutive RK4 steps as in a real run",
