@@ -76,9 +76,11 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-sweep comparison")
     ap.add_argument("--no-served", action="store_true", help="skip the served-mix comparison")
     ap.add_argument("--no-extra", action="store_true", help="skip the small-ring and lattice lines")
-    ap.add_argument("--only", choices=["dp5", "graph"], default=None,
-                    help="run only one side line (for profiling): the Dormand-Prince sweep or the link matrices")
-    ap.add_argument("--instances", type=int, default=4096, help="networks in the Dormand-Prince sweep")
+    ap.add_argument("--only", choices=["dp5", "graph", "served"], default=None,
+                    help="run only one side line (for profiling): the Dormand-Prince sweep, the link matrices "
+                         "or the batched server on the scaled served trace")
+    ap.add_argument("--instances", type=int, default=4096,
+                    help="networks in the Dormand-Prince sweep; jobs of --only served")
     ap.add_argument("--graph-ball", action="store_true",
                     help="also time the 100^3 ball lattice (P = 6) as a compressed link matrix (~25 s set-up)")
     return ap.parse_args()
@@ -809,6 +811,11 @@ def run_only(args):
     torch.cuda.set_device(0)
     if args.only == "dp5":
         out = bench_dp5_sweep(args, n_inst=args.instances, plain_inst=min(32, args.instances))
+    elif args.only == "served":
+        # the batched server alone on the scaled trace (args.instances jobs at 200 jobs/s)
+        jobs = I.served_trace(n_jobs=args.instances, rate=200.0, seed=2415, size_scale=0.05, steps_scale=0.1)
+        inits = [I.initial_state(j.model, j.seed, j.job_id + 1, j.N ** 3 if j.topo == 1 else j.N) for j in jobs]
+        out = serve_trace(jobs, inits, 4096, 64 << 30, 32, torch.cuda.current_stream())
     else:
         flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
         out = bench_graph(args, torch.cuda.current_stream(), flush, ball=args.graph_ball)
