@@ -287,11 +287,12 @@ void sim_batch_destroy(sim_batch_t b);
  *
  * sim_autotune times trial_steps RK4 steps of dt with every variant of a ring
  * network, on its current state, and keeps the fastest: *npt_out = nodes per
- * thread (1 or 2), *flat_out = 1 for the one-pass prefix (either may be NULL).
+ * thread (1 or 2; HH always 1), *flat_out = 1 for the one-pass prefix (either
+ * may be NULL).
  * Afterwards the state is the one before the call, and the order-parameter
  * record, step count and error word are as after sim_set_state (R(t0) is
- * recorded again).  Networks without variants (lattices, link matrices, HH,
- * rings small enough for the cluster kernel) report their fixed choice and run
+ * recorded again).  Networks without variants (lattices, link matrices, rings
+ * small enough for the cluster kernel) report their fixed choice and run
  * nothing.  Needs a device copy of the state; SIM_ENOMEM if it does not fit.
  * The choice is also stored in a process-wide cache under (model, N, radius):
  * later sim_create calls with the same key start with it. */

@@ -55,7 +55,7 @@ struct RingPlan {
     // unsigned, and t >> 54 signed) in 32-bit words, exact because no sum of
     // chunks over at most 8192 sub-tiles reaches 2^31; the next kernel's CTAs
     // sum those themselves, so no CTA waits for the last one of its launch.
-    int flat;             // requires npt == 2
+    int flat;             // plain stage kernels only (batched members keep the two-level scan)
     int npt;              // nodes per thread of the stage kernels: 2 (128 threads per sub-tile;
                           // not HH) or 1 (256); set by sim_create and the autotuner
     int64_t *fsub[2];     // NQ * nsub each: sub-tile totals (same parity as lam)

@@ -69,14 +69,19 @@ template <int NQ> struct RingGather {
 };
 
 // One 256-node sub-tile `sub` of ring P, one node per thread (the whole CTA).
-template <int M, int STAGE>
+// FLAT_OK: the plain kernel, which may run the one-pass prefix (batched members
+// always keep the two-level scan).
+template <int M, int STAGE, bool FLAT_OK>
 __device__ __forceinline__ void ring_stage_body(const RingPlan &P, const RingStageIO &a, const StepSize &h,
                                                 int64_t sub)
 {
     constexpr int NQ = Model<M>::NQ;
     __shared__ RingBases<NQ> s_bases;
-    if (STAGE > 0) ring_compute_bases<NQ>(P, a.ingrp_in, a.grpofs_in, sub, s_bases);
-    stage_body<M, STAGE>(P, a, h, sub, RingGather<NQ>{P, a.lam_in, s_bases});
+    if (STAGE > 0) {
+        if (FLAT_OK && P.flat) ring_flat_bases<NQ>(P, a.fsub_in, a.facc_in, sub, s_bases);
+        else ring_compute_bases<NQ>(P, a.ingrp_in, a.grpofs_in, sub, s_bases);
+    }
+    stage_body<M, STAGE, RingGather<NQ>, FLAT_OK>(P, a, h, sub, RingGather<NQ>{P, a.lam_in, s_bases});
 }
 
 // Two adjacent nodes per thread, 128 threads per 256-node sub-tile: two
@@ -208,7 +213,7 @@ template <int M, int STAGE>
 __global__ void __launch_bounds__(kRingThreads, MinBlocks<M>::value) ring_stage_kernel(const RingPlan p, const StepSize h)
 {
     if (p.skip && *(const volatile int *)p.skip) return; // uniform over the launch
-    ring_stage_body<M, STAGE>(p, stage_io<M, STAGE>(p), h, blockIdx.x);
+    ring_stage_body<M, STAGE, true>(p, stage_io<M, STAGE>(p), h, blockIdx.x);
 }
 
 // Batched path: CTA b works on sub-tile b - item_base[inst] of ring inst =
@@ -223,7 +228,7 @@ __global__ void __launch_bounds__(kRingThreads, MinBlocks<M>::value)
     const int inst = inst_of_item[blockIdx.x];
     const RingPlan &p = plans[inst];
     if (p.steps_left && *(volatile long long *)p.steps_left <= 0) return;
-    ring_stage_body<M, STAGE>(p, stage_io<M, STAGE>(p), h, (int64_t)blockIdx.x - item_base[inst]);
+    ring_stage_body<M, STAGE, false>(p, stage_io<M, STAGE>(p), h, (int64_t)blockIdx.x - item_base[inst]);
 }
 
 // The same with two adjacent nodes per thread (ring_stage_body2).
@@ -321,7 +326,7 @@ cudaError_t ring_batch_step(const RingBatchGroup &g, double dt, cudaStream_t s)
 
 static size_t flat_slot_bytes(const RingPlan &p)
 {
-    return sizeof(unsigned) * 4 * (size_t)Model<0>::NQ * (size_t)p.ngroups;
+    return sizeof(unsigned) * 4 * (size_t)(p.model == 2 ? Model<2>::NQ : Model<0>::NQ) * (size_t)p.ngroups;
 }
 
 cudaError_t ring_prologue(const RingPlan &p, cudaStream_t s)

@@ -12,8 +12,8 @@
 //                     sub-tile start: the last CTA to finish in each group of 64
 //                     sub-tiles scans that group, and the last group scans the
 //                     groups (and may record the Kuramoto order parameter);
-//   one-pass prefix   (RingPlan::flat, the RK4 kernels of rings of at most 128
-//                     groups) no scan at the end of a launch at all: each CTA
+//   one-pass prefix   (RingPlan::flat, the plain RK4 kernels of rings of at most
+//                     128 groups) no scan at the end of a launch at all: each CTA
 //                     stores its sub-tile total and adds its 18-bit chunks into
 //                     its group's 32-bit accumulators; two warps of each CTA of
 //                     the next launch sum the group totals and the sub-tile
@@ -525,7 +525,7 @@ __host__ __device__ __forceinline__ RingStageIO stage_io(const RingPlan &p)
 // fixed-point coupled quantity, its window sums W, its link count and coupling
 // scale (see models.cuh).  The node's state loads are issued before the barrier
 // as well, so the CTA's start latency overlaps the bases' computation.
-template <int M, int STAGE, class Gather>
+template <int M, int STAGE, class Gather, bool FLAT_OK = false>
 __device__ __forceinline__ void stage_body(const RingPlan &P, const RingStageIO &a, const StepSize &h, int64_t sub,
                                            const Gather &gather)
 {
@@ -600,8 +600,18 @@ __device__ __forceinline__ void stage_body(const RingPlan &P, const RingStageIO 
         for (int c = 0; c < NQ; ++c) qv[c] = to_fixed(f[c], P.F, P.lim, ok);
     }
     if (!ok) raise_error(P.err, ERR_RANGE);
-    ring_prefix_tail<NQ, (M == 0 || M == 3) && (STAGE == 0 || STAGE == 4), STAGE == 4>(P, a.lam_out, a.ingrp_out,
-                                                                                     a.grpofs_out, sub, i, qv);
+    constexpr bool RECORD = (M == 0 || M == 3) && (STAGE == 0 || STAGE == 4);
+    if constexpr (FLAT_OK) {
+        if (P.flat) { // the one-pass prefix (both forms in the prologue)
+            int64_t qv1[NQ][1];
+#pragma unroll
+            for (int c = 0; c < NQ; ++c) qv1[c][0] = qv[c];
+            ring_prefix_tail_n<NQ, 1, RECORD, STAGE == 4>(P, a.lam_out, a.ingrp_out, a.grpofs_out, sub, i, qv1, true,
+                                                          STAGE == 0, a.fsub_out, a.facc_out, a.facc_zero);
+            return;
+        }
+    }
+    ring_prefix_tail<NQ, RECORD, STAGE == 4>(P, a.lam_out, a.ingrp_out, a.grpofs_out, sub, i, qv);
 }
 
 } // namespace simk

@@ -88,11 +88,12 @@ int ceil_log2(uint64_t x)
     return r;
 }
 
-// Rings whose RK4 stage kernels use the one-pass prefix: two nodes per thread
-// (not HH) and few enough groups for one warp to sum their totals.
+// Rings whose RK4 stage kernels may use the one-pass prefix: few enough groups
+// for the 32-bit chunk sums (any model, either kernel variant).
 bool ring_flat_eligible(int model, int64_t ngroups)
 {
-    return model != SIM_HH && ngroups <= kFlatMaxGroups;
+    (void)model;
+    return ngroups <= kFlatMaxGroups;
 }
 
 // Autotuner cache (process-wide): the kernel variant that measured fastest for
@@ -493,9 +494,9 @@ static int create_impl(sim_t *out, int model, int topology, int64_t N, int64_t r
         p.flat = ring_flat_eligible(model, p.ngroups) ? 1 : 0;
         p.npt = model == SIM_HH ? 1 : 2;
         TuneVal tv;
-        if (model != SIM_HH && tune_lookup(TuneKey{0, model, N, radius}, &tv)) {
-            p.npt = tv.npt == 1 ? 1 : 2;
-            p.flat = p.flat && tv.flat && p.npt == 2 ? 1 : 0;
+        if (tune_lookup(TuneKey{0, model, N, radius}, &tv)) {
+            p.npt = model == SIM_HH || tv.npt == 1 ? 1 : 2;
+            p.flat = p.flat && tv.flat ? 1 : 0;
         }
         if (p.flat) {
             const size_t slot = 4 * (size_t)model_nq(model) * p.ngroups;
@@ -1742,11 +1743,15 @@ int sim_autotune(sim_t h, double dt, int64_t trial_steps, int *npt_out, int *fla
         return SIM_OK;
     };
     // only the stage kernels of rings have variants (HH: one node per thread)
-    if (h->topo != SIM_RING || h->model == SIM_HH || use_cluster(h)) return report();
+    if (h->topo != SIM_RING || use_cluster(h)) return report();
+    const bool flat_ok = ring_flat_eligible(h->model, h->ring.ngroups);
     std::vector<TuneVal> cand;
-    if (ring_flat_eligible(h->model, h->ring.ngroups)) cand.push_back({2, 1});
-    cand.push_back({2, 0});
-    cand.push_back({1, 0});
+    for (int npt : {2, 1}) {
+        if (npt == 2 && h->model == SIM_HH) continue;
+        if (flat_ok) cand.push_back({npt, 1});
+        cand.push_back({npt, 0});
+    }
+    if (cand.size() < 2) return report();
     const size_t ybytes = sizeof(double) * h->d * h->nodes;
     void *save = nullptr;
     cudaError_t e = cudaMallocAsync(&save, ybytes, h->stream);
