@@ -299,7 +299,7 @@ void sim_batch_destroy(sim_batch_t b);
 int sim_autotune(sim_t h, double dt, int64_t trial_steps, int *npt_out, int *flat_out);
 
 /* The variant a ring network runs (npt 1 or 2, flat 0 or 1; 0 and 0 for
- * lattices and link matrices). */
+ * lattices and link matrices).  SIM_EINVAL for a NULL argument. */
 int sim_tune_info(sim_t h, int *npt, int *flat);
 
 /* The same for a batch: times trial_steps batched RK4 steps with one and with
@@ -311,7 +311,11 @@ int sim_batch_autotune(sim_batch_t b, double dt, int64_t trial_steps, int *npt_o
 
 /* Write the cache as text (one "kind model a b npt flat" line per entry; kind 0
  * = plain ring (model, N, radius), kind 1 = batch (-1, ring sub-tiles, ring
- * members)), merge a file written that way into it, or empty it.  Host only. */
+ * members)), merge a file written that way into it, or empty it.  Host only;
+ * the caller owns path.  SIM_EINVAL if the file cannot be written or read, or
+ * if a line is malformed (then nothing of the file is merged).  An entry only
+ * selects among variants that give the same results, so a stale file can cost
+ * speed, never correctness. */
 int sim_tune_save(const char *path);
 int sim_tune_load(const char *path);
 int sim_tune_clear(void);
