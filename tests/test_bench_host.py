@@ -1,0 +1,49 @@
+"""Host-side helpers of bench.py on CPU: the clock-record parser, the oracle
+rate calibration and the workload config."""
+import argparse
+import subprocess
+
+import numpy as np
+
+
+class _FakeSmi:
+    """Stands in for the nvidia-smi clock sampler process."""
+
+    def __init__(self, out):
+        self.out = out
+
+    def terminate(self):
+        pass
+
+    def communicate(self, timeout=None):
+        return self.out, ""
+
+
+def test_clock_sampler_parses_the_record(monkeypatch):
+    import bench
+    lines = ["0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+             "0, 2055, 2070, 1390.5, 0x4, Not Active, Not Active, Not Active, Active",
+             "0, 2070, 2070, 1400.0, 0x4, Not Active, Not Active, Not Active, Active",
+             "garbled line"]
+    monkeypatch.setattr(subprocess, "Popen", lambda *a, **k: _FakeSmi("\n".join(lines) + "\n"))
+    c = bench.ClockSampler(0)
+    c.start()
+    r = c.stop()
+    assert r == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    monkeypatch.setattr(subprocess, "Popen", lambda *a, **k: _FakeSmi(""))
+    c = bench.ClockSampler(0)
+    c.start()
+    assert c.stop() is None
+
+
+def test_oracle_rate_and_config():
+    import bench
+    from paper_2410_19075_gb300 import inputs as I
+    y = I.ks_phases(1, 0, 300)
+    rate, n = bench.oracle_rate(0, 0, 300, 100, I.ks_params(), y, 0.2, 1)
+    assert rate > 0 and 1 <= n <= 300
+    args = argparse.Namespace(model=1, topo=0, dt=0.01, chunk=100, gpus=1)
+    cfg = bench.config_of(args, 10 ** 6, 350000)
+    assert cfg["workload"] == "FitzHugh-Nagumo ring, N=1000000, R=350000, RK4 dt=0.01"
+    assert cfg["N"] == 10 ** 6 and cfg["parallelism"] == "single" and "flushed" in cfg["l2"]
+    assert np.isfinite(bench.RING_FLOPS[1]) and bench.RING_BYTES[1] == 432
