@@ -1,13 +1,26 @@
 """Benchmark: FP64 node-steps/s of the fused RK4 stage kernels on one GB300.
 
-Default workload: FitzHugh-Nagumo ring with rotational coupling, N = 10^6 nodes,
-R = 350000 (r = 0.35), eps = 0.05, a = 0.5, sigma = 0.1, phi = pi/2 - 0.1,
-(u, v) uniform on the circle of radius 2, RK4 at dt = 0.01.  One bench step is one
-RK4 step of the whole network (4 fused stage kernels).  Timed iterations are
-chunks of --chunk RK4 steps; L2 is flushed (a 512 MiB write) between them.
+Headline workload: 3D Kuramoto-Sakaguchi on the periodic cubic lattice, edge
+N1 = 464 (99,897,344 nodes), box window P = floor(0.2 N1) = 92 (6,331,624 links
+per node, self excluded), omega = 0, mu = 1, alpha = 1.52, phases i.i.d.
+U[-pi, pi) from a seed, classic RK4 at dt = 0.01 (Section IV, 3D networks).  One
+bench step is one RK4 step of the whole lattice: per stage the x, y and z passes
+of the separable exact box sums, the z pass fused with the right-hand side and
+the RK4 update.  The timed iterations are chunks of --chunk RK4 steps launched
+kernel by kernel through sim_step_timed (a CUDA event after every kernel on the
+handle's stream), so the same events give the whole-step time (value) and each
+kernel's average launch time (roofline); 512 MiB are written between iterations
+to flush L2 (the lattice's 4 GB of state exceed L2 anyway).
 
-Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on the
-host cores instead (bounded samples of the same workload).
+Beside the headline the JSON line carries the FitzHugh-Nagumo ring of 10^6 nodes
+(the plain one-network path at its config), the 1000-node Kuramoto ring, rings of
+10^7 and 10^8 nodes, Hodgkin-Huxley rings, the paper's 3D inertia network, link
+matrices, the 4096-ring batched sweep, Dormand-Prince sweeps and the served mix
+(a bounded window of the full-size trace, and a scaled trace with a rate sweep);
+each with its own clock record.
+
+``--impl reference`` times the CPU oracle (brute-force coupling sums) on the host
+cores instead, on bounded samples of the same workload.
 """
 from __future__ import annotations
 
@@ -36,15 +49,21 @@ TOPO_NAMES = {1: "periodic cubic lattice", 2: "periodic 3D lattice, ball window"
 # variables (nx * 8) and the node parameter, and writes the next prefix entry
 # (nq * 8), acc or y (d * 8) and the next local stage variables (nx * 8).
 RING_BYTES = {0: 344, 1: 432, 2: 704, 3: 480}
-# FP64 flops per node-step (DFMA = 2, DADD/DMUL = 1) of the arithmetic the method
-# needs, from the kernels' expressions; a sincos counts 25 and an exp 17, the
-# FP64 instructions of the kernels' table-driven routines (11 FMA + 3 MUL and
-# 8 FMA + 1 MUL).
-RING_FLOPS = {0: 4 * (25 + 13) + 14, 1: 4 * 15 + 3 * 8 + 6, 2: 4 * (6 * 17 + 40) + 3 * 16 + 12,
-              3: 4 * (25 + 16) + 3 * 8 + 6}
-# Cube (Kuramoto): per stage the x, y and z passes move 32 + 32 + 72 bytes per
-# node; FP64 flops as the Kuramoto ring.
-CUBE_BYTES = 544
+# FP64 flops per node-step (DFMA = 2, DADD/DMUL = 1) of the arithmetic the
+# kernels execute in FP64: the right-hand side from the converted window sums
+# and the RK4 updates (13 per state variable: FMA, 2 FMA, 2 FMA, ADD + FMA).
+# Sine and cosine run in integer arithmetic (no FP64); the Hodgkin-Huxley rates
+# use the table-driven exp (8 FMA + 1 MUL = 17 flops) and reciprocal.
+RING_FLOPS = {0: 4 * 5 + 13, 1: 4 * 15 + 2 * 13, 2: 4 * (6 * 17 + 40) + 3 * 16 + 12, 3: 4 * 6 + 2 * 13}
+# Cube (Kuramoto), bytes per node of each pass (launch): x pass reads (sin, cos)
+# on the 2^-62 grid and writes the x-window sums (16 + 16); y pass reads those
+# and writes the xy-window sums (16 + 16); z pass reads the xy sums (16), the
+# node's own (sin, cos) (16), y (8) and acc (8, stages 2-4), writes the next
+# (sin, cos) (16) and acc or y (8): 64 B in stage 1, 72 B in stages 2-4.
+CUBE_PASS_BYTES = {0: 32.0, 1: 32.0, 2: (64.0 + 3 * 72.0) / 4}
+CUBE_BYTES = 4 * (32 + 32) + 64 + 3 * 72  # 536 per node-step
+CUBE_BYTES_SURVEY = 432  # the survey's model of the same three passes (24 + 32 + 56 per stage)
+CUBE_PASS_FLOPS = {0: 0.0, 1: 0.0, 2: RING_FLOPS[0] / 4}
 # Ball / disk lattices: per stage the x pass reads (sin, cos) and writes the row
 # prefixes (32 B per node); the gather reads each prefix once from HBM (16 B; the
 # chord reads re-hit L1/L2), the stage-input (sin, cos) (16 B), y, acc and the
@@ -52,33 +71,36 @@ CUBE_BYTES = 544
 # (sin, cos).  Kuramoto with inertia (d = 2, one local variable): 120 + 2 * 144 +
 # 136 B per node-step; Kuramoto (d = 1): 96 + 2 * 104 + 104 B.
 LATTICE_BYTES = {0: 408, 3: 544}
-# DRAM bytes per stage launch (dram__bytes_read.sum + dram__bytes_write.sum, mean
-# over the four stages) from an ncu capture of the current ring stage kernel on
-# the FitzHugh-Nagumo ring N = 10^6, R = 350000; reported only for that workload.
-MEASURED_TRAFFIC = {(0, 1, 10 ** 6, 350000): 44.20e6}
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# current kernels from ncu captures, keyed by (topology, model, N, radius,
+# kernel kind); the captures and any scaling are described with the profiles.
+MEASURED_TRAFFIC = {}
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3000)
-    ap.add_argument("--warmup", type=int, default=100)
-    ap.add_argument("--chunk", type=int, default=100, help="RK4 steps per timed iteration")
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--chunk", type=int, default=5, help="RK4 steps per timed iteration")
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--model", type=int, default=1)
-    ap.add_argument("--topo", type=int, default=0,
+    ap.add_argument("--model", type=int, default=0)
+    ap.add_argument("--topo", type=int, default=1,
                     help="0 ring; lattices (Kuramoto models, N = edge N1, radius floor(r N1)): 1 cube, 2 ball, 3 disk")
-    ap.add_argument("--N", type=int, default=10 ** 6)
-    ap.add_argument("--r", type=float, default=0.35)
+    ap.add_argument("--N", type=int, default=464)
+    ap.add_argument("--r", type=float, default=0.2)
     ap.add_argument("--dt", type=float, default=0.01)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-sweep comparison")
     ap.add_argument("--no-served", action="store_true", help="skip the served-mix comparison")
-    ap.add_argument("--no-extra", action="store_true", help="skip the small-ring and lattice lines")
-    ap.add_argument("--only", choices=["dp5", "graph", "served"], default=None,
-                    help="run only one side line (for profiling): the Dormand-Prince sweep, the link matrices "
-                         "or the batched server on the scaled served trace")
+    ap.add_argument("--no-extra", action="store_true", help="skip the side lines (rings, lattices, link matrices)")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="rings: keep the creation-time kernel variant instead of autotuning (for profiling)")
+    ap.add_argument("--served-jobs", type=int, default=200,
+                    help="jobs of the full-size served window (the first jobs of the trace)")
+    ap.add_argument("--only", choices=["dp5", "graph", "served", "served_full", "rings"], default=None,
+                    help="run only one side line (for profiling)")
     ap.add_argument("--instances", type=int, default=4096,
                     help="networks in the Dormand-Prince sweep; jobs of --only served")
     ap.add_argument("--graph-ball", action="store_true",
@@ -97,22 +119,36 @@ def workload(args):
     return N, R, params
 
 
-def nodes_of(args, N):
-    return N ** 3 if args.topo in (1, 2) else N * N if args.topo == 3 else N
+def nodes_of(topo, N):
+    return N ** 3 if topo in (1, 2) else N * N if topo == 3 else N
 
 
-def config_of(args, N, R):
-    name = (f"{MODEL_NAMES[args.model]} {TOPO_NAMES[args.topo]}, N1={N} ({nodes_of(args, N)} nodes), P={R}, "
-            f"RK4 dt={args.dt}" if args.topo != 0 else
-            f"{MODEL_NAMES[args.model]} ring, N={N}, R={R}, RK4 dt={args.dt}")
+def workload_name(model, topo, N, R, dt):
+    if topo == 0:
+        return f"{MODEL_NAMES[model]} ring, N={N}, R={R}, RK4 dt={dt}"
+    return (f"{MODEL_NAMES[model]} {TOPO_NAMES[topo]}, N1={N} ({nodes_of(topo, N)} nodes), P={R}, "
+            f"RK4 dt={dt}")
+
+
+def config_of(args, N, R, chunks=None):
     return {
-        "workload": name,
+        "workload": workload_name(args.model, args.topo, N, R, args.dt),
         "N": N, "R": R, "dt": args.dt,
-        "rk4_steps_per_iteration": args.chunk,
+        "rk4_steps_per_iteration": (sorted(set(chunks)) if chunks else [args.chunk]),
+        "timed_iterations": len(chunks) if chunks else None,
         "l2": "flushed (512 MiB write) between timed iterations; within an iteration the network "
               "state is reused across consecutive RK4 steps as in a real run",
         "parallelism": "replicas" if args.gpus > 1 else "single",
     }
+
+
+def chunks_of(total, chunk):
+    out = []
+    while total > 0:
+        c = min(chunk, total)
+        out.append(c)
+        total -= c
+    return out
 
 
 # ----------------------------------------------------------------------------- distributed
@@ -147,15 +183,16 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index):
+    def __init__(self, gpu_index, interval_ms=50):
         self.proc = None
         self.idx = gpu_index
+        self.interval_ms = interval_ms
 
     def start(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", str(self.interval_ms)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
 
@@ -188,13 +225,51 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+class Clocked:
+    """Context manager: a clock record of the enclosed GPU work (``.record``)."""
+
+    def __init__(self, gpu_index=0):
+        self.s = ClockSampler(gpu_index)
+        self.record = None
+
+    def __enter__(self):
+        self.s.start()
+        return self
+
+    def __exit__(self, *exc):
+        self.record = self.s.stop()
+
+
+# ----------------------------------------------------------------------------- peaks
+def measured_peaks():
+    """HBM copy bandwidth from MEASURED_PEAKS.json (the pool's own measurement)
+    and the FP64 FMA and 64-bit multiply-high rates of this GPU, measured now by
+    the library's probe kernels."""
+    from paper_2410_19075_gb300 import sim
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except OSError:
+        pass
+    hbm = peaks.get("hbm_gbs")
+    with Clocked() as ck:
+        dfma = sim.probe_peak(0)
+        mulhi = sim.probe_peak(1)
+    return {"hbm_gbs": float(hbm) if hbm else 6800.0,
+            "hbm_source": "MEASURED_PEAKS.json (copy, read + write)" if hbm else "fallback 6.8 TB/s",
+            "fp64_gflops": 2.0 * dfma / 1e9, "dfma_per_s": dfma, "mulhi64_per_s": mulhi,
+            "fp64_source": "sim_probe_peak(0): DFMA throughput measured in this run (2 flops each)",
+            "probe_clocks": ck.record}
+
+
 # ----------------------------------------------------------------------------- CPU baseline
 def oracle_rate(model, topo, N, R, params, y, seconds, threads, node_param=None):
     """Oracle throughput: brute-force RHS of a sample of nodes for the 4 stages of
     one RK4 step, the sample grown until it takes about `seconds`; returns
     (node-steps/s, sample size)."""
     import oracle
-    n_all = N ** 3 if topo in (1, 2) else N * N if topo == 3 else N
+    n_all = nodes_of(topo, N)
     rng = np.random.default_rng(0)
     n = 4
     while True:
@@ -208,19 +283,30 @@ def oracle_rate(model, topo, N, R, params, y, seconds, threads, node_param=None)
         n = min(n_all, max(n * 2, int(n * (seconds / 4) / max(dt, 1e-3))))
 
 
-def cpu_baseline(args, N, R, params, seconds):
+def links_of(topo, N, R):
+    if topo == 0:
+        return 2 * R
+    if topo == 1:
+        return (2 * R + 1) ** 3 - 1
+    r = range(-R, R + 1)
+    return (sum(1 for a in r for b in r for c in r if a * a + b * b + c * c <= R * R) if topo == 2
+            else sum(1 for a in r for b in r if a * a + b * b <= R * R)) - 1
+
+
+def cpu_baseline(model, topo, N, R, params, seconds, seed=2412):
     """Oracle throughput on the host cores (all of them, and one): brute-force RHS
     of a bounded sample of nodes for the 4 stages of one RK4 step, extrapolated
     per node-step."""
     cores = os.cpu_count() or 1
-    y0 = I.initial_state(args.model, 2412, 0, N)
-    npar = I.hh_iext(2412, 0, N) if args.model == 2 else None
-    value, n = oracle_rate(args.model, 0, N, R, params, y0, seconds, cores, npar)
-    one, n1 = oracle_rate(args.model, 0, N, R, params, y0, seconds / 3, 1, npar)
+    n = nodes_of(topo, N)
+    y0 = I.initial_state(model, seed, 0, n)
+    npar = I.hh_iext(seed, 0, n) if model == 2 else None
+    value, k = oracle_rate(model, topo, N, R, params, y0, seconds, cores, npar)
+    one, k1 = oracle_rate(model, topo, N, R, params, y0, seconds / 3, 1, npar)
     return {"value": value, "unit": "node-steps/s", "cores": cores, "kind": "oracle",
-            "single_core_value": one,
-            "sample": f"brute-force RHS of {n} ({n1} on one core) sampled nodes x 4 RK4 stages on the "
-                      f"{N}-node network ({2 * R} links each), extrapolated per node-step"}
+            "single_core_value": one, "extrapolated": k < n,
+            "sample": f"brute-force RHS of {k} ({k1} on one core) sampled nodes x 4 RK4 stages of the "
+                      f"{n}-node network ({links_of(topo, N, R)} links each), extrapolated per node-step"}
 
 
 def run_reference(args):
@@ -230,16 +316,21 @@ def run_reference(args):
         return
     import oracle
     cores = os.cpu_count() or 1
-    y0 = I.initial_state(args.model, 2412, 0, N)
-    npar = I.hh_iext(2412, 0, N) if args.model == 2 else None
-    budget = 120.0  # seconds for the whole timed run
-    per_step_nodes = max(1, int(2.0e9 / (4 * 2 * R) * budget / max(1, args.steps + args.warmup) / 10))
+    n = nodes_of(args.topo, N)
+    y0 = I.initial_state(args.model, 2412, 0, n)
+    npar = I.hh_iext(2412, 0, n) if args.model == 2 else None
+    budget = 60.0  # seconds for the whole timed run
+    links = links_of(args.topo, N, R)
+    # the oracle evaluates about 4e7 brute-force pair terms per second per core
+    per_step_nodes = max(1, min(n, int(4e7 * cores * budget / max(1, args.steps + args.warmup) / (4 * links))))
     rng = np.random.default_rng(1)
+
     def one_step():
-        q = np.sort(rng.choice(N, min(N, per_step_nodes), replace=False))
+        q = np.sort(rng.choice(n, per_step_nodes, replace=False))
         for _ in range(4):
-            oracle.rhs_sampled(args.model, 0, N, R, params, y0, q, node_param=npar, threads=cores)
+            oracle.rhs_sampled(args.model, args.topo, N, R, params, y0, q, node_param=npar, threads=cores)
         return q.size
+
     for _ in range(args.warmup):
         one_step()
     t0 = time.perf_counter()
@@ -254,9 +345,141 @@ def run_reference(args):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_of(args, N, R),
             "cpu_baseline": {"value": v, "unit": "node-steps/s", "cores": cores, "kind": "oracle",
                              "sample": f"each step: brute-force RHS of {per_step_nodes} sampled nodes x 4 "
-                                       f"stages of the {N}-node network"},
+                                       f"stages of the {n}-node network ({links} links each), extrapolated "
+                                       f"per node-step"},
             "e2e": {"value": v, "unit": "node-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- timing helpers
+def timed_chunks(net, chunks, dt, flush, world=1):
+    """The timed region: every chunk launched kernel by kernel through
+    sim_step_timed after an L2 flush; returns the device milliseconds of the
+    whole region and the per-kind sums."""
+    import torch
+    kinds = {}
+    total = 0.0
+    barrier(world)
+    torch.cuda.synchronize()
+    for c in chunks:
+        flush.zero_()
+        torch.cuda.synchronize()
+        r = net.step_timed(c, dt)
+        for k, v in r.items():
+            d = kinds.setdefault(k, {"ms": 0.0, "launches": 0})
+            d["ms"] += v["ms"]
+            d["launches"] += v["launches"]
+            total += v["ms"]
+    torch.cuda.synchronize()
+    barrier(world)
+    return total, kinds
+
+
+def graph_timed(net, steps, dt, flush, stream):
+    """The same work through sim_step (captured CUDA graphs), bracketed by CUDA
+    events on the handle's stream: milliseconds."""
+    import torch
+    flush.zero_()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    net.step(steps, dt)
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b)
+
+
+def roofline_of(kinds, bytes_per_node, flops_per_node, nodes, peaks, traffic_key=None):
+    """Roofline of the dominant kernel kind (largest share of the timed region):
+    algorithmic bytes and FP64 flops per launch over its average launch time,
+    against the measured HBM and FP64 peaks."""
+    kind = max(kinds, key=lambda k: kinds[k]["ms"])
+    d = kinds[kind]
+    avg_s = d["ms"] * 1e-3 / d["launches"]
+    b = bytes_per_node[kind] * nodes
+    f = flops_per_node[kind] * nodes
+    gbs = b / avg_s / 1e9
+    gfl = f / avg_s / 1e9
+    hbm_frac = gbs / peaks["hbm_gbs"]
+    fp_frac = gfl / peaks["fp64_gflops"]
+    bound = "hbm" if hbm_frac >= fp_frac else "alu"
+    total_ms = sum(v["ms"] for v in kinds.values())
+    tr = MEASURED_TRAFFIC.get(traffic_key + (kind,)) if traffic_key else None
+    out = {"kernel": kind, "share_of_timed_region": d["ms"] / total_ms, "avg_launch_ms": avg_s * 1e3,
+           "algorithmic_bytes_per_launch": b, "algorithmic_fp64_flops_per_launch": f,
+           "traffic": tr}
+    if bound == "hbm":
+        out.update({"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": hbm_frac,
+                    "fp64_achieved_gflops": gfl, "fp64_frac": fp_frac})
+    else:
+        out.update({"bound": "alu", "achieved": gfl, "peak": peaks["fp64_gflops"], "unit": "GFLOP/s",
+                    "frac": fp_frac, "hbm_achieved_gbs": gbs, "hbm_frac": hbm_frac})
+    out["peak_note"] = (f"HBM: {peaks['hbm_source']}; FP64: {peaks['fp64_source']} "
+                        f"({peaks['fp64_gflops']:.1f} GFLOP/s of measured)")
+    return out
+
+
+def per_kind_table(kinds, nodes, bytes_per_node, peaks):
+    out = {}
+    for k, d in kinds.items():
+        avg = d["ms"] / d["launches"]
+        e = {"launches": d["launches"], "avg_ms": avg}
+        if k in bytes_per_node:
+            gbs = bytes_per_node[k] * nodes / (avg * 1e-3) / 1e9
+            e.update({"algorithmic_gbs": gbs, "hbm_frac": gbs / peaks["hbm_gbs"]})
+        out[k] = e
+    return out
+
+
+def ring_kind_bytes(model):
+    return {"stage_or_x": RING_BYTES[model] / 4}
+
+
+def ring_kind_flops(model):
+    return {"stage_or_x": RING_FLOPS[model] / 4}
+
+
+CUBE_KIND_BYTES = {"stage_or_x": CUBE_PASS_BYTES[0], "cube_y": CUBE_PASS_BYTES[1], "node_pass": CUBE_PASS_BYTES[2]}
+CUBE_KIND_FLOPS = {"stage_or_x": 0.0, "cube_y": 0.0, "node_pass": CUBE_PASS_FLOPS[2]}
+
+
+def network_leg(model, topo, N, R, params, steps, chunk, dt, flush, stream, peaks, seed=2419, tune=True,
+                node_param=None, graphs=True):
+    """One network: steps RK4 steps in timed chunks (kernel by kernel, per-kernel
+    events), then the same steps through the graph path; clocks of both."""
+    from paper_2410_19075_gb300 import Network
+    import torch
+    n = nodes_of(topo, N)
+    net = Network(model, topo, N, R, params, stream=stream)
+    if node_param is not None:
+        net.set_node_param(node_param)
+    net.set_state(torch.from_numpy(I.initial_state(model, seed, 0, n)).cuda())
+    tuned = net.autotune(dt, 16) if (tune and topo == 0) else None
+    net.step(3, dt)
+    net.step_timed(1, dt)
+    chunks = chunks_of(steps, chunk)
+    with Clocked() as ck:
+        ms, kinds = timed_chunks(net, chunks, dt, flush)
+        g_ms = graph_timed(net, steps, dt, flush, stream) if graphs else None
+    y = net.get_state()
+    assert np.isfinite(y).all()
+    net.close()
+    if topo == 0:
+        kb, kf = ring_kind_bytes(model), ring_kind_flops(model)
+    elif topo == 1:
+        kb, kf = CUBE_KIND_BYTES, CUBE_KIND_FLOPS
+    else:
+        kb, kf = {}, {}
+    out = {"workload": workload_name(model, topo, N, R, dt), "steps": steps,
+           "ms_per_step": ms / steps, "value": n * steps / (ms * 1e-3), "unit": "node-steps/s",
+           "kernels": per_kind_table(kinds, n, kb, peaks), "clocks": ck.record}
+    if g_ms is not None:
+        out["graph_path"] = {"ms_per_step": g_ms / steps, "value": n * steps / (g_ms * 1e-3)}
+    if kb:
+        out["roofline"] = roofline_of(kinds, kb, kf, n, peaks, (topo, model, N, R))
+    if tuned:
+        out["autotune"] = tuned
+    return out
 
 
 # ----------------------------------------------------------------------------- batched sweep
@@ -285,12 +508,13 @@ def bench_batched(args, flush, stream, n_inst=4096, steps=2000, plain_steps=20):
     chunks = [min(100, steps - k) for k in range(0, steps, 100)]
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in chunks]
     torch.cuda.synchronize()
-    for (a, b), c in zip(ev, chunks):
-        flush.zero_()
-        a.record(stream)
-        batch.step(c, args.dt)
-        b.record(stream)
-    torch.cuda.synchronize()
+    with Clocked() as ck:
+        for (a, b), c in zip(ev, chunks):
+            flush.zero_()
+            a.record(stream)
+            batch.step(c, args.dt)
+            b.record(stream)
+        torch.cuda.synchronize()
     batch.sync()
     ms = sum(a.elapsed_time(b) for a, b in ev)
     value = total_nodes * steps / (ms * 1e-3)
@@ -316,7 +540,7 @@ def bench_batched(args, flush, stream, n_inst=4096, steps=2000, plain_steps=20):
             "plain_value": plain_value, "plain_steps_timed": plain_steps,
             "speedup_vs_plain": value / plain_value,
             "autotune": {"npt": npt, "seconds": tune_s},
-            "gpu_launches": 4 * steps * 1}
+            "gpu_launches": 4 * steps * 1, "clocks": ck.record}
 
 
 def bench_dp5_sweep(args, n_inst=4096, N=1000, t_end=100.0, tol=1e-8, plain_inst=32):
@@ -346,9 +570,10 @@ def bench_dp5_sweep(args, n_inst=4096, N=1000, t_end=100.0, tol=1e-8, plain_inst
         net.close()
     nets = make(sweep)
     batch = Batch(nets)
-    t0 = time.perf_counter()
-    stats = batch.dp5([opts] * n_inst)
-    wall = time.perf_counter() - t0
+    with Clocked() as ck:
+        t0 = time.perf_counter()
+        stats = batch.dp5([opts] * n_inst)
+        wall = time.perf_counter() - t0
     batch.close()
     assert all(st["status"] == 0 for st in stats)
     acc = sum(st["accepted"] for st in stats)
@@ -371,7 +596,7 @@ def bench_dp5_sweep(args, n_inst=4096, N=1000, t_end=100.0, tol=1e-8, plain_inst
             "rhs_node_evals_per_s": 6.0 * N * att / wall,
             "plain_value": plain_value, "plain_instances_timed": plain_inst,
             "speedup_vs_plain": value / plain_value,
-            "gpu_launches": 7 * (att // n_inst + 1)}
+            "gpu_launches": 7 * (att // n_inst + 1), "clocks": ck.record}
 
 
 def ball_links(N1, P):
@@ -424,17 +649,18 @@ def bench_graph(args, stream, flush, ball=False, steps=100):
         links = int(rp[-1])
         del rp, col
         entries, runs, nbytes = net.graph_info()
-        ms = timed(net, model, n)
+        with Clocked() as ck:
+            ms = timed(net, model, n)
         net.close()
         out.append({"workload": f"{MODEL_NAMES[model]} on a {name}, N={n}", "links": links,
                     "compressed": {"entries": entries, "runs_of_common_vector": runs, "device_bytes": nbytes,
                                    "host_compress_s": compress_s},
                     "ms_per_step": ms, "value": n * steps / (ms * steps * 1e-3), "unit": "node-steps/s",
-                    "links_per_s": links / (ms * 1e-3)})
+                    "links_per_s": links / (ms * 1e-3), "clocks": ck.record})
     return out
 
 
-# ----------------------------------------------------------------------------- c1 and c3
+# ----------------------------------------------------------------------------- side lines
 def bench_small_ring(args, stream, flush, steps=200, reps=5):
     """Kuramoto ring N=1000, R=350, alpha=1.46: latency of one RK4 step (the whole
     200-step run per timed iteration, median of reps, L2 flushed between)."""
@@ -446,15 +672,16 @@ def bench_small_ring(args, stream, flush, steps=200, reps=5):
     net.set_state(y0)
     net.step(steps, args.dt)
     times = []
-    for _ in range(reps):
-        net.set_state(y0)
-        flush.zero_()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        net.step(steps, args.dt)
-        b.record(stream)
-        torch.cuda.synchronize()
-        times.append(a.elapsed_time(b))
+    with Clocked() as ck:
+        for _ in range(reps):
+            net.set_state(y0)
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            net.step(steps, args.dt)
+            b.record(stream)
+            torch.cuda.synchronize()
+            times.append(a.elapsed_time(b))
     net.close()
     ms = statistics.median(times)
     cores = os.cpu_count() or 1
@@ -463,35 +690,34 @@ def bench_small_ring(args, stream, flush, steps=200, reps=5):
     orc1, _ = oracle_rate(0, 0, N, R, I.ks_params(alpha=1.46), y_host, 2.0, 1)
     return {"workload": f"Kuramoto ring N={N}, R={R}, alpha=1.46, {steps} RK4 steps (cluster-resident kernel)",
             "us_per_step": 1e3 * ms / steps, "value": N * steps / (ms * 1e-3), "unit": "node-steps/s",
+            "clocks": ck.record,
             "oracle": {"value": orc, "single_core_value": orc1, "cores": cores, "unit": "node-steps/s",
                        "sample": "brute-force RHS of every node (all 700 links), 4 stages"}}
 
 
-def bench_roofline_sweep(args, stream, flush, steps=100):
-    """Kuramoto and FHN rings of 10^7 and 10^8 nodes, r = 0.35: steps RK4 steps
-    per timed iteration after 10 warm-up steps (L2 flushed before), with the FP64
-    and HBM fractions of the algorithmic flops and bytes."""
-    import torch
-    from paper_2410_19075_gb300 import Network
+def bench_fhn_ring(args, stream, flush, peaks, N=10 ** 6, R=350000, steps=200):
+    """The FitzHugh-Nagumo ring of 10^6 nodes, R = 350000 (the plain one-network
+    path at its own config), with the same fields as the headline line."""
+    out = network_leg(1, 0, N, R, I.fhn_params(), steps, 100, args.dt, flush, stream, peaks, seed=2412)
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(1, 0, N, R, I.fhn_params(), 8.0)
+    out["e2e"] = e2e_leg(1, 0, N, R, I.fhn_params(), [100] * 3, args.dt, stream)
+    return out
+
+
+def bench_rings(args, stream, flush, peaks):
+    """Rings that stream from HBM: Kuramoto and FHN at 10^7 and 10^8 nodes
+    (r = 0.35), and Hodgkin-Huxley at 10^5 (R = 3 10^4) and 10^6 (r = 0.3) nodes,
+    each with its per-kernel times and roofline."""
     out = []
-    for model in (0, 1):
-        for N in (10 ** 7, 10 ** 8):
-            R = int(0.35 * N)
-            net = Network(model, 0, N, R, I.ks_params() if model == 0 else I.fhn_params(), stream=stream)
-            net.set_state(I.initial_state(model, 2419, 0, N))
-            net.step(10, args.dt)
-            flush.zero_()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            net.step(steps, args.dt)
-            b.record(stream)
-            torch.cuda.synchronize()
-            net.close()
-            s_step = a.elapsed_time(b) * 1e-3 / steps
-            out.append({"workload": f"{MODEL_NAMES[model]} ring N={N}, R={R}", "steps": steps,
-                        "ms_per_step": s_step * 1e3, "value": N / s_step, "unit": "node-steps/s",
-                        "fp64_frac": RING_FLOPS[model] * N / s_step / 1e9 / (2 * 504.3),
-                        "hbm_frac": RING_BYTES[model] * N / s_step / 1e9 / 6693.8})
+    for model, N, r, steps in ((0, 10 ** 7, 0.35, 50), (0, 10 ** 8, 0.35, 10), (1, 10 ** 7, 0.35, 50),
+                               (1, 10 ** 8, 0.35, 10)):
+        R = int(r * N)
+        out.append(network_leg(model, 0, N, R, I.ks_params() if model == 0 else I.fhn_params(), steps,
+                               min(steps, 25), args.dt, flush, stream, peaks))
+    for N, R, steps in ((10 ** 5, 30000, 400), (10 ** 6, 300000, 50)):
+        out.append(network_leg(2, 0, N, R, I.hh_params(), steps, min(steps, 100), args.dt, flush, stream, peaks,
+                               node_param=I.hh_iext(2419, 0, N)))
     return out
 
 
@@ -500,36 +726,33 @@ def bench_lattice(args, stream, flush, model, topo, N1, P, params, steps=100):
     steps, L2 flushed before the timed region."""
     import torch
     from paper_2410_19075_gb300 import Network
-    nodes = N1 ** 3 if topo in (1, 2) else N1 * N1
+    nodes = nodes_of(topo, N1)
     net = Network(model, topo, N1, P, params, stream=stream)
     net.set_state(torch.from_numpy(I.initial_state(model, 2413, 0, nodes)).cuda())
     net.step(3, args.dt)
     net.step(steps, args.dt)
     net.sync()
     times = []
-    for _ in range(3):
-        flush.zero_()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        net.step(steps, args.dt)
-        b.record(stream)
-        torch.cuda.synchronize()
-        times.append(a.elapsed_time(b))
+    with Clocked() as ck:
+        for _ in range(3):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            net.step(steps, args.dt)
+            b.record(stream)
+            torch.cuda.synchronize()
+            times.append(a.elapsed_time(b))
     y = net.get_state()
     assert np.isfinite(y).all()
     net.close()
     ms = statistics.median(times)
-    links = {1: (2 * P + 1) ** 3 - 1}.get(topo)
-    if links is None:
-        r = range(-P, P + 1)
-        links = (sum(1 for a in r for b in r for c in r if a * a + b * b + c * c <= P * P) if topo == 2
-                 else sum(1 for a in r for b in r if a * a + b * b <= P * P)) - 1
+    links = links_of(topo, N1, P)
     per_byte = CUBE_BYTES if topo == 1 else LATTICE_BYTES[model]
     return {"workload": f"{MODEL_NAMES[model]} {TOPO_NAMES[topo]}, N1={N1} ({nodes} nodes), P={P} "
                         f"({links} links per node), params={list(map(float, params))}",
             "steps": steps, "ms_per_step": ms / steps, "value": nodes * steps / (ms * 1e-3),
             "unit": "node-steps/s", "links_per_s": nodes * links * steps / (ms * 1e-3),
-            "hbm_gbs_algorithmic": per_byte * nodes * steps / (ms * 1e-3) / 1e9}
+            "hbm_gbs_algorithmic": per_byte * nodes * steps / (ms * 1e-3) / 1e9, "clocks": ck.record}
 
 
 def bench_ball_dp5(args, t_end=100.0, tol=1e-10):
@@ -547,16 +770,17 @@ def bench_ball_dp5(args, t_end=100.0, tol=1e-10):
             net.set_state(y0)
             net.dp5(t_end=0.5, rtol=tol, atol=tol, h0=0.01)  # first run allocates its buffers
             net.set_state(y0)
-            t0 = time.perf_counter()
-            st = net.dp5(t_end=t_end, rtol=tol, atol=tol, h0=0.01, out_dt=1.0)
-            wall = time.perf_counter() - t0
+            with Clocked() as ck:
+                t0 = time.perf_counter()
+                st = net.dp5(t_end=t_end, rtol=tol, atol=tol, h0=0.01, out_dt=1.0)
+                wall = time.perf_counter() - t0
         assert st["status"] == 0
         out.append({"workload": f"Kuramoto with inertia, 100^3 ball, P={P}, Dormand-Prince 5(4) to t={t_end} at "
                                 f"rtol=atol={tol}, R every time unit",
                     "wall_s": wall, "accepted_steps": st["accepted"], "rejected_steps": st["rejected"],
                     "ms_per_accepted_step": 1e3 * wall / st["accepted"],
                     "rhs_node_evals_per_s": 6.0 * n * (st["accepted"] + st["rejected"]) / wall,
-                    "value": n * st["accepted"] / wall, "unit": "accepted node-steps/s"})
+                    "value": n * st["accepted"] / wall, "unit": "accepted node-steps/s", "clocks": ck.record})
     return out
 
 
@@ -567,37 +791,41 @@ def bench_ball(args, stream, flush):
     return [bench_lattice(args, stream, flush, 3, 2, 100, P, I.ksi_params(), steps=200) for P in (2, 4, 6)]
 
 
-def bench_cube(args, stream, flush, N1=464, P=92, steps=20):
-    """Kuramoto periodic cubic lattice 464^3 (99.9 million nodes), P=92 box,
-    alpha=1.52: separable exact box sums, steps RK4 steps per timed iteration."""
+# ----------------------------------------------------------------------------- end to end
+def e2e_leg(model, topo, N, R, params, chunks, dt, stream, world=1, seed=2412, rank=0):
+    """The same metric through the public API with host buffers: every iteration
+    loads the initial state from pinned host memory (sim_set_state), advances
+    the network (sim_step) and reads the state back to pinned host memory
+    (sim_get_state, which synchronises); wall time of all iterations."""
     import torch
     from paper_2410_19075_gb300 import Network
-    net = Network(0, 1, N1, P, I.ks_params(alpha=1.52), stream=stream)
-    net.set_state(torch.from_numpy(I.ks_phases(2413, 0, N1 ** 3)).cuda())
-    net.step(3, args.dt)
-    net.sync()
-    flush.zero_()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    net.step(steps, args.dt)
-    b.record(stream)
+    n = nodes_of(topo, N)
+    d = {0: 1, 1: 2, 2: 4, 3: 2}[model]
+    y0 = I.initial_state(model, seed, rank, n)
+    pin_in = torch.from_numpy(y0).pin_memory()
+    pin_out = torch.empty(d * n, dtype=torch.float64).pin_memory()
+    net = Network(model, topo, N, R, params, stream=stream)
+    if model == 2:
+        net.set_node_param(I.hh_iext(seed, rank, n))
+    net.set_state(pin_in.numpy())
+    for c in set(chunks):
+        net.step(c, dt)  # graphs captured
+    net.get_state(pin_out.numpy())
+    barrier(world)
     torch.cuda.synchronize()
-    ms = a.elapsed_time(b)
-    net.sync()
+    t0 = time.perf_counter()
+    for c in chunks:
+        net.set_state(pin_in.numpy())
+        net.step(c, dt)
+        net.get_state(pin_out.numpy())
+    el = max_over_ranks(time.perf_counter() - t0, world)
     net.close()
-    nodes = N1 ** 3
-    cores = os.cpu_count() or 1
-    y_host = I.ks_phases(2413, 0, nodes)
-    orc, n = oracle_rate(0, 1, N1, P, I.ks_params(alpha=1.52), y_host, 6.0, cores)
-    orc1, n1 = oracle_rate(0, 1, N1, P, I.ks_params(alpha=1.52), y_host, 3.0, 1)
-    del y_host
-    oracle_line = {"value": orc, "single_core_value": orc1, "cores": cores, "unit": "node-steps/s",
-                   "sample": f"brute-force RHS of {n} ({n1} on one core) sampled nodes x 4 stages, "
-                             f"{(2 * P + 1) ** 3 - 1} links each, extrapolated per node-step"}
-    return {"workload": f"Kuramoto periodic cubic lattice N1={N1} ({nodes} nodes), P={P}, alpha=1.52",
-            "oracle": oracle_line,
-            "steps": steps, "ms_per_step": ms / steps, "value": nodes * steps / (ms * 1e-3),
-            "unit": "node-steps/s", "hbm_gbs_algorithmic": CUBE_BYTES * nodes * steps / (ms * 1e-3) / 1e9}
+    steps = sum(chunks)
+    state_bytes = 8 * d * n
+    return {"value": float(n) * steps * world / el, "unit": "node-steps/s",
+            "h2d_bytes_per_step": state_bytes * len(chunks) / steps,
+            "d2h_bytes_per_step": state_bytes * len(chunks) / steps,
+            "iterations": len(chunks), "rk4_steps": steps}
 
 
 # ----------------------------------------------------------------------------- served mix
@@ -618,6 +846,7 @@ def serve_trace(jobs, inits, slots, budget, chunk, stream):
             r = srv.poll(jid)
             times.append(r[2])
         stats = srv.stats()
+        mem = srv.memory()
         phases = srv.timings()
     t = np.array(times)
     lat = t[:, 2] - t[:, 0]
@@ -625,8 +854,12 @@ def serve_trace(jobs, inits, slots, budget, chunk, stream):
     return {"p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
             "mean_queue_wait_s": float(np.mean(t[:, 1] - t[:, 0])),
             "value": stats["node_steps"] / span, "unit": "node-steps/s", "span_s": span,
-            "batches_formed": stats["batches_formed"],
+            "batches_formed": stats["batches_formed"], "memory": mem,
             "worker_seconds": {k: round(v, 4) for k, v in phases.items()}}
+
+
+def _trace_inits(jobs):
+    return [I.initial_state(j.model, j.seed, j.job_id + 1, nodes_of(j.topo, j.N)) for j in jobs]
 
 
 def bench_served(args, stream, n_jobs=400, rate=200.0, size_scale=0.05, steps_scale=0.1):
@@ -636,16 +869,46 @@ def bench_served(args, stream, n_jobs=400, rate=200.0, size_scale=0.05, steps_sc
     that the trace runs in seconds.  Continuous batching versus one job at a time
     on the plain path."""
     jobs = I.served_trace(n_jobs=n_jobs, rate=rate, seed=2415, size_scale=size_scale, steps_scale=steps_scale)
-    inits = [I.initial_state(j.model, j.seed, j.job_id + 1, j.N ** 3 if j.topo == 1 else j.N) for j in jobs]
-    node_steps = sum((j.N ** 3 if j.topo == 1 else j.N) * j.n_steps for j in jobs)
+    inits = _trace_inits(jobs)
+    node_steps = sum(nodes_of(j.topo, j.N) * j.n_steps for j in jobs)
     budget = 64 << 30
-    batched = serve_trace(jobs, inits, 4096, budget, 32, stream)
-    plain = serve_trace(jobs, inits, 1, budget, 32, stream)
+    with Clocked() as ck:
+        batched = serve_trace(jobs, inits, 4096, budget, 32, stream)
+        plain = serve_trace(jobs, inits, 1, budget, 32, stream)
     return {"workload": f"{n_jobs} jobs, Poisson {rate:g} jobs/s, 40/30/20/10 KS ring/FHN ring/HH ring/KS cube, "
                         f"sizes x{size_scale:g}, horizons x{steps_scale:g}, dt=0.01, HBM budget {budget >> 30} GiB",
             "total_node_steps": node_steps, "batched": batched, "plain_one_at_a_time": plain,
             "speedup_vs_plain": batched["value"] / plain["value"],
-            "p99_latency_ratio_plain_over_batched": plain["p99_latency_s"] / batched["p99_latency_s"]}
+            "p99_latency_ratio_plain_over_batched": plain["p99_latency_s"] / batched["p99_latency_s"],
+            "clocks": ck.record}
+
+
+def bench_served_full(args, stream, n_jobs=200, rate=200.0):
+    """A bounded window of the full-size served trace: the first n_jobs jobs of
+    the Poisson trace at rate jobs/s with the stated sizes (Kuramoto and FHN
+    rings of 10^3-10^6 nodes, HH rings of 10^3-10^5, cubes of 32^3-128^3) and
+    horizons (10^3-10^4 RK4 steps).  It offers far more work than one GPU
+    serves, so the queue grows: saturated throughput, latency and queue wait,
+    continuous batching versus one job at a time on the same jobs."""
+    jobs = I.served_trace(n_jobs=n_jobs, rate=rate, seed=2415)
+    inits = _trace_inits(jobs)
+    node_steps = sum(nodes_of(j.topo, j.N) * j.n_steps for j in jobs)
+    budget = 64 << 30
+    with Clocked() as ck:
+        batched = serve_trace(jobs, inits, 4096, budget, 64, stream)
+        plain = serve_trace(jobs, inits, 1, budget, 64, stream)
+    mix = {}
+    for j in jobs:
+        key = {(0, 0): "ks_ring", (1, 0): "fhn_ring", (2, 0): "hh_ring", (0, 1): "ks_cube"}[(j.model, j.topo)]
+        mix[key] = mix.get(key, 0) + 1
+    return {"workload": f"first {n_jobs} jobs of the full-size trace, Poisson {rate:g} jobs/s, 40/30/20/10 KS ring/"
+                        f"FHN ring/HH ring/KS cube, horizons 1e3-1e4 steps, dt=0.01, HBM budget {budget >> 30} GiB",
+            "jobs_by_kind": mix, "total_node_steps": node_steps,
+            "offered_node_steps_per_s": node_steps / max(1e-9, jobs[-1].arrival),
+            "batched": batched, "plain_one_at_a_time": plain,
+            "speedup_vs_plain": batched["value"] / plain["value"],
+            "p99_latency_ratio_plain_over_batched": plain["p99_latency_s"] / batched["p99_latency_s"],
+            "clocks": ck.record}
 
 
 def bench_served_sweep(args, stream, rates=(10.0, 50.0, 200.0, 800.0, 3200.0)):
@@ -657,12 +920,13 @@ def bench_served_sweep(args, stream, rates=(10.0, 50.0, 200.0, 800.0, 3200.0)):
     for rate in rates:
         n_jobs = int(min(400, max(60, 5 * rate)))
         jobs = I.served_trace(n_jobs=n_jobs, rate=rate, seed=2418, size_scale=0.05, steps_scale=0.1)
-        inits = [I.initial_state(j.model, j.seed, j.job_id + 1, j.N ** 3 if j.topo == 1 else j.N) for j in jobs]
-        offered = sum((j.N ** 3 if j.topo == 1 else j.N) * j.n_steps for j in jobs) / jobs[-1].arrival
-        r = serve_trace(jobs, inits, 4096, 64 << 30, 32, stream)
+        inits = _trace_inits(jobs)
+        offered = sum(nodes_of(j.topo, j.N) * j.n_steps for j in jobs) / jobs[-1].arrival
+        with Clocked() as ck:
+            r = serve_trace(jobs, inits, 4096, 64 << 30, 32, stream)
         out.append({"rate_jobs_per_s": rate, "jobs": n_jobs, "offered_node_steps_per_s": offered, "value": r["value"],
                     "p50_latency_s": r["p50_latency_s"], "p99_latency_s": r["p99_latency_s"],
-                    "mean_queue_wait_s": r["mean_queue_wait_s"]})
+                    "mean_queue_wait_s": r["mean_queue_wait_s"], "clocks": ck.record})
     return out
 
 
@@ -677,128 +941,88 @@ def run_native(args):
     if args.topo != 0 and args.model not in (0, 3):
         args.model = 0
     N, R, params = workload(args)
-    nodes = nodes_of(args, N)
-    d = {0: 1, 1: 2, 2: 4, 3: 2}[args.model]
+    nodes = nodes_of(args.topo, N)
     stream = torch.cuda.current_stream()
+    peaks = measured_peaks()
     y0_host = I.initial_state(args.model, 2412, rank, nodes)
-    npar = I.hh_iext(2412, rank, N) if args.model == 2 else None
+    npar = I.hh_iext(2412, rank, nodes) if args.model == 2 else None
     y0_dev = torch.from_numpy(y0_host).cuda()
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     net = Network(args.model, args.topo, N, R, params, stream=stream)
     if npar is not None:
         net.set_node_param(npar)
     net.set_state(y0_dev)
-    # the kernel variant from the autotuner (state unchanged; outside the timing)
-    t_tune = time.perf_counter()
-    tuned = net.autotune(args.dt, 32)
-    tuned["seconds"] = time.perf_counter() - t_tune
+    tuned = None
+    if args.topo == 0 and not args.no_tune:  # the ring kernel variant from the autotuner (state unchanged; untimed)
+        t_tune = time.perf_counter()
+        tuned = net.autotune(args.dt, 32)
+        tuned["seconds"] = time.perf_counter() - t_tune
 
-    chunks = []
-    left = args.steps
-    while left > 0:
-        c = min(args.chunk, left)
-        chunks.append(c)
-        left -= c
-
-    # warm-up (also captures the CUDA graphs)
-    w = args.warmup
-    while w > 0:
-        c = min(args.chunk, w)
-        net.step(c, args.dt)
-        w -= c
+    chunks = chunks_of(args.steps, args.chunk)
+    # warm-up: W untimed RK4 steps (graph capture of the e2e path's chunk sizes too)
+    for c in chunks_of(args.warmup, args.chunk):
+        net.step_timed(c, args.dt)
     for c in set(chunks):
         net.step(c, args.dt)
     net.set_state(y0_dev)
     net.sync()
 
-    # --- device-resident timing: K RK4 steps in chunks, L2 flushed between chunks
-    clocks = ClockSampler(local)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in chunks]
-    barrier(world)
-    torch.cuda.synchronize()
-    clocks.start()
-    for (a, b), c in zip(ev, chunks):
-        flush.zero_()
-        a.record(stream)
-        net.step(c, args.dt)
-        b.record(stream)
-    torch.cuda.synchronize()
-    clk = clocks.stop()
-    barrier(world)
-    ms = sum(a.elapsed_time(b) for a, b in ev)
+    # --- device-resident timing: K RK4 steps in chunks, L2 flushed between chunks,
+    # every kernel bracketed by CUDA events on the handle's stream
+    with Clocked(local) as ck:
+        ms, kinds = timed_chunks(net, chunks, args.dt, flush, world)
     ms = max_over_ranks(ms, world)
     y_check = net.get_state()  # surfaces any device error
     assert np.isfinite(y_check).all()
-    node_steps = float(nodes) * args.steps * world
-    value = node_steps / (ms * 1e-3)
+    net.close()
+    del y_check
+    value = float(nodes) * args.steps * world / (ms * 1e-3)
 
-    # --- end to end through the public API with host buffers: each iteration
-    # loads its input state from pinned host memory, steps, reads the result back
-    pin_in = torch.from_numpy(y0_host).pin_memory()
-    pin_out = torch.empty(d * nodes, dtype=torch.float64).pin_memory()
-    e2e_chunks = chunks[: max(1, min(len(chunks), 10))]
-    barrier(world)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for c in e2e_chunks:
-        net.set_state(pin_in.numpy())
-        net.step(c, args.dt)
-        net.get_state(pin_out.numpy())
-    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
-    e2e_steps = sum(e2e_chunks)
-    e2e_value = float(nodes) * e2e_steps * world / e2e_s
-    state_bytes = 8 * d * nodes
+    # --- end to end through the public API with host buffers
+    e2e = e2e_leg(args.model, args.topo, N, R, params, chunks[: max(1, min(len(chunks), 4))], args.dt, stream,
+                  world, rank=rank)
 
-    # --- dominant kernel: the ring stage kernel (4 launches per RK4 step); for
-    # the lattices the passes of a stage are counted together as one launch
-    launches = 4 * args.steps
-    avg_launch_s = ms * 1e-3 / launches
-    bytes_ns = {0: RING_BYTES.get(args.model), 1: CUBE_BYTES}.get(args.topo, LATTICE_BYTES.get(args.model))
-    flops_ns = RING_FLOPS[args.model]
-    alg_bytes_launch = bytes_ns / 4 * nodes
-    alg_flops_launch = flops_ns / 4 * nodes
-    peaks = {}
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
-            peaks = json.load(fh)
-    except OSError:
-        pass
-    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    fp64_peak_gflops = 2 * 504.3  # DFMA rate measured on GB300 (504.3 G/s), 2 flops each
-    achieved_gflops = alg_flops_launch / avg_launch_s / 1e9
-    achieved_gbs = alg_bytes_launch / avg_launch_s / 1e9
-    traffic = MEASURED_TRAFFIC.get((args.topo, args.model, N, R))
-    roofline = {"bound": "alu", "achieved": achieved_gflops, "peak": fp64_peak_gflops, "unit": "GFLOP/s",
-                "frac": achieved_gflops / fp64_peak_gflops, "traffic": traffic,
-                "hbm_achieved_gbs": achieved_gbs, "hbm_peak_gbs": hbm_peak,
-                "hbm_frac": achieved_gbs / hbm_peak,
-                "note": "FP64 pipe of measured DFMA throughput; HBM fraction from algorithmic bytes"}
+    # --- dominant kernel and its roofline
+    if args.topo == 0:
+        kb, kf = ring_kind_bytes(args.model), ring_kind_flops(args.model)
+    elif args.topo == 1:
+        kb, kf = CUBE_KIND_BYTES, CUBE_KIND_FLOPS
+    else:
+        per = LATTICE_BYTES[args.model] / 4
+        kb, kf = {"stage_or_x": 32.0, "node_pass": per - 32.0}, {"stage_or_x": 0.0, "node_pass": RING_FLOPS[3] / 4}
+    roofline = roofline_of(kinds, kb, kf, nodes, peaks, (args.topo, args.model, N, R))
+    launches = sum(d["launches"] for d in kinds.values())
 
     line = {"metric": "FP64 node-steps/s", "value": value, "unit": "node-steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config_of(args, N, R),
-            "e2e": {"value": e2e_value, "unit": "node-steps/s",
-                    "h2d_bytes_per_step": state_bytes / max(1, e2e_chunks[0]),
-                    "d2h_bytes_per_step": state_bytes / max(1, e2e_chunks[0])},
-            "gpu_launches": launches * {0: 1, 1: 3}.get(args.topo, 2), "roofline": roofline, "clocks": clk,
-            "autotune": tuned}
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.topo == 0:
-        line["cpu_baseline"] = cpu_baseline(args, N, R, params, args.cpu_seconds)
-    if not args.no_extra and args.topo == 0 and world == 1:
+            "data": "synthetic", "config": config_of(args, N, R, chunks), "e2e": e2e,
+            "gpu_launches": launches, "roofline": roofline, "clocks": ck.record,
+            "kernels": per_kind_table(kinds, nodes, kb, peaks), "peaks": peaks}
+    if args.topo == 1:
+        line["algorithmic_bytes_per_node_step"] = {"this_build": CUBE_BYTES, "survey": CUBE_BYTES_SURVEY,
+                                                   "hbm_frac_survey_bytes":
+                                                       CUBE_BYTES_SURVEY * value / 1e9 / peaks["hbm_gbs"],
+                                                   "hbm_frac_this_build":
+                                                       CUBE_BYTES * value / 1e9 / peaks["hbm_gbs"]}
+    if tuned:
+        line["autotune"] = tuned
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.model, args.topo, N, R, params, args.cpu_seconds)
+    if not args.no_extra and world == 1:
+        line["fhn_ring_1e6"] = bench_fhn_ring(args, stream, flush, peaks)
         line["small_ring"] = bench_small_ring(args, stream, flush)
-        line["cube"] = bench_cube(args, stream, flush)
+        line["rings"] = bench_rings(args, stream, flush, peaks)
         line["ball3d_inertia"] = bench_ball(args, stream, flush)
         line["ball3d_inertia_dp5"] = bench_ball_dp5(args)
         line["graph"] = bench_graph(args, stream, flush, ball=args.graph_ball)
-        line["roofline_sweep"] = bench_roofline_sweep(args, stream, flush)
-    if not args.no_batched:
+    if not args.no_batched and world == 1:
         line["batched"] = bench_batched(args, flush, stream)
         line["batched_dp5"] = bench_dp5_sweep(args, n_inst=args.instances)
-    if not args.no_served:
+    if not args.no_served and world == 1:
+        line["served_full"] = bench_served_full(args, stream, n_jobs=args.served_jobs)
         line["served"] = bench_served(args, stream)
         line["served_rate_sweep"] = bench_served_sweep(args, stream)
-    net.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -809,16 +1033,20 @@ def run_native(args):
 def run_only(args):
     import torch
     torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     if args.only == "dp5":
         out = bench_dp5_sweep(args, n_inst=args.instances, plain_inst=min(32, args.instances))
     elif args.only == "served":
         # the batched server alone on the scaled trace (args.instances jobs at 200 jobs/s)
         jobs = I.served_trace(n_jobs=args.instances, rate=200.0, seed=2415, size_scale=0.05, steps_scale=0.1)
-        inits = [I.initial_state(j.model, j.seed, j.job_id + 1, j.N ** 3 if j.topo == 1 else j.N) for j in jobs]
-        out = serve_trace(jobs, inits, 4096, 64 << 30, 32, torch.cuda.current_stream())
+        out = serve_trace(jobs, _trace_inits(jobs), 4096, 64 << 30, 32, stream)
+    elif args.only == "served_full":
+        out = bench_served_full(args, stream, n_jobs=args.served_jobs)
+    elif args.only == "rings":
+        out = bench_rings(args, stream, flush, measured_peaks())
     else:
-        flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
-        out = bench_graph(args, torch.cuda.current_stream(), flush, ball=args.graph_ball)
+        out = bench_graph(args, stream, flush, ball=args.graph_ball)
     print(json.dumps({"only": args.only, "result": out}), flush=True)
 
 

@@ -101,6 +101,7 @@ typedef enum {
 size_t sim_workspace_bytes(int model, int topology, int64_t N, int64_t radius);
 
 /* Create a network.  params: n_params doubles in the model's order (above).
+ * flags: SIM_FLAG_* above (0 for the defaults).
  * stream: a cudaStream_t (may be torch's current stream) or NULL.
  * The initial state is all zeros until sim_set_state().
  * Errors: SIM_EINVAL (unknown model/topology, 2*radius+1 > N, radius < 1,
@@ -163,6 +164,20 @@ int sim_set_node_param(sim_t h, int which, const double *host, int64_t n);
  * Errors from the device (SIM_ETIMEOUT, SIM_ENONFINITE) surface at the next
  * synchronising call. */
 int sim_step(sim_t h, int64_t n_steps, double dt);
+
+/* As sim_step, for measurement: the n_steps RK4 steps (1 <= n_steps <= 4096)
+ * are launched kernel by kernel, not as CUDA graphs, with a CUDA event recorded
+ * on the handle's stream after every launch, and the call synchronises.
+ * ms_by_kind[k] receives the summed time between consecutive events that ended
+ * with a kernel of kind k, launches_by_kind[k] their number (4 entries each):
+ * kind 0 = the fused stage kernel of a ring or link matrix (one per stage; the
+ * whole call for the cluster-resident small-ring kernel) or the x pass of a
+ * lattice, 1 = the y pass of the cube, 2 = the node pass of a lattice (the z
+ * pass of the cube, the chord gather of the ball and disk), 3 = unused.  The
+ * state advances exactly as with sim_step (the same bits).  Returns the device
+ * error status like sim_sync.  Errors: SIM_EINVAL (NULL handle or output,
+ * n_steps out of range, invalid dt), SIM_EDEVICE. */
+int sim_step_timed(sim_t h, int64_t n_steps, double dt, double *ms_by_kind, int64_t *launches_by_kind);
 
 /* Copy the state to host memory (synchronises the stream).  Returns the device
  * error status accumulated since creation, if any. */
@@ -247,7 +262,11 @@ int sim_dp5(sim_t h, const sim_dp5_opts *opts, sim_dp5_stats *stats);
  */
 typedef struct sim_batch_handle *sim_batch_t;
 
-/* Group existing networks into a batch.  The batch does not own the members;
+/* Group existing networks into a batch.  Members are networks made with
+ * sim_create (or sim_create_in / sim_create_graph), each with its own model,
+ * topology, size, parameters and state, so that a batch can mix everything a
+ * single network can be and members keep working on their own between batches;
+ * the batch does not own the members;
  * they must outlive it and must not be stepped on their own streams while the
  * batch's work is in flight.  stream: where the batch issues work (NULL =
  * legacy default).  Errors: SIM_EINVAL (no members, NULL or duplicate member),
@@ -261,7 +280,17 @@ int sim_batch_create(sim_batch_t *out, const sim_t *members, int n_members, void
 int sim_batch_set_budgets(sim_batch_t b, const int64_t *steps);
 
 /* Advance every member by n_steps RK4 steps of size dt (asynchronous; CUDA
- * graphs of 16 steps).  sim_steps_done() of each member is updated. */
+ * graphs of 16 steps).  sim_steps_done() of each member is updated.
+ * How a batch is launched: per RK4 stage one launch for all ring members of a
+ * model, whose CTAs are (member, 256-node sub-tile) work items listed in a
+ * device table built at sim_batch_create (CTA b reads its item directly); the
+ * stage boundary is the launch boundary, and the step loop is captured in CUDA
+ * graphs.  This takes the place of one persistent launch pulling (member, tile)
+ * items from a device work queue, which would need every stage of every member
+ * to wait, inside the launch, for the CTAs of its previous stage; here no CTA
+ * ever waits for another.  The 256-node sub-tile is fixed (it is the unit of
+ * the exact prefix); what sim_batch_autotune chooses is the number of nodes per
+ * thread (1 or 2). */
 int sim_batch_step(sim_batch_t b, int64_t n_steps, double dt);
 
 /* Dormand-Prince runs of every member, each with its own
@@ -362,6 +391,13 @@ int srv_wait_idle(srv_t s);
  * node-steps done, batches formed, device bytes in use}. */
 int srv_stats(srv_t s, int64_t *out6);
 
+/* Device-memory accounting of the admission loop: out3 = {bytes of the budget
+ * in use now, the largest number of bytes in use at any moment since
+ * srv_create (never above hbm_budget_bytes), jobs whose admission had to wait
+ * for device memory (the head of the queue did not fit the budget, or no free
+ * block of the arena was large enough, while a slot was free)}. */
+int srv_memory(srv_t s, int64_t *out3);
+
 /* out5 = the worker thread's cumulative time (seconds) in admission (network
  * creation and state upload), batch formation, stepping (launches of each chunk
  * and the wait for it), retirement (result download, release) and waiting for
@@ -389,9 +425,14 @@ void srv_destroy(srv_t s);
  * The first call on each device does a one-time set-up with that device
  * current (it looks up the static array's device address and copies the
  * fast-math tables into it); make that first call before any stream capture.
- * All calls share the static array: calls whose work overlaps on the GPU (other
- * streams or host threads) race with each other and must be serialised by the
- * caller. */
+ * The set-up is kept for the life of the process: calls after a
+ * cudaDeviceReset() of that device are not supported.
+ * All calls share the static array, which keeps the last call's contents (each
+ * call clears the counters and the error word it needs at zero): calls whose
+ * work overlaps on the GPU (other streams or host threads) race with each
+ * other and must be serialised by the caller.
+ * Errors: SIM_EINVAL (the same argument checks as sim_create, or N > 65536),
+ * SIM_ENONFINITE, SIM_EDEVICE; sim_last_error() gives the reason. */
 int sim_ring_step_noalloc(int model, int64_t N, int64_t radius, const double *params, int n_params,
                           unsigned flags, double *dev_state, const double *dev_node_param, int64_t n_steps,
                           double dt, void *stream);
@@ -403,7 +444,20 @@ int sim_ring_step_noalloc(int model, int64_t N, int64_t radius, const double *pa
  * rates of Eq. (1)).  Allocates and frees its own device buffers. */
 int sim_math_eval(int fn, const double *host_x, double *host_out, int64_t n);
 
-/* Message of the last non-OK status returned on this thread (never NULL). */
+/* Measured peak rate of one arithmetic pipe of the current device, for roofline
+ * denominators (not part of the method; a utility of the benchmark): kind 0 =
+ * FP64 fused multiply-adds per second (count 2 flops each), 1 = 64-bit integer
+ * multiply-highs (mul.hi.u64) per second, 2 = 32-bit integer multiply-adds per
+ * second.  Every thread of a grid of 8 CTAs per SM runs 8 independent dependent
+ * chains of the operation; one warm-up launch, then one launch timed with CUDA
+ * events (tens of milliseconds).  Allocates and frees 64 bytes of device memory
+ * and a stream; synchronous.  Errors: SIM_EINVAL (unknown kind or NULL output),
+ * SIM_EDEVICE. */
+int sim_probe_peak(int kind, double *ops_per_s);
+
+/* Message of the last non-OK status returned on this thread (never NULL).  It
+ * takes no handle: a failed sim_create has no handle to ask, and the message is
+ * per host thread, as handles are used from one thread each. */
 const char *sim_last_error(void);
 
 /* Free all device memory of the handle (synchronises first).  NULL is a no-op. */

@@ -48,6 +48,7 @@ SIGNATURES = {
     "sim_set_state_device": (_int, [_vp, _vp, _i64]),
     "sim_set_node_param": (_int, [_vp, _int, _vp, _i64]),
     "sim_step": (_int, [_vp, _i64, _dbl]),
+    "sim_step_timed": (_int, [_vp, _i64, _dbl, _dp, ctypes.POINTER(_i64)]),
     "sim_get_state": (_int, [_vp, _vp, _i64]),
     "sim_get_state_device": (_int, [_vp, _vp, _i64]),
     "sim_rhs": (_int, [_vp, _vp, _i64]),
@@ -64,6 +65,7 @@ SIGNATURES = {
     "srv_wait_idle": (_int, [_vp]),
     "srv_stats": (_int, [_vp, ctypes.POINTER(_i64)]),
     "srv_timings": (_int, [_vp, _dp]),
+    "srv_memory": (_int, [_vp, ctypes.POINTER(_i64)]),
     "sim_autotune": (_int, [_vp, ctypes.c_double, _i64, ctypes.POINTER(_int), ctypes.POINTER(_int)]),
     "sim_tune_info": (_int, [_vp, ctypes.POINTER(_int), ctypes.POINTER(_int)]),
     "sim_batch_autotune": (_int, [_vp, ctypes.c_double, _i64, ctypes.POINTER(_int)]),
@@ -72,6 +74,7 @@ SIGNATURES = {
     "sim_tune_clear": (_int, []),
     "srv_destroy": (None, [_vp]),
     "sim_math_eval": (_int, [_int, _vp, _vp, _i64]),
+    "sim_probe_peak": (_int, [_int, ctypes.POINTER(ctypes.c_double)]),
     "sim_ring_step_noalloc": (_int, [_int, _i64, _i64, _dp, _int, _uint, _vp, _vp, _i64, _dbl, _vp]),
     "sim_steps_done": (_i64, [_vp]),
     "sim_dp5": (_int, [_vp, ctypes.POINTER(DP5Opts), ctypes.POINTER(DP5Stats)]),

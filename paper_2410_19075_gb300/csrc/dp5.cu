@@ -92,10 +92,7 @@ __global__ void __launch_bounds__(kRingThreads, DpMinBlocks<M>::value)
             xn[v] = y[q];
             if (DS == 9 && cur == 1) Q.ybuf[0][q] = xn[v];
         }
-        double f[NQ];
-        Mo::coupled(P.mp, xn, f);
-#pragma unroll
-        for (int c = 0; c < NQ; ++c) qv[c] = to_fixed(f[c], P.F, P.lim, ok);
+        Mo::coupled_q(P.mp, xn, P.F, P.lim, ok, qv);
     }
     if (EDGE) {
         if (!ok) raise_error(P.err, ERR_RANGE);
@@ -139,10 +136,7 @@ __global__ void __launch_bounds__(kRingThreads, DpMinBlocks<M>::value)
 #pragma unroll
                 for (int g = 0; g < NX; ++g) P.xg[pout][g * N + i] = xn[XOFF + g];
             }
-            double f[NQ];
-            Mo::coupled(P.mp, xn, f);
-#pragma unroll
-            for (int c = 0; c < NQ; ++c) qv[c] = to_fixed(f[c], P.F, P.lim, ok);
+            Mo::coupled_q(P.mp, xn, P.F, P.lim, ok, qv);
         } else {
             const double atol = ctl->atol, rtol = ctl->rtol;
 #pragma unroll
@@ -195,10 +189,10 @@ __global__ void __launch_bounds__(kRingThreads, DpMinBlocks<M>::value)
             const double a0 = y[i], a1 = y5[i], f0 = k1[i], f1 = k[0];
             const double ph = (1.0 - th) * a0 + th * a1 +
                               th * (th - 1.0) * ((1.0 - 2.0 * th) * (a1 - a0) + (th - 1.0) * h * f0 + th * h * f1);
-            double sn, cn;
-            fast_sincos(ph, P.mp.tab, sn, cn);
-            ss = to_fixed(sn, P.F, 1, ok);
-            cc = to_fixed(cn, P.F, 1, ok);
+            int64_t s62, c62;
+            fixed_sincos(ph, P.mp.tab, s62, c62, ok);
+            ss = q62_to(s62, P.F);
+            cc = q62_to(c62, P.F);
         }
         ss = warp_sum_i64(ss);
         cc = warp_sum_i64(cc);

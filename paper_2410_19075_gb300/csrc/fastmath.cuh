@@ -1,29 +1,41 @@
-// FP64 elementary functions with few FP64 instructions.
+// Elementary functions of the node right-hand sides with few FP64 instructions.
 //
-// GB300 issues FP64 arithmetic at 2 operations per clock per SM, while integer
-// and FP32 instructions run at up to 64-128 per clock.  The routines below keep
-// every FP64 instruction that the result's accuracy needs and move the rest
-// (choosing the reduction integer, building doubles from integers, scaling by
-// powers of two) to the integer and FP32 pipes.
+// GB300 retires about 2 FP64 lanes per clock per SM, against 64 lanes of 32-bit
+// integer arithmetic and 128 of FP32.  The routines below keep every FP64
+// instruction that the result's accuracy needs and move the rest to the
+// integer and FP32 pipes; sin and cos need none at all.
 //
-// Methods (textbook, constants derived for this code from pi and ln 2 in
-// 300-bit arithmetic):
-//   sin/cos  Cody & Waite (1980) additive range reduction by pi/512 with a
-//            three-part constant, then the angle-addition formula around a table
-//            point j*pi/512 (the "accurate table" approach of Tang and Gal) with
-//            Taylor polynomials for sin r and cos r - 1, |r| <= ~3 pi/1024.
-//            13 FP64 instructions + one 16-byte table load.
+// Methods (textbook; constants derived for this code from pi and ln 2 in
+// high-precision arithmetic):
+//   sin/cos  fixed_sincos, in 64-bit integer arithmetic only: additive range
+//            reduction by pi/512 (Cody & Waite 1980) done exactly, as
+//            t = |x| * 512/pi with 64 fractional bits from the 117-bit product of
+//            x's significand and 512/pi rounded to 64 bits (relative error
+//            2^-69.4); k = nearest integer to t, r = (t - k) pi/512 with
+//            |r| <= pi/1024; Taylor polynomials sin r = r - r^3 (1/6 - r^2/120)
+//            and cos r - 1 = -r^2/2 + r^4/24 (first omitted terms below 2^-70
+//            and 2^-59); the angle-addition formula around the table point
+//            j pi/512, j = k mod 1024 (the "accurate table" approach of Tang and
+//            Gal): sin x = S_j + C_j sin r + S_j (cos r - 1) and
+//            cos x = C_j - S_j sin r + C_j (cos r - 1), (S_j, C_j) rounded to
+//            2^-62.  Every product is a signed 64 x 64 -> high-64 multiply on
+//            scaled operands (each quantity's scale is in its name).  The result
+//            is sin and cos on the grid 2^-62, within about 2^-59 of the true
+//            values for |x| < 256 (a host model of the same integer steps was
+//            checked against long double sinl/cosl over 2 * 10^7 arguments:
+//            worst error 8.25 * 2^-62); that grid is what the exact window sums
+//            consume.  |x| >= 256, Inf and NaN use the library routine.
 //   exp      Tang (1989) table-driven method: x = (64 m + j) ln2/64 + r,
 //            exp(x) = 2^m 2^(j/64) exp(r), degree-5 Taylor polynomial for
 //            exp(r) - 1, |r| <= ~ln2/128.  8 FP64 instructions.
 //   1/d      FP32 hardware reciprocal as the seed, then two Newton steps
 //            y <- y + y (1 - d y) in FP64.  4 FP64 instructions, error <= 1 ulp.
-// Accuracy (checked on the GPU against the C library, see the tests): within a
-// few ulp over the argument ranges used here; arguments outside them fall back
-// to the CUDA library routine.
+// Accuracy is checked on the GPU against the C library (see the tests).
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
+
+#include "common.cuh"
 
 namespace simk {
 
@@ -32,9 +44,21 @@ constexpr int kSinTab = 1024;  // sin/cos(j pi/512), j in [0, 1024)
 constexpr int kExpTab = 64;    // 2^(j/64), j in [0, 64)
 
 struct MathTables {
-    const double2 *sincos; // (sin, cos) of j*pi/512
-    const double *exp2j;   // 2^(j/64)
+    const double2 *sincos;     // (sin, cos) of j*pi/512
+    const double *exp2j;       // 2^(j/64)
+    const longlong2 *sincos_q; // (sin, cos) of j*pi/512 rounded onto the grid 2^-62
 };
+
+// The tables as one block of 64-bit words (host-filled in long double, uploaded
+// once per network or device): sincos (2 kSinTab doubles), exp2j (kExpTab
+// doubles), sincos_q (2 kSinTab int64).
+constexpr int kMathTableWords = 2 * kSinTab + kExpTab + 2 * kSinTab;
+__host__ __device__ inline MathTables math_tables_at(const void *block)
+{
+    const double *d = static_cast<const double *>(block);
+    return MathTables{reinterpret_cast<const double2 *>(d), d + 2 * kSinTab,
+                      reinterpret_cast<const longlong2 *>(d + 2 * kSinTab + kExpTab)};
+}
 
 // |x| as a float by truncating the mantissa (integer instructions; |x| must be
 // inside the float exponent range, which every caller checks first).
@@ -68,34 +92,79 @@ __device__ __forceinline__ int round_scaled(float xf, float scale)
     return __float_as_int(t) - 0x4B400000;
 }
 
-// pi/512 = C1 + C2 + C3 to about 150 bits (C1, C2 rounded to 32 significant
-// bits).  Each reduction step is one FMA, whose product is exact, so
-// r = x - k pi/512 is accurate to about one ulp of r.
-constexpr double kPio512_1 = 0x1.921fb544p-8;
-constexpr double kPio512_2 = 0x1.0b4611a6p-42;
-constexpr double kPio512_3 = 0x1.3198a2e037073p-77;
-constexpr float k512oPi = 162.974655f;
+// Constants of fixed_sincos (derived from pi in 80-digit arithmetic).
+constexpr uint64_t kPio512Inv56 = 0xa2f9836e4e44152aull; // round(512/pi * 2^56)
+constexpr int64_t kPio512Q69 = 3622009729038561421ll;    // round(pi/512 * 2^69)
+constexpr int64_t kSixthQ65 = 6148914691236517205ll;     // round(2^65 / 6)
+constexpr int64_t kInv120Q55 = 300239975158033ll;        // round(2^55 / 120)
+constexpr int64_t kInv24Q55 = 1501199875790165ll;        // round(2^55 / 24)
 
-__device__ __forceinline__ void fast_sincos(double x, const MathTables &T, double &s, double &c)
+// sin x and cos x rounded onto the grid 2^-62 (s62, c62 in [-2^62, 2^62]).
+// Integer instructions only on the fast path |x| < 256; beyond it, and for Inf
+// and NaN, the library routine (ok = false for a non-finite x).
+__device__ __forceinline__ void fixed_sincos(double x, const MathTables &T, int64_t &s62, int64_t &c62, bool &ok)
 {
-    const float xf = dbl_to_flt_trunc(x);
-    if (!(fabsf(xf) < 16384.0f)) { // large, Inf or NaN: library routine
+    const uint64_t b = (uint64_t)__double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7FF);
+    if (e >= 1023 + 8) {
+        double s, c;
         sincos(x, &s, &c);
+        s62 = to_fixed(s, 62, 1, ok);
+        c62 = to_fixed(c, 62, 1, ok);
         return;
     }
-    const int k = round_scaled(xf, k512oPi);
-    const double dk = int_to_dbl(k);
-    double r = fma(-dk, kPio512_1, x);
-    r = fma(-dk, kPio512_2, r);
-    r = fma(-dk, kPio512_3, r);
-    const double z = r * r;
-    // sin r = r + r^3 (-1/6 + r^2/120)           (|r| <= 0.01: next term < 2^-59 |r|)
-    const double sr = fma(r * z, fma(z, 1.0 / 120.0, -1.0 / 6.0), r);
-    // cos r - 1 = z (-1/2 + z (1/24 - z/720))
-    const double cm1 = z * fma(z, fma(z, -1.0 / 720.0, 1.0 / 24.0), -0.5);
-    const double2 t = __ldg(T.sincos + (k & (kSinTab - 1)));
-    s = fma(t.x, cm1, fma(t.y, sr, t.x));
-    c = fma(t.y, cm1, fma(-t.x, sr, t.y));
+    int64_t k = 0, f = 0; // x * 512/pi = k + f 2^-64
+    if (e >= 1023 - 60) { // below that, x is 0 on this grid
+        const uint64_t m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+        const uint64_t lo = m * kPio512Inv56, hi = __umul64hi(m, kPio512Inv56);
+        const int sh = 1067 - e; // the product times 2^-sh has 64 fractional bits; sh in [37, 104]
+        uint64_t th, tl;
+        if (sh < 64) {
+            th = hi >> sh;
+            tl = (lo >> sh) | (hi << (64 - sh));
+        } else {
+            th = 0;
+            tl = hi >> (sh - 64);
+        }
+        if (b >> 63) { // negative x: negate the 128-bit value
+            tl = ~tl + 1ull;
+            th = ~th + (tl == 0ull ? 1ull : 0ull);
+        }
+        k = (int64_t)th + (int64_t)(tl >> 63); // round to the nearest integer
+        f = (int64_t)tl;                       // t - k in [-1/2, 1/2) times 2^64
+    }
+    const int64_t r69 = __mul64hi(f, kPio512Q69);               // r 2^69
+    const int64_t z74 = __mul64hi(r69, r69);                    // r^2 2^74
+    const int64_t u65 = kSixthQ65 - __mul64hi(z74, kInv120Q55); // (1/6 - r^2/120) 2^65
+    const int64_t v79 = __mul64hi(r69, z74);                    // r^3 2^79
+    const int64_t sr69 = r69 - (__mul64hi(v79, u65) >> 11);    // sin r 2^69
+    const int64_t zz84 = __mul64hi(z74, z74);                   // r^4 2^84
+    const int64_t cm75 = __mul64hi(zz84, kInv24Q55) - z74;      // (cos r - 1) 2^75
+    const longlong2 t = __ldg(T.sincos_q + (k & (kSinTab - 1)));
+    s62 = t.x + (__mul64hi(t.y, sr69) >> 5) + (__mul64hi(t.x, cm75) >> 11);
+    c62 = t.y - (__mul64hi(t.x, sr69) >> 5) + (__mul64hi(t.y, cm75) >> 11);
+}
+
+// v 2^-62 rounded onto the coarser grid 2^-F (F <= 61), half up.
+__device__ __forceinline__ int64_t q62_to(int64_t v, int F)
+{
+    const int sh = 62 - F;
+    return (v + (1ll << (sh - 1))) >> sh;
+}
+
+// sin and cos as doubles, correctly rounded from fixed_sincos's values on the
+// grid 2^-62 (NaN for an infinite or NaN x).
+__device__ __forceinline__ void fast_sincos(double x, const MathTables &T, double &s, double &c)
+{
+    int64_t s62, c62;
+    bool ok = true;
+    fixed_sincos(x, T, s62, c62, ok);
+    if (!ok) {
+        s = c = x - x;
+        return;
+    }
+    s = fixed_to_double(s62, 62);
+    c = fixed_to_double(c62, 62);
 }
 
 // ln2/64 = L1 + L2 + L3 (L1, L2 rounded to 32 significant bits; two parts are

@@ -210,6 +210,7 @@ cudaError_t graph_step(const GraphPlan &g, double dt, cudaStream_t s)
     for (int stage = 1; stage <= 4; ++stage) {
         const cudaError_t e = launch_any(stage, g, dt, s);
         if (e != cudaSuccess) return e;
+        kernel_mark(s, 0);
     }
     return cudaSuccess;
 }

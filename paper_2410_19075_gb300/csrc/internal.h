@@ -165,7 +165,7 @@ struct LatticePlan {
     int F;            // fixed-point grid of the window sums
     ModelParams mp;
     double *y, *acc;  // D * nodes
-    double *f;        // 2 * nodes: sin, cos of the current stage-input phase
+    int64_t *f;       // 2 * nodes: sin, cos of the current stage-input phase on the grid 2^-62
     double *xs;       // NX * nodes: local stage-input variables (psi of model 3)
     int64_t *sx;      // cube: 2 * nodes window sums along x (SoA); ball, disk: per row,
                       // rs (sin, cos) pairs of the periodically extended inclusive
@@ -175,7 +175,8 @@ struct LatticePlan {
                       // x-window sums S_w (one load per chord) instead of the row prefixes
     int64_t *sxy;     // 2 * nodes: cube box sums over x and y
     i128 *partial;    // per-CTA partial sums of the order parameter
-    unsigned long long *done_ctr;
+    unsigned long long *done_ctr; // arrival counter of the sliding-window node passes (and the prologue)
+    unsigned long long *tile_ctr; // arrival counter of the tiled cube z pass (another CTA count per launch)
     unsigned *err;
     double *obs;
     int64_t obs_cap;
@@ -199,7 +200,7 @@ struct ElemDpPlan {
     double *err_part;    // nblk
     i128 *out_part;      // nblk * kDpMaxOut * 2
     unsigned long long *dp_ctr;
-    double *f;           // lattices: (sin, cos) of the stage input's phase (else nullptr)
+    int64_t *f;          // lattices: (sin, cos) of the stage input's phase on the grid 2^-62 (else nullptr)
     MathTables tab;
     int F;               // fixed-point grid of the dense order-parameter sums
     double *obs;
@@ -221,7 +222,8 @@ cudaError_t graph_dp_start(const GraphDpPlan &d, cudaStream_t s);
 cudaError_t graph_dp_attempt(const GraphDpPlan &d, cudaStream_t s);
 
 cudaError_t lattice_configure(); // once per process, before the first launch
-int64_t lattice_order_blocks(int topo, int64_t N1); // CTAs of the order-parameter passes
+int64_t lattice_order_blocks(int topo, int64_t N1); // CTAs of the order-parameter passes (sliding-window grid)
+int64_t lattice_partial_blocks(int topo, int64_t N1); // order-parameter partials to allocate (every grid)
 int64_t lattice_sx_elems(int topo, int64_t N1, int64_t P, bool wmode); // int64 elements of sx
 constexpr int64_t kLatticeWindowBudget = int64_t(8) << 30; // bytes of the per-w window arrays
 cudaError_t lattice_prologue(const LatticePlan &p, cudaStream_t s);
@@ -245,7 +247,36 @@ struct CubeBatchGroup {
 cudaError_t cube_batch_step(const CubeBatchGroup &g, double dt, cudaStream_t s); // one RK4 step of every member
 int lattice_row_warps(int64_t N1); // warps per CTA of the x pass for edge N1
 
-// Host-side values of the fast-math tables (long double, rounded to double).
-void fill_math_tables(double *sincos /* 2 * kSinTab */, double *exp2j /* kExpTab */);
+// Per-kernel timing of sim_step_timed: while set on the launching host thread,
+// every stage-kernel launch of ring_step, graph_step, lattice_step and
+// ring_cluster_steps records an event of its kind right after itself (kinds:
+// 0 fused ring / link-matrix stage kernel or lattice x pass, 1 cube y pass,
+// 2 lattice node pass (cube z pass, ball / disk gather)).  Never set during a
+// stream capture.
+struct KernelMarks {
+    cudaEvent_t *ev;
+    unsigned char *kind;
+    int cap, n;
+};
+extern thread_local KernelMarks *g_kernel_marks;
+inline void kernel_mark(cudaStream_t s, int kind)
+{
+    KernelMarks *m = g_kernel_marks;
+    if (m && m->n < m->cap && cudaEventRecord(m->ev[m->n], s) == cudaSuccess) m->kind[m->n++] = (unsigned char)kind;
+}
+
+// Derived model constants of ModelParams (c, q) for K links per node, computed
+// on the host in FP64 (sim_api.cu).
+void model_constants(int model, const double *params, double K, ModelParams &mp);
+
+// Set the calling thread's sim_last_error() message and return status
+// (report_cuda_error: SIM_EDEVICE with "what: <CUDA error string>").
+int report_error(int status, const char *msg);
+int report_cuda_error(cudaError_t e, const char *what);
+
+// Host-side values of the fast-math tables (long double, rounded to double, and
+// the fixed-point sin/cos table rounded onto 2^-62): kMathTableWords 64-bit
+// words in the layout of math_tables_at().
+void fill_math_tables(double *block);
 
 } // namespace simk

@@ -21,6 +21,8 @@
 //           read as S_w (one 16-byte load) or E(i + w) - E(i - w - 1) (two),
 //           O(P^2) resp. O(P) reads per node, fused with the right-hand side and
 //           RK4 update.
+#include <algorithm>
+
 #include "internal.h"
 
 namespace simk {
@@ -56,22 +58,22 @@ __device__ __forceinline__ void lattice_x_row(const LatticePlan &p, int64_t row,
     const int lane = threadIdx.x & 31;
     const int64_t N1 = p.N1, P = p.P, nodes = p.nodes;
     const int per = (int)((N1 + 31) / 32);
-    const double *__restrict__ fs = p.f + row * N1;
-    const double *__restrict__ fc = p.f + nodes + row * N1;
+    const int64_t *__restrict__ fs = p.f + row * N1;
+    const int64_t *__restrict__ fc = p.f + nodes + row * N1;
     for (int64_t mb = lane; mb < N1; mb += 32 * 8) { // coalesced, 8 loads in flight per lane
-        double vs[8], vc[8];
+        int64_t vs[8], vc[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             const int64_t m = mb + 32 * u;
-            vs[u] = m < N1 ? __ldg(fs + m) : 0.0;
-            vc[u] = m < N1 ? __ldg(fc + m) : 0.0;
+            vs[u] = m < N1 ? __ldg(fs + m) : 0;
+            vc[u] = m < N1 ? __ldg(fc + m) : 0;
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             const int64_t m = mb + 32 * u;
             if (m < N1) {
-                pre0[m + 1] = to_fixed(vs[u], p.F, 1, ok);
-                pre1[m + 1] = to_fixed(vc[u], p.F, 1, ok);
+                pre0[m + 1] = q62_to(vs[u], p.F);
+                pre1[m + 1] = q62_to(vc[u], p.F);
             }
         }
     }
@@ -281,7 +283,8 @@ __global__ void __launch_bounds__(kColThreads)
 // fixed-point (sin, cos) (exact i128, so the reduction order does not matter),
 // and the last CTA to finish sums every partial and records R.  bid / nblk: the
 // CTA's index among the network's CTAs of this launch and their number.
-__device__ void lattice_record_order(const LatticePlan &p, i128 ps, i128 pc, unsigned bid, unsigned nblk)
+__device__ void lattice_record_order(const LatticePlan &p, i128 ps, i128 pc, unsigned bid, unsigned nblk,
+                                     unsigned long long *ctr)
 {
     __shared__ i128 s_ws[32], s_wc[32];
     __shared__ bool s_last;
@@ -302,7 +305,7 @@ __device__ void lattice_record_order(const LatticePlan &p, i128 ps, i128 pc, uns
         st_i128(p.partial + 2 * bid, ts);
         st_i128(p.partial + 2 * bid + 1, tc);
         __threadfence();
-        s_last = last_arrival(p.done_ctr, nblk);
+        s_last = last_arrival(ctr, nblk);
     }
     __syncthreads();
     if (!s_last) return;
@@ -349,14 +352,15 @@ __device__ __forceinline__ void lattice_node(const LatticePlan &p, int64_t n, in
 #pragma unroll
         for (int v = 0; v < D; ++v) xn[v] = p.y[v * nodes + n];
     } else {
-        const double fo[2] = {p.f[n], p.f[nodes + n]};
-        const int64_t qo[2] = {to_fixed(fo[0], p.F, 1, ok), to_fixed(fo[1], p.F, 1, ok)};
+        const int64_t f62[2] = {p.f[n], p.f[nodes + n]};
+        const double fo[2] = {fixed_to_double(f62[0], 62), fixed_to_double(f62[1], 62)};
+        const int64_t qo[2] = {q62_to(f62[0], p.F), q62_to(f62[1], p.F)};
         const i128 W[2] = {(i128)W0, (i128)W1};
         double X[NX > 0 ? NX : 1];
 #pragma unroll
         for (int g = 0; g < NX; ++g) X[g] = STAGE == 1 ? p.y[(XOFF + g) * nodes + n] : p.xs[g * nodes + n];
         double k[D];
-        Model<M>::rhs(p.mp, p.F, fo, qo, W, X, 0.0, k);
+        Model<M>::rhs(p.mp, p.F, fo, qo, W, X, 0.0, k, -1, 1.0, f62);
 #pragma unroll
         for (int v = 0; v < D; ++v) {
             const double yv = p.y[v * nodes + n];
@@ -379,13 +383,13 @@ __device__ __forceinline__ void lattice_node(const LatticePlan &p, int64_t n, in
             for (int g = 0; g < NX; ++g) p.xs[g * nodes + n] = xn[XOFF + g];
         }
     }
-    double sn, cn;
-    fast_sincos(xn[0], p.mp.tab, sn, cn);
-    p.f[n] = sn;
-    p.f[nodes + n] = cn;
+    int64_t s62, c62;
+    fixed_sincos(xn[0], p.mp.tab, s62, c62, ok);
+    p.f[n] = s62;
+    p.f[nodes + n] = c62;
     if (STAGE == 0 || STAGE == 4) {
-        ps += to_fixed(sn, p.F, 1, ok);
-        pc += to_fixed(cn, p.F, 1, ok);
+        ps += q62_to(s62, p.F);
+        pc += q62_to(c62, p.F);
     }
 }
 
@@ -428,7 +432,7 @@ __device__ __forceinline__ void cube_z_col(const LatticePlan &p, const StepSize 
         }
     }
     if (!ok) raise_error(p.err, ERR_RANGE);
-    if (STAGE == 0 || STAGE == 4) lattice_record_order(p, ps, pc, bid, nblk);
+    if (STAGE == 0 || STAGE == 4) lattice_record_order(p, ps, pc, bid, nblk, p.done_ctr);
 }
 
 template <int M, int STAGE>
@@ -438,6 +442,145 @@ __global__ void __launch_bounds__(kColThreads) cube_z_kernel(LatticePlan p, cons
     cube_z_col<M, STAGE>(p, h, blockIdx.x, blockIdx.y, blockIdx.z,
                          (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x,
                          gridDim.x * gridDim.y * gridDim.z);
+}
+
+// ---------------------------------------------------------------------------
+// Tiled y and z passes of a single cube (the batched cubes keep the sliding
+// windows above and below; both give the same exact sums).  CTA (ib, m) loads
+// the 2 x N1 x BI block of one plane (y pass: plane k = m, i-block ib, all j) or
+// one row of columns (z pass: row j = m, i-block ib, all k) into shared memory,
+// so that every element crosses HBM once (a sliding window re-reads the element
+// leaving the window, 2P+1 rows or planes after it entered, long gone from L2
+// on large cubes).  The block is scanned in place into the exact inclusive
+// prefix along the window axis (wrapping int64 arithmetic, as the x pass), and
+// every window sum is Pe(a+P+1) - Pe(a-P) on its periodic extension.
+constexpr int kTileThreads = 256;
+constexpr int kTileSeg = 8; // segments of one column in the in-place scan
+
+// i-columns per tile: shared memory 2 (N1 + 1) BI 8 bytes stays below ~76 KB
+// (two or three CTAs per SM) and every row segment of a load is BI * 8 bytes.
+__host__ __device__ inline int cube_tile_bi(int64_t N1) { return N1 <= 297 ? 16 : N1 <= 594 ? 8 : 4; }
+
+__host__ __device__ inline size_t cube_tile_smem(int64_t N1)
+{
+    return (size_t)2 * (size_t)(N1 + 1) * (size_t)cube_tile_bi(N1) * sizeof(int64_t);
+}
+
+// Load src[c * nodes + base + a * stride + ii] for c < 2, a < N1, ii < BI into
+// tile[(c (N1 + 1) + a + 1) BI + ii] (0 past the cube's edge), and row 0 of both
+// components as 0; then every column (c, ii) becomes its inclusive prefix along a
+// (kTileSeg segments per column: segment sums, their exclusive scan, rewrite).
+// Called by every thread of the CTA; ends with a barrier.
+__device__ __forceinline__ void cube_tile_load_scan(const int64_t *__restrict__ src, int64_t nodes, int64_t base,
+                                                    int64_t stride, int64_t N1, int BI, int bi, int64_t *tile)
+{
+    const int tid = threadIdx.x;
+    const int lg = BI == 16 ? 4 : BI == 8 ? 3 : 2;
+    const int64_t per_c = N1 * BI;
+    for (int64_t e = tid; e < 2 * per_c; e += kTileThreads) {
+        const int c = e >= per_c ? 1 : 0;
+        const int64_t r = e - c * per_c;
+        const int64_t a = r >> lg;
+        const int ii = (int)(r & (BI - 1));
+        tile[(c * (N1 + 1) + a + 1) * BI + ii] = ii < bi ? __ldg(src + c * nodes + base + a * stride + ii) : 0;
+    }
+    if (tid < 2 * BI) tile[(tid / BI) * (N1 + 1) * BI + (tid & (BI - 1))] = 0;
+    __syncthreads();
+    // in-place inclusive prefix: thread (column col, segment sg) for col < 2 BI
+    __shared__ uint64_t s_seg[2 * 16 * kTileSeg];
+    const int ncol = 2 * BI;
+    const int64_t seg = (N1 + kTileSeg - 1) / kTileSeg;
+    const int col = tid % ncol, sg = tid / ncol;
+    const bool act = tid < ncol * kTileSeg;
+    const int c = col / BI, ii = col % BI;
+    uint64_t *colp = reinterpret_cast<uint64_t *>(tile) + (int64_t)c * (N1 + 1) * BI + ii;
+    const int64_t a0 = 1 + sg * seg, a1 = min(N1 + 1, a0 + seg);
+    if (act) {
+        uint64_t t = 0;
+        for (int64_t a = a0; a < a1; ++a) t += colp[a * BI];
+        s_seg[col * kTileSeg + sg] = t;
+    }
+    __syncthreads();
+    if (act) {
+        uint64_t run = 0;
+        for (int q = 0; q < sg; ++q) run += s_seg[col * kTileSeg + q];
+        for (int64_t a = a0; a < a1; ++a) {
+            run += colp[a * BI];
+            colp[a * BI] = run;
+        }
+    }
+    __syncthreads();
+}
+
+// Window sum of column (c, ii) of a scanned tile at position a (0 <= a < N1):
+// Pe(a + P + 1) - Pe(a - P) with Pe(x) = pre(x mod N1) + floor(x / N1) pre(N1).
+__device__ __forceinline__ int64_t cube_tile_window(const int64_t *tile, int64_t N1, int64_t P, int BI, int c, int ii,
+                                                    int64_t a)
+{
+    const uint64_t *colp = reinterpret_cast<const uint64_t *>(tile) + (int64_t)c * (N1 + 1) * BI + ii;
+    int64_t b = a + P + 1, lo = a - P;
+    uint64_t w = 0;
+    if (b > N1) {
+        b -= N1;
+        w += colp[N1 * BI];
+    }
+    if (lo < 0) {
+        lo += N1;
+        w += colp[N1 * BI];
+    }
+    return (int64_t)(w + colp[b * BI] - colp[lo * BI]);
+}
+
+// Tiled cube y pass: CTA (ib, k).
+__global__ void __launch_bounds__(kTileThreads) cube_y_tile_kernel(LatticePlan p)
+{
+    if (p.skip && *(const volatile int *)p.skip) return;
+    extern __shared__ int64_t tile[];
+    const int64_t N1 = p.N1, P = p.P, nodes = p.nodes;
+    const int BI = cube_tile_bi(N1);
+    const int64_t i0 = (int64_t)blockIdx.x * BI, k = blockIdx.y;
+    const int bi = (int)min((int64_t)BI, N1 - i0);
+    const int64_t base = k * N1 * N1 + i0;
+    cube_tile_load_scan(p.sx, nodes, base, N1, N1, BI, bi, tile);
+    const int lg = BI == 16 ? 4 : BI == 8 ? 3 : 2;
+    const int64_t per_c = N1 * BI;
+    for (int64_t e = threadIdx.x; e < 2 * per_c; e += kTileThreads) {
+        const int c = e >= per_c ? 1 : 0;
+        const int64_t r = e - c * per_c;
+        const int64_t j = r >> lg;
+        const int ii = (int)(r & (BI - 1));
+        if (ii < bi) p.sxy[c * nodes + base + j * N1 + ii] = cube_tile_window(tile, N1, P, BI, c, ii, j);
+    }
+}
+
+// Tiled cube z pass (stages 1-4): CTA (ib, j) scans the xy-window sums of its
+// columns along k, then runs the node update of each of its nodes (one per
+// thread in turn, consecutive i fastest).
+template <int M, int STAGE>
+__global__ void __launch_bounds__(kTileThreads) cube_z_tile_kernel(LatticePlan p, const StepSize h)
+{
+    if (STAGE == 1 && p.skip && *(const volatile int *)p.skip) return; // stage 1 records nothing
+    extern __shared__ int64_t tile[];
+    const int64_t N1 = p.N1, P = p.P, nodes = p.nodes, plane = N1 * N1;
+    const int BI = cube_tile_bi(N1);
+    const int64_t i0 = (int64_t)blockIdx.x * BI, j = blockIdx.y;
+    const int bi = (int)min((int64_t)BI, N1 - i0);
+    const int64_t base = j * N1 + i0;
+    cube_tile_load_scan(p.sxy, nodes, base, plane, N1, BI, bi, tile);
+    const int lg = BI == 16 ? 4 : BI == 8 ? 3 : 2;
+    i128 ps = 0, pc = 0;
+    bool ok = true;
+    for (int64_t r = threadIdx.x; r < N1 * BI; r += kTileThreads) {
+        const int64_t k = r >> lg;
+        const int ii = (int)(r & (BI - 1));
+        if (ii >= bi) continue;
+        const int64_t W0 = cube_tile_window(tile, N1, P, BI, 0, ii, k);
+        const int64_t W1 = cube_tile_window(tile, N1, P, BI, 1, ii, k);
+        lattice_node<M, STAGE>(p, base + k * plane + ii, W0, W1, h, ok, ps, pc);
+    }
+    if (!ok) raise_error(p.err, ERR_RANGE);
+    if (STAGE == 4)
+        lattice_record_order(p, ps, pc, blockIdx.y * gridDim.x + blockIdx.x, gridDim.x * gridDim.y, p.tile_ctr);
 }
 
 // Batched cube z pass (stages 1-4): CTA b is CTA b - yz_base[m] of member m.
@@ -499,13 +642,19 @@ __global__ void __launch_bounds__(kGatherThreads) lattice_gather_kernel(LatticeP
         lattice_node<M, STAGE>(p, n, (int64_t)w0, (int64_t)w1, h, ok, ps, pc);
     }
     if (!ok) raise_error(p.err, ERR_RANGE);
-    if (STAGE == 0 || STAGE == 4) lattice_record_order(p, ps, pc, blockIdx.x, gridDim.x);
+    if (STAGE == 0 || STAGE == 4) lattice_record_order(p, ps, pc, blockIdx.x, gridDim.x, p.done_ctr);
 }
 
 // ---------------------------------------------------------------------------
 static dim3 col_grid(int64_t N1)
 {
     return dim3((unsigned)((N1 + kColThreads - 1) / kColThreads), (unsigned)N1, (unsigned)col_segments(N1));
+}
+
+static dim3 tile_grid(int64_t N1)
+{
+    const int BI = cube_tile_bi(N1);
+    return dim3((unsigned)((N1 + BI - 1) / BI), (unsigned)N1, 1);
 }
 
 static unsigned gather_grid(const LatticePlan &p)
@@ -518,6 +667,15 @@ int64_t lattice_sx_elems(int topo, int64_t N1, int64_t P, bool wmode)
     if (topo == 1) return 2 * N1 * N1 * N1;
     const int64_t rows = topo == 3 ? N1 : N1 * N1;
     return wmode ? 2 * (P + 1) * rows * N1 : 2 * rows * (N1 + 2 * P + 1);
+}
+
+int64_t lattice_partial_blocks(int topo, int64_t N1)
+{
+    const int64_t a = lattice_order_blocks(topo, N1);
+    if (topo != 1) return a;
+    const dim3 g = tile_grid(N1);
+    const int64_t b = (int64_t)g.x * g.y;
+    return a > b ? a : b;
 }
 
 int64_t lattice_order_blocks(int topo, int64_t N1)
@@ -540,6 +698,15 @@ cudaError_t lattice_configure()
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(cube_batch_x_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kRowSmemMax);
+    // the largest tile of any edge: the top edge of each tile width
+    const int tmax = (int)std::max(std::max(cube_tile_smem(297), cube_tile_smem(594)), cube_tile_smem(1024));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(cube_y_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tmax);
+#define SIM_TILE_Z_ATTR(M, S)                                                                                          \
+    if (e == cudaSuccess)                                                                                              \
+        e = cudaFuncSetAttribute(cube_z_tile_kernel<M, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, tmax);
+    SIM_TILE_Z_ATTR(0, 1) SIM_TILE_Z_ATTR(0, 2) SIM_TILE_Z_ATTR(0, 3) SIM_TILE_Z_ATTR(0, 4)
+    SIM_TILE_Z_ATTR(3, 1) SIM_TILE_Z_ATTR(3, 2) SIM_TILE_Z_ATTR(3, 3) SIM_TILE_Z_ATTR(3, 4)
+#undef SIM_TILE_Z_ATTR
     return e;
 }
 
@@ -594,7 +761,8 @@ static cudaError_t launch_x(const LatticePlan &p, cudaStream_t s)
 template <int M, int STAGE>
 static cudaError_t launch_node_pass(const LatticePlan &p, double dt, cudaStream_t s)
 {
-    if (p.topo == 1) cube_z_kernel<M, STAGE><<<col_grid(p.N1), kColThreads, 0, s>>>(p, step_size(dt));
+    if (p.topo == 1)
+        cube_z_tile_kernel<M, STAGE><<<tile_grid(p.N1), kTileThreads, cube_tile_smem(p.N1), s>>>(p, step_size(dt));
     else if (p.wmode) lattice_gather_kernel<M, STAGE, true><<<gather_grid(p), kGatherThreads, 0, s>>>(p, step_size(dt));
     else lattice_gather_kernel<M, STAGE, false><<<gather_grid(p), kGatherThreads, 0, s>>>(p, step_size(dt));
     return cudaGetLastError();
@@ -613,16 +781,20 @@ static cudaError_t launch_stage(int stage, const LatticePlan &p, double dt, cuda
     }
     cudaError_t e = launch_x(p, s);
     if (e != cudaSuccess) return e;
+    kernel_mark(s, 0);
     if (p.topo == 1) {
-        cube_y_kernel<<<col_grid(p.N1), kColThreads, 0, s>>>(p);
+        cube_y_tile_kernel<<<tile_grid(p.N1), kTileThreads, cube_tile_smem(p.N1), s>>>(p);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        kernel_mark(s, 1);
     }
     switch (stage) {
-    case 1: return launch_node_pass<M, 1>(p, dt, s);
-    case 2: return launch_node_pass<M, 2>(p, dt, s);
-    case 3: return launch_node_pass<M, 3>(p, dt, s);
-    default: return launch_node_pass<M, 4>(p, dt, s);
+    case 1: e = launch_node_pass<M, 1>(p, dt, s); break;
+    case 2: e = launch_node_pass<M, 2>(p, dt, s); break;
+    case 3: e = launch_node_pass<M, 3>(p, dt, s); break;
+    default: e = launch_node_pass<M, 4>(p, dt, s); break;
     }
+    if (e == cudaSuccess) kernel_mark(s, 2);
+    return e;
 }
 
 static cudaError_t launch_any(int stage, const LatticePlan &p, double dt, cudaStream_t s)

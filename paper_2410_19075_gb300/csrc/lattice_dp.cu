@@ -47,11 +47,13 @@ __global__ void __launch_bounds__(kLdpThreads) lat_dp_input_kernel(const ElemDpP
         if (S == 7) d.y5[q] = x;
         if (v == 0) phase = x;
     }
-    if (d.f) { // lattices: the x pass reads the (sin, cos) of the phase
-        double sn, cn;
-        fast_sincos(phase, d.tab, sn, cn);
-        d.f[n] = sn;
-        d.f[nodes + n] = cn;
+    if (d.f) { // lattices: the x pass reads the (sin, cos) of the phase on the grid 2^-62
+        int64_t s62, c62;
+        bool ok = true;
+        fixed_sincos(phase, d.tab, s62, c62, ok);
+        d.f[n] = s62;
+        d.f[nodes + n] = c62;
+        if (!ok) raise_error(d.err, ERR_RANGE);
     }
 }
 
@@ -110,10 +112,10 @@ __global__ void __launch_bounds__(kLdpThreads) lat_dp_error_kernel(const ElemDpP
             const double a0 = d.y[n], a1 = d.y5[n], f0 = d.k[1][n], f1 = d.k[7][n];
             const double ph = (1.0 - th) * a0 + th * a1 +
                               th * (th - 1.0) * ((1.0 - 2.0 * th) * (a1 - a0) + (th - 1.0) * h * f0 + th * h * f1);
-            double sn, cn;
-            fast_sincos(ph, d.tab, sn, cn);
-            ss = to_fixed(sn, d.F, 1, ok);
-            cc = to_fixed(cn, d.F, 1, ok);
+            int64_t s62, c62;
+            fixed_sincos(ph, d.tab, s62, c62, ok);
+            ss = q62_to(s62, d.F);
+            cc = q62_to(c62, d.F);
         }
         ss = warp_sum_i128(ss);
         cc = warp_sum_i128(cc);

@@ -9,13 +9,17 @@
 
 namespace simk {
 
-void fill_math_tables(double *sincos, double *exp2j)
+void fill_math_tables(double *block)
 {
     const long double pi = 3.141592653589793238462643383279502884L;
+    double *sincos = block, *exp2j = block + 2 * kSinTab;
+    int64_t *sincos_q = reinterpret_cast<int64_t *>(block + 2 * kSinTab + kExpTab);
     for (int j = 0; j < kSinTab; ++j) {
         const long double a = pi * (long double)j / 512.0L;
         sincos[2 * j] = (double)sinl(a);
         sincos[2 * j + 1] = (double)cosl(a);
+        sincos_q[2 * j] = (int64_t)llroundl(sinl(a) * 4611686018427387904.0L); // 2^62
+        sincos_q[2 * j + 1] = (int64_t)llroundl(cosl(a) * 4611686018427387904.0L);
     }
     for (int j = 0; j < kExpTab; ++j) exp2j[j] = (double)exp2l((long double)j / 64.0L);
 }
@@ -44,8 +48,8 @@ extern "C" int sim_math_eval(int fn, const double *host_x, double *host_out, int
 {
     if (fn < 0 || fn > 4 || n < 0 || (n > 0 && (!host_x || !host_out))) return SIM_EINVAL;
     if (n == 0) return SIM_OK;
-    std::vector<double> tab(2 * kSinTab + kExpTab);
-    fill_math_tables(tab.data(), tab.data() + 2 * kSinTab);
+    std::vector<double> tab(kMathTableWords);
+    fill_math_tables(tab.data());
     double *d = nullptr;
     const size_t bytes = sizeof(double) * (tab.size() + 2 * (size_t)n);
     if (cudaMalloc(&d, bytes) != cudaSuccess) {
@@ -56,7 +60,7 @@ extern "C" int sim_math_eval(int fn, const double *host_x, double *host_out, int
     cudaError_t e = cudaMemcpy(dtab, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(dx, host_x, sizeof(double) * n, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
-        MathTables T{reinterpret_cast<const double2 *>(dtab), dtab + 2 * kSinTab};
+        const MathTables T = math_tables_at(dtab);
         math_eval_kernel<<<(unsigned)((n + 255) / 256), 256>>>(fn, dx, dout, n, T);
         e = cudaGetLastError();
     }

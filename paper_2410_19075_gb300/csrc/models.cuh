@@ -10,6 +10,10 @@
 
 namespace simk {
 
+// coupled_q() rounds a node's coupled quantity f(x) onto the grid 2^-F (sin and
+// cos of the phase through the integer-only fixed_sincos for the Kuramoto
+// models; u, v or V themselves otherwise), checking |f| < 2^lim (ok = false
+// outside it or for a non-finite value).
 // Every rhs() takes the node's window sums W; on a general link matrix it also
 // takes the node's link count (wsize, the FHN/HH self-term multiplier; -1 = the
 // network's) and a coupling scale cs = 1/K_i applied to the converted sums (the
@@ -18,6 +22,7 @@ namespace simk {
 // Derived constants, computed once on the host in FP64.
 struct ModelParams {
     double c[8];
+    int64_t q[2];     // Kuramoto models: cos alpha and sin alpha on the grid 2^-62
     MathTables tab;   // device tables of the fast elementary functions
     int64_t wsize;    // window size including the node itself (2R+1 or (2P+1)^3)
     int include_self; // 1: the node is one of its own links
@@ -25,29 +30,49 @@ struct ModelParams {
 
 template <int M> struct Model;
 
+// sin(phi + alpha) and cos(phi + alpha) of a Kuramoto node from its own sin phi,
+// cos phi, by the angle-addition formula in 64-bit integer arithmetic (no FP64
+// instruction): the own values on the grid 2^-62 (f62, where the caller has
+// them; else its window-sum grid values qo shifted up from 2^-F), times cos alpha
+// and sin alpha on the grid 2^-62, summed on the grid 2^-60 and converted once
+// (correctly rounded) to double.  Absolute error below 2^-58.
+__device__ __forceinline__ void angle_add(const ModelParams &P, const int64_t (&qo)[2], int F, const int64_t *f62,
+                                          double &sxa, double &cxa)
+{
+    const int64_t s = f62 ? f62[0] : qo[0] * (int64_t(1) << (62 - F));
+    const int64_t c = f62 ? f62[1] : qo[1] * (int64_t(1) << (62 - F));
+    const int64_t ca = P.q[0], sa = P.q[1];
+    sxa = fixed_to_double((int64_t)(__mul64hi(s, ca) + __mul64hi(c, sa)), 60);
+    cxa = fixed_to_double((int64_t)(__mul64hi(c, ca) - __mul64hi(s, sa)), 60);
+}
+
 // Kuramoto-Sakaguchi, Eq. (3) with m = 0, eps = 1 (Algorithm 1):
 //   dphi_i/dt = omega - (mu/K) sum_{j in W(i)} sin(phi_i - phi_j + alpha)
 //             = omega + (mu/K) [cos(phi_i+alpha) S_sin - sin(phi_i+alpha) S_cos],
 // S_sin = sum_j sin phi_j, S_cos = sum_j cos phi_j (angle-difference identity,
 // so the window only needs sums of sin and cos).
-// c = {omega, mu/K, sin alpha, cos alpha}.  Coupled quantity (sin phi, cos phi).
+// c = {omega, mu/K, sin alpha, cos alpha}, q = {cos alpha, sin alpha} on the grid
+// 2^-62.  Coupled quantity (sin phi, cos phi).
 template <> struct Model<0> {
     static constexpr int D = 1, NQ = 2, NX = 0, F = 53;
-    __device__ __forceinline__ static void coupled(const ModelParams &P, const double (&x)[D], double (&f)[NQ])
+    __device__ __forceinline__ static void coupled_q(const ModelParams &P, const double (&x)[D], int F, int,
+                                                     bool &ok, int64_t (&q)[NQ])
     {
-        fast_sincos(x[0], P.tab, f[0], f[1]);
+        int64_t s62, c62;
+        fixed_sincos(x[0], P.tab, s62, c62, ok);
+        q[0] = q62_to(s62, F);
+        q[1] = q62_to(c62, F);
     }
     __device__ __forceinline__ static void rhs(const ModelParams &P, int F_, const double (&fo)[NQ],
                                                const int64_t (&qo)[NQ], const i128 (&W)[NQ],
                                                const double *X, double Iext, double (&k)[D],
-                                               int64_t = 0, double cs = 1.0)
+                                               int64_t = 0, double cs = 1.0, const int64_t *f62 = nullptr)
     {
         const i128 ss = P.include_self ? W[0] : W[0] - (i128)qo[0];
         const i128 sc = P.include_self ? W[1] : W[1] - (i128)qo[1];
         const double Ss = cs * fixed_to_double_wide(ss, F_), Sc = cs * fixed_to_double_wide(sc, F_);
-        const double s = fo[0], c = fo[1];
-        const double sxa = s * P.c[3] + c * P.c[2]; // sin(phi + alpha)
-        const double cxa = c * P.c[3] - s * P.c[2]; // cos(phi + alpha)
+        double sxa, cxa;
+        angle_add(P, qo, F_, f62, sxa, cxa);
         k[0] = P.c[0] + P.c[1] * (cxa * Ss - sxa * Sc);
     }
 };
@@ -62,15 +87,16 @@ template <> struct Model<0> {
 // Coupled quantity (u, v).
 template <> struct Model<1> {
     static constexpr int D = 2, NQ = 2, NX = 0, F = 51;
-    __device__ __forceinline__ static void coupled(const ModelParams &, const double (&x)[D], double (&f)[NQ])
+    __device__ __forceinline__ static void coupled_q(const ModelParams &, const double (&x)[D], int F, int lim,
+                                                     bool &ok, int64_t (&q)[NQ])
     {
-        f[0] = x[0];
-        f[1] = x[1];
+        q[0] = to_fixed(x[0], F, lim, ok);
+        q[1] = to_fixed(x[1], F, lim, ok);
     }
     __device__ __forceinline__ static void rhs(const ModelParams &P, int F_, const double (&fo)[NQ],
                                                const int64_t (&qo)[NQ], const i128 (&W)[NQ],
                                                const double *X, double Iext, double (&k)[D],
-                                               int64_t wsize = -1, double cs = 1.0)
+                                               int64_t wsize = -1, double cs = 1.0, const int64_t * = nullptr)
     {
         const int64_t ws = wsize < 0 ? P.wsize : wsize;
         const double Cu = cs * fixed_to_double_wide(W[0] - (i128)qo[0] * ws, F_);
@@ -92,14 +118,15 @@ template <> struct Model<1> {
 // local variables.  Rates use the table-driven exp and reciprocal of fastmath.cuh.
 template <> struct Model<2> {
     static constexpr int D = 4, NQ = 1, NX = 3, F = 46;
-    __device__ __forceinline__ static void coupled(const ModelParams &, const double (&x)[D], double (&f)[NQ])
+    __device__ __forceinline__ static void coupled_q(const ModelParams &, const double (&x)[D], int F, int lim,
+                                                     bool &ok, int64_t (&q)[NQ])
     {
-        f[0] = x[0];
+        q[0] = to_fixed(x[0], F, lim, ok);
     }
     __device__ __forceinline__ static void rhs(const ModelParams &P, int F_, const double (&fo)[NQ],
                                                const int64_t (&qo)[NQ], const i128 (&W)[NQ],
                                                const double *X, double Iext, double (&k)[D],
-                                               int64_t wsize = -1, double cs = 1.0)
+                                               int64_t wsize = -1, double cs = 1.0, const int64_t * = nullptr)
     {
         const int64_t ws = wsize < 0 ? P.wsize : wsize;
         const double CV = cs * fixed_to_double_wide(W[0] - (i128)qo[0] * ws, F_);
@@ -124,25 +151,30 @@ template <> struct Model<2> {
 // Kuramoto-Sakaguchi with inertia, Eq. (3) with m != 0, as a first-order system:
 //   dphi/dt = psi,   dpsi/dt = ((mu/K) sum_{j in W(i)} sin(phi_j - phi_i - alpha) - eps psi) / m
 // with sum_j sin(phi_j - phi_i - alpha) = cos(phi_i+alpha) S_sin - sin(phi_i+alpha) S_cos.
-// c = {mu/(m K), eps/m, sin alpha, cos alpha}.  Coupled quantity (sin phi, cos phi);
+// c = {mu/(m K), eps/m, sin alpha, cos alpha}, q as for Model<0>.  Coupled
+// quantity (sin phi, cos phi);
 // psi is a local variable.
 template <> struct Model<3> {
     static constexpr int D = 2, NQ = 2, NX = 1, F = 53;
-    __device__ __forceinline__ static void coupled(const ModelParams &P, const double (&x)[D], double (&f)[NQ])
+    __device__ __forceinline__ static void coupled_q(const ModelParams &P, const double (&x)[D], int F, int,
+                                                     bool &ok, int64_t (&q)[NQ])
     {
-        fast_sincos(x[0], P.tab, f[0], f[1]);
+        int64_t s62, c62;
+        fixed_sincos(x[0], P.tab, s62, c62, ok);
+        q[0] = q62_to(s62, F);
+        q[1] = q62_to(c62, F);
     }
     __device__ __forceinline__ static void rhs(const ModelParams &P, int F_, const double (&fo)[NQ],
                                                const int64_t (&qo)[NQ], const i128 (&W)[NQ],
                                                const double *X, double Iext, double (&k)[D],
-                                               int64_t = 0, double cs = 1.0)
+                                               int64_t = 0, double cs = 1.0, const int64_t *f62 = nullptr)
     {
         const i128 ss = P.include_self ? W[0] : W[0] - (i128)qo[0];
         const i128 sc = P.include_self ? W[1] : W[1] - (i128)qo[1];
         const double Ss = cs * fixed_to_double_wide(ss, F_), Sc = cs * fixed_to_double_wide(sc, F_);
-        const double s = fo[0], c = fo[1], psi = X[0];
-        const double sxa = s * P.c[3] + c * P.c[2]; // sin(phi + alpha)
-        const double cxa = c * P.c[3] - s * P.c[2]; // cos(phi + alpha)
+        const double psi = X[0];
+        double sxa, cxa;
+        angle_add(P, qo, F_, f62, sxa, cxa);
         k[0] = psi;
         k[1] = fma(P.c[0], cxa * Ss - sxa * Sc, -P.c[1] * psi);
     }

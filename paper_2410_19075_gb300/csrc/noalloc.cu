@@ -10,7 +10,11 @@
 // static device array below, which each GPU that loads this library keeps until
 // the process exits.
 //
-// The array is sized for rings of at most kNoAllocMaxNodes nodes.  Every call
+// The array is sized for rings of at most kNoAllocMaxNodes nodes.  The first
+// call on a device looks the array's address up and fills its fast-math tables;
+// both are kept for the life of the process, so a cudaDeviceReset() between
+// calls (which gives the device a fresh, zeroed copy of the array at a possibly
+// different address) is not supported.  Every call
 // shares it and it keeps the last call's contents: the call clears the parts
 // that must start at zero (arrival counters, error word) itself.  Two calls whose
 // work overlaps on the GPU (different streams, or different host threads) race
@@ -38,14 +42,14 @@ struct DeviceSetup {
 };
 DeviceSetup g_setup[kMaxDevices];
 std::mutex g_setup_mu;
-double g_host_tables[2 * kSinTab + kExpTab]; // filled once, static (no allocation)
+double g_host_tables[kMathTableWords]; // filled once, static (no allocation)
 bool g_host_tables_ready = false;
 
 size_t up256(size_t x) { return (x + 255) / 256 * 256; }
 
 // The fast-math tables sit at the start of the scratch array (written once per
 // device); the ring buffers follow (sizes as in sim_create).
-constexpr size_t kTablesBytes = sizeof(double) * (2 * kSinTab + kExpTab);
+constexpr size_t kTablesBytes = sizeof(double) * kMathTableWords;
 struct NoAllocLayout {
     size_t acc, xg0, xg1, lam0, lam1, ingrp0, ingrp1, grpofs0, grpofs1, subtot, grptot, grpctr, ctrs, obs, total;
 };
@@ -79,21 +83,29 @@ NoAllocLayout noalloc_layout(int d, int nq, int nx, int64_t N)
 int setup_device(unsigned char **out)
 {
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SIM_EDEVICE;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return report_cuda_error(e, "sim_ring_step_noalloc: cudaGetDevice");
+    }
+    if (dev < 0 || dev >= kMaxDevices)
+        return report_error(SIM_EDEVICE, "sim_ring_step_noalloc: device index beyond the set-up table (64)");
     std::lock_guard<std::mutex> lock(g_setup_mu);
     if (!g_setup[dev].done) {
         void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) {
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || p == nullptr) {
             cudaGetLastError();
-            return SIM_EDEVICE;
+            return report_cuda_error(e, "sim_ring_step_noalloc: cudaGetSymbolAddress of the static array");
         }
         if (!g_host_tables_ready) {
-            fill_math_tables(g_host_tables, g_host_tables + 2 * kSinTab);
+            fill_math_tables(g_host_tables);
             g_host_tables_ready = true;
         }
-        if (cudaMemcpy(p, g_host_tables, kTablesBytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+        e = cudaMemcpy(p, g_host_tables, kTablesBytes, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
             cudaGetLastError();
-            return SIM_EDEVICE;
+            return report_cuda_error(e, "sim_ring_step_noalloc: copy of the fast-math tables");
         }
         g_setup[dev].scratch = static_cast<unsigned char *>(p);
         g_setup[dev].done = true;
@@ -110,18 +122,25 @@ extern "C" int sim_ring_step_noalloc(int model, int64_t N, int64_t radius, const
 {
     const int d = model == SIM_KS ? 1 : model == SIM_FHN ? 2 : model == SIM_HH ? 4 : 0;
     const int np = model == SIM_KS ? 3 : model == SIM_FHN ? 4 : model == SIM_HH ? 8 : -1;
-    if (d == 0 || !params || n_params != np || !dev_state) return SIM_EINVAL;
-    if (radius < 1 || N < 2 * radius + 1) return SIM_EINVAL;
-    if (N > kNoAllocMaxNodes) return SIM_EINVAL; // beyond the static scratch array
-    if (flags & ~SIM_FLAG_INCLUDE_SELF) return SIM_EINVAL;
-    if (n_steps < 0 || !(dt > 0.0) || !std::isfinite(dt)) return SIM_EINVAL;
+    if (d == 0) return report_error(SIM_EINVAL, "sim_ring_step_noalloc: model must be SIM_KS, SIM_FHN or SIM_HH");
+    if (!params || n_params != np) return report_error(SIM_EINVAL, "sim_ring_step_noalloc: wrong parameter count");
+    if (!dev_state) return report_error(SIM_EINVAL, "sim_ring_step_noalloc: dev_state is NULL");
+    if (radius < 1 || N < 2 * radius + 1)
+        return report_error(SIM_EINVAL, "sim_ring_step_noalloc: need radius >= 1 and 2 * radius + 1 <= N");
+    if (N > kNoAllocMaxNodes)
+        return report_error(SIM_EINVAL, "sim_ring_step_noalloc: N exceeds the static scratch array (65536 nodes)");
+    if (flags & ~SIM_FLAG_INCLUDE_SELF) return report_error(SIM_EINVAL, "sim_ring_step_noalloc: unknown flags");
+    if (n_steps < 0 || !(dt > 0.0) || !std::isfinite(dt))
+        return report_error(SIM_EINVAL, "sim_ring_step_noalloc: need n_steps >= 0 and a finite dt > 0");
     for (int i = 0; i < n_params; ++i)
-        if (!std::isfinite(params[i])) return SIM_EINVAL;
-    if ((model == SIM_FHN || model == SIM_HH) && params[0] == 0.0) return SIM_EINVAL;
+        if (!std::isfinite(params[i])) return report_error(SIM_EINVAL, "sim_ring_step_noalloc: non-finite parameter");
+    if ((model == SIM_FHN || model == SIM_HH) && params[0] == 0.0)
+        return report_error(SIM_EINVAL, "sim_ring_step_noalloc: eps (FHN) or Cm (HH) must be non-zero");
 
     const int nq = model == SIM_HH ? 1 : 2, nx = model == SIM_HH ? 3 : 0;
     const NoAllocLayout L = noalloc_layout(d, nq, nx, N);
-    if (L.total > kNoAllocScratchBytes) return SIM_EINVAL;
+    if (L.total > kNoAllocScratchBytes)
+        return report_error(SIM_EINVAL, "sim_ring_step_noalloc: the ring's buffers exceed the static scratch array");
 
     unsigned char *b = nullptr;
     int st = setup_device(&b);
@@ -133,27 +152,8 @@ extern "C" int sim_ring_step_noalloc(int model, int64_t N, int64_t radius, const
     const bool self = (flags & SIM_FLAG_INCLUDE_SELF) != 0;
     mp.include_self = self ? 1 : 0;
     mp.wsize = 2 * radius + 1;
-    const double K = (double)(self ? mp.wsize : mp.wsize - 1);
-    if (model == SIM_KS) {
-        mp.c[0] = params[0];
-        mp.c[1] = params[1] / K;
-        mp.c[2] = std::sin(params[2]);
-        mp.c[3] = std::cos(params[2]);
-    } else if (model == SIM_FHN) {
-        const double ph = params[3], inv_eps = 1.0 / params[0], sK = params[2] / K;
-        mp.c[0] = inv_eps;
-        mp.c[1] = params[1];
-        mp.c[2] = sK * std::cos(ph) * inv_eps;
-        mp.c[3] = sK * std::sin(ph) * inv_eps;
-        mp.c[4] = -sK * std::sin(ph);
-        mp.c[5] = sK * std::cos(ph);
-    } else {
-        mp.c[0] = 1.0 / params[0];
-        for (int i = 1; i < 7; ++i) mp.c[i] = params[i];
-        mp.c[7] = params[7] / K;
-    }
-    mp.tab.sincos = reinterpret_cast<const double2 *>(b);
-    mp.tab.exp2j = reinterpret_cast<const double *>(b) + 2 * kSinTab;
+    model_constants(model, params, (double)(self ? mp.wsize : mp.wsize - 1), mp);
+    mp.tab = math_tables_at(b);
 
     RingPlan p{};
     p.model = model;
@@ -198,9 +198,12 @@ extern "C" int sim_ring_step_noalloc(int model, int64_t N, int64_t radius, const
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        return SIM_EDEVICE;
+        return report_cuda_error(e, "sim_ring_step_noalloc");
     }
-    if (err_word & ERR_RANGE) return SIM_ENONFINITE;
-    if (err_word & ERR_TIMEOUT) return SIM_ETIMEOUT;
+    if (err_word & ERR_RANGE)
+        return report_error(SIM_ENONFINITE,
+                            "sim_ring_step_noalloc: the state became non-finite or left the fixed-point range");
+    if (err_word & ERR_TIMEOUT)
+        return report_error(SIM_ETIMEOUT, "sim_ring_step_noalloc: a device-side wait exceeded its bound");
     return SIM_OK;
 }

@@ -188,10 +188,10 @@ __device__ __forceinline__ void ring_stage_body2(const RingPlan &P, const RingSt
                 for (int g = 0; g < NX; ++g) a.x_out[g * N + i] = xn[XOFF + g];
             }
         }
-        double f[NQ];
-        Mo::coupled(P.mp, xn, f);
+        int64_t qn[NQ];
+        Mo::coupled_q(P.mp, xn, P.F, P.lim, ok, qn);
 #pragma unroll
-        for (int c = 0; c < NQ; ++c) qv[c][u] = to_fixed(f[c], P.F, P.lim, ok);
+        for (int c = 0; c < NQ; ++c) qv[c][u] = qn[c];
     }
     if (!ok) raise_error(P.err, ERR_RANGE);
     // the prologue writes both prefix forms (a later kernel of either kind may read it)
@@ -351,6 +351,7 @@ cudaError_t ring_step(const RingPlan &p, double dt, cudaStream_t s)
     for (int stage = 1; stage <= 4; ++stage) {
         const cudaError_t e = launch_any(stage, p, dt, s);
         if (e != cudaSuccess) return e;
+        kernel_mark(s, 0);
     }
     return cudaSuccess;
 }

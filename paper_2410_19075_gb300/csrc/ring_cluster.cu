@@ -160,10 +160,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
     // state was set)
 #pragma unroll
     for (int k = 0; k < MPT; ++k) {
-        double f[NQ];
-        Mo::coupled(P.mp, y[k], f);
-#pragma unroll
-        for (int c = 0; c < NQ; ++c) qn[k][c] = to_fixed(f[c], P.F, P.lim, ok);
+        Mo::coupled_q(P.mp, y[k], P.F, P.lim, ok, qn[k]);
     }
     broadcast(qbuf0);
     cluster.sync();
@@ -208,10 +205,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
                 }
 #pragma unroll
                 for (int g = 0; g < NX; ++g) xs[k][g] = xn[XOFF + g];
-                double f[NQ];
-                Mo::coupled(P.mp, xn, f);
-#pragma unroll
-                for (int c = 0; c < NQ; ++c) qn[k][c] = to_fixed(f[c], P.F, P.lim, ok);
+                Mo::coupled_q(P.mp, xn, P.F, P.lim, ok, qn[k]);
             }
             cur ^= 1;
             broadcast(cur ? qbuf1 : qbuf0);
@@ -318,12 +312,15 @@ cudaError_t ring_cluster_steps(const RingPlan &p, double dt, int64_t n_steps, cu
 {
     const int cl = cluster_size_for(p.N);
     if (cl == 0) return cudaErrorInvalidValue;
+    cudaError_t e;
     switch (p.model) {
-    case 0: return launch_cluster<0>(p, dt, n_steps, cl, s);
-    case 1: return launch_cluster<1>(p, dt, n_steps, cl, s);
-    case 2: return launch_cluster<2>(p, dt, n_steps, cl, s);
-    default: return launch_cluster<3>(p, dt, n_steps, cl, s);
+    case 0: e = launch_cluster<0>(p, dt, n_steps, cl, s); break;
+    case 1: e = launch_cluster<1>(p, dt, n_steps, cl, s); break;
+    case 2: e = launch_cluster<2>(p, dt, n_steps, cl, s); break;
+    default: e = launch_cluster<3>(p, dt, n_steps, cl, s); break;
     }
+    if (e == cudaSuccess) kernel_mark(s, 0);
+    return e;
 }
 
 } // namespace simk

@@ -594,10 +594,7 @@ __device__ __forceinline__ void stage_body(const RingPlan &P, const RingStageIO 
             }
         }
         // a2: coupled quantity of the next stage input on the fixed-point grid
-        double f[NQ];
-        Mo::coupled(P.mp, xn, f);
-#pragma unroll
-        for (int c = 0; c < NQ; ++c) qv[c] = to_fixed(f[c], P.F, P.lim, ok);
+        Mo::coupled_q(P.mp, xn, P.F, P.lim, ok, qv);
     }
     if (!ok) raise_error(P.err, ERR_RANGE);
     constexpr bool RECORD = (M == 0 || M == 3) && (STAGE == 0 || STAGE == 4);

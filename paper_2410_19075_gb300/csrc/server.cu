@@ -97,6 +97,7 @@ class Arena {
 
 struct Job {
     int64_t id = 0;
+    bool waited_hbm = false; // its admission was held back by the budget or by fragmentation
     int64_t arena_at = -1;
     int model = 0, topo = 0;
     int64_t N = 0, R = 0, steps = 0, left = 0;
@@ -127,6 +128,8 @@ struct srv_handle {
     bool stop = false;
     int64_t next_id = 0;
     size_t used = 0;
+    size_t peak_used = 0;     // largest `used` seen at any admission
+    int64_t hbm_waits = 0;    // jobs whose admission waited for device memory while a slot was free
     // statistics
     int64_t completed = 0, node_steps = 0, batches_formed = 0, ticks = 0;
     // worker time by phase (seconds): admission, batch formation, stepping
@@ -220,12 +223,18 @@ void worker_loop(srv_t s)
             }
             while (!s->queue.empty() && (int)(s->resident.size() + to_admit.size()) < s->max_slots) {
                 Job *j = s->queue.front();
-                if (s->used + j->bytes > s->budget) break;
-                const int64_t at = s->arena.take(j->bytes);
-                if (at < 0) break; // fragmented: wait for retirements
+                const int64_t at = s->used + j->bytes > s->budget ? -1 : s->arena.take(j->bytes);
+                if (at < 0) { // over the budget, or fragmented: wait for retirements
+                    if (!j->waited_hbm) {
+                        j->waited_hbm = true;
+                        s->hbm_waits++;
+                    }
+                    break;
+                }
                 j->arena_at = at;
                 s->queue.pop_front();
                 s->used += j->bytes;
+                if (s->used > s->peak_used) s->peak_used = s->used;
                 to_admit.push_back(j);
             }
         }
@@ -460,6 +469,16 @@ int srv_stats(srv_t s, int64_t *out6)
     out6[3] = s->node_steps;
     out6[4] = s->batches_formed;
     out6[5] = (int64_t)s->used;
+    return SIM_OK;
+}
+
+int srv_memory(srv_t s, int64_t *out3)
+{
+    if (!s || !out3) return SIM_EINVAL;
+    std::lock_guard<std::mutex> lock(s->mu);
+    out3[0] = (int64_t)s->used;
+    out3[1] = (int64_t)s->peak_used;
+    out3[2] = s->hbm_waits;
     return SIM_OK;
 }
 

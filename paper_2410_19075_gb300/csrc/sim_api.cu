@@ -16,6 +16,8 @@
 
 using namespace simk;
 
+thread_local KernelMarks *simk::g_kernel_marks = nullptr;
+
 namespace {
 
 thread_local std::string g_last_error = "no error";
@@ -30,6 +32,21 @@ int cuda_fail(cudaError_t e, const char *what)
 {
     return fail(SIM_EDEVICE, std::string(what) + ": " + cudaGetErrorString(e));
 }
+
+} // namespace
+
+// The thread's last-error message for the other translation units (internal.h).
+int simk::report_error(int status, const char *msg)
+{
+    return fail(status, msg);
+}
+
+int simk::report_cuda_error(cudaError_t e, const char *what)
+{
+    return cuda_fail(e, what);
+}
+
+namespace {
 
 constexpr int64_t kObsCap = 65536;
 constexpr int kGraphChunk = 16; // RK4 steps per captured graph
@@ -183,10 +200,10 @@ Layout layout_of(int model, int topo, int64_t N, int64_t R, unsigned flags = 0)
         L.facc = take(flat ? sizeof(unsigned) * 4 * 4 * nq * ngroups : 0);
     } else {
         const int64_t n = nodes_of(topo, N);
-        const int64_t nblk = lattice_order_blocks(topo, N);
+        const int64_t nblk = lattice_partial_blocks(topo, N);
         L.y = take(sizeof(double) * d * n);
         L.acc = take(sizeof(double) * d * n);
-        L.f = take(sizeof(double) * 2 * n);
+        L.f = take(sizeof(int64_t) * 2 * n);
         L.xs = take(sizeof(double) * model_nx(model) * n);
         L.sx = take(sizeof(int64_t) * lattice_sx_elems(topo, N, R, lattice_wmode(topo, N, R, flags)));
         L.sxy = take(topo == SIM_CUBE3D ? sizeof(int64_t) * 2 * n : 0);
@@ -195,7 +212,7 @@ Layout layout_of(int model, int topo, int64_t N, int64_t R, unsigned flags = 0)
     }
     L.ctrs = take(64);
     L.obs = take(sizeof(double) * kObsCap);
-    L.tabs = take(sizeof(double) * (2 * kSinTab + kExpTab));
+    L.tabs = take(sizeof(double) * kMathTableWords);
     L.total = o;
     return L;
 }
@@ -349,36 +366,22 @@ int prologue(sim_t h)
 
 } // namespace
 
-extern "C" {
-
-size_t sim_workspace_bytes(int model, int topology, int64_t N, int64_t radius)
-{
-    double dummy[8] = {1, 1, 1, 1, 1, 1, 1, 1};
-    if (validate(model, topology, N, radius, dummy, model_nparams(model))) return 0;
-    return layout_of(model, topology, N, radius).total;
-}
-
-static const double *host_tables()
-{
-    static double tab[2 * kSinTab + kExpTab];
-    static std::once_flag once;
-    std::call_once(once, [] { fill_math_tables(tab, tab + 2 * kSinTab); });
-    return tab;
-}
-
 // Derived model constants for K links per node (FP64 on the host).
-static void model_constants(int model, const double *params, double K, ModelParams &mp)
+void simk::model_constants(int model, const double *params, double K, ModelParams &mp)
 {
-    if (model == SIM_KS) {
-        mp.c[0] = params[0];
-        mp.c[1] = params[1] / K;
-        mp.c[2] = std::sin(params[2]);
-        mp.c[3] = std::cos(params[2]);
-    } else if (model == SIM_KSI) {
-        mp.c[0] = params[2] / (params[0] * K); // mu / (m K)
-        mp.c[1] = params[1] / params[0];       // eps / m
-        mp.c[2] = std::sin(params[3]);
-        mp.c[3] = std::cos(params[3]);
+    if (model == SIM_KS || model == SIM_KSI) {
+        const double alpha = model == SIM_KS ? params[2] : params[3];
+        if (model == SIM_KS) {
+            mp.c[0] = params[0];
+            mp.c[1] = params[1] / K;
+        } else {
+            mp.c[0] = params[2] / (params[0] * K); // mu / (m K)
+            mp.c[1] = params[1] / params[0];       // eps / m
+        }
+        mp.c[2] = std::sin(alpha);
+        mp.c[3] = std::cos(alpha);
+        mp.q[0] = (int64_t)std::llround(std::ldexp(mp.c[3], 62)); // exact: |cos| <= 1, 53-bit significand
+        mp.q[1] = (int64_t)std::llround(std::ldexp(mp.c[2], 62));
     } else if (model == SIM_FHN) {
         const double ph = params[3], inv_eps = 1.0 / params[0], sK = params[2] / K;
         mp.c[0] = inv_eps;
@@ -392,6 +395,23 @@ static void model_constants(int model, const double *params, double K, ModelPara
         for (int i = 1; i < 7; ++i) mp.c[i] = params[i];
         mp.c[7] = params[7] / K;
     }
+}
+
+extern "C" {
+
+size_t sim_workspace_bytes(int model, int topology, int64_t N, int64_t radius)
+{
+    double dummy[8] = {1, 1, 1, 1, 1, 1, 1, 1};
+    if (validate(model, topology, N, radius, dummy, model_nparams(model))) return 0;
+    return layout_of(model, topology, N, radius).total;
+}
+
+static const double *host_tables()
+{
+    static double tab[kMathTableWords];
+    static std::once_flag once;
+    std::call_once(once, [] { fill_math_tables(tab); });
+    return tab;
 }
 
 static int create_impl(sim_t *out, int model, int topology, int64_t N, int64_t radius, const double *params,
@@ -447,7 +467,7 @@ static int create_impl(sim_t *out, int model, int topology, int64_t N, int64_t r
 
     // Tables of the fast elementary functions (from a static host copy, so the
     // copy needs no synchronisation).
-    e = cudaMemcpyAsync(b + L.tabs, host_tables(), sizeof(double) * (2 * kSinTab + kExpTab), cudaMemcpyHostToDevice,
+    e = cudaMemcpyAsync(b + L.tabs, host_tables(), sizeof(double) * kMathTableWords, cudaMemcpyHostToDevice,
                         h->stream);
     if (e != cudaSuccess) {
         sim_destroy(h);
@@ -455,8 +475,7 @@ static int create_impl(sim_t *out, int model, int topology, int64_t N, int64_t r
     }
     // Derived model constants (FP64 on the host).
     ModelParams mp{};
-    mp.tab.sincos = reinterpret_cast<const double2 *>(b + L.tabs);
-    mp.tab.exp2j = reinterpret_cast<const double *>(b + L.tabs) + 2 * kSinTab;
+    mp.tab = math_tables_at(b + L.tabs);
     const bool self = (flags & SIM_FLAG_INCLUDE_SELF) != 0;
     mp.include_self = self ? 1 : 0;
     mp.wsize = window_of(topology, radius);
@@ -523,7 +542,7 @@ static int create_impl(sim_t *out, int model, int topology, int64_t N, int64_t r
         p.mp = mp;
         p.y = reinterpret_cast<double *>(b + L.y);
         p.acc = reinterpret_cast<double *>(b + L.acc);
-        p.f = reinterpret_cast<double *>(b + L.f);
+        p.f = reinterpret_cast<int64_t *>(b + L.f);
         p.xs = reinterpret_cast<double *>(b + L.xs);
         p.sx = reinterpret_cast<int64_t *>(b + L.sx);
         p.rs = N + 2 * radius + 1;
@@ -531,6 +550,7 @@ static int create_impl(sim_t *out, int model, int topology, int64_t N, int64_t r
         p.sxy = reinterpret_cast<int64_t *>(b + L.sxy);
         p.partial = reinterpret_cast<i128 *>(b + L.partial);
         p.done_ctr = ticket;
+        p.tile_ctr = ctrs + 4;
         p.err = h->err;
         p.obs = h->obs;
         p.obs_cap = kObsCap;
@@ -809,6 +829,54 @@ int sim_step(sim_t h, int64_t n_steps, double dt)
         h->steps_done += chunk;
     }
     return SIM_OK;
+}
+
+int sim_step_timed(sim_t h, int64_t n_steps, double dt, double *ms_by_kind, int64_t *launches_by_kind)
+{
+    if (!h) return fail(SIM_EINVAL, "NULL handle");
+    if (n_steps < 1 || n_steps > 4096) return fail(SIM_EINVAL, "n_steps must be in [1, 4096]");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(SIM_EINVAL, "dt must be finite and > 0");
+    if (!ms_by_kind || !launches_by_kind) return fail(SIM_EINVAL, "NULL output");
+    if (ring_flat(h)) {
+        if (use_cluster(h)) {
+            h->pfx = 1;
+        } else {
+            if (!(h->pfx & 2)) {
+                const cudaError_t e = ring_refresh(h, h->stream);
+                if (e != cudaSuccess) return cuda_fail(e, "prefix refresh");
+            }
+            h->pfx = 2;
+        }
+    }
+    const int per_step = use_cluster(h) ? 1 : h->topo == SIM_CUBE3D ? 12 : is_lattice(h->topo) ? 8 : 4;
+    const int cap = (int)(use_cluster(h) ? 1 : per_step * n_steps);
+    std::vector<cudaEvent_t> ev(cap + 1, nullptr);
+    std::vector<unsigned char> kind(cap, 0);
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i <= cap && e == cudaSuccess; ++i) e = cudaEventCreate(&ev[i]);
+    KernelMarks marks{ev.data() + 1, kind.data(), cap, 0};
+    if (e == cudaSuccess) e = cudaEventRecord(ev[0], h->stream);
+    if (e == cudaSuccess) {
+        g_kernel_marks = &marks;
+        e = launch_steps(h, n_steps, dt, h->stream);
+        g_kernel_marks = nullptr;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    for (int k = 0; k < 4; ++k) {
+        ms_by_kind[k] = 0.0;
+        launches_by_kind[k] = 0;
+    }
+    for (int i = 0; i < marks.n && e == cudaSuccess; ++i) {
+        float ms = 0.0f;
+        e = cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+        ms_by_kind[kind[i] & 3] += ms;
+        launches_by_kind[kind[i] & 3] += 1;
+    }
+    for (cudaEvent_t x : ev)
+        if (x) cudaEventDestroy(x);
+    if (e != cudaSuccess) return cuda_fail(e, "sim_step_timed");
+    h->steps_done += n_steps;
+    return check_device_error(h);
 }
 
 static int get_state_impl(sim_t h, double *dst, int64_t n_values, cudaMemcpyKind kind)

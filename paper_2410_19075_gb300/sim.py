@@ -35,6 +35,14 @@ def math_eval(fn: int, x) -> np.ndarray:
     return out
 
 
+def probe_peak(kind: int) -> float:
+    """Measured peak rate of one arithmetic pipe (``sim_probe_peak``): kind 0 =
+    FP64 FMAs/s, 1 = 64-bit multiply-highs/s, 2 = 32-bit integer multiply-adds/s."""
+    v = ctypes.c_double(0.0)
+    check(lib().sim_probe_peak(int(kind), ctypes.byref(v)))
+    return float(v.value)
+
+
 def _dp5_opts(t_end, rtol, atol, h0, t0=0.0, h_max=0.0, out_dt=0.0, max_attempts=10 ** 6):
     return DP5Opts(float(t0), float(t_end), float(rtol), float(atol), float(h0), float(h_max), float(out_dt),
                    int(max_attempts))
@@ -127,6 +135,16 @@ class Network:
 
     def step(self, n_steps: int, dt: float):
         check(lib().sim_step(self._handle(), int(n_steps), float(dt)))
+
+    def step_timed(self, n_steps: int, dt: float) -> dict:
+        """``sim_step_timed``: n_steps RK4 steps launched kernel by kernel with
+        an event after each; per kernel kind the summed milliseconds and the
+        launch count (kinds: stage or x pass, cube y pass, lattice node pass)."""
+        ms = (ctypes.c_double * 4)()
+        n = (ctypes.c_int64 * 4)()
+        check(lib().sim_step_timed(self._handle(), int(n_steps), float(dt), ms, n))
+        names = ("stage_or_x", "cube_y", "node_pass", "other")
+        return {names[k]: {"ms": float(ms[k]), "launches": int(n[k])} for k in range(4) if n[k]}
 
     def dp5(self, t_end, rtol, atol, h0, t0=0.0, h_max=0.0, out_dt=0.0, max_attempts=10 ** 6):
         """Adaptive Dormand-Prince 5(4) from t0 to t_end (``sim_dp5``).  Returns the
@@ -300,6 +318,13 @@ class Server:
         check(lib().srv_stats(self._h, a))
         keys = ("completed", "pending", "queued", "node_steps", "batches_formed", "bytes_in_use")
         return dict(zip(keys, list(a)))
+
+    def memory(self):
+        """Device bytes in use now, the peak since creation, and the number of
+        jobs whose admission waited for device memory (``srv_memory``)."""
+        a = (ctypes.c_int64 * 3)()
+        check(lib().srv_memory(self._h, a))
+        return dict(zip(("bytes_in_use", "peak_bytes_in_use", "jobs_waited_for_memory"), list(a)))
 
     def timings(self):
         """Worker time (s) by phase: admit, form (batches), step, retire, idle."""

@@ -47,3 +47,20 @@ def test_oracle_rate_and_config():
     assert cfg["workload"] == "FitzHugh-Nagumo ring, N=1000000, R=350000, RK4 dt=0.01"
     assert cfg["N"] == 10 ** 6 and cfg["parallelism"] == "single" and "flushed" in cfg["l2"]
     assert np.isfinite(bench.RING_FLOPS[1]) and bench.RING_BYTES[1] == 432
+
+
+def test_chunks_links_and_roofline():
+    import bench
+    assert bench.chunks_of(20, 5) == [5, 5, 5, 5] and bench.chunks_of(7, 5) == [5, 2] and bench.chunks_of(0, 5) == []
+    assert bench.links_of(0, 1000, 350) == 700
+    assert bench.links_of(1, 464, 92) == 185 ** 3 - 1
+    assert bench.links_of(2, 100, 2) == 32 and bench.links_of(2, 100, 6) == 924  # the paper's 33 and 925 with self
+    assert bench.CUBE_BYTES == 4 * (32 + 32) + 64 + 3 * 72
+    peaks = {"hbm_gbs": 6000.0, "fp64_gflops": 1000.0, "hbm_source": "x", "fp64_source": "y"}
+    kinds = {"stage_or_x": {"ms": 2.0, "launches": 4}, "cube_y": {"ms": 2.0, "launches": 4},
+             "node_pass": {"ms": 8.0, "launches": 4}}
+    r = bench.roofline_of(kinds, bench.CUBE_KIND_BYTES, bench.CUBE_KIND_FLOPS, 10 ** 8, peaks)
+    assert r["kernel"] == "node_pass" and abs(r["share_of_timed_region"] - 8 / 12) < 1e-12
+    gbs = bench.CUBE_PASS_BYTES[2] * 1e8 / 2e-3 / 1e9  # 2 ms per launch
+    assert r["bound"] == "hbm" and abs(r["achieved"] - gbs) < 1e-6 and abs(r["frac"] - gbs / 6000.0) < 1e-12
+    assert r["traffic"] is None

@@ -120,6 +120,32 @@ def test_hbm_budget_admission_and_one_at_a_time_baseline():
         assert np.array_equal(served[job.job_id][0], single[job.job_id][0])
 
 
+def test_admission_waits_for_memory_and_stays_within_budget():
+    """Six equal Kuramoto rings submitted together into a budget that holds two
+    of them: admission must make jobs wait for device memory, the peak of the
+    bytes in use must never exceed the budget, and every result must equal the
+    job run alone."""
+    from paper_2410_19075_gb300 import Server, workspace_bytes
+    from paper_2410_19075_gb300 import inputs as Ii
+    N, R, steps = 3000, 900, 400
+    one = workspace_bytes(0, 0, N, R)
+    budget = int(2.5 * one)
+    specs = [Ii.Job(k, 0.0, 0, 0, N, R, Ii.ks_params(alpha=1.3 + 0.02 * k), steps, 40 + k) for k in range(6)]
+    inits = [_init(j) for j in specs]
+    with Server(budget, max_slots=64, chunk_steps=50) as srv:
+        ids = [srv.submit(j.model, j.topo, j.N, j.R, j.params, y0, j.n_steps, 0.01) for j, y0 in zip(specs, inits)]
+        srv.wait_idle()
+        mem = srv.memory()
+        res = [srv.poll(i) for i in ids]
+    assert 0 < mem["peak_bytes_in_use"] <= budget
+    assert mem["peak_bytes_in_use"] >= one
+    assert mem["bytes_in_use"] == 0
+    assert mem["jobs_waited_for_memory"] >= 1
+    for job, y0, r in zip(specs, inits, res):
+        ya, _ = _alone(job, y0)
+        assert np.array_equal(r[0], ya)
+
+
 def test_submit_rejects_invalid_and_oversized_jobs():
     from paper_2410_19075_gb300 import Server
     from paper_2410_19075_gb300._lib import SimError

@@ -49,11 +49,13 @@ def test_max_over_ranks_with_gloo():
     assert res == {0: 2.0, 1: 2.0}
 
 
-def test_reference_arm_under_torchrun_prints_one_line_from_rank_zero():
+@pytest.mark.parametrize("workload", [["--topo", "0", "--model", "1", "--N", "3000"],
+                                      ["--N", "40"]])  # a FitzHugh-Nagumo ring; the default cube, small
+def test_reference_arm_under_torchrun_prints_one_line_from_rank_zero(workload):
     port = _free_port()
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node=2",
            "--master-addr=127.0.0.1", f"--master-port={port}", "bench.py", "--impl", "reference",
-           "--gpus", "2", "--steps", "2", "--warmup", "1", "--N", "3000"]
+           "--gpus", "2", "--steps", "2", "--warmup", "1", *workload]
     r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
