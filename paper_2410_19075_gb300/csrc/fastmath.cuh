@@ -7,24 +7,23 @@
 //
 // Methods (textbook; constants derived for this code from pi and ln 2 in
 // high-precision arithmetic):
-//   sin/cos  fixed_sincos, in 64-bit integer arithmetic only: additive range
-//            reduction by pi/512 (Cody & Waite 1980) done exactly, as
-//            t = |x| * 512/pi with 64 fractional bits from the 117-bit product of
-//            x's significand and 512/pi rounded to 64 bits (relative error
-//            2^-69.4); k = nearest integer to t, r = (t - k) pi/512 with
+//   sin/cos  fixed_sincos, in integer arithmetic only: additive range
+//            reduction by pi/512 (Cody & Waite 1980), t = |x| * 512/pi from one
+//            unsigned 64 x 64 high product of |x| 2^55 and 512/pi 2^56 (grid
+//            2^-47); k = nearest integer to t, r = (t - k) pi/512 with
 //            |r| <= pi/1024; Taylor polynomials sin r = r - r^3 (1/6 - r^2/120)
-//            and cos r - 1 = -r^2/2 + r^4/24 (first omitted terms below 2^-70
-//            and 2^-59); the angle-addition formula around the table point
-//            j pi/512, j = k mod 1024 (the "accurate table" approach of Tang and
-//            Gal): sin x = S_j + C_j sin r + S_j (cos r - 1) and
+//            and cos r - 1 = -r^2/2 + r^4/24 (first omitted terms below 2^-73
+//            and 2^-59), whose small terms take 32 x 32 products; the
+//            angle-addition formula around the table point j pi/512,
+//            j = k mod 1024 (the "accurate table" approach of Tang and Gal):
+//            sin x = S_j + C_j sin r + S_j (cos r - 1) and
 //            cos x = C_j - S_j sin r + C_j (cos r - 1), (S_j, C_j) rounded to
-//            2^-62.  Every product is a signed 64 x 64 -> high-64 multiply on
-//            scaled operands (each quantity's scale is in its name).  The result
-//            is sin and cos on the grid 2^-62, within about 2^-59 of the true
-//            values for |x| < 256 (a host model of the same integer steps was
-//            checked against long double sinl/cosl over 2 * 10^7 arguments:
-//            worst error 8.25 * 2^-62); that grid is what the exact window sums
-//            consume.  |x| >= 256, Inf and NaN use the library routine.
+//            2^-62.  The result is sin and cos on the grid 2^-62 within 2^-53.4
+//            of the true values for |x| < 256 (a host model of the same integer
+//            steps was checked against long double sinl/cosl over 2 * 10^7
+//            arguments and every reduction edge: worst error 7.7e-17, set by the
+//            grid 2^-47 of t); that grid is what the exact window sums consume.
+//            |x| >= 256, Inf and NaN use the library routine.
 //   exp      Tang (1989) table-driven method: x = (64 m + j) ln2/64 + r,
 //            exp(x) = 2^m 2^(j/64) exp(r), degree-5 Taylor polynomial for
 //            exp(r) - 1, |r| <= ~ln2/128.  8 FP64 instructions.
@@ -92,16 +91,31 @@ __device__ __forceinline__ int round_scaled(float xf, float scale)
     return __float_as_int(t) - 0x4B400000;
 }
 
-// Constants of fixed_sincos (derived from pi in 80-digit arithmetic).
+// Constants of fixed_sincos (derived from pi in 60-digit arithmetic).
 constexpr uint64_t kPio512Inv56 = 0xa2f9836e4e44152aull; // round(512/pi * 2^56)
-constexpr int64_t kPio512Q69 = 3622009729038561421ll;    // round(pi/512 * 2^69)
-constexpr int64_t kSixthQ65 = 6148914691236517205ll;     // round(2^65 / 6)
-constexpr int64_t kInv120Q55 = 300239975158033ll;        // round(2^55 / 120)
-constexpr int64_t kInv24Q55 = 1501199875790165ll;        // round(2^55 / 24)
+constexpr uint64_t kPio512Q71 = 0xc90fdaa22168c235ull;   // round(pi/512 * 2^71)
+constexpr uint32_t kSixthQ34 = 2863311531u;               // round(2^34 / 6)
+constexpr uint32_t kInv120Q32 = 35791394u;                // round(2^32 / 120)
+constexpr uint32_t kInv24Q36 = 2863311531u;               // round(2^36 / 24)
 
-// sin x and cos x rounded onto the grid 2^-62 (s62, c62 in [-2^62, 2^62]).
-// Integer instructions only on the fast path |x| < 256; beyond it, and for Inf
-// and NaN, the library routine (ok = false for a non-finite x).
+// floor(a b / 2^64) for signed a and unsigned b: the unsigned high product of
+// a's two's-complement bits, less b when a is negative.
+__device__ __forceinline__ int64_t mulhi_su(int64_t a, uint64_t b)
+{
+    return (int64_t)(__umul64hi((uint64_t)a, b) - (a < 0 ? b : 0ull));
+}
+
+// sin x and cos x on the grid 2^-62 (s62, c62 in [-2^62, 2^62]), absolute
+// error below 2^-53.4.  Integer instructions only on the fast path |x| < 256;
+// beyond it, and for Inf and NaN, the library routine (ok = false for a
+// non-finite x).  Every 64 x 64 product is unsigned (on GB300 the signed
+// high product costs about 1.7 unsigned ones):
+//   X = |x| 2^55 (truncated), t = X (512/pi) 2^-64 on the grid 2^-47,
+//   k = nearest integer to t, f = t - k in [-1/2, 1/2), r = f pi/512;
+//   sin|r| = |r| - |r|^3 (1/6 - r^2/120) and 1 - cos r = r^2/2 - r^4/24, the
+//   small terms from 32 x 32 products of the top words;
+//   the angle-addition formula around the table point j pi/512, j = k mod 1024:
+//   sin = S_j - S_j (1 - cos r) + C_j sin r, cos = C_j - C_j (1 - cos r) - S_j sin r.
 __device__ __forceinline__ void fixed_sincos(double x, const MathTables &T, int64_t &s62, int64_t &c62, bool &ok)
 {
     const uint64_t b = (uint64_t)__double_as_longlong(x);
@@ -113,36 +127,26 @@ __device__ __forceinline__ void fixed_sincos(double x, const MathTables &T, int6
         c62 = to_fixed(c, 62, 1, ok);
         return;
     }
-    int64_t k = 0, f = 0; // x * 512/pi = k + f 2^-64
-    if (e >= 1023 - 60) { // below that, x is 0 on this grid
-        const uint64_t m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-        const uint64_t lo = m * kPio512Inv56, hi = __umul64hi(m, kPio512Inv56);
-        const int sh = 1067 - e; // the product times 2^-sh has 64 fractional bits; sh in [37, 104]
-        uint64_t th, tl;
-        if (sh < 64) {
-            th = hi >> sh;
-            tl = (lo >> sh) | (hi << (64 - sh));
-        } else {
-            th = 0;
-            tl = hi >> (sh - 64);
-        }
-        if (b >> 63) { // negative x: negate the 128-bit value
-            tl = ~tl + 1ull;
-            th = ~th + (tl == 0ull ? 1ull : 0ull);
-        }
-        k = (int64_t)th + (int64_t)(tl >> 63); // round to the nearest integer
-        f = (int64_t)tl;                       // t - k in [-1/2, 1/2) times 2^64
-    }
-    const int64_t r69 = __mul64hi(f, kPio512Q69);               // r 2^69
-    const int64_t z74 = __mul64hi(r69, r69);                    // r^2 2^74
-    const int64_t u65 = kSixthQ65 - __mul64hi(z74, kInv120Q55); // (1/6 - r^2/120) 2^65
-    const int64_t v79 = __mul64hi(r69, z74);                    // r^3 2^79
-    const int64_t sr69 = r69 - (__mul64hi(v79, u65) >> 11);    // sin r 2^69
-    const int64_t zz84 = __mul64hi(z74, z74);                   // r^4 2^84
-    const int64_t cm75 = __mul64hi(zz84, kInv24Q55) - z74;      // (cos r - 1) 2^75
-    const longlong2 t = __ldg(T.sincos_q + (k & (kSinTab - 1)));
-    s62 = t.x + (__mul64hi(t.y, sr69) >> 5) + (__mul64hi(t.x, cm75) >> 11);
-    c62 = t.y - (__mul64hi(t.x, sr69) >> 5) + (__mul64hi(t.y, cm75) >> 11);
+    const uint64_t m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const uint64_t X = e >= 1020 ? m << (e - 1020) : m >> min(1020 - e, 63); // |x| 2^55 < 2^63
+    const uint64_t t = __umul64hi(X, kPio512Inv56);                          // |x| 512/pi 2^47
+    const uint64_t k = (t + (1ull << 46)) >> 47;
+    const int64_t f47 = (int64_t)(t - (k << 47)); // f 2^47, |f| <= 1/2
+    const bool rneg = f47 < 0;
+    const uint64_t R = __umul64hi((uint64_t)(rneg ? -f47 : f47) << 17, kPio512Q71); // |r| 2^71
+    const uint64_t z = __umul64hi(R, R);                                             // r^2 2^78
+    const uint32_t zh = (uint32_t)(z >> 32);                                         // r^2 2^46
+    const uint32_t v57 = (uint32_t)(((uint64_t)(uint32_t)(R >> 32) * zh) >> 28);    // |r|^3 2^57
+    const uint32_t u34 = kSixthQ34 - __umulhi((uint32_t)(z >> 44), kInv120Q32);     // (1/6 - r^2/120) 2^34
+    const uint64_t sr = (R >> 7) - (((uint64_t)v57 * u34) >> 27);                   // sin|r| 2^64
+    const uint32_t w = (uint32_t)(((uint64_t)zh * zh) >> 32);                       // r^4 2^60
+    const uint64_t cm = (z >> 15) - (((uint64_t)w * kInv24Q36) >> 32);              // (1 - cos r) 2^64
+    const longlong2 tq = __ldg(T.sincos_q + (k & (kSinTab - 1)));                   // (S_j, C_j) 2^62
+    const int64_t p1 = mulhi_su(tq.y, sr), p3 = mulhi_su(tq.x, sr);
+    const int64_t s = tq.x - mulhi_su(tq.x, cm) + (rneg ? -p1 : p1);
+    const int64_t c = tq.y - mulhi_su(tq.y, cm) - (rneg ? -p3 : p3);
+    s62 = (b >> 63) ? -s : s;
+    c62 = c;
 }
 
 // v 2^-62 rounded onto the coarser grid 2^-F (F <= 61), half up.

@@ -3,7 +3,9 @@
 //   ball  N1^3 nodes, the sphere dx^2 + dy^2 + dz^2 <= P^2 (3D networks);
 //   disk  N1^2 nodes, index j N1 + i, the circle dx^2 + dy^2 <= P^2 (2D networks).
 // f = (sin, cos) of the stage-input phase, rounded onto the grid 2^-F (F chosen
-// so that a full window sum fits in int64), so every window sum is exact.
+// so that a full window sum fits in int64) and rotated by -alpha in the x pass
+// (lattice_rotated_q), so every window sum is exact integer arithmetic and the
+// node's right-hand side needs one cross product with its own (sin, cos).
 //
 // Cube, per RK4 stage (the box is separable):
 //   x pass  SX(i,j,k)  = sum_{|dx|<=P} Q(f(i+dx,j,k))      (row prefix in shared memory)
@@ -41,7 +43,26 @@ static int row_warps(int64_t N1)
     return w < 1 ? 1 : (w > kRowWarpsMax ? kRowWarpsMax : w);
 }
 
-// x pass: one warp per row.  pre(p) = sum_{m<p} Q(f(m)) for p in [0, N1] is built
+// The coupled quantity a lattice's window sums add up: the node's (sin, cos) on
+// the grid 2^-62 rotated by -alpha,
+//   e^{-i alpha} (c + i s) = (c cos a + s sin a) + i (s cos a - c sin a),
+// four 64 x 64 high products with cos alpha and sin alpha on the grid 2^-62
+// (which land on the grid 2^-60, so their truncation leaves no bias that a
+// window of millions of terms could accumulate), then rounded to nearest onto
+// the grid 2^-F.  The right-hand side then needs only the node's own unrotated
+// (sin, cos) (lattice_coupling).
+__device__ __forceinline__ void lattice_rotated_q(const LatticePlan &p, int64_t s62, int64_t c62, int64_t &qs,
+                                                  int64_t &qc)
+{
+    const int64_t ca = p.mp.q[0], sa = p.mp.q[1];
+    const int64_t s60 = (int64_t)__mul64hi(s62, ca) - (int64_t)__mul64hi(c62, sa);
+    const int64_t c60 = (int64_t)__mul64hi(c62, ca) + (int64_t)__mul64hi(s62, sa);
+    const int sh = 60 - p.F;
+    qs = (s60 + (int64_t(1) << (sh - 1))) >> sh;
+    qc = (c60 + (int64_t(1) << (sh - 1))) >> sh;
+}
+
+// x pass: one warp per row.  pre(p) = sum_{m<p} Q'(f(m)) for p in [0, N1] is built
 // in shared memory (stride N1 + 1 per component).  With Pe(p) = pre(p mod N1) +
 // floor(p / N1) pre(N1) the periodic extension:
 //   MODE 0 (cube)        SX(i) = Pe(i+P+1) - Pe(i-P), sin and cos in two arrays;
@@ -71,10 +92,7 @@ __device__ __forceinline__ void lattice_x_row(const LatticePlan &p, int64_t row,
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             const int64_t m = mb + 32 * u;
-            if (m < N1) {
-                pre0[m + 1] = q62_to(vs[u], p.F);
-                pre1[m + 1] = q62_to(vc[u], p.F);
-            }
+            if (m < N1) lattice_rotated_q(p, vs[u], vc[u], pre0[m + 1], pre1[m + 1]);
         }
     }
     __syncwarp();
@@ -353,14 +371,11 @@ __device__ __forceinline__ void lattice_node(const LatticePlan &p, int64_t n, in
         for (int v = 0; v < D; ++v) xn[v] = p.y[v * nodes + n];
     } else {
         const int64_t f62[2] = {p.f[n], p.f[nodes + n]};
-        const double fo[2] = {fixed_to_double(f62[0], 62), fixed_to_double(f62[1], 62)};
-        const int64_t qo[2] = {q62_to(f62[0], p.F), q62_to(f62[1], p.F)};
-        const i128 W[2] = {(i128)W0, (i128)W1};
         double X[NX > 0 ? NX : 1];
 #pragma unroll
         for (int g = 0; g < NX; ++g) X[g] = STAGE == 1 ? p.y[(XOFF + g) * nodes + n] : p.xs[g * nodes + n];
         double k[D];
-        Model<M>::rhs(p.mp, p.F, fo, qo, W, X, 0.0, k, -1, 1.0, f62);
+        Model<M>::rhs_lattice(p.mp, p.F, f62, W0, W1, X, k);
 #pragma unroll
         for (int v = 0; v < D; ++v) {
             const double yv = p.y[v * nodes + n];
@@ -455,128 +470,122 @@ __global__ void __launch_bounds__(kColThreads) cube_z_kernel(LatticePlan p, cons
 // prefix along the window axis (wrapping int64 arithmetic, as the x pass), and
 // every window sum is Pe(a+P+1) - Pe(a-P) on its periodic extension.
 constexpr int kTileThreads = 256;
-constexpr int kTileSeg = 8; // segments of one column in the in-place scan
 
 // i-columns per tile: shared memory 2 (N1 + 1) BI 8 bytes stays below ~76 KB
 // (two or three CTAs per SM) and every row segment of a load is BI * 8 bytes.
-__host__ __device__ inline int cube_tile_bi(int64_t N1) { return N1 <= 297 ? 16 : N1 <= 594 ? 8 : 4; }
+__host__ __device__ inline int cube_tile_lg(int64_t N1) { return N1 <= 297 ? 4 : N1 <= 594 ? 3 : 2; }
+__host__ __device__ inline int cube_tile_bi(int64_t N1) { return 1 << cube_tile_lg(N1); }
 
 __host__ __device__ inline size_t cube_tile_smem(int64_t N1)
 {
     return (size_t)2 * (size_t)(N1 + 1) * (size_t)cube_tile_bi(N1) * sizeof(int64_t);
 }
 
-// Load src[c * nodes + base + a * stride + ii] for c < 2, a < N1, ii < BI into
-// tile[(c (N1 + 1) + a + 1) BI + ii] (0 past the cube's edge), and row 0 of both
-// components as 0; then every column (c, ii) becomes its inclusive prefix along a
-// (kTileSeg segments per column: segment sums, their exclusive scan, rewrite).
-// Called by every thread of the CTA; ends with a barrier.
+// Load src[c nodes + base + a stride + ii] for c < 2, a < N1, ii < BI = 2^lg (0
+// for ii >= bi, past the cube's edge) into tile[(c (N1 + 1) + a + 1) BI + ii],
+// zero row 0 of both components, then turn every column (c, ii) into its
+// inclusive prefix along a (wrapping uint64): kTileThreads / (2 BI) segments per
+// column, segment sums, their exclusive scan, rewrite.  Offsets inside the cube
+// are 32-bit (N1 <= 1024, so a * stride < 2^30).  Called by every thread of the
+// CTA; ends with a barrier.
 __device__ __forceinline__ void cube_tile_load_scan(const int64_t *__restrict__ src, int64_t nodes, int64_t base,
-                                                    int64_t stride, int64_t N1, int BI, int bi, int64_t *tile)
+                                                    unsigned stride, int N1, int lg, int bi, uint64_t *tile)
 {
-    const int tid = threadIdx.x;
-    const int lg = BI == 16 ? 4 : BI == 8 ? 3 : 2;
-    const int64_t per_c = N1 * BI;
-    for (int64_t e = tid; e < 2 * per_c; e += kTileThreads) {
-        const int c = e >= per_c ? 1 : 0;
-        const int64_t r = e - c * per_c;
-        const int64_t a = r >> lg;
-        const int ii = (int)(r & (BI - 1));
-        tile[(c * (N1 + 1) + a + 1) * BI + ii] = ii < bi ? __ldg(src + c * nodes + base + a * stride + ii) : 0;
+    const int tid = threadIdx.x, BI = 1 << lg, rstep = kTileThreads >> lg;
+    const int ii = tid & (BI - 1), r0 = tid >> lg;
+    const bool live = ii < bi;
+    const unsigned cstride = (unsigned)(N1 + 1) << lg; // tile words per component
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const uint64_t *__restrict__ s = reinterpret_cast<const uint64_t *>(src) + c * nodes + base + ii;
+        uint64_t *t = tile + c * cstride + BI + ii;
+#pragma unroll 4
+        for (int a = r0; a < N1; a += rstep) t[(unsigned)a << lg] = live ? __ldg(s + (unsigned)a * stride) : 0ull;
     }
-    if (tid < 2 * BI) tile[(tid / BI) * (N1 + 1) * BI + (tid & (BI - 1))] = 0;
+    if (tid < 2 * BI) tile[(tid >> lg) * cstride + (tid & (BI - 1))] = 0ull;
     __syncthreads();
-    // in-place inclusive prefix: thread (column col, segment sg) for col < 2 BI
-    __shared__ uint64_t s_seg[2 * 16 * kTileSeg];
-    const int ncol = 2 * BI;
-    const int64_t seg = (N1 + kTileSeg - 1) / kTileSeg;
-    const int col = tid % ncol, sg = tid / ncol;
-    const bool act = tid < ncol * kTileSeg;
-    const int c = col / BI, ii = col % BI;
-    uint64_t *colp = reinterpret_cast<uint64_t *>(tile) + (int64_t)c * (N1 + 1) * BI + ii;
-    const int64_t a0 = 1 + sg * seg, a1 = min(N1 + 1, a0 + seg);
-    if (act) {
-        uint64_t t = 0;
-        for (int64_t a = a0; a < a1; ++a) t += colp[a * BI];
-        s_seg[col * kTileSeg + sg] = t;
-    }
+    __shared__ uint64_t s_seg[kTileThreads];
+    const int ncol = 2 * BI, nseg = kTileThreads / ncol;
+    const int col = tid & (ncol - 1), sg = tid >> (lg + 1);
+    uint64_t *colp = tile + (col >> lg) * cstride + (col & (BI - 1));
+    const int seg = (N1 + nseg - 1) / nseg;
+    const int a0 = 1 + sg * seg, a1 = min(N1 + 1, a0 + seg);
+    uint64_t t = 0;
+    for (int a = a0; a < a1; ++a) t += colp[(unsigned)a << lg];
+    s_seg[sg * ncol + col] = t;
     __syncthreads();
-    if (act) {
-        uint64_t run = 0;
-        for (int q = 0; q < sg; ++q) run += s_seg[col * kTileSeg + q];
-        for (int64_t a = a0; a < a1; ++a) {
-            run += colp[a * BI];
-            colp[a * BI] = run;
-        }
+    uint64_t run = 0;
+    for (int q = 0; q < sg; ++q) run += s_seg[q * ncol + col];
+    for (int a = a0; a < a1; ++a) {
+        run += colp[(unsigned)a << lg];
+        colp[(unsigned)a << lg] = run;
     }
     __syncthreads();
 }
 
-// Window sum of column (c, ii) of a scanned tile at position a (0 <= a < N1):
-// Pe(a + P + 1) - Pe(a - P) with Pe(x) = pre(x mod N1) + floor(x / N1) pre(N1).
-__device__ __forceinline__ int64_t cube_tile_window(const int64_t *tile, int64_t N1, int64_t P, int BI, int c, int ii,
-                                                    int64_t a)
+// Window sum at a (0 <= a < N1) of a scanned column colp (its words BI = 2^lg
+// apart, total = colp[N1 BI]): Pe(a + P + 1) - Pe(a - P) on the periodic
+// extension Pe(x) = pre(x mod N1) + floor(x / N1) total.  As 2P + 1 <= N1, at
+// most one end wraps, and either wrap adds the total once.
+__device__ __forceinline__ int64_t cube_tile_window(const uint64_t *colp, int N1, int P, int lg, int a, uint64_t total)
 {
-    const uint64_t *colp = reinterpret_cast<const uint64_t *>(tile) + (int64_t)c * (N1 + 1) * BI + ii;
-    int64_t b = a + P + 1, lo = a - P;
-    uint64_t w = 0;
-    if (b > N1) {
-        b -= N1;
-        w += colp[N1 * BI];
-    }
-    if (lo < 0) {
-        lo += N1;
-        w += colp[N1 * BI];
-    }
-    return (int64_t)(w + colp[b * BI] - colp[lo * BI]);
+    int b = a + P + 1, lo = a - P;
+    const bool wb = b > N1, wl = lo < 0;
+    b -= wb ? N1 : 0;
+    lo += wl ? N1 : 0;
+    return (int64_t)(colp[(unsigned)b << lg] - colp[(unsigned)lo << lg] + ((wb || wl) ? total : 0ull));
 }
 
 // Tiled cube y pass: CTA (ib, k).
 __global__ void __launch_bounds__(kTileThreads) cube_y_tile_kernel(LatticePlan p)
 {
     if (p.skip && *(const volatile int *)p.skip) return;
-    extern __shared__ int64_t tile[];
-    const int64_t N1 = p.N1, P = p.P, nodes = p.nodes;
-    const int BI = cube_tile_bi(N1);
-    const int64_t i0 = (int64_t)blockIdx.x * BI, k = blockIdx.y;
-    const int bi = (int)min((int64_t)BI, N1 - i0);
-    const int64_t base = k * N1 * N1 + i0;
-    cube_tile_load_scan(p.sx, nodes, base, N1, N1, BI, bi, tile);
-    const int lg = BI == 16 ? 4 : BI == 8 ? 3 : 2;
-    const int64_t per_c = N1 * BI;
-    for (int64_t e = threadIdx.x; e < 2 * per_c; e += kTileThreads) {
-        const int c = e >= per_c ? 1 : 0;
-        const int64_t r = e - c * per_c;
-        const int64_t j = r >> lg;
-        const int ii = (int)(r & (BI - 1));
-        if (ii < bi) p.sxy[c * nodes + base + j * N1 + ii] = cube_tile_window(tile, N1, P, BI, c, ii, j);
+    extern __shared__ int64_t tile_mem[];
+    uint64_t *tile = reinterpret_cast<uint64_t *>(tile_mem);
+    const int N1 = (int)p.N1, P = (int)p.P, lg = cube_tile_lg(N1), BI = 1 << lg;
+    const int i0 = (int)blockIdx.x << lg, k = blockIdx.y;
+    const int bi = min(BI, N1 - i0);
+    const int64_t base = (int64_t)k * N1 * N1 + i0;
+    cube_tile_load_scan(p.sx, p.nodes, base, (unsigned)N1, N1, lg, bi, tile);
+    const int ii = threadIdx.x & (BI - 1), r0 = threadIdx.x >> lg, rstep = kTileThreads >> lg;
+    if (ii >= bi) return; // past every barrier
+    const unsigned cstride = (unsigned)(N1 + 1) << lg;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const uint64_t *colp = tile + c * cstride + ii;
+        const uint64_t total = colp[(unsigned)N1 << lg];
+        int64_t *__restrict__ d = p.sxy + c * p.nodes + base + ii;
+#pragma unroll 4
+        for (int a = r0; a < N1; a += rstep) d[(unsigned)a * (unsigned)N1] = cube_tile_window(colp, N1, P, lg, a, total);
     }
 }
 
 // Tiled cube z pass (stages 1-4): CTA (ib, j) scans the xy-window sums of its
-// columns along k, then runs the node update of each of its nodes (one per
-// thread in turn, consecutive i fastest).
+// columns along k, then runs the node update of each of its nodes (thread
+// (ii, r0) takes the planes k = r0, r0 + 256 / BI, ...).
 template <int M, int STAGE>
 __global__ void __launch_bounds__(kTileThreads) cube_z_tile_kernel(LatticePlan p, const StepSize h)
 {
     if (STAGE == 1 && p.skip && *(const volatile int *)p.skip) return; // stage 1 records nothing
-    extern __shared__ int64_t tile[];
-    const int64_t N1 = p.N1, P = p.P, nodes = p.nodes, plane = N1 * N1;
-    const int BI = cube_tile_bi(N1);
-    const int64_t i0 = (int64_t)blockIdx.x * BI, j = blockIdx.y;
-    const int bi = (int)min((int64_t)BI, N1 - i0);
-    const int64_t base = j * N1 + i0;
-    cube_tile_load_scan(p.sxy, nodes, base, plane, N1, BI, bi, tile);
-    const int lg = BI == 16 ? 4 : BI == 8 ? 3 : 2;
+    extern __shared__ int64_t tile_mem[];
+    uint64_t *tile = reinterpret_cast<uint64_t *>(tile_mem);
+    const int N1 = (int)p.N1, P = (int)p.P, lg = cube_tile_lg(N1), BI = 1 << lg;
+    const int i0 = (int)blockIdx.x << lg, j = blockIdx.y;
+    const int bi = min(BI, N1 - i0);
+    const unsigned plane = (unsigned)N1 * (unsigned)N1;
+    const int64_t base = (int64_t)j * N1 + i0;
+    cube_tile_load_scan(p.sxy, p.nodes, base, plane, N1, lg, bi, tile);
+    const int ii = threadIdx.x & (BI - 1), r0 = threadIdx.x >> lg, rstep = kTileThreads >> lg;
     i128 ps = 0, pc = 0;
     bool ok = true;
-    for (int64_t r = threadIdx.x; r < N1 * BI; r += kTileThreads) {
-        const int64_t k = r >> lg;
-        const int ii = (int)(r & (BI - 1));
-        if (ii >= bi) continue;
-        const int64_t W0 = cube_tile_window(tile, N1, P, BI, 0, ii, k);
-        const int64_t W1 = cube_tile_window(tile, N1, P, BI, 1, ii, k);
-        lattice_node<M, STAGE>(p, base + k * plane + ii, W0, W1, h, ok, ps, pc);
+    if (ii < bi) {
+        const unsigned cstride = (unsigned)(N1 + 1) << lg;
+        const uint64_t *col0 = tile + ii, *col1 = tile + cstride + ii;
+        const uint64_t t0 = col0[(unsigned)N1 << lg], t1 = col1[(unsigned)N1 << lg];
+        for (int a = r0; a < N1; a += rstep)
+            lattice_node<M, STAGE>(p, base + (int64_t)((unsigned)a * plane) + ii,
+                                   cube_tile_window(col0, N1, P, lg, a, t0), cube_tile_window(col1, N1, P, lg, a, t1),
+                                   h, ok, ps, pc);
     }
     if (!ok) raise_error(p.err, ERR_RANGE);
     if (STAGE == 4)

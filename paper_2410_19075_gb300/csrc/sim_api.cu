@@ -382,6 +382,10 @@ void simk::model_constants(int model, const double *params, double K, ModelParam
         mp.c[3] = std::cos(alpha);
         mp.q[0] = (int64_t)std::llround(std::ldexp(mp.c[3], 62)); // exact: |cos| <= 1, 53-bit significand
         mp.q[1] = (int64_t)std::llround(std::ldexp(mp.c[2], 62));
+        // lattices: the constant of the right-hand side with the node's own term
+        // (-sin alpha in the rotated window sum) taken out
+        if (model == SIM_KS) mp.c[4] = mp.include_self ? mp.c[0] : mp.c[0] + mp.c[1] * mp.c[2];
+        else mp.c[4] = mp.include_self ? 0.0 : mp.c[0] * mp.c[2];
     } else if (model == SIM_FHN) {
         const double ph = params[3], inv_eps = 1.0 / params[0], sK = params[2] / K;
         mp.c[0] = inv_eps;
