@@ -105,6 +105,15 @@ __device__ __forceinline__ int64_t mulhi_su(int64_t a, uint64_t b)
     return (int64_t)(__umul64hi((uint64_t)a, b) - (a < 0 ? b : 0ull));
 }
 
+// floor(a b / 2^64) for signed a and b, from the unsigned high product.
+__device__ __forceinline__ int64_t mulhi_ss(int64_t a, int64_t b)
+{
+    uint64_t h = __umul64hi((uint64_t)a, (uint64_t)b);
+    h -= a < 0 ? (uint64_t)b : 0ull;
+    h -= b < 0 ? (uint64_t)a : 0ull;
+    return (int64_t)h;
+}
+
 // sin x and cos x on the grid 2^-62 (s62, c62 in [-2^62, 2^62]), absolute
 // error below 2^-53.4.  Integer instructions only on the fast path |x| < 256;
 // beyond it, and for Inf and NaN, the library routine (ok = false for a

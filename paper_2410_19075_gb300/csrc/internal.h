@@ -163,6 +163,11 @@ struct LatticePlan {
     int model, topo, dims;
     int64_t N1, P, nodes;
     int F;            // fixed-point grid of the window sums
+    // cube: the y pass rotates its window sums by -alpha = -(rot_q pi/2 + alpha0),
+    // alpha0 in [0, pi/2): rot_c, rot_s = cos alpha0, sin alpha0 on the grid 2^-63,
+    // the sums shifted up by rot_g bits before the products (cube_rotate)
+    uint64_t rot_c, rot_s;
+    int rot_q, rot_g;
     ModelParams mp;
     double *y, *acc;  // D * nodes
     int64_t *f;       // 2 * nodes: sin, cos of the current stage-input phase on the grid 2^-62
@@ -246,6 +251,7 @@ struct CubeBatchGroup {
 };
 cudaError_t cube_batch_step(const CubeBatchGroup &g, double dt, cudaStream_t s); // one RK4 step of every member
 int lattice_row_warps(int64_t N1); // warps per CTA of the x pass for edge N1
+void lattice_rotation(LatticePlan &p, double alpha); // rot_* and mp.c[5] of a lattice (sim_api.cu)
 
 // Per-kernel timing of sim_step_timed: while set on the launching host thread,
 // every stage-kernel launch of ring_step, graph_step, lattice_step and

@@ -43,8 +43,8 @@ static int row_warps(int64_t N1)
     return w < 1 ? 1 : (w > kRowWarpsMax ? kRowWarpsMax : w);
 }
 
-// The coupled quantity a lattice's window sums add up: the node's (sin, cos) on
-// the grid 2^-62 rotated by -alpha,
+// The coupled quantity a ball's or disk's window sums add up: the node's (sin,
+// cos) on the grid 2^-62 rotated by -alpha,
 //   e^{-i alpha} (c + i s) = (c cos a + s sin a) + i (s cos a - c sin a),
 // four 64 x 64 high products with cos alpha and sin alpha on the grid 2^-62
 // (which land on the grid 2^-60, so their truncation leaves no bias that a
@@ -92,7 +92,14 @@ __device__ __forceinline__ void lattice_x_row(const LatticePlan &p, int64_t row,
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             const int64_t m = mb + 32 * u;
-            if (m < N1) lattice_rotated_q(p, vs[u], vc[u], pre0[m + 1], pre1[m + 1]);
+            if (m < N1) {
+                if (MODE == 0) { // cube: the y pass rotates the window sums
+                    pre0[m + 1] = q62_to(vs[u], p.F);
+                    pre1[m + 1] = q62_to(vc[u], p.F);
+                } else {
+                    lattice_rotated_q(p, vs[u], vc[u], pre0[m + 1], pre1[m + 1]);
+                }
+            }
         }
     }
     __syncwarp();
@@ -202,6 +209,28 @@ __global__ void __launch_bounds__(32 * kRowWarpsMax)
     if (!ok) raise_error(p.err, ERR_RANGE);
 }
 
+// A cube's y-window sums (sin component ws, cos component wc, on the grid 2^-F)
+// rotated by -alpha = -(rot_q pi/2 + alpha0): the sums shifted up by rot_g bits,
+// four high products with cos alpha0 and sin alpha0 (non-negative, on the grid
+// 2^-63; the products land on the grid 2^-(F + rot_g - 1), fine enough that
+// their truncation leaves no bias a z window could accumulate), rounded to
+// nearest back onto the grid 2^-F, then rot_q quarter turns.  The z window sums
+// of the results are W' of lattice_coupling.
+__device__ __forceinline__ void cube_rotate(const LatticePlan &p, int64_t ws, int64_t wc, int64_t &rs, int64_t &rc)
+{
+    const int g = p.rot_g, sh = g - 1;
+    const int64_t s = (int64_t)((uint64_t)ws << g), c = (int64_t)((uint64_t)wc << g);
+    const int64_t h = int64_t(1) << (sh - 1);
+    const int64_t c1 = (mulhi_su(c, p.rot_c) + mulhi_su(s, p.rot_s) + h) >> sh;
+    const int64_t s1 = (mulhi_su(s, p.rot_c) - mulhi_su(c, p.rot_s) + h) >> sh;
+    switch (p.rot_q) { // e^{-i q pi/2}: 1, -i, -1, i
+    case 0: rc = c1; rs = s1; break;
+    case 1: rc = s1; rs = -c1; break;
+    case 2: rc = -c1; rs = -s1; break;
+    default: rc = -s1; rs = c1; break;
+    }
+}
+
 // Columns of the y and z passes are split into gridDim.z segments of
 // col_seg_len() nodes (small cubes would otherwise run a few thousand threads,
 // each walking its column serially); every segment starts its own sliding
@@ -221,7 +250,8 @@ __host__ __device__ inline int64_t col_seg_len(int64_t N1)
 }
 
 // cube y pass: one thread per segment of an (i, k) column, sliding window along
-// j (exact int64), 8 rows of window loads issued together.
+// j (exact int64), 8 rows of window loads issued together; writes the window
+// sums rotated by -alpha (cube_rotate).
 __device__ __forceinline__ void cube_y_col(const LatticePlan &p, int64_t i, int64_t k, int64_t seg)
 {
     constexpr int U = 8;
@@ -260,8 +290,10 @@ __device__ __forceinline__ void cube_y_col(const LatticePlan &p, int64_t i, int6
         for (int u = 0; u < U; ++u) {
             const int64_t j = j0 + u;
             if (j < je) {
-                o0[j * N1] = s0;
-                o1[j * N1] = s1;
+                int64_t r0, r1;
+                cube_rotate(p, s0, s1, r0, r1);
+                o0[j * N1] = r0;
+                o1[j * N1] = r1;
             }
             s0 += in0[u] - out0[u];
             s1 += in1[u] - out1[u];
@@ -358,38 +390,61 @@ __device__ void lattice_record_order(const LatticePlan &p, i128 ps, i128 pc, uns
 
 // One node's RK4 stage: right-hand side from the window sums (W0, W1) and its own
 // stage input, the RK4 update, the next stage input's local variables and (sin,
-// cos).  STAGE 0 (prologue) only computes (sin, cos) of y.
+// cos).  STAGE 0 (prologue) only computes (sin, cos) of y.  In two parts, so
+// that a thread can issue the loads of its next node before it computes this
+// one: lattice_node_load reads what the node needs, lattice_node_finish
+// computes and writes; lattice_node is the two in a row.
+template <int M> struct LatNodeIn {
+    int64_t f62[2];                                // (sin, cos) of the stage input, grid 2^-62
+    double y[Model<M>::D], acc[Model<M>::D];
+    double X[Model<M>::NX > 0 ? Model<M>::NX : 1]; // local stage-input variables
+};
+
 template <int M, int STAGE>
-__device__ __forceinline__ void lattice_node(const LatticePlan &p, int64_t n, int64_t W0, int64_t W1, const StepSize &h,
-                                             bool &ok, i128 &ps, i128 &pc)
+__device__ __forceinline__ void lattice_node_load(const LatticePlan &p, int64_t n, LatNodeIn<M> &in)
+{
+    constexpr int D = Model<M>::D, NX = Model<M>::NX, XOFF = D - NX;
+    const int64_t nodes = p.nodes;
+#pragma unroll
+    for (int v = 0; v < D; ++v) {
+        in.y[v] = p.y[v * nodes + n];
+        in.acc[v] = STAGE >= 2 ? p.acc[v * nodes + n] : 0.0;
+    }
+    if (STAGE > 0) {
+        in.f62[0] = p.f[n];
+        in.f62[1] = p.f[nodes + n];
+#pragma unroll
+        for (int g = 0; g < NX; ++g) in.X[g] = STAGE == 1 ? in.y[XOFF + g] : p.xs[g * nodes + n];
+    }
+}
+
+template <int M, int STAGE>
+__device__ __forceinline__ void lattice_node_finish(const LatticePlan &p, int64_t n, int64_t W0, int64_t W1,
+                                                    const LatNodeIn<M> &in, const StepSize &h, bool &ok, i128 &ps,
+                                                    i128 &pc)
 {
     constexpr int D = Model<M>::D, NX = Model<M>::NX, XOFF = D - NX;
     const int64_t nodes = p.nodes;
     double xn[D];
     if (STAGE == 0) {
 #pragma unroll
-        for (int v = 0; v < D; ++v) xn[v] = p.y[v * nodes + n];
+        for (int v = 0; v < D; ++v) xn[v] = in.y[v];
     } else {
-        const int64_t f62[2] = {p.f[n], p.f[nodes + n]};
-        double X[NX > 0 ? NX : 1];
-#pragma unroll
-        for (int g = 0; g < NX; ++g) X[g] = STAGE == 1 ? p.y[(XOFF + g) * nodes + n] : p.xs[g * nodes + n];
         double k[D];
-        Model<M>::rhs_lattice(p.mp, p.F, f62, W0, W1, X, k);
+        Model<M>::rhs_lattice(p.mp, in.f62, W0, W1, in.X, k);
 #pragma unroll
         for (int v = 0; v < D; ++v) {
-            const double yv = p.y[v * nodes + n];
             if (STAGE == 1) {
                 p.acc[v * nodes + n] = k[v];
-                xn[v] = yv + h.half * k[v];
+                xn[v] = in.y[v] + h.half * k[v];
             } else if (STAGE == 2) {
-                p.acc[v * nodes + n] = p.acc[v * nodes + n] + 2.0 * k[v];
-                xn[v] = yv + h.half * k[v];
+                p.acc[v * nodes + n] = in.acc[v] + 2.0 * k[v];
+                xn[v] = in.y[v] + h.half * k[v];
             } else if (STAGE == 3) {
-                p.acc[v * nodes + n] = p.acc[v * nodes + n] + 2.0 * k[v];
-                xn[v] = yv + h.dt * k[v];
+                p.acc[v * nodes + n] = in.acc[v] + 2.0 * k[v];
+                xn[v] = in.y[v] + h.dt * k[v];
             } else {
-                xn[v] = yv + h.sixth * (p.acc[v * nodes + n] + k[v]);
+                xn[v] = in.y[v] + h.sixth * (in.acc[v] + k[v]);
                 p.y[v * nodes + n] = xn[v];
             }
         }
@@ -406,6 +461,15 @@ __device__ __forceinline__ void lattice_node(const LatticePlan &p, int64_t n, in
         ps += q62_to(s62, p.F);
         pc += q62_to(c62, p.F);
     }
+}
+
+template <int M, int STAGE>
+__device__ __forceinline__ void lattice_node(const LatticePlan &p, int64_t n, int64_t W0, int64_t W1, const StepSize &h,
+                                             bool &ok, i128 &ps, i128 &pc)
+{
+    LatNodeIn<M> in;
+    lattice_node_load<M, STAGE>(p, n, in);
+    lattice_node_finish<M, STAGE>(p, n, W0, W1, in, h, ok, ps, pc);
 }
 
 // cube z pass: one thread per segment of an (i, j) column, sliding window along
@@ -471,6 +535,17 @@ __global__ void __launch_bounds__(kColThreads) cube_z_kernel(LatticePlan p, cons
 // every window sum is Pe(a+P+1) - Pe(a-P) on its periodic extension.
 constexpr int kTileThreads = 256;
 
+// Asynchronous 8-byte copy global -> shared (zero fill when !live); the copies
+// of a thread complete at cp_async_wait_all.
+__device__ __forceinline__ void cp_async8(uint64_t *dst, const uint64_t *src, bool live)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(live ? 8 : 0)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // i-columns per tile: shared memory 2 (N1 + 1) BI 8 bytes stays below ~76 KB
 // (two or three CTAs per SM) and every row segment of a load is BI * 8 bytes.
 __host__ __device__ inline int cube_tile_lg(int64_t N1) { return N1 <= 297 ? 4 : N1 <= 594 ? 3 : 2; }
@@ -482,30 +557,34 @@ __host__ __device__ inline size_t cube_tile_smem(int64_t N1)
 }
 
 // Load src[c nodes + base + a stride + ii] for c < 2, a < N1, ii < BI = 2^lg (0
-// for ii >= bi, past the cube's edge) into tile[(c (N1 + 1) + a + 1) BI + ii],
+// for ii >= bi, past the cube's edge) into tile[(c (N1 + 1) + a + 1) BI + ii]
+// (asynchronous 8-byte copies, so that the whole tile is in flight at once),
 // zero row 0 of both components, then turn every column (c, ii) into its
 // inclusive prefix along a (wrapping uint64): kTileThreads / (2 BI) segments per
-// column, segment sums, their exclusive scan, rewrite.  Offsets inside the cube
+// column, segment sums, their exclusive scan, rewrite (NT threads; NT / (2 BI)
+// segments per column).  Offsets inside the cube
 // are 32-bit (N1 <= 1024, so a * stride < 2^30).  Called by every thread of the
 // CTA; ends with a barrier.
+template <int NT>
 __device__ __forceinline__ void cube_tile_load_scan(const int64_t *__restrict__ src, int64_t nodes, int64_t base,
                                                     unsigned stride, int N1, int lg, int bi, uint64_t *tile)
 {
-    const int tid = threadIdx.x, BI = 1 << lg, rstep = kTileThreads >> lg;
+    const int tid = threadIdx.x, BI = 1 << lg, rstep = NT >> lg;
     const int ii = tid & (BI - 1), r0 = tid >> lg;
     const bool live = ii < bi;
     const unsigned cstride = (unsigned)(N1 + 1) << lg; // tile words per component
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
-        const uint64_t *__restrict__ s = reinterpret_cast<const uint64_t *>(src) + c * nodes + base + ii;
+        // past the cube's edge: a zero fill from an in-bounds address
+        const uint64_t *__restrict__ s = reinterpret_cast<const uint64_t *>(src) + c * nodes + base + (live ? ii : 0);
         uint64_t *t = tile + c * cstride + BI + ii;
-#pragma unroll 4
-        for (int a = r0; a < N1; a += rstep) t[(unsigned)a << lg] = live ? __ldg(s + (unsigned)a * stride) : 0ull;
+        for (int a = r0; a < N1; a += rstep) cp_async8(t + ((unsigned)a << lg), s + (unsigned)a * stride, live);
     }
     if (tid < 2 * BI) tile[(tid >> lg) * cstride + (tid & (BI - 1))] = 0ull;
+    cp_async_wait_all();
     __syncthreads();
-    __shared__ uint64_t s_seg[kTileThreads];
-    const int ncol = 2 * BI, nseg = kTileThreads / ncol;
+    __shared__ uint64_t s_seg[NT];
+    const int ncol = 2 * BI, nseg = NT / ncol;
     const int col = tid & (ncol - 1), sg = tid >> (lg + 1);
     uint64_t *colp = tile + (col >> lg) * cstride + (col & (BI - 1));
     const int seg = (N1 + nseg - 1) / nseg;
@@ -536,7 +615,7 @@ __device__ __forceinline__ int64_t cube_tile_window(const uint64_t *colp, int N1
     return (int64_t)(colp[(unsigned)b << lg] - colp[(unsigned)lo << lg] + ((wb || wl) ? total : 0ull));
 }
 
-// Tiled cube y pass: CTA (ib, k).
+// Tiled cube y pass: CTA (ib, k); writes the window sums rotated by -alpha.
 __global__ void __launch_bounds__(kTileThreads) cube_y_tile_kernel(LatticePlan p)
 {
     if (p.skip && *(const volatile int *)p.skip) return;
@@ -546,25 +625,32 @@ __global__ void __launch_bounds__(kTileThreads) cube_y_tile_kernel(LatticePlan p
     const int i0 = (int)blockIdx.x << lg, k = blockIdx.y;
     const int bi = min(BI, N1 - i0);
     const int64_t base = (int64_t)k * N1 * N1 + i0;
-    cube_tile_load_scan(p.sx, p.nodes, base, (unsigned)N1, N1, lg, bi, tile);
+    cube_tile_load_scan<kTileThreads>(p.sx, p.nodes, base, (unsigned)N1, N1, lg, bi, tile);
     const int ii = threadIdx.x & (BI - 1), r0 = threadIdx.x >> lg, rstep = kTileThreads >> lg;
     if (ii >= bi) return; // past every barrier
     const unsigned cstride = (unsigned)(N1 + 1) << lg;
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-        const uint64_t *colp = tile + c * cstride + ii;
-        const uint64_t total = colp[(unsigned)N1 << lg];
-        int64_t *__restrict__ d = p.sxy + c * p.nodes + base + ii;
-#pragma unroll 4
-        for (int a = r0; a < N1; a += rstep) d[(unsigned)a * (unsigned)N1] = cube_tile_window(colp, N1, P, lg, a, total);
+    const uint64_t *col0 = tile + ii, *col1 = tile + cstride + ii;
+    const uint64_t t0 = col0[(unsigned)N1 << lg], t1 = col1[(unsigned)N1 << lg];
+    int64_t *__restrict__ d0 = p.sxy + base + ii;
+    int64_t *__restrict__ d1 = d0 + p.nodes;
+#pragma unroll 2
+    for (int a = r0; a < N1; a += rstep) {
+        int64_t r0s, r1c;
+        cube_rotate(p, cube_tile_window(col0, N1, P, lg, a, t0), cube_tile_window(col1, N1, P, lg, a, t1), r0s, r1c);
+        d0[(unsigned)a * (unsigned)N1] = r0s;
+        d1[(unsigned)a * (unsigned)N1] = r1c;
     }
 }
 
 // Tiled cube z pass (stages 1-4): CTA (ib, j) scans the xy-window sums of its
 // columns along k, then runs the node update of each of its nodes (thread
-// (ii, r0) takes the planes k = r0, r0 + 256 / BI, ...).
+// (ii, r0) takes the planes k = r0, r0 + kZThreads / BI, ...), the loads of the
+// next two nodes in flight while one computes.  384 threads: three CTAs per SM
+// at the tile sizes of N1 <= 594 (up to 60 KB of shared memory each).
+constexpr int kZThreads = 384;
+
 template <int M, int STAGE>
-__global__ void __launch_bounds__(kTileThreads) cube_z_tile_kernel(LatticePlan p, const StepSize h)
+__global__ void __launch_bounds__(kZThreads, 3) cube_z_tile_kernel(LatticePlan p, const StepSize h)
 {
     if (STAGE == 1 && p.skip && *(const volatile int *)p.skip) return; // stage 1 records nothing
     extern __shared__ int64_t tile_mem[];
@@ -574,18 +660,28 @@ __global__ void __launch_bounds__(kTileThreads) cube_z_tile_kernel(LatticePlan p
     const int bi = min(BI, N1 - i0);
     const unsigned plane = (unsigned)N1 * (unsigned)N1;
     const int64_t base = (int64_t)j * N1 + i0;
-    cube_tile_load_scan(p.sxy, p.nodes, base, plane, N1, lg, bi, tile);
-    const int ii = threadIdx.x & (BI - 1), r0 = threadIdx.x >> lg, rstep = kTileThreads >> lg;
+    cube_tile_load_scan<kZThreads>(p.sxy, p.nodes, base, plane, N1, lg, bi, tile);
+    const int ii = threadIdx.x & (BI - 1), r0 = threadIdx.x >> lg, rstep = kZThreads >> lg;
     i128 ps = 0, pc = 0;
     bool ok = true;
-    if (ii < bi) {
+    if (ii < bi && r0 < N1) {
         const unsigned cstride = (unsigned)(N1 + 1) << lg;
         const uint64_t *col0 = tile + ii, *col1 = tile + cstride + ii;
         const uint64_t t0 = col0[(unsigned)N1 << lg], t1 = col1[(unsigned)N1 << lg];
-        for (int a = r0; a < N1; a += rstep)
-            lattice_node<M, STAGE>(p, base + (int64_t)((unsigned)a * plane) + ii,
-                                   cube_tile_window(col0, N1, P, lg, a, t0), cube_tile_window(col1, N1, P, lg, a, t1),
-                                   h, ok, ps, pc);
+        const int64_t nb = base + ii;
+        LatNodeIn<M> b0, b1;
+        lattice_node_load<M, STAGE>(p, nb + (int64_t)((unsigned)r0 * plane), b0);
+        if (r0 + rstep < N1) lattice_node_load<M, STAGE>(p, nb + (int64_t)((unsigned)(r0 + rstep) * plane), b1);
+        for (int a = r0; a < N1; a += rstep) {
+            const int a2 = a + 2 * rstep;
+            LatNodeIn<M> b2;
+            if (a2 < N1) lattice_node_load<M, STAGE>(p, nb + (int64_t)((unsigned)a2 * plane), b2);
+            lattice_node_finish<M, STAGE>(p, nb + (int64_t)((unsigned)a * plane),
+                                          cube_tile_window(col0, N1, P, lg, a, t0),
+                                          cube_tile_window(col1, N1, P, lg, a, t1), b0, h, ok, ps, pc);
+            b0 = b1;
+            b1 = b2;
+        }
     }
     if (!ok) raise_error(p.err, ERR_RANGE);
     if (STAGE == 4)
@@ -771,7 +867,7 @@ template <int M, int STAGE>
 static cudaError_t launch_node_pass(const LatticePlan &p, double dt, cudaStream_t s)
 {
     if (p.topo == 1)
-        cube_z_tile_kernel<M, STAGE><<<tile_grid(p.N1), kTileThreads, cube_tile_smem(p.N1), s>>>(p, step_size(dt));
+        cube_z_tile_kernel<M, STAGE><<<tile_grid(p.N1), kZThreads, cube_tile_smem(p.N1), s>>>(p, step_size(dt));
     else if (p.wmode) lattice_gather_kernel<M, STAGE, true><<<gather_grid(p), kGatherThreads, 0, s>>>(p, step_size(dt));
     else lattice_gather_kernel<M, STAGE, false><<<gather_grid(p), kGatherThreads, 0, s>>>(p, step_size(dt));
     return cudaGetLastError();

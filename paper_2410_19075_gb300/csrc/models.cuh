@@ -46,21 +46,21 @@ __device__ __forceinline__ void angle_add(const ModelParams &P, const int64_t (&
     cxa = fixed_to_double((int64_t)(__mul64hi(c, ca) - __mul64hi(s, sa)), 60);
 }
 
-// Kuramoto coupling on a lattice.  The lattice x pass sums the coupled quantity
-// rotated by -alpha, so the window sums are W' = W'c + i W's = sum over the
-// window (the node itself included) of e^{-i alpha} Q(e^{i phi_j}), int64 on the
-// grid 2^-F.  Then
+// Kuramoto coupling on a lattice.  The window sums arrive rotated by -alpha:
+// W' = W'c + i W's = sum over the window (the node itself included) of
+// e^{-i alpha} Q(e^{i phi_j}), int64 on the grid 2^-F (the ball and disk x pass
+// rotates every node's quantity, the cube y pass its window sums).  Then
 //   T = Im[e^{-i phi_i} W'] = cos(phi_i) W's - sin(phi_i) W'c
 //     = sum_j sin(phi_j - phi_i - alpha)   (the node's own term is -sin alpha),
 // two 64 x 64 high products of the node's own (sin, cos) on the grid 2^-62 with
-// the sums (grid 2^-(F-2)) and one correctly rounded conversion.  The window
-// without the node itself is T + sin alpha, the constant being folded into
-// c[4] on the host (quantisation makes the node's own rotated term differ from
-// -sin alpha by a few units of 2^-F).
-__device__ __forceinline__ double lattice_coupling(const int64_t (&f62)[2], int64_t W0, int64_t W1, int F)
+// the sums, on the grid 2^-(F-2).  The caller converts T once (correctly
+// rounded, the grid's power of two folded into c[5]); the window without the
+// node itself is T + sin alpha, the constant folded into c[4] on the host
+// (quantisation makes the node's own rotated term differ from -sin alpha by a
+// few units of 2^-F).
+__device__ __forceinline__ double lattice_coupling(const int64_t (&f62)[2], int64_t W0, int64_t W1)
 {
-    const int64_t T = (int64_t)__mul64hi(f62[1], W0) - (int64_t)__mul64hi(f62[0], W1);
-    return fixed_to_double(T, F - 2);
+    return __ll2double_rn(mulhi_ss(f62[1], W0) - mulhi_ss(f62[0], W1));
 }
 
 // Kuramoto-Sakaguchi, Eq. (3) with m = 0, eps = 1 (Algorithm 1):
@@ -92,11 +92,12 @@ template <> struct Model<0> {
         angle_add(P, qo, F_, f62, sxa, cxa);
         k[0] = P.c[0] + P.c[1] * (cxa * Ss - sxa * Sc);
     }
-    // Lattices: c[4] = omega + (mu/K) sin alpha (omega with the node itself as a link).
-    __device__ __forceinline__ static void rhs_lattice(const ModelParams &P, int F, const int64_t (&f62)[2],
-                                                       int64_t W0, int64_t W1, const double *, double (&k)[D])
+    // Lattices: c[4] = omega + (mu/K) sin alpha (omega with the node itself as a
+    // link), c[5] = (mu/K) 2^-(F-2).
+    __device__ __forceinline__ static void rhs_lattice(const ModelParams &P, const int64_t (&f62)[2], int64_t W0,
+                                                       int64_t W1, const double *, double (&k)[D])
     {
-        k[0] = fma(P.c[1], lattice_coupling(f62, W0, W1, F), P.c[4]);
+        k[0] = fma(P.c[5], lattice_coupling(f62, W0, W1), P.c[4]);
     }
 };
 
@@ -201,12 +202,13 @@ template <> struct Model<3> {
         k[0] = psi;
         k[1] = fma(P.c[0], cxa * Ss - sxa * Sc, -P.c[1] * psi);
     }
-    // Lattices: c[4] = (mu/(m K)) sin alpha (0 with the node itself as a link).
-    __device__ __forceinline__ static void rhs_lattice(const ModelParams &P, int F, const int64_t (&f62)[2],
-                                                       int64_t W0, int64_t W1, const double *X, double (&k)[D])
+    // Lattices: c[4] = (mu/(m K)) sin alpha (0 with the node itself as a link),
+    // c[5] = (mu/(m K)) 2^-(F-2).
+    __device__ __forceinline__ static void rhs_lattice(const ModelParams &P, const int64_t (&f62)[2], int64_t W0,
+                                                       int64_t W1, const double *X, double (&k)[D])
     {
         k[0] = X[0];
-        k[1] = fma(P.c[0], lattice_coupling(f62, W0, W1, F), fma(-P.c[1], X[0], P.c[4]));
+        k[1] = fma(P.c[5], lattice_coupling(f62, W0, W1), fma(-P.c[1], X[0], P.c[4]));
     }
 };
 

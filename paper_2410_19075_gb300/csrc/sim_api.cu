@@ -401,6 +401,27 @@ void simk::model_constants(int model, const double *params, double K, ModelParam
     }
 }
 
+// A lattice's rotation of the window sums by -alpha and the scale of the
+// right-hand side's cross product (see lattice_coupling and cube_rotate).
+void simk::lattice_rotation(LatticePlan &p, double alpha)
+{
+    const long double half_pi = 1.570796326794896619231321691639751442L;
+    const long double a = (long double)alpha;
+    long double q = floorl(a / half_pi);
+    const long double a0 = a - q * half_pi; // in [0, pi/2) up to rounding
+    const long double c0 = cosl(a0), s0 = sinl(a0);
+    const long double two63 = 9223372036854775808.0L;
+    p.rot_c = (uint64_t)roundl(fminl(fmaxl(c0, 0.0L), 1.0L) * two63); // <= 2^63
+    p.rot_s = (uint64_t)roundl(fminl(fmaxl(s0, 0.0L), 1.0L) * two63);
+    long long qi = (long long)q % 4;
+    p.rot_q = (int)(qi < 0 ? qi + 4 : qi);
+    // shift of the y-window sums (|W| <= (2P+1)^2 2^F) that keeps them below 2^62
+    const int g = 62 - p.F - ceil_log2((uint64_t)((2 * p.P + 1) * (2 * p.P + 1)));
+    p.rot_g = g < 10 ? g : 10;
+    // the cross product T lands on the grid 2^-(F-2): fold that scale into the coefficient
+    p.mp.c[5] = std::ldexp(p.model == SIM_KS ? p.mp.c[1] : p.mp.c[0], -(p.F - 2));
+}
+
 extern "C" {
 
 size_t sim_workspace_bytes(int model, int topology, int64_t N, int64_t radius)
@@ -544,6 +565,7 @@ static int create_impl(sim_t *out, int model, int topology, int64_t N, int64_t r
         p.nodes = h->nodes;
         p.F = 61 - ceil_log2((uint64_t)mp.wsize);
         p.mp = mp;
+        lattice_rotation(p, model == SIM_KS ? params[2] : params[3]);
         p.y = reinterpret_cast<double *>(b + L.y);
         p.acc = reinterpret_cast<double *>(b + L.acc);
         p.f = reinterpret_cast<int64_t *>(b + L.f);
