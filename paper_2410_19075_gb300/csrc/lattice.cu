@@ -44,22 +44,26 @@ static int row_warps(int64_t N1)
 }
 
 // The coupled quantity a ball's or disk's window sums add up: the node's (sin,
-// cos) on the grid 2^-62 rotated by -alpha,
-//   e^{-i alpha} (c + i s) = (c cos a + s sin a) + i (s cos a - c sin a),
-// four 64 x 64 high products with cos alpha and sin alpha on the grid 2^-62
-// (which land on the grid 2^-60, so their truncation leaves no bias that a
-// window of millions of terms could accumulate), then rounded to nearest onto
-// the grid 2^-F.  The right-hand side then needs only the node's own unrotated
-// (sin, cos) (lattice_coupling).
+// cos) on the grid 2^-62 rotated by -alpha = -(rot_q pi/2 + alpha0),
+//   e^{-i alpha0} (c + i s) = (c cos a0 + s sin a0) + i (s cos a0 - c sin a0),
+// four high products with cos alpha0 and sin alpha0 (non-negative, grid 2^-63),
+// which land on the grid 2^-61 (so their truncation leaves no bias that a
+// window of millions of terms could accumulate), rounded to nearest onto the
+// grid 2^-F, then rot_q quarter turns.  The right-hand side then needs only the
+// node's own unrotated (sin, cos) (lattice_coupling).
 __device__ __forceinline__ void lattice_rotated_q(const LatticePlan &p, int64_t s62, int64_t c62, int64_t &qs,
                                                   int64_t &qc)
 {
-    const int64_t ca = p.mp.q[0], sa = p.mp.q[1];
-    const int64_t s60 = (int64_t)__mul64hi(s62, ca) - (int64_t)__mul64hi(c62, sa);
-    const int64_t c60 = (int64_t)__mul64hi(c62, ca) + (int64_t)__mul64hi(s62, sa);
-    const int sh = 60 - p.F;
-    qs = (s60 + (int64_t(1) << (sh - 1))) >> sh;
-    qc = (c60 + (int64_t(1) << (sh - 1))) >> sh;
+    const int sh = 61 - p.F;
+    const int64_t h = int64_t(1) << (sh - 1);
+    const int64_t c1 = (mulhi_su(c62, p.rot_c) + mulhi_su(s62, p.rot_s) + h) >> sh;
+    const int64_t s1 = (mulhi_su(s62, p.rot_c) - mulhi_su(c62, p.rot_s) + h) >> sh;
+    switch (p.rot_q) { // e^{-i q pi/2}: 1, -i, -1, i
+    case 0: qc = c1; qs = s1; break;
+    case 1: qc = s1; qs = -c1; break;
+    case 2: qc = -c1; qs = -s1; break;
+    default: qc = -s1; qs = c1; break;
+    }
 }
 
 // x pass: one warp per row.  pre(p) = sum_{m<p} Q'(f(m)) for p in [0, N1] is built
@@ -418,10 +422,12 @@ __device__ __forceinline__ void lattice_node_load(const LatticePlan &p, int64_t 
     }
 }
 
-template <int M, int STAGE>
+// Acc: the type of the thread's order-parameter sums (int64 where a thread
+// handles few enough nodes that |sum| <= nodes 2^F stays below 2^63).
+template <int M, int STAGE, typename Acc>
 __device__ __forceinline__ void lattice_node_finish(const LatticePlan &p, int64_t n, int64_t W0, int64_t W1,
-                                                    const LatNodeIn<M> &in, const StepSize &h, bool &ok, i128 &ps,
-                                                    i128 &pc)
+                                                    const LatNodeIn<M> &in, const StepSize &h, bool &ok, Acc &ps,
+                                                    Acc &pc)
 {
     constexpr int D = Model<M>::D, NX = Model<M>::NX, XOFF = D - NX;
     const int64_t nodes = p.nodes;
@@ -469,7 +475,7 @@ __device__ __forceinline__ void lattice_node(const LatticePlan &p, int64_t n, in
 {
     LatNodeIn<M> in;
     lattice_node_load<M, STAGE>(p, n, in);
-    lattice_node_finish<M, STAGE>(p, n, W0, W1, in, h, ok, ps, pc);
+    lattice_node_finish<M, STAGE, i128>(p, n, W0, W1, in, h, ok, ps, pc);
 }
 
 // cube z pass: one thread per segment of an (i, j) column, sliding window along
@@ -645,7 +651,7 @@ __global__ void __launch_bounds__(kTileThreads) cube_y_tile_kernel(LatticePlan p
 // Tiled cube z pass (stages 1-4): CTA (ib, j) scans the xy-window sums of its
 // columns along k, then runs the node update of each of its nodes (thread
 // (ii, r0) takes the planes k = r0, r0 + kZThreads / BI, ...), the loads of the
-// next two nodes in flight while one computes.  384 threads: three CTAs per SM
+// next two nodes (one for the inertia model) in flight while one computes.  384 threads: three CTAs per SM
 // at the tile sizes of N1 <= 594 (up to 60 KB of shared memory each).
 constexpr int kZThreads = 384;
 
@@ -662,30 +668,45 @@ __global__ void __launch_bounds__(kZThreads, 3) cube_z_tile_kernel(LatticePlan p
     const int64_t base = (int64_t)j * N1 + i0;
     cube_tile_load_scan<kZThreads>(p.sxy, p.nodes, base, plane, N1, lg, bi, tile);
     const int ii = threadIdx.x & (BI - 1), r0 = threadIdx.x >> lg, rstep = kZThreads >> lg;
-    i128 ps = 0, pc = 0;
+    int64_t ps = 0, pc = 0; // at most ceil(N1 / rstep) <= 13 nodes of |q| <= 2^F per thread
     bool ok = true;
     if (ii < bi && r0 < N1) {
         const unsigned cstride = (unsigned)(N1 + 1) << lg;
         const uint64_t *col0 = tile + ii, *col1 = tile + cstride + ii;
         const uint64_t t0 = col0[(unsigned)N1 << lg], t1 = col1[(unsigned)N1 << lg];
         const int64_t nb = base + ii;
-        LatNodeIn<M> b0, b1;
-        lattice_node_load<M, STAGE>(p, nb + (int64_t)((unsigned)r0 * plane), b0);
-        if (r0 + rstep < N1) lattice_node_load<M, STAGE>(p, nb + (int64_t)((unsigned)(r0 + rstep) * plane), b1);
-        for (int a = r0; a < N1; a += rstep) {
-            const int a2 = a + 2 * rstep;
-            LatNodeIn<M> b2;
-            if (a2 < N1) lattice_node_load<M, STAGE>(p, nb + (int64_t)((unsigned)a2 * plane), b2);
-            lattice_node_finish<M, STAGE>(p, nb + (int64_t)((unsigned)a * plane),
-                                          cube_tile_window(col0, N1, P, lg, a, t0),
-                                          cube_tile_window(col1, N1, P, lg, a, t1), b0, h, ok, ps, pc);
-            b0 = b1;
-            b1 = b2;
+        if constexpr (Model<M>::D == 1) { // the loads of the next two nodes in flight
+            LatNodeIn<M> b0, b1;
+            lattice_node_load<M, STAGE>(p, nb + (int64_t)((unsigned)r0 * plane), b0);
+            if (r0 + rstep < N1) lattice_node_load<M, STAGE>(p, nb + (int64_t)((unsigned)(r0 + rstep) * plane), b1);
+            for (int a = r0; a < N1; a += rstep) {
+                const int a2 = a + 2 * rstep;
+                LatNodeIn<M> b2;
+                if (a2 < N1) lattice_node_load<M, STAGE>(p, nb + (int64_t)((unsigned)a2 * plane), b2);
+                lattice_node_finish<M, STAGE, int64_t>(p, nb + (int64_t)((unsigned)a * plane),
+                                                       cube_tile_window(col0, N1, P, lg, a, t0),
+                                                       cube_tile_window(col1, N1, P, lg, a, t1), b0, h, ok, ps, pc);
+                b0 = b1;
+                b1 = b2;
+            }
+        } else { // more state per node: the next node's loads only
+            LatNodeIn<M> b0;
+            lattice_node_load<M, STAGE>(p, nb + (int64_t)((unsigned)r0 * plane), b0);
+            for (int a = r0; a < N1; a += rstep) {
+                const int a1 = a + rstep;
+                LatNodeIn<M> b1;
+                if (a1 < N1) lattice_node_load<M, STAGE>(p, nb + (int64_t)((unsigned)a1 * plane), b1);
+                lattice_node_finish<M, STAGE, int64_t>(p, nb + (int64_t)((unsigned)a * plane),
+                                                       cube_tile_window(col0, N1, P, lg, a, t0),
+                                                       cube_tile_window(col1, N1, P, lg, a, t1), b0, h, ok, ps, pc);
+                b0 = b1;
+            }
         }
     }
     if (!ok) raise_error(p.err, ERR_RANGE);
     if (STAGE == 4)
-        lattice_record_order(p, ps, pc, blockIdx.y * gridDim.x + blockIdx.x, gridDim.x * gridDim.y, p.tile_ctr);
+        lattice_record_order(p, (i128)ps, (i128)pc, blockIdx.y * gridDim.x + blockIdx.x, gridDim.x * gridDim.y,
+                             p.tile_ctr);
 }
 
 // Batched cube z pass (stages 1-4): CTA b is CTA b - yz_base[m] of member m.
