@@ -57,13 +57,17 @@ RING_BYTES = {0: 344, 1: 432, 2: 704, 3: 480}
 RING_FLOPS = {0: 4 * 5 + 13, 1: 4 * 15 + 2 * 13, 2: 4 * (6 * 17 + 40) + 3 * 16 + 12, 3: 4 * 6 + 2 * 13}
 # Cube (Kuramoto), bytes per node of each pass (launch): x pass reads (sin, cos)
 # on the 2^-62 grid and writes the x-window sums (16 + 16); y pass reads those
-# and writes the xy-window sums (16 + 16); z pass reads the xy sums (16), the
-# node's own (sin, cos) (16), y (8) and acc (8, stages 2-4), writes the next
-# (sin, cos) (16) and acc or y (8): 64 B in stage 1, 72 B in stages 2-4.
-CUBE_PASS_BYTES = {0: 32.0, 1: 32.0, 2: (64.0 + 3 * 72.0) / 4}
-CUBE_BYTES = 4 * (32 + 32) + 64 + 3 * 72  # 536 per node-step
+# and writes the xy-window sums (16 + 16); z-window pass reads the xy sums (16)
+# and the node's own (sin, cos) (16) and writes the coupling term (8); node
+# pass reads the coupling term (8), y (8) and acc (8, stages 2-4), writes acc
+# (8, stages 1-3) or y (8, stage 4) and the next (sin, cos) (16): 40 B in stage
+# 1, 48 B in stages 2-4.
+CUBE_PASS_BYTES = {0: 32.0, 1: 32.0, 3: 40.0, 2: (40.0 + 3 * 48.0) / 4}
+CUBE_BYTES = 4 * (32 + 32 + 40) + 40 + 3 * 48  # 600 per node-step
 CUBE_BYTES_SURVEY = 432  # the survey's model of the same three passes (24 + 32 + 56 per stage)
-CUBE_PASS_FLOPS = {0: 0.0, 1: 0.0, 2: RING_FLOPS[0] / 4}
+# FP64 flops per node and launch: the z-window pass's FMA on the converted cross
+# product, the node pass's RK4 update (13 per node-step).
+CUBE_PASS_FLOPS = {0: 0.0, 1: 0.0, 3: 2.0, 2: 13 / 4}
 # Ball / disk lattices: per stage the x pass reads (sin, cos) and writes the row
 # prefixes (32 B per node); the gather reads each prefix once from HBM (16 B; the
 # chord reads re-hit L1/L2), the stage-input (sin, cos) (16 B), y, acc and the
@@ -256,9 +260,13 @@ def measured_peaks():
     with Clocked() as ck:
         dfma = sim.probe_peak(0)
         mulhi = sim.probe_peak(1)
+        imad = sim.probe_peak(2)
+        cvt = sim.probe_peak(3)
+        mulhi_s = sim.probe_peak(4)
     return {"hbm_gbs": float(hbm) if hbm else 6800.0,
             "hbm_source": "MEASURED_PEAKS.json (copy, read + write)" if hbm else "fallback 6.8 TB/s",
             "fp64_gflops": 2.0 * dfma / 1e9, "dfma_per_s": dfma, "mulhi64_per_s": mulhi,
+            "imad32_per_s": imad, "cvt_f64_s64_per_s": cvt, "mulhi64_signed_per_s": mulhi_s,
             "fp64_source": "sim_probe_peak(0): DFMA throughput measured in this run (2 flops each)",
             "probe_clocks": ck.record}
 
@@ -439,8 +447,9 @@ def ring_kind_flops(model):
     return {"stage_or_x": RING_FLOPS[model] / 4}
 
 
-CUBE_KIND_BYTES = {"stage_or_x": CUBE_PASS_BYTES[0], "cube_y": CUBE_PASS_BYTES[1], "node_pass": CUBE_PASS_BYTES[2]}
-CUBE_KIND_FLOPS = {"stage_or_x": 0.0, "cube_y": 0.0, "node_pass": CUBE_PASS_FLOPS[2]}
+CUBE_KIND_BYTES = {"stage_or_x": CUBE_PASS_BYTES[0], "cube_y": CUBE_PASS_BYTES[1], "cube_z": CUBE_PASS_BYTES[3],
+                   "node_pass": CUBE_PASS_BYTES[2]}
+CUBE_KIND_FLOPS = {"stage_or_x": 0.0, "cube_y": 0.0, "cube_z": CUBE_PASS_FLOPS[3], "node_pass": CUBE_PASS_FLOPS[2]}
 
 
 def network_leg(model, topo, N, R, params, steps, chunk, dt, flush, stream, peaks, seed=2419, tune=True,

@@ -172,8 +172,9 @@ int sim_step(sim_t h, int64_t n_steps, double dt);
  * with a kernel of kind k, launches_by_kind[k] their number (4 entries each):
  * kind 0 = the fused stage kernel of a ring or link matrix (one per stage; the
  * whole call for the cluster-resident small-ring kernel) or the x pass of a
- * lattice, 1 = the y pass of the cube, 2 = the node pass of a lattice (the z
- * pass of the cube, the chord gather of the ball and disk), 3 = unused.  The
+ * lattice, 1 = the y pass of the cube, 2 = the node pass of a lattice (the
+ * elementwise RK4 pass of the cube, the chord gather of the ball and disk), 3 =
+ * the z-window pass of the cube.  The
  * state advances exactly as with sim_step (the same bits).  Returns the device
  * error status like sim_sync.  Errors: SIM_EINVAL (NULL handle or output,
  * n_steps out of range, invalid dt), SIM_EDEVICE. */
@@ -448,7 +449,8 @@ int sim_math_eval(int fn, const double *host_x, double *host_out, int64_t n);
  * denominators (not part of the method; a utility of the benchmark): kind 0 =
  * FP64 fused multiply-adds per second (count 2 flops each), 1 = 64-bit integer
  * multiply-highs (mul.hi.u64) per second, 2 = 32-bit integer multiply-adds per
- * second.  Every thread of a grid of 8 CTAs per SM runs 8 independent dependent
+ * second, 3 = int64 -> double conversions (cvt.rn.f64.s64) per second, 4 =
+ * signed 64-bit multiply-highs (mul.hi.s64) per second.  Every thread of a grid of 8 CTAs per SM runs 8 independent dependent
  * chains of the operation; one warm-up launch, then one launch timed with CUDA
  * events (tens of milliseconds).  Allocates and frees 64 bytes of device memory
  * and a stream; synchronous.  Errors: SIM_EINVAL (unknown kind or NULL output),

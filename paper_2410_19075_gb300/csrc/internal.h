@@ -179,9 +179,10 @@ struct LatticePlan {
     int wmode;        // ball, disk: sx holds, for w = 0..P, nodes (sin, cos) pairs of the
                       // x-window sums S_w (one load per chord) instead of the row prefixes
     int64_t *sxy;     // 2 * nodes: cube box sums over x and y
+    double *cpl;      // cube: nodes coupling terms of the current stage (window pass -> node pass)
     i128 *partial;    // per-CTA partial sums of the order parameter
     unsigned long long *done_ctr; // arrival counter of the sliding-window node passes (and the prologue)
-    unsigned long long *tile_ctr; // arrival counter of the tiled cube z pass (another CTA count per launch)
+    unsigned long long *tile_ctr; // arrival counter of the cube node pass (another CTA count per launch)
     unsigned *err;
     double *obs;
     int64_t obs_cap;
@@ -257,8 +258,8 @@ void lattice_rotation(LatticePlan &p, double alpha); // rot_* and mp.c[5] of a l
 // every stage-kernel launch of ring_step, graph_step, lattice_step and
 // ring_cluster_steps records an event of its kind right after itself (kinds:
 // 0 fused ring / link-matrix stage kernel or lattice x pass, 1 cube y pass,
-// 2 lattice node pass (cube z pass, ball / disk gather)).  Never set during a
-// stream capture.
+// 2 lattice node pass (cube node pass, ball / disk gather), 3 cube z-window
+// pass).  Never set during a stream capture.
 struct KernelMarks {
     cudaEvent_t *ev;
     unsigned char *kind;

@@ -422,10 +422,12 @@ __device__ __forceinline__ void lattice_node_load(const LatticePlan &p, int64_t 
     }
 }
 
-// Acc: the type of the thread's order-parameter sums (int64 where a thread
-// handles few enough nodes that |sum| <= nodes 2^F stays below 2^63).
+// The RK4 update of a node from its slope k (stages 1-4), the next stage
+// input's local variables and (sin, cos); STAGE 0 (prologue) only the (sin,
+// cos) of y.  Acc: the type of the thread's order-parameter sums (int64 where a
+// thread handles few enough nodes that |sum| <= nodes 2^F stays below 2^63).
 template <int M, int STAGE, typename Acc>
-__device__ __forceinline__ void lattice_node_finish(const LatticePlan &p, int64_t n, int64_t W0, int64_t W1,
+__device__ __forceinline__ void lattice_node_update(const LatticePlan &p, int64_t n, const double (&k)[Model<M>::D],
                                                     const LatNodeIn<M> &in, const StepSize &h, bool &ok, Acc &ps,
                                                     Acc &pc)
 {
@@ -436,8 +438,6 @@ __device__ __forceinline__ void lattice_node_finish(const LatticePlan &p, int64_
 #pragma unroll
         for (int v = 0; v < D; ++v) xn[v] = in.y[v];
     } else {
-        double k[D];
-        Model<M>::rhs_lattice(p.mp, in.f62, W0, W1, in.X, k);
 #pragma unroll
         for (int v = 0; v < D; ++v) {
             if (STAGE == 1) {
@@ -467,6 +467,18 @@ __device__ __forceinline__ void lattice_node_finish(const LatticePlan &p, int64_
         ps += q62_to(s62, p.F);
         pc += q62_to(c62, p.F);
     }
+}
+
+// The whole node stage: right-hand side from the window sums and the node's own
+// stage input, then lattice_node_update.
+template <int M, int STAGE, typename Acc>
+__device__ __forceinline__ void lattice_node_finish(const LatticePlan &p, int64_t n, int64_t W0, int64_t W1,
+                                                    const LatNodeIn<M> &in, const StepSize &h, bool &ok, Acc &ps,
+                                                    Acc &pc)
+{
+    double k[Model<M>::D] = {};
+    if (STAGE > 0) Model<M>::rhs_lattice(p.mp, in.f62, W0, W1, in.X, k);
+    lattice_node_update<M, STAGE, Acc>(p, n, k, in, h, ok, ps, pc);
 }
 
 template <int M, int STAGE>
@@ -648,17 +660,24 @@ __global__ void __launch_bounds__(kTileThreads) cube_y_tile_kernel(LatticePlan p
     }
 }
 
-// Tiled cube z pass (stages 1-4): CTA (ib, j) scans the xy-window sums of its
-// columns along k, then runs the node update of each of its nodes (thread
-// (ii, r0) takes the planes k = r0, r0 + kZThreads / BI, ...), the loads of the
-// next two nodes (one for the inertia model) in flight while one computes.  384 threads: three CTAs per SM
-// at the tile sizes of N1 <= 594 (up to 60 KB of shared memory each).
+// Tiled cube z pass, split in two kernels per stage:
+//   window pass  CTA (ib, j) scans the xy-window sums of its columns along k and
+//                writes every node's coupling term (lattice_coupling_term, the
+//                cross product of its own (sin, cos) with its window sums) to
+//                cpl; thread (ii, r0) takes the planes k = r0, r0 + kZThreads /
+//                BI, ..., the own (sin, cos) of the next two in flight;
+//   node pass    elementwise over the nodes (contiguous, grid-stride): the
+//                slope from cpl, the RK4 update, the next (sin, cos), and in
+//                stage 4 the order parameter.
+// The window pass keeps the tile's 64-byte row segments (the z columns are
+// N1^2 elements apart), the node pass reads and writes whole warps of
+// consecutive nodes.  Three window CTAs per SM at the tile sizes of N1 <= 594.
 constexpr int kZThreads = 384;
+constexpr int kNodeThreads = 256;
 
-template <int M, int STAGE>
-__global__ void __launch_bounds__(kZThreads, 3) cube_z_tile_kernel(LatticePlan p, const StepSize h)
+__global__ void __launch_bounds__(kZThreads, 3) cube_zw_tile_kernel(LatticePlan p)
 {
-    if (STAGE == 1 && p.skip && *(const volatile int *)p.skip) return; // stage 1 records nothing
+    if (p.skip && *(const volatile int *)p.skip) return;
     extern __shared__ int64_t tile_mem[];
     uint64_t *tile = reinterpret_cast<uint64_t *>(tile_mem);
     const int N1 = (int)p.N1, P = (int)p.P, lg = cube_tile_lg(N1), BI = 1 << lg;
@@ -668,45 +687,74 @@ __global__ void __launch_bounds__(kZThreads, 3) cube_z_tile_kernel(LatticePlan p
     const int64_t base = (int64_t)j * N1 + i0;
     cube_tile_load_scan<kZThreads>(p.sxy, p.nodes, base, plane, N1, lg, bi, tile);
     const int ii = threadIdx.x & (BI - 1), r0 = threadIdx.x >> lg, rstep = kZThreads >> lg;
-    int64_t ps = 0, pc = 0; // at most ceil(N1 / rstep) <= 13 nodes of |q| <= 2^F per thread
+    if (ii >= bi || r0 >= N1) return; // past every barrier
+    const unsigned cstride = (unsigned)(N1 + 1) << lg;
+    const uint64_t *col0 = tile + ii, *col1 = tile + cstride + ii;
+    const uint64_t t0 = col0[(unsigned)N1 << lg], t1 = col1[(unsigned)N1 << lg];
+    const int64_t *__restrict__ fs = p.f + base + ii;
+    const int64_t *__restrict__ fc = fs + p.nodes;
+    double *__restrict__ cpl = p.cpl + base + ii;
+    int64_t f0[2] = {fs[(unsigned)r0 * plane], fc[(unsigned)r0 * plane]}, f1[2] = {0, 0};
+    if (r0 + rstep < N1) {
+        f1[0] = fs[(unsigned)(r0 + rstep) * plane];
+        f1[1] = fc[(unsigned)(r0 + rstep) * plane];
+    }
+    for (int a = r0; a < N1; a += rstep) {
+        const int a2 = a + 2 * rstep;
+        int64_t f2[2] = {0, 0};
+        if (a2 < N1) {
+            f2[0] = fs[(unsigned)a2 * plane];
+            f2[1] = fc[(unsigned)a2 * plane];
+        }
+        cpl[(unsigned)a * plane] = lattice_coupling_term(p.mp, f0, cube_tile_window(col0, N1, P, lg, a, t0),
+                                                         cube_tile_window(col1, N1, P, lg, a, t1));
+        f0[0] = f1[0];
+        f0[1] = f1[1];
+        f1[0] = f2[0];
+        f1[1] = f2[1];
+    }
+}
+
+template <int M, int STAGE>
+__device__ __forceinline__ void cube_node_load(const LatticePlan &p, int64_t n, LatNodeIn<M> &in, double &c)
+{
+    constexpr int D = Model<M>::D, NX = Model<M>::NX, XOFF = D - NX;
+    const int64_t nodes = p.nodes;
+#pragma unroll
+    for (int v = 0; v < D; ++v) {
+        in.y[v] = p.y[v * nodes + n];
+        in.acc[v] = STAGE >= 2 ? p.acc[v * nodes + n] : 0.0;
+    }
+#pragma unroll
+    for (int g = 0; g < NX; ++g) in.X[g] = STAGE == 1 ? in.y[XOFF + g] : p.xs[g * nodes + n];
+    c = p.cpl[n];
+}
+
+template <int M, int STAGE>
+__global__ void __launch_bounds__(kNodeThreads) cube_node_kernel(LatticePlan p, const StepSize h)
+{
+    if (p.skip && *(const volatile int *)p.skip) return;
+    const int64_t nodes = p.nodes, stride = (int64_t)gridDim.x * kNodeThreads;
+    i128 ps = 0, pc = 0;
     bool ok = true;
-    if (ii < bi && r0 < N1) {
-        const unsigned cstride = (unsigned)(N1 + 1) << lg;
-        const uint64_t *col0 = tile + ii, *col1 = tile + cstride + ii;
-        const uint64_t t0 = col0[(unsigned)N1 << lg], t1 = col1[(unsigned)N1 << lg];
-        const int64_t nb = base + ii;
-        if constexpr (Model<M>::D == 1) { // the loads of the next two nodes in flight
-            LatNodeIn<M> b0, b1;
-            lattice_node_load<M, STAGE>(p, nb + (int64_t)((unsigned)r0 * plane), b0);
-            if (r0 + rstep < N1) lattice_node_load<M, STAGE>(p, nb + (int64_t)((unsigned)(r0 + rstep) * plane), b1);
-            for (int a = r0; a < N1; a += rstep) {
-                const int a2 = a + 2 * rstep;
-                LatNodeIn<M> b2;
-                if (a2 < N1) lattice_node_load<M, STAGE>(p, nb + (int64_t)((unsigned)a2 * plane), b2);
-                lattice_node_finish<M, STAGE, int64_t>(p, nb + (int64_t)((unsigned)a * plane),
-                                                       cube_tile_window(col0, N1, P, lg, a, t0),
-                                                       cube_tile_window(col1, N1, P, lg, a, t1), b0, h, ok, ps, pc);
-                b0 = b1;
-                b1 = b2;
-            }
-        } else { // more state per node: the next node's loads only
-            LatNodeIn<M> b0;
-            lattice_node_load<M, STAGE>(p, nb + (int64_t)((unsigned)r0 * plane), b0);
-            for (int a = r0; a < N1; a += rstep) {
-                const int a1 = a + rstep;
-                LatNodeIn<M> b1;
-                if (a1 < N1) lattice_node_load<M, STAGE>(p, nb + (int64_t)((unsigned)a1 * plane), b1);
-                lattice_node_finish<M, STAGE, int64_t>(p, nb + (int64_t)((unsigned)a * plane),
-                                                       cube_tile_window(col0, N1, P, lg, a, t0),
-                                                       cube_tile_window(col1, N1, P, lg, a, t1), b0, h, ok, ps, pc);
-                b0 = b1;
-            }
+    int64_t n = (int64_t)blockIdx.x * kNodeThreads + threadIdx.x;
+    if (n < nodes) {
+        LatNodeIn<M> cur;
+        double c;
+        cube_node_load<M, STAGE>(p, n, cur, c);
+        for (; n < nodes; n += stride) { // the next node's loads in flight
+            LatNodeIn<M> nxt;
+            double cn = 0.0;
+            if (n + stride < nodes) cube_node_load<M, STAGE>(p, n + stride, nxt, cn);
+            double k[Model<M>::D];
+            Model<M>::rhs_from_coupling(p.mp, c, cur.X, k);
+            lattice_node_update<M, STAGE, i128>(p, n, k, cur, h, ok, ps, pc);
+            cur = nxt;
+            c = cn;
         }
     }
     if (!ok) raise_error(p.err, ERR_RANGE);
-    if (STAGE == 4)
-        lattice_record_order(p, (i128)ps, (i128)pc, blockIdx.y * gridDim.x + blockIdx.x, gridDim.x * gridDim.y,
-                             p.tile_ctr);
+    if (STAGE == 4) lattice_record_order(p, ps, pc, blockIdx.x, gridDim.x, p.tile_ctr);
 }
 
 // Batched cube z pass (stages 1-4): CTA b is CTA b - yz_base[m] of member m.
@@ -783,6 +831,20 @@ static dim3 tile_grid(int64_t N1)
     return dim3((unsigned)((N1 + BI - 1) / BI), (unsigned)N1, 1);
 }
 
+// CTAs of the cube node pass: every node once, at most as many CTAs as fit on
+// the device at once, per model (0 Kuramoto, 1 with inertia) and for stages 1-3
+// and stage 4 (set by lattice_configure; the partial sums of the order
+// parameter, recorded in stage 4, are allocated for up to
+// lattice_partial_blocks of them, and a plan's stage-4 count never changes).
+static int64_t g_node_grid[2][2] = {{152 * 3, 152 * 3}, {152 * 3, 152 * 3}};
+
+static int64_t cube_node_grid(int model, int stage, int64_t nodes)
+{
+    const int64_t want = (nodes + kNodeThreads - 1) / kNodeThreads;
+    const int64_t cap = g_node_grid[model == 3 ? 1 : 0][stage == 4 ? 1 : 0];
+    return want < cap ? want : cap;
+}
+
 static unsigned gather_grid(const LatticePlan &p)
 {
     return (unsigned)((p.nodes + kGatherThreads - 1) / kGatherThreads);
@@ -799,8 +861,7 @@ int64_t lattice_partial_blocks(int topo, int64_t N1)
 {
     const int64_t a = lattice_order_blocks(topo, N1);
     if (topo != 1) return a;
-    const dim3 g = tile_grid(N1);
-    const int64_t b = (int64_t)g.x * g.y;
+    const int64_t b = (N1 * N1 * N1 + kNodeThreads - 1) / kNodeThreads; // the node pass, uncapped
     return a > b ? a : b;
 }
 
@@ -827,12 +888,18 @@ cudaError_t lattice_configure()
     // the largest tile of any edge: the top edge of each tile width
     const int tmax = (int)std::max(std::max(cube_tile_smem(297), cube_tile_smem(594)), cube_tile_smem(1024));
     if (e == cudaSuccess) e = cudaFuncSetAttribute(cube_y_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tmax);
-#define SIM_TILE_Z_ATTR(M, S)                                                                                          \
-    if (e == cudaSuccess)                                                                                              \
-        e = cudaFuncSetAttribute(cube_z_tile_kernel<M, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, tmax);
-    SIM_TILE_Z_ATTR(0, 1) SIM_TILE_Z_ATTR(0, 2) SIM_TILE_Z_ATTR(0, 3) SIM_TILE_Z_ATTR(0, 4)
-    SIM_TILE_Z_ATTR(3, 1) SIM_TILE_Z_ATTR(3, 2) SIM_TILE_Z_ATTR(3, 3) SIM_TILE_Z_ATTR(3, 4)
-#undef SIM_TILE_Z_ATTR
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(cube_zw_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tmax);
+    // the node pass: a grid of as many CTAs as fit on the device at once
+    int dev = 0, sms = 0, per_sm[4] = {0, 0, 0, 0};
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[0], cube_node_kernel<0, 2>, kNodeThreads, 0);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[1], cube_node_kernel<0, 4>, kNodeThreads, 0);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[2], cube_node_kernel<3, 2>, kNodeThreads, 0);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[3], cube_node_kernel<3, 4>, kNodeThreads, 0);
+    if (e == cudaSuccess)
+        for (int m = 0; m < 2; ++m)
+            for (int st = 0; st < 2; ++st) g_node_grid[m][st] = (int64_t)(per_sm[2 * m + st] > 0 ? per_sm[2 * m + st] : 1) * sms;
     return e;
 }
 
@@ -887,9 +954,13 @@ static cudaError_t launch_x(const LatticePlan &p, cudaStream_t s)
 template <int M, int STAGE>
 static cudaError_t launch_node_pass(const LatticePlan &p, double dt, cudaStream_t s)
 {
-    if (p.topo == 1)
-        cube_z_tile_kernel<M, STAGE><<<tile_grid(p.N1), kZThreads, cube_tile_smem(p.N1), s>>>(p, step_size(dt));
-    else if (p.wmode) lattice_gather_kernel<M, STAGE, true><<<gather_grid(p), kGatherThreads, 0, s>>>(p, step_size(dt));
+    if (p.topo == 1) {
+        cube_zw_tile_kernel<<<tile_grid(p.N1), kZThreads, cube_tile_smem(p.N1), s>>>(p);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        kernel_mark(s, 3);
+        cube_node_kernel<M, STAGE><<<(unsigned)cube_node_grid(M, STAGE, p.nodes), kNodeThreads, 0, s>>>(p, step_size(dt));
+    } else if (p.wmode) lattice_gather_kernel<M, STAGE, true><<<gather_grid(p), kGatherThreads, 0, s>>>(p, step_size(dt));
     else lattice_gather_kernel<M, STAGE, false><<<gather_grid(p), kGatherThreads, 0, s>>>(p, step_size(dt));
     return cudaGetLastError();
 }

@@ -63,6 +63,14 @@ __device__ __forceinline__ double lattice_coupling(const int64_t (&f62)[2], int6
     return __ll2double_rn(mulhi_ss(f62[1], W0) - mulhi_ss(f62[0], W1));
 }
 
+// Both Kuramoto models' coupling term on a lattice, c[5] T + c[4] (the whole
+// slope of the plain model, the coupling part of dpsi/dt with inertia).
+__device__ __forceinline__ double lattice_coupling_term(const ModelParams &P, const int64_t (&f62)[2], int64_t W0,
+                                                        int64_t W1)
+{
+    return fma(P.c[5], lattice_coupling(f62, W0, W1), P.c[4]);
+}
+
 // Kuramoto-Sakaguchi, Eq. (3) with m = 0, eps = 1 (Algorithm 1):
 //   dphi_i/dt = omega - (mu/K) sum_{j in W(i)} sin(phi_i - phi_j + alpha)
 //             = omega + (mu/K) [cos(phi_i+alpha) S_sin - sin(phi_i+alpha) S_cos],
@@ -97,7 +105,12 @@ template <> struct Model<0> {
     __device__ __forceinline__ static void rhs_lattice(const ModelParams &P, const int64_t (&f62)[2], int64_t W0,
                                                        int64_t W1, const double *, double (&k)[D])
     {
-        k[0] = fma(P.c[5], lattice_coupling(f62, W0, W1), P.c[4]);
+        k[0] = lattice_coupling_term(P, f62, W0, W1);
+    }
+    __device__ __forceinline__ static void rhs_from_coupling(const ModelParams &, double c, const double *,
+                                                             double (&k)[D])
+    {
+        k[0] = c;
     }
 };
 
@@ -203,12 +216,21 @@ template <> struct Model<3> {
         k[1] = fma(P.c[0], cxa * Ss - sxa * Sc, -P.c[1] * psi);
     }
     // Lattices: c[4] = (mu/(m K)) sin alpha (0 with the node itself as a link),
-    // c[5] = (mu/(m K)) 2^-(F-2).
+    // c[5] = (mu/(m K)) 2^-(F-2).  The coupling term first, then the damping
+    // (the order of the split cube node pass, which takes the coupling term
+    // from the window pass).
     __device__ __forceinline__ static void rhs_lattice(const ModelParams &P, const int64_t (&f62)[2], int64_t W0,
                                                        int64_t W1, const double *X, double (&k)[D])
     {
         k[0] = X[0];
-        k[1] = fma(P.c[5], lattice_coupling(f62, W0, W1), fma(-P.c[1], X[0], P.c[4]));
+        k[1] = fma(-P.c[1], X[0], lattice_coupling_term(P, f62, W0, W1));
+    }
+    // The slope from the coupling term c of lattice_coupling_term.
+    __device__ __forceinline__ static void rhs_from_coupling(const ModelParams &P, double c, const double *X,
+                                                             double (&k)[D])
+    {
+        k[0] = X[0];
+        k[1] = fma(-P.c[1], X[0], c);
     }
 };
 

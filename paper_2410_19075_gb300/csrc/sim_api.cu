@@ -152,7 +152,7 @@ struct Layout {
     size_t total = 0;
     size_t y, acc, xg0, xg1, npar, lam0, lam1, ingrp0, ingrp1, grpofs0, grpofs1, subtot, grptot, grpctr;
     size_t fsub0, fsub1, facc; // one-pass prefix (rings of at most kFlatMaxGroups groups)
-    size_t f, xs, sx, sxy, partial, chords, ctrs, obs, tabs;
+    size_t f, xs, sx, sxy, cpl, partial, chords, ctrs, obs, tabs;
 };
 
 // Ball and disk: one x-window array per chord half-width (one load per chord
@@ -207,6 +207,7 @@ Layout layout_of(int model, int topo, int64_t N, int64_t R, unsigned flags = 0)
         L.xs = take(sizeof(double) * model_nx(model) * n);
         L.sx = take(sizeof(int64_t) * lattice_sx_elems(topo, N, R, lattice_wmode(topo, N, R, flags)));
         L.sxy = take(topo == SIM_CUBE3D ? sizeof(int64_t) * 2 * n : 0);
+        L.cpl = take(topo == SIM_CUBE3D ? sizeof(double) * n : 0);
         L.partial = take(sizeof(i128) * 2 * nblk);
         L.chords = take(topo == SIM_CUBE3D ? 0 : sizeof(int4) * (2 * R + 1) * (2 * R + 1));
     }
@@ -574,6 +575,7 @@ static int create_impl(sim_t *out, int model, int topology, int64_t N, int64_t r
         p.rs = N + 2 * radius + 1;
         p.wmode = lattice_wmode(topology, N, radius, flags) ? 1 : 0;
         p.sxy = reinterpret_cast<int64_t *>(b + L.sxy);
+        p.cpl = reinterpret_cast<double *>(b + L.cpl);
         p.partial = reinterpret_cast<i128 *>(b + L.partial);
         p.done_ctr = ticket;
         p.tile_ctr = ctrs + 4;
@@ -874,7 +876,7 @@ int sim_step_timed(sim_t h, int64_t n_steps, double dt, double *ms_by_kind, int6
             h->pfx = 2;
         }
     }
-    const int per_step = use_cluster(h) ? 1 : h->topo == SIM_CUBE3D ? 12 : is_lattice(h->topo) ? 8 : 4;
+    const int per_step = use_cluster(h) ? 1 : h->topo == SIM_CUBE3D ? 16 : is_lattice(h->topo) ? 8 : 4;
     const int cap = (int)(use_cluster(h) ? 1 : per_step * n_steps);
     std::vector<cudaEvent_t> ev(cap + 1, nullptr);
     std::vector<unsigned char> kind(cap, 0);

@@ -37,7 +37,8 @@ def math_eval(fn: int, x) -> np.ndarray:
 
 def probe_peak(kind: int) -> float:
     """Measured peak rate of one arithmetic pipe (``sim_probe_peak``): kind 0 =
-    FP64 FMAs/s, 1 = 64-bit multiply-highs/s, 2 = 32-bit integer multiply-adds/s."""
+    FP64 FMAs/s, 1 = 64-bit multiply-highs/s, 2 = 32-bit integer multiply-adds/s,
+    3 = int64 -> double conversions/s, 4 = signed 64-bit multiply-highs/s."""
     v = ctypes.c_double(0.0)
     check(lib().sim_probe_peak(int(kind), ctypes.byref(v)))
     return float(v.value)
@@ -143,7 +144,7 @@ class Network:
         ms = (ctypes.c_double * 4)()
         n = (ctypes.c_int64 * 4)()
         check(lib().sim_step_timed(self._handle(), int(n_steps), float(dt), ms, n))
-        names = ("stage_or_x", "cube_y", "node_pass", "other")
+        names = ("stage_or_x", "cube_y", "node_pass", "cube_z")
         return {names[k]: {"ms": float(ms[k]), "launches": int(n[k])} for k in range(4) if n[k]}
 
     def dp5(self, t_end, rtol, atol, h0, t0=0.0, h_max=0.0, out_dt=0.0, max_attempts=10 ** 6):
