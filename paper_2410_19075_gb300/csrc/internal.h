@@ -178,7 +178,8 @@ struct LatticePlan {
     int64_t rs;       // ball, disk: row stride of sx in (sin, cos) pairs, N1 + 2P + 1
     int wmode;        // ball, disk: sx holds, for w = 0..P, nodes (sin, cos) pairs of the
                       // x-window sums S_w (one load per chord) instead of the row prefixes
-    int64_t *sxy;     // 2 * nodes: cube box sums over x and y
+    int64_t *sxy;     // cube box sums over x and y: 2 components, i-block-major (tiled passes)
+                      // or node order (the batched sliding passes)
     double *cpl;      // cube: nodes coupling terms of the current stage (window pass -> node pass)
     i128 *partial;    // per-CTA partial sums of the order parameter
     unsigned long long *done_ctr; // arrival counter of the sliding-window node passes (and the prologue)
@@ -229,6 +230,7 @@ cudaError_t graph_dp_attempt(const GraphDpPlan &d, cudaStream_t s);
 
 cudaError_t lattice_configure(); // once per process, before the first launch
 int64_t lattice_order_blocks(int topo, int64_t N1); // CTAs of the order-parameter passes (sliding-window grid)
+int64_t lattice_sxy_elems(int64_t N1); // cube: xy-window sums (both layouts of the y pass's output)
 int64_t lattice_partial_blocks(int topo, int64_t N1); // order-parameter partials to allocate (every grid)
 int64_t lattice_sx_elems(int topo, int64_t N1, int64_t P, bool wmode); // int64 elements of sx
 constexpr int64_t kLatticeWindowBudget = int64_t(8) << 30; // bytes of the per-w window arrays

@@ -562,6 +562,14 @@ __device__ __forceinline__ void cp_async8(uint64_t *dst, const uint64_t *src, bo
                  : "memory");
 }
 
+// Asynchronous 16-byte copy global -> shared (both addresses 16-byte aligned).
+__device__ __forceinline__ void cp_async16(uint64_t *dst, const uint64_t *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // i-columns per tile: shared memory 2 (N1 + 1) BI 8 bytes stays below ~76 KB
@@ -569,38 +577,28 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 __host__ __device__ inline int cube_tile_lg(int64_t N1) { return N1 <= 297 ? 4 : N1 <= 594 ? 3 : 2; }
 __host__ __device__ inline int cube_tile_bi(int64_t N1) { return 1 << cube_tile_lg(N1); }
 
+// Component stride of the tiled cube's xy-window sums in their i-block-major
+// layout [i-block][j][k][ii]: every i-block padded to BI columns.
+__host__ __device__ inline int64_t cube_sxy_cstride(int64_t N1)
+{
+    const int BI = cube_tile_bi(N1);
+    return ((N1 + BI - 1) / BI) * BI * N1 * N1;
+}
+
 __host__ __device__ inline size_t cube_tile_smem(int64_t N1)
 {
     return (size_t)2 * (size_t)(N1 + 1) * (size_t)cube_tile_bi(N1) * sizeof(int64_t);
 }
 
-// Load src[c nodes + base + a stride + ii] for c < 2, a < N1, ii < BI = 2^lg (0
-// for ii >= bi, past the cube's edge) into tile[(c (N1 + 1) + a + 1) BI + ii]
-// (asynchronous 8-byte copies, so that the whole tile is in flight at once),
-// zero row 0 of both components, then turn every column (c, ii) into its
-// inclusive prefix along a (wrapping uint64): kTileThreads / (2 BI) segments per
-// column, segment sums, their exclusive scan, rewrite (NT threads; NT / (2 BI)
-// segments per column).  Offsets inside the cube
-// are 32-bit (N1 <= 1024, so a * stride < 2^30).  Called by every thread of the
-// CTA; ends with a barrier.
+// Turn every column (c, ii) of a loaded tile into its inclusive prefix along a
+// (wrapping uint64): NT / (2 BI) segments per column, segment sums, their
+// exclusive scan, rewrite.  Called by every thread of the CTA after the tile's
+// rows 1..N1 and its zero row 0 are in place and visible; ends with a barrier.
 template <int NT>
-__device__ __forceinline__ void cube_tile_load_scan(const int64_t *__restrict__ src, int64_t nodes, int64_t base,
-                                                    unsigned stride, int N1, int lg, int bi, uint64_t *tile)
+__device__ __forceinline__ void cube_tile_scan(int N1, int lg, uint64_t *tile)
 {
-    const int tid = threadIdx.x, BI = 1 << lg, rstep = NT >> lg;
-    const int ii = tid & (BI - 1), r0 = tid >> lg;
-    const bool live = ii < bi;
+    const int tid = threadIdx.x, BI = 1 << lg;
     const unsigned cstride = (unsigned)(N1 + 1) << lg; // tile words per component
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-        // past the cube's edge: a zero fill from an in-bounds address
-        const uint64_t *__restrict__ s = reinterpret_cast<const uint64_t *>(src) + c * nodes + base + (live ? ii : 0);
-        uint64_t *t = tile + c * cstride + BI + ii;
-        for (int a = r0; a < N1; a += rstep) cp_async8(t + ((unsigned)a << lg), s + (unsigned)a * stride, live);
-    }
-    if (tid < 2 * BI) tile[(tid >> lg) * cstride + (tid & (BI - 1))] = 0ull;
-    cp_async_wait_all();
-    __syncthreads();
     __shared__ uint64_t s_seg[NT];
     const int ncol = 2 * BI, nseg = NT / ncol;
     const int col = tid & (ncol - 1), sg = tid >> (lg + 1);
@@ -620,6 +618,55 @@ __device__ __forceinline__ void cube_tile_load_scan(const int64_t *__restrict__ 
     __syncthreads();
 }
 
+// Load src[c nodes + base + a stride + ii] for c < 2, a < N1, ii < BI = 2^lg (0
+// for ii >= bi, past the cube's edge) into tile[(c (N1 + 1) + a + 1) BI + ii]
+// (asynchronous 8-byte copies, so that the whole tile is in flight at once),
+// zero row 0 of both components, then scan (cube_tile_scan).  Offsets inside
+// the cube are 32-bit (N1 <= 1024, so a * stride < 2^30).  Called by every
+// thread of the CTA; ends with a barrier.
+template <int NT>
+__device__ __forceinline__ void cube_tile_load_scan(const int64_t *__restrict__ src, int64_t nodes, int64_t base,
+                                                    unsigned stride, int N1, int lg, int bi, uint64_t *tile)
+{
+    const int tid = threadIdx.x, BI = 1 << lg, rstep = NT >> lg;
+    const int ii = tid & (BI - 1), r0 = tid >> lg;
+    const bool live = ii < bi;
+    const unsigned cstride = (unsigned)(N1 + 1) << lg;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        // past the cube's edge: a zero fill from an in-bounds address
+        const uint64_t *__restrict__ s = reinterpret_cast<const uint64_t *>(src) + c * nodes + base + (live ? ii : 0);
+        uint64_t *t = tile + c * cstride + BI + ii;
+        for (int a = r0; a < N1; a += rstep) cp_async8(t + ((unsigned)a << lg), s + (unsigned)a * stride, live);
+    }
+    if (tid < 2 * BI) tile[(tid >> lg) * cstride + (tid & (BI - 1))] = 0ull;
+    cp_async_wait_all();
+    __syncthreads();
+    cube_tile_scan<NT>(N1, lg, tile);
+}
+
+// The same from a contiguous block per component (the i-block-major layout of
+// the xy-window sums, blk[c] + a BI + ii, zeros already stored past the edge):
+// asynchronous 16-byte copies.
+template <int NT>
+__device__ __forceinline__ void cube_tile_load_scan_contig(const int64_t *blk0, const int64_t *blk1, int N1, int lg,
+                                                           uint64_t *tile)
+{
+    const int tid = threadIdx.x, BI = 1 << lg;
+    const unsigned cstride = (unsigned)(N1 + 1) << lg;
+    const int words = N1 << lg; // even: BI >= 4
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const uint64_t *__restrict__ s = reinterpret_cast<const uint64_t *>(c ? blk1 : blk0);
+        uint64_t *t = tile + c * cstride + BI;
+        for (int e = 2 * tid; e < words; e += 2 * NT) cp_async16(t + e, s + e);
+    }
+    if (tid < 2 * BI) tile[(tid >> lg) * cstride + (tid & (BI - 1))] = 0ull;
+    cp_async_wait_all();
+    __syncthreads();
+    cube_tile_scan<NT>(N1, lg, tile);
+}
+
 // Window sum at a (0 <= a < N1) of a scanned column colp (its words BI = 2^lg
 // apart, total = colp[N1 BI]): Pe(a + P + 1) - Pe(a - P) on the periodic
 // extension Pe(x) = pre(x mod N1) + floor(x / N1) total.  As 2P + 1 <= N1, at
@@ -633,7 +680,8 @@ __device__ __forceinline__ int64_t cube_tile_window(const uint64_t *colp, int N1
     return (int64_t)(colp[(unsigned)b << lg] - colp[(unsigned)lo << lg] + ((wb || wl) ? total : 0ull));
 }
 
-// Tiled cube y pass: CTA (ib, k); writes the window sums rotated by -alpha.
+// Tiled cube y pass: CTA (ib, k); writes the window sums rotated by -alpha, in
+// the i-block-major layout the z-window pass reads as one contiguous block.
 __global__ void __launch_bounds__(kTileThreads) cube_y_tile_kernel(LatticePlan p)
 {
     if (p.skip && *(const volatile int *)p.skip) return;
@@ -645,18 +693,22 @@ __global__ void __launch_bounds__(kTileThreads) cube_y_tile_kernel(LatticePlan p
     const int64_t base = (int64_t)k * N1 * N1 + i0;
     cube_tile_load_scan<kTileThreads>(p.sx, p.nodes, base, (unsigned)N1, N1, lg, bi, tile);
     const int ii = threadIdx.x & (BI - 1), r0 = threadIdx.x >> lg, rstep = kTileThreads >> lg;
-    if (ii >= bi) return; // past every barrier
     const unsigned cstride = (unsigned)(N1 + 1) << lg;
     const uint64_t *col0 = tile + ii, *col1 = tile + cstride + ii;
     const uint64_t t0 = col0[(unsigned)N1 << lg], t1 = col1[(unsigned)N1 << lg];
-    int64_t *__restrict__ d0 = p.sxy + base + ii;
-    int64_t *__restrict__ d1 = d0 + p.nodes;
+    // i-block-major output: element (ii, j = a, k) at ((ib N1 + a) N1 + k) BI + ii,
+    // zeros past the cube's edge
+    int64_t *__restrict__ d0 = p.sxy + (((int64_t)blockIdx.x * N1) * N1 + k) * BI + ii;
+    int64_t *__restrict__ d1 = d0 + cube_sxy_cstride(N1);
+    const unsigned dstep = (unsigned)N1 << lg;
 #pragma unroll 2
     for (int a = r0; a < N1; a += rstep) {
-        int64_t r0s, r1c;
-        cube_rotate(p, cube_tile_window(col0, N1, P, lg, a, t0), cube_tile_window(col1, N1, P, lg, a, t1), r0s, r1c);
-        d0[(unsigned)a * (unsigned)N1] = r0s;
-        d1[(unsigned)a * (unsigned)N1] = r1c;
+        int64_t r0s = 0, r1c = 0;
+        if (ii < bi)
+            cube_rotate(p, cube_tile_window(col0, N1, P, lg, a, t0), cube_tile_window(col1, N1, P, lg, a, t1), r0s,
+                        r1c);
+        d0[(unsigned)a * dstep] = r0s;
+        d1[(unsigned)a * dstep] = r1c;
     }
 }
 
@@ -685,7 +737,8 @@ __global__ void __launch_bounds__(kZThreads, 3) cube_zw_tile_kernel(LatticePlan 
     const int bi = min(BI, N1 - i0);
     const unsigned plane = (unsigned)N1 * (unsigned)N1;
     const int64_t base = (int64_t)j * N1 + i0;
-    cube_tile_load_scan<kZThreads>(p.sxy, p.nodes, base, plane, N1, lg, bi, tile);
+    const int64_t *blk = p.sxy + (((int64_t)blockIdx.x * N1 + j) * N1) * BI; // i-block-major
+    cube_tile_load_scan_contig<kZThreads>(blk, blk + cube_sxy_cstride(N1), N1, lg, tile);
     const int ii = threadIdx.x & (BI - 1), r0 = threadIdx.x >> lg, rstep = kZThreads >> lg;
     if (ii >= bi || r0 >= N1) return; // past every barrier
     const unsigned cstride = (unsigned)(N1 + 1) << lg;
@@ -855,6 +908,12 @@ int64_t lattice_sx_elems(int topo, int64_t N1, int64_t P, bool wmode)
     if (topo == 1) return 2 * N1 * N1 * N1;
     const int64_t rows = topo == 3 ? N1 : N1 * N1;
     return wmode ? 2 * (P + 1) * rows * N1 : 2 * rows * (N1 + 2 * P + 1);
+}
+
+int64_t lattice_sxy_elems(int64_t N1)
+{
+    const int64_t a = N1 * N1 * N1, b = cube_sxy_cstride(N1);
+    return 2 * (a > b ? a : b);
 }
 
 int64_t lattice_partial_blocks(int topo, int64_t N1)

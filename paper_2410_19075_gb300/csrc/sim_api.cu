@@ -206,7 +206,7 @@ Layout layout_of(int model, int topo, int64_t N, int64_t R, unsigned flags = 0)
         L.f = take(sizeof(int64_t) * 2 * n);
         L.xs = take(sizeof(double) * model_nx(model) * n);
         L.sx = take(sizeof(int64_t) * lattice_sx_elems(topo, N, R, lattice_wmode(topo, N, R, flags)));
-        L.sxy = take(topo == SIM_CUBE3D ? sizeof(int64_t) * 2 * n : 0);
+        L.sxy = take(topo == SIM_CUBE3D ? sizeof(int64_t) * lattice_sxy_elems(N) : 0);
         L.cpl = take(topo == SIM_CUBE3D ? sizeof(double) * n : 0);
         L.partial = take(sizeof(i128) * 2 * nblk);
         L.chords = take(topo == SIM_CUBE3D ? 0 : sizeof(int4) * (2 * R + 1) * (2 * R + 1));
