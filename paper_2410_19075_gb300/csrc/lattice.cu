@@ -36,6 +36,19 @@ constexpr int64_t kColTarget = 152 * 1024; // cube y and z passes: columns are s
 constexpr int kGatherThreads = 256;   // ball/disk gather: one node per thread
 constexpr size_t kRowSmemMax = 220 * 1024;
 
+// i-columns per tile: shared memory 2 (N1 + 1) BI 8 bytes stays below ~76 KB
+// (two or three CTAs per SM) and every row segment of a load is BI * 8 bytes.
+__host__ __device__ inline int cube_tile_lg(int64_t N1) { return N1 <= 297 ? 4 : N1 <= 594 ? 3 : 2; }
+__host__ __device__ inline int cube_tile_bi(int64_t N1) { return 1 << cube_tile_lg(N1); }
+
+// Component stride of the tiled cube's xy-window sums in their i-block-major
+// layout [i-block][j][k][ii]: every i-block padded to BI columns.
+__host__ __device__ inline int64_t cube_sxy_cstride(int64_t N1)
+{
+    const int BI = cube_tile_bi(N1);
+    return ((N1 + BI - 1) / BI) * BI * N1 * N1;
+}
+
 static int row_warps(int64_t N1)
 {
     const size_t per_warp = 2 * (size_t)(N1 + 1) * sizeof(int64_t);
@@ -76,7 +89,10 @@ __device__ __forceinline__ void lattice_rotated_q(const LatticePlan &p, int64_t 
 //                        S_w(i) = Pe(i+w+1) - Pe(i-w), (sin, cos) pairs, one
 //                        array of nodes pairs per w.
 // One row of the x pass (one warp; pre0/pre1 its shared prefix rows).
-template <int MODE>
+// IBLK (cube, the tiled passes): SX in the plane-wise i-block-major layout
+// [k][i-block][j][ii] (cube_sx_index), which each y tile reads as one
+// contiguous block; otherwise node order (the batched sliding passes).
+template <int MODE, bool IBLK = false>
 __device__ __forceinline__ void lattice_x_row(const LatticePlan &p, int64_t row, int64_t *pre0, int64_t *pre1,
                                               bool &ok)
 {
@@ -164,16 +180,41 @@ __device__ __forceinline__ void lattice_x_row(const LatticePlan &p, int64_t row,
             o[e] = make_longlong2((long long)v0, (long long)v1);
         }
     } else {
-        int64_t *__restrict__ o0 = p.sx + row * N1;
-        int64_t *__restrict__ o1 = p.sx + nodes + row * N1;
         const int64_t t0 = pre0[N1], t1 = pre1[N1];
-        for (int64_t i = lane; i < N1; i += 32) {
-            int64_t b = i + P + 1, a = i - P;
-            int64_t s0 = 0, s1 = 0;
-            if (b > N1) { b -= N1; s0 += t0; s1 += t1; }
-            if (a < 0) { a += N1; s0 += t0; s1 += t1; } // Pe(a) = pre(a+N1) - total
-            o0[i] = s0 + pre0[b] - pre0[a];
-            o1[i] = s1 + pre1[b] - pre1[a];
+        if (IBLK) {
+            // row = k N1 + j; element i at ((k tiles + i / BI) N1 + j) BI + i % BI
+            const int lg = cube_tile_lg(N1), BI = 1 << lg;
+            const int64_t k = row / N1, j = row - k * N1, tiles = (N1 + BI - 1) >> lg;
+            int64_t *__restrict__ o0 = p.sx + (k * tiles * N1 + j) * BI;
+            int64_t *__restrict__ o1 = o0 + cube_sxy_cstride(N1);
+            const int64_t bstep = N1 * BI; // one i-block further
+            for (int64_t i = lane; i < N1; i += 32) {
+                int64_t b = i + P + 1, a = i - P;
+                int64_t s0 = 0, s1 = 0;
+                if (b > N1) { b -= N1; s0 += t0; s1 += t1; }
+                if (a < 0) { a += N1; s0 += t0; s1 += t1; } // Pe(a) = pre(a+N1) - total
+                const int64_t o = (i >> lg) * bstep + (i & (BI - 1));
+                o0[o] = s0 + pre0[b] - pre0[a];
+                o1[o] = s1 + pre1[b] - pre1[a];
+            }
+            // the last i-block's columns past the cube's edge read as zeros
+            const int64_t pad = tiles * BI - N1;
+            if (lane < pad) {
+                const int64_t o = (tiles - 1) * bstep + (BI - pad + lane);
+                o0[o] = 0;
+                o1[o] = 0;
+            }
+        } else {
+            int64_t *__restrict__ o0 = p.sx + row * N1;
+            int64_t *__restrict__ o1 = p.sx + nodes + row * N1;
+            for (int64_t i = lane; i < N1; i += 32) {
+                int64_t b = i + P + 1, a = i - P;
+                int64_t s0 = 0, s1 = 0;
+                if (b > N1) { b -= N1; s0 += t0; s1 += t1; }
+                if (a < 0) { a += N1; s0 += t0; s1 += t1; } // Pe(a) = pre(a+N1) - total
+                o0[i] = s0 + pre0[b] - pre0[a];
+                o1[i] = s1 + pre1[b] - pre1[a];
+            }
         }
     }
     __syncwarp();
@@ -190,7 +231,7 @@ __global__ void __launch_bounds__(32 * kRowWarpsMax) lattice_x_kernel(LatticePla
     int64_t *pre1 = pre0 + stride;
     bool ok = true;
     for (int64_t row = (int64_t)blockIdx.x * nwarps + warp; row < rows; row += (int64_t)gridDim.x * nwarps)
-        lattice_x_row<MODE>(p, row, pre0, pre1, ok);
+        lattice_x_row<MODE, MODE == 0>(p, row, pre0, pre1, ok);
     if (!ok) raise_error(p.err, ERR_RANGE);
 }
 
@@ -572,19 +613,6 @@ __device__ __forceinline__ void cp_async16(uint64_t *dst, const uint64_t *src)
 
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-// i-columns per tile: shared memory 2 (N1 + 1) BI 8 bytes stays below ~76 KB
-// (two or three CTAs per SM) and every row segment of a load is BI * 8 bytes.
-__host__ __device__ inline int cube_tile_lg(int64_t N1) { return N1 <= 297 ? 4 : N1 <= 594 ? 3 : 2; }
-__host__ __device__ inline int cube_tile_bi(int64_t N1) { return 1 << cube_tile_lg(N1); }
-
-// Component stride of the tiled cube's xy-window sums in their i-block-major
-// layout [i-block][j][k][ii]: every i-block padded to BI columns.
-__host__ __device__ inline int64_t cube_sxy_cstride(int64_t N1)
-{
-    const int BI = cube_tile_bi(N1);
-    return ((N1 + BI - 1) / BI) * BI * N1 * N1;
-}
-
 __host__ __device__ inline size_t cube_tile_smem(int64_t N1)
 {
     return (size_t)2 * (size_t)(N1 + 1) * (size_t)cube_tile_bi(N1) * sizeof(int64_t);
@@ -690,8 +718,9 @@ __global__ void __launch_bounds__(kTileThreads) cube_y_tile_kernel(LatticePlan p
     const int N1 = (int)p.N1, P = (int)p.P, lg = cube_tile_lg(N1), BI = 1 << lg;
     const int i0 = (int)blockIdx.x << lg, k = blockIdx.y;
     const int bi = min(BI, N1 - i0);
-    const int64_t base = (int64_t)k * N1 * N1 + i0;
-    cube_tile_load_scan<kTileThreads>(p.sx, p.nodes, base, (unsigned)N1, N1, lg, bi, tile);
+    const int64_t tiles = (N1 + BI - 1) >> lg;
+    const int64_t *blk = p.sx + ((int64_t)k * tiles + blockIdx.x) * N1 * BI; // plane-wise i-block-major
+    cube_tile_load_scan_contig<kTileThreads>(blk, blk + cube_sxy_cstride(N1), N1, lg, tile);
     const int ii = threadIdx.x & (BI - 1), r0 = threadIdx.x >> lg, rstep = kTileThreads >> lg;
     const unsigned cstride = (unsigned)(N1 + 1) << lg;
     const uint64_t *col0 = tile + ii, *col1 = tile + cstride + ii;
@@ -905,7 +934,7 @@ static unsigned gather_grid(const LatticePlan &p)
 
 int64_t lattice_sx_elems(int topo, int64_t N1, int64_t P, bool wmode)
 {
-    if (topo == 1) return 2 * N1 * N1 * N1;
+    if (topo == 1) return lattice_sxy_elems(N1); // both layouts of the x pass's output
     const int64_t rows = topo == 3 ? N1 : N1 * N1;
     return wmode ? 2 * (P + 1) * rows * N1 : 2 * rows * (N1 + 2 * P + 1);
 }
