@@ -78,7 +78,12 @@ LATTICE_BYTES = {0: 408, 3: 544}
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # current kernels from ncu captures, keyed by (topology, model, N, radius,
 # kernel kind); the captures and any scaling are described with the profiles.
-MEASURED_TRAFFIC = {}
+MEASURED_TRAFFIC = {
+    # the cube's node pass at 464^3, P = 92: 43.97 B per node averaged over the
+    # four stages, measured by ncu at N1 = 300 (the full size is too large to
+    # capture), times the 99,897,344 nodes
+    (1, 0, 464, 92, "node_pass"): 43.97 * 464 ** 3,
+}
 
 
 def parse():

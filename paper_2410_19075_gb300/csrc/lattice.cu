@@ -531,9 +531,8 @@ __device__ __forceinline__ void lattice_node(const LatticePlan &p, int64_t n, in
     lattice_node_finish<M, STAGE, i128>(p, n, W0, W1, in, h, ok, ps, pc);
 }
 
-// cube z pass: one thread per segment of an (i, j) column, sliding window along
-// k, fused with the node update.  Also the prologue of the cube (STAGE 0, no
-// window).
+// Batched cube z pass: one thread per segment of an (i, j) column, sliding
+// window along k, fused with the node update.
 template <int M, int STAGE>
 __device__ __forceinline__ void cube_z_col(const LatticePlan &p, const StepSize &h, int64_t bx, int64_t j,
                                            int64_t seg, unsigned bid, unsigned nblk)
@@ -571,15 +570,6 @@ __device__ __forceinline__ void cube_z_col(const LatticePlan &p, const StepSize 
     }
     if (!ok) raise_error(p.err, ERR_RANGE);
     if (STAGE == 0 || STAGE == 4) lattice_record_order(p, ps, pc, bid, nblk, p.done_ctr);
-}
-
-template <int M, int STAGE>
-__global__ void __launch_bounds__(kColThreads) cube_z_kernel(LatticePlan p, const StepSize h)
-{
-    if (STAGE == 1 && p.skip && *(const volatile int *)p.skip) return; // stage 1 records nothing
-    cube_z_col<M, STAGE>(p, h, blockIdx.x, blockIdx.y, blockIdx.z,
-                         (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x,
-                         gridDim.x * gridDim.y * gridDim.z);
 }
 
 // ---------------------------------------------------------------------------
@@ -749,7 +739,8 @@ __global__ void __launch_bounds__(kTileThreads) cube_y_tile_kernel(LatticePlan p
 //                BI, ..., the own (sin, cos) of the next two in flight;
 //   node pass    elementwise over the nodes (contiguous, grid-stride): the
 //                slope from cpl, the RK4 update, the next (sin, cos), and in
-//                stage 4 the order parameter.
+//                stage 4 the order parameter.  STAGE 0 is the prologue: the
+//                (sin, cos) of y and its order parameter.
 // The window pass keeps the tile's 64-byte row segments (the z columns are
 // N1^2 elements apart), the node pass reads and writes whole warps of
 // consecutive nodes.  Three window CTAs per SM at the tile sizes of N1 <= 594.
@@ -808,8 +799,8 @@ __device__ __forceinline__ void cube_node_load(const LatticePlan &p, int64_t n, 
         in.acc[v] = STAGE >= 2 ? p.acc[v * nodes + n] : 0.0;
     }
 #pragma unroll
-    for (int g = 0; g < NX; ++g) in.X[g] = STAGE == 1 ? in.y[XOFF + g] : p.xs[g * nodes + n];
-    c = p.cpl[n];
+    for (int g = 0; g < NX; ++g) in.X[g] = STAGE <= 1 ? in.y[XOFF + g] : p.xs[g * nodes + n];
+    c = STAGE > 0 ? p.cpl[n] : 0.0;
 }
 
 template <int M, int STAGE>
@@ -836,7 +827,7 @@ __global__ void __launch_bounds__(kNodeThreads) cube_node_kernel(LatticePlan p, 
         }
     }
     if (!ok) raise_error(p.err, ERR_RANGE);
-    if (STAGE == 4) lattice_record_order(p, ps, pc, blockIdx.x, gridDim.x, p.tile_ctr);
+    if (STAGE == 0 || STAGE == 4) lattice_record_order(p, ps, pc, blockIdx.x, gridDim.x, p.tile_ctr);
 }
 
 // Batched cube z pass (stages 1-4): CTA b is CTA b - yz_base[m] of member m.
@@ -902,11 +893,6 @@ __global__ void __launch_bounds__(kGatherThreads) lattice_gather_kernel(LatticeP
 }
 
 // ---------------------------------------------------------------------------
-static dim3 col_grid(int64_t N1)
-{
-    return dim3((unsigned)((N1 + kColThreads - 1) / kColThreads), (unsigned)N1, (unsigned)col_segments(N1));
-}
-
 static dim3 tile_grid(int64_t N1)
 {
     const int BI = cube_tile_bi(N1);
@@ -923,7 +909,7 @@ static int64_t g_node_grid[2][2] = {{152 * 3, 152 * 3}, {152 * 3, 152 * 3}};
 static int64_t cube_node_grid(int model, int stage, int64_t nodes)
 {
     const int64_t want = (nodes + kNodeThreads - 1) / kNodeThreads;
-    const int64_t cap = g_node_grid[model == 3 ? 1 : 0][stage == 4 ? 1 : 0];
+    const int64_t cap = g_node_grid[model == 3 ? 1 : 0][stage == 4 || stage == 0 ? 1 : 0]; // the recording grid
     return want < cap ? want : cap;
 }
 
@@ -1058,7 +1044,8 @@ static cudaError_t launch_stage(int stage, const LatticePlan &p, double dt, cuda
 {
     if (stage == 0) {
         // prologue: (sin, cos) of y and its order parameter, no window
-        return p.topo == 1 ? (cube_z_kernel<M, 0><<<col_grid(p.N1), kColThreads, 0, s>>>(p, step_size(0.0)),
+        return p.topo == 1 ? (cube_node_kernel<M, 0><<<(unsigned)cube_node_grid(M, 0, p.nodes), kNodeThreads, 0, s>>>(
+                                  p, step_size(0.0)),
                               cudaGetLastError())
                            : (lattice_gather_kernel<M, 0, false><<<gather_grid(p), kGatherThreads, 0, s>>>(
                                   p, step_size(0.0)),
