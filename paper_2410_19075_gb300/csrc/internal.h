@@ -255,6 +255,7 @@ struct CubeBatchGroup {
 cudaError_t cube_batch_step(const CubeBatchGroup &g, double dt, cudaStream_t s); // one RK4 step of every member
 int lattice_row_warps(int64_t N1); // warps per CTA of the x pass for edge N1
 void lattice_rotation(LatticePlan &p, double alpha); // rot_* and mp.c[5] of a lattice (sim_api.cu)
+void ring_coupling_constants(ModelParams &mp, int model, int F); // ksh and c[5] of a Kuramoto ring (sim_api.cu)
 
 // Per-kernel timing of sim_step_timed: while set on the launching host thread,
 // every stage-kernel launch of ring_step, graph_step, lattice_step and

@@ -23,28 +23,15 @@ namespace simk {
 struct ModelParams {
     double c[8];
     int64_t q[2];     // Kuramoto models: cos alpha and sin alpha on the grid 2^-62
+    uint64_t a0[2];   // Kuramoto models: alpha = aq pi/2 + alpha0, alpha0 in [0, pi/2):
+    int aq;           //   cos alpha0, sin alpha0 on the grid 2^-63 (non-negative), aq in 0..3
+    int ksh;          // Kuramoto rings: right shift taking the exact window sums into int64
     MathTables tab;   // device tables of the fast elementary functions
     int64_t wsize;    // window size including the node itself (2R+1 or (2P+1)^3)
     int include_self; // 1: the node is one of its own links
 };
 
 template <int M> struct Model;
-
-// sin(phi + alpha) and cos(phi + alpha) of a Kuramoto node from its own sin phi,
-// cos phi, by the angle-addition formula in 64-bit integer arithmetic (no FP64
-// instruction): the own values on the grid 2^-62 (f62, where the caller has
-// them; else its window-sum grid values qo shifted up from 2^-F), times cos alpha
-// and sin alpha on the grid 2^-62, summed on the grid 2^-60 and converted once
-// (correctly rounded) to double.  Absolute error below 2^-58.
-__device__ __forceinline__ void angle_add(const ModelParams &P, const int64_t (&qo)[2], int F, const int64_t *f62,
-                                          double &sxa, double &cxa)
-{
-    const int64_t s = f62 ? f62[0] : qo[0] * (int64_t(1) << (62 - F));
-    const int64_t c = f62 ? f62[1] : qo[1] * (int64_t(1) << (62 - F));
-    const int64_t ca = P.q[0], sa = P.q[1];
-    sxa = fixed_to_double((int64_t)(__mul64hi(s, ca) + __mul64hi(c, sa)), 60);
-    cxa = fixed_to_double((int64_t)(__mul64hi(c, ca) - __mul64hi(s, sa)), 60);
-}
 
 // Kuramoto coupling on a lattice.  The window sums arrive rotated by -alpha:
 // W' = W'c + i W's = sum over the window (the node itself included) of
@@ -71,6 +58,46 @@ __device__ __forceinline__ double lattice_coupling_term(const ModelParams &P, co
     return fma(P.c[5], lattice_coupling(f62, W0, W1), P.c[4]);
 }
 
+// Kuramoto coupling on a ring or a link matrix: T = Im[e^{-i(phi+alpha)} S] =
+// cos(phi+alpha) S_sin - sin(phi+alpha) S_cos, with S the exact window sum
+// (int128 on the grid 2^-F; without the node itself unless it is one of its own
+// links) shifted right by sh bits into int64, and (cos, sin)(phi + alpha) from
+// the node's own grid values by the angle-addition formula: four high products
+// with the non-negative cos alpha0, sin alpha0 (grid 2^-61), then aq quarter
+// turns.  Two signed high products give T on the grid 2^-(F - sh - 3).  No FP64
+// instruction and no conversion until the caller's single one.
+__device__ __forceinline__ int64_t ring_coupling(const ModelParams &P, const int64_t (&qo)[2], int F,
+                                                 const i128 (&W)[2], int sh)
+{
+    const i128 ss = P.include_self ? W[0] : W[0] - (i128)qo[0];
+    const i128 sc = P.include_self ? W[1] : W[1] - (i128)qo[1];
+    const int64_t S_s = (int64_t)(ss >> sh), S_c = (int64_t)(sc >> sh);
+    const int64_t s = qo[0] * (int64_t(1) << (62 - F)), c = qo[1] * (int64_t(1) << (62 - F));
+    const int64_t c1 = mulhi_su(c, P.a0[0]) - mulhi_su(s, P.a0[1]); // e^{i alpha0} (c + i s), grid 2^-61
+    const int64_t s1 = mulhi_su(s, P.a0[0]) + mulhi_su(c, P.a0[1]);
+    int64_t ca, sa;
+    switch (P.aq) { // times i^aq
+    case 0: ca = c1; sa = s1; break;
+    case 1: ca = -s1; sa = c1; break;
+    case 2: ca = -c1; sa = -s1; break;
+    default: ca = s1; sa = -c1; break;
+    }
+    return mulhi_ss(ca, S_s) - mulhi_ss(sa, S_c);
+}
+
+// The shift and the scale of ring_coupling's T for a window of ws links (the
+// node itself included or not): sh = max(0, ceil(log2 ws) + F - 61) keeps
+// |S >> sh| < 2^62; the returned scale is coef 2^(sh + 3 - F), with coef the
+// coupling constant (times the link-matrix node's 1/K_i).
+__device__ __forceinline__ double ring_coupling_scale(int64_t ws, int F, double coef, int &sh)
+{
+    const int lg = ws > 1 ? 64 - __clzll((long long)(ws - 1)) : 0;
+    sh = lg + F - 61 > 0 ? lg + F - 61 : 0;
+    // coef 2^(sh + 3 - F) by the exponent field (coef is a normal double, the
+    // power of two keeps it one)
+    return __longlong_as_double(__double_as_longlong(coef) + ((long long)(sh + 3 - F) << 52));
+}
+
 // Kuramoto-Sakaguchi, Eq. (3) with m = 0, eps = 1 (Algorithm 1):
 //   dphi_i/dt = omega - (mu/K) sum_{j in W(i)} sin(phi_i - phi_j + alpha)
 //             = omega + (mu/K) [cos(phi_i+alpha) S_sin - sin(phi_i+alpha) S_cos],
@@ -88,17 +115,16 @@ template <> struct Model<0> {
         q[0] = q62_to(s62, F);
         q[1] = q62_to(c62, F);
     }
-    __device__ __forceinline__ static void rhs(const ModelParams &P, int F_, const double (&fo)[NQ],
+    // Rings and link matrices: c[5] = (mu/K) 2^(ksh + 3 - F) (rings; a link
+    // matrix's node of wsize links scales mu cs instead).
+    __device__ __forceinline__ static void rhs(const ModelParams &P, int F_, const double (&)[NQ],
                                                const int64_t (&qo)[NQ], const i128 (&W)[NQ],
-                                               const double *X, double Iext, double (&k)[D],
-                                               int64_t = 0, double cs = 1.0, const int64_t *f62 = nullptr)
+                                               const double *, double, double (&k)[D],
+                                               int64_t wsize = -1, double cs = 1.0, const int64_t * = nullptr)
     {
-        const i128 ss = P.include_self ? W[0] : W[0] - (i128)qo[0];
-        const i128 sc = P.include_self ? W[1] : W[1] - (i128)qo[1];
-        const double Ss = cs * fixed_to_double_wide(ss, F_), Sc = cs * fixed_to_double_wide(sc, F_);
-        double sxa, cxa;
-        angle_add(P, qo, F_, f62, sxa, cxa);
-        k[0] = P.c[0] + P.c[1] * (cxa * Ss - sxa * Sc);
+        int sh = P.ksh;
+        const double sc = wsize < 0 ? P.c[5] : ring_coupling_scale(wsize, F_, P.c[1] * cs, sh);
+        k[0] = fma(sc, __ll2double_rn(ring_coupling(P, qo, F_, W, sh)), P.c[0]);
     }
     // Lattices: c[4] = omega + (mu/K) sin alpha (omega with the node itself as a
     // link), c[5] = (mu/K) 2^-(F-2).
@@ -201,19 +227,17 @@ template <> struct Model<3> {
         q[0] = q62_to(s62, F);
         q[1] = q62_to(c62, F);
     }
-    __device__ __forceinline__ static void rhs(const ModelParams &P, int F_, const double (&fo)[NQ],
+    // Rings and link matrices: c[5] = (mu/(m K)) 2^(ksh + 3 - F).
+    __device__ __forceinline__ static void rhs(const ModelParams &P, int F_, const double (&)[NQ],
                                                const int64_t (&qo)[NQ], const i128 (&W)[NQ],
-                                               const double *X, double Iext, double (&k)[D],
-                                               int64_t = 0, double cs = 1.0, const int64_t *f62 = nullptr)
+                                               const double *X, double, double (&k)[D],
+                                               int64_t wsize = -1, double cs = 1.0, const int64_t * = nullptr)
     {
-        const i128 ss = P.include_self ? W[0] : W[0] - (i128)qo[0];
-        const i128 sc = P.include_self ? W[1] : W[1] - (i128)qo[1];
-        const double Ss = cs * fixed_to_double_wide(ss, F_), Sc = cs * fixed_to_double_wide(sc, F_);
+        int sh = P.ksh;
+        const double sc = wsize < 0 ? P.c[5] : ring_coupling_scale(wsize, F_, P.c[0] * cs, sh);
         const double psi = X[0];
-        double sxa, cxa;
-        angle_add(P, qo, F_, f62, sxa, cxa);
         k[0] = psi;
-        k[1] = fma(P.c[0], cxa * Ss - sxa * Sc, -P.c[1] * psi);
+        k[1] = fma(sc, __ll2double_rn(ring_coupling(P, qo, F_, W, sh)), -P.c[1] * psi);
     }
     // Lattices: c[4] = (mu/(m K)) sin alpha (0 with the node itself as a link),
     // c[5] = (mu/(m K)) 2^-(F-2).  The coupling term first, then the damping

@@ -165,6 +165,7 @@ extern "C" int sim_ring_step_noalloc(int model, int64_t N, int64_t radius, const
     p.F = model == SIM_KS ? Model<0>::F : model == SIM_FHN ? Model<1>::F : Model<2>::F;
     p.lim = 54 - p.F;
     p.mp = mp;
+    if (model == SIM_KS) ring_coupling_constants(p.mp, model, p.F);
     p.y = dev_state;
     p.acc = reinterpret_cast<double *>(b + L.acc);
     p.xg[0] = reinterpret_cast<double *>(b + L.xg0);

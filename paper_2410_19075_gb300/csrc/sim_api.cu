@@ -383,6 +383,17 @@ void simk::model_constants(int model, const double *params, double K, ModelParam
         mp.c[3] = std::cos(alpha);
         mp.q[0] = (int64_t)std::llround(std::ldexp(mp.c[3], 62)); // exact: |cos| <= 1, 53-bit significand
         mp.q[1] = (int64_t)std::llround(std::ldexp(mp.c[2], 62));
+        // alpha = aq pi/2 + alpha0 with alpha0 in [0, pi/2): the angle addition of
+        // the ring and link-matrix right-hand side (ring_coupling)
+        {
+            const long double half_pi = 1.570796326794896619231321691639751442L;
+            const long double a = (long double)alpha, q = floorl(a / half_pi), a0 = a - q * half_pi;
+            const long double two63 = 9223372036854775808.0L;
+            mp.a0[0] = (uint64_t)roundl(fminl(fmaxl(cosl(a0), 0.0L), 1.0L) * two63);
+            mp.a0[1] = (uint64_t)roundl(fminl(fmaxl(sinl(a0), 0.0L), 1.0L) * two63);
+            const long long qi = (long long)q % 4;
+            mp.aq = (int)(qi < 0 ? qi + 4 : qi);
+        }
         // lattices: the constant of the right-hand side with the node's own term
         // (-sin alpha in the rotated window sum) taken out
         if (model == SIM_KS) mp.c[4] = mp.include_self ? mp.c[0] : mp.c[0] + mp.c[1] * mp.c[2];
@@ -400,6 +411,15 @@ void simk::model_constants(int model, const double *params, double K, ModelParam
         for (int i = 1; i < 7; ++i) mp.c[i] = params[i];
         mp.c[7] = params[7] / K;
     }
+}
+
+// A Kuramoto ring's shift of its exact window sums into int64 and the scale of
+// the cross product T on the grid 2^-(F - ksh - 3) (see ring_coupling).
+void simk::ring_coupling_constants(ModelParams &mp, int model, int F)
+{
+    const int lg = ceil_log2((uint64_t)mp.wsize);
+    mp.ksh = lg + F - 61 > 0 ? lg + F - 61 : 0;
+    mp.c[5] = std::ldexp(model == SIM_KS ? mp.c[1] : mp.c[0], mp.ksh + 3 - F);
 }
 
 // A lattice's rotation of the window sums by -alpha and the scale of the
@@ -517,6 +537,7 @@ static int create_impl(sim_t *out, int model, int topology, int64_t N, int64_t r
         p.F = ring_F(model);
         p.lim = 54 - p.F;
         p.mp = mp;
+        if (model == SIM_KS || model == SIM_KSI) ring_coupling_constants(p.mp, model, p.F);
         p.y = reinterpret_cast<double *>(b + L.y);
         p.acc = reinterpret_cast<double *>(b + L.acc);
         p.xg[0] = reinterpret_cast<double *>(b + L.xg0);
