@@ -55,15 +55,15 @@ RING_BYTES = {0: 344, 1: 432, 2: 704, 3: 480}
 # Sine and cosine run in integer arithmetic (no FP64); the Hodgkin-Huxley rates
 # use the table-driven exp (8 FMA + 1 MUL = 17 flops) and reciprocal.
 RING_FLOPS = {0: 4 * 5 + 13, 1: 4 * 15 + 2 * 13, 2: 4 * (6 * 17 + 40) + 3 * 16 + 12, 3: 4 * 6 + 2 * 13}
-# Cube (Kuramoto), bytes per node of each pass (launch): x pass reads (sin, cos)
-# on the 2^-62 grid and writes the x-window sums (16 + 16); y pass reads those
-# and writes the xy-window sums (16 + 16); z-window pass reads the xy sums (16)
-# and the node's own (sin, cos) (16) and writes the coupling term (8); node
-# pass reads the coupling term (8), y (8) and acc (8, stages 2-4), writes acc
-# (8, stages 1-3) or y (8, stage 4) and the next (sin, cos) (16): 40 B in stage
-# 1, 48 B in stages 2-4.
-CUBE_PASS_BYTES = {0: 32.0, 1: 32.0, 3: 40.0, 2: (40.0 + 3 * 48.0) / 4}
-CUBE_BYTES = 4 * (32 + 32 + 40) + 40 + 3 * 48  # 600 per node-step
+# Cube (Kuramoto), bytes per node of each pass (launch): y pass reads the x
+# sums and writes the xy sums (16 + 16); z-window pass reads the xy sums (16) and
+# the node's own (sin, cos) (16) and writes the coupling term (8); the node pass,
+# fused with the next stage's x pass, reads the coupling term (8), y (8) and acc
+# (8, stages 2-4), writes acc (8, stages 1-3) or y (8, stage 4), the next (sin,
+# cos) (16) and its x sums (16): 56 B in stage 1, 64 B in stages 2-4.  (A plain
+# x pass, 16 + 16 B, runs only before a right-hand-side evaluation.)
+CUBE_PASS_BYTES = {0: 32.0, 1: 32.0, 3: 40.0, 2: (56.0 + 3 * 64.0) / 4}
+CUBE_BYTES = 4 * (32 + 40) + 56 + 3 * 64  # 536 per node-step
 CUBE_BYTES_SURVEY = 432  # the survey's model of the same three passes (24 + 32 + 56 per stage)
 # FP64 flops per node and launch: the z-window pass's FMA on the converted cross
 # product, the node pass's RK4 update (13 per node-step).
@@ -79,10 +79,11 @@ LATTICE_BYTES = {0: 408, 3: 544}
 # current kernels from ncu captures, keyed by (topology, model, N, radius,
 # kernel kind); the captures and any scaling are described with the profiles.
 MEASURED_TRAFFIC = {
-    # the cube's node pass at 464^3, P = 92: 43.97 B per node averaged over the
-    # four stages, measured by ncu at N1 = 300 (the full size is too large to
-    # capture), times the 99,897,344 nodes
-    (1, 0, 464, 92, "node_pass"): 43.97 * 464 ** 3,
+    # the cube's node pass (fused with the next x pass) at 464^3, P = 92: 60.1 B
+    # per node averaged over the four stages (54.1, 62.1, 62.1, 62.2), measured by
+    # ncu at N1 = 300 (the full size is too large to capture), times the
+    # 99,897,344 nodes
+    (1, 0, 464, 92, "node_pass"): 60.1 * 464 ** 3,
 }
 
 
@@ -452,9 +453,14 @@ def ring_kind_flops(model):
     return {"stage_or_x": RING_FLOPS[model] / 4}
 
 
-CUBE_KIND_BYTES = {"stage_or_x": CUBE_PASS_BYTES[0], "cube_y": CUBE_PASS_BYTES[1], "cube_z": CUBE_PASS_BYTES[3],
-                   "node_pass": CUBE_PASS_BYTES[2]}
-CUBE_KIND_FLOPS = {"stage_or_x": 0.0, "cube_y": 0.0, "cube_z": CUBE_PASS_FLOPS[3], "node_pass": CUBE_PASS_FLOPS[2]}
+CUBE_KIND_BYTES = {"cube_y": CUBE_PASS_BYTES[1], "cube_z": CUBE_PASS_BYTES[3], "node_pass": CUBE_PASS_BYTES[2]}
+CUBE_KIND_FLOPS = {"cube_y": 0.0, "cube_z": CUBE_PASS_FLOPS[3], "node_pass": CUBE_PASS_FLOPS[2]}
+
+
+def cube_kinds(kinds):
+    """A cube's RK4 steps run no plain x pass: their kernels of kind 0 are the
+    order-parameter totals (one small launch per step, no per-node bytes)."""
+    return {("order_total" if k == "stage_or_x" else k): v for k, v in kinds.items()}
 
 
 def network_leg(model, topo, N, R, params, steps, chunk, dt, flush, stream, peaks, seed=2419, tune=True,
@@ -482,6 +488,7 @@ def network_leg(model, topo, N, R, params, steps, chunk, dt, flush, stream, peak
         kb, kf = ring_kind_bytes(model), ring_kind_flops(model)
     elif topo == 1:
         kb, kf = CUBE_KIND_BYTES, CUBE_KIND_FLOPS
+        kinds = cube_kinds(kinds)
     else:
         kb, kf = {}, {}
     out = {"workload": workload_name(model, topo, N, R, dt), "steps": steps,
@@ -1001,6 +1008,7 @@ def run_native(args):
         kb, kf = ring_kind_bytes(args.model), ring_kind_flops(args.model)
     elif args.topo == 1:
         kb, kf = CUBE_KIND_BYTES, CUBE_KIND_FLOPS
+        kinds = cube_kinds(kinds)
     else:
         per = LATTICE_BYTES[args.model] / 4
         kb, kf = {"stage_or_x": 32.0, "node_pass": per - 32.0}, {"stage_or_x": 0.0, "node_pass": RING_FLOPS[3] / 4}

@@ -171,10 +171,11 @@ int sim_step(sim_t h, int64_t n_steps, double dt);
  * ms_by_kind[k] receives the summed time between consecutive events that ended
  * with a kernel of kind k, launches_by_kind[k] their number (4 entries each):
  * kind 0 = the fused stage kernel of a ring or link matrix (one per stage; the
- * whole call for the cluster-resident small-ring kernel) or the x pass of a
- * lattice, 1 = the y pass of the cube, 2 = the node pass of a lattice (the
- * elementwise RK4 pass of the cube, the chord gather of the ball and disk), 3 =
- * the z-window pass of the cube.  The
+ * whole call for the cluster-resident small-ring kernel), the x pass of a ball
+ * or disk, or the cube's order-parameter total (once per step), 1 = the y pass
+ * of the cube, 2 = the node pass of a lattice (the cube's elementwise RK4 pass
+ * fused with the next stage's x pass, the chord gather of the ball and disk),
+ * 3 = the z-window pass of the cube.  The
  * state advances exactly as with sim_step (the same bits).  Returns the device
  * error status like sim_sync.  Errors: SIM_EINVAL (NULL handle or output,
  * n_steps out of range, invalid dt), SIM_EDEVICE. */
@@ -422,7 +423,9 @@ void srv_destroy(srv_t s);
  * model parameters are as for sim_create with topology SIM_RING.
  * The work is issued on `stream` (a cudaStream_t, NULL = legacy default) and the
  * call synchronises that stream before it returns, so that it can report
- * SIM_ENONFINITE.  It calls no cudaMalloc, cudaFree or other allocator.
+ * SIM_ENONFINITE; it therefore cannot be captured into a CUDA graph, and a call
+ * on a capturing stream returns SIM_EINVAL without touching the stream.  It
+ * calls no cudaMalloc, cudaFree or other allocator.
  * The first call on each device does a one-time set-up with that device
  * current (it looks up the static array's device address and copies the
  * fast-math tables into it); make that first call before any stream capture.
@@ -432,8 +435,9 @@ void srv_destroy(srv_t s);
  * call clears the counters and the error word it needs at zero): calls whose
  * work overlaps on the GPU (other streams or host threads) race with each
  * other and must be serialised by the caller.
- * Errors: SIM_EINVAL (the same argument checks as sim_create, or N > 65536),
- * SIM_ENONFINITE, SIM_EDEVICE; sim_last_error() gives the reason. */
+ * Errors: SIM_EINVAL (the same argument checks as sim_create, N > 65536, or a
+ * capturing stream), SIM_ENONFINITE, SIM_ETIMEOUT, SIM_EDEVICE;
+ * sim_last_error() gives the reason. */
 int sim_ring_step_noalloc(int model, int64_t N, int64_t radius, const double *params, int n_params,
                           unsigned flags, double *dev_state, const double *dev_node_param, int64_t n_steps,
                           double dt, void *stream);

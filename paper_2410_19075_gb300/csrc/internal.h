@@ -260,9 +260,9 @@ void ring_coupling_constants(ModelParams &mp, int model, int F); // ksh and c[5]
 // Per-kernel timing of sim_step_timed: while set on the launching host thread,
 // every stage-kernel launch of ring_step, graph_step, lattice_step and
 // ring_cluster_steps records an event of its kind right after itself (kinds:
-// 0 fused ring / link-matrix stage kernel or lattice x pass, 1 cube y pass,
-// 2 lattice node pass (cube node pass, ball / disk gather), 3 cube z-window
-// pass).  Never set during a stream capture.
+// 0 fused ring / link-matrix stage kernel, lattice x pass or the cube's
+// order-parameter total, 1 cube y pass, 2 lattice node pass (cube node pass
+// fused with the next x pass, ball / disk gather), 3 cube z-window pass).  Never set during a stream capture.
 struct KernelMarks {
     cudaEvent_t *ev;
     unsigned char *kind;

@@ -56,6 +56,16 @@ static int row_warps(int64_t N1)
     return w < 1 ? 1 : (w > kRowWarpsMax ? kRowWarpsMax : w);
 }
 
+// The cube's fused node pass: smaller CTAs than the x pass, so that the shared
+// prefix rows of a CTA round up to less of the SM (seven CTAs of four 464-node
+// rows, against three of eight).
+constexpr int kNodexWarpsMax = 4;
+static int nodex_warps(int64_t N1)
+{
+    const int w = row_warps(N1);
+    return w > kNodexWarpsMax ? kNodexWarpsMax : w;
+}
+
 // The coupled quantity a ball's or disk's window sums add up: the node's (sin,
 // cos) on the grid 2^-62 rotated by -alpha = -(rot_q pi/2 + alpha0),
 //   e^{-i alpha0} (c + i s) = (c cos a0 + s sin a0) + i (s cos a0 - c sin a0),
@@ -92,13 +102,13 @@ __device__ __forceinline__ void lattice_rotated_q(const LatticePlan &p, int64_t 
 // IBLK (cube, the tiled passes): SX in the plane-wise i-block-major layout
 // [k][i-block][j][ii] (cube_sx_index), which each y tile reads as one
 // contiguous block; otherwise node order (the batched sliding passes).
-template <int MODE, bool IBLK = false>
-__device__ __forceinline__ void lattice_x_row(const LatticePlan &p, int64_t row, int64_t *pre0, int64_t *pre1,
-                                              bool &ok)
+// The row's own part: pre0/pre1[m + 1] = Q'(f(m)) for m < N1 from the stored
+// (sin, cos).
+template <int MODE>
+__device__ __forceinline__ void lattice_x_fill(const LatticePlan &p, int64_t row, int64_t *pre0, int64_t *pre1)
 {
     const int lane = threadIdx.x & 31;
-    const int64_t N1 = p.N1, P = p.P, nodes = p.nodes;
-    const int per = (int)((N1 + 31) / 32);
+    const int64_t N1 = p.N1, nodes = p.nodes;
     const int64_t *__restrict__ fs = p.f + row * N1;
     const int64_t *__restrict__ fc = p.f + nodes + row * N1;
     for (int64_t mb = lane; mb < N1; mb += 32 * 8) { // coalesced, 8 loads in flight per lane
@@ -122,26 +132,31 @@ __device__ __forceinline__ void lattice_x_row(const LatticePlan &p, int64_t row,
             }
         }
     }
+}
+
+// The row's prefix and window sums from pre0/pre1[1..N1] (filled by the warp).
+template <int MODE, bool IBLK>
+__device__ __forceinline__ void lattice_x_scan_out(const LatticePlan &p, int64_t row, int64_t *pre0, int64_t *pre1)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t N1 = p.N1, P = p.P, nodes = p.nodes;
+    const int n1 = (int)N1, per = (n1 + 31) >> 5;
     __syncwarp();
-    const int m0 = lane * per;
+    // lane l owns the prefix slots m0 .. m1 - 1: its part's total, the warp's
+    // exclusive scan of the totals, then the part's prefix written once
+    const int m0 = min(lane * per, n1) + 1, m1 = min(m0 + per, n1 + 1);
     uint64_t r0 = 0, r1 = 0; // wrapping sums
-    for (int t = 0; t < per; ++t) {
-        const int m = m0 + t;
-        if (m < N1) {
-            r0 += (uint64_t)pre0[m + 1];
-            r1 += (uint64_t)pre1[m + 1];
-            pre0[m + 1] = (int64_t)r0;
-            pre1[m + 1] = (int64_t)r1;
-        }
+    for (int m = m0; m < m1; ++m) {
+        r0 += (uint64_t)pre0[m];
+        r1 += (uint64_t)pre1[m];
     }
-    const uint64_t e0 = (uint64_t)warp_incl_scan((int64_t)r0) - r0;
-    const uint64_t e1 = (uint64_t)warp_incl_scan((int64_t)r1) - r1;
-    for (int t = 0; t < per; ++t) {
-        const int m = m0 + t;
-        if (m < N1) {
-            pre0[m + 1] = (int64_t)((uint64_t)pre0[m + 1] + e0);
-            pre1[m + 1] = (int64_t)((uint64_t)pre1[m + 1] + e1);
-        }
+    uint64_t e0 = (uint64_t)warp_incl_scan((int64_t)r0) - r0;
+    uint64_t e1 = (uint64_t)warp_incl_scan((int64_t)r1) - r1;
+    for (int m = m0; m < m1; ++m) {
+        e0 += (uint64_t)pre0[m];
+        e1 += (uint64_t)pre1[m];
+        pre0[m] = (int64_t)e0;
+        pre1[m] = (int64_t)e1;
     }
     if (lane == 0) {
         pre0[0] = 0;
@@ -182,20 +197,25 @@ __device__ __forceinline__ void lattice_x_row(const LatticePlan &p, int64_t row,
     } else {
         const int64_t t0 = pre0[N1], t1 = pre1[N1];
         if (IBLK) {
-            // row = k N1 + j; element i at ((k tiles + i / BI) N1 + j) BI + i % BI
-            const int lg = cube_tile_lg(N1), BI = 1 << lg;
+            // row = k N1 + j; element i at ((k tiles + i / BI) N1 + j) BI + i % BI.
+            // BI divides 32, so lane's column within its i-block stays fixed and
+            // every 32 columns move 32 / BI i-blocks further.
+            const int lg = cube_tile_lg(N1), BI = 1 << lg, p1 = (int)P;
             const int64_t k = row / N1, j = row - k * N1, tiles = (N1 + BI - 1) >> lg;
+            const int64_t bstep = N1 * BI; // one i-block further
             int64_t *__restrict__ o0 = p.sx + (k * tiles * N1 + j) * BI;
             int64_t *__restrict__ o1 = o0 + cube_sxy_cstride(N1);
-            const int64_t bstep = N1 * BI; // one i-block further
-            for (int64_t i = lane; i < N1; i += 32) {
-                int64_t b = i + P + 1, a = i - P;
-                int64_t s0 = 0, s1 = 0;
-                if (b > N1) { b -= N1; s0 += t0; s1 += t1; }
-                if (a < 0) { a += N1; s0 += t0; s1 += t1; } // Pe(a) = pre(a+N1) - total
-                const int64_t o = (i >> lg) * bstep + (i & (BI - 1));
-                o0[o] = s0 + pre0[b] - pre0[a];
-                o1[o] = s1 + pre1[b] - pre1[a];
+            const unsigned ostep = (unsigned)bstep << (5 - lg);
+            unsigned o = (unsigned)((lane >> lg) * bstep) + (lane & (BI - 1));
+#pragma unroll 2
+            for (int i = lane; i < n1; i += 32, o += ostep) {
+                // 2P + 1 <= N1: at most one end of the window wraps, adding the total
+                const int b = i + p1 + 1, a = i - p1;
+                const bool hi = b > n1, lo = a < 0;
+                const int bb = hi ? b - n1 : b, aa = lo ? a + n1 : a;
+                const int64_t s0 = (hi || lo) ? t0 : 0, s1 = (hi || lo) ? t1 : 0;
+                o0[o] = s0 + pre0[bb] - pre0[aa];
+                o1[o] = s1 + pre1[bb] - pre1[aa];
             }
             // the last i-block's columns past the cube's edge read as zeros
             const int64_t pad = tiles * BI - N1;
@@ -218,6 +238,14 @@ __device__ __forceinline__ void lattice_x_row(const LatticePlan &p, int64_t row,
         }
     }
     __syncwarp();
+}
+
+template <int MODE, bool IBLK = false>
+__device__ __forceinline__ void lattice_x_row(const LatticePlan &p, int64_t row, int64_t *pre0, int64_t *pre1,
+                                              bool &)
+{
+    lattice_x_fill<MODE>(p, row, pre0, pre1);
+    lattice_x_scan_out<MODE, IBLK>(p, row, pre0, pre1);
 }
 
 template <int MODE>
@@ -250,7 +278,7 @@ __global__ void __launch_bounds__(32 * kRowWarpsMax)
     int64_t *pre1 = pre0 + stride;
     const int64_t row = ((int64_t)blockIdx.x - x_base[inst]) * nwarps + warp;
     bool ok = true;
-    if (row < rows) lattice_x_row<0>(p, row, pre0, pre1, ok); // uniform over the warp
+    if (row < rows) lattice_x_row<0, true>(p, row, pre0, pre1, ok); // uniform over the warp
     if (!ok) raise_error(p.err, ERR_RANGE);
 }
 
@@ -305,8 +333,12 @@ __device__ __forceinline__ void cube_y_col(const LatticePlan &p, int64_t i, int6
     const int64_t je = jb + len < N1 ? jb + len : N1;
     if (i >= N1 || jb >= N1) return;
     const int64_t col = k * N1 * N1 + i; // + j * N1
-    const int64_t *__restrict__ a0 = p.sx + col;
-    const int64_t *__restrict__ a1 = p.sx + nodes + col;
+    // the x sums in the plane-wise i-block-major layout: (i, j, k) at
+    // ((k tiles + i / BI) N1 + j) BI + i % BI, so consecutive j are BI apart
+    const int lg = cube_tile_lg(N1), BI = 1 << lg;
+    const int64_t tiles = (N1 + BI - 1) >> lg;
+    const int64_t *__restrict__ a0 = p.sx + ((k * tiles + (i >> lg)) * N1) * BI + (i & (BI - 1));
+    const int64_t *__restrict__ a1 = a0 + cube_sxy_cstride(N1);
     int64_t *__restrict__ o0 = p.sxy + col;
     int64_t *__restrict__ o1 = p.sxy + nodes + col;
     int64_t s0 = 0, s1 = 0;
@@ -314,8 +346,8 @@ __device__ __forceinline__ void cube_y_col(const LatticePlan &p, int64_t i, int6
         int64_t j = jb + d;
         j += j < 0 ? N1 : 0;
         j -= j >= N1 ? N1 : 0;
-        s0 += __ldg(a0 + j * N1);
-        s1 += __ldg(a1 + j * N1);
+        s0 += __ldg(a0 + j * BI);
+        s1 += __ldg(a1 + j * BI);
     }
     for (int64_t j0 = jb; j0 < je; j0 += U) {
         int64_t in0[U], out0[U], in1[U], out1[U];
@@ -326,10 +358,10 @@ __device__ __forceinline__ void cube_y_col(const LatticePlan &p, int64_t i, int6
             if (jin >= N1) jin -= N1;
             if (jout < 0) jout += N1;
             const bool live = j < je;
-            in0[u] = live ? __ldg(a0 + jin * N1) : 0;
-            out0[u] = live ? __ldg(a0 + jout * N1) : 0;
-            in1[u] = live ? __ldg(a1 + jin * N1) : 0;
-            out1[u] = live ? __ldg(a1 + jout * N1) : 0;
+            in0[u] = live ? __ldg(a0 + jin * BI) : 0;
+            out0[u] = live ? __ldg(a0 + jout * BI) : 0;
+            in1[u] = live ? __ldg(a1 + jin * BI) : 0;
+            out1[u] = live ? __ldg(a1 + jout * BI) : 0;
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -344,12 +376,6 @@ __device__ __forceinline__ void cube_y_col(const LatticePlan &p, int64_t i, int6
             s1 += in1[u] - out1[u];
         }
     }
-}
-
-__global__ void __launch_bounds__(kColThreads) cube_y_kernel(LatticePlan p)
-{
-    if (p.skip && *(const volatile int *)p.skip) return;
-    cube_y_col(p, (int64_t)blockIdx.x * kColThreads + threadIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // The (column block, plane, segment) of CTA b of a batched y or z pass: the
@@ -378,52 +404,51 @@ __global__ void __launch_bounds__(kColThreads)
 // fixed-point (sin, cos) (exact i128, so the reduction order does not matter),
 // and the last CTA to finish sums every partial and records R.  bid / nblk: the
 // CTA's index among the network's CTAs of this launch and their number.
-__device__ void lattice_record_order(const LatticePlan &p, i128 ps, i128 pc, unsigned bid, unsigned nblk,
-                                     unsigned long long *ctr)
+// (ps, pc) summed over the CTA, valid in thread 0; every thread of the CTA calls it.
+__device__ __forceinline__ void cta_sum_pair(i128 &ps, i128 &pc)
 {
     __shared__ i128 s_ws[32], s_wc[32];
-    __shared__ bool s_last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     ps = warp_sum_i128(ps);
     pc = warp_sum_i128(pc);
+    __syncthreads(); // an earlier use of s_ws / s_wc is over
     if (lane == 0) {
         s_ws[warp] = ps;
         s_wc[warp] = pc;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        i128 ts = 0, tc = 0;
+        ps = 0;
+        pc = 0;
         for (int w = 0; w < nw; ++w) {
-            ts += s_ws[w];
-            tc += s_wc[w];
+            ps += s_ws[w];
+            pc += s_wc[w];
         }
-        st_i128(p.partial + 2 * bid, ts);
-        st_i128(p.partial + 2 * bid + 1, tc);
-        __threadfence();
-        s_last = last_arrival(ctr, nblk);
     }
-    __syncthreads();
-    if (!s_last) return;
+}
+
+// The order parameter R = |sum_n e^{i theta_n}| / nodes from the exact sums of
+// nblk CTA partials (p.partial), by one CTA; recorded in p.obs.
+__device__ __forceinline__ void lattice_order_total(const LatticePlan &p, unsigned nblk)
+{
     i128 ts = 0, tc = 0;
-    for (unsigned b = threadIdx.x; b < nblk; b += blockDim.x) {
-        ts += ld_cg_i128(p.partial + 2 * b);
-        tc += ld_cg_i128(p.partial + 2 * b + 1);
-    }
-    ts = warp_sum_i128(ts);
-    tc = warp_sum_i128(tc);
-    __syncthreads();
-    if (lane == 0) {
-        s_ws[warp] = ts;
-        s_wc[warp] = tc;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        ts = 0;
-        tc = 0;
-        for (int w = 0; w < nw; ++w) {
-            ts += s_ws[w];
-            tc += s_wc[w];
+    constexpr int U = 8; // partials of a thread in flight
+    for (unsigned b0 = threadIdx.x; b0 < nblk; b0 += U * blockDim.x) {
+        i128 vs[U], vc[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const unsigned b = b0 + u * blockDim.x;
+            vs[u] = b < nblk ? ld_cg_i128(p.partial + 2 * b) : 0;
+            vc[u] = b < nblk ? ld_cg_i128(p.partial + 2 * b + 1) : 0;
         }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            ts += vs[u];
+            tc += vc[u];
+        }
+    }
+    cta_sum_pair(ts, tc);
+    if (threadIdx.x == 0) {
         const double S = fixed_to_double(ts, p.F), C = fixed_to_double(tc, p.F);
         if (p.obs) {
             const unsigned long long n = *p.obs_ctr;
@@ -431,6 +456,32 @@ __device__ void lattice_record_order(const LatticePlan &p, i128 ps, i128 pc, uns
             *p.obs_ctr = n + 1;
         }
     }
+}
+
+// The CTA's partial sums to p.partial[2 bid, 2 bid + 1]; the last CTA of nblk
+// to arrive at *ctr adds them all up and records the order parameter.
+__device__ void lattice_record_order(const LatticePlan &p, i128 ps, i128 pc, unsigned bid, unsigned nblk,
+                                     unsigned long long *ctr)
+{
+    __shared__ bool s_last;
+    cta_sum_pair(ps, pc);
+    if (threadIdx.x == 0) {
+        st_i128(p.partial + 2 * bid, ps);
+        st_i128(p.partial + 2 * bid + 1, pc);
+        __threadfence();
+        s_last = last_arrival(ctr, nblk);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    lattice_order_total(p, nblk);
+}
+
+// The order parameter from the partials of a previous launch of nblk CTAs (the
+// cube's fused node pass, whose CTAs only store their partials).
+__global__ void __launch_bounds__(512) lattice_order_kernel(LatticePlan p, unsigned nblk)
+{
+    if (p.skip && *(const volatile int *)p.skip) return;
+    lattice_order_total(p, nblk);
 }
 
 // One node's RK4 stage: right-hand side from the window sums (W0, W1) and its own
@@ -470,7 +521,7 @@ __device__ __forceinline__ void lattice_node_load(const LatticePlan &p, int64_t 
 template <int M, int STAGE, typename Acc>
 __device__ __forceinline__ void lattice_node_update(const LatticePlan &p, int64_t n, const double (&k)[Model<M>::D],
                                                     const LatNodeIn<M> &in, const StepSize &h, bool &ok, Acc &ps,
-                                                    Acc &pc)
+                                                    Acc &pc, int64_t *sc_out = nullptr)
 {
     constexpr int D = Model<M>::D, NX = Model<M>::NX, XOFF = D - NX;
     const int64_t nodes = p.nodes;
@@ -507,6 +558,10 @@ __device__ __forceinline__ void lattice_node_update(const LatticePlan &p, int64_
     if (STAGE == 0 || STAGE == 4) {
         ps += q62_to(s62, p.F);
         pc += q62_to(c62, p.F);
+    }
+    if (sc_out) {
+        sc_out[0] = s62;
+        sc_out[1] = c62;
     }
 }
 
@@ -745,7 +800,6 @@ __global__ void __launch_bounds__(kTileThreads) cube_y_tile_kernel(LatticePlan p
 // N1^2 elements apart), the node pass reads and writes whole warps of
 // consecutive nodes.  Three window CTAs per SM at the tile sizes of N1 <= 594.
 constexpr int kZThreads = 384;
-constexpr int kNodeThreads = 256;
 
 __global__ void __launch_bounds__(kZThreads, 3) cube_zw_tile_kernel(LatticePlan p)
 {
@@ -803,31 +857,80 @@ __device__ __forceinline__ void cube_node_load(const LatticePlan &p, int64_t n, 
     c = STAGE > 0 ? p.cpl[n] : 0.0;
 }
 
+// Node pass fused with the next stage's x pass: one warp per row (k, j).  Every
+// lane updates its nodes i = lane, lane + 32, ... (the next 4 nodes' loads in
+// flight), and their new (sin, cos) rounded onto 2^-F fill the row's prefix
+// rows in shared memory; the row's x-window sums then go out in the plane-wise
+// i-block-major layout the y pass reads.  In stage 4 (and the prologue, STAGE 0:
+// the (sin, cos) of y, no update) the row's sums give the order parameter.
 template <int M, int STAGE>
-__global__ void __launch_bounds__(kNodeThreads) cube_node_kernel(LatticePlan p, const StepSize h)
+__device__ __forceinline__ void cube_nodex_row(const LatticePlan &p, const StepSize &h, int64_t row, int64_t *pre0,
+                                               int64_t *pre1, bool &ok, i128 &ps, i128 &pc)
 {
-    if (p.skip && *(const volatile int *)p.skip) return;
-    const int64_t nodes = p.nodes, stride = (int64_t)gridDim.x * kNodeThreads;
-    i128 ps = 0, pc = 0;
-    bool ok = true;
-    int64_t n = (int64_t)blockIdx.x * kNodeThreads + threadIdx.x;
-    if (n < nodes) {
-        LatNodeIn<M> cur;
-        double c;
-        cube_node_load<M, STAGE>(p, n, cur, c);
-        for (; n < nodes; n += stride) { // the next node's loads in flight
-            LatNodeIn<M> nxt;
-            double cn = 0.0;
-            if (n + stride < nodes) cube_node_load<M, STAGE>(p, n + stride, nxt, cn);
-            double k[Model<M>::D];
-            Model<M>::rhs_from_coupling(p.mp, c, cur.X, k);
-            lattice_node_update<M, STAGE, i128>(p, n, k, cur, h, ok, ps, pc);
-            cur = nxt;
-            c = cn;
+    constexpr int D = Model<M>::D, U = 4;
+    const int lane = threadIdx.x & 31, n1 = (int)p.N1;
+    // the row's own pointers, so that every node address is a 32-bit offset
+    const int64_t base = row * p.N1;
+    LatticePlan q = p;
+    q.y += base;
+    q.acc += base;
+    q.f += base;
+    q.cpl += base;
+    if (Model<M>::NX > 0) q.xs += base;
+    for (int mb = lane; mb < n1; mb += 32 * U) {
+        LatNodeIn<M> in[U];
+        double c[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = mb + 32 * u;
+            if (i < n1) cube_node_load<M, STAGE>(q, (unsigned)i, in[u], c[u]);
+        }
+        int64_t rs = 0, rc = 0; // U terms of |Q| <= 2^F
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = mb + 32 * u;
+            if (i < n1) {
+                double k[D] = {};
+                if (STAGE > 0) Model<M>::rhs_from_coupling(q.mp, c[u], in[u].X, k);
+                int64_t sc[2];
+                int64_t unused_s = 0, unused_c = 0;
+                lattice_node_update<M, STAGE, int64_t>(q, (unsigned)i, k, in[u], h, ok, unused_s, unused_c, sc);
+                const int64_t qs = q62_to(sc[0], p.F), qc = q62_to(sc[1], p.F);
+                pre0[i + 1] = qs;
+                pre1[i + 1] = qc;
+                rs += qs;
+                rc += qc;
+            }
+        }
+        if (STAGE == 0 || STAGE == 4) {
+            ps += rs;
+            pc += rc;
         }
     }
+    lattice_x_scan_out<0, true>(p, row, pre0, pre1);
+}
+
+template <int M, int STAGE>
+__global__ void __launch_bounds__(32 * kNodexWarpsMax) cube_nodex_kernel(LatticePlan p, const StepSize h)
+{
+    if (p.skip && *(const volatile int *)p.skip) return;
+    extern __shared__ int64_t smem[];
+    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int64_t stride = p.N1 + 1, rows = p.nodes / p.N1;
+    int64_t *pre0 = smem + (int64_t)warp * 2 * stride;
+    int64_t *pre1 = pre0 + stride;
+    const int64_t row = (int64_t)blockIdx.x * nwarps + warp;
+    i128 ps = 0, pc = 0;
+    bool ok = true;
+    if (row < rows) cube_nodex_row<M, STAGE>(p, h, row, pre0, pre1, ok, ps, pc); // uniform over the warp
     if (!ok) raise_error(p.err, ERR_RANGE);
-    if (STAGE == 0 || STAGE == 4) lattice_record_order(p, ps, pc, blockIdx.x, gridDim.x, p.tile_ctr);
+    if (STAGE == 0 || STAGE == 4) { // the order parameter's partials (lattice_order_kernel adds them up)
+        cta_sum_pair(ps, pc);
+        if (threadIdx.x == 0) {
+            st_i128(p.partial + 2 * blockIdx.x, ps);
+            st_i128(p.partial + 2 * blockIdx.x + 1, pc);
+        }
+    }
 }
 
 // Batched cube z pass (stages 1-4): CTA b is CTA b - yz_base[m] of member m.
@@ -899,20 +1002,6 @@ static dim3 tile_grid(int64_t N1)
     return dim3((unsigned)((N1 + BI - 1) / BI), (unsigned)N1, 1);
 }
 
-// CTAs of the cube node pass: every node once, at most as many CTAs as fit on
-// the device at once, per model (0 Kuramoto, 1 with inertia) and for stages 1-3
-// and stage 4 (set by lattice_configure; the partial sums of the order
-// parameter, recorded in stage 4, are allocated for up to
-// lattice_partial_blocks of them, and a plan's stage-4 count never changes).
-static int64_t g_node_grid[2][2] = {{152 * 3, 152 * 3}, {152 * 3, 152 * 3}};
-
-static int64_t cube_node_grid(int model, int stage, int64_t nodes)
-{
-    const int64_t want = (nodes + kNodeThreads - 1) / kNodeThreads;
-    const int64_t cap = g_node_grid[model == 3 ? 1 : 0][stage == 4 || stage == 0 ? 1 : 0]; // the recording grid
-    return want < cap ? want : cap;
-}
-
 static unsigned gather_grid(const LatticePlan &p)
 {
     return (unsigned)((p.nodes + kGatherThreads - 1) / kGatherThreads);
@@ -935,7 +1024,7 @@ int64_t lattice_partial_blocks(int topo, int64_t N1)
 {
     const int64_t a = lattice_order_blocks(topo, N1);
     if (topo != 1) return a;
-    const int64_t b = (N1 * N1 * N1 + kNodeThreads - 1) / kNodeThreads; // the node pass, uncapped
+    const int64_t b = (N1 * N1 + nodex_warps(N1) - 1) / nodex_warps(N1); // the fused node pass (one row per warp)
     return a > b ? a : b;
 }
 
@@ -963,34 +1052,36 @@ cudaError_t lattice_configure()
     const int tmax = (int)std::max(std::max(cube_tile_smem(297), cube_tile_smem(594)), cube_tile_smem(1024));
     if (e == cudaSuccess) e = cudaFuncSetAttribute(cube_y_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tmax);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(cube_zw_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tmax);
-    // the node pass: a grid of as many CTAs as fit on the device at once
-    int dev = 0, sms = 0, per_sm[4] = {0, 0, 0, 0};
-    if (e == cudaSuccess) e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[0], cube_node_kernel<0, 2>, kNodeThreads, 0);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[1], cube_node_kernel<0, 4>, kNodeThreads, 0);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[2], cube_node_kernel<3, 2>, kNodeThreads, 0);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[3], cube_node_kernel<3, 4>, kNodeThreads, 0);
-    if (e == cudaSuccess)
-        for (int m = 0; m < 2; ++m)
-            for (int st = 0; st < 2; ++st) g_node_grid[m][st] = (int64_t)(per_sm[2 * m + st] > 0 ? per_sm[2 * m + st] : 1) * sms;
+#define SIM_NODEX_ATTR(M, S)                                                                                           \
+    if (e == cudaSuccess)                                                                                              \
+        e = cudaFuncSetAttribute(cube_nodex_kernel<M, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRowSmemMax);
+    SIM_NODEX_ATTR(0, 0) SIM_NODEX_ATTR(0, 1) SIM_NODEX_ATTR(0, 2) SIM_NODEX_ATTR(0, 3) SIM_NODEX_ATTR(0, 4)
+    SIM_NODEX_ATTR(3, 0) SIM_NODEX_ATTR(3, 1) SIM_NODEX_ATTR(3, 2) SIM_NODEX_ATTR(3, 3) SIM_NODEX_ATTR(3, 4)
+#undef SIM_NODEX_ATTR
     return e;
 }
 
 int lattice_row_warps(int64_t N1) { return row_warps(N1); }
 
-// Batched cube members of one model: per RK4 stage one x, one y and one z
-// launch over all of them (each member with its own plan, prefix rows and
-// order-parameter counter), the same bits as lattice_step on each alone.
-template <int M>
-static cudaError_t cube_batch_stage(int stage, const CubeBatchGroup &g, double dt, cudaStream_t s)
+// Batched cube members of one model: one x, one y and one z launch over all of
+// them per pass (each member with its own plan, prefix rows and order-parameter
+// counter).  Between steps a cube's x-window sums hold the sums of y (the
+// prologue, the fused node pass of a single cube's stage 4 and the batch's last
+// x pass keep it so), so a step begins with the y pass and a member can be
+// stepped alone or in a batch in any order; the results are the same bits.
+static cudaError_t cube_batch_x(const CubeBatchGroup &g, cudaStream_t s)
 {
     const size_t smem = (size_t)g.w * 2 * (size_t)(g.n1_max + 1) * sizeof(int64_t);
     cube_batch_x_kernel<<<(unsigned)g.n_x, 32 * g.w, smem, s>>>(g.plans, g.x_item, g.x_base);
+    return cudaGetLastError();
+}
+
+template <int M>
+static cudaError_t cube_batch_yz(int stage, const CubeBatchGroup &g, double dt, cudaStream_t s)
+{
+    cube_batch_y_kernel<<<(unsigned)g.n_yz, kColThreads, 0, s>>>(g.plans, g.yz_item, g.yz_base);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    cube_batch_y_kernel<<<(unsigned)g.n_yz, kColThreads, 0, s>>>(g.plans, g.yz_item, g.yz_base);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const StepSize h = step_size(dt);
     const dim3 grid((unsigned)g.n_yz);
     switch (stage) {
@@ -1006,67 +1097,99 @@ cudaError_t cube_batch_step(const CubeBatchGroup &g, double dt, cudaStream_t s)
 {
     if (g.n_x == 0) return cudaSuccess;
     for (int stage = 1; stage <= 4; ++stage) {
-        const cudaError_t e = g.model == 3 ? cube_batch_stage<3>(stage, g, dt, s) : cube_batch_stage<0>(stage, g, dt, s);
+        cudaError_t e = stage > 1 ? cube_batch_x(g, s) : cudaSuccess;
+        if (e == cudaSuccess) e = g.model == 3 ? cube_batch_yz<3>(stage, g, dt, s) : cube_batch_yz<0>(stage, g, dt, s);
         if (e != cudaSuccess) return e;
     }
-    return cudaSuccess;
+    return cube_batch_x(g, s); // the x sums of y_{n+1}
+}
+
+// CTAs of a lattice x pass and of the cube's fused node pass: one row per warp.
+static unsigned x_grid(const LatticePlan &p)
+{
+    const int w = row_warps(p.N1);
+    const int64_t rows = p.nodes / p.N1;
+    return (unsigned)((rows + w - 1) / w);
+}
+
+static size_t x_smem(const LatticePlan &p)
+{
+    return (size_t)row_warps(p.N1) * 2 * (size_t)(p.N1 + 1) * sizeof(int64_t);
 }
 
 static cudaError_t launch_x(const LatticePlan &p, cudaStream_t s)
 {
     const int w = row_warps(p.N1);
-    const size_t smem = (size_t)w * 2 * (size_t)(p.N1 + 1) * sizeof(int64_t);
-    const int64_t rows = p.nodes / p.N1;
-    const int64_t want = (rows + w - 1) / w;
-    const unsigned grid = (unsigned)(want < 152 * 16 ? want : 152 * 16);
-    if (p.topo == 1) lattice_x_kernel<0><<<grid, 32 * w, smem, s>>>(p);
-    else if (p.wmode) lattice_x_kernel<2><<<grid, 32 * w, smem, s>>>(p);
-    else lattice_x_kernel<1><<<grid, 32 * w, smem, s>>>(p);
-    return cudaGetLastError();
+    if (p.topo == 1) lattice_x_kernel<0><<<x_grid(p), 32 * w, x_smem(p), s>>>(p);
+    else if (p.wmode) lattice_x_kernel<2><<<x_grid(p), 32 * w, x_smem(p), s>>>(p);
+    else lattice_x_kernel<1><<<x_grid(p), 32 * w, x_smem(p), s>>>(p);
+    const cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) kernel_mark(s, 0);
+    return e;
 }
 
+// Stage STAGE of a single cube after its x pass: y pass, z-window pass, and the
+// node pass fused with the next x pass (STAGE 0: the fused pass alone, the
+// prologue).
 template <int M, int STAGE>
-static cudaError_t launch_node_pass(const LatticePlan &p, double dt, cudaStream_t s)
+static cudaError_t launch_cube_stage(const LatticePlan &p, double dt, cudaStream_t s)
 {
-    if (p.topo == 1) {
+    cudaError_t e = cudaSuccess;
+    if (STAGE > 0) {
+        cube_y_tile_kernel<<<tile_grid(p.N1), kTileThreads, cube_tile_smem(p.N1), s>>>(p);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        kernel_mark(s, 1);
         cube_zw_tile_kernel<<<tile_grid(p.N1), kZThreads, cube_tile_smem(p.N1), s>>>(p);
-        const cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
         kernel_mark(s, 3);
-        cube_node_kernel<M, STAGE><<<(unsigned)cube_node_grid(M, STAGE, p.nodes), kNodeThreads, 0, s>>>(p, step_size(dt));
-    } else if (p.wmode) lattice_gather_kernel<M, STAGE, true><<<gather_grid(p), kGatherThreads, 0, s>>>(p, step_size(dt));
+    }
+    const int w = nodex_warps(p.N1);
+    const int64_t rows = p.nodes / p.N1;
+    const unsigned nblk = (unsigned)((rows + w - 1) / w);
+    cube_nodex_kernel<M, STAGE><<<nblk, 32 * w, (size_t)w * 2 * (size_t)(p.N1 + 1) * sizeof(int64_t), s>>>(
+        p, step_size(dt));
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    kernel_mark(s, 2);
+    if (STAGE == 0 || STAGE == 4) {
+        lattice_order_kernel<<<1, 512, 0, s>>>(p, nblk);
+        if ((e = cudaGetLastError()) == cudaSuccess) kernel_mark(s, 0);
+    }
+    return e;
+}
+
+// Stage STAGE of a ball or disk: x pass and gather (STAGE 0: the gather alone,
+// the prologue).
+template <int M, int STAGE>
+static cudaError_t launch_gather_stage(const LatticePlan &p, double dt, cudaStream_t s)
+{
+    cudaError_t e = STAGE > 0 ? launch_x(p, s) : cudaSuccess;
+    if (e != cudaSuccess) return e;
+    if (p.wmode && STAGE > 0)
+        lattice_gather_kernel<M, STAGE, true><<<gather_grid(p), kGatherThreads, 0, s>>>(p, step_size(dt));
     else lattice_gather_kernel<M, STAGE, false><<<gather_grid(p), kGatherThreads, 0, s>>>(p, step_size(dt));
-    return cudaGetLastError();
+    if ((e = cudaGetLastError()) == cudaSuccess && STAGE > 0) kernel_mark(s, 2);
+    return e;
 }
 
 template <int M>
 static cudaError_t launch_stage(int stage, const LatticePlan &p, double dt, cudaStream_t s)
 {
-    if (stage == 0) {
-        // prologue: (sin, cos) of y and its order parameter, no window
-        return p.topo == 1 ? (cube_node_kernel<M, 0><<<(unsigned)cube_node_grid(M, 0, p.nodes), kNodeThreads, 0, s>>>(
-                                  p, step_size(0.0)),
-                              cudaGetLastError())
-                           : (lattice_gather_kernel<M, 0, false><<<gather_grid(p), kGatherThreads, 0, s>>>(
-                                  p, step_size(0.0)),
-                              cudaGetLastError());
-    }
-    cudaError_t e = launch_x(p, s);
-    if (e != cudaSuccess) return e;
-    kernel_mark(s, 0);
     if (p.topo == 1) {
-        cube_y_tile_kernel<<<tile_grid(p.N1), kTileThreads, cube_tile_smem(p.N1), s>>>(p);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        kernel_mark(s, 1);
+        switch (stage) {
+        case 0: return launch_cube_stage<M, 0>(p, dt, s);
+        case 1: return launch_cube_stage<M, 1>(p, dt, s);
+        case 2: return launch_cube_stage<M, 2>(p, dt, s);
+        case 3: return launch_cube_stage<M, 3>(p, dt, s);
+        default: return launch_cube_stage<M, 4>(p, dt, s);
+        }
     }
     switch (stage) {
-    case 1: e = launch_node_pass<M, 1>(p, dt, s); break;
-    case 2: e = launch_node_pass<M, 2>(p, dt, s); break;
-    case 3: e = launch_node_pass<M, 3>(p, dt, s); break;
-    default: e = launch_node_pass<M, 4>(p, dt, s); break;
+    case 0: return launch_gather_stage<M, 0>(p, dt, s);
+    case 1: return launch_gather_stage<M, 1>(p, dt, s);
+    case 2: return launch_gather_stage<M, 2>(p, dt, s);
+    case 3: return launch_gather_stage<M, 3>(p, dt, s);
+    default: return launch_gather_stage<M, 4>(p, dt, s);
     }
-    if (e == cudaSuccess) kernel_mark(s, 2);
-    return e;
 }
 
 static cudaError_t launch_any(int stage, const LatticePlan &p, double dt, cudaStream_t s)
@@ -1074,13 +1197,19 @@ static cudaError_t launch_any(int stage, const LatticePlan &p, double dt, cudaSt
     return p.model == 3 ? launch_stage<3>(stage, p, dt, s) : launch_stage<0>(stage, p, dt, s);
 }
 
+// The (sin, cos) of y and its order parameter (the cube: also its x sums).
 cudaError_t lattice_prologue(const LatticePlan &p, cudaStream_t s)
 {
     return launch_any(0, p, 0.0, s);
 }
 
+// k = f(y) into acc (stage 1 with dt = 0, from the stored (sin, cos) of y).
 cudaError_t lattice_rhs(const LatticePlan &p, cudaStream_t s)
 {
+    if (p.topo == 1) {
+        const cudaError_t e = launch_x(p, s); // y may be a stage input that has no x sums yet
+        if (e != cudaSuccess) return e;
+    }
     return launch_any(1, p, 0.0, s);
 }
 

@@ -142,10 +142,19 @@ extern "C" int sim_ring_step_noalloc(int model, int64_t N, int64_t radius, const
     if (L.total > kNoAllocScratchBytes)
         return report_error(SIM_EINVAL, "sim_ring_step_noalloc: the ring's buffers exceed the static scratch array");
 
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // The call reads the error word back and synchronises the stream, neither of
+    // which a capturing stream allows: refuse before touching the stream, so that
+    // the caller's capture stays intact.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t ce = cudaStreamIsCapturing(s, &cap);
+    if (ce != cudaSuccess) return report_cuda_error(ce, "sim_ring_step_noalloc: cudaStreamIsCapturing");
+    if (cap != cudaStreamCaptureStatusNone)
+        return report_error(SIM_EINVAL, "sim_ring_step_noalloc: the stream is capturing; this call synchronises and cannot be captured");
+
     unsigned char *b = nullptr;
     int st = setup_device(&b);
     if (st != SIM_OK) return st;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
 
     // Derived constants, as sim_create computes them.
     ModelParams mp{};

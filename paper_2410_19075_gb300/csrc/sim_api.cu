@@ -897,7 +897,7 @@ int sim_step_timed(sim_t h, int64_t n_steps, double dt, double *ms_by_kind, int6
             h->pfx = 2;
         }
     }
-    const int per_step = use_cluster(h) ? 1 : h->topo == SIM_CUBE3D ? 16 : is_lattice(h->topo) ? 8 : 4;
+    const int per_step = use_cluster(h) ? 1 : h->topo == SIM_CUBE3D ? 13 : is_lattice(h->topo) ? 8 : 4;
     const int cap = (int)(use_cluster(h) ? 1 : per_step * n_steps);
     std::vector<cudaEvent_t> ev(cap + 1, nullptr);
     std::vector<unsigned char> kind(cap, 0);

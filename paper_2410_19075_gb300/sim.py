@@ -140,7 +140,8 @@ class Network:
     def step_timed(self, n_steps: int, dt: float) -> dict:
         """``sim_step_timed``: n_steps RK4 steps launched kernel by kernel with
         an event after each; per kernel kind the summed milliseconds and the
-        launch count (kinds: stage or x pass, cube y pass, lattice node pass)."""
+        launch count (kinds: ring stage, lattice x pass or cube order total; cube y
+        pass; lattice node pass; cube z-window pass)."""
         ms = (ctypes.c_double * 4)()
         n = (ctypes.c_int64 * 4)()
         check(lib().sim_step_timed(self._handle(), int(n_steps), float(dt), ms, n))

@@ -55,14 +55,19 @@ def test_chunks_links_and_roofline():
     assert bench.links_of(0, 1000, 350) == 700
     assert bench.links_of(1, 464, 92) == 185 ** 3 - 1
     assert bench.links_of(2, 100, 2) == 32 and bench.links_of(2, 100, 6) == 924  # the paper's 33 and 925 with self
-    # four x, y and z-window passes (16 + 16, 16 + 16, 16 + 16 + 8 B), and the node
-    # passes of stages 1-4 (8 + 8 in, 8 + 16 out; +8 acc in stages 2-4)
-    assert bench.CUBE_BYTES == 4 * (32 + 32 + 40) + 40 + 48 + 48 + 48
+    # four y and z-window passes (16 + 16, 16 + 16 + 8 B), and the node passes
+    # fused with the next x pass in stages 1-4 (8 + 8 in, 8 + 16 + 16 out; +8 acc
+    # in stages 2-4)
+    assert bench.CUBE_BYTES == 4 * (32 + 40) + 56 + 64 + 64 + 64
     peaks = {"hbm_gbs": 6000.0, "fp64_gflops": 1000.0, "hbm_source": "x", "fp64_source": "y"}
-    kinds = {"stage_or_x": {"ms": 2.0, "launches": 4}, "cube_y": {"ms": 2.0, "launches": 4},
+    kinds = {"stage_or_x": {"ms": 0.02, "launches": 1}, "cube_y": {"ms": 2.0, "launches": 4},
              "cube_z": {"ms": 3.0, "launches": 4}, "node_pass": {"ms": 8.0, "launches": 4}}
+    kinds = bench.cube_kinds(kinds)  # a cube step's kind 0 is its order-parameter total
+    assert "order_total" in kinds and "stage_or_x" not in kinds
     r = bench.roofline_of(kinds, bench.CUBE_KIND_BYTES, bench.CUBE_KIND_FLOPS, 10 ** 8, peaks)
-    assert r["kernel"] == "node_pass" and abs(r["share_of_timed_region"] - 8 / 15) < 1e-12
+    assert r["kernel"] == "node_pass" and abs(r["share_of_timed_region"] - 8 / 13.02) < 1e-12
+    table = bench.per_kind_table(kinds, 10 ** 8, bench.CUBE_KIND_BYTES, peaks)
+    assert "algorithmic_gbs" not in table["order_total"] and "algorithmic_gbs" in table["node_pass"]
     gbs = bench.CUBE_PASS_BYTES[2] * 1e8 / 2e-3 / 1e9  # 2 ms per launch
     assert r["bound"] == "hbm" and abs(r["achieved"] - gbs) < 1e-6 and abs(r["frac"] - gbs / 6000.0) < 1e-12
     assert r["traffic"] is None

@@ -102,3 +102,25 @@ def test_noalloc_rejects_rings_beyond_its_static_array():
     state = torch.zeros(N, dtype=torch.float64, device="cuda")
     assert _noalloc(0, N, 100, I.ks_params(), state, None, 1, 0.01) == SIM_EINVAL
     assert b"65536" in lib().sim_last_error()
+
+
+def test_noalloc_refuses_a_capturing_stream_and_leaves_the_capture_intact():
+    import torch
+    from paper_2410_19075_gb300._lib import SIM_EINVAL, lib
+    N, R = 2000, 600
+    y0 = I.ks_phases(65, 0, N)
+    state = torch.from_numpy(y0.copy()).cuda()
+    side = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(graph, stream=side):
+        # inside the capture the current stream is the capturing one
+        st = _noalloc(0, N, R, I.ks_params(), state, None, 5, 0.01)
+        state.add_(0.0)  # the capture goes on after the refused call
+    assert st == SIM_EINVAL
+    assert b"capturing" in lib().sim_last_error()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert np.array_equal(state.cpu().numpy(), y0)  # the refused call did nothing
+    expect = _regular(0, N, R, I.ks_params(), y0, None, 5, 0.01)
+    assert np.array_equal(_run_noalloc(0, N, R, I.ks_params(), y0, None, 5), expect)
