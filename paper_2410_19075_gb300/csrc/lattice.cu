@@ -428,32 +428,21 @@ __device__ __forceinline__ void cta_sum_pair(i128 &ps, i128 &pc)
 }
 
 // The order parameter R = |sum_n e^{i theta_n}| / nodes from the exact sums of
-// nblk CTA partials (p.partial), by one CTA; recorded in p.obs.
-__device__ __forceinline__ void lattice_order_total(const LatticePlan &p, unsigned nblk)
+// the n partial pairs at part (p.partial or beyond), by one CTA; recorded in p.obs.
+__device__ __forceinline__ void lattice_order_total(const LatticePlan &p, const i128 *part, unsigned n)
 {
     i128 ts = 0, tc = 0;
-    constexpr int U = 8; // partials of a thread in flight
-    for (unsigned b0 = threadIdx.x; b0 < nblk; b0 += U * blockDim.x) {
-        i128 vs[U], vc[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const unsigned b = b0 + u * blockDim.x;
-            vs[u] = b < nblk ? ld_cg_i128(p.partial + 2 * b) : 0;
-            vc[u] = b < nblk ? ld_cg_i128(p.partial + 2 * b + 1) : 0;
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            ts += vs[u];
-            tc += vc[u];
-        }
+    for (unsigned b = threadIdx.x; b < n; b += blockDim.x) {
+        ts += ld_cg_i128(part + 2 * b);
+        tc += ld_cg_i128(part + 2 * b + 1);
     }
     cta_sum_pair(ts, tc);
     if (threadIdx.x == 0) {
         const double S = fixed_to_double(ts, p.F), C = fixed_to_double(tc, p.F);
         if (p.obs) {
-            const unsigned long long n = *p.obs_ctr;
-            p.obs[n % (unsigned long long)p.obs_cap] = sqrt(S * S + C * C) / (double)p.nodes;
-            *p.obs_ctr = n + 1;
+            const unsigned long long n_rec = *p.obs_ctr;
+            p.obs[n_rec % (unsigned long long)p.obs_cap] = sqrt(S * S + C * C) / (double)p.nodes;
+            *p.obs_ctr = n_rec + 1;
         }
     }
 }
@@ -473,15 +462,34 @@ __device__ void lattice_record_order(const LatticePlan &p, i128 ps, i128 pc, uns
     }
     __syncthreads();
     if (!s_last) return;
-    lattice_order_total(p, nblk);
+    lattice_order_total(p, p.partial, nblk);
 }
 
 // The order parameter from the partials of a previous launch of nblk CTAs (the
-// cube's fused node pass, whose CTAs only store their partials).
-__global__ void __launch_bounds__(512) lattice_order_kernel(LatticePlan p, unsigned nblk)
+// cube's fused node pass, whose CTAs only store their partials): CTA g adds up
+// its slice of them into the pair nblk + g, and the last of the kOrderCtas CTAs
+// to finish (arrival counter tile_ctr) adds those up.
+constexpr int kOrderCtas = 128, kOrderThreads = 256;
+__global__ void __launch_bounds__(kOrderThreads) lattice_order_kernel(LatticePlan p, unsigned nblk)
 {
     if (p.skip && *(const volatile int *)p.skip) return;
-    lattice_order_total(p, nblk);
+    __shared__ bool s_last;
+    const unsigned per = (nblk + gridDim.x - 1) / gridDim.x, b0 = blockIdx.x * per, b1 = min(nblk, b0 + per);
+    i128 ts = 0, tc = 0;
+    for (unsigned b = b0 + threadIdx.x; b < b1; b += blockDim.x) {
+        ts += ld_cg_i128(p.partial + 2 * b);
+        tc += ld_cg_i128(p.partial + 2 * b + 1);
+    }
+    cta_sum_pair(ts, tc);
+    if (threadIdx.x == 0) {
+        st_i128(p.partial + 2 * (nblk + blockIdx.x), ts);
+        st_i128(p.partial + 2 * (nblk + blockIdx.x) + 1, tc);
+        __threadfence();
+        s_last = last_arrival(p.tile_ctr, gridDim.x);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    lattice_order_total(p, p.partial + 2 * nblk, gridDim.x);
 }
 
 // One node's RK4 stage: right-hand side from the window sums (W0, W1) and its own
@@ -792,10 +800,11 @@ __global__ void __launch_bounds__(kTileThreads) cube_y_tile_kernel(LatticePlan p
 //                cross product of its own (sin, cos) with its window sums) to
 //                cpl; thread (ii, r0) takes the planes k = r0, r0 + kZThreads /
 //                BI, ..., the own (sin, cos) of the next two in flight;
-//   node pass    elementwise over the nodes (contiguous, grid-stride): the
-//                slope from cpl, the RK4 update, the next (sin, cos), and in
-//                stage 4 the order parameter.  STAGE 0 is the prologue: the
-//                (sin, cos) of y and its order parameter.
+//   node pass    one warp per row of consecutive nodes (cube_nodex_kernel): the
+//                slope from cpl, the RK4 update, the next (sin, cos), the next
+//                stage's x-window sums of the row, and in stage 4 the order
+//                parameter's partials.  STAGE 0 is the prologue: the (sin, cos)
+//                of y, its x sums and its order parameter.
 // The window pass keeps the tile's 64-byte row segments (the z columns are
 // N1^2 elements apart), the node pass reads and writes whole warps of
 // consecutive nodes.  Three window CTAs per SM at the tile sizes of N1 <= 594.
@@ -865,7 +874,7 @@ __device__ __forceinline__ void cube_node_load(const LatticePlan &p, int64_t n, 
 // the (sin, cos) of y, no update) the row's sums give the order parameter.
 template <int M, int STAGE>
 __device__ __forceinline__ void cube_nodex_row(const LatticePlan &p, const StepSize &h, int64_t row, int64_t *pre0,
-                                               int64_t *pre1, bool &ok, i128 &ps, i128 &pc)
+                                               int64_t *pre1, bool &ok, int64_t &ps, int64_t &pc)
 {
     constexpr int D = Model<M>::D, U = 4;
     const int lane = threadIdx.x & 31, n1 = (int)p.N1;
@@ -885,7 +894,6 @@ __device__ __forceinline__ void cube_nodex_row(const LatticePlan &p, const StepS
             const int i = mb + 32 * u;
             if (i < n1) cube_node_load<M, STAGE>(q, (unsigned)i, in[u], c[u]);
         }
-        int64_t rs = 0, rc = 0; // U terms of |Q| <= 2^F
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int i = mb + 32 * u;
@@ -898,13 +906,11 @@ __device__ __forceinline__ void cube_nodex_row(const LatticePlan &p, const StepS
                 const int64_t qs = q62_to(sc[0], p.F), qc = q62_to(sc[1], p.F);
                 pre0[i + 1] = qs;
                 pre1[i + 1] = qc;
-                rs += qs;
-                rc += qc;
+                if (STAGE == 0 || STAGE == 4) {
+                    ps += qs;
+                    pc += qc;
+                }
             }
-        }
-        if (STAGE == 0 || STAGE == 4) {
-            ps += rs;
-            pc += rc;
         }
     }
     lattice_x_scan_out<0, true>(p, row, pre0, pre1);
@@ -920,15 +926,18 @@ __global__ void __launch_bounds__(32 * kNodexWarpsMax) cube_nodex_kernel(Lattice
     int64_t *pre0 = smem + (int64_t)warp * 2 * stride;
     int64_t *pre1 = pre0 + stride;
     const int64_t row = (int64_t)blockIdx.x * nwarps + warp;
-    i128 ps = 0, pc = 0;
+    // a lane's order sums: at most ceil(N1 / 32) <= 32 terms of |Q| <= 2^F <= 2^56
+    // (F = 61 - ceil(log2 K+) and K+ >= 27), so int64 holds them
+    int64_t ps = 0, pc = 0;
     bool ok = true;
     if (row < rows) cube_nodex_row<M, STAGE>(p, h, row, pre0, pre1, ok, ps, pc); // uniform over the warp
     if (!ok) raise_error(p.err, ERR_RANGE);
     if (STAGE == 0 || STAGE == 4) { // the order parameter's partials (lattice_order_kernel adds them up)
-        cta_sum_pair(ps, pc);
+        i128 ts = ps, tc = pc;
+        cta_sum_pair(ts, tc);
         if (threadIdx.x == 0) {
-            st_i128(p.partial + 2 * blockIdx.x, ps);
-            st_i128(p.partial + 2 * blockIdx.x + 1, pc);
+            st_i128(p.partial + 2 * blockIdx.x, ts);
+            st_i128(p.partial + 2 * blockIdx.x + 1, tc);
         }
     }
 }
@@ -1024,7 +1033,8 @@ int64_t lattice_partial_blocks(int topo, int64_t N1)
 {
     const int64_t a = lattice_order_blocks(topo, N1);
     if (topo != 1) return a;
-    const int64_t b = (N1 * N1 + nodex_warps(N1) - 1) / nodex_warps(N1); // the fused node pass (one row per warp)
+    // the fused node pass (one row per warp) and the order kernel's second level
+    const int64_t b = (N1 * N1 + nodex_warps(N1) - 1) / nodex_warps(N1) + kOrderCtas;
     return a > b ? a : b;
 }
 
@@ -1104,7 +1114,7 @@ cudaError_t cube_batch_step(const CubeBatchGroup &g, double dt, cudaStream_t s)
     return cube_batch_x(g, s); // the x sums of y_{n+1}
 }
 
-// CTAs of a lattice x pass and of the cube's fused node pass: one row per warp.
+// CTAs of a lattice x pass: one row per warp.
 static unsigned x_grid(const LatticePlan &p)
 {
     const int w = row_warps(p.N1);
@@ -1151,7 +1161,7 @@ static cudaError_t launch_cube_stage(const LatticePlan &p, double dt, cudaStream
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     kernel_mark(s, 2);
     if (STAGE == 0 || STAGE == 4) {
-        lattice_order_kernel<<<1, 512, 0, s>>>(p, nblk);
+        lattice_order_kernel<<<kOrderCtas, kOrderThreads, 0, s>>>(p, nblk);
         if ((e = cudaGetLastError()) == cudaSuccess) kernel_mark(s, 0);
     }
     return e;
