@@ -867,16 +867,21 @@ __device__ __forceinline__ void cube_node_load(const LatticePlan &p, int64_t n, 
 }
 
 // Node pass fused with the next stage's x pass: one warp per row (k, j).  Every
-// lane updates its nodes i = lane, lane + 32, ... (the next 4 nodes' loads in
-// flight), and their new (sin, cos) rounded onto 2^-F fill the row's prefix
-// rows in shared memory; the row's x-window sums then go out in the plane-wise
-// i-block-major layout the y pass reads.  In stage 4 (and the prologue, STAGE 0:
-// the (sin, cos) of y, no update) the row's sums give the order parameter.
+// lane updates its nodes i = lane, lane + 32, ..., and their new (sin, cos)
+// rounded onto 2^-F fill the row's prefix rows in shared memory; the row's
+// x-window sums then go out in the plane-wise i-block-major layout the y pass
+// reads.  In stage 4 (and the prologue, STAGE 0: the (sin, cos) of y, no
+// update) the row's sums give the order parameter.
+// The loads go through registers, U nodes of a lane ahead: six for Kuramoto
+// (78 registers in stages 2-3, six CTAs per SM), four for the model with
+// inertia.  Measured on the 464^3 cube, stages 2-4: U = 6 1.18 ms, U = 8 (92
+// registers) 1.21 ms, U = 4 1.33 ms; staging the row's y and coupling terms
+// through shared memory by cp.async instead took 1.39 ms.
 template <int M, int STAGE>
 __device__ __forceinline__ void cube_nodex_row(const LatticePlan &p, const StepSize &h, int64_t row, int64_t *pre0,
                                                int64_t *pre1, bool &ok, int64_t &ps, int64_t &pc)
 {
-    constexpr int D = Model<M>::D, U = 4;
+    constexpr int D = Model<M>::D, U = D == 1 ? 6 : 4;
     const int lane = threadIdx.x & 31, n1 = (int)p.N1;
     // the row's own pointers, so that every node address is a 32-bit offset
     const int64_t base = row * p.N1;

@@ -1744,7 +1744,7 @@ int dp_run(const std::vector<sim_t> &mem, const sim_dp5_opts *opts, sim_dp5_stat
     // path, the control words and the OR of the members' error words.
     for (const DpGroup &g : groups)
         if (e == cudaSuccess) e = dp_launch(9, g, s);
-    for (int i : lat_idx) { // (sin, cos) of y for the RK4 kernels, without recording R
+    for (int i : lat_idx) { // (sin, cos) of y and a cube's x sums of y for the RK4 kernels, without recording R
         LatticePlan quiet = mem[i]->lat;
         quiet.obs = nullptr;
         if (e == cudaSuccess) e = lattice_prologue(quiet, s);
