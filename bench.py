@@ -356,7 +356,8 @@ def run_reference(args):
     line = {"impl": "reference", "metric": "FP64 node-steps/s", "value": v, "unit": "node-steps/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_of(args, N, R),
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(args, N, R, chunks_of(args.steps, args.chunk)),  # the native arm's config
             "cpu_baseline": {"value": v, "unit": "node-steps/s", "cores": cores, "kind": "oracle",
                              "sample": f"each step: brute-force RHS of {per_step_nodes} sampled nodes x 4 "
                                        f"stages of the {n}-node network ({links} links each), extrapolated "

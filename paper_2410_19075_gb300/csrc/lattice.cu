@@ -807,10 +807,12 @@ __global__ void __launch_bounds__(kTileThreads) cube_y_tile_kernel(LatticePlan p
 //                of y, its x sums and its order parameter.
 // The window pass keeps the tile's 64-byte row segments (the z columns are
 // N1^2 elements apart), the node pass reads and writes whole warps of
-// consecutive nodes.  Three window CTAs per SM at the tile sizes of N1 <= 594.
-constexpr int kZThreads = 384;
+// consecutive nodes.  Three window CTAs per SM at the tile sizes of N1 <= 594;
+// 512 threads each measured 1.3% faster than 384 at 464^3 (256: 4-7% slower,
+// whatever the prefetch depth).
+constexpr int kZThreads = 512, kZAhead = 2, kZBlocks = 3; // kZAhead: planes of own (sin, cos) in flight
 
-__global__ void __launch_bounds__(kZThreads, 3) cube_zw_tile_kernel(LatticePlan p)
+__global__ void __launch_bounds__(kZThreads, kZBlocks) cube_zw_tile_kernel(LatticePlan p)
 {
     if (p.skip && *(const volatile int *)p.skip) return;
     extern __shared__ int64_t tile_mem[];
@@ -830,24 +832,24 @@ __global__ void __launch_bounds__(kZThreads, 3) cube_zw_tile_kernel(LatticePlan 
     const int64_t *__restrict__ fs = p.f + base + ii;
     const int64_t *__restrict__ fc = fs + p.nodes;
     double *__restrict__ cpl = p.cpl + base + ii;
-    int64_t f0[2] = {fs[(unsigned)r0 * plane], fc[(unsigned)r0 * plane]}, f1[2] = {0, 0};
-    if (r0 + rstep < N1) {
-        f1[0] = fs[(unsigned)(r0 + rstep) * plane];
-        f1[1] = fc[(unsigned)(r0 + rstep) * plane];
+    int64_t f[kZAhead + 1][2]; // own (sin, cos) of the planes a, a + rstep, ...
+#pragma unroll
+    for (int d = 0; d < kZAhead; ++d) {
+        const int ad = r0 + d * rstep;
+        f[d][0] = ad < N1 ? fs[(unsigned)ad * plane] : 0;
+        f[d][1] = ad < N1 ? fc[(unsigned)ad * plane] : 0;
     }
     for (int a = r0; a < N1; a += rstep) {
-        const int a2 = a + 2 * rstep;
-        int64_t f2[2] = {0, 0};
-        if (a2 < N1) {
-            f2[0] = fs[(unsigned)a2 * plane];
-            f2[1] = fc[(unsigned)a2 * plane];
-        }
-        cpl[(unsigned)a * plane] = lattice_coupling_term(p.mp, f0, cube_tile_window(col0, N1, P, lg, a, t0),
+        const int an = a + kZAhead * rstep;
+        f[kZAhead][0] = an < N1 ? fs[(unsigned)an * plane] : 0;
+        f[kZAhead][1] = an < N1 ? fc[(unsigned)an * plane] : 0;
+        cpl[(unsigned)a * plane] = lattice_coupling_term(p.mp, f[0], cube_tile_window(col0, N1, P, lg, a, t0),
                                                          cube_tile_window(col1, N1, P, lg, a, t1));
-        f0[0] = f1[0];
-        f0[1] = f1[1];
-        f1[0] = f2[0];
-        f1[1] = f2[1];
+#pragma unroll
+        for (int d = 0; d < kZAhead; ++d) {
+            f[d][0] = f[d + 1][0];
+            f[d][1] = f[d + 1][1];
+        }
     }
 }
 
@@ -874,9 +876,10 @@ __device__ __forceinline__ void cube_node_load(const LatticePlan &p, int64_t n, 
 // update) the row's sums give the order parameter.
 // The loads go through registers, U nodes of a lane ahead: six for Kuramoto
 // (78 registers in stages 2-3, six CTAs per SM), four for the model with
-// inertia.  Measured on the 464^3 cube, stages 2-4: U = 6 1.18 ms, U = 8 (92
-// registers) 1.21 ms, U = 4 1.33 ms; staging the row's y and coupling terms
-// through shared memory by cp.async instead took 1.39 ms.
+// inertia.  Measured on the 464^3 cube, stages 2-4: U = 6 1.18 ms, U = 7 (94
+// registers) 1.25 ms, U = 8 1.21 ms, U = 5 (70 registers) 1.34 ms, U = 4
+// 1.33 ms; staging the row's y and coupling terms through shared memory by
+// cp.async instead took 1.39 ms.
 template <int M, int STAGE>
 __device__ __forceinline__ void cube_nodex_row(const LatticePlan &p, const StepSize &h, int64_t row, int64_t *pre0,
                                                int64_t *pre1, bool &ok, int64_t &ps, int64_t &pc)
