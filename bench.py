@@ -79,11 +79,11 @@ LATTICE_BYTES = {0: 408, 3: 544}
 # current kernels from ncu captures, keyed by (topology, model, N, radius,
 # kernel kind); the captures and any scaling are described with the profiles.
 MEASURED_TRAFFIC = {
-    # the cube's node pass (fused with the next x pass) at 464^3, P = 92: 60.1 B
-    # per node averaged over the four stages (54.1, 62.1, 62.1, 62.2), measured by
+    # the cube's node pass (fused with the next x pass) at 464^3, P = 92: 60.0 B
+    # per node averaged over the four stages (54.0, 62.0, 62.0, 62.1), measured by
     # ncu at N1 = 300 (the full size is too large to capture), times the
     # 99,897,344 nodes
-    (1, 0, 464, 92, "node_pass"): 60.1 * 464 ** 3,
+    (1, 0, 464, 92, "node_pass"): 60.0 * 464 ** 3,
 }
 
 
