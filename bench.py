@@ -367,10 +367,11 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------- timing helpers
-def timed_chunks(net, chunks, dt, flush, world=1):
+def timed_chunks(net, chunks, dt, flush, world=1, per_chunk=None):
     """The timed region: every chunk launched kernel by kernel through
     sim_step_timed after an L2 flush; returns the device milliseconds of the
-    whole region and the per-kind sums."""
+    whole region and the per-kind sums (and appends each chunk's milliseconds
+    to per_chunk when given)."""
     import torch
     kinds = {}
     total = 0.0
@@ -380,14 +381,26 @@ def timed_chunks(net, chunks, dt, flush, world=1):
         flush.zero_()
         torch.cuda.synchronize()
         r = net.step_timed(c, dt)
+        chunk_ms = 0.0
         for k, v in r.items():
             d = kinds.setdefault(k, {"ms": 0.0, "launches": 0})
             d["ms"] += v["ms"]
             d["launches"] += v["launches"]
-            total += v["ms"]
+            chunk_ms += v["ms"]
+        total += chunk_ms
+        if per_chunk is not None:
+            per_chunk.append(chunk_ms)
     torch.cuda.synchronize()
     barrier(world)
     return total, kinds
+
+
+def iteration_spread(per_chunk, chunks, nodes):
+    """Node-steps/s of every timed iteration (chunk) and their median: the
+    spread behind the whole-region value."""
+    vals = [nodes * c / (ms * 1e-3) for c, ms in zip(chunks, per_chunk) if ms > 0]
+    return {"per_iteration": vals, "median": float(np.median(vals)) if vals else None,
+            "min": min(vals) if vals else None, "max": max(vals) if vals else None}
 
 
 def graph_timed(net, steps, dt, flush, stream):
@@ -992,7 +1005,8 @@ def run_native(args):
     # --- device-resident timing: K RK4 steps in chunks, L2 flushed between chunks,
     # every kernel bracketed by CUDA events on the handle's stream
     with Clocked(local) as ck:
-        ms, kinds = timed_chunks(net, chunks, args.dt, flush, world)
+        per_chunk = []
+        ms, kinds = timed_chunks(net, chunks, args.dt, flush, world, per_chunk)
     ms = max_over_ranks(ms, world)
     y_check = net.get_state()  # surfaces any device error
     assert np.isfinite(y_check).all()
@@ -1021,7 +1035,8 @@ def run_native(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config_of(args, N, R, chunks), "e2e": e2e,
             "gpu_launches": launches, "roofline": roofline, "clocks": ck.record,
-            "kernels": per_kind_table(kinds, nodes, kb, peaks), "peaks": peaks}
+            "kernels": per_kind_table(kinds, nodes, kb, peaks), "peaks": peaks,
+            "iterations": iteration_spread(per_chunk, chunks, nodes * world)}
     if args.topo == 1:
         line["algorithmic_bytes_per_node_step"] = {"this_build": CUBE_BYTES, "survey": CUBE_BYTES_SURVEY,
                                                    "hbm_frac_survey_bytes":

@@ -860,12 +860,12 @@ __device__ __forceinline__ void cube_node_load(const LatticePlan &p, int64_t n, 
     const int64_t nodes = p.nodes;
 #pragma unroll
     for (int v = 0; v < D; ++v) {
-        in.y[v] = p.y[v * nodes + n];
-        in.acc[v] = STAGE >= 2 ? p.acc[v * nodes + n] : 0.0;
+        in.y[v] = __ldcg(p.y + v * nodes + n); // streamed once: L2 only, L1 left to the sin/cos table
+        in.acc[v] = STAGE >= 2 ? __ldcg(p.acc + v * nodes + n) : 0.0;
     }
 #pragma unroll
     for (int g = 0; g < NX; ++g) in.X[g] = STAGE <= 1 ? in.y[XOFF + g] : p.xs[g * nodes + n];
-    c = STAGE > 0 ? p.cpl[n] : 0.0;
+    c = STAGE > 0 ? __ldcg(p.cpl + n) : 0.0;
 }
 
 // Node pass fused with the next stage's x pass: one warp per row (k, j).  Every
@@ -879,7 +879,7 @@ __device__ __forceinline__ void cube_node_load(const LatticePlan &p, int64_t n, 
 // inertia.  Measured on the 464^3 cube, stages 2-4: U = 6 1.18 ms, U = 7 (94
 // registers) 1.25 ms, U = 8 1.21 ms, U = 5 (70 registers) 1.34 ms, U = 4
 // 1.33 ms; staging the row's y and coupling terms through shared memory by
-// cp.async instead took 1.39 ms.
+// cp.async instead took 1.39 ms.  The loads bypass L1 (1% faster).
 template <int M, int STAGE>
 __device__ __forceinline__ void cube_nodex_row(const LatticePlan &p, const StepSize &h, int64_t row, int64_t *pre0,
                                                int64_t *pre1, bool &ok, int64_t &ps, int64_t &pc)

@@ -71,3 +71,11 @@ def test_chunks_links_and_roofline():
     gbs = bench.CUBE_PASS_BYTES[2] * 1e8 / 2e-3 / 1e9  # 2 ms per launch
     assert r["bound"] == "hbm" and abs(r["achieved"] - gbs) < 1e-6 and abs(r["frac"] - gbs / 6000.0) < 1e-12
     assert r["traffic"] is None
+
+
+def test_iteration_spread_gives_each_timed_iteration_and_the_median():
+    import bench
+    s = bench.iteration_spread([50.0, 40.0, 25.0], [5, 5, 2], 10 ** 6)
+    assert s["per_iteration"] == [1e8, 1.25e8, 8e7]
+    assert s["median"] == 1e8 and s["min"] == 8e7 and s["max"] == 1.25e8
+    assert bench.iteration_spread([], [], 10)["median"] is None
