@@ -849,18 +849,26 @@ def e2e_leg(model, topo, N, R, params, chunks, dt, stream, world=1, seed=2412, r
     barrier(world)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    per_ms = []
     for c in chunks:
+        ti = time.perf_counter()
         net.set_state(pin_in.numpy())
         net.step(c, dt)
         net.get_state(pin_out.numpy())
+        per_ms.append((time.perf_counter() - ti) * 1e3)
     el = max_over_ranks(time.perf_counter() - t0, world)
     net.close()
     steps = sum(chunks)
     state_bytes = 8 * d * n
+    # the host link's rate varies between runs (the copies are ~15% of an
+    # iteration), so every iteration's wall time is reported beside the total
     return {"value": float(n) * steps * world / el, "unit": "node-steps/s",
             "h2d_bytes_per_step": state_bytes * len(chunks) / steps,
             "d2h_bytes_per_step": state_bytes * len(chunks) / steps,
-            "iterations": len(chunks), "rk4_steps": steps}
+            "iterations": len(chunks), "rk4_steps": steps,
+            "per_iteration_ms": per_ms,
+            "median_iteration_value": float(np.median([float(n) * world * c / (ms * 1e-3)
+                                                       for c, ms in zip(chunks, per_ms)]))}
 
 
 # ----------------------------------------------------------------------------- served mix
