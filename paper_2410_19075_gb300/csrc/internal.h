@@ -163,11 +163,11 @@ struct LatticePlan {
     int model, topo, dims;
     int64_t N1, P, nodes;
     int F;            // fixed-point grid of the window sums
-    // cube: the y pass rotates its window sums by -alpha = -(rot_q pi/2 + alpha0),
-    // alpha0 in [0, pi/2): rot_c, rot_s = cos alpha0, sin alpha0 on the grid 2^-63,
-    // the sums shifted up by rot_g bits before the products (cube_rotate)
+    // ball, disk: the x pass rotates every node's (sin, cos) by -alpha =
+    // -(rot_q pi/2 + alpha0), alpha0 in [0, pi/2): rot_c, rot_s = cos alpha0,
+    // sin alpha0 on the grid 2^-63 (lattice_rotated_q)
     uint64_t rot_c, rot_s;
-    int rot_q, rot_g;
+    int rot_q;
     ModelParams mp;
     double *y, *acc;  // D * nodes
     int64_t *f;       // 2 * nodes: sin, cos of the current stage-input phase on the grid 2^-62

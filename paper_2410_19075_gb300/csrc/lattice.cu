@@ -3,15 +3,20 @@
 //   ball  N1^3 nodes, the sphere dx^2 + dy^2 + dz^2 <= P^2 (3D networks);
 //   disk  N1^2 nodes, index j N1 + i, the circle dx^2 + dy^2 <= P^2 (2D networks).
 // f = (sin, cos) of the stage-input phase, rounded onto the grid 2^-F (F chosen
-// so that a full window sum fits in int64) and rotated by -alpha in the x pass
-// (lattice_rotated_q), so every window sum is exact integer arithmetic and the
-// node's right-hand side needs one cross product with its own (sin, cos).
+// so that a full window sum fits in int64), so every window sum is exact
+// integer arithmetic and the node's right-hand side needs one cross product of
+// the sums with its own (sin, cos).  The ball and disk rotate every node's
+// quantity by -alpha in the x pass (lattice_rotated_q); the cube keeps its sums
+// unrotated and turns the node's own phase by +alpha (own_phase_turned).
 //
 // Cube, per RK4 stage (the box is separable):
 //   x pass  SX(i,j,k)  = sum_{|dx|<=P} Q(f(i+dx,j,k))      (row prefix in shared memory)
-//   y pass  SXY(i,j,k) = sum_{|dy|<=P} SX(i,j+dy,k)        (sliding window along j)
-//   z pass  W(i,j,k)   = sum_{|dz|<=P} SXY(i,j,k+dz)       (sliding window along k)
-//           fused with the right-hand side, the RK4 update and the next (sin, cos).
+//   y pass  SXY(i,j,k) = sum_{|dy|<=P} SX(i,j+dy,k)        (column prefix in a tile)
+//   z pass  W(i,j,k)   = sum_{|dz|<=P} SXY(i,j,k+dz)       (column prefix in a tile)
+//           and the coupling term; the node pass then runs the right-hand side,
+//           the RK4 update, the next (sin, cos) and the next stage's x pass.
+//           Batched cubes use sliding windows along j and k instead, the z pass
+//           fused with the node update.
 // Ball and disk, per RK4 stage:
 //   x pass  for every half-width w = 0..P the x-window sums S_w(i) of Q(f) along
 //           every row, sin and cos interleaved; or, when those P+1 arrays would
@@ -123,7 +128,7 @@ __device__ __forceinline__ void lattice_x_fill(const LatticePlan &p, int64_t row
         for (int u = 0; u < 8; ++u) {
             const int64_t m = mb + 32 * u;
             if (m < N1) {
-                if (MODE == 0) { // cube: the y pass rotates the window sums
+                if (MODE == 0) { // cube: the node's own phase is turned instead
                     pre0[m + 1] = q62_to(vs[u], p.F);
                     pre1[m + 1] = q62_to(vc[u], p.F);
                 } else {
@@ -282,28 +287,6 @@ __global__ void __launch_bounds__(32 * kRowWarpsMax)
     if (!ok) raise_error(p.err, ERR_RANGE);
 }
 
-// A cube's y-window sums (sin component ws, cos component wc, on the grid 2^-F)
-// rotated by -alpha = -(rot_q pi/2 + alpha0): the sums shifted up by rot_g bits,
-// four high products with cos alpha0 and sin alpha0 (non-negative, on the grid
-// 2^-63; the products land on the grid 2^-(F + rot_g - 1), fine enough that
-// their truncation leaves no bias a z window could accumulate), rounded to
-// nearest back onto the grid 2^-F, then rot_q quarter turns.  The z window sums
-// of the results are W' of lattice_coupling.
-__device__ __forceinline__ void cube_rotate(const LatticePlan &p, int64_t ws, int64_t wc, int64_t &rs, int64_t &rc)
-{
-    const int g = p.rot_g, sh = g - 1;
-    const int64_t s = (int64_t)((uint64_t)ws << g), c = (int64_t)((uint64_t)wc << g);
-    const int64_t h = int64_t(1) << (sh - 1);
-    const int64_t c1 = (mulhi_su(c, p.rot_c) + mulhi_su(s, p.rot_s) + h) >> sh;
-    const int64_t s1 = (mulhi_su(s, p.rot_c) - mulhi_su(c, p.rot_s) + h) >> sh;
-    switch (p.rot_q) { // e^{-i q pi/2}: 1, -i, -1, i
-    case 0: rc = c1; rs = s1; break;
-    case 1: rc = s1; rs = -c1; break;
-    case 2: rc = -c1; rs = -s1; break;
-    default: rc = -s1; rs = c1; break;
-    }
-}
-
 // Columns of the y and z passes are split into gridDim.z segments of
 // col_seg_len() nodes (small cubes would otherwise run a few thousand threads,
 // each walking its column serially); every segment starts its own sliding
@@ -324,7 +307,7 @@ __host__ __device__ inline int64_t col_seg_len(int64_t N1)
 
 // cube y pass: one thread per segment of an (i, k) column, sliding window along
 // j (exact int64), 8 rows of window loads issued together; writes the window
-// sums rotated by -alpha (cube_rotate).
+// sums.
 __device__ __forceinline__ void cube_y_col(const LatticePlan &p, int64_t i, int64_t k, int64_t seg)
 {
     constexpr int U = 8;
@@ -367,10 +350,8 @@ __device__ __forceinline__ void cube_y_col(const LatticePlan &p, int64_t i, int6
         for (int u = 0; u < U; ++u) {
             const int64_t j = j0 + u;
             if (j < je) {
-                int64_t r0, r1;
-                cube_rotate(p, s0, s1, r0, r1);
-                o0[j * N1] = r0;
-                o1[j * N1] = r1;
+                o0[j * N1] = s0;
+                o1[j * N1] = s1;
             }
             s0 += in0[u] - out0[u];
             s1 += in1[u] - out1[u];
@@ -585,12 +566,20 @@ __device__ __forceinline__ void lattice_node_finish(const LatticePlan &p, int64_
     lattice_node_update<M, STAGE, Acc>(p, n, k, in, h, ok, ps, pc);
 }
 
-template <int M, int STAGE>
+// TURN (the cube): the window sums are unrotated, and the node's own phase is
+// turned by +alpha for the cross product instead (own_phase_turned).
+template <int M, int STAGE, bool TURN = false>
 __device__ __forceinline__ void lattice_node(const LatticePlan &p, int64_t n, int64_t W0, int64_t W1, const StepSize &h,
                                              bool &ok, i128 &ps, i128 &pc)
 {
     LatNodeIn<M> in;
     lattice_node_load<M, STAGE>(p, n, in);
+    if (TURN && STAGE > 0) {
+        int64_t t62[2];
+        own_phase_turned(p.mp, in.f62, t62);
+        in.f62[0] = t62[0];
+        in.f62[1] = t62[1];
+    }
     lattice_node_finish<M, STAGE, i128>(p, n, W0, W1, in, h, ok, ps, pc);
 }
 
@@ -621,7 +610,7 @@ __device__ __forceinline__ void cube_z_col(const LatticePlan &p, const StepSize 
             }
         }
         for (int64_t k = kb; k < ke; ++k) {
-            lattice_node<M, STAGE>(p, col + k * plane, s0, s1, h, ok, ps, pc);
+            lattice_node<M, STAGE, true>(p, col + k * plane, s0, s1, h, ok, ps, pc);
             if (STAGE > 0) {
                 int64_t kin = k + P + 1, kout = k - P;
                 if (kin >= N1) kin -= N1;
@@ -761,8 +750,8 @@ __device__ __forceinline__ int64_t cube_tile_window(const uint64_t *colp, int N1
     return (int64_t)(colp[(unsigned)b << lg] - colp[(unsigned)lo << lg] + ((wb || wl) ? total : 0ull));
 }
 
-// Tiled cube y pass: CTA (ib, k); writes the window sums rotated by -alpha, in
-// the i-block-major layout the z-window pass reads as one contiguous block.
+// Tiled cube y pass: CTA (ib, k); writes the window sums in the i-block-major
+// layout the z-window pass reads as one contiguous block.
 __global__ void __launch_bounds__(kTileThreads) cube_y_tile_kernel(LatticePlan p)
 {
     if (p.skip && *(const volatile int *)p.skip) return;
@@ -785,12 +774,9 @@ __global__ void __launch_bounds__(kTileThreads) cube_y_tile_kernel(LatticePlan p
     const unsigned dstep = (unsigned)N1 << lg;
 #pragma unroll 2
     for (int a = r0; a < N1; a += rstep) {
-        int64_t r0s = 0, r1c = 0;
-        if (ii < bi)
-            cube_rotate(p, cube_tile_window(col0, N1, P, lg, a, t0), cube_tile_window(col1, N1, P, lg, a, t1), r0s,
-                        r1c);
-        d0[(unsigned)a * dstep] = r0s;
-        d1[(unsigned)a * dstep] = r1c;
+        const bool live = ii < bi;
+        d0[(unsigned)a * dstep] = live ? cube_tile_window(col0, N1, P, lg, a, t0) : 0;
+        d1[(unsigned)a * dstep] = live ? cube_tile_window(col1, N1, P, lg, a, t1) : 0;
     }
 }
 
@@ -807,10 +793,10 @@ __global__ void __launch_bounds__(kTileThreads) cube_y_tile_kernel(LatticePlan p
 //                of y, its x sums and its order parameter.
 // The window pass keeps the tile's 64-byte row segments (the z columns are
 // N1^2 elements apart), the node pass reads and writes whole warps of
-// consecutive nodes.  Three window CTAs per SM at the tile sizes of N1 <= 594;
-// 512 threads each measured 1.3% faster than 384 at 464^3 (256: 4-7% slower,
-// whatever the prefetch depth).
-constexpr int kZThreads = 512, kZAhead = 2, kZBlocks = 3; // kZAhead: planes of own (sin, cos) in flight
+// consecutive nodes.  Three window CTAs per SM at the tile sizes of N1 <= 594.
+// At 464^3: 384 threads 0.875 ms, 512 threads 0.918 ms (42 registers, a spill),
+// three planes of prefetch 0.900 ms.
+constexpr int kZThreads = 384, kZAhead = 2, kZBlocks = 3; // kZAhead: planes of own (sin, cos) in flight
 
 __global__ void __launch_bounds__(kZThreads, kZBlocks) cube_zw_tile_kernel(LatticePlan p)
 {
@@ -843,7 +829,9 @@ __global__ void __launch_bounds__(kZThreads, kZBlocks) cube_zw_tile_kernel(Latti
         const int an = a + kZAhead * rstep;
         f[kZAhead][0] = an < N1 ? fs[(unsigned)an * plane] : 0;
         f[kZAhead][1] = an < N1 ? fc[(unsigned)an * plane] : 0;
-        cpl[(unsigned)a * plane] = lattice_coupling_term(p.mp, f[0], cube_tile_window(col0, N1, P, lg, a, t0),
+        int64_t t62[2];
+        own_phase_turned(p.mp, f[0], t62);
+        cpl[(unsigned)a * plane] = lattice_coupling_term(p.mp, t62, cube_tile_window(col0, N1, P, lg, a, t0),
                                                          cube_tile_window(col1, N1, P, lg, a, t1));
 #pragma unroll
         for (int d = 0; d < kZAhead; ++d) {

@@ -33,10 +33,12 @@ struct ModelParams {
 
 template <int M> struct Model;
 
-// Kuramoto coupling on a lattice.  The window sums arrive rotated by -alpha:
-// W' = W'c + i W's = sum over the window (the node itself included) of
-// e^{-i alpha} Q(e^{i phi_j}), int64 on the grid 2^-F (the ball and disk x pass
-// rotates every node's quantity, the cube y pass its window sums).  Then
+// Kuramoto coupling on a lattice.  On the ball and disk the window sums arrive
+// rotated by -alpha: W' = W'c + i W's = sum over the window (the node itself
+// included) of e^{-i alpha} Q(e^{i phi_j}), int64 on the grid 2^-F (their x pass
+// rotates every node's quantity).  The cube keeps its sums unrotated and turns
+// the node's own phase by +alpha instead (own_phase_turned), which gives the
+// same T.  Then
 //   T = Im[e^{-i phi_i} W'] = cos(phi_i) W's - sin(phi_i) W'c
 //     = sum_j sin(phi_j - phi_i - alpha)   (the node's own term is -sin alpha),
 // two 64 x 64 high products of the node's own (sin, cos) on the grid 2^-62 with
@@ -48,6 +50,29 @@ template <int M> struct Model;
 __device__ __forceinline__ double lattice_coupling(const int64_t (&f62)[2], int64_t W0, int64_t W1)
 {
     return __ll2double_rn(mulhi_ss(f62[1], W0) - mulhi_ss(f62[0], W1));
+}
+
+// The node's own (sin, cos) on the grid 2^-62 turned by +alpha = aq pi/2 +
+// alpha0: e^{i alpha0} (c + i s) by four high products with the non-negative cos
+// alpha0, sin alpha0 (grid 2^-63, landing on 2^-61), back onto 2^-62 by one bit
+// (|values| <= 1, so they stay below 2^62 + 2), then aq quarter turns.  With
+// the turned phase the cross product of lattice_coupling takes the unrotated
+// window sums: Im[e^{-i(phi + alpha)} S] = Im[e^{-i phi} e^{-i alpha} S] (the
+// cube; the ball and disk rotate their sums instead).
+__device__ __forceinline__ void own_phase_turned(const ModelParams &P, const int64_t (&f62)[2], int64_t (&t62)[2])
+{
+    const int64_t s = f62[0], c = f62[1];
+    const int64_t c1 = mulhi_su(c, P.a0[0]) - mulhi_su(s, P.a0[1]);
+    const int64_t s1 = mulhi_su(s, P.a0[0]) + mulhi_su(c, P.a0[1]);
+    int64_t ca, sa;
+    switch (P.aq) { // times i^aq
+    case 0: ca = c1; sa = s1; break;
+    case 1: ca = -s1; sa = c1; break;
+    case 2: ca = -c1; sa = -s1; break;
+    default: ca = s1; sa = -c1; break;
+    }
+    t62[0] = (int64_t)((uint64_t)sa << 1);
+    t62[1] = (int64_t)((uint64_t)ca << 1);
 }
 
 // Both Kuramoto models' coupling term on a lattice, c[5] T + c[4] (the whole

@@ -422,8 +422,10 @@ void simk::ring_coupling_constants(ModelParams &mp, int model, int F)
     mp.c[5] = std::ldexp(model == SIM_KS ? mp.c[1] : mp.c[0], mp.ksh + 3 - F);
 }
 
-// A lattice's rotation of the window sums by -alpha and the scale of the
-// right-hand side's cross product (see lattice_coupling and cube_rotate).
+// A lattice's rotation by -alpha (the ball's and disk's x pass rotate every
+// node's (sin, cos); the cube turns the node's own phase by +alpha with the
+// model's a0, aq instead) and the scale of the right-hand side's cross product
+// (see lattice_coupling).
 void simk::lattice_rotation(LatticePlan &p, double alpha)
 {
     const long double half_pi = 1.570796326794896619231321691639751442L;
@@ -436,9 +438,6 @@ void simk::lattice_rotation(LatticePlan &p, double alpha)
     p.rot_s = (uint64_t)roundl(fminl(fmaxl(s0, 0.0L), 1.0L) * two63);
     long long qi = (long long)q % 4;
     p.rot_q = (int)(qi < 0 ? qi + 4 : qi);
-    // shift of the y-window sums (|W| <= (2P+1)^2 2^F) that keeps them below 2^62
-    const int g = 62 - p.F - ceil_log2((uint64_t)((2 * p.P + 1) * (2 * p.P + 1)));
-    p.rot_g = g < 10 ? g : 10;
     // the cross product T lands on the grid 2^-(F-2): fold that scale into the coefficient
     p.mp.c[5] = std::ldexp(p.model == SIM_KS ? p.mp.c[1] : p.mp.c[0], -(p.F - 2));
 }
