@@ -170,7 +170,7 @@ struct LatticePlan {
     int rot_q;
     ModelParams mp;
     double *y, *acc;  // D * nodes
-    int64_t *f;       // 2 * nodes: sin, cos of the current stage-input phase on the grid 2^-62
+    int64_t *f;       // nodes (sin, cos) pairs (f[2n], f[2n+1]) of the current stage-input phase on the grid 2^-62
     double *xs;       // NX * nodes: local stage-input variables (psi of model 3)
     int64_t *sx;      // cube: 2 * nodes window sums along x (SoA); ball, disk: per row,
                       // rs (sin, cos) pairs of the periodically extended inclusive
@@ -207,7 +207,7 @@ struct ElemDpPlan {
     double *err_part;    // nblk
     i128 *out_part;      // nblk * kDpMaxOut * 2
     unsigned long long *dp_ctr;
-    int64_t *f;          // lattices: (sin, cos) of the stage input's phase on the grid 2^-62 (else nullptr)
+    int64_t *f;          // lattices: (sin, cos) pairs of the stage input's phase on the grid 2^-62 (else nullptr)
     MathTables tab;
     int F;               // fixed-point grid of the dense order-parameter sums
     double *obs;

@@ -65,6 +65,9 @@ static int row_warps(int64_t N1)
 // prefix rows of a CTA round up to less of the SM (seven CTAs of four 464-node
 // rows, against three of eight).
 constexpr int kNodexWarpsMax = 4;
+// CTAs per SM the fused node pass is compiled for: six for Kuramoto (at most 80
+// registers, so stage 4 fits six too), five for the model with inertia.
+template <int M> constexpr int kNodexBlocks = M == 0 ? 6 : 5;
 static int nodex_warps(int64_t N1)
 {
     const int w = row_warps(N1);
@@ -114,15 +117,15 @@ __device__ __forceinline__ void lattice_x_fill(const LatticePlan &p, int64_t row
 {
     const int lane = threadIdx.x & 31;
     const int64_t N1 = p.N1, nodes = p.nodes;
-    const int64_t *__restrict__ fs = p.f + row * N1;
-    const int64_t *__restrict__ fc = p.f + nodes + row * N1;
+    const longlong2 *__restrict__ fr = reinterpret_cast<const longlong2 *>(p.f) + row * N1; // (sin, cos) pairs
     for (int64_t mb = lane; mb < N1; mb += 32 * 8) { // coalesced, 8 loads in flight per lane
         int64_t vs[8], vc[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             const int64_t m = mb + 32 * u;
-            vs[u] = m < N1 ? __ldg(fs + m) : 0;
-            vc[u] = m < N1 ? __ldg(fc + m) : 0;
+            const longlong2 v = m < N1 ? __ldg(fr + m) : make_longlong2(0, 0);
+            vs[u] = v.x;
+            vc[u] = v.y;
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
@@ -496,8 +499,9 @@ __device__ __forceinline__ void lattice_node_load(const LatticePlan &p, int64_t 
         in.acc[v] = STAGE >= 2 ? p.acc[v * nodes + n] : 0.0;
     }
     if (STAGE > 0) {
-        in.f62[0] = p.f[n];
-        in.f62[1] = p.f[nodes + n];
+        const longlong2 v = reinterpret_cast<const longlong2 *>(p.f)[n];
+        in.f62[0] = v.x;
+        in.f62[1] = v.y;
 #pragma unroll
         for (int g = 0; g < NX; ++g) in.X[g] = STAGE == 1 ? in.y[XOFF + g] : p.xs[g * nodes + n];
     }
@@ -542,8 +546,7 @@ __device__ __forceinline__ void lattice_node_update(const LatticePlan &p, int64_
     }
     int64_t s62, c62;
     fixed_sincos(xn[0], p.mp.tab, s62, c62, ok);
-    p.f[n] = s62;
-    p.f[nodes + n] = c62;
+    reinterpret_cast<longlong2 *>(p.f)[n] = make_longlong2(s62, c62);
     if (STAGE == 0 || STAGE == 4) {
         ps += q62_to(s62, p.F);
         pc += q62_to(c62, p.F);
@@ -815,20 +818,21 @@ __global__ void __launch_bounds__(kZThreads, kZBlocks) cube_zw_tile_kernel(Latti
     const unsigned cstride = (unsigned)(N1 + 1) << lg;
     const uint64_t *col0 = tile + ii, *col1 = tile + cstride + ii;
     const uint64_t t0 = col0[(unsigned)N1 << lg], t1 = col1[(unsigned)N1 << lg];
-    const int64_t *__restrict__ fs = p.f + base + ii;
-    const int64_t *__restrict__ fc = fs + p.nodes;
+    const longlong2 *__restrict__ fp = reinterpret_cast<const longlong2 *>(p.f) + base + ii; // (sin, cos) pairs
     double *__restrict__ cpl = p.cpl + base + ii;
     int64_t f[kZAhead + 1][2]; // own (sin, cos) of the planes a, a + rstep, ...
 #pragma unroll
     for (int d = 0; d < kZAhead; ++d) {
         const int ad = r0 + d * rstep;
-        f[d][0] = ad < N1 ? fs[(unsigned)ad * plane] : 0;
-        f[d][1] = ad < N1 ? fc[(unsigned)ad * plane] : 0;
+        const longlong2 v = ad < N1 ? fp[(unsigned)ad * plane] : make_longlong2(0, 0);
+        f[d][0] = v.x;
+        f[d][1] = v.y;
     }
     for (int a = r0; a < N1; a += rstep) {
         const int an = a + kZAhead * rstep;
-        f[kZAhead][0] = an < N1 ? fs[(unsigned)an * plane] : 0;
-        f[kZAhead][1] = an < N1 ? fc[(unsigned)an * plane] : 0;
+        const longlong2 v = an < N1 ? fp[(unsigned)an * plane] : make_longlong2(0, 0);
+        f[kZAhead][0] = v.x;
+        f[kZAhead][1] = v.y;
         int64_t t62[2];
         own_phase_turned(p.mp, f[0], t62);
         cpl[(unsigned)a * plane] = lattice_coupling_term(p.mp, t62, cube_tile_window(col0, N1, P, lg, a, t0),
@@ -863,8 +867,8 @@ __device__ __forceinline__ void cube_node_load(const LatticePlan &p, int64_t n, 
 // reads.  In stage 4 (and the prologue, STAGE 0: the (sin, cos) of y, no
 // update) the row's sums give the order parameter.
 // The loads go through registers, U nodes of a lane ahead: six for Kuramoto
-// (78 registers in stages 2-3, six CTAs per SM), four for the model with
-// inertia.  Measured on the 464^3 cube, stages 2-4: U = 6 1.18 ms, U = 7 (94
+// (compiled for six CTAs per SM, at most 80 registers), four for the model
+// with inertia.  Measured on the 464^3 cube, stages 2-4: U = 6 1.18 ms, U = 7 (94
 // registers) 1.25 ms, U = 8 1.21 ms, U = 5 (70 registers) 1.34 ms, U = 4
 // 1.33 ms; staging the row's y and coupling terms through shared memory by
 // cp.async instead took 1.39 ms.  The loads bypass L1 (1% faster).
@@ -879,7 +883,7 @@ __device__ __forceinline__ void cube_nodex_row(const LatticePlan &p, const StepS
     LatticePlan q = p;
     q.y += base;
     q.acc += base;
-    q.f += base;
+    q.f += 2 * base; // (sin, cos) pairs
     q.cpl += base;
     if (Model<M>::NX > 0) q.xs += base;
     for (int mb = lane; mb < n1; mb += 32 * U) {
@@ -913,7 +917,7 @@ __device__ __forceinline__ void cube_nodex_row(const LatticePlan &p, const StepS
 }
 
 template <int M, int STAGE>
-__global__ void __launch_bounds__(32 * kNodexWarpsMax) cube_nodex_kernel(LatticePlan p, const StepSize h)
+__global__ void __launch_bounds__(32 * kNodexWarpsMax, kNodexBlocks<M>) cube_nodex_kernel(LatticePlan p, const StepSize h)
 {
     if (p.skip && *(const volatile int *)p.skip) return;
     extern __shared__ int64_t smem[];

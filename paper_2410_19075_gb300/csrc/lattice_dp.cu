@@ -51,8 +51,7 @@ __global__ void __launch_bounds__(kLdpThreads) lat_dp_input_kernel(const ElemDpP
         int64_t s62, c62;
         bool ok = true;
         fixed_sincos(phase, d.tab, s62, c62, ok);
-        d.f[n] = s62;
-        d.f[nodes + n] = c62;
+        reinterpret_cast<longlong2 *>(d.f)[n] = make_longlong2(s62, c62); // (sin, cos) pairs
         if (!ok) raise_error(d.err, ERR_RANGE);
     }
 }
