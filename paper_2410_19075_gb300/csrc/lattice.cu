@@ -797,9 +797,10 @@ __global__ void __launch_bounds__(kTileThreads) cube_y_tile_kernel(LatticePlan p
 // The window pass keeps the tile's 64-byte row segments (the z columns are
 // N1^2 elements apart), the node pass reads and writes whole warps of
 // consecutive nodes.  Three window CTAs per SM at the tile sizes of N1 <= 594.
-// At 464^3: 384 threads 0.875 ms, 512 threads 0.918 ms (42 registers, a spill),
-// three planes of prefetch 0.900 ms.
-constexpr int kZThreads = 384, kZAhead = 2, kZBlocks = 3; // kZAhead: planes of own (sin, cos) in flight
+// At 464^3 (interleaved (sin, cos) pairs): two planes per unrolled iteration
+// with three planes of prefetch 0.826 ms, two planes of prefetch 0.831 ms, one
+// plane per iteration 0.860 ms; 512 threads (at most 42 registers) 0.884 ms.
+constexpr int kZThreads = 384, kZAhead = 3, kZBlocks = 3; // kZAhead: planes of own (sin, cos) in flight
 
 __global__ void __launch_bounds__(kZThreads, kZBlocks) cube_zw_tile_kernel(LatticePlan p)
 {
@@ -828,6 +829,7 @@ __global__ void __launch_bounds__(kZThreads, kZBlocks) cube_zw_tile_kernel(Latti
         f[d][0] = v.x;
         f[d][1] = v.y;
     }
+#pragma unroll 2 // two planes' independent chains interleaved
     for (int a = r0; a < N1; a += rstep) {
         const int an = a + kZAhead * rstep;
         const longlong2 v = an < N1 ? fp[(unsigned)an * plane] : make_longlong2(0, 0);
