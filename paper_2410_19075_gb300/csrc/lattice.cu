@@ -775,7 +775,7 @@ __global__ void __launch_bounds__(kTileThreads) cube_y_tile_kernel(LatticePlan p
     int64_t *__restrict__ d0 = p.sxy + (((int64_t)blockIdx.x * N1) * N1 + k) * BI + ii;
     int64_t *__restrict__ d1 = d0 + cube_sxy_cstride(N1);
     const unsigned dstep = (unsigned)N1 << lg;
-#pragma unroll 2
+#pragma unroll 4 // 464^3: 0.493 ms, against 0.515 (unroll 2) and 0.516-0.517 (6, 8)
     for (int a = r0; a < N1; a += rstep) {
         const bool live = ii < bi;
         d0[(unsigned)a * dstep] = live ? cube_tile_window(col0, N1, P, lg, a, t0) : 0;
