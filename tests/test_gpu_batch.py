@@ -218,3 +218,29 @@ def test_batched_cubes_of_both_models_equal_plain():
     finally:
         for n in nets:
             n.close()
+
+
+def test_cube_stepped_alone_and_in_batches_in_turn_equals_alone():
+    """Between steps a cube holds its state, the (sin, cos) of it and its x-window
+    sums, whichever path stepped it: steps alone (tiled passes), steps in a
+    batch (sliding passes) and a right-hand-side evaluation, in turn, give the
+    same bits as steps alone."""
+    from paper_2410_19075_gb300 import CUBE3D, KS, KSI, Batch, Network
+    for model, N1, P, params in ((KS, 20, 4, I.ks_params(alpha=1.52)), (KSI, 15, 3, I.ksi_params(mu=1.0))):
+        n = N1 ** 3
+        y0 = I.initial_state(model, 1300 + model, 0, n)
+        ref, ref_order = _alone(model, CUBE3D, N1, P, params, y0, 25)
+        with Network(model, CUBE3D, N1, P, params) as net:
+            net.set_state(y0)
+            net.step(7, 0.01)
+            with Batch([net]) as b:
+                b.step(9, 0.01)
+                b.sync()
+            net.rhs()  # evaluates f(y) without changing the state
+            net.step(5, 0.01)
+            with Batch([net]) as b:
+                b.step(4, 0.01)
+                b.sync()
+            y, order = net.get_state(), net.observables()
+        assert np.array_equal(y, ref), model
+        assert np.array_equal(order, ref_order), model
